@@ -1,0 +1,313 @@
+"""FP64 CPU oracle for PIMD with a symmetry-function neural-network potential.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's cpu_baseline / reference legs are its only users. It is a plain,
+slow restatement of the method (paper Sec. 2.1 ring-polymer Hamiltonian,
+normal modes and estimators; descriptor-based energy model of Sec. 1 / ref.
+[17] with forces as the energy gradient, Sec. 2.2; PILE-L of Tables S2-S3) in
+C, loaded through ctypes. It shares no code with the CUDA library.
+
+Parity pins live in tests/test_oracle_*.py. Parts without an independent pin:
+long-time trajectory physics of the random-init network (parity unpinned).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ND = 64
+MAX_ELEM = 8
+MAX_LAYERS = 8
+
+_lib = None
+
+
+class OrModel(ct.Structure):
+    _fields_ = [
+        ("n_elem", ct.c_int),
+        ("Z", ct.c_int * MAX_ELEM),
+        ("n_hidden", ct.c_int),
+        ("width", ct.c_int * MAX_LAYERS),
+        ("params", ct.POINTER(ct.c_double) * MAX_ELEM),
+        ("rc", ct.c_double),
+        ("eta_R", ct.c_double),
+        ("r_mu", ct.c_double * 32),
+        ("zeta", ct.c_int * 4),
+        ("lam", ct.c_double * 2),
+        ("eta_A", ct.c_double * 4),
+    ]
+
+
+class OrSys(ct.Structure):
+    _fields_ = [
+        ("N", ct.c_int), ("P", ct.c_int),
+        ("Z", ct.POINTER(ct.c_int)),
+        ("mass", ct.POINTER(ct.c_double)),
+        ("box", ct.c_double * 3),
+        ("T", ct.c_double),
+        ("seed", ct.c_uint64),
+        ("replica", ct.c_int),
+        ("dt", ct.c_double),
+        ("gamma0", ct.c_double),
+        ("pile_lambda", ct.c_double),
+        ("thermostat", ct.c_int),
+        ("potential", ct.c_int),
+        ("omega_harm", ct.c_double),
+        ("maxnb", ct.c_int),
+    ]
+
+
+class OrEst(ct.Structure):
+    _fields_ = [("V_mean", ct.c_double), ("K_prim", ct.c_double), ("K_cv", ct.c_double),
+                ("E_tot", ct.c_double), ("W", ct.c_double * 9), ("H_cons", ct.c_double),
+                ("Q_thermo", ct.c_double), ("T_kin", ct.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k in ("V_mean", "K_prim", "K_cv", "E_tot", "H_cons", "Q_thermo", "T_kin")}
+        d["W"] = np.array(list(self.W)).reshape(3, 3)
+        return d
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        dp = ct.POINTER(ct.c_double)
+        ip = ct.POINTER(ct.c_int)
+        L.or_neighbours.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_int, ip, ip]
+        L.or_descriptors.argtypes = [ct.POINTER(OrModel), ct.c_int, dp, dp, ip, ip, ct.c_int, dp]
+        L.or_mlp.argtypes = [ct.POINTER(OrModel), ct.c_int, dp, dp]
+        L.or_mlp.restype = ct.c_double
+        L.or_energy_forces.argtypes = [ct.POINTER(OrModel), ct.c_int, ip, dp, dp, ct.c_int, dp, dp, dp]
+        L.or_energy_forces_batch.argtypes = [ct.POINTER(OrModel), ct.c_int, ct.c_int, ip, dp, dp,
+                                             ct.c_int, dp, dp, dp]
+        L.or_nm_matrix.argtypes = [ct.c_int, dp]
+        L.or_nm_freqs.argtypes = [ct.c_int, ct.c_double, dp]
+        u32p = ct.POINTER(ct.c_uint32)
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_normal.argtypes = [ct.c_uint64, ct.c_uint32, ct.c_uint32, ct.c_uint32, ct.c_uint32]
+        L.or_normal.restype = ct.c_double
+        L.or_init.argtypes = [ct.POINTER(OrSys), dp, dp, dp]
+        L.or_forces.argtypes = [ct.POINTER(OrSys), ct.POINTER(OrModel), dp, dp, dp, dp, dp]
+        L.or_step.argtypes = [ct.POINTER(OrSys), ct.POINTER(OrModel), ct.c_int, ct.POINTER(ct.c_uint64),
+                              dp, dp, dp, dp, dp, dp]
+        L.or_estimators.argtypes = [ct.POINTER(OrSys), dp, dp, dp, dp, dp, ct.c_double, ct.POINTER(OrEst)]
+        L.or_set_threads.argtypes = [ct.c_int]
+        L.or_get_threads.restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ct.POINTER(ct.c_int))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _box(box) -> np.ndarray:
+    return _f64(box if box is not None else (0.0, 0.0, 0.0))
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().or_get_threads())
+
+
+class ModelHandle:
+    """ctypes view of a synth.Model (keeps its parameter blobs alive)."""
+
+    def __init__(self, model):
+        self.model = model
+        s = OrModel()
+        s.n_elem = len(model.elements)
+        self._blobs = []
+        for e, z in enumerate(model.elements):
+            s.Z[e] = int(z)
+            b = _f64(model.params[z])
+            self._blobs.append(b)
+            s.params[e] = _dp(b)
+        s.n_hidden = len(model.widths)
+        for l, w in enumerate(model.widths):
+            s.width[l] = int(w)
+        d = model.desc
+        s.rc = d["cutoff"]
+        s.eta_R = d["eta_R"]
+        for m, r in enumerate(d["r_mu"]):
+            s.r_mu[m] = r
+        for k, z in enumerate(d["zeta"]):
+            s.zeta[k] = int(z)
+        for k, l in enumerate(d["lam"]):
+            s.lam[k] = l
+        for k, e in enumerate(d["eta_A"]):
+            s.eta_A[k] = e
+        self.s = s
+
+    @property
+    def ptr(self):
+        return ct.byref(self.s)
+
+
+def neighbours(x, box, rc: float, maxnb: int = 256):
+    """Sorted neighbour sets under the exact FP32 inclusion rule."""
+    x = _f64(x)
+    n = len(x)
+    nbr = np.zeros((n, maxnb), dtype=np.int32)
+    nnb = np.zeros(n, dtype=np.int32)
+    worst = lib().or_neighbours(n, _dp(x), _dp(_box(box)), rc, maxnb, _ip(nbr), _ip(nnb))
+    if worst > maxnb:
+        raise ValueError("neighbour overflow: %d > %d" % (worst, maxnb))
+    return [nbr[i, :nnb[i]].copy() for i in range(n)], nbr, nnb
+
+
+def descriptors(model, x, box, maxnb: int = 256) -> np.ndarray:
+    mh = model if isinstance(model, ModelHandle) else ModelHandle(model)
+    x = _f64(x)
+    _, nbr, nnb = neighbours(x, box, mh.model.desc["cutoff"], maxnb)
+    G = np.zeros((len(x), ND))
+    lib().or_descriptors(mh.ptr, len(x), _dp(x), _dp(_box(box)), _ip(nbr), _ip(nnb), maxnb, _dp(G))
+    return G
+
+
+def mlp(model, z: int, G) -> tuple[float, np.ndarray]:
+    mh = model if isinstance(model, ModelHandle) else ModelHandle(model)
+    G = _f64(G)
+    g = np.zeros(ND)
+    E = lib().or_mlp(mh.ptr, int(z), _dp(G), _dp(g))
+    return E, g
+
+
+def energy_forces(model, Z, x, box, maxnb: int = 256):
+    """Per-atom energies E_i (eV), forces -dV/dx (eV/A), virial W (eV)."""
+    mh = model if isinstance(model, ModelHandle) else ModelHandle(model)
+    x = _f64(x)
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    n = len(x)
+    E = np.zeros(n)
+    F = np.zeros((n, 3))
+    W = np.zeros(9)
+    r = lib().or_energy_forces(mh.ptr, n, _ip(Z), _dp(x), _dp(_box(box)), maxnb, _dp(E), _dp(F), _dp(W))
+    if r < 0:
+        raise ValueError("oracle energy_forces failed (%d)" % r)
+    return E, F, W.reshape(3, 3)
+
+
+def energy_forces_batch(model, Z, xs, box, maxnb: int = 256):
+    mh = model if isinstance(model, ModelHandle) else ModelHandle(model)
+    xs = _f64(xs)
+    nconf, n = xs.shape[0], xs.shape[1]
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    E = np.zeros((nconf, n))
+    F = np.zeros((nconf, n, 3))
+    W = np.zeros((nconf, 9))
+    r = lib().or_energy_forces_batch(mh.ptr, nconf, n, _ip(Z), _dp(xs), _dp(_box(box)), maxnb,
+                                     _dp(E), _dp(F), _dp(W))
+    if r < 0:
+        raise ValueError("oracle energy_forces failed (%d)" % r)
+    return E, F, W.reshape(nconf, 3, 3)
+
+
+def nm_matrix(P: int) -> np.ndarray:
+    C = np.zeros((P, P))
+    lib().or_nm_matrix(P, _dp(C))
+    return C
+
+
+def nm_freqs(P: int, omega_P: float) -> np.ndarray:
+    w = np.zeros(P)
+    lib().or_nm_freqs(P, omega_P, _dp(w))
+    return w
+
+
+def philox(ctr, key) -> tuple:
+    c = (ct.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ct.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ct.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return tuple(int(v) for v in o)
+
+
+def normal(seed: int, index: int, step: int, replica: int, stream: int) -> float:
+    return float(lib().or_normal(seed, index, step, replica, stream))
+
+
+class System:
+    """One ring-polymer system advanced by the oracle integrator.
+
+    potential = "model" (symmetry-function network) or "harmonic" with
+    angular frequency omega (1/fs)."""
+
+    def __init__(self, replica, masses: dict, dt: float, gamma0: float, pile_lambda: float = 1.0,
+                 model=None, thermostat: bool = True, potential: str = "model", omega: float = 0.0,
+                 replica_index: int = 0, maxnb: int = 256):
+        self.mh = None if model is None else (model if isinstance(model, ModelHandle) else ModelHandle(model))
+        self.Z = np.ascontiguousarray(replica.Z, dtype=np.int32)
+        self.mass = _f64([masses[int(z)] for z in replica.Z])
+        N, P = len(self.Z), int(replica.n_beads)
+        s = OrSys()
+        s.N, s.P = N, P
+        s.Z = _ip(self.Z)
+        s.mass = _dp(self.mass)
+        for a in range(3):
+            s.box[a] = float(replica.box[a])
+        s.T = float(replica.T)
+        s.seed = int(replica.seed)
+        s.replica = int(replica_index)
+        s.dt = float(dt)
+        s.gamma0 = float(gamma0)
+        s.pile_lambda = float(pile_lambda)
+        s.thermostat = 1 if thermostat else 0
+        s.potential = 1 if potential == "harmonic" else 0
+        s.omega_harm = float(omega)
+        s.maxnb = int(maxnb)
+        self.s = s
+        self.N, self.P = N, P
+        self.q = np.zeros((P, N, 3))
+        self.p = np.zeros((P, N, 3))
+        self.f = np.zeros((P, N, 3))
+        self.xb = np.zeros((P, N, 3))
+        self.V = np.zeros(P)
+        self.W = np.zeros((P, 9))
+        self.Q = ct.c_double(0.0)
+        self.step_count = ct.c_uint64(0)
+        x0 = _f64(replica.x0)
+        lib().or_init(ct.byref(s), _dp(x0), _dp(self.q), _dp(self.p))
+        self.compute_forces()
+
+    def _mptr(self):
+        return self.mh.ptr if self.mh is not None else None
+
+    def compute_forces(self):
+        r = lib().or_forces(ct.byref(self.s), self._mptr(), _dp(self.q), _dp(self.xb), _dp(self.f),
+                            _dp(self.V), _dp(self.W))
+        if r < 0:
+            raise ValueError("oracle forces failed (%d)" % r)
+
+    def step(self, n: int = 1):
+        r = lib().or_step(ct.byref(self.s), self._mptr(), int(n), ct.byref(self.step_count), _dp(self.q),
+                          _dp(self.p), _dp(self.f), _dp(self.V), _dp(self.W), ct.byref(self.Q))
+        if r < 0:
+            raise ValueError("oracle step failed (%d)" % r)
+
+    def beads(self) -> np.ndarray:
+        C = nm_matrix(self.P)
+        return np.einsum("jk,kia->jia", C, self.q)
+
+    def estimators(self) -> dict:
+        e = OrEst()
+        lib().or_estimators(ct.byref(self.s), _dp(self.q), _dp(self.p), _dp(self.f), _dp(self.V),
+                            _dp(self.W), self.Q.value, ct.byref(e))
+        return e.as_dict()

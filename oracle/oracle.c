@@ -1,0 +1,643 @@
+/*
+ * oracle.c -- FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see oracle.h).
+ *
+ * Every routine follows a definition literally, in the order the method
+ * states it: no blocking, fusion or reordering beyond the definition.
+ *   - ring-polymer Hamiltonian, normal modes, estimator: paper Sec. 2.1;
+ *   - descriptor + per-element network energy and its gradient (forces as
+ *     -dE/dx of an energy model): Sec. 1 (BPNN, ref. [17]) and Sec. 2.2;
+ *   - thermostat: PILE-L named in Tables of Sec. S2/S3 (Ceriotti et al. 2010);
+ *   - noise: Philox4x32-10 (Salmon et al., SC'11) + Box-Muller.
+ * Compile with -O2 -ffp-contract=off (no fast-math): the neighbour rule is an
+ * exact FP32 computation that must not be contracted into FMAs.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#else
+static int omp_in_parallel(void) { return 0; }
+#endif
+
+/* physical constants (CODATA 2018) */
+static const double KB = 8.617333262e-5;          /* eV / K                  */
+static const double HBAR = 0.6582119569;          /* eV fs                   */
+static const double MVV2E = 103.64269652680505;   /* eV per amu A^2 fs^-2    */
+
+static int g_threads = 0;
+
+void or_set_threads(int n) { g_threads = n; }
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* neighbour rule: FP32, no contraction, fixed operation order               */
+/* ------------------------------------------------------------------------ */
+int or_neighbours(int n, const double* x, const double* box, double rc, int maxnb,
+                  int* nbr, int* nnb)
+{
+    int periodic = box != NULL && box[0] > 0.0;
+    float L32[3], inv32[3];
+    for (int d = 0; d < 3; ++d) {
+        L32[d] = periodic ? (float)box[d] : 0.0f;
+        inv32[d] = periodic ? (float)(1.0 / box[d]) : 0.0f;
+    }
+    float rc2 = (float)(rc * rc);
+    int worst = 0;
+#pragma omp parallel for num_threads(or_get_threads()) reduction(max : worst) if (!omp_in_parallel())
+    for (int i = 0; i < n; ++i) {
+        float xi[3] = {(float)x[3 * i], (float)x[3 * i + 1], (float)x[3 * i + 2]};
+        int cnt = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            float dd[3];
+            for (int d = 0; d < 3; ++d) {
+                float t = (float)x[3 * j + d] - xi[d];
+                if (periodic) {
+                    float k = rintf(t * inv32[d]);
+                    float s = L32[d] * k;
+                    t = t - s;
+                }
+                dd[d] = t;
+            }
+            float r2 = dd[0] * dd[0];
+            float yy = dd[1] * dd[1];
+            float zz = dd[2] * dd[2];
+            r2 = r2 + yy;
+            r2 = r2 + zz;
+            if (r2 < rc2) {
+                if (cnt < maxnb) nbr[(size_t)i * maxnb + cnt] = j;
+                ++cnt;
+            }
+        }
+        nnb[i] = cnt;
+        if (cnt > worst) worst = cnt;
+    }
+    return worst;
+}
+
+/* ------------------------------------------------------------------------ */
+/* geometry and symmetry functions                                          */
+/* ------------------------------------------------------------------------ */
+static void min_image(const double* xi, const double* xj, const double* box, double* d)
+{
+    for (int a = 0; a < 3; ++a) {
+        d[a] = xj[a] - xi[a];
+        if (box != NULL && box[0] > 0.0) d[a] -= box[a] * nearbyint(d[a] / box[a]);
+    }
+}
+
+/* Behler cosine cutoff and its derivative */
+static double cutoff_fn(double r, double rc) { return r < rc ? 0.5 * (cos(M_PI * r / rc) + 1.0) : 0.0; }
+static double cutoff_dr(double r, double rc) { return r < rc ? -0.5 * M_PI / rc * sin(M_PI * r / rc) : 0.0; }
+
+static double ipow(double b, int e)
+{
+    double p = 1.0;
+    for (int k = 0; k < e; ++k) p *= b;
+    return p;
+}
+
+/* angular channel nu = (zeta_index * 2 + lambda_index) * 4 + eta_index */
+static void channel(const or_model* m, int nu, int* zeta, double* lambda, double* eta)
+{
+    *zeta = m->zeta[nu / 8];
+    *lambda = m->lambda[(nu / 4) % 2];
+    *eta = m->eta_A[nu % 4];
+}
+
+/* G2_mu = sum_j exp(-eta_R (r_ij - r_mu)^2) fc(r_ij)
+ * G5_nu = 2^(1-zeta) sum_{j<k} (1 + lambda cos theta_jik)^zeta
+ *                       exp(-eta (r_ij^2 + r_ik^2)) fc(r_ij) fc(r_ik)        */
+static void descriptor_atom(const or_model* m, const double* x, const double* box, int i,
+                            const int* nb, int cnt, double* G)
+{
+    for (int c = 0; c < OR_ND; ++c) G[c] = 0.0;
+    for (int s = 0; s < cnt; ++s) {
+        double d[3];
+        min_image(x + 3 * i, x + 3 * nb[s], box, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int mu = 0; mu < OR_NR; ++mu) {
+            double t = r - m->r_mu[mu];
+            G[mu] += exp(-m->eta_R * t * t) * cutoff_fn(r, m->rc);
+        }
+    }
+    for (int s = 0; s < cnt; ++s) {
+        for (int t = s + 1; t < cnt; ++t) {
+            double dj[3], dk[3];
+            min_image(x + 3 * i, x + 3 * nb[s], box, dj);
+            min_image(x + 3 * i, x + 3 * nb[t], box, dk);
+            double rj = sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
+            double rk = sqrt(dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2]);
+            double cth = (dj[0] * dk[0] + dj[1] * dk[1] + dj[2] * dk[2]) / (rj * rk);
+            for (int nu = 0; nu < OR_NA; ++nu) {
+                int zeta;
+                double lam, eta;
+                channel(m, nu, &zeta, &lam, &eta);
+                G[OR_NR + nu] += pow(2.0, 1 - zeta) * ipow(1.0 + lam * cth, zeta) *
+                                 exp(-eta * (rj * rj + rk * rk)) *
+                                 cutoff_fn(rj, m->rc) * cutoff_fn(rk, m->rc);
+            }
+        }
+    }
+}
+
+void or_descriptors(const or_model* m, int n, const double* x, const double* box,
+                    const int* nbr, const int* nnb, int maxnb, double* G)
+{
+#pragma omp parallel for num_threads(or_get_threads()) schedule(dynamic, 4) if (!omp_in_parallel())
+    for (int i = 0; i < n; ++i)
+        descriptor_atom(m, x, box, i, nbr + (size_t)i * maxnb, nnb[i], G + (size_t)i * OR_ND);
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-element network: E = s_E (w_out . h_L + b_out) + e_Z,                 */
+/* h_l = tanh(W_l h_{l-1} + b_l), h_0 = (G - mu) / sigma; returns E and      */
+/* dE/dG by back-propagation through the same layers.                        */
+/* ------------------------------------------------------------------------ */
+static int elem_index(const or_model* m, int z)
+{
+    for (int e = 0; e < m->n_elem; ++e)
+        if (m->Z[e] == z) return e;
+    return -1;
+}
+
+double or_mlp(const or_model* m, int z, const double* G, double* dEdG)
+{
+    int e = elem_index(m, z);
+    const double* p = m->params[e];
+    int L = m->n_hidden;
+    /* locate the blob's pieces */
+    const double* W[OR_MAX_LAYERS];
+    const double* b[OR_MAX_LAYERS];
+    int prev = OR_ND, off = 0;
+    for (int l = 0; l < L; ++l) {
+        W[l] = p + off; off += m->width[l] * prev;
+        b[l] = p + off; off += m->width[l];
+        prev = m->width[l];
+    }
+    const double* w_out = p + off; off += prev;
+    double b_out = p[off]; off += 1;
+    const double* mu = p + off; off += OR_ND;
+    const double* sigma = p + off; off += OR_ND;
+    double s_E = p[off];
+    double e_Z = p[off + 1];
+
+    /* forward, keeping every layer's output */
+    double* h[OR_MAX_LAYERS + 1];
+    int width_in[OR_MAX_LAYERS + 1];
+    width_in[0] = OR_ND;
+    h[0] = malloc(sizeof(double) * OR_ND);
+    for (int c = 0; c < OR_ND; ++c) h[0][c] = (G[c] - mu[c]) / sigma[c];
+    for (int l = 0; l < L; ++l) {
+        int nin = width_in[l], nout = m->width[l];
+        h[l + 1] = malloc(sizeof(double) * nout);
+        width_in[l + 1] = nout;
+        for (int o = 0; o < nout; ++o) {
+            double a = b[l][o];
+            for (int k = 0; k < nin; ++k) a += W[l][(size_t)o * nin + k] * h[l][k];
+            h[l + 1][o] = tanh(a);
+        }
+    }
+    double y = b_out;
+    for (int k = 0; k < width_in[L]; ++k) y += w_out[k] * h[L][k];
+    double E = s_E * y + e_Z;
+
+    if (dEdG != NULL) {
+        /* backward: dE/dh_L = s_E w_out; dE/da_l = dE/dh_l (1 - h_l^2);
+           dE/dh_{l-1} = W_l^T dE/da_l */
+        double* gh = malloc(sizeof(double) * width_in[L]);
+        for (int k = 0; k < width_in[L]; ++k) gh[k] = s_E * w_out[k];
+        for (int l = L - 1; l >= 0; --l) {
+            int nin = width_in[l], nout = m->width[l];
+            double* gprev = malloc(sizeof(double) * nin);
+            for (int k = 0; k < nin; ++k) gprev[k] = 0.0;
+            for (int o = 0; o < nout; ++o) {
+                double ga = gh[o] * (1.0 - h[l + 1][o] * h[l + 1][o]);
+                for (int k = 0; k < nin; ++k) gprev[k] += W[l][(size_t)o * nin + k] * ga;
+            }
+            free(gh);
+            gh = gprev;
+        }
+        for (int c = 0; c < OR_ND; ++c) dEdG[c] = gh[c] / sigma[c];
+        free(gh);
+    }
+    for (int l = 0; l <= L; ++l) free(h[l]);
+    return E;
+}
+
+/* ------------------------------------------------------------------------ */
+/* forces: chain rule of E_i(G_i(r_ij)) onto the pair vectors r_ij           */
+/* v_s = dE_i / d r_{i j_s}; then F_j -= v_s, F_i += v_s,                    */
+/* W_ab -= r_ij,a v_s,b (virial of the per-atom energy)                      */
+/* ------------------------------------------------------------------------ */
+static void pair_gradients(const or_model* m, const double* x, const double* box, int i,
+                           const int* nb, int cnt, const double* g, double* v)
+{
+    for (int s = 0; s < 3 * cnt; ++s) v[s] = 0.0;
+    double rc = m->rc;
+    for (int s = 0; s < cnt; ++s) {
+        double d[3];
+        min_image(x + 3 * i, x + 3 * nb[s], box, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double dEdr = 0.0;
+        for (int mu = 0; mu < OR_NR; ++mu) {
+            double t = r - m->r_mu[mu];
+            double ex = exp(-m->eta_R * t * t);
+            dEdr += g[mu] * ex * (-2.0 * m->eta_R * t * cutoff_fn(r, rc) + cutoff_dr(r, rc));
+        }
+        for (int a = 0; a < 3; ++a) v[3 * s + a] += dEdr * d[a] / r;
+    }
+    for (int s = 0; s < cnt; ++s) {
+        for (int t = s + 1; t < cnt; ++t) {
+            double dj[3], dk[3], uj[3], uk[3];
+            min_image(x + 3 * i, x + 3 * nb[s], box, dj);
+            min_image(x + 3 * i, x + 3 * nb[t], box, dk);
+            double rj = sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
+            double rk = sqrt(dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2]);
+            for (int a = 0; a < 3; ++a) { uj[a] = dj[a] / rj; uk[a] = dk[a] / rk; }
+            double cth = uj[0] * uk[0] + uj[1] * uk[1] + uj[2] * uk[2];
+            double fj = cutoff_fn(rj, rc), fk = cutoff_fn(rk, rc);
+            double dfj = cutoff_dr(rj, rc), dfk = cutoff_dr(rk, rc);
+            for (int nu = 0; nu < OR_NA; ++nu) {
+                int zeta;
+                double lam, eta;
+                channel(m, nu, &zeta, &lam, &eta);
+                double pre = pow(2.0, 1 - zeta);
+                double ang = ipow(1.0 + lam * cth, zeta);
+                double dang = zeta * lam * ipow(1.0 + lam * cth, zeta - 1);
+                double ex = exp(-eta * (rj * rj + rk * rk));
+                double T_c = pre * dang * ex * fj * fk;                        /* dT/dcos   */
+                double T_rj = pre * ang * ex * fk * (-2.0 * eta * rj * fj + dfj); /* dT/dr_ij */
+                double T_rk = pre * ang * ex * fj * (-2.0 * eta * rk * fk + dfk); /* dT/dr_ik */
+                for (int a = 0; a < 3; ++a) {
+                    /* d cos / d r_ij = (u_k - cos u_j) / r_ij, and symmetrically */
+                    v[3 * s + a] += g[OR_NR + nu] * (T_rj * uj[a] + T_c * (uk[a] - cth * uj[a]) / rj);
+                    v[3 * t + a] += g[OR_NR + nu] * (T_rk * uk[a] + T_c * (uj[a] - cth * uk[a]) / rk);
+                }
+            }
+        }
+    }
+}
+
+int or_energy_forces(const or_model* m, int n, const int* Z, const double* x,
+                     const double* box, int maxnb, double* E_atom, double* F, double* W)
+{
+    int* nbr = malloc(sizeof(int) * (size_t)n * maxnb);
+    int* nnb = malloc(sizeof(int) * (size_t)n);
+    double* v = malloc(sizeof(double) * (size_t)n * maxnb * 3);
+    int worst = or_neighbours(n, x, box, m->rc, maxnb, nbr, nnb);
+    if (worst > maxnb) {
+        free(nbr); free(nnb); free(v);
+        return -worst;
+    }
+    int bad = 0;
+#pragma omp parallel for num_threads(or_get_threads()) schedule(dynamic, 4) reduction(| : bad) if (!omp_in_parallel())
+    for (int i = 0; i < n; ++i) {
+        double G[OR_ND], g[OR_ND];
+        const int* nb = nbr + (size_t)i * maxnb;
+        if (elem_index(m, Z[i]) < 0) { bad = 1; continue; }
+        descriptor_atom(m, x, box, i, nb, nnb[i], G);
+        E_atom[i] = or_mlp(m, Z[i], G, g);
+        pair_gradients(m, x, box, i, nb, nnb[i], g, v + (size_t)i * maxnb * 3);
+    }
+    if (bad) {
+        free(nbr); free(nnb); free(v);
+        return -1;
+    }
+    for (int k = 0; k < 3 * n; ++k) F[k] = 0.0;
+    for (int k = 0; k < 9; ++k) W[k] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        for (int s = 0; s < nnb[i]; ++s) {
+            int j = nbr[(size_t)i * maxnb + s];
+            const double* vs = v + ((size_t)i * maxnb + s) * 3;
+            double d[3];
+            min_image(x + 3 * i, x + 3 * j, box, d);
+            for (int a = 0; a < 3; ++a) {
+                F[3 * j + a] -= vs[a];
+                F[3 * i + a] += vs[a];
+                for (int b2 = 0; b2 < 3; ++b2) W[3 * a + b2] -= d[a] * vs[b2];
+            }
+        }
+    }
+    free(nbr); free(nnb); free(v);
+    return worst;
+}
+
+int or_energy_forces_batch(const or_model* m, int nconf, int n, const int* Z,
+                           const double* x, const double* box, int maxnb,
+                           double* E_atom, double* F, double* W)
+{
+    int worst = 0;
+    for (int c = 0; c < nconf; ++c) {
+        int r = or_energy_forces(m, n, Z, x + (size_t)c * n * 3, box, maxnb,
+                                 E_atom + (size_t)c * n, F + (size_t)c * n * 3, W + 9 * c);
+        if (r < 0) return r;
+        if (r > worst) worst = r;
+    }
+    return worst;
+}
+
+/* ------------------------------------------------------------------------ */
+/* normal modes of the cyclic ring polymer                                   */
+/* C[j][k]: bead j, mode k;  q_bead = C q_nm;  C^T C = I                      */
+/* ------------------------------------------------------------------------ */
+void or_nm_matrix(int P, double* C)
+{
+    for (int j = 0; j < P; ++j) {
+        for (int k = 0; k < P; ++k) {
+            double v;
+            if (k == 0)
+                v = 1.0 / sqrt((double)P);
+            else if (2 * k < P)
+                v = sqrt(2.0 / P) * cos(2.0 * M_PI * j * k / P);
+            else if (2 * k == P)
+                v = ((j % 2) ? -1.0 : 1.0) / sqrt((double)P);
+            else
+                v = sqrt(2.0 / P) * sin(2.0 * M_PI * j * k / P);
+            C[j * P + k] = v;
+        }
+    }
+}
+
+/* free ring-polymer mode frequencies omega_k = 2 omega_P sin(k pi / P) */
+void or_nm_freqs(int P, double omega_P, double* wk)
+{
+    for (int k = 0; k < P; ++k) wk[k] = 2.0 * omega_P * sin(k * M_PI / P);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 and Box-Muller                                              */
+/* ------------------------------------------------------------------------ */
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo)
+{
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
+}
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo32(0xD2511F53u, c[0], &hi0, &lo0);
+        mulhilo32(0xCD9E8D57u, c[2], &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    for (int a = 0; a < 4; ++a) out[a] = c[a];
+}
+
+/* one standard normal: counter (index, step, replica, stream), key = seed;
+ * two 53-bit uniforms in (0, 1] from word pairs, then Box-Muller */
+double or_normal(uint64_t seed, uint32_t index, uint32_t step, uint32_t replica, uint32_t stream)
+{
+    uint32_t ctr[4] = {index, step, replica, stream};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    double u1 = ((double)(w[0] >> 5) * 67108864.0 + (double)(w[1] >> 6) + 1.0) / 9007199254740992.0;
+    double u2 = ((double)(w[2] >> 5) * 67108864.0 + (double)(w[3] >> 6) + 1.0) / 9007199254740992.0;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* ring-polymer dynamics in normal-mode space (state layout [P][N][3])       */
+/* i-PI convention: beta_P = beta / P, omega_P = P k_B T / hbar               */
+/* ------------------------------------------------------------------------ */
+static double omega_P_of(const or_sys* s) { return s->P * KB * s->T / HBAR; }
+static double kT_P_md(const or_sys* s) { return s->P * KB * s->T / MVV2E; }
+
+int or_init(const or_sys* s, const double* x0, double* q_nm, double* p_nm)
+{
+    int N = s->N, P = s->P;
+    double kT = kT_P_md(s);
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                size_t g = ((size_t)k * N + i) * 3 + d;
+                q_nm[g] = (k == 0) ? sqrt((double)P) * x0[3 * i + d] : 0.0;
+                p_nm[g] = sqrt(s->mass[i] * kT) *
+                          or_normal(s->seed, (uint32_t)g, 0u, (uint32_t)s->replica, 1u);
+            }
+    return 0;
+}
+
+static void to_beads(const or_sys* s, const double* C, const double* q_nm, double* xb)
+{
+    int N = s->N, P = s->P;
+    for (int j = 0; j < P; ++j)
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                double acc = 0.0;
+                for (int k = 0; k < P; ++k) acc += C[j * P + k] * q_nm[((size_t)k * N + i) * 3 + d];
+                xb[((size_t)j * N + i) * 3 + d] = acc;
+            }
+}
+
+int or_forces(const or_sys* s, const or_model* m, const double* q_nm,
+              double* xb, double* f, double* V, double* W)
+{
+    int N = s->N, P = s->P;
+    double* C = malloc(sizeof(double) * P * P);
+    or_nm_matrix(P, C);
+    to_beads(s, C, q_nm, xb);
+    free(C);
+    if (s->potential == 1) {
+        for (int j = 0; j < P; ++j) {
+            double v = 0.0;
+            for (int i = 0; i < N; ++i)
+                for (int d = 0; d < 3; ++d) {
+                    size_t g = ((size_t)j * N + i) * 3 + d;
+                    double k = s->mass[i] * s->omega_harm * s->omega_harm * MVV2E; /* eV/A^2 */
+                    v += 0.5 * k * xb[g] * xb[g];
+                    f[g] = -k * xb[g];
+                }
+            V[j] = v;
+            for (int a = 0; a < 3; ++a)
+                for (int b2 = 0; b2 < 3; ++b2) {
+                    double w = 0.0;
+                    for (int i = 0; i < N; ++i)
+                        w += xb[((size_t)j * N + i) * 3 + a] * f[((size_t)j * N + i) * 3 + b2];
+                    W[9 * j + 3 * a + b2] = w;
+                }
+        }
+        return 0;
+    }
+    double* E = malloc(sizeof(double) * N);
+    int rc = 0;
+    for (int j = 0; j < P && rc >= 0; ++j) {
+        int r = or_energy_forces(m, N, s->Z, xb + (size_t)j * N * 3, s->box, s->maxnb, E,
+                                 f + (size_t)j * N * 3, W + 9 * j);
+        if (r < 0) { rc = r; break; }
+        double v = 0.0;
+        for (int i = 0; i < N; ++i) v += E[i];
+        V[j] = v;
+    }
+    free(E);
+    return rc;
+}
+
+/* O: p <- c1 p + sqrt(m k_B T_P) c2 xi over time dt/2 (PILE-L friction
+ * gamma_0 on the centroid, 2 lambda omega_k on internal modes) */
+static void step_O(const or_sys* s, const double* wk, uint32_t step, uint32_t stream,
+                   double* p_nm, double* Q)
+{
+    int N = s->N, P = s->P;
+    double kT = kT_P_md(s), dq = 0.0;
+    for (int k = 0; k < P; ++k) {
+        double gam = (k == 0) ? s->gamma0 : 2.0 * s->pile_lambda * wk[k];
+        double c1 = exp(-0.5 * s->dt * gam);
+        double c2 = sqrt(1.0 - c1 * c1);
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                size_t g = ((size_t)k * N + i) * 3 + d;
+                double xi = or_normal(s->seed, (uint32_t)g, step, (uint32_t)s->replica, stream);
+                double pn = c1 * p_nm[g] + sqrt(s->mass[i] * kT) * c2 * xi;
+                dq += (pn * pn - p_nm[g] * p_nm[g]) / (2.0 * s->mass[i]);
+                p_nm[g] = pn;
+            }
+    }
+    *Q += dq * MVV2E;
+}
+
+/* B: p_nm += dt/2 C^T f */
+static void step_B(const or_sys* s, const double* C, const double* f, double* p_nm)
+{
+    int N = s->N, P = s->P;
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                double fn = 0.0;
+                for (int j = 0; j < P; ++j) fn += C[j * P + k] * f[((size_t)j * N + i) * 3 + d];
+                p_nm[((size_t)k * N + i) * 3 + d] += 0.5 * s->dt * fn / MVV2E;
+            }
+}
+
+/* A: exact free ring-polymer evolution of each normal mode over dt */
+static void step_A(const or_sys* s, const double* wk, double* q_nm, double* p_nm)
+{
+    int N = s->N, P = s->P;
+    double dt = s->dt;
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                size_t g = ((size_t)k * N + i) * 3 + d;
+                double m = s->mass[i], p = p_nm[g], q = q_nm[g];
+                if (k == 0) {
+                    q_nm[g] = q + p * dt / m;
+                } else {
+                    double w = wk[k], cw = cos(w * dt), sw = sin(w * dt);
+                    p_nm[g] = cw * p - m * w * sw * q;
+                    q_nm[g] = sw / (m * w) * p + cw * q;
+                }
+            }
+}
+
+/* one step = O(dt/2) B(dt/2) A(dt) [forces] B(dt/2) O(dt/2); the noise of
+ * step n uses counter step n, streams 2 (first O) and 3 (second O) */
+int or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
+            double* q_nm, double* p_nm, double* f, double* V, double* W, double* Q_thermo)
+{
+    int N = s->N, P = s->P;
+    double* C = malloc(sizeof(double) * P * P);
+    double* wk = malloc(sizeof(double) * P);
+    double* xb = malloc(sizeof(double) * (size_t)P * N * 3);
+    or_nm_matrix(P, C);
+    or_nm_freqs(P, omega_P_of(s), wk);
+    int rc = 0;
+    for (int n = 0; n < nsteps; ++n) {
+        uint32_t st = (uint32_t)(*step);
+        if (s->thermostat) step_O(s, wk, st, 2u, p_nm, Q_thermo);
+        step_B(s, C, f, p_nm);
+        step_A(s, wk, q_nm, p_nm);
+        rc = or_forces(s, m, q_nm, xb, f, V, W);
+        if (rc < 0) break;
+        step_B(s, C, f, p_nm);
+        if (s->thermostat) step_O(s, wk, st, 3u, p_nm, Q_thermo);
+        *step += 1;
+    }
+    free(C); free(wk); free(xb);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* estimators of the finite-P ensemble average                               */
+/* ------------------------------------------------------------------------ */
+void or_estimators(const or_sys* s, const double* q_nm, const double* p_nm,
+                   const double* f, const double* V, const double* W, double Q_thermo,
+                   or_est* out)
+{
+    int N = s->N, P = s->P;
+    double beta = 1.0 / (KB * s->T);
+    double wP = omega_P_of(s);
+    double* C = malloc(sizeof(double) * P * P);
+    double* xb = malloc(sizeof(double) * (size_t)P * N * 3);
+    or_nm_matrix(P, C);
+    to_beads(s, C, q_nm, xb);
+
+    double Vbar = 0.0;
+    for (int j = 0; j < P; ++j) Vbar += V[j];
+    Vbar /= P;
+
+    double spring = 0.0; /* sum_k sum_i 1/2 m omega_P^2 |q^k - q^{k+1}|^2, eV */
+    for (int j = 0; j < P; ++j) {
+        int jn = (j + 1) % P;
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                double dq = xb[((size_t)j * N + i) * 3 + d] - xb[((size_t)jn * N + i) * 3 + d];
+                spring += 0.5 * s->mass[i] * wP * wP * dq * dq * MVV2E;
+            }
+    }
+    double K_prim = 3.0 * N * P / (2.0 * beta) - spring / P;
+
+    double cv = 0.0; /* sum_k sum_i (q_i^k - centroid_i) . f_i^k */
+    for (int i = 0; i < N; ++i)
+        for (int d = 0; d < 3; ++d) {
+            double cen = 0.0;
+            for (int j = 0; j < P; ++j) cen += xb[((size_t)j * N + i) * 3 + d];
+            cen /= P;
+            for (int j = 0; j < P; ++j) {
+                size_t g = ((size_t)j * N + i) * 3 + d;
+                cv += (xb[g] - cen) * f[g];
+            }
+        }
+    double K_cv = 3.0 * N / (2.0 * beta) - cv / (2.0 * P);
+
+    double kin = 0.0; /* sum p^2 / 2m over all modes, eV */
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                double p = p_nm[((size_t)k * N + i) * 3 + d];
+                kin += p * p / (2.0 * s->mass[i]) * MVV2E;
+            }
+    double H_P = kin + spring;
+    for (int j = 0; j < P; ++j) H_P += V[j];
+
+    out->V_mean = Vbar;
+    out->K_prim = K_prim;
+    out->K_cv = K_cv;
+    out->E_tot = K_cv + Vbar;
+    for (int a = 0; a < 9; ++a) {
+        double w = 0.0;
+        for (int j = 0; j < P; ++j) w += W[9 * j + a];
+        out->W[a] = w / P;
+    }
+    out->H_cons = H_P - Q_thermo;
+    out->Q_thermo = Q_thermo;
+    out->T_kin = 2.0 * kin / (3.0 * N * P * KB);
+    free(C); free(xb);
+}

@@ -1,0 +1,102 @@
+/*
+ * oracle.h -- FP64 CPU oracle for path-integral MD with a symmetry-function
+ * neural-network potential.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * cpu_baseline / reference legs may load this library. It shares no code with
+ * the CUDA path: it is a plain, slow restatement of the method's definitions
+ * (paper Sec. 2.1 Eqs. for H_eff, H_p, U and the estimator; BPNN descriptors
+ * of ref. [17] cited in Sec. 1; energy-derived forces of Sec. 2.2) written for
+ * a reader to check against the paper by eye.
+ *
+ * Units: Angstrom, fs, amu, eV, K.
+ */
+#ifndef PIMD_ORACLE_H
+#define PIMD_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_NR 32          /* radial channels                                  */
+#define OR_NA 32          /* angular channels (4 zeta x 2 lambda x 4 eta)     */
+#define OR_ND 64          /* descriptor length                                */
+#define OR_MAX_ELEM 8
+#define OR_MAX_LAYERS 8
+
+/* Symmetry-function network. params[e] is element e's flat FP64 blob:
+ * for l in hidden layers: W_l [h_l][h_{l-1}] row-major, b_l [h_l];
+ * then w_out [h_L], b_out, mu [64], sigma [64], s_E, e_Z. */
+typedef struct {
+    int n_elem;
+    int Z[OR_MAX_ELEM];
+    int n_hidden;
+    int width[OR_MAX_LAYERS];
+    const double* params[OR_MAX_ELEM];
+    double rc;
+    double eta_R;
+    double r_mu[OR_NR];
+    int zeta[4];
+    double lambda[2];
+    double eta_A[4];
+} or_model;
+
+/* One ring-polymer system and its integrator settings. */
+typedef struct {
+    int N, P;
+    const int* Z;            /* [N]                                          */
+    const double* mass;      /* [N] amu                                      */
+    double box[3];           /* 0 = non-periodic                             */
+    double T;                /* physical temperature, K                      */
+    uint64_t seed;
+    int replica;             /* replica index (enters the noise counter)     */
+    double dt;               /* fs                                           */
+    double gamma0;           /* centroid friction, 1/fs                      */
+    double pile_lambda;      /* PILE-L scaling of internal-mode friction     */
+    int thermostat;          /* 0 = NVE, 1 = PILE-L                          */
+    int potential;           /* 0 = network, 1 = harmonic 0.5 m w^2 |x|^2    */
+    double omega_harm;       /* 1/fs                                         */
+    int maxnb;               /* neighbour slots per atom                     */
+} or_sys;
+
+/* estimator record, all eV except T_kin (K) */
+typedef struct {
+    double V_mean, K_prim, K_cv, E_tot;
+    double W[9];
+    double H_cons, Q_thermo, T_kin;
+} or_est;
+
+/* --- symmetry-function potential for one configuration ------------------ */
+int  or_neighbours(int n, const double* x, const double* box, double rc, int maxnb,
+                   int* nbr, int* nnb);
+void or_descriptors(const or_model* m, int n, const double* x, const double* box,
+                    const int* nbr, const int* nnb, int maxnb, double* G);
+double or_mlp(const or_model* m, int z, const double* G, double* dEdG);
+int  or_energy_forces(const or_model* m, int n, const int* Z, const double* x,
+                      const double* box, int maxnb, double* E_atom, double* F, double* W);
+int  or_energy_forces_batch(const or_model* m, int nconf, int n, const int* Z,
+                            const double* x, const double* box, int maxnb,
+                            double* E_atom, double* F, double* W);
+
+/* --- ring polymer ---------------------------------------------------------- */
+void or_nm_matrix(int P, double* C);
+void or_nm_freqs(int P, double omega_P, double* wk);
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_normal(uint64_t seed, uint32_t index, uint32_t step, uint32_t replica, uint32_t stream);
+int  or_init(const or_sys* s, const double* x0, double* q_nm, double* p_nm);
+int  or_forces(const or_sys* s, const or_model* m, const double* q_nm,
+               double* xb, double* f, double* V, double* W);
+int  or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
+             double* q_nm, double* p_nm, double* f, double* V, double* W, double* Q_thermo);
+void or_estimators(const or_sys* s, const double* q_nm, const double* p_nm,
+                   const double* f, const double* V, const double* W, double Q_thermo,
+                   or_est* out);
+void or_set_threads(int n);
+int  or_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,44 @@
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: long-running statistical check")
+
+
+@pytest.fixture(scope="session")
+def water64_model():
+    """Water-64 box with a 3x128 random-init network whose normalisation and
+    energy scale were fixed from oracle descriptors/forces of bead 0."""
+    import oracle as O
+    from paper_2503_23728_gb300 import synth as s
+    w = s.workload("water64")
+    r = w.replicas[0]
+    m = s.xavier_model(s.elements_of(w.replicas), w.widths, seed=7)
+    G = O.descriptors(m, r.x0, r.box)
+    s.set_normalisation(m, G, r.Z)
+    _, F, _ = O.energy_forces(m, r.Z, r.x0, r.box)
+    s.set_energy_scale(m, 1.0 / float(np.sqrt((F ** 2).mean())))
+    return w, r, m
+
+
+@pytest.fixture(scope="session")
+def fad_model():
+    import oracle as O
+    from paper_2503_23728_gb300 import synth as s
+    w = s.workload("fad")
+    r = w.replicas[0]
+    m = s.xavier_model(s.elements_of(w.replicas), w.widths, seed=11)
+    G = O.descriptors(m, r.x0, r.box)
+    s.set_normalisation(m, G, r.Z)
+    _, F, _ = O.energy_forces(m, r.Z, r.x0, r.box)
+    s.set_energy_scale(m, 1.0 / float(np.sqrt((F ** 2).mean())))
+    return w, r, m

@@ -1,0 +1,178 @@
+"""Pins for the oracle's ring-polymer part (Sec. 2.1: effective Hamiltonian,
+normal-mode transformation, H_eff = H_p + U splitting, finite-P estimator;
+Sec. S1: harmonic-oscillator validation)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_23728_gb300 import synth as s
+
+KB = 8.617333262e-5
+HBAR = 0.6582119569
+MVV2E = 103.64269652680505
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 8, 16, 31, 32])
+def test_normal_modes_orthogonal_and_diagonalise_springs(P):
+    C = O.nm_matrix(P)
+    np.testing.assert_allclose(C.T @ C, np.eye(P), atol=1e-14)
+    wP = 0.37
+    K = np.zeros((P, P))
+    for j in range(P):
+        K[j, j] += 2.0
+        K[j, (j + 1) % P] -= 1.0
+        K[j, (j - 1) % P] -= 1.0
+    K *= wP * wP
+    if P == 1:
+        K[:] = 0.0
+    if P == 2:
+        K = wP * wP * np.array([[2.0, -2.0], [-2.0, 2.0]])
+    ev = np.sort(np.linalg.eigvalsh(K))
+    wk = O.nm_freqs(P, wP)
+    np.testing.assert_allclose(np.sort(wk ** 2), ev, atol=1e-12)
+    # and the columns of C are the matching eigenvectors, mode 0 = centroid
+    D = C.T @ K @ C
+    np.testing.assert_allclose(D, np.diag(wk ** 2), atol=1e-12)
+    np.testing.assert_allclose(C[:, 0], 1.0 / math.sqrt(P))
+
+
+def _harmonic_system(P, N=1, T=300.0, omega=0.0, dt=0.5, gamma0=0.01, thermostat=True, seed=5):
+    x0 = np.random.default_rng(seed).normal(size=(N, 3)) * 0.1
+    rep = s.Replica(np.full(N, s.H, dtype=np.int32), x0, (0.0, 0.0, 0.0), P, T, seed)
+    return O.System(rep, s.MASS, dt, gamma0, thermostat=thermostat, potential="harmonic", omega=omega)
+
+
+def test_free_ring_polymer_matches_ode_solver():
+    """With V = 0 and no thermostat the exact normal-mode propagation must
+    reproduce the bead-space spring dynamics m q_j'' = -m w_P^2 (2 q_j -
+    q_{j-1} - q_{j+1}) integrated by scipy's DOP853."""
+    from scipy.integrate import solve_ivp
+    P, N = 8, 2
+    sysm = _harmonic_system(P, N, omega=0.0, dt=2.0, thermostat=False)
+    rng = np.random.default_rng(3)
+    sysm.q[:] = rng.normal(size=sysm.q.shape) * 0.2
+    sysm.p[:] = rng.normal(size=sysm.p.shape) * 0.05
+    C = O.nm_matrix(P)
+    qb0 = np.einsum("jk,kia->jia", C, sysm.q)
+    pb0 = np.einsum("jk,kia->jia", C, sysm.p)
+    m = s.MASS[s.H]
+    wP = P * KB * 300.0 / HBAR
+    nsteps = 40
+    sysm.step(nsteps)
+    qb = np.einsum("jk,kia->jia", C, sysm.q)
+
+    def rhs(t, y):
+        q = y[: P * N * 3].reshape(P, N, 3)
+        p = y[P * N * 3:].reshape(P, N, 3)
+        f = -m * wP * wP * (2 * q - np.roll(q, 1, axis=0) - np.roll(q, -1, axis=0))
+        return np.concatenate([(p / m).ravel(), f.ravel()])
+
+    sol = solve_ivp(rhs, (0.0, nsteps * 2.0), np.concatenate([qb0.ravel(), pb0.ravel()]),
+                    method="DOP853", rtol=1e-12, atol=1e-12)
+    qode = sol.y[: P * N * 3, -1].reshape(P, N, 3)
+    np.testing.assert_allclose(qb, qode, atol=1e-8)
+
+
+def test_step_is_time_reversible():
+    sysm = _harmonic_system(8, 3, omega=0.02, dt=0.5, thermostat=False)
+    q0, p0 = sysm.q.copy(), sysm.p.copy()
+    sysm.step(25)
+    sysm.s.dt = -0.5
+    sysm.step(25)
+    np.testing.assert_allclose(sysm.q, q0, atol=1e-11)
+    np.testing.assert_allclose(sysm.p, p0, atol=1e-11)
+
+
+def test_initial_state_and_equipartition():
+    """All beads start at x0; momenta are drawn at T_P = P T. Under PILE-L on a
+    free ring polymer <p^2/m> -> k_B T_P per degree of freedom."""
+    P, N, T = 8, 16, 200.0
+    sysm = _harmonic_system(P, N, T=T, omega=0.0, dt=1.0, gamma0=0.02)
+    xb = sysm.beads()
+    for j in range(P):
+        np.testing.assert_allclose(xb[j], xb[0], atol=1e-13)
+    tk = []
+    for _ in range(400):
+        sysm.step(5)
+        tk.append(sysm.estimators()["T_kin"])
+    tk = np.array(tk[40:])
+    assert abs(tk.mean() / (P * T) - 1.0) < 0.02
+
+
+def _qho_exact_EP(P, T, omega):
+    """<E_P> of a 3D oscillator with P beads (Sec. S1, with the square of the
+    bracket restored): 3 k_B T sum_l 1 / (1 + [(2 P k_B T / hbar w) sin(l pi / P)]^2)."""
+    kT = KB * T
+    return 3 * kT * sum(1.0 / (1.0 + ((2 * P * kT / (HBAR * omega)) * math.sin(l * math.pi / P)) ** 2)
+                        for l in range(1, P + 1))
+
+
+def _block_mean(x, nblock=20):
+    x = np.asarray(x)
+    n = len(x) // nblock
+    b = x[: n * nblock].reshape(nblock, n).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nblock)
+
+
+def test_qho_closed_form_limits():
+    w, T = 0.0786, 300.0
+    kT = KB * T
+    assert abs(_qho_exact_EP(1, T, w) - 3 * kT) < 1e-15
+    big = _qho_exact_EP(4096, T, w)
+    exact = 3 * 0.5 * HBAR * w / math.tanh(HBAR * w / (2 * kT))
+    assert abs(big / exact - 1) < 1e-5
+
+
+@pytest.mark.parametrize("P", [1, 4, 16])
+def test_qho_thermostatted_averages_match_closed_form(P):
+    """Harmonic oscillator (hbar w / k_B T ~ 2): PILE-L averages of the
+    virial and primitive estimators against the P-bead closed form."""
+    T, w, N = 300.0, 0.0786, 8
+    sysm = _harmonic_system(P, N, T=T, omega=w, dt=0.25, gamma0=0.08)
+    sysm.step(2000)
+    Ev, Kp, Kc, x2 = [], [], [], []
+    m = s.MASS[s.H]
+    for _ in range(6000):
+        sysm.step(10)
+        e = sysm.estimators()
+        Ev.append(e["E_tot"] / N)
+        Kp.append(e["K_prim"] / N)
+        Kc.append(e["K_cv"] / N)
+        x2.append((sysm.beads() ** 2).sum(axis=2).mean())
+    exact = _qho_exact_EP(P, T, w)
+    mean, err = _block_mean(Ev)
+    assert abs(mean - exact) < 4 * err + 0.004 * exact, (mean, err, exact)
+    mk, ek = _block_mean(Kc)
+    assert abs(mk - exact / 2) < 4 * ek + 0.004 * exact
+    mp, ep = _block_mean(Kp)
+    assert abs(mp - exact / 2) < 4 * ep + 0.004 * exact
+    # <|x|^2> per atom = 3 / (beta m) sum_k 1 / (w^2 + w_k^2)
+    wP = P * KB * T / HBAR
+    wk = 2 * wP * np.sin(np.arange(P) * np.pi / P)
+    x2_exact = 3 * (KB * T / MVV2E) / m * np.sum(1.0 / (w * w + wk ** 2))
+    mx, ex = _block_mean(x2)
+    assert abs(mx - x2_exact) < 4 * ex + 0.004 * x2_exact
+
+
+def test_nve_energy_conservation(fad_model):
+    """No thermostat: the ring-polymer Hamiltonian H_P shows no drift and its
+    fluctuation scales as dt^2 (symplectic splitting)."""
+    w, r, m = fad_model
+    amp = []
+    for dt in (0.1, 0.05):
+        rep = s.Replica(r.Z, r.x0, r.box, 4, 300.0, r.seed)
+        sysm = O.System(rep, s.MASS, dt, 0.0, model=m, thermostat=False)
+        H = []
+        nst = int(round(10.0 / dt))
+        for _ in range(nst):
+            sysm.step(1)
+            H.append(sysm.estimators()["H_cons"])
+        H = np.array(H)
+        t = np.arange(len(H))
+        slope = np.polyfit(t, H, 1)[0]
+        amp.append(H.std())
+        assert abs(slope * len(H)) < 3 * H.std() + 1e-12
+    ratio = amp[0] / amp[1]
+    assert 2.5 < ratio < 6.0, amp
