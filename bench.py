@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of the bead-batched PIMD step on one GB300 (per rank).
+
+Workload: proton-disordered ice Ih, 432 H2O (1296 atoms), P = 32 beads,
+T = 250 K, dt = 0.5 fs, 3 x 128 tanh network on 32 radial + 32 angular
+symmetry functions, cutoff 6 A (synthetic, seeded; random-init weights).
+A step is one full pass of the hot path: normal modes -> beads, neighbour
+lists, descriptors, network forward + input gradient, adjoint forces and
+virial, per-bead energies, OBABO ring-polymer update in normal-mode space.
+
+Metric: bead-atom force evaluations per second (and ns/day) of the BF16
+tensor-core path; the plain FP32 GPU path is measured beside it.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "bead-atom force evals/sec & ns/day, ice P=32: BF16-TC fused vs plain FP32 GPU"
+UNIT = "bead-atom force evals/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12    # SMs x FP32 lanes x 2 flop x max SM clock
+# algorithmic FP32 flops of the adjoint (forces + virial) per unit
+ADJ_FLOP_PER_PAIR = 205
+ADJ_FLOP_PER_NBR = 380
+
+
+def args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16_tc", choices=["bf16_tc", "fp32", "fp64"])
+    ap.add_argument("--workload", default="ice", choices=["ice", "water64", "fad", "batch"])
+    ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def build_model(ctx, workload, precision_ctx_factory):
+    """Random-init network; input normalisation and energy scale fixed from
+    the library's own descriptors / forces of the initial configuration."""
+    from paper_2503_23728_gb300 import synth as s
+    rep = workload.replicas[0]
+    m = s.xavier_model(s.elements_of(workload.replicas), workload.widths, seed=7)
+    ctx.set_weights(m)
+    G = ctx.descriptors().cpu().numpy()
+    Z = np.concatenate([np.tile(r.Z, r.n_beads) for r in workload.replicas])
+    s.set_normalisation(m, G, Z)
+    ctx.set_weights(m)
+    _, f, _ = ctx.energy_forces()
+    rms = float(np.sqrt((f.cpu().numpy() ** 2).mean()))
+    s.set_energy_scale(m, 1.0 / rms)
+    ctx.set_weights(m)
+    return m
+
+
+def run_gpu(a, workload, precision, model=None):
+    import torch
+    from paper_2503_23728_gb300 import pimd as P
+    ctx = P.Context(workload.replicas, workload.dt_fs, workload.gamma0_per_fs, precision=precision,
+                    widths=workload.widths, timing=True)
+    if model is None:
+        model = build_model(ctx, workload, None)
+    else:
+        ctx.set_weights(model)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(a.warmup):
+        ctx.step(1)
+    torch.cuda.synchronize()
+    return ctx, model, stream, flush
+
+
+def timed_steps(a, ctx, stream, flush, barrier):
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    stages = []
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(a.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        ctx.step(1)
+        ends[k].record(stream)
+        stages.append(ctx.stage_times())
+    torch.cuda.synchronize()
+    barrier()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return ms, stages
+
+
+def adjoint_flops(ctx) -> float:
+    nnb, _ = ctx.neighbours()
+    n = nnb.astype(np.float64)
+    return float(np.sum(ADJ_FLOP_PER_PAIR * n * (n - 1) / 2 + ADJ_FLOP_PER_NBR * n))
+
+
+def network_flops(ctx, widths) -> float:
+    # forward + input gradient, 2 flop per MAC, over the padded element tiles
+    macs = 0
+    prev = 64
+    for w in widths:
+        macs += prev * w
+        prev = w
+    macs = 2 * macs + prev   # backward mirrors forward; output layer on CUDA cores
+    return 2.0 * macs * ctx.B
+
+
+def e2e_host(a, ctx, stream, barrier):
+    """Force evaluation through the C ABI with host buffers: H2D of the bead
+    positions from pinned memory, pimd_energy_forces, D2H of forces and
+    energies, every step."""
+    import torch
+    _, f0, _ = ctx.energy_forces()
+    x_dev0 = torch.empty(ctx.B, 3, dtype=torch.float64, device="cuda")
+    xh, _, _ = ctx.get_forces()
+    x_host = torch.tensor(xh, dtype=torch.float64).pin_memory()
+    f_host = torch.empty(ctx.B, 3, dtype=torch.float64).pin_memory()
+    e_host = torch.empty(ctx.S, dtype=torch.float64).pin_memory()
+    e_dev = torch.empty(ctx.S, dtype=torch.float64, device="cuda")
+    f_dev = torch.empty(ctx.B, 3, dtype=torch.float64, device="cuda")
+    from paper_2503_23728_gb300 import pimd as P
+    import ctypes as ct
+    n = max(3, a.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(n):
+        x_dev0.copy_(x_host, non_blocking=True)
+        P.pimd_energy_forces(ctx.h, ct.c_void_p(x_dev0.data_ptr()), ct.c_void_p(e_dev.data_ptr()),
+                             ct.c_void_p(f_dev.data_ptr()), None)
+        f_host.copy_(f_dev, non_blocking=True)
+        e_host.copy_(e_dev, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = t0.elapsed_time(t1) / n
+    return ms, ctx.B * 3 * 8, ctx.B * 3 * 8 + ctx.S * 8
+
+
+def cpu_baseline(workload, model, budget_s=15.0):
+    """FP64 oracle on the host cores: force evaluations of whole beads of the
+    same workload until ~budget_s of CPU work."""
+    import oracle as O
+    rep = workload.replicas[0]
+    rng = np.random.default_rng(5)
+    threads = O.threads()
+    done, t0 = 0, time.perf_counter()
+    beads = 0
+    while beads < rep.n_beads:
+        x = rep.x0 + rng.normal(scale=0.05, size=rep.x0.shape)
+        O.energy_forces(model, rep.Z, x, rep.box)
+        beads += 1
+        done += rep.n_atoms
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of %d beads of the %s workload (%d bead-atoms), full FP64 force evaluation, "
+                      "OpenMP over atoms" % (beads, rep.n_beads, workload.name, done),
+            "seconds": dt}
+
+
+def workload_of(name, rank):
+    from paper_2503_23728_gb300 import synth as s
+    w = s.workload(name)
+    if rank:
+        seeds = s.replica_seeds(0xC0FFEE + rank, len(w.replicas))
+        for r, sd in zip(w.replicas, seeds):
+            r.seed = sd
+    return w
+
+
+def config_of(w, precision, world):
+    desc = {"ice": "ice Ih 432 H2O (1296 atoms), P=32, T=250 K, dt=0.5 fs, 3x128 tanh, cutoff 6 A",
+            "water64": "water 64 H2O (192 atoms), P=32, T=300 K, dt=0.5 fs, 3x128 tanh, cutoff 6 A",
+            "fad": "formic-acid dimer (10 atoms), P=16, T=300 K, dt=0.25 fs, 2x64 tanh, cutoff 6 A",
+            "batch": "256 gas-phase clusters of 6-24 atoms, P in {8,16,32,64}, 2x64 tanh"}[w.name]
+    return {"workload": desc, "bead_atoms_per_gpu": w.bead_atoms, "replicas_per_gpu": len(w.replicas),
+            "path": precision, "parallelism": "independent replicas per GPU" if world > 1 else "1 GPU",
+            "l2": "flushed between timed steps (256 MB write)",
+            "precision": {"network": {"bf16_tc": "bf16 tcgen05, fp32 accumulate", "fp32": "fp32",
+                                      "fp64": "fp64"}[precision],
+                          "descriptors_adjoint": "fp64" if precision == "fp64" else "fp32",
+                          "ring_polymer_estimators": "fp64"}}
+
+
+def main():
+    a = args()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        return reference(a, rank, world)
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import __graft_entry__ as ge
+    ge.build()
+    w = workload_of(a.workload, rank)
+    ctx, model, stream, flush = run_gpu(a, w, a.precision)
+    clk = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    ms, stages = timed_steps(a, ctx, stream, flush, barrier)
+    clocks = clk.stop()
+    total_ms = float(np.sum(ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    steps_per_s = a.steps / (total_ms / 1e3)
+    value = world * w.bead_atoms * steps_per_s
+    ns_day = steps_per_s * w.dt_fs * 86400 / 1e6
+    st_mean = {k: float(np.mean([s[k] for s in stages])) for k in stages[0]}
+    adj_flops = adjoint_flops(ctx)
+    adj_ms = st_mean["adjoint"]
+    achieved = adj_flops / (adj_ms / 1e3) / 1e12
+    net_flops = network_flops(ctx, w.widths)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    e2e_ms, h2d, d2h = e2e_host(a, ctx, stream, barrier)
+    launches = ctx.kernels_per_step() * a.steps
+    fp32 = None
+    if not a.no_fp32 and a.precision != "fp32":
+        ctx2, _, stream2, flush2 = run_gpu(a, w, "fp32", model)
+        ms2, stages2 = timed_steps(a, ctx2, stream2, flush2, barrier)
+        t2 = float(np.sum(ms2))
+        fp32 = {"value": world * w.bead_atoms * a.steps / (t2 / 1e3), "ms_per_step": t2 / a.steps,
+                "stages_ms": {k: float(np.mean([s[k] for s in stages2])) for k in stages2[0]}}
+        ctx2.close()
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16_tc": "bf16", "fp32": "f32", "fp64": "f64"}[a.precision], "data": "synthetic",
+        "config": config_of(w, a.precision, world),
+        "ns_per_day": ns_day,
+        "stages_ms": st_mean,
+        "fp32_plain": fp32,
+        "speedup_vs_fp32_plain": (value / fp32["value"]) if fp32 else None,
+        "roofline": {"bound": "alu", "kernel": "desc_adj_kernel (angular+radial adjoint, forces, virial)",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "flops_per_launch": adj_flops,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+        "network_tensor": {"flops_per_launch": net_flops, "ms": st_mean["network"],
+                           "achieved_tflops": net_flops / (st_mean["network"] / 1e3) / 1e12,
+                           "peak_bf16_tflops_measured": peaks.get("bf16_tflops")},
+        "clocks": clocks,
+        "e2e": {"value": world * w.bead_atoms / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "what": "pimd_energy_forces with host positions in, forces out"},
+        "gpu_launches": launches,
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, model)
+    ctx.close()
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference(a, rank, world):
+    """The FP64 CPU oracle as it stands: each step is the force evaluation of
+    one bead of the workload (bounded sample)."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2503_23728_gb300 import synth as s
+    w = s.workload(a.workload)
+    rep = w.replicas[0]
+    m = s.xavier_model(s.elements_of(w.replicas), w.widths, seed=7)
+    G = O.descriptors(m, rep.x0, rep.box)
+    s.set_normalisation(m, G, rep.Z)
+    rng = np.random.default_rng(3)
+    steps = min(a.steps, 20)
+    warm = min(a.warmup, 2)
+    for _ in range(warm):
+        O.energy_forces(m, rep.Z, rep.x0 + rng.normal(scale=0.05, size=rep.x0.shape), rep.box)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.energy_forces(m, rep.Z, rep.x0 + rng.normal(scale=0.05, size=rep.x0.shape), rep.box)
+    dt = time.perf_counter() - t0
+    value = steps * rep.n_atoms / dt
+    sample = "%d steps x 1 bead (%d bead-atoms) of the %s workload, FP64 oracle force evaluation" % (
+        steps, rep.n_atoms, w.name)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w, "fp64", 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

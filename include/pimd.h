@@ -1,0 +1,253 @@
+/*
+ * pimd.h -- C ABI of the GB300 path-integral molecular dynamics library with a
+ * symmetry-function neural-network potential.
+ *
+ * The library advances ring polymers (paper Sec. 2.1: effective Hamiltonian
+ * with P beads per atom, normal-mode transformation, H_eff = H_p + U) whose
+ * potential U is a per-element network on radial/angular symmetry functions
+ * (the descriptor-based energy model of Sec. 1, ref. [17]); forces are the
+ * analytic gradient of that energy (Sec. 2.2). One context holds any number
+ * of independent replicas with their own N, P, temperature and seed (the
+ * multi-trajectory mode of Sec. 2.3), all advanced by the same launches.
+ *
+ * Conventions
+ *   units: Angstrom, fs, amu, eV, K.
+ *   ring polymer: i-PI form, beta_P = beta / P, omega_P = P k_B T / hbar,
+ *   sampled at T_P = P T (equivalent to Sec. 2.1 after dividing by P).
+ *   bead-atom order: replica-major, then bead, then atom.
+ *   normal-mode state: per replica [P][N][3] FP64, replicas concatenated.
+ *
+ * Memory ownership
+ *   The library never allocates device memory. The caller passes one device
+ *   workspace to pimd_create (size from pimd_workspace_size) and keeps it
+ *   alive until pimd_destroy. Host arrays passed in are copied before the
+ *   call returns. Device pointers passed to pimd_energy_forces /
+ *   pimd_descriptors are caller-owned and used stream-ordered on the
+ *   context's stream.
+ *
+ * Errors
+ *   Every call returns a pimd_status. Argument and state errors leave the
+ *   context unchanged. Errors detected on the device (non-finite forces,
+ *   neighbour overflow) are reported at the next synchronising call
+ *   (pimd_sync, pimd_estimators, pimd_get_state, pimd_get_forces). A CUDA
+ *   error is sticky: destroy the context. Nothing here throws or exits.
+ */
+#ifndef PIMD_H
+#define PIMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIMD_ABI_VERSION 1
+#define PIMD_N_RADIAL 32
+#define PIMD_N_ANGULAR 32
+#define PIMD_N_DESC 64
+#define PIMD_MAX_ELEMENTS 8
+#define PIMD_MAX_LAYERS 4
+#define PIMD_MAX_WIDTH 256
+#define PIMD_MAX_BEADS 256
+#define PIMD_MAX_NEIGHBOURS 256
+
+typedef enum {
+    PIMD_OK = 0,
+    PIMD_ERR_INVALID_ARG = -1,
+    PIMD_ERR_STATE = -2,
+    PIMD_ERR_WORKSPACE_TOO_SMALL = -3,
+    PIMD_ERR_CUDA = -4,
+    PIMD_ERR_NONFINITE = -5,
+    PIMD_ERR_TIMEOUT = -6,
+    PIMD_ERR_NBR_OVERFLOW = -7,
+    PIMD_ERR_UNSUPPORTED = -8
+} pimd_status;
+
+/* arithmetic of the force evaluation */
+typedef enum {
+    PIMD_FP64 = 0,     /* descriptors, network, adjoint all FP64                    */
+    PIMD_FP32 = 1,     /* FP32 descriptors/adjoint, FP32 network on CUDA cores      */
+    PIMD_BF16_TC = 2   /* FP32 descriptors/adjoint, BF16 network on tcgen05 tensor
+                          cores with FP32 accumulation in tensor memory            */
+} pimd_precision;
+
+typedef enum {
+    PIMD_POT_MODEL = 0,     /* symmetry-function network (set by pimd_set_weights)  */
+    PIMD_POT_HARMONIC = 1   /* V = sum_i 1/2 m_i omega^2 |x_i|^2 (Sec. S1 test case) */
+} pimd_potential;
+
+typedef struct {
+    double dt_fs;            /* time step                                          */
+    double gamma0_per_fs;    /* PILE-L centroid friction 1/tau_0                   */
+    double pile_lambda;      /* internal-mode friction gamma_k = 2 lambda omega_k  */
+    double cutoff_A;         /* symmetry-function cutoff r_c (graph edges)         */
+    int precision;           /* pimd_precision                                     */
+    int thermostat;          /* 0 = NVE, 1 = PILE-L                                */
+    int potential;           /* pimd_potential                                     */
+    int max_neighbours;      /* neighbour slots per atom, multiple of 32, <= 256;
+                                0 selects 128                                      */
+    double omega_harm;       /* 1/fs, PIMD_POT_HARMONIC only                       */
+    int n_hidden;            /* network hidden layers (1..4)                       */
+    int widths[PIMD_MAX_LAYERS]; /* hidden widths, each a multiple of 32, <= 256   */
+    void* stream;            /* cudaStream_t for all work; NULL = default stream   */
+    int timing;              /* nonzero: record CUDA events around every stage of
+                                a step (see pimd_stage_times)                      */
+    int nbr_algo;            /* 0: cell lists where a periodic box holds >= 3
+                                cells of edge >= cutoff per side, else all pairs;
+                                1: all pairs everywhere. Same lists either way.    */
+} pimd_config;
+
+/* stages of one step, in launch order (pimd_stage_times) */
+enum {
+    PIMD_STAGE_RING_START = 0,   /* O B A in normal-mode space + beads           */
+    PIMD_STAGE_NEIGHBOURS = 1,   /* neighbour lists                              */
+    PIMD_STAGE_DESCRIPTORS = 2,  /* radial + angular symmetry functions          */
+    PIMD_STAGE_NETWORK = 3,      /* per-element network forward + input gradient */
+    PIMD_STAGE_ADJOINT = 4,      /* forces and virial                            */
+    PIMD_STAGE_ENERGY = 5,       /* per-bead energies                            */
+    PIMD_STAGE_RING_FINISH = 6,  /* C^T f, B O, step counter                     */
+    PIMD_N_STAGES = 7
+};
+
+typedef struct {
+    int n_atoms;             /* N >= 1                                             */
+    int n_beads;             /* P, 1..256                                          */
+    const int* Z;            /* host [N] element numbers                           */
+    const double* x0;        /* host [N][3] initial positions (all beads start here) */
+    const double* mass;      /* host [N] amu, or NULL for standard masses of H C N O */
+    double box[3];           /* orthorhombic periodic box; all 0 = non-periodic.
+                                Periodic boxes need min(box) >= 2 cutoff            */
+    double T_K;              /* physical temperature                               */
+    uint64_t seed;           /* Philox key of this replica's noise                 */
+} pimd_replica_desc;
+
+/* Per-element network on the descriptor G (64 = 32 radial + 32 angular):
+ *   h_0 = (G - mu) / sigma,  h_l = tanh(W_l h_{l-1} + b_l),
+ *   E_i = s_E (w_out . h_L + b_out) + e_Z.
+ * params[e] is element Z[e]'s flat FP64 host blob in this order:
+ *   for each hidden layer l: W_l [h_l][h_{l-1}] row-major, b_l [h_l];
+ *   w_out [h_L]; b_out; mu [64]; sigma [64]; s_E; e_Z.
+ * Descriptors (cutoff fc(r) = (cos(pi r / r_c) + 1) / 2 for r < r_c):
+ *   G[mu]      = sum_j exp(-eta_R (r_ij - r_mu[mu])^2) fc(r_ij),    mu < 32
+ *   G[32 + nu] = 2^(1-zeta) sum_{j<k} (1 + lambda cos theta_jik)^zeta
+ *                exp(-eta_A (r_ij^2 + r_ik^2)) fc(r_ij) fc(r_ik)
+ *   with nu = (zeta_index * 2 + lambda_index) * 4 + eta_index; zeta must be
+ *   {1, 2, 4, 8} and lambda {+1, -1} in that order.                        */
+typedef struct {
+    int n_elements;
+    const int* Z;                 /* [n_elements]                                  */
+    int n_hidden;                 /* must equal pimd_config.n_hidden               */
+    const int* widths;            /* [n_hidden], must equal pimd_config.widths     */
+    const double* const* params;  /* [n_elements] host blobs (layout above)        */
+    double eta_R;
+    const double* r_mu;           /* [32]                                          */
+    const int* zeta;              /* [4]                                           */
+    const double* lambda;         /* [2]                                           */
+    const double* eta_A;          /* [4]                                           */
+} pimd_model_desc;
+
+/* per-replica estimators (finite-P ensemble averages of Sec. 2.1), eV */
+typedef struct {
+    double V_mean;     /* (1/P) sum_k V_k                                          */
+    double K_prim;     /* primitive kinetic-energy estimator                       */
+    double K_cv;       /* centroid-virial kinetic-energy estimator                 */
+    double E_tot;      /* K_cv + V_mean                                            */
+    double W[9];       /* bead-averaged virial tensor, W_ab = sum_i x_a f_b form    */
+    double H_cons;     /* ring-polymer Hamiltonian minus thermostat heat           */
+    double Q_thermo;   /* kinetic energy added by all thermostat steps             */
+    double T_kin;      /* ring-polymer kinetic temperature (expect P T), K         */
+    double nbr_mean;   /* mean neighbours per bead-atom at the last evaluation     */
+    double nbr_max;    /* largest neighbour count at the last evaluation           */
+} pimd_est;
+
+typedef struct pimd_ctx pimd_ctx;
+
+/* Device workspace bytes needed for this configuration and replica set.
+ * Errors: INVALID_ARG for NULL pointers or inconsistent sizes.            */
+int pimd_workspace_size(const pimd_config* cfg, const pimd_replica_desc* reps, int n_reps,
+                        size_t* bytes);
+
+/* Create a context. Initial state (Sec. 2.1 ring polymer): every bead at x0,
+ * normal-mode momenta drawn from N(0, m k_B T_P) with Philox stream 1.
+ * `workspace` is a caller-owned device buffer of >= pimd_workspace_size bytes,
+ * aligned to 256 bytes. Errors: INVALID_ARG, WORKSPACE_TOO_SMALL, CUDA.      */
+int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_reps,
+                void* workspace, size_t ws_bytes, pimd_ctx** out);
+
+/* Load the network (FP64 host parameters, converted to the working precision)
+ * and evaluate forces at the current state. Every element present in the
+ * replicas must be in the model. Errors: INVALID_ARG (shape mismatch, missing
+ * element, unsupported zeta/lambda), STATE (potential is not PIMD_POT_MODEL). */
+int pimd_set_weights(pimd_ctx* ctx, const pimd_model_desc* model);
+
+/* Advance all replicas by n_steps of OBABO in normal-mode space:
+ * O(dt/2) B(dt/2) A(dt) [forces] B(dt/2) O(dt/2) with exact free-ring-polymer
+ * A and PILE-L O (Philox counter: index, step, replica, stream 2 / 3).
+ * Asynchronous on the context stream. Errors: STATE if weights are missing. */
+int pimd_step(pimd_ctx* ctx, int n_steps);
+
+/* Potential energy, forces and virial of arbitrary bead positions, without
+ * touching the dynamical state. x_dev: device [B][3] FP64 positions in
+ * bead-atom order (B = sum_r N_r P_r), or NULL for the current beads.
+ * e_dev: device [S] FP64 per-bead energies V_k (S = sum_r P_r), may be NULL.
+ * f_dev: device [B][3] FP64 forces -dV_k/dx, may be NULL.
+ * virial_dev: device [S][9] FP64 per-bead virials, may be NULL.
+ * Stream-ordered; returns without synchronising.                            */
+int pimd_energy_forces(pimd_ctx* ctx, const double* x_dev, double* e_dev, double* f_dev,
+                       double* virial_dev);
+
+/* Raw descriptors G (before normalisation) of arbitrary bead positions:
+ * x_dev as in pimd_energy_forces (NULL = current beads); G_dev: device
+ * [B][64] FP64. Stream-ordered.                                             */
+int pimd_descriptors(pimd_ctx* ctx, const double* x_dev, double* G_dev);
+
+/* Synchronise and fill out_host[0..n_reps) with each replica's estimators.
+ * Errors: INVALID_ARG if n_reps differs from the context's count; device
+ * errors (NONFINITE, NBR_OVERFLOW) detected since the last sync.             */
+int pimd_estimators(pimd_ctx* ctx, pimd_est* out_host, int n_reps);
+
+/* Checkpoint / resume. Host arrays of 3 sum_r P_r N_r doubles each (normal-
+ * mode positions and momenta), the step counter and the accumulated
+ * thermostat heat per replica ([n_reps]). set_state recomputes forces; a
+ * resumed run is bit-identical to an uninterrupted one. get_state syncs.    */
+int pimd_get_state(pimd_ctx* ctx, double* q_nm, double* p_nm, uint64_t* step, double* Q_thermo);
+int pimd_set_state(pimd_ctx* ctx, const double* q_nm, const double* p_nm, uint64_t step,
+                   const double* Q_thermo);
+
+/* Current bead positions [B][3], forces [B][3] and per-bead energies [S]
+ * copied to host arrays (any may be NULL). Synchronises.                     */
+int pimd_get_forces(pimd_ctx* ctx, double* x_host, double* f_host, double* V_host);
+
+/* Neighbour lists of the last force evaluation: nnb_host [B] counts and
+ * nbr_host [B][max_neighbours] atom indices within each bead (ascending).
+ * Synchronises.                                                             */
+int pimd_get_neighbours(pimd_ctx* ctx, int* nnb_host, int* nbr_host);
+
+/* Device time (ms) of each stage of the most recent step run by pimd_step,
+ * measured with CUDA events on the context stream (requires cfg.timing).
+ * ms: host [PIMD_N_STAGES]. Synchronises. Errors: STATE without timing or
+ * before the first step.                                                    */
+int pimd_stage_times(pimd_ctx* ctx, float* ms);
+
+/* Number of kernels one step launches (memset nodes not counted).          */
+int pimd_kernels_per_step(const pimd_ctx* ctx);
+
+/* Block until all queued work is done; report device-side errors.          */
+int pimd_sync(pimd_ctx* ctx);
+
+/* Sizes of the context: bead-atoms B, bead-systems S, replicas R, slots.  */
+int pimd_sizes(const pimd_ctx* ctx, int64_t* B, int64_t* S, int* R, int* max_neighbours);
+
+void pimd_destroy(pimd_ctx* ctx);
+
+/* Message of the last failed call on ctx (NULL ctx: the calling thread's
+ * last failure outside a context). Never NULL.                              */
+const char* pimd_last_error(const pimd_ctx* ctx);
+
+int pimd_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

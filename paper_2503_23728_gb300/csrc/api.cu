@@ -1,0 +1,932 @@
+// api.cu -- the C ABI (include/pimd.h): context set-up inside the caller's
+// workspace, weight loading, the per-step launch sequence captured in CUDA
+// graphs, and the synchronising queries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pimd.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace pimd;
+
+namespace {
+
+thread_local std::string g_tls_error;
+
+struct HostRep {
+    int N = 0, P = 0;
+    std::vector<int> Z;
+    std::vector<double> mass, x0;
+    double box[3] = {0, 0, 0};
+    double T = 0;
+    unsigned long long seed = 0;
+};
+
+double default_mass(int z)
+{
+    switch (z) {
+        case 1: return 1.008;
+        case 6: return 12.011;
+        case 7: return 14.007;
+        case 8: return 15.999;
+        default: return -1.0;
+    }
+}
+
+// Everything the host computes before touching the device.
+struct Build {
+    std::vector<Rep> reps;
+    std::vector<BeadSys> bsys;
+    std::vector<int> ba_sys, atype, perm, tile_type;
+    std::vector<double> mass, x0, cmat;
+    std::vector<Mode> modes;
+    std::vector<int2> rp_blocks;
+    std::vector<int> typeZ;
+    std::vector<int> cell_bs;
+    int total_cells = 0, max_cells = 0;
+    int R = 0, S = 0, B = 0, NA = 0, rows_pad = 0;
+    size_t blob = 0, wtc_bytes = 0, wtc_vec = 0;
+    bool periodic_any = false;
+};
+
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        off = (off + 255) & ~size_t(255);
+        size_t o = off;
+        off += bytes;
+        return o;
+    }
+};
+
+struct Offsets {
+    size_t reps, bsys, ba_sys, mass, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
+        cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
+        fnm, Q, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
+};
+
+int check_config(const pimd_config* cfg, std::string& e)
+{
+    if (!cfg) { e = "cfg is NULL"; return PIMD_ERR_INVALID_ARG; }
+    if (!(cfg->dt_fs != 0.0) || !std::isfinite(cfg->dt_fs)) { e = "dt_fs must be finite and non-zero"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->precision < 0 || cfg->precision > 2) { e = "unknown precision"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->thermostat != 0 && cfg->thermostat != 1) { e = "thermostat must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->nbr_algo != 0 && cfg->nbr_algo != 1) { e = "nbr_algo must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->potential != PIMD_POT_MODEL && cfg->potential != PIMD_POT_HARMONIC) { e = "unknown potential"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->thermostat == 1 && !(cfg->gamma0_per_fs >= 0.0)) { e = "gamma0_per_fs must be >= 0"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->thermostat == 1 && !(cfg->pile_lambda >= 0.0)) { e = "pile_lambda must be >= 0"; return PIMD_ERR_INVALID_ARG; }
+    int mnb = cfg->max_neighbours == 0 ? 128 : cfg->max_neighbours;
+    if (mnb < 32 || mnb > PIMD_MAX_NEIGHBOURS || mnb % 32) { e = "max_neighbours must be a multiple of 32 in [32, 256]"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->potential == PIMD_POT_MODEL) {
+        if (!(cfg->cutoff_A > 0.0)) { e = "cutoff_A must be > 0"; return PIMD_ERR_INVALID_ARG; }
+        if (cfg->n_hidden < 1 || cfg->n_hidden > PIMD_MAX_LAYERS) { e = "n_hidden must be 1..4"; return PIMD_ERR_INVALID_ARG; }
+        for (int l = 0; l < cfg->n_hidden; ++l) {
+            if (cfg->widths[l] != cfg->widths[0]) { e = "hidden layers must share one width"; return PIMD_ERR_UNSUPPORTED; }
+        }
+        int w = cfg->widths[0];
+        if (w != 64 && w != 128 && w != 256) { e = "hidden width must be 64, 128 or 256"; return PIMD_ERR_UNSUPPORTED; }
+        if (cfg->precision == PIMD_BF16_TC && !network_tc_supported(w, cfg->n_hidden)) {
+            e = "tensor-core network does not support this width"; return PIMD_ERR_UNSUPPORTED;
+        }
+    } else if (!(cfg->omega_harm >= 0.0)) {
+        e = "omega_harm must be >= 0"; return PIMD_ERR_INVALID_ARG;
+    }
+    return PIMD_OK;
+}
+
+void nm_matrix(int P, double* C)
+{
+    for (int j = 0; j < P; ++j)
+        for (int k = 0; k < P; ++k) {
+            double v;
+            if (k == 0) v = 1.0 / std::sqrt((double)P);
+            else if (2 * k < P) v = std::sqrt(2.0 / P) * std::cos(2.0 * M_PI * j * k / P);
+            else if (2 * k == P) v = ((j & 1) ? -1.0 : 1.0) / std::sqrt((double)P);
+            else v = std::sqrt(2.0 / P) * std::sin(2.0 * M_PI * j * k / P);
+            C[(size_t)j * P + k] = v;
+        }
+}
+
+int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Build& b, std::string& e)
+{
+    int rc = check_config(cfg, e);
+    if (rc) return rc;
+    if (!reps || n < 1) { e = "need at least one replica"; return PIMD_ERR_INVALID_ARG; }
+    const int mnb = cfg->max_neighbours == 0 ? 128 : cfg->max_neighbours;
+    (void)mnb;
+    std::vector<HostRep> hr(n);
+    long long B = 0, S = 0, NA = 0;
+    std::vector<int> zs;
+    for (int r = 0; r < n; ++r) {
+        const pimd_replica_desc& d = reps[r];
+        if (d.n_atoms < 1 || d.n_beads < 1 || d.n_beads > PIMD_MAX_BEADS) { e = "replica " + std::to_string(r) + ": bad N or P"; return PIMD_ERR_INVALID_ARG; }
+        if (!d.Z || !d.x0) { e = "replica " + std::to_string(r) + ": Z and x0 are required"; return PIMD_ERR_INVALID_ARG; }
+        if (!(d.T_K > 0.0) || !std::isfinite(d.T_K)) { e = "replica " + std::to_string(r) + ": T_K must be > 0"; return PIMD_ERR_INVALID_ARG; }
+        const bool per = d.box[0] != 0.0 || d.box[1] != 0.0 || d.box[2] != 0.0;
+        if (per) {
+            for (int a = 0; a < 3; ++a)
+                if (!(d.box[a] > 0.0)) { e = "replica " + std::to_string(r) + ": box lengths must all be > 0 or all 0"; return PIMD_ERR_INVALID_ARG; }
+            if (cfg->potential == PIMD_POT_MODEL && std::min(d.box[0], std::min(d.box[1], d.box[2])) < 2.0 * cfg->cutoff_A) {
+                e = "replica " + std::to_string(r) + ": periodic box shorter than twice the cutoff"; return PIMD_ERR_INVALID_ARG;
+            }
+        }
+        HostRep& h = hr[r];
+        h.N = d.n_atoms; h.P = d.n_beads; h.T = d.T_K; h.seed = d.seed;
+        for (int a = 0; a < 3; ++a) h.box[a] = d.box[a];
+        h.Z.assign(d.Z, d.Z + d.n_atoms);
+        h.x0.assign(d.x0, d.x0 + 3 * (size_t)d.n_atoms);
+        h.mass.resize(d.n_atoms);
+        for (int i = 0; i < d.n_atoms; ++i) {
+            double m = d.mass ? d.mass[i] : default_mass(h.Z[i]);
+            if (!(m > 0.0)) { e = "replica " + std::to_string(r) + ": no mass for element " + std::to_string(h.Z[i]); return PIMD_ERR_INVALID_ARG; }
+            if (!std::isfinite(h.x0[3 * i]) || !std::isfinite(h.x0[3 * i + 1]) || !std::isfinite(h.x0[3 * i + 2])) {
+                e = "replica " + std::to_string(r) + ": non-finite x0"; return PIMD_ERR_INVALID_ARG;
+            }
+            h.mass[i] = m;
+            zs.push_back(h.Z[i]);
+        }
+        B += (long long)d.n_atoms * d.n_beads;
+        S += d.n_beads;
+        NA += d.n_atoms;
+    }
+    if (3 * B >= (1ll << 31) - 1024) { e = "too many bead-atoms"; return PIMD_ERR_INVALID_ARG; }
+    std::sort(zs.begin(), zs.end());
+    zs.erase(std::unique(zs.begin(), zs.end()), zs.end());
+    if ((int)zs.size() > PIMD_MAX_ELEMENTS) { e = "more than 8 elements"; return PIMD_ERR_UNSUPPORTED; }
+    b.typeZ = zs;
+    b.R = n; b.S = (int)S; b.B = (int)B; b.NA = (int)NA;
+
+    // normal-mode matrices, one per distinct P
+    std::map<int, int> cm_off;
+    for (int r = 0; r < n; ++r) {
+        int P = hr[r].P;
+        if (!cm_off.count(P)) {
+            cm_off[P] = (int)b.cmat.size();
+            b.cmat.resize(b.cmat.size() + (size_t)P * P);
+            nm_matrix(P, b.cmat.data() + cm_off[P]);
+        }
+    }
+    const int rp_threads = 256;
+    int ba0 = 0, bs0 = 0, atom0 = 0, mode0 = 0;
+    for (int r = 0; r < n; ++r) {
+        const HostRep& h = hr[r];
+        Rep rp;
+        std::memset(&rp, 0, sizeof(rp));
+        rp.N = h.N; rp.P = h.P; rp.ba0 = ba0; rp.bs0 = bs0; rp.atom0 = atom0; rp.cmat = cm_off[h.P]; rp.mode0 = mode0;
+        rp.periodic = (h.box[0] != 0.0) ? 1 : 0;
+        if (rp.periodic) b.periodic_any = true;
+        for (int a = 0; a < 3; ++a) {
+            rp.L[a] = rp.periodic ? h.box[a] : 0.0;
+            rp.invL[a] = rp.periodic ? 1.0 / h.box[a] : 0.0;
+            rp.Lf[a] = (float)rp.L[a];
+            rp.invLf[a] = (float)rp.invL[a];
+        }
+        rp.kT_md = h.P * KB * h.T / MVV2E;
+        rp.seed = h.seed;
+        // cell lists: >= 3 cells per side with edge >= cutoff (1e-5 margin
+        // against rounding of the FP32 cell coordinate)
+        if (rp.periodic && cfg->potential == PIMD_POT_MODEL && cfg->nbr_algo == 0) {
+            int nc[3];
+            for (int a = 0; a < 3; ++a) nc[a] = (int)std::floor(h.box[a] / (cfg->cutoff_A * (1.0 + 1e-5)));
+            if (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3 && (long long)nc[0] * nc[1] * nc[2] <= 16384) {
+                for (int a = 0; a < 3; ++a) rp.nc[a] = nc[a];
+                rp.ncells = nc[0] * nc[1] * nc[2];
+                rp.cell0 = b.total_cells;
+                b.total_cells += rp.ncells * h.P;
+                b.max_cells = std::max(b.max_cells, rp.ncells);
+                for (int k = 0; k < h.P; ++k) b.cell_bs.push_back(bs0 + k);
+            }
+        }
+        b.reps.push_back(rp);
+        const double wP = h.P * KB * h.T / HBAR;
+        for (int k = 0; k < h.P; ++k) {
+            Mode md;
+            std::memset(&md, 0, sizeof(md));
+            md.w = 2.0 * wP * std::sin(k * M_PI / h.P);
+            md.cw = std::cos(md.w * cfg->dt_fs);
+            md.sw = std::sin(md.w * cfg->dt_fs);
+            const double gam = (k == 0) ? cfg->gamma0_per_fs : 2.0 * cfg->pile_lambda * md.w;
+            md.c1 = std::exp(-0.5 * cfg->dt_fs * gam);
+            md.c2 = std::sqrt(1.0 - md.c1 * md.c1);
+            b.modes.push_back(md);
+        }
+        for (int k = 0; k < h.P; ++k) {
+            BeadSys s;
+            s.ba0 = ba0 + k * h.N; s.N = h.N; s.rep = r; s.bead = k;
+            b.bsys.push_back(s);
+            for (int i = 0; i < h.N; ++i) b.ba_sys.push_back(bs0 + k);
+        }
+        for (int i = 0; i < h.N; ++i) {
+            b.mass.push_back(h.mass[i]);
+            b.atype.push_back((int)(std::lower_bound(zs.begin(), zs.end(), h.Z[i]) - zs.begin()));
+            for (int a = 0; a < 3; ++a) b.x0.push_back(h.x0[3 * i + a]);
+        }
+        const int T = rp_threads / h.P;
+        for (int first = 0; first < 3 * h.N; first += T) b.rp_blocks.push_back(make_int2(r, first));
+        ba0 += h.N * h.P; bs0 += h.P; atom0 += h.N; mode0 += h.P;
+    }
+    // network rows grouped by element type, each group padded to 128 rows
+    if (cfg->potential == PIMD_POT_MODEL) {
+        std::vector<std::vector<int>> rows(zs.size());
+        for (int r = 0; r < n; ++r) {
+            const Rep& rp = b.reps[r];
+            for (int k = 0; k < rp.P; ++k)
+                for (int i = 0; i < rp.N; ++i) rows[b.atype[rp.atom0 + i]].push_back(rp.ba0 + k * rp.N + i);
+        }
+        for (size_t t = 0; t < zs.size(); ++t) {
+            std::vector<int> v = rows[t];
+            std::sort(v.begin(), v.end());
+            size_t padded = (v.size() + TILE_ROWS - 1) / TILE_ROWS * TILE_ROWS;
+            for (size_t q = 0; q < padded; ++q) b.perm.push_back(q < v.size() ? v[q] : -1);
+            for (size_t q = 0; q < padded / TILE_ROWS; ++q) b.tile_type.push_back((int)t);
+        }
+        b.rows_pad = (int)b.perm.size();
+        b.blob = blob_elems(cfg->n_hidden, cfg->widths);
+        if (cfg->precision == PIMD_BF16_TC) {
+            b.wtc_bytes = tc_weight_bytes(cfg->widths[0], cfg->n_hidden);
+            b.wtc_vec = (size_t)cfg->n_hidden * cfg->widths[0] + cfg->widths[0] + 2 * ND + 4;
+        }
+    }
+    return PIMD_OK;
+}
+
+Offsets layout(const pimd_config* cfg, const Build& b)
+{
+    const int mnb = cfg->max_neighbours == 0 ? 128 : cfg->max_neighbours;
+    const size_t rs = cfg->precision == PIMD_FP64 ? sizeof(double) : sizeof(float);
+    const size_t v4 = cfg->precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
+    Carve c;
+    Offsets o;
+    o.reps = c.take(sizeof(Rep) * b.R);
+    o.bsys = c.take(sizeof(BeadSys) * b.S);
+    o.ba_sys = c.take(sizeof(int) * b.B);
+    o.mass = c.take(sizeof(double) * b.NA);
+    o.atype = c.take(sizeof(int) * b.NA);
+    o.x0 = c.take(sizeof(double) * 3 * (size_t)b.NA);
+    o.cmat = c.take(sizeof(double) * b.cmat.size());
+    o.modes = c.take(sizeof(Mode) * b.modes.size());
+    o.rp_blocks = c.take(sizeof(int2) * b.rp_blocks.size());
+    o.x = c.take(v4 * b.B);
+    o.f = c.take(v4 * b.B);
+    const bool model = cfg->potential == PIMD_POT_MODEL;
+    o.nbr = c.take(model ? sizeof(int) * (size_t)b.B * mnb : 0);
+    o.nnb = c.take(sizeof(int) * b.B);
+    o.cell_start = c.take(sizeof(int) * (size_t)b.total_cells);
+    o.cell_cnt = c.take(sizeof(int) * (size_t)b.total_cells);
+    o.cell_atoms = c.take(b.total_cells ? sizeof(int) * (size_t)b.B : 0);
+    o.cell_bs = c.take(sizeof(int) * b.cell_bs.size());
+    o.G = c.take(model ? rs * (size_t)b.B * ND : 0);
+    o.dEdG = c.take(model ? rs * (size_t)b.B * ND : 0);
+    o.Eatom = c.take(rs * b.B);
+    o.V = c.take(sizeof(double) * b.S);
+    o.W = c.take(sizeof(double) * 9 * (size_t)b.S);
+    o.q = c.take(sizeof(double) * 3 * (size_t)b.B);
+    o.p = c.take(sizeof(double) * 3 * (size_t)b.B);
+    o.fnm = c.take(sizeof(double) * 3 * (size_t)b.B);
+    o.Q = c.take(sizeof(double) * b.R);
+    o.step = c.take(sizeof(unsigned long long));
+    o.err = c.take(sizeof(DevErr));
+    o.est = c.take(sizeof(double) * EST_STRIDE * b.R);
+    o.perm = c.take(sizeof(int) * b.perm.size());
+    o.tile_type = c.take(sizeof(int) * b.tile_type.size());
+    o.wts = c.take(rs * b.blob * b.typeZ.size());
+    o.wtc = c.take(b.wtc_bytes * b.typeZ.size());
+    o.wtc_vec = c.take(sizeof(float) * b.wtc_vec * b.typeZ.size());
+    o.total = c.take(0) + 256;
+    return o;
+}
+
+}  // namespace
+
+struct pimd_ctx {
+    Dev d;
+    pimd_config cfg;
+    cudaStream_t st = nullptr;
+    Build build;
+    DescParams<float> dpf;
+    DescParams<double> dpd;
+    bool weights_set = false, forces_valid = false, beads_current = true;
+    unsigned long long step_host = 0;
+    cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev[PIMD_N_STAGES + 1] = {};
+    bool stepped = false;
+    std::string err;
+    unsigned char* ws = nullptr;
+};
+
+namespace {
+
+int fail(pimd_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_tls_error = msg;
+    return code;
+}
+
+int cuda_check(pimd_ctx* c, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return PIMD_OK;
+    // report, and clear the runtime's last-error slot so that an error that
+    // is not sticky does not surface in the caller's next CUDA call
+    cudaGetLastError();
+    return fail(c, PIMD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+const void* dparams(const pimd_ctx* c)
+{
+    return c->d.precision == PIMD_FP64 ? (const void*)&c->dpd : (const void*)&c->dpf;
+}
+
+// event i marks the start of stage i (i = PIMD_N_STAGES: end of the step)
+void mark(pimd_ctx* c, int i, cudaStream_t st, bool timed)
+{
+    // external record nodes: the events fire when the captured graph runs
+    if (timed && c->ev[i]) cudaEventRecordWithFlags(c->ev[i], st, cudaEventRecordExternal);
+}
+
+void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false)
+{
+    Dev& d = c->d;
+    const size_t v4 = d.precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
+    cudaMemsetAsync(d.f, 0, v4 * d.B, st);
+    cudaMemsetAsync(d.W, 0, sizeof(double) * 9 * d.S, st);
+    mark(c, PIMD_STAGE_NEIGHBOURS, st, timed);
+    if (d.potential == PIMD_POT_HARMONIC) {
+        launch_harmonic(d, st);
+        mark(c, PIMD_STAGE_DESCRIPTORS, st, timed);
+        mark(c, PIMD_STAGE_NETWORK, st, timed);
+        mark(c, PIMD_STAGE_ADJOINT, st, timed);
+    } else {
+        launch_neighbours(d, st);
+        mark(c, PIMD_STAGE_DESCRIPTORS, st, timed);
+        launch_descriptors(d, dparams(c), st);
+        mark(c, PIMD_STAGE_NETWORK, st, timed);
+        if (d.precision == PIMD_BF16_TC) launch_network_tc(d, st);
+        else launch_network_fp(d, st);
+        mark(c, PIMD_STAGE_ADJOINT, st, timed);
+        launch_adjoint(d, dparams(c), st);
+    }
+    mark(c, PIMD_STAGE_ENERGY, st, timed);
+    launch_energy_reduce(d, st);
+}
+void eval_forces(pimd_ctx* c) { eval_forces(c, c->st); }
+
+void one_step(pimd_ctx* c, cudaStream_t st, bool timed)
+{
+    mark(c, PIMD_STAGE_RING_START, st, timed);
+    launch_rp_start(c->d, st);
+    eval_forces(c, st, timed);
+    mark(c, PIMD_STAGE_RING_FINISH, st, timed);
+    launch_rp_finish(c->d, true, st);
+    launch_bump_step(c->d, st);
+    mark(c, PIMD_N_STAGES, st, timed);
+}
+
+int refresh_forces(pimd_ctx* c)
+{
+    if (!c->beads_current) {
+        launch_beads(c->d, c->st);
+        c->beads_current = true;
+    }
+    eval_forces(c);
+    launch_rp_finish(c->d, false, c->st);
+    c->forces_valid = true;
+    return cuda_check(c, cudaGetLastError(), "force evaluation launch");
+}
+
+// Graphs are recorded on a private stream (the caller's stream may be the
+// legacy default stream, which cannot be captured) and launched on the
+// context stream.
+int capture(pimd_ctx* c, int nsteps, cudaGraphExec_t* out)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!c->cap) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamCreateWithFlags");
+    e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamBeginCapture");
+    for (int s = 0; s < nsteps; ++s) one_step(c, c->cap, c->cfg.timing != 0 && s == nsteps - 1);
+    e = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_check(c, e, "cudaGraphInstantiate");
+}
+
+int device_errors(pimd_ctx* c)
+{
+    DevErr h;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d.err, sizeof(DevErr), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_check(c, e, "synchronise");
+    if (h.flags) {
+        cudaMemsetAsync(c->d.err, 0, sizeof(DevErr), c->st);
+        cudaStreamSynchronize(c->st);
+        if (h.flags & ERR_NBR_OVERFLOW)
+            return fail(c, PIMD_ERR_NBR_OVERFLOW, "neighbour list overflow: an atom has " + std::to_string(h.max_nbr) +
+                                                      " neighbours, max_neighbours is " + std::to_string(c->d.maxnb));
+        if (h.flags & ERR_NONFINITE) return fail(c, PIMD_ERR_NONFINITE, "non-finite forces");
+        if (h.flags & ERR_TIMEOUT) return fail(c, PIMD_ERR_TIMEOUT, "device wait timed out");
+    }
+    return PIMD_OK;
+}
+
+template <typename T>
+int upload(pimd_ctx* c, void* dst, const std::vector<T>& v)
+{
+    if (v.empty()) return PIMD_OK;
+    return cuda_check(c, cudaMemcpyAsync(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->st),
+                      "upload");
+}
+
+}  // namespace
+
+extern "C" {
+
+int pimd_abi_version(void) { return PIMD_ABI_VERSION; }
+
+int pimd_workspace_size(const pimd_config* cfg, const pimd_replica_desc* reps, int n_reps, size_t* bytes)
+{
+    if (!bytes) return fail(nullptr, PIMD_ERR_INVALID_ARG, "bytes is NULL");
+    Build b;
+    std::string e;
+    int rc = make_build(cfg, reps, n_reps, b, e);
+    if (rc) return fail(nullptr, rc, e);
+    *bytes = layout(cfg, b).total;
+    return PIMD_OK;
+}
+
+int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_reps, void* workspace,
+                size_t ws_bytes, pimd_ctx** out)
+{
+    if (!out) return fail(nullptr, PIMD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    pimd_ctx* c = new (std::nothrow) pimd_ctx();
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "host allocation failed");
+    std::string e;
+    int rc = make_build(cfg, reps, n_reps, c->build, e);
+    if (rc) { delete c; return fail(nullptr, rc, e); }
+    const Build& b = c->build;
+    Offsets o = layout(cfg, b);
+    if (!workspace) { delete c; return fail(nullptr, PIMD_ERR_INVALID_ARG, "workspace is NULL"); }
+    if (((uintptr_t)workspace & 255u) != 0) { delete c; return fail(nullptr, PIMD_ERR_INVALID_ARG, "workspace must be 256-byte aligned"); }
+    if (ws_bytes < o.total) {
+        delete c;
+        return fail(nullptr, PIMD_ERR_WORKSPACE_TOO_SMALL,
+                    "workspace has " + std::to_string(ws_bytes) + " bytes, needs " + std::to_string(o.total));
+    }
+    c->cfg = *cfg;
+    c->st = (cudaStream_t)cfg->stream;
+    if (cfg->timing) {
+        for (int i = 0; i <= PIMD_N_STAGES; ++i) {
+            if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+                for (int k = 0; k < i; ++k) cudaEventDestroy(c->ev[k]);
+                delete c;
+                return fail(nullptr, PIMD_ERR_CUDA, "cudaEventCreate failed");
+            }
+        }
+    }
+    c->ws = (unsigned char*)workspace;
+    Dev& d = c->d;
+    unsigned char* w = c->ws;
+    d.R = b.R; d.S = b.S; d.B = b.B; d.NA = b.NA;
+    d.maxnb = cfg->max_neighbours == 0 ? 128 : cfg->max_neighbours;
+    d.precision = cfg->precision;
+    d.periodic_any = b.periodic_any;
+    d.reps = (Rep*)(w + o.reps);
+    d.bsys = (BeadSys*)(w + o.bsys);
+    d.ba_sys = (int*)(w + o.ba_sys);
+    d.mass = (double*)(w + o.mass);
+    d.atype = (int*)(w + o.atype);
+    d.x0 = (double*)(w + o.x0);
+    d.cmat = (double*)(w + o.cmat);
+    d.modes = (Mode*)(w + o.modes);
+    d.rp_blocks = (int2*)(w + o.rp_blocks);
+    d.n_rp_blocks = (int)b.rp_blocks.size();
+    d.rp_threads = 256;
+    d.x = w + o.x;
+    d.f = w + o.f;
+    d.nbr = (int*)(w + o.nbr);
+    d.nnb = (int*)(w + o.nnb);
+    d.cell_start = (int*)(w + o.cell_start);
+    d.cell_cnt = (int*)(w + o.cell_cnt);
+    d.cell_atoms = (int*)(w + o.cell_atoms);
+    d.cell_bs = (int*)(w + o.cell_bs);
+    d.n_cell_bs = (int)b.cell_bs.size();
+    d.max_cells = b.max_cells;
+    d.G = w + o.G;
+    d.dEdG = w + o.dEdG;
+    d.Eatom = w + o.Eatom;
+    d.V = (double*)(w + o.V);
+    d.W = (double*)(w + o.W);
+    d.q = (double*)(w + o.q);
+    d.p = (double*)(w + o.p);
+    d.fnm = (double*)(w + o.fnm);
+    d.Q = (double*)(w + o.Q);
+    d.step = (unsigned long long*)(w + o.step);
+    d.err = (DevErr*)(w + o.err);
+    d.est = (double*)(w + o.est);
+    d.perm = (int*)(w + o.perm);
+    d.tile_type = (int*)(w + o.tile_type);
+    d.rows_pad = b.rows_pad;
+    d.n_types = (int)b.typeZ.size();
+    d.n_hidden = cfg->n_hidden;
+    d.width = cfg->widths[0];
+    d.blob = b.blob;
+    d.wts = w + o.wts;
+    d.wtc = w + o.wtc;
+    d.wtc_bytes_per_type = b.wtc_bytes;
+    d.wtc_vec = (float*)(w + o.wtc_vec);
+    d.wtc_vec_per_type = b.wtc_vec;
+    d.dt = cfg->dt_fs;
+    d.gamma0 = cfg->gamma0_per_fs;
+    d.lambda = cfg->pile_lambda;
+    d.thermostat = cfg->thermostat;
+    d.potential = cfg->potential;
+    d.omega_harm = cfg->omega_harm;
+    d.rc = cfg->cutoff_A;
+
+    rc = upload(c, d.reps, b.reps);
+    if (!rc) rc = upload(c, d.bsys, b.bsys);
+    if (!rc) rc = upload(c, d.ba_sys, b.ba_sys);
+    if (!rc) rc = upload(c, d.mass, b.mass);
+    if (!rc) rc = upload(c, d.atype, b.atype);
+    if (!rc) rc = upload(c, d.x0, b.x0);
+    if (!rc) rc = upload(c, d.cmat, b.cmat);
+    if (!rc) rc = upload(c, d.modes, b.modes);
+    if (!rc) rc = upload(c, d.rp_blocks, b.rp_blocks);
+    if (!rc) rc = upload(c, d.perm, b.perm);
+    if (!rc) rc = upload(c, d.tile_type, b.tile_type);
+    if (!rc) rc = upload(c, d.cell_bs, b.cell_bs);
+    if (rc) { std::string m = c->err; delete c; return fail(nullptr, rc, m); }
+    // positions carry the element type in w
+    {
+        std::vector<unsigned char> xs(d.precision == PIMD_FP64 ? sizeof(Dbl4) * b.B : sizeof(float4) * b.B);
+        for (int r = 0; r < b.R; ++r) {
+            const Rep& rp = b.reps[r];
+            for (int k = 0; k < rp.P; ++k)
+                for (int i = 0; i < rp.N; ++i) {
+                    const size_t ba = rp.ba0 + (size_t)k * rp.N + i;
+                    const int t = b.atype[rp.atom0 + i];
+                    if (d.precision == PIMD_FP64) {
+                        Dbl4 v = {b.x0[3 * (rp.atom0 + i)], b.x0[3 * (rp.atom0 + i) + 1], b.x0[3 * (rp.atom0 + i) + 2], 0.0};
+                        long long tb = t;
+                        std::memcpy(&v.w, &tb, sizeof(double));
+                        std::memcpy(xs.data() + sizeof(Dbl4) * ba, &v, sizeof(Dbl4));
+                    } else {
+                        float4 v = make_float4((float)b.x0[3 * (rp.atom0 + i)], (float)b.x0[3 * (rp.atom0 + i) + 1],
+                                               (float)b.x0[3 * (rp.atom0 + i) + 2], 0.0f);
+                        std::memcpy(&v.w, &t, sizeof(float));
+                        std::memcpy(xs.data() + sizeof(float4) * ba, &v, sizeof(float4));
+                    }
+                }
+        }
+        rc = upload(c, d.x, xs);
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "create upload");
+        if (rc) { std::string m = c->err; delete c; return fail(nullptr, rc, m); }
+    }
+    cudaMemsetAsync(d.Q, 0, sizeof(double) * d.R, c->st);
+    cudaMemsetAsync(d.step, 0, sizeof(unsigned long long), c->st);
+    cudaMemsetAsync(d.err, 0, sizeof(DevErr), c->st);
+    cudaMemsetAsync(d.nnb, 0, sizeof(int) * d.B, c->st);
+    cudaMemsetAsync(d.V, 0, sizeof(double) * d.S, c->st);
+    cudaMemsetAsync(d.W, 0, sizeof(double) * 9 * d.S, c->st);
+    cudaMemsetAsync(d.fnm, 0, sizeof(double) * 3 * d.B, c->st);
+    launch_rp_init(d, c->st);
+    launch_beads(d, c->st);
+    c->beads_current = true;
+    rc = cuda_check(c, cudaGetLastError(), "initial state");
+    if (!rc && d.potential == PIMD_POT_HARMONIC) rc = refresh_forces(c);
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "initial state");
+    if (rc) { std::string m = c->err; delete c; return fail(nullptr, rc, m); }
+    *out = c;
+    return PIMD_OK;
+}
+
+int pimd_set_weights(pimd_ctx* c, const pimd_model_desc* m)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!m) return fail(c, PIMD_ERR_INVALID_ARG, "model is NULL");
+    if (c->d.potential != PIMD_POT_MODEL) return fail(c, PIMD_ERR_STATE, "context does not use the network potential");
+    if (m->n_hidden != c->cfg.n_hidden || !m->widths) return fail(c, PIMD_ERR_INVALID_ARG, "n_hidden differs from the config");
+    for (int l = 0; l < m->n_hidden; ++l)
+        if (m->widths[l] != c->cfg.widths[l]) return fail(c, PIMD_ERR_INVALID_ARG, "widths differ from the config");
+    if (!m->Z || !m->params || !m->r_mu || !m->zeta || !m->lambda || !m->eta_A)
+        return fail(c, PIMD_ERR_INVALID_ARG, "model arrays must not be NULL");
+    const int zeta_ok[4] = {1, 2, 4, 8};
+    for (int q = 0; q < 4; ++q)
+        if (m->zeta[q] != zeta_ok[q]) return fail(c, PIMD_ERR_UNSUPPORTED, "zeta must be {1, 2, 4, 8}");
+    if (m->lambda[0] != 1.0 || m->lambda[1] != -1.0) return fail(c, PIMD_ERR_UNSUPPORTED, "lambda must be {+1, -1}");
+    const Build& b = c->build;
+    Dev& d = c->d;
+    const size_t blob = d.blob;
+    std::vector<double> all((size_t)d.n_types * blob);
+    for (int t = 0; t < d.n_types; ++t) {
+        int e = -1;
+        for (int q = 0; q < m->n_elements; ++q)
+            if (m->Z[q] == b.typeZ[t]) e = q;
+        if (e < 0 || !m->params[e]) return fail(c, PIMD_ERR_INVALID_ARG, "model has no parameters for element " + std::to_string(b.typeZ[t]));
+        std::memcpy(all.data() + (size_t)t * blob, m->params[e], sizeof(double) * blob);
+        for (size_t q = 0; q < blob; ++q)
+            if (!std::isfinite(all[(size_t)t * blob + q])) return fail(c, PIMD_ERR_INVALID_ARG, "non-finite model parameter");
+        const double* sig = all.data() + (size_t)t * blob + blob - 2 - ND;
+        for (int q = 0; q < ND; ++q)
+            if (!(sig[q] > 0.0)) return fail(c, PIMD_ERR_INVALID_ARG, "sigma must be > 0");
+    }
+    // descriptor parameters in both precisions
+    c->dpd.rc = c->cfg.cutoff_A;
+    c->dpd.pi_over_rc = M_PI / c->cfg.cutoff_A;
+    c->dpd.eta_R = m->eta_R;
+    for (int q = 0; q < NR; ++q) c->dpd.r_mu[q] = m->r_mu[q];
+    for (int q = 0; q < 4; ++q) c->dpd.eta_A[q] = m->eta_A[q];
+    c->dpf.rc = (float)c->dpd.rc;
+    c->dpf.pi_over_rc = (float)c->dpd.pi_over_rc;
+    c->dpf.eta_R = (float)c->dpd.eta_R;
+    for (int q = 0; q < NR; ++q) c->dpf.r_mu[q] = (float)c->dpd.r_mu[q];
+    for (int q = 0; q < 4; ++q) c->dpf.eta_A[q] = (float)c->dpd.eta_A[q];
+    int rc;
+    if (d.precision == PIMD_FP64) {
+        rc = upload(c, d.wts, all);
+    } else {
+        std::vector<float> f32(all.begin(), all.end());
+        rc = upload(c, d.wts, f32);
+        if (!rc && d.precision == PIMD_BF16_TC) {
+            std::vector<unsigned char> img(d.wtc_bytes_per_type * d.n_types);
+            std::vector<float> vec(d.wtc_vec_per_type * d.n_types);
+            for (int t = 0; t < d.n_types; ++t)
+                prepare_tc_weights(d, t, all.data() + (size_t)t * blob, img.data() + d.wtc_bytes_per_type * t,
+                                   vec.data() + d.wtc_vec_per_type * t);
+            rc = upload(c, d.wtc, img);
+            if (!rc) rc = upload(c, d.wtc_vec, vec);
+            if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "weights upload");
+        }
+    }
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "weights upload");
+    if (rc) return rc;
+    c->weights_set = true;
+    rc = refresh_forces(c);
+    if (!rc) rc = device_errors(c);
+    return rc;
+}
+
+int pimd_step(pimd_ctx* c, int n_steps)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_steps < 0) return fail(c, PIMD_ERR_INVALID_ARG, "n_steps < 0");
+    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    if (n_steps == 0) return PIMD_OK;
+    int rc = PIMD_OK;
+    if (!c->forces_valid) {
+        rc = refresh_forces(c);
+        if (rc) return rc;
+    }
+    if (!c->g1) {
+        rc = capture(c, 1, &c->g1);
+        if (rc) return rc;
+    }
+    if (n_steps >= 8 && !c->g8) {
+        rc = capture(c, 8, &c->g8);
+        if (rc) return rc;
+    }
+    int left = n_steps;
+    while (left >= 8) {
+        rc = cuda_check(c, cudaGraphLaunch(c->g8, c->st), "cudaGraphLaunch");
+        if (rc) return rc;
+        left -= 8;
+    }
+    while (left-- > 0) {
+        rc = cuda_check(c, cudaGraphLaunch(c->g1, c->st), "cudaGraphLaunch");
+        if (rc) return rc;
+    }
+    c->step_host += (unsigned long long)n_steps;
+    c->stepped = true;
+    return PIMD_OK;
+}
+
+int pimd_stage_times(pimd_ctx* c, float* ms)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ms) return fail(c, PIMD_ERR_INVALID_ARG, "ms is NULL");
+    if (!c->cfg.timing || !c->ev[0]) return fail(c, PIMD_ERR_STATE, "context was created without timing");
+    if (!c->stepped) return fail(c, PIMD_ERR_STATE, "no step has run yet");
+    int rc = cuda_check(c, cudaEventSynchronize(c->ev[PIMD_N_STAGES]), "cudaEventSynchronize");
+    if (rc) return rc;
+    for (int i = 0; i < PIMD_N_STAGES; ++i) {
+        float t = 0.0f;
+        rc = cuda_check(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]), "cudaEventElapsedTime");
+        if (rc) return rc;
+        ms[i] = t;
+    }
+    return PIMD_OK;
+}
+
+int pimd_kernels_per_step(const pimd_ctx* c)
+{
+    if (!c) return 0;
+    // ring start, neighbours, descriptors, network, adjoint, energy, ring finish, step counter
+    return c->d.potential == PIMD_POT_HARMONIC ? 5 : 8;
+}
+
+int pimd_energy_forces(pimd_ctx* c, const double* x_dev, double* e_dev, double* f_dev, double* virial_dev)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    if (x_dev) {
+        launch_pack_positions(c->d, x_dev, c->st);
+        c->beads_current = false;
+        c->forces_valid = false;
+    } else if (!c->beads_current) {
+        launch_beads(c->d, c->st);
+        c->beads_current = true;
+    }
+    eval_forces(c);
+    if (!x_dev) {
+        launch_rp_finish(c->d, false, c->st);
+        c->forces_valid = true;
+    }
+    launch_unpack(c->d, f_dev, e_dev, virial_dev, nullptr, c->st);
+    return cuda_check(c, cudaGetLastError(), "energy_forces launch");
+}
+
+int pimd_descriptors(pimd_ctx* c, const double* x_dev, double* G_dev)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!G_dev) return fail(c, PIMD_ERR_INVALID_ARG, "G_dev is NULL");
+    if (c->d.potential != PIMD_POT_MODEL) return fail(c, PIMD_ERR_STATE, "context does not use the network potential");
+    if (!c->weights_set) {
+        // descriptor hyper-parameters arrive with the weights
+        return fail(c, PIMD_ERR_STATE, "weights not set");
+    }
+    if (x_dev) {
+        launch_pack_positions(c->d, x_dev, c->st);
+        c->beads_current = false;
+        c->forces_valid = false;
+    } else if (!c->beads_current) {
+        launch_beads(c->d, c->st);
+        c->beads_current = true;
+    }
+    launch_neighbours(c->d, c->st);
+    launch_descriptors(c->d, dparams(c), c->st);
+    launch_descriptors_out(c->d, G_dev, c->st);
+    return cuda_check(c, cudaGetLastError(), "descriptors launch");
+}
+
+int pimd_estimators(pimd_ctx* c, pimd_est* out, int n_reps)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out || n_reps != c->d.R) return fail(c, PIMD_ERR_INVALID_ARG, "n_reps must equal the replica count");
+    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    int rc = PIMD_OK;
+    if (!c->forces_valid) {
+        rc = refresh_forces(c);
+        if (rc) return rc;
+    }
+    launch_estimators(c->d, c->st);
+    std::vector<double> h((size_t)EST_STRIDE * c->d.R);
+    rc = cuda_check(c, cudaMemcpyAsync(h.data(), c->d.est, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st),
+                    "estimators copy");
+    if (rc) return rc;
+    rc = device_errors(c);
+    if (rc) return rc;
+    for (int r = 0; r < c->d.R; ++r) {
+        const double* o = h.data() + (size_t)r * EST_STRIDE;
+        pimd_est& e = out[r];
+        e.V_mean = o[0]; e.K_prim = o[1]; e.K_cv = o[2]; e.E_tot = o[3];
+        for (int a = 0; a < 9; ++a) e.W[a] = o[4 + a];
+        e.H_cons = o[13]; e.Q_thermo = o[14]; e.T_kin = o[15]; e.nbr_mean = o[16]; e.nbr_max = o[17];
+    }
+    return PIMD_OK;
+}
+
+int pimd_get_state(pimd_ctx* c, double* q_nm, double* p_nm, uint64_t* step, double* Q)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    const size_t n = 3 * (size_t)c->d.B;
+    int rc = PIMD_OK;
+    if (q_nm) rc = cuda_check(c, cudaMemcpyAsync(q_nm, c->d.q, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st), "copy");
+    if (!rc && p_nm) rc = cuda_check(c, cudaMemcpyAsync(p_nm, c->d.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st), "copy");
+    if (!rc && Q) rc = cuda_check(c, cudaMemcpyAsync(Q, c->d.Q, sizeof(double) * c->d.R, cudaMemcpyDeviceToHost, c->st), "copy");
+    if (rc) return rc;
+    rc = device_errors(c);
+    if (step) *step = c->step_host;
+    return rc;
+}
+
+int pimd_set_state(pimd_ctx* c, const double* q_nm, const double* p_nm, uint64_t step, const double* Q)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!q_nm || !p_nm) return fail(c, PIMD_ERR_INVALID_ARG, "q_nm and p_nm are required");
+    const size_t n = 3 * (size_t)c->d.B;
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(q_nm[i]) || !std::isfinite(p_nm[i])) return fail(c, PIMD_ERR_INVALID_ARG, "non-finite state");
+    int rc = cuda_check(c, cudaMemcpyAsync(c->d.q, q_nm, sizeof(double) * n, cudaMemcpyHostToDevice, c->st), "copy");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d.p, p_nm, sizeof(double) * n, cudaMemcpyHostToDevice, c->st), "copy");
+    unsigned long long s = step;
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d.step, &s, sizeof(s), cudaMemcpyHostToDevice, c->st), "copy");
+    std::vector<double> Qz(c->d.R, 0.0);
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(c->d.Q, Q ? Q : Qz.data(), sizeof(double) * c->d.R,
+                                                cudaMemcpyHostToDevice, c->st), "copy");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "set_state");
+    if (rc) return rc;
+    c->step_host = step;
+    c->beads_current = false;
+    c->forces_valid = false;
+    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return PIMD_OK;
+    rc = refresh_forces(c);
+    if (!rc) rc = device_errors(c);
+    return rc;
+}
+
+int pimd_get_forces(pimd_ctx* c, double* x_host, double* f_host, double* V_host)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    int rc = PIMD_OK;
+    if (!c->forces_valid) {
+        rc = refresh_forces(c);
+        if (rc) return rc;
+    }
+    Dev& d = c->d;
+    const size_t v4 = d.precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
+    std::vector<unsigned char> xs(v4 * d.B), fs(v4 * d.B);
+    rc = cuda_check(c, cudaMemcpyAsync(xs.data(), d.x, xs.size(), cudaMemcpyDeviceToHost, c->st), "copy");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(fs.data(), d.f, fs.size(), cudaMemcpyDeviceToHost, c->st), "copy");
+    if (!rc && V_host) rc = cuda_check(c, cudaMemcpyAsync(V_host, d.V, sizeof(double) * d.S, cudaMemcpyDeviceToHost, c->st), "copy");
+    if (rc) return rc;
+    rc = device_errors(c);
+    if (rc) return rc;
+    for (int b = 0; b < d.B; ++b)
+        for (int a = 0; a < 3; ++a) {
+            double xv, fv;
+            if (d.precision == PIMD_FP64) {
+                xv = ((const double*)xs.data())[4 * (size_t)b + a];
+                fv = ((const double*)fs.data())[4 * (size_t)b + a];
+            } else {
+                xv = ((const float*)xs.data())[4 * (size_t)b + a];
+                fv = ((const float*)fs.data())[4 * (size_t)b + a];
+            }
+            if (x_host) x_host[3 * (size_t)b + a] = xv;
+            if (f_host) f_host[3 * (size_t)b + a] = fv;
+        }
+    return PIMD_OK;
+}
+
+int pimd_get_neighbours(pimd_ctx* c, int* nnb_host, int* nbr_host)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d.potential != PIMD_POT_MODEL) return fail(c, PIMD_ERR_STATE, "no neighbour lists for this potential");
+    int rc = PIMD_OK;
+    if (nnb_host) rc = cuda_check(c, cudaMemcpyAsync(nnb_host, c->d.nnb, sizeof(int) * c->d.B, cudaMemcpyDeviceToHost, c->st), "copy");
+    if (!rc && nbr_host)
+        rc = cuda_check(c, cudaMemcpyAsync(nbr_host, c->d.nbr, sizeof(int) * (size_t)c->d.B * c->d.maxnb,
+                                           cudaMemcpyDeviceToHost, c->st), "copy");
+    if (rc) return rc;
+    return device_errors(c);
+}
+
+int pimd_sync(pimd_ctx* c)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    return device_errors(c);
+}
+
+int pimd_sizes(const pimd_ctx* c, int64_t* B, int64_t* S, int* R, int* maxnb)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (B) *B = c->d.B;
+    if (S) *S = c->d.S;
+    if (R) *R = c->d.R;
+    if (maxnb) *maxnb = c->d.maxnb;
+    return PIMD_OK;
+}
+
+void pimd_destroy(pimd_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    if (c->g1) cudaGraphExecDestroy(c->g1);
+    if (c->g8) cudaGraphExecDestroy(c->g8);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    for (int i = 0; i <= PIMD_N_STAGES; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    delete c;
+}
+
+const char* pimd_last_error(const pimd_ctx* c)
+{
+    if (c) return c->err.c_str();
+    return g_tls_error.c_str();
+}
+
+}  // extern "C"

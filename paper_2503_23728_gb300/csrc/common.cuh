@@ -1,0 +1,105 @@
+// common.cuh -- device-side types shared by the PIMD kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pimd {
+
+// physical constants (CODATA 2018)
+constexpr double KB = 8.617333262e-5;          // eV / K
+constexpr double HBAR = 0.6582119569;          // eV fs
+constexpr double MVV2E = 103.64269652680505;   // eV per amu A^2 fs^-2
+
+constexpr int NR = 32;    // radial channels
+constexpr int NA = 32;    // angular channels
+constexpr int ND = 64;    // descriptor length
+constexpr int MAX_LAYERS = 4;
+constexpr int TILE_ROWS = 128;     // network rows per tensor-core tile; element groups pad to it
+#define PIMD_SORT_CAP 256          // neighbour-list sort buffer per warp (>= max_neighbours)
+
+// device error word
+enum : unsigned { ERR_NBR_OVERFLOW = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u };
+struct DevErr {
+    unsigned flags;
+    int max_nbr;
+    int pad[2];
+};
+
+// FP64 position / force record (x, y, z, w); w of positions carries the
+// element type as an integer bit pattern
+struct __align__(32) Dbl4 {
+    double x, y, z, w;
+};
+
+template <typename Real> struct Vec4T;
+template <> struct Vec4T<float> { using type = float4; };
+template <> struct Vec4T<double> { using type = Dbl4; };
+template <typename Real> using Vec4 = typename Vec4T<Real>::type;
+
+// one ring polymer (replica)
+struct Rep {
+    int N, P;
+    int ba0;          // bead-atom index of (bead 0, atom 0); state index base / 3
+    int bs0;          // bead-system index of bead 0
+    int atom0;        // index into per-atom arrays (mass, type)
+    int cmat;         // offset of this P's normal-mode matrix C[P][P] (doubles)
+    int mode0;        // offset of this replica's per-mode records
+    int periodic;
+    double L[3], invL[3];
+    float Lf[3], invLf[3];   // FP32 box for the exact neighbour rule
+    double kT_md;            // k_B T_P in amu A^2 / fs^2
+    unsigned long long seed;
+    int nc[3];               // cells per side (cell lists), 0 = scan all atoms
+    int ncells;              // nc[0] nc[1] nc[2], 0 without cells
+    int cell0;               // first cell of bead 0; bead k owns cell0 + k ncells ..
+    int pad;
+};
+
+// one bead of one replica: N atoms starting at bead-atom index ba0
+struct BeadSys {
+    int ba0, N, rep, bead;
+};
+
+// per normal mode of a replica
+struct Mode {
+    double w, cw, sw, c1, c2, pad[3];
+};
+
+// symmetry-function parameters in the working precision
+template <typename Real>
+struct DescParams {
+    Real rc, pi_over_rc, eta_R;
+    Real r_mu[NR];
+    Real eta_A[4];
+};
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Reduce 32 per-lane values so that lane c ends with the sum over lanes of
+// v[c] (31 shuffles): recursive halving of the channel set.
+template <typename Real>
+__device__ __forceinline__ Real transpose_reduce32(Real (&v)[32], unsigned lane)
+{
+#pragma unroll
+    for (int o = 16, n = 32; o >= 1; o >>= 1, n >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < n / 2; ++q) {
+            Real send = upper ? v[q] : v[q + n / 2];
+            Real keep = upper ? v[q + n / 2] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+template <typename Real>
+__device__ __forceinline__ Real warp_sum(Real v)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace pimd

@@ -1,0 +1,964 @@
+// force.cu -- neighbour lists, symmetry-function descriptors, the network on
+// CUDA cores and the hand-written adjoint (forces and virial as the gradient
+// of the per-atom energies). One warp per bead-atom for the neighbour-bound
+// parts; bead-atoms are batched over all beads of all replicas.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace pimd {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+// Raise a kernel's dynamic shared-memory limit once (before any graph capture
+// records the launch).
+template <typename K>
+static void set_smem(K kernel, size_t bytes, size_t& done)
+{
+    if (bytes > done) {
+        cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        done = bytes;
+    }
+}
+
+__device__ __forceinline__ float f_exp(float v) { return __expf(v); }
+__device__ __forceinline__ double f_exp(double v) { return exp(v); }
+__device__ __forceinline__ float f_sqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double f_sqrt(double v) { return sqrt(v); }
+
+// Behler cosine cutoff fc(r) and its slope, from sincospi(r / rc)
+__device__ __forceinline__ void cutoff(float r, float rc, float pi_over_rc, float& fc, float& dfc)
+{
+    if (r < rc) {
+        float s, c;
+        sincospif(r / rc, &s, &c);
+        fc = 0.5f * (c + 1.0f);
+        dfc = -0.5f * pi_over_rc * s;
+    } else {
+        fc = 0.0f;
+        dfc = 0.0f;
+    }
+}
+__device__ __forceinline__ void cutoff(double r, double rc, double pi_over_rc, double& fc, double& dfc)
+{
+    if (r < rc) {
+        double s, c;
+        sincospi(r / rc, &s, &c);
+        fc = 0.5 * (c + 1.0);
+        dfc = -0.5 * pi_over_rc * s;
+    } else {
+        fc = 0.0;
+        dfc = 0.0;
+    }
+}
+
+// minimum-image pair vector in the working precision
+__device__ __forceinline__ void min_image(const Rep& rp, float& dx, float& dy, float& dz)
+{
+    if (rp.periodic) {
+        dx = __fsub_rn(dx, __fmul_rn(rp.Lf[0], rintf(__fmul_rn(dx, rp.invLf[0]))));
+        dy = __fsub_rn(dy, __fmul_rn(rp.Lf[1], rintf(__fmul_rn(dy, rp.invLf[1]))));
+        dz = __fsub_rn(dz, __fmul_rn(rp.Lf[2], rintf(__fmul_rn(dz, rp.invLf[2]))));
+    }
+}
+__device__ __forceinline__ void min_image(const Rep& rp, double& dx, double& dy, double& dz)
+{
+    if (rp.periodic) {
+        dx = __dsub_rn(dx, __dmul_rn(rp.L[0], rint(dx / rp.L[0])));
+        dy = __dsub_rn(dy, __dmul_rn(rp.L[1], rint(dy / rp.L[1])));
+        dz = __dsub_rn(dz, __dmul_rn(rp.L[2], rint(dz / rp.L[2])));
+    }
+}
+
+__device__ __forceinline__ float3 as_f32(const float4& v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 as_f32(const Dbl4& v)
+{
+    return make_float3(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z));
+}
+
+template <typename V4, typename Real>
+__device__ __forceinline__ V4 make4(Real a, Real b, Real c, Real d)
+{
+    V4 v;
+    v.x = a; v.y = b; v.z = c; v.w = d;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// a3: descriptors. Warp per bead-atom. Neighbour records (unit vector, r,
+// A_eta = exp(-eta r^2) fc) in shared memory; radial channels accumulated
+// per lane over its neighbours, angular channels over the unordered
+// neighbour pairs, then 32-way transposed warp reductions.
+//
+// Pair schedule. The unordered pairs of n neighbours are (j, k = j + d mod n)
+// for diagonals d = 1..D, D = (n-1)/2, plus the half diagonal d = n/2, j < n/2
+// when n is even. For n >= BAND_MIN the diagonals are cut into bands of R <=
+// RMAX; cell (band, j) is one lane's run of R pairs with j fixed in
+// registers, so each pair loads only k's record, and 32 consecutive cells
+// (one warp step) touch consecutive k (conflict-free shared loads). Small n
+// use a flat walk over all pairs instead.
+// ---------------------------------------------------------------------------
+constexpr int RMAX = 8;
+constexpr int BAND_MIN = 48;   // >= RMAX + 32: lanes of one step never share a k
+
+struct PairWalk {
+    int n, j, d, t, npairs;
+    __device__ __forceinline__ void init(int n_, int start)
+    {
+        n = n_;
+        npairs = n * (n - 1) / 2;
+        t = start;
+        if (n > 1) {
+            d = 1 + start / n;
+            j = start - (d - 1) * n;
+        } else {
+            d = 1;
+            j = 0;
+        }
+    }
+    __device__ __forceinline__ bool valid() const { return t < npairs; }
+    __device__ __forceinline__ int k() const
+    {
+        int kk = j + d;
+        return kk >= n ? kk - n : kk;
+    }
+    __device__ __forceinline__ void advance(int by)
+    {
+        t += by;
+        j += by;
+        while (j >= n) {
+            j -= n;
+            ++d;
+        }
+    }
+};
+
+// one warp step of the band schedule: this lane's cell
+struct BandCell {
+    int j, dlo, len, band;
+    bool act;
+};
+
+__device__ __forceinline__ void band_geometry(int n, int& D, int& NB, int& R, int& ncell)
+{
+    D = (n - 1) >> 1;
+    NB = (D + RMAX - 1) / RMAX;
+    R = (D + NB - 1) / NB;
+    ncell = NB * n;
+}
+
+__device__ __forceinline__ BandCell band_cell(int c, int n, int D, int R, int ncell)
+{
+    BandCell b;
+    b.act = c < ncell;
+    b.band = b.act ? c / n : -1;
+    b.j = b.act ? c - b.band * n : 0;
+    b.dlo = 1 + b.band * R;
+    b.len = b.act ? min(D - b.dlo + 1, R) : 0;
+    return b;
+}
+
+// forward contribution of pair (j, k): ga[q*4+e] += (1 + lambda c)^zeta B_e
+template <typename Real, typename V4>
+__device__ __forceinline__ void fwd_pair(const V4& uj, const V4& aj, const V4& uk, const V4& ak, Real (&ga)[NA])
+{
+    const Real c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+    const Real Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
+    const Real xp = Real(1) + c, xm = Real(1) - c;
+    const Real xp2 = xp * xp, xm2 = xm * xm;
+    const Real xp4 = xp2 * xp2, xm4 = xm2 * xm2;
+    const Real Pq[8] = {xp, xm, xp2, xm2, xp4, xm4, xp4 * xp4, xm4 * xm4};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ga[q * 4 + e] += Pq[q] * Bv[e];
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) desc_fwd_kernel(
+    const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<Real> dp, Real* __restrict__ G)
+{
+    using V4 = Vec4<Real>;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    V4* U = reinterpret_cast<V4*>(smem_raw) + (size_t)wib * 2 * maxnb;
+    V4* A = U + maxnb;
+    const int b = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (b >= B) return;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const Rep& rp = reps[sy.rep];
+    const int n = min(nnb[b], maxnb);
+    const V4 xi = x[b];
+
+    Real gr[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) gr[c] = Real(0);
+    for (int s = (int)lane; s < n; s += 32) {
+        const int j = nbr[(size_t)b * maxnb + s];
+        const V4 xj = x[sy.ba0 + j];
+        Real dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        min_image(rp, dx, dy, dz);
+        const Real r2 = dx * dx + dy * dy + dz * dz;
+        const Real r = f_sqrt(r2);
+        const Real ir = Real(1) / r;
+        Real fc, dfc;
+        cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            const Real t = r - dp.r_mu[c];
+            gr[c] += f_exp(-dp.eta_R * t * t) * fc;
+        }
+        U[s] = make4<V4, Real>(dx * ir, dy * ir, dz * ir, r);
+        A[s] = make4<V4, Real>(f_exp(-dp.eta_A[0] * r2) * fc, f_exp(-dp.eta_A[1] * r2) * fc,
+                               f_exp(-dp.eta_A[2] * r2) * fc, f_exp(-dp.eta_A[3] * r2) * fc);
+    }
+    const Real Gr = transpose_reduce32(gr, lane);
+    __syncwarp();
+
+    Real ga[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) ga[c] = Real(0);
+    if (n >= BAND_MIN) {
+        int D, NB, R, ncell;
+        band_geometry(n, D, NB, R, ncell);
+        for (int c0 = 0; c0 < ncell; c0 += 32) {
+            const BandCell cl = band_cell(c0 + (int)lane, n, D, R, ncell);
+            const V4 uj = U[cl.j], aj = A[cl.j];
+            for (int r = 0; r < cl.len; ++r) {
+                int k = cl.j + cl.dlo + r;
+                k = k >= n ? k - n : k;
+                fwd_pair(uj, aj, U[k], A[k], ga);
+            }
+        }
+        if ((n & 1) == 0) {
+            const int h = n >> 1;
+            for (int j = (int)lane; j < h; j += 32) fwd_pair(U[j], A[j], U[j + h], A[j + h], ga);
+        }
+    } else {
+        PairWalk w;
+        w.init(n, (int)lane);
+        for (; w.valid(); w.advance(32)) {
+            const int k = w.k();
+            fwd_pair(U[w.j], A[w.j], U[k], A[k], ga);
+        }
+    }
+    Real Ga = transpose_reduce32(ga, lane);
+    // 2^(1 - zeta) for zeta = 1, 2, 4, 8 (channel zeta index = lane / 8)
+    const int zi = (int)lane >> 3;
+    Ga *= (zi == 0) ? Real(1) : (zi == 1) ? Real(0.5) : (zi == 2) ? Real(0.125) : Real(0.0078125);
+    G[(size_t)b * ND + lane] = Gr;
+    G[(size_t)b * ND + NR + lane] = Ga;
+}
+
+template <typename Real>
+static int desc_warps(int maxnb)
+{
+    // shared memory per warp: U, A records
+    const size_t per = (size_t)2 * maxnb * sizeof(Vec4<Real>);
+    int w = 8;
+    while (w > 1 && per * w > 200 * 1024) w >>= 1;
+    return w;
+}
+
+void launch_descriptors(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    if (d.precision == 0) {
+        const int w = desc_warps<double>(d.maxnb);
+        const size_t sm = (size_t)w * 2 * d.maxnb * sizeof(Dbl4);
+        { static size_t done = 0; set_smem(desc_fwd_kernel<double>, sm, done); }
+        desc_fwd_kernel<double><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+            (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+            *(const DescParams<double>*)dpv, (double*)d.G);
+    } else {
+        const int w = desc_warps<float>(d.maxnb);
+        const size_t sm = (size_t)w * 2 * d.maxnb * sizeof(float4);
+        { static size_t done = 0; set_smem(desc_fwd_kernel<float>, sm, done); }
+        desc_fwd_kernel<float><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+            (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+            *(const DescParams<float>*)dpv, (float*)d.G);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5: adjoint. With g = dE_i/dG_i from the network, accumulate per neighbour
+//   dE/dA_eta(j) = sum_k sum_(zeta,lambda) g'_(zeta,lambda,eta) (1+lambda c)^zeta A_eta(k)
+//   w_j = sum_k dE/dc_jk u_k,   s_j = sum_k dE/dc_jk c_jk
+// over the neighbour pairs (g' = 2^(1-zeta) g), then
+//   v_j = dE_i/dr_ij = [dE/dr_radial + sum_eta dE/dA_eta dA_eta/dr] u_j + (w_j - s_j u_j) / r_j
+// and scatter F_j -= v_j, F_i += v_j, W -= r_ij (x) v_j.
+//
+// In the band schedule the j-side sums stay in registers for the lane's run,
+// and the k-side sums ride down the lanes as a shuffle carry: lane L at step
+// r and lane L-1 at step r+1 handle the same k. A carry is added into k's
+// shared-memory accumulator when its chain ends: at the band's last step
+// (all lanes, distinct k), or earlier at lane 0 / the first lane of a new
+// band, whose finished carries are parked in a small staging area and
+// added after the run.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_add_vec(float4* f, float ax, float ay, float az)
+{
+    atomicAdd(f, make_float4(ax, ay, az, 0.0f));
+}
+__device__ __forceinline__ void atomic_add_vec(Dbl4* f, double ax, double ay, double az)
+{
+    atomicAdd(&f->x, ax);
+    atomicAdd(&f->y, ay);
+    atomicAdd(&f->z, az);
+}
+
+// adjoint contribution of pair (j, k): jd / kd += (dE/dA(.)[4], w[3], s)
+template <typename Real, typename V4>
+__device__ __forceinline__ void adj_pair(const Real (&gp)[NA], const V4& uj, const V4& aj, const V4& uk,
+                                         const V4& ak, Real (&jd)[8], Real (&kd)[8])
+{
+    const Real c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+    const Real Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
+    const Real xp = Real(1) + c, xm = Real(1) - c;
+    const Real xp2 = xp * xp, xm2 = xm * xm;
+    const Real xp3 = xp2 * xp, xm3 = xm2 * xm;
+    const Real xp4 = xp2 * xp2, xm4 = xm2 * xm2;
+    const Real xp7 = xp4 * xp3, xm7 = xm4 * xm3;
+    const Real Pq[8] = {xp, xm, xp2, xm2, xp4, xm4, xp4 * xp4, xm4 * xm4};
+    Real H[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        H[q] = gp[q * 4] * Bv[0];
+#pragma unroll
+        for (int e = 1; e < 4; ++e) H[q] += gp[q * 4 + e] * Bv[e];
+    }
+    // dE/dc = sum_q zeta lambda (1 + lambda c)^(zeta - 1) H_q
+    Real dEdc = H[0] - H[1];
+    dEdc += Real(2) * (xp * H[2] - xm * H[3]);
+    dEdc += Real(4) * (xp3 * H[4] - xm3 * H[5]);
+    dEdc += Real(8) * (xp7 * H[6] - xm7 * H[7]);
+    Real K[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        K[e] = gp[e] * Pq[0];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) K[e] += gp[q * 4 + e] * Pq[q];
+    }
+    jd[0] += K[0] * ak.x; jd[1] += K[1] * ak.y; jd[2] += K[2] * ak.z; jd[3] += K[3] * ak.w;
+    kd[0] += K[0] * aj.x; kd[1] += K[1] * aj.y; kd[2] += K[2] * aj.z; kd[3] += K[3] * aj.w;
+    jd[4] += dEdc * uk.x; jd[5] += dEdc * uk.y; jd[6] += dEdc * uk.z; jd[7] += dEdc * c;
+    kd[4] += dEdc * uj.x; kd[5] += dEdc * uj.y; kd[6] += dEdc * uj.z; kd[7] += dEdc * c;
+}
+
+template <typename Real, typename V4>
+__device__ __forceinline__ void acc_rmw(V4* ACC0, V4* ACC1, int s, const Real (&v)[8])
+{
+    V4 a = ACC0[s];
+    a.x += v[0]; a.y += v[1]; a.z += v[2]; a.w += v[3];
+    ACC0[s] = a;
+    V4 b = ACC1[s];
+    b.x += v[4]; b.y += v[5]; b.z += v[6]; b.w += v[7];
+    ACC1[s] = b;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) desc_adj_kernel(
+    const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<Real> dp, const Real* __restrict__ dEdG, Vec4<Real>* __restrict__ f, double* __restrict__ Wv)
+{
+    using V4 = Vec4<Real>;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    // per warp: U, A, DA, ACC0 (dE/dA), ACC1 (w, s) records; staging [2][RMAX][2];
+    // radial dE/dr and g
+    V4* U = reinterpret_cast<V4*>(smem_raw) + (size_t)wib * (5 * maxnb + 4 * RMAX);
+    V4* A = U + maxnb;
+    V4* DA = A + maxnb;
+    V4* ACC0 = DA + maxnb;
+    V4* ACC1 = ACC0 + maxnb;
+    V4* STG = ACC1 + maxnb;   // [2 buffers][RMAX][2 records]
+    Real* RAD = reinterpret_cast<Real*>(reinterpret_cast<V4*>(smem_raw) + (size_t)nw * (5 * maxnb + 4 * RMAX)) +
+                (size_t)wib * (maxnb + ND);
+    Real* gs = RAD + maxnb;
+    const int b = blockIdx.x * nw + wib;
+    if (b >= B) return;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const Rep& rp = reps[sy.rep];
+    const int n = min(nnb[b], maxnb);
+    const V4 xi = x[b];
+    gs[lane] = dEdG[(size_t)b * ND + lane];
+    gs[NR + lane] = dEdG[(size_t)b * ND + NR + lane];
+    __syncwarp();
+
+    for (int s = (int)lane; s < n; s += 32) {
+        const int j = nbr[(size_t)b * maxnb + s];
+        const V4 xj = x[sy.ba0 + j];
+        Real dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        min_image(rp, dx, dy, dz);
+        const Real r2 = dx * dx + dy * dy + dz * dz;
+        const Real r = f_sqrt(r2);
+        const Real ir = Real(1) / r;
+        Real fc, dfc;
+        cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+        Real dEdr = Real(0);
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            const Real t = r - dp.r_mu[c];
+            const Real e = f_exp(-dp.eta_R * t * t);
+            dEdr += gs[c] * e * (Real(-2) * dp.eta_R * t * fc + dfc);
+        }
+        Real a[4], da[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const Real ex = f_exp(-dp.eta_A[e] * r2);
+            a[e] = ex * fc;
+            da[e] = ex * (Real(-2) * dp.eta_A[e] * r * fc + dfc);
+        }
+        U[s] = make4<V4, Real>(dx * ir, dy * ir, dz * ir, r);
+        A[s] = make4<V4, Real>(a[0], a[1], a[2], a[3]);
+        DA[s] = make4<V4, Real>(da[0], da[1], da[2], da[3]);
+        ACC0[s] = make4<V4, Real>(Real(0), Real(0), Real(0), Real(0));
+        ACC1[s] = make4<V4, Real>(Real(0), Real(0), Real(0), Real(0));
+        RAD[s] = dEdr;
+    }
+    __syncwarp();
+
+    // angular coefficients g'_nu = 2^(1-zeta) g_(32+nu)
+    Real gp[NA];
+#pragma unroll
+    for (int nu = 0; nu < NA; ++nu) {
+        const int zi = nu >> 3;
+        const Real sc = (zi == 0) ? Real(1) : (zi == 1) ? Real(0.5) : (zi == 2) ? Real(0.125) : Real(0.0078125);
+        gp[nu] = gs[NR + nu] * sc;
+    }
+    if (n >= BAND_MIN) {
+        int D, NB, R, ncell;
+        band_geometry(n, D, NB, R, ncell);
+        for (int c0 = 0; c0 < ncell; c0 += 32) {
+            const BandCell cl = band_cell(c0 + (int)lane, n, D, R, ncell);
+            const int band_up = __shfl_down_sync(0xffffffffu, cl.band, 1);
+            const int band_dn = __shfl_up_sync(0xffffffffu, cl.band, 1);
+            const bool recv = cl.act && lane < 31 && band_up == cl.band;   // carry arrives from lane + 1
+            const bool pass = cl.act && lane > 0 && band_dn == cl.band;    // carry leaves to lane - 1
+            const int nst = __reduce_max_sync(0xffffffffu, (unsigned)cl.len);
+            // exit lanes: lane 0 (buffer 0) and the first lane of a second band (buffer 1)
+            const int sbuf = lane == 0 ? 0 : 1;
+            const V4 uj = U[cl.j], aj = A[cl.j];
+            Real jd[8], kd[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) jd[q] = kd[q] = Real(0);
+            for (int r = 0; r < nst; ++r) {
+                const bool valid = r < cl.len;
+                if (valid) {
+                    int k = cl.j + cl.dlo + r;
+                    k = k >= n ? k - n : k;
+                    adj_pair(gp, uj, aj, U[k], A[k], jd, kd);
+                    if (!pass && r < cl.len - 1) {
+                        V4* st = STG + (size_t)(sbuf * RMAX + r) * 2;
+                        st[0] = make4<V4, Real>(kd[0], kd[1], kd[2], kd[3]);
+                        st[1] = make4<V4, Real>(kd[4], kd[5], kd[6], kd[7]);
+                    }
+                }
+                const bool shift = r < cl.len - 1;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const Real nk = __shfl_down_sync(0xffffffffu, kd[q], 1);
+                    if (shift) kd[q] = recv ? nk : Real(0);
+                }
+            }
+            __syncwarp();
+            // j-side sums, distinct j per lane
+            if (cl.act) acc_rmw(ACC0, ACC1, cl.j, jd);
+            __syncwarp();
+            // chains ending at the band's last step, distinct k per lane
+            if (cl.act && cl.len > 0) {
+                int k = cl.j + cl.dlo + cl.len - 1;
+                acc_rmw(ACC0, ACC1, k >= n ? k - n : k, kd);
+            }
+            __syncwarp();
+            // parked chains of lane 0 (buffer 0) and of the first lane of the second band (buffer 1)
+            const unsigned seams = __ballot_sync(0xffffffffu, cl.act && lane > 0 && !pass);
+            const int sl = seams ? __ffs(seams) - 1 : 0;
+            const int j0 = __shfl_sync(0xffffffffu, cl.j, 0), d0 = __shfl_sync(0xffffffffu, cl.dlo, 0);
+            const int l0 = __shfl_sync(0xffffffffu, cl.len, 0);
+            const int js = __shfl_sync(0xffffffffu, cl.j, sl), ds = __shfl_sync(0xffffffffu, cl.dlo, sl);
+            const int ls = seams ? __shfl_sync(0xffffffffu, cl.len, sl) : 0;
+            const int rr = (int)(lane & 15);
+            const int buf = (int)(lane >> 4);
+            const int jb = buf ? js : j0, db = buf ? ds : d0, lb = buf ? ls : l0;
+            if (rr < RMAX && rr < lb - 1) {
+                const V4* st = STG + (size_t)(buf * RMAX + rr) * 2;
+                const Real v[8] = {st[0].x, st[0].y, st[0].z, st[0].w, st[1].x, st[1].y, st[1].z, st[1].w};
+                int k = jb + db + rr;
+                acc_rmw(ACC0, ACC1, k >= n ? k - n : k, v);
+            }
+            __syncwarp();
+        }
+        if ((n & 1) == 0) {
+            const int h = n >> 1;
+            for (int j0 = 0; j0 < h; j0 += 32) {
+                const int j = j0 + (int)lane;
+                Real jd[8], kd[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) jd[q] = kd[q] = Real(0);
+                if (j < h) adj_pair(gp, U[j], A[j], U[j + h], A[j + h], jd, kd);
+                if (j < h) acc_rmw(ACC0, ACC1, j, jd);
+                __syncwarp();
+                if (j < h) acc_rmw(ACC0, ACC1, j + h, kd);
+                __syncwarp();
+            }
+        }
+    } else {
+        PairWalk w;
+        w.init(n, (int)lane);
+        for (; w.valid(); w.advance(32)) {
+            const int j = w.j, k = w.k();
+            Real jd[8], kd[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) jd[q] = kd[q] = Real(0);
+            adj_pair(gp, U[j], A[j], U[k], A[k], jd, kd);
+            Real* a0j = reinterpret_cast<Real*>(&ACC0[j]);
+            Real* a1j = reinterpret_cast<Real*>(&ACC1[j]);
+            Real* a0k = reinterpret_cast<Real*>(&ACC0[k]);
+            Real* a1k = reinterpret_cast<Real*>(&ACC1[k]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                atomicAdd(a0j + q, jd[q]);
+                atomicAdd(a1j + q, jd[4 + q]);
+                atomicAdd(a0k + q, kd[q]);
+                atomicAdd(a1k + q, kd[4 + q]);
+            }
+        }
+    }
+    __syncwarp();
+
+    Real fi[3] = {Real(0), Real(0), Real(0)};
+    Real wl[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wl[q] = Real(0);
+    for (int s = (int)lane; s < n; s += 32) {
+        const int j = nbr[(size_t)b * maxnb + s];
+        const V4 u = U[s], da = DA[s], a0 = ACC0[s], a1 = ACC1[s];
+        const Real dEdr = RAD[s] + a0.x * da.x + a0.y * da.y + a0.z * da.z + a0.w * da.w;
+        const Real ir = Real(1) / u.w;
+        const Real v[3] = {dEdr * u.x + (a1.x - a1.w * u.x) * ir, dEdr * u.y + (a1.y - a1.w * u.y) * ir,
+                           dEdr * u.z + (a1.z - a1.w * u.z) * ir};
+        atomic_add_vec(&f[sy.ba0 + j], -v[0], -v[1], -v[2]);
+        const Real d3[3] = {u.x * u.w, u.y * u.w, u.z * u.w};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            fi[a] += v[a];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) wl[3 * a + c] -= d3[a] * v[c];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fi[a] = warp_sum(fi[a]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wl[q] = warp_sum(wl[q]);
+    if (lane == 0) {
+        atomic_add_vec(&f[b], fi[0], fi[1], fi[2]);
+        const int s = ba_sys[b];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) atomicAdd(&Wv[(size_t)s * 9 + q], (double)wl[q]);
+    }
+}
+
+template <typename Real>
+static size_t adj_smem_per_warp(int maxnb)
+{
+    return (size_t)(5 * maxnb + 4 * RMAX) * sizeof(Vec4<Real>) + (size_t)(maxnb + ND) * sizeof(Real);
+}
+
+template <typename Real>
+static int adj_warps(int maxnb)
+{
+    const size_t per = adj_smem_per_warp<Real>(maxnb);
+    int w = 8;
+    while (w > 1 && per * w > 200 * 1024) w >>= 1;
+    return w;
+}
+
+void launch_adjoint(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    if (d.precision == 0) {
+        const int w = adj_warps<double>(d.maxnb);
+        const size_t sm = (size_t)w * adj_smem_per_warp<double>(d.maxnb);
+        { static size_t done = 0; set_smem(desc_adj_kernel<double>, sm, done); }
+        desc_adj_kernel<double><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+            (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+            *(const DescParams<double>*)dpv, (const double*)d.dEdG, (Dbl4*)d.f, d.W);
+    } else {
+        const int w = adj_warps<float>(d.maxnb);
+        const size_t sm = (size_t)w * adj_smem_per_warp<float>(d.maxnb);
+        { static size_t done = 0; set_smem(desc_adj_kernel<float>, sm, done); }
+        desc_adj_kernel<float><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+            (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+            *(const DescParams<float>*)dpv, (const float*)d.dEdG, (float4*)d.f, d.W);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a4 on CUDA cores: per-element network forward and input gradient for a
+// tile of TM rows of one element. Activations of every layer stay in shared
+// memory; weight chunks of 32 along K are staged through shared memory.
+// ---------------------------------------------------------------------------
+size_t blob_elems(int n_hidden, const int* widths)
+{
+    size_t o = 0;
+    int prev = ND;
+    for (int l = 0; l < n_hidden; ++l) {
+        o += (size_t)widths[l] * prev + widths[l];
+        prev = widths[l];
+    }
+    return o + prev + 1 + 2 * ND + 2;
+}
+
+constexpr int KC = 32;   // K chunk staged per step
+
+// out[TM][NOUT] = A[TM][K] * Bmat[K][NOUT]; Bmat(k, o) = W[o * ldw + k] when
+// transB (forward: W is [out][in]), else W[k * ldw + o] (backward).
+// 256 threads: row group tr = tid / 16 owns RT rows, column lane tc owns
+// columns tc + 16 m.
+template <typename Real, int RT, int CT, bool transB>
+__device__ __forceinline__ void tile_gemm(const Real* __restrict__ Asm, int lda, int K, const Real* __restrict__ W,
+                                          int ldw, int NOUT, Real* __restrict__ Bs, Real (&acc)[RT][CT])
+{
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    const int ldb = NOUT + 1;
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int m = 0; m < CT; ++m) acc[i][m] = Real(0);
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        __syncthreads();
+        if (transB) {
+            for (int e = tid; e < KC * NOUT; e += 256) {
+                const int o = e / KC, kk = e - o * KC;
+                Bs[kk * ldb + o] = W[(size_t)o * ldw + k0 + kk];
+            }
+        } else {
+            for (int e = tid; e < KC * NOUT; e += 256) {
+                const int kk = e / NOUT, o = e - kk * NOUT;
+                Bs[kk * ldb + o] = W[(size_t)(k0 + kk) * ldw + o];
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KC; ++kk) {
+            Real a[RT], bb[CT];
+#pragma unroll
+            for (int i = 0; i < RT; ++i) a[i] = Asm[(tr * RT + i) * lda + k0 + kk];
+#pragma unroll
+            for (int m = 0; m < CT; ++m) bb[m] = Bs[kk * ldb + tc + 16 * m];
+#pragma unroll
+            for (int i = 0; i < RT; ++i)
+#pragma unroll
+                for (int m = 0; m < CT; ++m) acc[i][m] += a[i] * bb[m];
+        }
+    }
+}
+
+__device__ __forceinline__ float f_tanh(float v) { return tanhf(v); }
+__device__ __forceinline__ double f_tanh(double v) { return tanh(v); }
+
+template <typename Real, int RT, int CT>
+__global__ void __launch_bounds__(256) mlp_fp_kernel(
+    const Real* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
+    const Real* __restrict__ wts, size_t blob, int n_hidden, Real* __restrict__ Eatom, Real* __restrict__ dEdG)
+{
+    constexpr int TM = RT * 16;
+    constexpr int Wd = CT * 16;         // hidden width
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* H0 = reinterpret_cast<Real*>(smem_raw);            // [TM][ND + 1]
+    Real* Hl = H0 + TM * (ND + 1);                          // [n_hidden][TM][Wd + 1]
+    Real* Bs = Hl + (size_t)n_hidden * TM * (Wd + 1);       // [KC][max(Wd, ND) + 1]
+    Real* yv = Bs + KC * (Wd + 1);                          // [TM]
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    const int row0 = blockIdx.x * TM;
+    const int type = tile_type[row0 / TILE_ROWS];
+    const Real* P = wts + (size_t)type * blob;
+    // blob pieces
+    const Real* Wl[MAX_LAYERS];
+    const Real* bl[MAX_LAYERS];
+    size_t off = 0;
+    int prev = ND;
+    for (int l = 0; l < n_hidden; ++l) {
+        Wl[l] = P + off; off += (size_t)Wd * prev;
+        bl[l] = P + off; off += Wd;
+        prev = Wd;
+    }
+    const Real* w_out = P + off; off += Wd;
+    const Real b_out = P[off]; off += 1;
+    const Real* mu = P + off; off += ND;
+    const Real* sigma = P + off; off += ND;
+    const Real s_E = P[off], e_Z = P[off + 1];
+
+    // h_0 = (G - mu) / sigma
+    for (int e = tid; e < TM * ND; e += 256) {
+        const int r = e / ND, c = e - r * ND;
+        const int ba = perm[row0 + r];
+        H0[r * (ND + 1) + c] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : Real(0);
+    }
+    // forward through the hidden layers
+    for (int l = 0; l < n_hidden; ++l) {
+        const Real* Ain = (l == 0) ? H0 : Hl + (size_t)(l - 1) * TM * (Wd + 1);
+        const int lda = (l == 0) ? ND + 1 : Wd + 1;
+        const int K = (l == 0) ? ND : Wd;
+        Real acc[RT][CT];
+        tile_gemm<Real, RT, CT, true>(Ain, lda, K, Wl[l], K, Wd, Bs, acc);
+        Real* Hout = Hl + (size_t)l * TM * (Wd + 1);
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int m = 0; m < CT; ++m) {
+                const int o = tc + 16 * m;
+                Hout[(tr * RT + i) * (Wd + 1) + o] = f_tanh(acc[i][m] + bl[l][o]);
+            }
+    }
+    __syncthreads();
+    Real* HL = Hl + (size_t)(n_hidden - 1) * TM * (Wd + 1);
+    if (tid < TM) {
+        Real y = b_out;
+        for (int k = 0; k < Wd; ++k) y += w_out[k] * HL[tid * (Wd + 1) + k];
+        yv[tid] = y;
+        const int ba = perm[row0 + tid];
+        if (ba >= 0) Eatom[ba] = s_E * y + e_Z;
+    }
+    __syncthreads();
+    // dE/da_L = s_E w_out (1 - h_L^2), written over h_L
+    for (int e = tid; e < TM * Wd; e += 256) {
+        const int r = e / Wd, k = e - r * Wd;
+        const Real h = HL[r * (Wd + 1) + k];
+        HL[r * (Wd + 1) + k] = s_E * w_out[k] * (Real(1) - h * h);
+    }
+    // backward: dE/dh_{l-1} = W_l^T dE/da_l
+    for (int l = n_hidden - 1; l >= 0; --l) {
+        const Real* Ga = Hl + (size_t)l * TM * (Wd + 1);
+        if (l > 0) {
+            Real acc[RT][CT];
+            tile_gemm<Real, RT, CT, false>(Ga, Wd + 1, Wd, Wl[l], Wd, Wd, Bs, acc);
+            Real* Hp = Hl + (size_t)(l - 1) * TM * (Wd + 1);
+#pragma unroll
+            for (int i = 0; i < RT; ++i)
+#pragma unroll
+                for (int m = 0; m < CT; ++m) {
+                    const int k = tc + 16 * m;
+                    const int r = tr * RT + i;
+                    const Real h = Hp[r * (Wd + 1) + k];
+                    Hp[r * (Wd + 1) + k] = acc[i][m] * (Real(1) - h * h);
+                }
+        } else {
+            Real acc[RT][ND / 16];
+            tile_gemm<Real, RT, ND / 16, false>(Ga, Wd + 1, Wd, Wl[0], ND, ND, Bs, acc);
+#pragma unroll
+            for (int i = 0; i < RT; ++i) {
+                const int r = tr * RT + i;
+                const int ba = perm[row0 + r];
+                if (ba < 0) continue;
+#pragma unroll
+                for (int m = 0; m < ND / 16; ++m) {
+                    const int c = tc + 16 * m;
+                    dEdG[(size_t)ba * ND + c] = acc[i][m] / sigma[c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Real, int RT, int CT>
+static void run_mlp_fp(const Dev& d, cudaStream_t st)
+{
+    constexpr int TM = RT * 16, Wd = CT * 16;
+    const size_t sm = sizeof(Real) * ((size_t)TM * (ND + 1) + (size_t)d.n_hidden * TM * (Wd + 1) +
+                                      (size_t)KC * (Wd + 1) + TM);
+    static size_t done = 0;
+    set_smem(mlp_fp_kernel<Real, RT, CT>, sm, done);
+    mlp_fp_kernel<Real, RT, CT><<<d.rows_pad / TM, 256, sm, st>>>(
+        (const Real*)d.G, d.perm, d.tile_type, (const Real*)d.wts, d.blob, d.n_hidden, (Real*)d.Eatom,
+        (Real*)d.dEdG);
+}
+
+template <typename Real, int CT>
+static void dispatch_rows(const Dev& d, cudaStream_t st)
+{
+    constexpr int Wd = CT * 16;
+    // largest row tile whose activations fit in ~200 KB of shared memory
+    const size_t per_row = sizeof(Real) * ((ND + 1) + (size_t)d.n_hidden * (Wd + 1) + 1);
+    const size_t fixed = sizeof(Real) * (size_t)KC * (Wd + 1);
+    if (fixed + per_row * 64 <= 200 * 1024)
+        run_mlp_fp<Real, 4, CT>(d, st);
+    else if (fixed + per_row * 32 <= 200 * 1024)
+        run_mlp_fp<Real, 2, CT>(d, st);
+    else
+        run_mlp_fp<Real, 1, CT>(d, st);
+}
+
+void launch_network_fp(const Dev& d, cudaStream_t st)
+{
+    if (d.precision == 0) {
+        switch (d.width) {
+            case 64: dispatch_rows<double, 4>(d, st); break;
+            case 128: dispatch_rows<double, 8>(d, st); break;
+            default: dispatch_rows<double, 16>(d, st); break;
+        }
+    } else {
+        switch (d.width) {
+            case 64: dispatch_rows<float, 4>(d, st); break;
+            case 128: dispatch_rows<float, 8>(d, st); break;
+            default: dispatch_rows<float, 16>(d, st); break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a6: per-bead energy V_k = sum_i E_i, FP64 sum in a fixed order (one warp
+// per bead).
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void energy_reduce_kernel(const Real* __restrict__ Eatom, const BeadSys* __restrict__ bsys, int S,
+                                     double* __restrict__ V)
+{
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = lane_id();
+    if (s >= S) return;
+    const BeadSys sy = bsys[s];
+    double acc = 0.0;
+    for (int i = (int)lane; i < sy.N; i += 32) acc += (double)Eatom[sy.ba0 + i];
+    acc = warp_sum(acc);
+    if (lane == 0) V[s] = acc;
+}
+
+void launch_energy_reduce(const Dev& d, cudaStream_t st)
+{
+    const int blocks = (d.S * 32 + 255) / 256;
+    if (d.precision == 0)
+        energy_reduce_kernel<double><<<blocks, 256, 0, st>>>((const double*)d.Eatom, d.bsys, d.S, d.V);
+    else
+        energy_reduce_kernel<float><<<blocks, 256, 0, st>>>((const float*)d.Eatom, d.bsys, d.S, d.V);
+}
+
+// ---------------------------------------------------------------------------
+// harmonic test potential V = sum_i 1/2 m_i omega^2 |x_i|^2 (Sec. S1)
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void harmonic_kernel(const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys,
+                                const BeadSys* __restrict__ bsys, const Rep* __restrict__ reps,
+                                const double* __restrict__ mass, int B, double omega, Real* __restrict__ Eatom,
+                                Vec4<Real>* __restrict__ f, double* __restrict__ Wv)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int s = ba_sys[b];
+    const BeadSys sy = bsys[s];
+    const Rep& rp = reps[sy.rep];
+    const double m = mass[rp.atom0 + (b - sy.ba0) % sy.N];
+    const double k = m * omega * omega * MVV2E;
+    const double p[3] = {(double)x[b].x, (double)x[b].y, (double)x[b].z};
+    Eatom[b] = (Real)(0.5 * k * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]));
+    Vec4<Real> fv;
+    fv.x = (Real)(-k * p[0]);
+    fv.y = (Real)(-k * p[1]);
+    fv.z = (Real)(-k * p[2]);
+    fv.w = Real(0);
+    f[b] = fv;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) atomicAdd(&Wv[(size_t)s * 9 + 3 * a + c], -k * p[a] * p[c]);
+}
+
+void launch_harmonic(const Dev& d, cudaStream_t st)
+{
+    const int blocks = (d.B + 255) / 256;
+    if (d.precision == 0)
+        harmonic_kernel<double><<<blocks, 256, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.mass, d.B,
+                                                        d.omega_harm, (double*)d.Eatom, (Dbl4*)d.f, d.W);
+    else
+        harmonic_kernel<float><<<blocks, 256, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.mass, d.B,
+                                                       d.omega_harm, (float*)d.Eatom, (float4*)d.f, d.W);
+}
+
+// ---------------------------------------------------------------------------
+// boundary conversions (FP64 [B][3] <-> internal 4-wide records)
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void pack_kernel(const double* __restrict__ x3, Vec4<Real>* __restrict__ x, int B)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    Vec4<Real> v = x[b];
+    v.x = (Real)x3[3 * (size_t)b];
+    v.y = (Real)x3[3 * (size_t)b + 1];
+    v.z = (Real)x3[3 * (size_t)b + 2];
+    x[b] = v;
+}
+
+void launch_pack_positions(const Dev& d, const double* x3, cudaStream_t st)
+{
+    const int blocks = (d.B + 255) / 256;
+    if (d.precision == 0)
+        pack_kernel<double><<<blocks, 256, 0, st>>>(x3, (Dbl4*)d.x, d.B);
+    else
+        pack_kernel<float><<<blocks, 256, 0, st>>>(x3, (float4*)d.x, d.B);
+}
+
+template <typename Real>
+__global__ void unpack_kernel(const Vec4<Real>* __restrict__ f, const Vec4<Real>* __restrict__ x,
+                              const double* __restrict__ V, const double* __restrict__ Wv, int B, int S,
+                              double* __restrict__ f3, double* __restrict__ e, double* __restrict__ vir,
+                              double* __restrict__ x3)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B) {
+        if (f3) {
+            const Vec4<Real> v = f[i];
+            f3[3 * (size_t)i] = v.x;
+            f3[3 * (size_t)i + 1] = v.y;
+            f3[3 * (size_t)i + 2] = v.z;
+        }
+        if (x3) {
+            const Vec4<Real> v = x[i];
+            x3[3 * (size_t)i] = v.x;
+            x3[3 * (size_t)i + 1] = v.y;
+            x3[3 * (size_t)i + 2] = v.z;
+        }
+    }
+    if (i < S) {
+        if (e) e[i] = V[i];
+        if (vir)
+            for (int q = 0; q < 9; ++q) vir[9 * (size_t)i + q] = Wv[9 * (size_t)i + q];
+    }
+}
+
+void launch_unpack(const Dev& d, double* f3, double* e, double* vir, double* x3, cudaStream_t st)
+{
+    const int n = d.B > d.S ? d.B : d.S;
+    const int blocks = (n + 255) / 256;
+    if (d.precision == 0)
+        unpack_kernel<double><<<blocks, 256, 0, st>>>((const Dbl4*)d.f, (const Dbl4*)d.x, d.V, d.W, d.B, d.S, f3, e,
+                                                      vir, x3);
+    else
+        unpack_kernel<float><<<blocks, 256, 0, st>>>((const float4*)d.f, (const float4*)d.x, d.V, d.W, d.B, d.S, f3,
+                                                     e, vir, x3);
+}
+
+template <typename Real>
+__global__ void desc_out_kernel(const Real* __restrict__ G, double* __restrict__ out, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)G[i];
+}
+
+void launch_descriptors_out(const Dev& d, double* G, cudaStream_t st)
+{
+    const size_t n = (size_t)d.B * ND;
+    const int blocks = (int)((n + 255) / 256);
+    if (d.precision == 0)
+        desc_out_kernel<double><<<blocks, 256, 0, st>>>((const double*)d.G, G, n);
+    else
+        desc_out_kernel<float><<<blocks, 256, 0, st>>>((const float*)d.G, G, n);
+}
+
+}  // namespace pimd

@@ -1,0 +1,100 @@
+// kernels.h -- host-side declarations of the kernel launchers (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace pimd {
+
+// Device pointers and sizes of one context (all inside the caller's workspace).
+struct Dev {
+    int R = 0, S = 0, B = 0, NA = 0;   // replicas, bead-systems, bead-atoms, atoms
+    int maxnb = 128;
+    int precision = 1;                 // 0 FP64, 1 FP32, 2 BF16 tensor cores
+    bool periodic_any = false;
+
+    Rep* reps = nullptr;
+    BeadSys* bsys = nullptr;
+    int* ba_sys = nullptr;             // [B] bead-system of each bead-atom
+    double* mass = nullptr;            // [NA]
+    int* atype = nullptr;              // [NA] element type index
+    double* x0 = nullptr;              // [NA][3]
+    double* cmat = nullptr;            // normal-mode matrices
+    Mode* modes = nullptr;             // [sum P]
+    int2* rp_blocks = nullptr;         // (replica, first entry) per ring-polymer block
+    int n_rp_blocks = 0;
+    int rp_threads = 256;
+
+    void* x = nullptr;                 // Vec4<Real>[B] positions (w = type)
+    void* f = nullptr;                 // Vec4<Real>[B] forces
+    int* nbr = nullptr;                // [B][maxnb]
+    int* nnb = nullptr;                // [B]
+    int* cell_start = nullptr;         // per cell: first slot in cell_atoms
+    int* cell_cnt = nullptr;           // per cell: atom count
+    int* cell_atoms = nullptr;         // [B] atoms of each bead grouped by cell
+    int* cell_bs = nullptr;            // beads that use cell lists
+    int n_cell_bs = 0, max_cells = 0;
+    void* G = nullptr;                 // Real[B][64]
+    void* dEdG = nullptr;              // Real[B][64]
+    void* Eatom = nullptr;             // Real[B]
+    double* V = nullptr;               // [S]
+    double* W = nullptr;               // [S][9]
+    double* q = nullptr;               // [3B] normal-mode positions
+    double* p = nullptr;               // [3B] normal-mode momenta
+    double* fnm = nullptr;             // [3B] normal-mode forces
+    double* Q = nullptr;               // [R] thermostat heat
+    unsigned long long* step = nullptr;
+    DevErr* err = nullptr;
+    double* est = nullptr;             // [R][EST_STRIDE]
+
+    // network
+    int n_types = 0, n_hidden = 0, width = 0;
+    size_t blob = 0;                   // elements per type blob
+    void* wts = nullptr;               // Real[n_types][blob]
+    int* perm = nullptr;               // [rows_pad] bead-atom of each network row, -1 pad
+    int* tile_type = nullptr;          // [rows_pad / 128]
+    int rows_pad = 0;
+    void* wtc = nullptr;               // tensor-core weight images
+    size_t wtc_bytes_per_type = 0;
+    float* wtc_vec = nullptr;          // FP32 vectors for the tensor-core epilogues
+    size_t wtc_vec_per_type = 0;
+
+    // integrator
+    double dt = 0.5, gamma0 = 0.0, lambda = 1.0;
+    int thermostat = 1;
+    int potential = 0;
+    double omega_harm = 0.0;
+    double rc = 6.0;
+};
+
+constexpr int EST_STRIDE = 24;
+
+size_t blob_elems(int n_hidden, const int* widths);
+
+// force evaluation pieces
+void launch_neighbours(const Dev& d, cudaStream_t st);
+void launch_descriptors(const Dev& d, const void* dp, cudaStream_t st);
+void launch_network_fp(const Dev& d, cudaStream_t st);
+void launch_network_tc(const Dev& d, cudaStream_t st);
+void launch_adjoint(const Dev& d, const void* dp, cudaStream_t st);
+void launch_energy_reduce(const Dev& d, cudaStream_t st);
+void launch_harmonic(const Dev& d, cudaStream_t st);
+void launch_pack_positions(const Dev& d, const double* x3, cudaStream_t st);
+void launch_unpack(const Dev& d, double* f3, double* e, double* vir, double* x3, cudaStream_t st);
+void launch_descriptors_out(const Dev& d, double* G, cudaStream_t st);
+bool network_tc_supported(int width, int n_hidden);
+size_t tc_weight_bytes(int width, int n_hidden);
+void prepare_tc_weights(const Dev& d, int type, const double* blob, void* host_img, float* host_vec);
+
+// ring polymer
+void launch_rp_init(const Dev& d, cudaStream_t st);
+void launch_beads(const Dev& d, cudaStream_t st);
+void launch_rp_start(const Dev& d, cudaStream_t st);
+void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st);
+void launch_bump_step(const Dev& d, cudaStream_t st);
+void launch_estimators(const Dev& d, cudaStream_t st);
+
+}  // namespace pimd

@@ -1,0 +1,498 @@
+// mlp_tc.cu -- per-element network forward and input gradient on the 5th-gen
+// tensor cores (tcgen05.mma kind::f16, BF16 x BF16 -> FP32 accumulators in
+// tensor memory), for tiles of 128 bead-atoms of one element.
+//
+// One CTA of 256 threads per tile. Thread 0 issues the bulk weight copies
+// (cp.async.bulk, double-buffered, completion on mbarriers) and the MMAs
+// (completion through tcgen05.commit on an mbarrier); all 8 warps run the
+// epilogues, warp w reading TMEM lanes 32 (w % 4).. and half of the columns.
+// Operands sit in shared memory in the no-swizzle K-major canonical layout:
+// 8-row x 16-byte core matrices, adjacent along K at 128 B (leading byte
+// offset), adjacent along M/N at (K / 8) * 128 B (stride byte offset).
+//
+// Layers: forward h_l = tanh(W_l h_{l-1} + b_l) (accumulator a_l in TMEM,
+// h_l stored as BF16 for the next layer and for tanh'), y = w_out . h_L
+// (FP32 epilogue), then backward dE/da_L = s_E w_out (1 - h_L^2),
+// dE/dh_{l-1} = W_l^T dE/da_l on the tensor cores with pre-transposed
+// weight images, and dE/dG = dE/dh_0 / sigma.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace pimd {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// element (r, k) of an R x K operand in the core-matrix layout, in elements
+__host__ __device__ __forceinline__ size_t cm_index(int r, int k, int K)
+{
+    return ((size_t)(r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version (tcgen05)
+    return d;                 // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major
+__device__ __forceinline__ uint32_t make_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false after ~1 s without the phase completing
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
+__device__ __forceinline__ float2 unpack_bf16(uint32_t u)
+{
+    __nv_bfloat162 h;
+    memcpy(&h, &u, 4);
+    return __bfloat1622float2(h);
+}
+
+__device__ __forceinline__ float tanh_f(float v) { return tanhf(v); }
+
+// byte sizes / offsets of the weight images of one element type:
+// forward images W_l [W][in_l], then backward images W_l^T [in_l][W]
+__host__ __device__ __forceinline__ size_t img_bytes(int n, int k) { return (size_t)n * k * 2; }
+
+__host__ __device__ __forceinline__ size_t img_offset(int W, int L, int phase)
+{
+    // phase 0..L-1: forward layer phase+1; phase L..2L-1: backward layer 2L-phase
+    size_t o = 0;
+    for (int p = 0; p < phase; ++p) {
+        const int l = p < L ? p + 1 : 2 * L - p;
+        const int in = l == 1 ? ND : W;
+        o += img_bytes(W, in);
+    }
+    return o;
+}
+
+}  // namespace
+
+template <int W, int L, bool DB>
+__global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(
+    const float* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
+    const unsigned char* __restrict__ wimg, size_t img_per_type, const float* __restrict__ wvec,
+    size_t vec_per_type, float* __restrict__ Eatom, float* __restrict__ dEdG, DevErr* __restrict__ err)
+{
+    constexpr int M = 128;
+    constexpr int A0_B = M * ND * 2;
+    constexpr int H_B = M * W * 2;
+    constexpr int WB_B = W * W * 2 > W * ND * 2 ? W * W * 2 : W * ND * 2;
+    constexpr int TCOLS = W < 64 ? 64 : W;   // TMEM columns (power of two >= 32)
+    constexpr int NPH = 2 * L;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A0 = sm;
+    unsigned char* Hs = A0 + A0_B;                 // h_1 .. h_{L-1} (h_L is not kept)
+    unsigned char* GA = Hs + (L > 1 ? (L - 1) : 1) * H_B;
+    unsigned char* WB0 = GA + H_B;
+    unsigned char* WB1 = WB0 + (DB ? WB_B : 0);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(WB1 + WB_B);   // [0] mma, [1] wbuf0, [2] wbuf1
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+    float* ysum = reinterpret_cast<float*>(tslot + 4);          // [2][128]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hsel = warp >> 2;
+    const int row = 32 * q + lane;                              // TMEM lane / tile row of this thread
+    const int row0 = blockIdx.x * M;
+    const int type = tile_type[row0 / TILE_ROWS];
+    const unsigned char* img = wimg + (size_t)type * img_per_type;
+    const float* vec = wvec + (size_t)type * vec_per_type;
+    const float* b_l = vec;                    // [L][W]
+    const float* w_out = vec + L * W;          // [W]
+    const float* mu = w_out + W;               // [64]
+    const float* sigma = mu + ND;              // [64]
+    const float b_out = sigma[ND], s_E = sigma[ND + 1], e_Z = sigma[ND + 2];
+
+    const uint32_t bar_mma = smem_u32(&bars[0]);
+    const uint32_t bar_w[2] = {smem_u32(&bars[1]), smem_u32(&bars[2])};
+    if (tid == 0) {
+        mbar_init(bar_mma, 1);
+        mbar_init(bar_w[0], 1);
+        mbar_init(bar_w[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    // weight loads: phase p uses buffer p % 2 (double-buffered) or buffer 0
+    bool w_issued[NPH];
+#pragma unroll
+    for (int p = 0; p < NPH; ++p) w_issued[p] = false;
+    auto issue_w = [&](int p) {
+        const int l = p < L ? p + 1 : 2 * L - p;
+        const int in = l == 1 ? ND : W;
+        const int buf = DB ? (p & 1) : 0;
+        bulk_load(smem_u32(buf ? WB1 : WB0), img + img_offset(W, L, p), (uint32_t)img_bytes(W, in), bar_w[buf]);
+    };
+    if (tid == 0) {
+        issue_w(0);
+        w_issued[0] = true;
+        if (DB && NPH > 1) {
+            issue_w(1);
+            w_issued[1] = true;
+        }
+    }
+
+    // h_0 = (G - mu) / sigma in BF16: thread -> (row tid % 128, 32 columns)
+    {
+        const int r = tid & (M - 1), c0 = (tid >> 7) * 32;
+        const int ba = perm[row0 + r];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + 8 * g + j;
+                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : 0.0f;
+            }
+            uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                  pack_bf16(v[6], v[7]));
+            *reinterpret_cast<uint4*>(A0 + 2 * cm_index(r, c0 + 8 * g, ND)) = pk;
+        }
+    }
+    fence_proxy();
+    __syncthreads();
+
+    bool ok = true;
+    float y_part = 0.0f;
+    for (int p = 0; p < NPH && ok; ++p) {
+        const bool fwd = p < L;
+        const int l = fwd ? p + 1 : 2 * L - p;             // layer of this phase
+        const int K = fwd ? (l == 1 ? ND : W) : W;          // reduction length
+        const int N = fwd ? W : (l == 1 ? ND : W);          // output columns
+        const unsigned char* Aop = fwd ? (l == 1 ? A0 : Hs + (size_t)(l - 2) * H_B) : GA;
+        const int buf = DB ? (p & 1) : 0;
+        const uint32_t wpar = DB ? ((p >> 1) & 1) : (p & 1);
+        // ---- MMA issue
+        bool good = true;
+        if (tid == 0) {
+            good = mbar_wait(bar_w[buf], wpar);
+            if (good) {
+                fence_after();
+                const uint32_t a0 = smem_u32(Aop), b0 = smem_u32(buf ? WB1 : WB0);
+                const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+                const uint32_t idesc = make_idesc(M, N);
+                for (int ks = 0; ks < K / 16; ++ks) {
+                    const uint64_t ad = make_desc(a0 + ks * 256u, 128u, sbo);
+                    const uint64_t bd = make_desc(b0 + ks * 256u, 128u, sbo);
+                    mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+                mma_commit(bar_mma);
+            }
+        }
+        good = mbar_wait(bar_mma, p & 1) && good;
+        ok = __syncthreads_and(good ? 1 : 0) != 0;
+        if (!ok) break;
+        fence_after();
+        // ---- the weight buffer of this phase is free: prefetch
+        if (tid == 0) {
+            const int nxt = DB ? p + 2 : p + 1;
+            if (nxt < NPH) {
+                issue_w(nxt);
+                w_issued[nxt] = true;
+            }
+        }
+        // ---- epilogue over this thread's row and column half
+        const int cbeg = hsel * (N / 2), cend = cbeg + N / 2;
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+            if (fwd) {
+                float h[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) h[j] = tanh_f(v[j] + b_l[(l - 1) * W + c0 + j]);
+                if (l < L) {
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        uint4 pk = make_uint4(pack_bf16(h[8 * g], h[8 * g + 1]), pack_bf16(h[8 * g + 2], h[8 * g + 3]),
+                                              pack_bf16(h[8 * g + 4], h[8 * g + 5]),
+                                              pack_bf16(h[8 * g + 6], h[8 * g + 7]));
+                        *reinterpret_cast<uint4*>(Hs + (size_t)(l - 1) * H_B + 2 * cm_index(row, c0 + 8 * g, W)) = pk;
+                    }
+                } else {
+                    float ga[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float wo = w_out[c0 + j];
+                        y_part += wo * h[j];
+                        ga[j] = s_E * wo * (1.0f - h[j] * h[j]);
+                    }
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        uint4 pk = make_uint4(pack_bf16(ga[8 * g], ga[8 * g + 1]), pack_bf16(ga[8 * g + 2], ga[8 * g + 3]),
+                                              pack_bf16(ga[8 * g + 4], ga[8 * g + 5]),
+                                              pack_bf16(ga[8 * g + 6], ga[8 * g + 7]));
+                        *reinterpret_cast<uint4*>(GA + 2 * cm_index(row, c0 + 8 * g, W)) = pk;
+                    }
+                }
+            } else if (l > 1) {
+                // dE/da_{l-1} = (W_l^T dE/da_l) * (1 - h_{l-1}^2)
+                const unsigned char* Hp = Hs + (size_t)(l - 2) * H_B;
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const uint4 hv = *reinterpret_cast<const uint4*>(Hp + 2 * cm_index(row, c0 + 8 * g, W));
+                    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                    float o[8];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float2 hh = unpack_bf16(hw[t]);
+                        o[2 * t] = v[8 * g + 2 * t] * (1.0f - hh.x * hh.x);
+                        o[2 * t + 1] = v[8 * g + 2 * t + 1] * (1.0f - hh.y * hh.y);
+                    }
+                    uint4 pk = make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]),
+                                          pack_bf16(o[6], o[7]));
+                    *reinterpret_cast<uint4*>(GA + 2 * cm_index(row, c0 + 8 * g, W)) = pk;
+                }
+            } else {
+                const int ba = perm[row0 + row];
+                if (ba >= 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4) {
+                        float4 o = make_float4(v[j] / sigma[c0 + j], v[j + 1] / sigma[c0 + j + 1],
+                                               v[j + 2] / sigma[c0 + j + 2], v[j + 3] / sigma[c0 + j + 3]);
+                        *reinterpret_cast<float4*>(dEdG + (size_t)ba * ND + c0 + j) = o;
+                    }
+                }
+            }
+        }
+        if (fwd && l == L) ysum[hsel * M + row] = y_part;
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (fwd && l == L && hsel == 0) {
+            const int ba = perm[row0 + row];
+            if (ba >= 0) Eatom[ba] = s_E * (ysum[row] + ysum[M + row] + b_out) + e_Z;
+        }
+    }
+    if (!ok) {
+        // a wait gave up: report, let issued copies land, then release TMEM
+        if (tid == 0) {
+            atomicOr(&err->flags, ERR_TIMEOUT);
+            for (int p = 0; p < NPH; ++p)
+                if (w_issued[p]) {
+                    const int buf = DB ? (p & 1) : 0;
+                    mbar_wait(bar_w[buf], DB ? ((p >> 1) & 1) : (p & 1));
+                }
+            mbar_wait(bar_mma, 0);
+        }
+        __syncthreads();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static size_t tc_smem(int W, int L, bool db)
+{
+    const size_t A0_B = 128 * ND * 2, H_B = (size_t)128 * W * 2;
+    const size_t WB_B = (size_t)W * (W > ND ? W : ND) * 2;
+    return A0_B + (L > 1 ? (L - 1) : 1) * H_B + H_B + (db ? 2 : 1) * WB_B + 64 + 2 * 128 * 4 + 1024;
+}
+
+bool network_tc_supported(int width, int n_hidden)
+{
+    if (width != 64 && width != 128) return false;
+    if (n_hidden < 1 || n_hidden > MAX_LAYERS) return false;
+    return tc_smem(width, n_hidden, false) <= 227 * 1024;
+}
+
+size_t tc_weight_bytes(int width, int n_hidden) { return img_offset(width, n_hidden, 2 * n_hidden); }
+
+// weight images (BF16, core-matrix layout) and FP32 epilogue vectors of one type
+void prepare_tc_weights(const Dev& d, int /*type*/, const double* blob, void* host_img, float* host_vec)
+{
+    const int W = d.width, L = d.n_hidden;
+    unsigned char* img = static_cast<unsigned char*>(host_img);
+    // blob pieces
+    const double* Wl[MAX_LAYERS];
+    const double* bl[MAX_LAYERS];
+    size_t off = 0;
+    int prev = ND;
+    for (int l = 0; l < L; ++l) {
+        Wl[l] = blob + off; off += (size_t)W * prev;
+        bl[l] = blob + off; off += W;
+        prev = W;
+    }
+    const double* w_out = blob + off; off += W;
+    const double b_out = blob[off]; off += 1;
+    const double* mu = blob + off; off += ND;
+    const double* sigma = blob + off; off += ND;
+    const double s_E = blob[off], e_Z = blob[off + 1];
+    for (int p = 0; p < 2 * L; ++p) {
+        const int l = p < L ? p + 1 : 2 * L - p;
+        const int in = l == 1 ? ND : W;
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(img + img_offset(W, L, p));
+        const double* Wm = Wl[l - 1];   // [W][in]
+        if (p < L) {
+            for (int n = 0; n < W; ++n)
+                for (int k = 0; k < in; ++k) dst[cm_index(n, k, in)] = __float2bfloat16_rn((float)Wm[(size_t)n * in + k]);
+        } else {
+            for (int n = 0; n < in; ++n)
+                for (int k = 0; k < W; ++k) dst[cm_index(n, k, W)] = __float2bfloat16_rn((float)Wm[(size_t)k * in + n]);
+        }
+    }
+    float* v = host_vec;
+    for (int l = 0; l < L; ++l)
+        for (int c = 0; c < W; ++c) *v++ = (float)bl[l][c];
+    for (int c = 0; c < W; ++c) *v++ = (float)w_out[c];
+    for (int c = 0; c < ND; ++c) *v++ = (float)mu[c];
+    for (int c = 0; c < ND; ++c) *v++ = (float)sigma[c];
+    *v++ = (float)b_out;
+    *v++ = (float)s_E;
+    *v++ = (float)e_Z;
+    *v++ = 0.0f;
+}
+
+template <int W, int L>
+static void run_tc(const Dev& d, cudaStream_t st)
+{
+    const bool db = tc_smem(W, L, true) <= 227 * 1024;
+    const size_t sm = tc_smem(W, L, db);
+    static size_t done[2] = {0, 0};
+    if (db) {
+        if (sm > done[1]) {
+            cudaFuncSetAttribute(mlp_tc_kernel<W, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            done[1] = sm;
+        }
+        mlp_tc_kernel<W, L, true><<<d.rows_pad / 128, TC_THREADS, sm, st>>>(
+            (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
+            d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err);
+    } else {
+        if (sm > done[0]) {
+            cudaFuncSetAttribute(mlp_tc_kernel<W, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            done[0] = sm;
+        }
+        mlp_tc_kernel<W, L, false><<<d.rows_pad / 128, TC_THREADS, sm, st>>>(
+            (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
+            d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err);
+    }
+}
+
+void launch_network_tc(const Dev& d, cudaStream_t st)
+{
+    if (d.rows_pad == 0) return;
+    if (d.width == 64) {
+        switch (d.n_hidden) {
+            case 1: run_tc<64, 1>(d, st); break;
+            case 2: run_tc<64, 2>(d, st); break;
+            case 3: run_tc<64, 3>(d, st); break;
+            default: run_tc<64, 4>(d, st); break;
+        }
+    } else {
+        switch (d.n_hidden) {
+            case 1: run_tc<128, 1>(d, st); break;
+            case 2: run_tc<128, 2>(d, st); break;
+            case 3: run_tc<128, 3>(d, st); break;
+            default: run_tc<128, 4>(d, st); break;
+        }
+    }
+}
+
+}  // namespace pimd

@@ -1,0 +1,202 @@
+// nbr.cu -- a2: neighbour lists under the exact FP32 rule
+//   d = x_j - x_i, d -= L rint(d / L) (FP32 box), r2 = (dx dx + dy dy) + dz dz
+//   without contraction, j in N(i) iff r2 < (float)(r_c^2),
+// stored per bead-atom as ascending atom indices within its bead.
+//
+// Periodic beads whose box holds >= 3 cells of edge >= r_c per side use cell
+// lists: one block per bead bins its atoms (shared-memory counting sort),
+// then one warp per bead-atom applies the rule to the 27 stencil cells and
+// sorts what passes. Other beads (gas phase, small boxes) scan all atoms of
+// the bead in ascending order, which yields sorted lists directly.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace pimd {
+
+namespace {
+
+__device__ __forceinline__ float3 pos_f32(const float4& v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 pos_f32(const Dbl4& v)
+{
+    return make_float3(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z));
+}
+
+// the inclusion rule on FP32 positions
+__device__ __forceinline__ bool within(const Rep& rp, const float3& xi, const float3& xj, float rc2)
+{
+    float dx = __fsub_rn(xj.x, xi.x), dy = __fsub_rn(xj.y, xi.y), dz = __fsub_rn(xj.z, xi.z);
+    if (rp.periodic) {
+        dx = __fsub_rn(dx, __fmul_rn(rp.Lf[0], rintf(__fmul_rn(dx, rp.invLf[0]))));
+        dy = __fsub_rn(dy, __fmul_rn(rp.Lf[1], rintf(__fmul_rn(dy, rp.invLf[1]))));
+        dz = __fsub_rn(dz, __fmul_rn(rp.Lf[2], rintf(__fmul_rn(dz, rp.invLf[2]))));
+    }
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return r2 < rc2;
+}
+
+// cell coordinate along one axis of a periodic box (wrapped fractional coordinate)
+__device__ __forceinline__ int cell_axis(float x, float invL, int nc)
+{
+    float s = __fmul_rn(x, invL);
+    s = s - floorf(s);
+    int c = (int)(s * (float)nc);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__device__ __forceinline__ int3 cell_of(const Rep& rp, const float3& p)
+{
+    return make_int3(cell_axis(p.x, rp.invLf[0], rp.nc[0]), cell_axis(p.y, rp.invLf[1], rp.nc[1]),
+                     cell_axis(p.z, rp.invLf[2], rp.nc[2]));
+}
+
+}  // namespace
+
+// one block per bead using cells: counting sort of its atoms into cells
+template <typename V4>
+__global__ void cell_build_kernel(const V4* __restrict__ x, const BeadSys* __restrict__ bsys,
+                                  const Rep* __restrict__ reps, const int* __restrict__ cell_bs,
+                                  int* __restrict__ cell_start, int* __restrict__ cell_cnt,
+                                  int* __restrict__ cell_atoms)
+{
+    extern __shared__ int sh[];   // [ncells] counters, then [ncells] fill offsets
+    const BeadSys sy = bsys[cell_bs[blockIdx.x]];
+    const Rep& rp = reps[sy.rep];
+    const int nc = rp.ncells;
+    int* cnt = sh;
+    int* off = sh + nc;
+    const int cbase = rp.cell0 + sy.bead * nc;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) cnt[c] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < sy.N; i += blockDim.x) {
+        const int3 c = cell_of(rp, pos_f32(x[sy.ba0 + i]));
+        atomicAdd(&cnt[(c.x * rp.nc[1] + c.y) * rp.nc[2] + c.z], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < nc; ++c) {
+            off[c] = acc;
+            cell_start[cbase + c] = sy.ba0 + acc;
+            cell_cnt[cbase + c] = cnt[c];
+            acc += cnt[c];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < sy.N; i += blockDim.x) {
+        const int3 c = cell_of(rp, pos_f32(x[sy.ba0 + i]));
+        const int pos = atomicAdd(&off[(c.x * rp.nc[1] + c.y) * rp.nc[2] + c.z], 1);
+        cell_atoms[sy.ba0 + pos] = i;
+    }
+}
+
+// warp per bead-atom
+template <typename V4>
+__global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, const int* __restrict__ ba_sys,
+                                                  const BeadSys* __restrict__ bsys, const Rep* __restrict__ reps,
+                                                  const int* __restrict__ cell_start, const int* __restrict__ cell_cnt,
+                                                  const int* __restrict__ cell_atoms, float rc2, int maxnb, int B,
+                                                  int* __restrict__ nbr, int* __restrict__ nnb,
+                                                  DevErr* __restrict__ err)
+{
+    __shared__ int lst[8][PIMD_SORT_CAP];
+    const int wib = threadIdx.x >> 5;
+    const int b = blockIdx.x * (blockDim.x >> 5) + wib;
+    const unsigned lane = lane_id();
+    if (b >= B) return;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const Rep& rp = reps[sy.rep];
+    const int il = b - sy.ba0;
+    const float3 xi = pos_f32(x[b]);
+    int cnt = 0;
+    if (rp.ncells == 0) {
+        for (int j0 = 0; j0 < sy.N; j0 += 32) {
+            const int j = j0 + (int)lane;
+            const bool in = j < sy.N && j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (in && pos < maxnb) nbr[(size_t)b * maxnb + pos] = j;
+            cnt += __popc(m);
+        }
+    } else {
+        int* L = lst[wib];
+        const int3 ci = cell_of(rp, xi);
+        const int cbase = rp.cell0 + sy.bead * rp.ncells;
+        for (int s = 0; s < 27; ++s) {
+            int cx = ci.x + s / 9 - 1, cy = ci.y + (s / 3) % 3 - 1, cz = ci.z + s % 3 - 1;
+            cx += cx < 0 ? rp.nc[0] : (cx >= rp.nc[0] ? -rp.nc[0] : 0);
+            cy += cy < 0 ? rp.nc[1] : (cy >= rp.nc[1] ? -rp.nc[1] : 0);
+            cz += cz < 0 ? rp.nc[2] : (cz >= rp.nc[2] ? -rp.nc[2] : 0);
+            const int cell = cbase + (cx * rp.nc[1] + cy) * rp.nc[2] + cz;
+            const int st = cell_start[cell], ct = cell_cnt[cell];
+            for (int t0 = 0; t0 < ct; t0 += 32) {
+                const int t = t0 + (int)lane;
+                int j = -1;
+                bool in = false;
+                if (t < ct) {
+                    j = cell_atoms[st + t];
+                    in = j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                if (in && pos < maxnb) L[pos] = j;
+                cnt += __popc(m);
+            }
+        }
+        __syncwarp();
+        // ascending order: bitonic sort over the next power of two, padded
+        const int m = cnt < maxnb ? cnt : maxnb;
+        int n2 = 1;
+        while (n2 < m) n2 <<= 1;
+        for (int t = m + (int)lane; t < n2; t += 32) L[t] = 0x7fffffff;
+        __syncwarp();
+        for (int k = 2; k <= n2; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int t = (int)lane; t < n2; t += 32) {
+                    const int p = t ^ jj;
+                    if (p > t) {
+                        const int a = L[t], c = L[p];
+                        const bool up = (t & k) == 0;
+                        if ((a > c) == up) {
+                            L[t] = c;
+                            L[p] = a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int t = (int)lane; t < m; t += 32) nbr[(size_t)b * maxnb + t] = L[t];
+    }
+    if (lane == 0) {
+        nnb[b] = cnt;
+        if (cnt > maxnb) {
+            atomicOr(&err->flags, ERR_NBR_OVERFLOW);
+            atomicMax(&err->max_nbr, cnt);
+        }
+    }
+}
+
+void launch_neighbours(const Dev& d, cudaStream_t st)
+{
+    const int threads = 256;
+    const int blocks = (int)(((size_t)d.B * 32 + threads - 1) / threads);
+    const float rc2 = (float)(d.rc * d.rc);
+    if (d.precision == 0) {
+        if (d.n_cell_bs)
+            cell_build_kernel<Dbl4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
+                (const Dbl4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
+        nbr_kernel<Dbl4><<<blocks, threads, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
+                                                     d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb, d.err);
+    } else {
+        if (d.n_cell_bs)
+            cell_build_kernel<float4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
+                (const float4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
+        nbr_kernel<float4><<<blocks, threads, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
+                                                       d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb,
+                                                       d.err);
+    }
+}
+
+}  // namespace pimd

@@ -1,0 +1,350 @@
+// ring.cu -- FP64 ring-polymer kernels: initial state, normal-mode <-> bead
+// transforms, the OBABO step in normal-mode space (exact free-ring-polymer A,
+// PILE-L O with Philox4x32-10 noise), and the finite-P estimators.
+//
+// Work decomposition: a block owns T = blockDim / P (atom, dimension)
+// entries of one replica and all P modes of each, so every P-point transform
+// is a shared-memory matrix-vector product spread over T * P threads.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace pimd {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 multiplies
+// with Weyl key increments; one standard normal per counter by Box-Muller on
+// two 53-bit uniforms in (0, 1].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ double normal_dev(unsigned long long seed, unsigned idx, unsigned step, unsigned rep,
+                                             unsigned stream)
+{
+    const uint4 w = philox10(make_uint4(idx, step, rep, stream), make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+    const double u1 = ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6) + 1.0) * (1.0 / 9007199254740992.0);
+    const double u2 = ((double)(w.z >> 5) * 67108864.0 + (double)(w.w >> 6) + 1.0) * (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real& comp(Vec4<Real>& v, int d)
+{
+    return reinterpret_cast<Real*>(&v)[d];
+}
+
+// ---------------------------------------------------------------------------
+// initial state: q_nm(k=0) = sqrt(P) x0, other modes 0; p_nm ~ N(0, m k_B T_P)
+// with Philox stream 1, step 0. One thread per state entry.
+// ---------------------------------------------------------------------------
+__global__ void rp_init_kernel(const Rep* __restrict__ reps, const BeadSys* __restrict__ bsys,
+                               const int* __restrict__ ba_sys, const double* __restrict__ mass,
+                               const double* __restrict__ x0, int B, double* __restrict__ q, double* __restrict__ p)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= 3 * B) return;
+    const int b = g / 3, dd = g - 3 * b;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const Rep& rp = reps[sy.rep];
+    const int i = b - sy.ba0;
+    const int k = sy.bead;
+    const unsigned local = (unsigned)((k * rp.N + i) * 3 + dd);
+    const double m = mass[rp.atom0 + i];
+    q[g] = (k == 0) ? sqrt((double)rp.P) * x0[3 * (size_t)(rp.atom0 + i) + dd] : 0.0;
+    p[g] = sqrt(m * rp.kT_md) * normal_dev(rp.seed, local, 0u, (unsigned)sy.rep, 1u);
+}
+
+void launch_rp_init(const Dev& d, cudaStream_t st)
+{
+    rp_init_kernel<<<(3 * d.B + 255) / 256, 256, 0, st>>>(d.reps, d.bsys, d.ba_sys, d.mass, d.x0, d.B, d.q, d.p);
+}
+
+// ---------------------------------------------------------------------------
+// block geometry: block -> (replica, first entry); thread -> (entry, mode)
+// ---------------------------------------------------------------------------
+struct RpThread {
+    int r, e, kk, N, P, i, dd;
+    bool active;
+};
+
+__device__ __forceinline__ RpThread rp_thread(const int2* __restrict__ blocks, const Rep* __restrict__ reps)
+{
+    RpThread t;
+    const int2 bl = blocks[blockIdx.x];
+    t.r = bl.x;
+    const Rep& rp = reps[t.r];
+    t.N = rp.N;
+    t.P = rp.P;
+    const int T = blockDim.x / t.P;
+    const int le = threadIdx.x / t.P;
+    t.kk = threadIdx.x - le * t.P;
+    t.e = bl.y + le;
+    t.active = le < T && t.e < 3 * t.N;
+    t.i = t.e / 3;
+    t.dd = t.e - 3 * t.i;
+    return t;
+}
+
+// normal-mode -> bead positions for all beads (no dynamics)
+template <typename Real>
+__global__ void beads_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
+                             const double* __restrict__ cmat, const double* __restrict__ q,
+                             Vec4<Real>* __restrict__ x)
+{
+    extern __shared__ double sq[];
+    const RpThread t = rp_thread(blocks, reps);
+    const Rep& rp = reps[t.r];
+    const int le = threadIdx.x / t.P;
+    if (t.active) sq[le * t.P + t.kk] = q[3 * ((size_t)rp.ba0 + (size_t)t.kk * t.N + t.i) + t.dd];
+    __syncthreads();
+    if (!t.active) return;
+    const int j = t.kk;
+    const double* C = cmat + rp.cmat + (size_t)j * t.P;
+    double acc = 0.0;
+    for (int k = 0; k < t.P; ++k) acc += C[k] * sq[le * t.P + k];
+    comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
+}
+
+// O(dt/2) B(dt/2) A(dt) on each mode, then the new bead positions
+template <typename Real>
+__global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
+                                const double* __restrict__ cmat, const Mode* __restrict__ modes,
+                                const double* __restrict__ mass, const unsigned long long* __restrict__ stepp,
+                                double dt, int thermostat, double* __restrict__ q, double* __restrict__ p,
+                                const double* __restrict__ fnm, Vec4<Real>* __restrict__ x, double* __restrict__ Q)
+{
+    extern __shared__ double sq[];
+    __shared__ double red[32];
+    const RpThread t = rp_thread(blocks, reps);
+    const Rep& rp = reps[t.r];
+    const int le = threadIdx.x / t.P;
+    double dK = 0.0;
+    if (t.active) {
+        const int k = t.kk;
+        const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
+        const Mode md = modes[rp.mode0 + k];
+        const double m = mass[rp.atom0 + t.i];
+        double pv = p[g], qv = q[g];
+        if (thermostat) {
+            const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
+            const double xi = normal_dev(rp.seed, local, (unsigned)(*stepp), (unsigned)t.r, 2u);
+            const double pn = md.c1 * pv + sqrt(m * rp.kT_md) * md.c2 * xi;
+            dK = (pn * pn - pv * pv) / (2.0 * m);
+            pv = pn;
+        }
+        pv += 0.5 * dt * fnm[g] / MVV2E;
+        if (k == 0) {
+            qv += pv * dt / m;
+        } else {
+            const double pn = md.cw * pv - m * md.w * md.sw * qv;
+            qv = md.sw / (m * md.w) * pv + md.cw * qv;
+            pv = pn;
+        }
+        p[g] = pv;
+        q[g] = qv;
+        sq[le * t.P + k] = qv;
+    }
+    // thermostat heat: block reduction, one atomic per block
+    dK = warp_sum(dK);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dK;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        if (thermostat) atomicAdd(&Q[t.r], s * MVV2E);
+    }
+    if (!t.active) return;
+    const int j = t.kk;
+    const double* C = cmat + rp.cmat + (size_t)j * t.P;
+    double acc = 0.0;
+    for (int k = 0; k < t.P; ++k) acc += C[k] * sq[le * t.P + k];
+    comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
+}
+
+// f_nm = C^T f; if do_step: B(dt/2) O(dt/2)
+template <typename Real>
+__global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
+                                 const double* __restrict__ cmat, const Mode* __restrict__ modes,
+                                 const double* __restrict__ mass, const unsigned long long* __restrict__ stepp,
+                                 double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
+                                 double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ Q,
+                                 DevErr* __restrict__ err)
+{
+    extern __shared__ double sf[];
+    __shared__ double red[32];
+    const RpThread t = rp_thread(blocks, reps);
+    const Rep& rp = reps[t.r];
+    const int le = threadIdx.x / t.P;
+    if (t.active) {
+        Vec4<Real> fv = f[rp.ba0 + (size_t)t.kk * t.N + t.i];
+        sf[le * t.P + t.kk] = (double)comp<Real>(fv, t.dd);
+    }
+    __syncthreads();
+    double dK = 0.0;
+    if (t.active) {
+        const int k = t.kk;
+        double fn = 0.0;
+        for (int j = 0; j < t.P; ++j) fn += cmat[rp.cmat + (size_t)j * t.P + k] * sf[le * t.P + j];
+        const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
+        fnm[g] = fn;
+        if (!isfinite(fn)) atomicOr(&err->flags, ERR_NONFINITE);
+        if (do_step) {
+            const double m = mass[rp.atom0 + t.i];
+            double pv = p[g] + 0.5 * dt * fn / MVV2E;
+            if (thermostat) {
+                const Mode md = modes[rp.mode0 + k];
+                const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
+                const double xi = normal_dev(rp.seed, local, (unsigned)(*stepp), (unsigned)t.r, 3u);
+                const double pn = md.c1 * pv + sqrt(m * rp.kT_md) * md.c2 * xi;
+                dK = (pn * pn - pv * pv) / (2.0 * m);
+                pv = pn;
+            }
+            p[g] = pv;
+        }
+    }
+    dK = warp_sum(dK);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dK;
+    __syncthreads();
+    if (threadIdx.x == 0 && do_step && thermostat) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(&Q[t.r], s * MVV2E);
+    }
+}
+
+__global__ void bump_step_kernel(unsigned long long* step) { *step += 1ull; }
+
+static size_t rp_smem(const Dev& d) { return (size_t)d.rp_threads * sizeof(double); }
+
+void launch_beads(const Dev& d, cudaStream_t st)
+{
+    if (d.precision == 0)
+        beads_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(d.rp_blocks, d.reps, d.cmat, d.q,
+                                                                                (Dbl4*)d.x);
+    else
+        beads_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(d.rp_blocks, d.reps, d.cmat, d.q,
+                                                                               (float4*)d.x);
+}
+
+void launch_rp_start(const Dev& d, cudaStream_t st)
+{
+    if (d.precision == 0)
+        rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.q, d.p, d.fnm, (Dbl4*)d.x,
+            d.Q);
+    else
+        rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.q, d.p, d.fnm, (float4*)d.x,
+            d.Q);
+}
+
+void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
+{
+    if (d.precision == 0)
+        rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, do_step ? 1 : 0,
+            (const Dbl4*)d.f, d.p, d.fnm, d.Q, d.err);
+    else
+        rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, do_step ? 1 : 0,
+            (const float4*)d.f, d.p, d.fnm, d.Q, d.err);
+}
+
+void launch_bump_step(const Dev& d, cudaStream_t st) { bump_step_kernel<<<1, 1, 0, st>>>(d.step); }
+
+// ---------------------------------------------------------------------------
+// a8: estimators in normal-mode space, one block per replica (FP64).
+//   spring = sum_k 1/2 m omega_k^2 q_k^2     (= bead-space spring energy)
+//   sum_k (x_k - centroid) . f_k = sum_{k>0} q_k f_nm,k
+//   kinetic = sum p^2 / 2m
+// record: V_mean K_prim K_cv E_tot W[9] H_cons Q_thermo T_kin nbr_mean nbr_max
+// ---------------------------------------------------------------------------
+__global__ void estimators_kernel(const Rep* __restrict__ reps, const Mode* __restrict__ modes,
+                                  const double* __restrict__ mass, const double* __restrict__ q,
+                                  const double* __restrict__ p, const double* __restrict__ fnm,
+                                  const double* __restrict__ V, const double* __restrict__ Wv,
+                                  const double* __restrict__ Q, const int* __restrict__ nnb,
+                                  double* __restrict__ est)
+{
+    __shared__ double red[4][32];
+    __shared__ int redm[32];
+    const int r = blockIdx.x;
+    const Rep& rp = reps[r];
+    const int N = rp.N, P = rp.P;
+    double spring = 0.0, cv = 0.0, kin = 0.0, nsum = 0.0;
+    int nmax = 0;
+    const int total = 3 * N * P;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int k = e / (3 * N);
+        const int i = (e - k * 3 * N) / 3;
+        const size_t g = 3 * (size_t)rp.ba0 + e;
+        const double m = mass[rp.atom0 + i];
+        const double w = modes[rp.mode0 + k].w;
+        spring += 0.5 * m * w * w * q[g] * q[g];
+        if (k > 0) cv += q[g] * fnm[g];
+        kin += p[g] * p[g] / (2.0 * m);
+    }
+    for (int b = threadIdx.x; b < N * P; b += blockDim.x) {
+        const int c = nnb[rp.ba0 + b];
+        nsum += c;
+        nmax = max(nmax, c);
+    }
+    double vals[4] = {spring, cv, kin, nsum};
+    for (int a = 0; a < 4; ++a) {
+        double v = warp_sum(vals[a]);
+        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
+    }
+    for (int o = 16; o >= 1; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = nmax;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double tot[4] = {0, 0, 0, 0};
+    int mx = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        for (int a = 0; a < 4; ++a) tot[a] += red[a][w];
+        mx = max(mx, redm[w]);
+    }
+    const double spring_eV = tot[0] * MVV2E, kin_eV = tot[2] * MVV2E;
+    const double beta = 1.0 / (rp.kT_md * MVV2E / P);   // 1 / (k_B T)
+    double Vsum = 0.0;
+    for (int k = 0; k < P; ++k) Vsum += V[rp.bs0 + k];
+    double* o = est + (size_t)r * EST_STRIDE;
+    const double Vbar = Vsum / P;
+    const double K_prim = 3.0 * N * P / (2.0 * beta) - spring_eV / P;
+    const double K_cv = 3.0 * N / (2.0 * beta) - tot[1] / (2.0 * P);
+    o[0] = Vbar;
+    o[1] = K_prim;
+    o[2] = K_cv;
+    o[3] = K_cv + Vbar;
+    for (int a = 0; a < 9; ++a) {
+        double w = 0.0;
+        for (int k = 0; k < P; ++k) w += Wv[9 * (size_t)(rp.bs0 + k) + a];
+        o[4 + a] = w / P;
+    }
+    o[13] = kin_eV + spring_eV + Vsum - Q[r];
+    o[14] = Q[r];
+    o[15] = 2.0 * kin_eV / (3.0 * N * P * KB);
+    o[16] = tot[3] / ((double)N * P);
+    o[17] = (double)mx;
+}
+
+void launch_estimators(const Dev& d, cudaStream_t st)
+{
+    estimators_kernel<<<d.R, 256, 0, st>>>(d.reps, d.modes, d.mass, d.q, d.p, d.fnm, d.V, d.W, d.Q, d.nnb, d.est);
+}
+
+}  // namespace pimd

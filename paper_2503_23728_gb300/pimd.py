@@ -1,0 +1,432 @@
+"""ctypes binding of libpimd.so (include/pimd.h), plus a small Context wrapper
+that takes device memory and the stream from PyTorch.
+
+Argument marshalling only: every step of the force evaluation and of the
+ring-polymer dynamics runs in the library's CUDA kernels. There is no CPU
+fallback; loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpimd.so")
+
+PIMD_OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "STATE", -3: "WORKSPACE_TOO_SMALL", -4: "CUDA", -5: "NONFINITE",
+          -6: "TIMEOUT", -7: "NBR_OVERFLOW", -8: "UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16_tc": 2}
+POT_MODEL, POT_HARMONIC = 0, 1
+EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_weights", "pimd_step",
+           "pimd_energy_forces", "pimd_descriptors", "pimd_estimators", "pimd_get_state", "pimd_set_state",
+           "pimd_get_forces", "pimd_get_neighbours", "pimd_sync", "pimd_sizes", "pimd_destroy", "pimd_last_error",
+           "pimd_stage_times", "pimd_kernels_per_step"]
+STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
+
+
+class PimdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class pimd_config(ct.Structure):
+    _fields_ = [("dt_fs", ct.c_double), ("gamma0_per_fs", ct.c_double), ("pile_lambda", ct.c_double),
+                ("cutoff_A", ct.c_double), ("precision", ct.c_int), ("thermostat", ct.c_int),
+                ("potential", ct.c_int), ("max_neighbours", ct.c_int), ("omega_harm", ct.c_double),
+                ("n_hidden", ct.c_int), ("widths", ct.c_int * 4), ("stream", ct.c_void_p), ("timing", ct.c_int),
+                ("nbr_algo", ct.c_int)]
+
+
+class pimd_replica_desc(ct.Structure):
+    _fields_ = [("n_atoms", ct.c_int), ("n_beads", ct.c_int), ("Z", ct.POINTER(ct.c_int)),
+                ("x0", ct.POINTER(ct.c_double)), ("mass", ct.POINTER(ct.c_double)), ("box", ct.c_double * 3),
+                ("T_K", ct.c_double), ("seed", ct.c_uint64)]
+
+
+class pimd_model_desc(ct.Structure):
+    _fields_ = [("n_elements", ct.c_int), ("Z", ct.POINTER(ct.c_int)), ("n_hidden", ct.c_int),
+                ("widths", ct.POINTER(ct.c_int)), ("params", ct.POINTER(ct.POINTER(ct.c_double))),
+                ("eta_R", ct.c_double), ("r_mu", ct.POINTER(ct.c_double)), ("zeta", ct.POINTER(ct.c_int)),
+                ("lam", ct.POINTER(ct.c_double)), ("eta_A", ct.POINTER(ct.c_double))]
+
+
+class pimd_est(ct.Structure):
+    _fields_ = [("V_mean", ct.c_double), ("K_prim", ct.c_double), ("K_cv", ct.c_double), ("E_tot", ct.c_double),
+                ("W", ct.c_double * 9), ("H_cons", ct.c_double), ("Q_thermo", ct.c_double),
+                ("T_kin", ct.c_double), ("nbr_mean", ct.c_double), ("nbr_max", ct.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k in ("V_mean", "K_prim", "K_cv", "E_tot", "H_cons", "Q_thermo", "T_kin",
+                                           "nbr_mean", "nbr_max")}
+        d["W"] = np.array(list(self.W)).reshape(3, 3)
+        return d
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpimd.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libpimd.so is not built (%s); run __graft_entry__.build()" % path)
+    L = ct.CDLL(path)
+    vp, dp, ip = ct.c_void_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)
+    L.pimd_abi_version.restype = ct.c_int
+    L.pimd_workspace_size.argtypes = [ct.POINTER(pimd_config), ct.POINTER(pimd_replica_desc), ct.c_int,
+                                      ct.POINTER(ct.c_size_t)]
+    L.pimd_create.argtypes = [ct.POINTER(pimd_config), ct.POINTER(pimd_replica_desc), ct.c_int, vp, ct.c_size_t,
+                              ct.POINTER(vp)]
+    L.pimd_set_weights.argtypes = [vp, ct.POINTER(pimd_model_desc)]
+    L.pimd_step.argtypes = [vp, ct.c_int]
+    L.pimd_energy_forces.argtypes = [vp, vp, vp, vp, vp]
+    L.pimd_descriptors.argtypes = [vp, vp, vp]
+    L.pimd_estimators.argtypes = [vp, ct.POINTER(pimd_est), ct.c_int]
+    L.pimd_get_state.argtypes = [vp, dp, dp, ct.POINTER(ct.c_uint64), dp]
+    L.pimd_set_state.argtypes = [vp, dp, dp, ct.c_uint64, dp]
+    L.pimd_get_forces.argtypes = [vp, dp, dp, dp]
+    L.pimd_get_neighbours.argtypes = [vp, ip, ip]
+    L.pimd_sync.argtypes = [vp]
+    L.pimd_sizes.argtypes = [vp, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64), ip, ip]
+    L.pimd_destroy.argtypes = [vp]
+    L.pimd_destroy.restype = None
+    L.pimd_last_error.argtypes = [vp]
+    L.pimd_last_error.restype = ct.c_char_p
+    L.pimd_stage_times.argtypes = [vp, ct.POINTER(ct.c_float)]
+    L.pimd_kernels_per_step.argtypes = [vp]
+    L.pimd_kernels_per_step.restype = ct.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, ctx=None):
+    if rc != PIMD_OK:
+        msg = load().pimd_last_error(ctx)
+        raise PimdError(rc, msg.decode() if msg else "")
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(ct.POINTER(ct.c_int))
+
+
+# ---------------------------------------------------------------- C-ABI calls
+def pimd_abi_version() -> int:
+    return int(load().pimd_abi_version())
+
+
+def pimd_workspace_size(cfg: pimd_config, reps) -> int:
+    n = ct.c_size_t(0)
+    _check(load().pimd_workspace_size(ct.byref(cfg), reps, len(reps), ct.byref(n)))
+    return int(n.value)
+
+
+def pimd_create(cfg: pimd_config, reps, workspace_ptr: int, ws_bytes: int):
+    h = ct.c_void_p()
+    _check(load().pimd_create(ct.byref(cfg), reps, len(reps), ct.c_void_p(workspace_ptr), ws_bytes, ct.byref(h)))
+    return h
+
+
+def pimd_set_weights(ctx, model: pimd_model_desc):
+    _check(load().pimd_set_weights(ctx, ct.byref(model)), ctx)
+
+
+def pimd_step(ctx, n_steps: int):
+    _check(load().pimd_step(ctx, int(n_steps)), ctx)
+
+
+def pimd_energy_forces(ctx, x_ptr, e_ptr, f_ptr, vir_ptr):
+    _check(load().pimd_energy_forces(ctx, x_ptr, e_ptr, f_ptr, vir_ptr), ctx)
+
+
+def pimd_descriptors(ctx, x_ptr, G_ptr):
+    _check(load().pimd_descriptors(ctx, x_ptr, G_ptr), ctx)
+
+
+def pimd_estimators(ctx, n_reps: int):
+    out = (pimd_est * n_reps)()
+    _check(load().pimd_estimators(ctx, out, n_reps), ctx)
+    return [o.as_dict() for o in out]
+
+
+def pimd_get_state(ctx, n_entries: int, n_reps: int):
+    q = np.zeros(n_entries)
+    p = np.zeros(n_entries)
+    Q = np.zeros(n_reps)
+    step = ct.c_uint64(0)
+    _check(load().pimd_get_state(ctx, _dp(q), _dp(p), ct.byref(step), _dp(Q)), ctx)
+    return q, p, int(step.value), Q
+
+
+def pimd_set_state(ctx, q, p, step: int, Q=None):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64)
+    _check(load().pimd_set_state(ctx, _dp(q), _dp(p), int(step), _dp(Qa)), ctx)
+
+
+def pimd_get_forces(ctx, B: int, S: int):
+    x = np.zeros((B, 3))
+    f = np.zeros((B, 3))
+    V = np.zeros(S)
+    _check(load().pimd_get_forces(ctx, _dp(x), _dp(f), _dp(V)), ctx)
+    return x, f, V
+
+
+def pimd_get_neighbours(ctx, B: int, maxnb: int):
+    nnb = np.zeros(B, dtype=np.int32)
+    nbr = np.zeros((B, maxnb), dtype=np.int32)
+    _check(load().pimd_get_neighbours(ctx, _ip(nnb), _ip(nbr)), ctx)
+    return nnb, nbr
+
+
+def pimd_stage_times(ctx) -> dict:
+    ms = (ct.c_float * len(STAGES))()
+    _check(load().pimd_stage_times(ctx, ms), ctx)
+    return {k: float(v) for k, v in zip(STAGES, ms)}
+
+
+def pimd_kernels_per_step(ctx) -> int:
+    return int(load().pimd_kernels_per_step(ctx))
+
+
+def pimd_sync(ctx):
+    _check(load().pimd_sync(ctx), ctx)
+
+
+def pimd_sizes(ctx):
+    B, S = ct.c_int64(0), ct.c_int64(0)
+    R, M = ct.c_int(0), ct.c_int(0)
+    _check(load().pimd_sizes(ctx, ct.byref(B), ct.byref(S), ct.byref(R), ct.byref(M)), ctx)
+    return int(B.value), int(S.value), int(R.value), int(M.value)
+
+
+def pimd_destroy(ctx):
+    load().pimd_destroy(ctx)
+
+
+def pimd_last_error(ctx=None) -> str:
+    m = load().pimd_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------- helpers
+def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128, 128, 128), pile_lambda=1.0,
+                thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128, stream=None,
+                timing=False, nbr_algo=0) -> pimd_config:
+    c = pimd_config()
+    c.dt_fs = dt_fs
+    c.gamma0_per_fs = gamma0_per_fs
+    c.pile_lambda = pile_lambda
+    c.cutoff_A = cutoff
+    c.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    c.thermostat = 1 if thermostat else 0
+    c.potential = potential
+    c.max_neighbours = max_neighbours
+    c.omega_harm = omega
+    c.n_hidden = len(widths)
+    for l, w in enumerate(widths):
+        c.widths[l] = int(w)
+    c.stream = stream
+    c.timing = 1 if timing else 0
+    c.nbr_algo = int(nbr_algo)
+    return c
+
+
+class _Keep:
+    """Holds numpy arrays referenced by ctypes structures."""
+
+    def __init__(self):
+        self.items = []
+
+    def add(self, a):
+        self.items.append(a)
+        return a
+
+
+def make_replicas(replicas, keep: _Keep, masses=None):
+    arr = (pimd_replica_desc * len(replicas))()
+    for k, r in enumerate(replicas):
+        Z = keep.add(np.ascontiguousarray(r.Z, dtype=np.int32))
+        x0 = keep.add(np.ascontiguousarray(r.x0, dtype=np.float64))
+        d = arr[k]
+        d.n_atoms = len(Z)
+        d.n_beads = int(r.n_beads)
+        d.Z = _ip(Z)
+        d.x0 = _dp(x0)
+        if masses is not None:
+            m = keep.add(np.ascontiguousarray([masses[int(z)] for z in Z], dtype=np.float64))
+            d.mass = _dp(m)
+        else:
+            d.mass = None
+        for a in range(3):
+            d.box[a] = float(r.box[a])
+        d.T_K = float(r.T)
+        d.seed = int(r.seed)
+    return arr
+
+
+def make_model(model, keep: _Keep) -> pimd_model_desc:
+    m = pimd_model_desc()
+    els = list(model.elements)
+    m.n_elements = len(els)
+    m.Z = _ip(keep.add(np.array(els, dtype=np.int32)))
+    m.n_hidden = len(model.widths)
+    m.widths = _ip(keep.add(np.array(model.widths, dtype=np.int32)))
+    ptrs = (ct.POINTER(ct.c_double) * len(els))()
+    for e, z in enumerate(els):
+        ptrs[e] = _dp(keep.add(np.ascontiguousarray(model.params[z], dtype=np.float64)))
+    keep.add(ptrs)
+    m.params = ct.cast(ptrs, ct.POINTER(ct.POINTER(ct.c_double)))
+    d = model.desc
+    m.eta_R = d["eta_R"]
+    m.r_mu = _dp(keep.add(np.array(d["r_mu"], dtype=np.float64)))
+    m.zeta = _ip(keep.add(np.array(d["zeta"], dtype=np.int32)))
+    m.lam = _dp(keep.add(np.array(d["lam"], dtype=np.float64)))
+    m.eta_A = _dp(keep.add(np.array(d["eta_A"], dtype=np.float64)))
+    return m
+
+
+class Context:
+    """One library context on the current CUDA device; device workspace and
+    the stream come from PyTorch."""
+
+    def __init__(self, replicas, dt_fs, gamma0_per_fs, precision="fp32", widths=(128, 128, 128), cutoff=6.0,
+                 pile_lambda=1.0, thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128,
+                 masses=None, stream=None, timing=False, nbr_algo=0):
+        import torch
+        self.torch = torch
+        self.keep = _Keep()
+        self.replicas = list(replicas)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.cfg = make_config(dt_fs, gamma0_per_fs, precision, cutoff, widths, pile_lambda, thermostat, potential,
+                               omega, max_neighbours, ct.c_void_p(stream.cuda_stream), timing, nbr_algo)
+        self.reps = make_replicas(self.replicas, self.keep, masses)
+        self.ws_bytes = pimd_workspace_size(self.cfg, self.reps)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        self.h = pimd_create(self.cfg, self.reps, self.workspace.data_ptr(), self.ws_bytes)
+        self.B, self.S, self.R, self.maxnb = pimd_sizes(self.h)
+
+    def close(self):
+        if self.h is not None:
+            pimd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, model):
+        keep = _Keep()
+        desc = make_model(model, keep)
+        pimd_set_weights(self.h, desc)
+
+    def step(self, n: int = 1):
+        pimd_step(self.h, n)
+
+    def energy_forces(self, x=None, want_virial=True):
+        """x: CUDA FP64 tensor [B, 3] or None (current beads). Returns per-bead
+        energies [S], forces [B, 3] and virials [S, 3, 3] as CUDA tensors."""
+        t = self.torch
+        e = t.empty(self.S, dtype=t.float64, device="cuda")
+        f = t.empty(self.B, 3, dtype=t.float64, device="cuda")
+        v = t.empty(self.S, 9, dtype=t.float64, device="cuda") if want_virial else None
+        xp = None
+        if x is not None:
+            x = x.to(device="cuda", dtype=t.float64).contiguous()
+            xp = ct.c_void_p(x.data_ptr())
+        pimd_energy_forces(self.h, xp, ct.c_void_p(e.data_ptr()), ct.c_void_p(f.data_ptr()),
+                           ct.c_void_p(v.data_ptr()) if v is not None else None)
+        return e, f, (v.view(self.S, 3, 3) if v is not None else None)
+
+    def descriptors(self, x=None):
+        t = self.torch
+        G = t.empty(self.B, 64, dtype=t.float64, device="cuda")
+        xp = None
+        if x is not None:
+            x = x.to(device="cuda", dtype=t.float64).contiguous()
+            xp = ct.c_void_p(x.data_ptr())
+        pimd_descriptors(self.h, xp, ct.c_void_p(G.data_ptr()))
+        return G
+
+    def estimators(self):
+        return pimd_estimators(self.h, self.R)
+
+    def get_state(self):
+        return pimd_get_state(self.h, 3 * self.B, self.R)
+
+    def set_state(self, q, p, step, Q=None):
+        pimd_set_state(self.h, q, p, step, Q)
+
+    def get_forces(self):
+        return pimd_get_forces(self.h, self.B, self.S)
+
+    def neighbours(self):
+        return pimd_get_neighbours(self.h, self.B, self.maxnb)
+
+    def sync(self):
+        pimd_sync(self.h)
+
+    def stage_times(self) -> dict:
+        return pimd_stage_times(self.h)
+
+    def kernels_per_step(self) -> int:
+        return pimd_kernels_per_step(self.h)
+
+
+def _autograd_function():
+    import torch
+
+    class PimdEnergy(torch.autograd.Function):
+        """Per-bead energies V_k(x) with dV/dx from the library's adjoint
+        kernel (forces are evaluated with the energies; backward scales them
+        by the incoming gradient)."""
+
+        @staticmethod
+        def forward(fctx, x, context):
+            e, f, _ = context.energy_forces(x.detach(), want_virial=False)
+            fctx.save_for_backward(f)
+            fctx.bead_of_atom = context._bead_index()
+            return e
+
+        @staticmethod
+        def backward(fctx, grad_e):
+            (f,) = fctx.saved_tensors
+            g = grad_e[fctx.bead_of_atom].unsqueeze(1)
+            return -(g * f), None
+
+    return PimdEnergy
+
+
+def _bead_index(self):
+    t = self.torch
+    if not hasattr(self, "_bidx"):
+        idx = []
+        s = 0
+        for r in self.replicas:
+            for k in range(int(r.n_beads)):
+                idx.extend([s] * r.n_atoms)
+                s += 1
+        self._bidx = t.tensor(idx, dtype=t.long, device="cuda")
+    return self._bidx
+
+
+Context._bead_index = _bead_index
+
+
+def pimd_energy(x, context):
+    """Differentiable per-bead energies (torch.autograd)."""
+    return _autograd_function().apply(x, context)

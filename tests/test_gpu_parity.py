@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Bars: neighbour lists bit-exact; FP32 path forces within 1e-5 relative
+max-norm; FP64 path within 1e-10; trajectories over <= 10 steps with the same
+Philox noise."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_23728_gb300 import synth as s
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _P():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2503_23728_gb300 import pimd as P
+    return P
+
+
+def _relmax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _bead_positions(rep, P, seed, sigma=0.08, f32=True):
+    rng = np.random.default_rng(seed)
+    x = np.repeat(rep.x0[None], P, axis=0) + rng.normal(scale=sigma, size=(P, rep.n_atoms, 3))
+    if f32:
+        x = x.astype(np.float32).astype(np.float64)
+    return x
+
+
+def _with_beads(rep, P):
+    return s.Replica(rep.Z, rep.x0, rep.box, P, rep.T, rep.seed, rep.name)
+
+
+# ---------------------------------------------------------------- water-64, FP32
+@pytest.fixture(scope="module")
+def water_fp32(water64_model):
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 7)
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+    ctx.set_weights(m)
+    xb = _bead_positions(rep, 7, seed=17)
+    return P, w, rep, m, ctx, xb
+
+
+def test_neighbours_bit_exact(water_fp32):
+    P, w, rep, m, ctx, xb = water_fp32
+    ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
+    nnb, nbr = ctx.neighbours()
+    for k in range(rep.n_beads):
+        want, _, _ = O.neighbours(xb[k], rep.box, 6.0)
+        for i in range(rep.n_atoms):
+            b = k * rep.n_atoms + i
+            got = nbr[b, :nnb[b]]
+            assert np.array_equal(np.sort(got), want[i]), (k, i)
+
+
+def test_descriptors_fp32(water_fp32):
+    P, w, rep, m, ctx, xb = water_fp32
+    G = ctx.descriptors(torch.tensor(xb.reshape(-1, 3), device="cuda")).cpu().numpy()
+    for k in range(rep.n_beads):
+        Go = O.descriptors(m, xb[k], rep.box)
+        Gg = G[k * rep.n_atoms:(k + 1) * rep.n_atoms]
+        scale = np.abs(Go).max(axis=0) + 1e-30
+        assert np.all(np.abs(Gg - Go) <= 1e-5 * scale), k
+
+
+def test_energy_forces_virial_fp32(water_fp32):
+    P, w, rep, m, ctx, xb = water_fp32
+    e, f, v = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
+    e, f, v = e.cpu().numpy(), f.cpu().numpy().reshape(rep.n_beads, rep.n_atoms, 3), v.cpu().numpy()
+    Eo, Fo, Wo = O.energy_forces_batch(m, rep.Z, xb, rep.box)
+    assert _relmax(f, Fo) < 1e-5
+    assert np.abs(e - Eo.sum(axis=1)).max() / rep.n_atoms < 1e-5
+    assert _relmax(v, Wo) < 1e-5
+    # translation invariance of the GPU forces
+    assert np.abs(f.sum(axis=1)).max() < 1e-4 * np.abs(f).max()
+
+
+# ---------------------------------------------------------------- FAD, FP64
+@pytest.fixture(scope="module")
+def fad_fp64(fad_model):
+    P = _P()
+    w, r, m = fad_model
+    ctx = P.Context([r], w.dt_fs, w.gamma0_per_fs, precision="fp64", widths=w.widths)
+    ctx.set_weights(m)
+    return P, w, r, m, ctx
+
+
+def test_energy_forces_fp64(fad_fp64):
+    P, w, rep, m, ctx = fad_fp64
+    xb = _bead_positions(rep, rep.n_beads, seed=3, sigma=0.1, f32=False)
+    e, f, v = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
+    e, f, v = e.cpu().numpy(), f.cpu().numpy().reshape(rep.n_beads, rep.n_atoms, 3), v.cpu().numpy()
+    Eo, Fo, Wo = O.energy_forces_batch(m, rep.Z, xb, None)
+    assert _relmax(f, Fo) < 1e-10
+    assert np.abs(e - Eo.sum(axis=1)).max() < 1e-10 * np.abs(Eo.sum(axis=1)).max()
+    assert _relmax(v, Wo) < 1e-10
+
+
+def test_trajectory_fp64_matches_oracle(fad_model):
+    """Config-1 shape (FAD, P = 16, 0.25 fs, PILE-L): 10 GPU steps against 10
+    oracle steps with the same Philox noise."""
+    P = _P()
+    w, rep, m = fad_model
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp64", widths=w.widths)
+    ctx.set_weights(m)
+    q0, p0, st0, _ = ctx.get_state()
+    so = O.System(rep, s.MASS, w.dt_fs, w.gamma0_per_fs, model=m)
+    np.testing.assert_allclose(q0.reshape(so.q.shape), so.q, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(p0.reshape(so.p.shape), so.p, rtol=1e-12, atol=1e-14)
+    ctx.step(10)
+    so.step(10)
+    q, p, st, Q = ctx.get_state()
+    assert st == 10
+    np.testing.assert_allclose(q.reshape(so.q.shape), so.q, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(p.reshape(so.p.shape), so.p, rtol=0, atol=1e-9 * np.abs(so.p).max())
+    eg = ctx.estimators()[0]
+    eo = so.estimators()
+    for k in ("V_mean", "K_prim", "K_cv", "E_tot", "H_cons", "Q_thermo", "T_kin"):
+        assert abs(eg[k] - eo[k]) <= 1e-8 * max(1.0, abs(eo[k])), k
+    np.testing.assert_allclose(eg["W"], eo["W"], atol=1e-8 * np.abs(eo["W"]).max())
+
+
+def test_trajectory_fp32_matches_oracle(water64_model):
+    """Water-64 (P = 4): 5 steps on the FP32 path against the FP64 oracle."""
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 4)
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+    ctx.set_weights(m)
+    so = O.System(rep, s.MASS, w.dt_fs, w.gamma0_per_fs, model=m)
+    ctx.step(5)
+    so.step(5)
+    q, p, _, _ = ctx.get_state()
+    np.testing.assert_allclose(q.reshape(so.q.shape), so.q, rtol=0, atol=2e-5)
+    assert _relmax(p.reshape(so.p.shape), so.p) < 1e-4
+    eg, eo = ctx.estimators()[0], so.estimators()
+    for k in ("V_mean", "K_cv", "E_tot"):
+        assert abs(eg[k] - eo[k]) <= 1e-4 * max(1.0, abs(eo[k])), k
+
+
+# ---------------------------------------------------------------- harmonic oscillator
+def test_qho_gpu_matches_closed_form():
+    """Sec. S1 check on the GPU integrator: 3D oscillators with P = 8 beads,
+    PILE-L, FP64; <E> of the virial estimator vs the P-bead closed form."""
+    P = _P()
+    KB, HBAR = 8.617333262e-5, 0.6582119569
+    T, wq, N, Pb = 300.0, 0.0786, 256, 8
+    x0 = np.random.default_rng(1).normal(size=(N, 3)) * 0.1
+    rep = s.Replica(np.full(N, s.H, dtype=np.int32), x0, (0.0, 0.0, 0.0), Pb, T, 99)
+    ctx = P.Context([rep], 0.25, 0.08, precision="fp64", potential=P.POT_HARMONIC, omega=wq)
+    ctx.step(2000)
+    E = []
+    for _ in range(1500):
+        ctx.step(10)
+        E.append(ctx.estimators()[0]["E_tot"] / N)
+    E = np.array(E)
+    kT = KB * T
+    exact = 3 * kT * sum(1.0 / (1.0 + ((2 * Pb * kT / (HBAR * wq)) * np.sin(l * np.pi / Pb)) ** 2)
+                         for l in range(1, Pb + 1))
+    blocks = E[: len(E) // 15 * 15].reshape(15, -1).mean(axis=1)
+    err = blocks.std(ddof=1) / np.sqrt(len(blocks))
+    assert abs(E.mean() - exact) < 4 * err + 0.004 * exact, (E.mean(), err, exact)
+
+
+# ---------------------------------------------------------------- state, errors
+def test_checkpoint_resume(water64_model):
+    """A run resumed from get_state/set_state follows the uninterrupted run.
+    Force accumulation uses atomics, so the two agree to round-off (FP32
+    path: 1e-5 relative) rather than bit for bit."""
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 4)
+    a = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+    a.set_weights(m)
+    a.step(3)
+    q, p, st, Q = a.get_state()
+    a.step(4)
+    qa, pa, sa, Qa = a.get_state()
+    b = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+    b.set_weights(m)
+    b.set_state(q, p, st, Q)
+    b.step(4)
+    qb, pb, sb, Qb = b.get_state()
+    assert sa == sb == 7
+    np.testing.assert_allclose(qb, qa, rtol=0, atol=1e-5)
+    assert _relmax(pb, pa) < 1e-5
+    np.testing.assert_allclose(Qb, Qa, rtol=1e-6, atol=1e-9)
+
+
+def test_neighbour_overflow_is_reported(water64_model):
+    P = _P()
+    w, r, m = water64_model
+    ctx = P.Context([_with_beads(r, 2)], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths,
+                    max_neighbours=32)
+    with pytest.raises(P.PimdError) as ei:
+        ctx.set_weights(m)
+    assert ei.value.code == -7
+
+
+def test_autograd_energy(water_fp32):
+    P, w, rep, m, ctx, xb = water_fp32
+    x = torch.tensor(xb.reshape(-1, 3), device="cuda", requires_grad=True)
+    e = P.pimd_energy(x, ctx)
+    coef = torch.linspace(0.5, 1.5, e.shape[0], device="cuda", dtype=torch.float64)
+    (e * coef).sum().backward()
+    _, f, _ = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
+    bead = torch.arange(rep.n_beads, device="cuda").repeat_interleave(rep.n_atoms)
+    want = -(coef[bead].unsqueeze(1) * f)
+    # two evaluations agree to FP32 round-off (atomic accumulation order)
+    assert float((x.grad - want).abs().max() / want.abs().max()) < 1e-5
+
+
+# ---------------------------------------------------------------- uneven replicas
+def test_uneven_replicas_fp32():
+    P = _P()
+    reps = s.batch(n_rep=6, seed=77, beads=(3, 5, 8))
+    m = s.xavier_model(s.elements_of(reps), (64, 64), seed=4)
+    G = np.concatenate([O.descriptors(m, r.x0, None) for r in reps])
+    Z = np.concatenate([r.Z for r in reps])
+    s.set_normalisation(m, G, Z)
+    ctx = P.Context(reps, 0.25, 0.01, precision="fp32", widths=(64, 64))
+    ctx.set_weights(m)
+    xs = [_bead_positions(r, r.n_beads, seed=10 + k, sigma=0.05) for k, r in enumerate(reps)]
+    e, f, _ = ctx.energy_forces(torch.tensor(np.concatenate([x.reshape(-1, 3) for x in xs]), device="cuda"))
+    e, f = e.cpu().numpy(), f.cpu().numpy()
+    b0 = s0 = 0
+    for r, x in zip(reps, xs):
+        Eo, Fo, _ = O.energy_forces_batch(m, r.Z, x, None)
+        n = r.n_atoms * r.n_beads
+        assert _relmax(f[b0:b0 + n].reshape(Fo.shape), Fo) < 1e-5
+        assert np.abs(e[s0:s0 + r.n_beads] - Eo.sum(axis=1)).max() < 1e-5 * r.n_atoms
+        b0 += n
+        s0 += r.n_beads
+    ctx.step(5)
+    est = ctx.estimators()
+    assert len(est) == len(reps) and all(np.isfinite(x["E_tot"]) for x in est)
+
+
+def test_cell_lists_equal_all_pairs():
+    """Ice (4 x 3 x 3 cells per bead): cell-list neighbour lists are the same
+    arrays as the all-pairs scan, and the forces agree."""
+    P = _P()
+    w = s.workload("ice")
+    r = w.replicas[0]
+    rep = _with_beads(r, 3)
+    m = s.xavier_model(s.elements_of([rep]), w.widths, seed=2)
+    G = O.descriptors(m, rep.x0, rep.box)
+    s.set_normalisation(m, G, rep.Z)
+    xb = _bead_positions(rep, 3, seed=9, sigma=0.3)
+    out = []
+    for algo in (0, 1):
+        ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths, nbr_algo=algo)
+        ctx.set_weights(m)
+        _, f, _ = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
+        nnb, nbr = ctx.neighbours()
+        out.append((nnb, nbr, f.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0])
+    for b in range(len(out[0][0])):
+        n = out[0][0][b]
+        assert np.array_equal(out[0][1][b, :n], out[1][1][b, :n])
+    assert _relmax(out[0][2], out[1][2]) < 1e-6
+    want, _, _ = O.neighbours(xb[1], rep.box, 6.0)
+    for i in range(0, rep.n_atoms, 5):
+        b = rep.n_atoms + i
+        assert np.array_equal(out[0][1][b, :out[0][0][b]], want[i])
