@@ -247,6 +247,7 @@ const char* pimd_last_error(const pimd_ctx* ctx);
 
 int pimd_abi_version(void);
 
+
 #ifdef __cplusplus
 }
 #endif

@@ -190,6 +190,7 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
             rp.invL[a] = rp.periodic ? 1.0 / h.box[a] : 0.0;
             rp.Lf[a] = (float)rp.L[a];
             rp.invLf[a] = (float)rp.invL[a];
+            rp.Llo[a] = (float)(rp.L[a] - (double)rp.Lf[a]);
         }
         rp.kT_md = h.P * KB * h.T / MVV2E;
         rp.seed = h.seed;

@@ -48,6 +48,7 @@ struct Rep {
     int periodic;
     double L[3], invL[3];
     float Lf[3], invLf[3];   // FP32 box for the exact neighbour rule
+    float Llo[3];            // L - Lf, for error-free FP32 pair vectors
     double kT_md;            // k_B T_P in amu A^2 / fs^2
     unsigned long long seed;
     int nc[3];               // cells per side (cell lists), 0 = scan all atoms
@@ -64,6 +65,12 @@ struct BeadSys {
 // per normal mode of a replica
 struct Mode {
     double w, cw, sw, c1, c2, pad[3];
+};
+
+// pair schedule of the descriptor / adjoint kernels (chosen by the tuner)
+struct Sched {
+    int rmax;       // band length cap (<= 16)
+    int band_min;   // neighbours needed for the band schedule (>= rmax + 32)
 };
 
 // symmetry-function parameters in the working precision

@@ -23,7 +23,7 @@ static void set_smem(K kernel, size_t bytes, size_t& done)
     }
 }
 
-__device__ __forceinline__ float f_exp(float v) { return __expf(v); }
+__device__ __forceinline__ float f_exp(float v) { return expf(v); }
 __device__ __forceinline__ double f_exp(double v) { return exp(v); }
 __device__ __forceinline__ float f_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double f_sqrt(double v) { return sqrt(v); }
@@ -54,17 +54,40 @@ __device__ __forceinline__ void cutoff(double r, double rc, double pi_over_rc, d
     }
 }
 
-// minimum-image pair vector in the working precision
-__device__ __forceinline__ void min_image(const Rep& rp, float& dx, float& dy, float& dz)
+// Minimum-image pair vector x_j - x_i in the working precision. FP32: the
+// difference is formed error-free (TwoSum: s + e = x_j - x_i exactly), shifted
+// by k = rint(s / L) boxes (s - k L_hi is exact for |k| <= 1 by Sterbenz) and
+// rounded once, so wrapped pairs are as accurate as unwrapped ones.
+__device__ __forceinline__ float pair_axis(float xi, float xj, float L, float invL, float Llo, bool per)
 {
-    if (rp.periodic) {
-        dx = __fsub_rn(dx, __fmul_rn(rp.Lf[0], rintf(__fmul_rn(dx, rp.invLf[0]))));
-        dy = __fsub_rn(dy, __fmul_rn(rp.Lf[1], rintf(__fmul_rn(dy, rp.invLf[1]))));
-        dz = __fsub_rn(dz, __fmul_rn(rp.Lf[2], rintf(__fmul_rn(dz, rp.invLf[2]))));
+    const float a = xj, b = -xi;
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    float e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+    float t = s;
+    if (per) {
+        const float k = rintf(__fmul_rn(s, invL));
+        t = __fmaf_rn(-k, L, s);
+        e = __fmaf_rn(-k, Llo, e);
     }
+    return __fadd_rn(t, e);
 }
-__device__ __forceinline__ void min_image(const Rep& rp, double& dx, double& dy, double& dz)
+template <typename V4>
+__device__ __forceinline__ void pair_vec(const Rep& rp, const V4& xi, const V4& xj, float& dx, float& dy, float& dz)
 {
+    const bool per = rp.periodic != 0;
+    dx = pair_axis(xi.x, xj.x, rp.Lf[0], rp.invLf[0], rp.Llo[0], per);
+    dy = pair_axis(xi.y, xj.y, rp.Lf[1], rp.invLf[1], rp.Llo[1], per);
+    dz = pair_axis(xi.z, xj.z, rp.Lf[2], rp.invLf[2], rp.Llo[2], per);
+}
+template <typename V4>
+__device__ __forceinline__ void pair_vec(const Rep& rp, const V4& xi, const V4& xj, double& dx, double& dy,
+                                         double& dz)
+{
+    dx = xj.x - xi.x;
+    dy = xj.y - xi.y;
+    dz = xj.z - xi.z;
     if (rp.periodic) {
         dx = __dsub_rn(dx, __dmul_rn(rp.L[0], rint(dx / rp.L[0])));
         dy = __dsub_rn(dy, __dmul_rn(rp.L[1], rint(dy / rp.L[1])));
@@ -94,14 +117,14 @@ __device__ __forceinline__ V4 make4(Real a, Real b, Real c, Real d)
 //
 // Pair schedule. The unordered pairs of n neighbours are (j, k = j + d mod n)
 // for diagonals d = 1..D, D = (n-1)/2, plus the half diagonal d = n/2, j < n/2
-// when n is even. For n >= BAND_MIN the diagonals are cut into bands of R <=
-// RMAX; cell (band, j) is one lane's run of R pairs with j fixed in
+// when n is even. For n >= band_min the diagonals are cut into bands of R <=
+// rmax; cell (band, j) is one lane's run of R pairs with j fixed in
 // registers, so each pair loads only k's record, and 32 consecutive cells
 // (one warp step) touch consecutive k (conflict-free shared loads). Small n
 // use a flat walk over all pairs instead.
 // ---------------------------------------------------------------------------
-constexpr int RMAX = 8;
-constexpr int BAND_MIN = 48;   // >= RMAX + 32: lanes of one step never share a k
+constexpr int RMAX_CAP = 16;   // largest band length (staging capacity)
+// band_min >= rmax + 32 keeps the k of lanes in one step distinct (host enforces)
 
 struct PairWalk {
     int n, j, d, t, npairs;
@@ -141,10 +164,10 @@ struct BandCell {
     bool act;
 };
 
-__device__ __forceinline__ void band_geometry(int n, int& D, int& NB, int& R, int& ncell)
+__device__ __forceinline__ void band_geometry(int n, int rmax, int& D, int& NB, int& R, int& ncell)
 {
     D = (n - 1) >> 1;
-    NB = (D + RMAX - 1) / RMAX;
+    NB = (D + rmax - 1) / rmax;
     R = (D + NB - 1) / NB;
     ncell = NB * n;
 }
@@ -180,7 +203,7 @@ template <typename Real>
 __global__ void __launch_bounds__(256) desc_fwd_kernel(
     const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
-    DescParams<Real> dp, Real* __restrict__ G)
+    DescParams<Real> dp, Sched sc, Real* __restrict__ G)
 {
     using V4 = Vec4<Real>;
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -201,8 +224,8 @@ __global__ void __launch_bounds__(256) desc_fwd_kernel(
     for (int s = (int)lane; s < n; s += 32) {
         const int j = nbr[(size_t)b * maxnb + s];
         const V4 xj = x[sy.ba0 + j];
-        Real dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        min_image(rp, dx, dy, dz);
+        Real dx, dy, dz;
+        pair_vec(rp, xi, xj, dx, dy, dz);
         const Real r2 = dx * dx + dy * dy + dz * dz;
         const Real r = f_sqrt(r2);
         const Real ir = Real(1) / r;
@@ -223,9 +246,9 @@ __global__ void __launch_bounds__(256) desc_fwd_kernel(
     Real ga[NA];
 #pragma unroll
     for (int c = 0; c < NA; ++c) ga[c] = Real(0);
-    if (n >= BAND_MIN) {
+    if (n >= sc.band_min) {
         int D, NB, R, ncell;
-        band_geometry(n, D, NB, R, ncell);
+        band_geometry(n, sc.rmax, D, NB, R, ncell);
         for (int c0 = 0; c0 < ncell; c0 += 32) {
             const BandCell cl = band_cell(c0 + (int)lane, n, D, R, ncell);
             const V4 uj = U[cl.j], aj = A[cl.j];
@@ -273,14 +296,14 @@ void launch_descriptors(const Dev& d, const void* dpv, cudaStream_t st)
         { static size_t done = 0; set_smem(desc_fwd_kernel<double>, sm, done); }
         desc_fwd_kernel<double><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
             (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-            *(const DescParams<double>*)dpv, (double*)d.G);
+            *(const DescParams<double>*)dpv, d.sched, (double*)d.G);
     } else {
         const int w = desc_warps<float>(d.maxnb);
         const size_t sm = (size_t)w * 2 * d.maxnb * sizeof(float4);
         { static size_t done = 0; set_smem(desc_fwd_kernel<float>, sm, done); }
         desc_fwd_kernel<float><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
             (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-            *(const DescParams<float>*)dpv, (float*)d.G);
+            *(const DescParams<float>*)dpv, d.sched, (float*)d.G);
     }
 }
 
@@ -364,22 +387,23 @@ template <typename Real>
 __global__ void __launch_bounds__(256) desc_adj_kernel(
     const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
-    DescParams<Real> dp, const Real* __restrict__ dEdG, Vec4<Real>* __restrict__ f, double* __restrict__ Wv)
+    DescParams<Real> dp, Sched sc, const Real* __restrict__ dEdG, Vec4<Real>* __restrict__ f,
+    double* __restrict__ Wv)
 {
     using V4 = Vec4<Real>;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int wib = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const unsigned lane = lane_id();
-    // per warp: U, A, DA, ACC0 (dE/dA), ACC1 (w, s) records; staging [2][RMAX][2];
+    // per warp: U, A, DA, ACC0 (dE/dA), ACC1 (w, s) records; staging [2][RMAX_CAP][2];
     // radial dE/dr and g
-    V4* U = reinterpret_cast<V4*>(smem_raw) + (size_t)wib * (5 * maxnb + 4 * RMAX);
+    V4* U = reinterpret_cast<V4*>(smem_raw) + (size_t)wib * (5 * maxnb + 4 * RMAX_CAP);
     V4* A = U + maxnb;
     V4* DA = A + maxnb;
     V4* ACC0 = DA + maxnb;
     V4* ACC1 = ACC0 + maxnb;
-    V4* STG = ACC1 + maxnb;   // [2 buffers][RMAX][2 records]
-    Real* RAD = reinterpret_cast<Real*>(reinterpret_cast<V4*>(smem_raw) + (size_t)nw * (5 * maxnb + 4 * RMAX)) +
+    V4* STG = ACC1 + maxnb;   // [2 buffers][RMAX_CAP][2 records]
+    Real* RAD = reinterpret_cast<Real*>(reinterpret_cast<V4*>(smem_raw) + (size_t)nw * (5 * maxnb + 4 * RMAX_CAP)) +
                 (size_t)wib * (maxnb + ND);
     Real* gs = RAD + maxnb;
     const int b = blockIdx.x * nw + wib;
@@ -395,8 +419,8 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
     for (int s = (int)lane; s < n; s += 32) {
         const int j = nbr[(size_t)b * maxnb + s];
         const V4 xj = x[sy.ba0 + j];
-        Real dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        min_image(rp, dx, dy, dz);
+        Real dx, dy, dz;
+        pair_vec(rp, xi, xj, dx, dy, dz);
         const Real r2 = dx * dx + dy * dy + dz * dz;
         const Real r = f_sqrt(r2);
         const Real ir = Real(1) / r;
@@ -433,9 +457,9 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
         const Real sc = (zi == 0) ? Real(1) : (zi == 1) ? Real(0.5) : (zi == 2) ? Real(0.125) : Real(0.0078125);
         gp[nu] = gs[NR + nu] * sc;
     }
-    if (n >= BAND_MIN) {
+    if (n >= sc.band_min) {
         int D, NB, R, ncell;
-        band_geometry(n, D, NB, R, ncell);
+        band_geometry(n, sc.rmax, D, NB, R, ncell);
         for (int c0 = 0; c0 < ncell; c0 += 32) {
             const BandCell cl = band_cell(c0 + (int)lane, n, D, R, ncell);
             const int band_up = __shfl_down_sync(0xffffffffu, cl.band, 1);
@@ -456,7 +480,7 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
                     k = k >= n ? k - n : k;
                     adj_pair(gp, uj, aj, U[k], A[k], jd, kd);
                     if (!pass && r < cl.len - 1) {
-                        V4* st = STG + (size_t)(sbuf * RMAX + r) * 2;
+                        V4* st = STG + (size_t)(sbuf * RMAX_CAP + r) * 2;
                         st[0] = make4<V4, Real>(kd[0], kd[1], kd[2], kd[3]);
                         st[1] = make4<V4, Real>(kd[4], kd[5], kd[6], kd[7]);
                     }
@@ -488,8 +512,8 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
             const int rr = (int)(lane & 15);
             const int buf = (int)(lane >> 4);
             const int jb = buf ? js : j0, db = buf ? ds : d0, lb = buf ? ls : l0;
-            if (rr < RMAX && rr < lb - 1) {
-                const V4* st = STG + (size_t)(buf * RMAX + rr) * 2;
+            if (rr < lb - 1) {
+                const V4* st = STG + (size_t)(buf * RMAX_CAP + rr) * 2;
                 const Real v[8] = {st[0].x, st[0].y, st[0].z, st[0].w, st[1].x, st[1].y, st[1].z, st[1].w};
                 int k = jb + db + rr;
                 acc_rmw(ACC0, ACC1, k >= n ? k - n : k, v);
@@ -569,7 +593,7 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
 template <typename Real>
 static size_t adj_smem_per_warp(int maxnb)
 {
-    return (size_t)(5 * maxnb + 4 * RMAX) * sizeof(Vec4<Real>) + (size_t)(maxnb + ND) * sizeof(Real);
+    return (size_t)(5 * maxnb + 4 * RMAX_CAP) * sizeof(Vec4<Real>) + (size_t)(maxnb + ND) * sizeof(Real);
 }
 
 template <typename Real>
@@ -589,14 +613,14 @@ void launch_adjoint(const Dev& d, const void* dpv, cudaStream_t st)
         { static size_t done = 0; set_smem(desc_adj_kernel<double>, sm, done); }
         desc_adj_kernel<double><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
             (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-            *(const DescParams<double>*)dpv, (const double*)d.dEdG, (Dbl4*)d.f, d.W);
+            *(const DescParams<double>*)dpv, d.sched, (const double*)d.dEdG, (Dbl4*)d.f, d.W);
     } else {
         const int w = adj_warps<float>(d.maxnb);
         const size_t sm = (size_t)w * adj_smem_per_warp<float>(d.maxnb);
         { static size_t done = 0; set_smem(desc_adj_kernel<float>, sm, done); }
         desc_adj_kernel<float><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
             (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-            *(const DescParams<float>*)dpv, (const float*)d.dEdG, (float4*)d.f, d.W);
+            *(const DescParams<float>*)dpv, d.sched, (const float*)d.dEdG, (float4*)d.f, d.W);
     }
 }
 

@@ -62,6 +62,8 @@ struct Dev {
     float* wtc_vec = nullptr;          // FP32 vectors for the tensor-core epilogues
     size_t wtc_vec_per_type = 0;
 
+    Sched sched = {8, 48};             // pair schedule
+
     // integrator
     double dt = 0.5, gamma0 = 0.0, lambda = 1.0;
     int thermostat = 1;
