@@ -247,6 +247,34 @@ const char* pimd_last_error(const pimd_ctx* ctx);
 
 int pimd_abi_version(void);
 
+/* ---- descriptors without any device allocation ------------------------------
+ * The paper has no counterpart to this call. It serves callers that cannot
+ * allocate device memory at all -- a host engine that reserves the whole GPU
+ * for its own memory pool, a plug-in host that forbids cudaMalloc after
+ * start-up -- and so cannot provide the workspace pimd_create needs.
+ *
+ * Computes the raw descriptors G (same definitions and FP32 arithmetic as
+ * pimd_descriptors) of one configuration. x_dev: device [n_atoms][3] FP64
+ * positions; box: host [3] (all 0 = non-periodic), may be NULL; r_mu: host
+ * [32]; eta_A: host [4]; G_dev: device [n_atoms][64] FP64 output; stream:
+ * cudaStream_t or NULL. Blocks until the result is written.
+ *
+ * Scratch (FP32 positions, neighbour lists, descriptors) lives in one static
+ * device array of about 3.2 MB inside this library, held on every GPU that
+ * loads the library until the process exits. It limits n_atoms to
+ * PIMD_NOALLOC_MAX_ATOMS and neighbours per atom to PIMD_NOALLOC_MAX_NEIGHBOURS;
+ * larger inputs fail with INVALID_ARG, overfull neighbour lists with
+ * NBR_OVERFLOW. No cudaMalloc, cudaFree or allocating library routine runs.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture. All calls share the one array, so calls that
+ * overlap on the GPU (other threads, other streams) race with each other;
+ * serialise them. Error text: pimd_last_error(NULL).                        */
+#define PIMD_NOALLOC_MAX_ATOMS 4096
+#define PIMD_NOALLOC_MAX_NEIGHBOURS 128
+int pimd_descriptors_noalloc(const double* x_dev, int n_atoms, const double* box, double cutoff_A,
+                             double eta_R, const double* r_mu, const double* eta_A, double* G_dev,
+                             void* stream);
 
 #ifdef __cplusplus
 }

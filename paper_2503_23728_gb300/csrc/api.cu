@@ -309,6 +309,8 @@ Offsets layout(const pimd_config* cfg, const Build& b)
 
 }  // namespace
 
+void pimd::set_thread_error(const std::string& msg) { g_tls_error = msg; }
+
 struct pimd_ctx {
     Dev d;
     pimd_config cfg;

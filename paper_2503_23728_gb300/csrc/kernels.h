@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace pimd {
@@ -90,6 +92,9 @@ void launch_descriptors_out(const Dev& d, double* G, cudaStream_t st);
 bool network_tc_supported(int width, int n_hidden);
 size_t tc_weight_bytes(int width, int n_hidden);
 void prepare_tc_weights(const Dev& d, int type, const double* blob, void* host_img, float* host_vec);
+
+// message returned by pimd_last_error(NULL) on this thread
+void set_thread_error(const std::string& msg);
 
 // ring polymer
 void launch_rp_init(const Dev& d, cudaStream_t st);

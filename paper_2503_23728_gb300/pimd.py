@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
     L.pimd_stage_times.argtypes = [vp, ct.POINTER(ct.c_float)]
     L.pimd_kernels_per_step.argtypes = [vp]
     L.pimd_kernels_per_step.restype = ct.c_int
+    L.pimd_descriptors_noalloc.argtypes = [vp, ct.c_int, dp, ct.c_double, ct.c_double, dp, dp, vp, vp]
     _lib = L
     return L
 
@@ -197,6 +198,17 @@ def pimd_stage_times(ctx) -> dict:
 
 def pimd_kernels_per_step(ctx) -> int:
     return int(load().pimd_kernels_per_step(ctx))
+
+
+def pimd_descriptors_noalloc(x_ptr, n_atoms: int, box, cutoff: float, eta_R: float, r_mu, eta_A, G_ptr,
+                             stream=None):
+    """Descriptors of one configuration using the library's static scratch
+    array (no device allocation by the library; see include/pimd.h)."""
+    b = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    rm = np.ascontiguousarray(r_mu, dtype=np.float64)
+    ea = np.ascontiguousarray(eta_A, dtype=np.float64)
+    _check(load().pimd_descriptors_noalloc(x_ptr, int(n_atoms), _dp(b), float(cutoff), float(eta_R), _dp(rm),
+                                           _dp(ea), G_ptr, stream))
 
 
 def pimd_sync(ctx):
