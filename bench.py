@@ -43,9 +43,10 @@ def args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16_tc", choices=["bf16_tc", "fp32", "fp64"])
-    ap.add_argument("--workload", default="ice", choices=["ice", "water64", "fad", "batch"])
+    ap.add_argument("--workload", default="ice", choices=["ice", "water64", "fad", "batch", "water4096"])
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default pair schedule")
     return ap.parse_args()
 
 
@@ -138,6 +139,10 @@ def run_gpu(a, workload, precision, model=None):
         model = build_model(ctx, workload, None)
     else:
         ctx.set_weights(model)
+    if not a.no_tune:
+        ctx.tune_result = ctx.tune(reps=3)   # pair schedule, set-up only (not timed)
+    else:
+        ctx.tune_result = None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     for _ in range(a.warmup):
@@ -239,6 +244,22 @@ def cpu_baseline(workload, model, budget_s=15.0):
             "seconds": dt}
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bead_atoms_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job bead-atom evaluations per second: every rank advances its own
+    replicas; the job takes as long as its slowest rank."""
+    return world * bead_atoms_per_rank * steps / (max_ms / 1e3)
+
+
 def workload_of(name, rank):
     from paper_2503_23728_gb300 import synth as s
     w = s.workload(name)
@@ -253,7 +274,8 @@ def config_of(w, precision, world):
     desc = {"ice": "ice Ih 432 H2O (1296 atoms), P=32, T=250 K, dt=0.5 fs, 3x128 tanh, cutoff 6 A",
             "water64": "water 64 H2O (192 atoms), P=32, T=300 K, dt=0.5 fs, 3x128 tanh, cutoff 6 A",
             "fad": "formic-acid dimer (10 atoms), P=16, T=300 K, dt=0.25 fs, 2x64 tanh, cutoff 6 A",
-            "batch": "256 gas-phase clusters of 6-24 atoms, P in {8,16,32,64}, 2x64 tanh"}[w.name]
+            "batch": "256 gas-phase clusters of 6-24 atoms, P in {8,16,32,64}, 2x64 tanh",
+            "water4096": "water 4096 H2O (12288 atoms), P=64, T=300 K, dt=0.5 fs, 4x256 tanh, cutoff 6 A"}[w.name]
     return {"workload": desc, "bead_atoms_per_gpu": w.bead_atoms, "replicas_per_gpu": len(w.replicas),
             "path": precision, "parallelism": "independent replicas per GPU" if world > 1 else "1 GPU",
             "l2": "flushed between timed steps (256 MB write)",
@@ -286,13 +308,9 @@ def main():
     clk = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     ms, stages = timed_steps(a, ctx, stream, flush, barrier)
     clocks = clk.stop()
-    total_ms = float(np.sum(ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(ms)), dist, "cuda")
     steps_per_s = a.steps / (total_ms / 1e3)
-    value = world * w.bead_atoms * steps_per_s
+    value = job_throughput(w.bead_atoms, world, a.steps, total_ms)
     ns_day = steps_per_s * w.dt_fs * 86400 / 1e6
     st_mean = {k: float(np.mean([s[k] for s in stages])) for k in stages[0]}
     adj_flops = adjoint_flops(ctx)
@@ -325,6 +343,7 @@ def main():
         "dtype": {"bf16_tc": "bf16", "fp32": "f32", "fp64": "f64"}[a.precision], "data": "synthetic",
         "config": config_of(w, a.precision, world),
         "ns_per_day": ns_day,
+        "tuned_schedule": ctx.tune_result,
         "stages_ms": st_mean,
         "fp32_plain": fp32,
         "speedup_vs_fp32_plain": (value / fp32["value"]) if fp32 else None,

@@ -94,8 +94,16 @@ typedef struct {
     int timing;              /* nonzero: record CUDA events around every stage of
                                 a step (see pimd_stage_times)                      */
     int nbr_algo;            /* 0: cell lists where a periodic box holds >= 3
-                                cells of edge >= cutoff per side, else all pairs;
-                                1: all pairs everywhere. Same lists either way.    */
+                                cells of edge >= cutoff per side and the stencil
+                                scan is cheaper than scanning the bead, else all
+                                pairs; 1: all pairs; 2: cells wherever the box
+                                allows. Same lists in every case.                 */
+    int deterministic;       /* 1: forces summed in a fixed order (pair vectors
+                                stored, then gathered per atom; small neighbour
+                                counts use ordered pairs), so runs and resumed
+                                runs are bit-identical. Costs B*max_neighbours
+                                records of workspace and one more kernel.
+                                0: atomic force accumulation (faster).           */
 } pimd_config;
 
 /* stages of one step, in launch order (pimd_stage_times) */
@@ -229,6 +237,20 @@ int pimd_get_neighbours(pimd_ctx* ctx, int* nnb_host, int* nbr_host);
  * ms: host [PIMD_N_STAGES]. Synchronises. Errors: STATE without timing or
  * before the first step.                                                    */
 int pimd_stage_times(pimd_ctx* ctx, float* ms);
+
+/* Autotuner. Times the descriptor + adjoint kernels on the context's current
+ * configuration for each candidate pair schedule (band length 4..16 with the
+ * shuffle-carry schedule, or the flat pair walk) and keeps the fastest; the
+ * per-step graphs are re-recorded at the next pimd_step. reps: timed
+ * repetitions per candidate (>= 1). out_ms: host [3] or NULL -> best time
+ * (ms, descriptors + adjoint), chosen band length (0 = flat walk), time of
+ * the default schedule. Synchronises. Errors: STATE before weights are set. */
+int pimd_tune(pimd_ctx* ctx, int reps, double* out_ms);
+
+/* Set the pair schedule directly: band_length 4..16 (shuffle-carry bands for
+ * atoms with >= band_length + 32 neighbours, flat walk below), or 0 for the
+ * flat walk everywhere. Errors: INVALID_ARG for other lengths.              */
+int pimd_set_schedule(pimd_ctx* ctx, int band_length);
 
 /* Number of kernels one step launches (memset nodes not counted).          */
 int pimd_kernels_per_step(const pimd_ctx* ctx);

@@ -50,6 +50,7 @@ struct Build {
     std::vector<double> mass, x0, cmat;
     std::vector<Mode> modes;
     std::vector<int2> rp_blocks;
+    std::vector<int> rep_blk0;
     std::vector<int> typeZ;
     std::vector<int> cell_bs;
     int total_cells = 0, max_cells = 0;
@@ -72,7 +73,7 @@ struct Carve {
 struct Offsets {
     size_t reps, bsys, ba_sys, mass, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
-        fnm, Q, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
+        fnm, Q, qpart, rep_blk0, wbuf, vbuf, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
 };
 
 int check_config(const pimd_config* cfg, std::string& e)
@@ -81,7 +82,8 @@ int check_config(const pimd_config* cfg, std::string& e)
     if (!(cfg->dt_fs != 0.0) || !std::isfinite(cfg->dt_fs)) { e = "dt_fs must be finite and non-zero"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->precision < 0 || cfg->precision > 2) { e = "unknown precision"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat != 0 && cfg->thermostat != 1) { e = "thermostat must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
-    if (cfg->nbr_algo != 0 && cfg->nbr_algo != 1) { e = "nbr_algo must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->nbr_algo < 0 || cfg->nbr_algo > 2) { e = "nbr_algo must be 0, 1 or 2"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->deterministic != 0 && cfg->deterministic != 1) { e = "deterministic must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->potential != PIMD_POT_MODEL && cfg->potential != PIMD_POT_HARMONIC) { e = "unknown potential"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat == 1 && !(cfg->gamma0_per_fs >= 0.0)) { e = "gamma0_per_fs must be >= 0"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat == 1 && !(cfg->pile_lambda >= 0.0)) { e = "pile_lambda must be >= 0"; return PIMD_ERR_INVALID_ARG; }
@@ -196,10 +198,15 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         rp.seed = h.seed;
         // cell lists: >= 3 cells per side with edge >= cutoff (1e-5 margin
         // against rounding of the FP32 cell coordinate)
-        if (rp.periodic && cfg->potential == PIMD_POT_MODEL && cfg->nbr_algo == 0) {
+        if (rp.periodic && cfg->potential == PIMD_POT_MODEL && cfg->nbr_algo != 1) {
             int nc[3];
             for (int a = 0; a < 3; ++a) nc[a] = (int)std::floor(h.box[a] / (cfg->cutoff_A * (1.0 + 1e-5)));
-            if (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3 && (long long)nc[0] * nc[1] * nc[2] <= 16384) {
+            const long long ncell = (long long)nc[0] * nc[1] * nc[2];
+            // auto: cells when the stencil scan (+ sort) beats scanning the bead
+            const double warp_iter_cells = 27.0 * h.N / std::max(1ll, ncell) / 32.0 + 12.0;
+            const double warp_iter_all = h.N / 32.0;
+            const bool pays = cfg->nbr_algo == 2 || warp_iter_cells < 0.8 * warp_iter_all;
+            if (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3 && ncell <= 16384 && pays) {
                 for (int a = 0; a < 3; ++a) rp.nc[a] = nc[a];
                 rp.ncells = nc[0] * nc[1] * nc[2];
                 rp.cell0 = b.total_cells;
@@ -233,9 +240,11 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
             for (int a = 0; a < 3; ++a) b.x0.push_back(h.x0[3 * i + a]);
         }
         const int T = rp_threads / h.P;
+        b.rep_blk0.push_back((int)b.rp_blocks.size());
         for (int first = 0; first < 3 * h.N; first += T) b.rp_blocks.push_back(make_int2(r, first));
         ba0 += h.N * h.P; bs0 += h.P; atom0 += h.N; mode0 += h.P;
     }
+    b.rep_blk0.push_back((int)b.rp_blocks.size());
     // network rows grouped by element type, each group padded to 128 rows
     if (cfg->potential == PIMD_POT_MODEL) {
         std::vector<std::vector<int>> rows(zs.size());
@@ -295,6 +304,10 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.p = c.take(sizeof(double) * 3 * (size_t)b.B);
     o.fnm = c.take(sizeof(double) * 3 * (size_t)b.B);
     o.Q = c.take(sizeof(double) * b.R);
+    o.qpart = c.take(sizeof(double) * 2 * b.rp_blocks.size());
+    o.rep_blk0 = c.take(sizeof(int) * b.rep_blk0.size());
+    o.wbuf = c.take(rs * 9 * (size_t)b.B);
+    o.vbuf = c.take(cfg->deterministic && model ? v4 * (size_t)b.B * mnb : 0);
     o.step = c.take(sizeof(unsigned long long));
     o.err = c.take(sizeof(DevErr));
     o.est = c.take(sizeof(double) * EST_STRIDE * b.R);
@@ -379,6 +392,7 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false)
         else launch_network_fp(d, st);
         mark(c, PIMD_STAGE_ADJOINT, st, timed);
         launch_adjoint(d, dparams(c), st);
+        if (d.deterministic) launch_force_gather(d, st);
     }
     mark(c, PIMD_STAGE_ENERGY, st, timed);
     launch_energy_reduce(d, st);
@@ -537,6 +551,11 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.p = (double*)(w + o.p);
     d.fnm = (double*)(w + o.fnm);
     d.Q = (double*)(w + o.Q);
+    d.qpart = (double*)(w + o.qpart);
+    d.rep_blk0 = (int*)(w + o.rep_blk0);
+    d.wbuf = w + o.wbuf;
+    d.vbuf = w + o.vbuf;
+    d.deterministic = cfg->deterministic ? 1 : 0;
     d.step = (unsigned long long*)(w + o.step);
     d.err = (DevErr*)(w + o.err);
     d.est = (double*)(w + o.est);
@@ -569,6 +588,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     if (!rc) rc = upload(c, d.cmat, b.cmat);
     if (!rc) rc = upload(c, d.modes, b.modes);
     if (!rc) rc = upload(c, d.rp_blocks, b.rp_blocks);
+    if (!rc) rc = upload(c, d.rep_blk0, b.rep_blk0);
     if (!rc) rc = upload(c, d.perm, b.perm);
     if (!rc) rc = upload(c, d.tile_type, b.tile_type);
     if (!rc) rc = upload(c, d.cell_bs, b.cell_bs);
@@ -658,6 +678,12 @@ int pimd_set_weights(pimd_ctx* c, const pimd_model_desc* m)
     c->dpf.eta_R = (float)c->dpd.eta_R;
     for (int q = 0; q < NR; ++q) c->dpf.r_mu[q] = (float)c->dpd.r_mu[q];
     for (int q = 0; q < 4; ++q) c->dpf.eta_A[q] = (float)c->dpd.eta_A[q];
+    c->dpd.eta_R_l2 = c->dpd.eta_R * M_LOG2E;
+    c->dpf.eta_R_l2 = (float)c->dpd.eta_R_l2;
+    for (int q = 0; q < 4; ++q) {
+        c->dpd.eta_A_l2[q] = c->dpd.eta_A[q] * M_LOG2E;
+        c->dpf.eta_A_l2[q] = (float)c->dpd.eta_A_l2[q];
+    }
     int rc;
     if (d.precision == PIMD_FP64) {
         rc = upload(c, d.wts, all);
@@ -734,11 +760,79 @@ int pimd_stage_times(pimd_ctx* c, float* ms)
     return PIMD_OK;
 }
 
+int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (reps < 1) return fail(c, PIMD_ERR_INVALID_ARG, "reps must be >= 1");
+    if (c->d.potential != PIMD_POT_MODEL || !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    int rc = refresh_forces(c);   // current neighbour lists, dE/dG
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_check(c, cudaErrorUnknown, "cudaEventCreate");
+    }
+    const Sched defaults = {8, 40};
+    Sched cands[8];
+    int nc = 0;
+    const int rl[6] = {4, 6, 8, 10, 12, 16};
+    for (int q = 0; q < 6; ++q) cands[nc++] = Sched{rl[q], rl[q] + 32};
+    cands[nc++] = Sched{8, 1 << 30};   // flat pair walk for every atom
+    double best = 1e30, t_default = 0.0;
+    Sched pick = defaults;
+    for (int q = 0; q < nc && !rc; ++q) {
+        c->d.sched = cands[q];
+        launch_descriptors(c->d, dparams(c), c->st);   // warm the schedule
+        launch_adjoint(c->d, dparams(c), c->st);
+        double tmin = 1e30;
+        for (int r = 0; r < reps && !rc; ++r) {
+            cudaEventRecord(e0, c->st);
+            launch_descriptors(c->d, dparams(c), c->st);
+            launch_adjoint(c->d, dparams(c), c->st);
+            cudaEventRecord(e1, c->st);
+            rc = cuda_check(c, cudaEventSynchronize(e1), "tune");
+            float ms = 0.0f;
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            tmin = std::min(tmin, (double)ms);
+        }
+        if (q == 2) t_default = tmin;   // band length 8 is the untuned default
+        if (tmin < best) {
+            best = tmin;
+            pick = cands[q];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->d.sched = pick;
+    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
+    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    if (!rc) rc = refresh_forces(c);   // forces with the chosen schedule
+    if (!rc) rc = device_errors(c);
+    if (out_ms) {
+        out_ms[0] = best;
+        out_ms[1] = pick.band_min >= (1 << 30) ? 0.0 : (double)pick.rmax;
+        out_ms[2] = t_default;
+    }
+    return rc;
+}
+
+int pimd_set_schedule(pimd_ctx* c, int band_length)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (band_length != 0 && (band_length < 1 || band_length > 16))
+        return fail(c, PIMD_ERR_INVALID_ARG, "band_length must be 0 or 1..16");
+    c->d.sched = band_length == 0 ? Sched{8, 1 << 30} : Sched{band_length, band_length + 32};
+    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
+    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    c->forces_valid = false;
+    return PIMD_OK;
+}
+
 int pimd_kernels_per_step(const pimd_ctx* c)
 {
     if (!c) return 0;
     // ring start, neighbours, descriptors, network, adjoint, energy, ring finish, step counter
-    return c->d.potential == PIMD_POT_HARMONIC ? 5 : 8;
+    return c->d.potential == PIMD_POT_HARMONIC ? 5 : (c->d.deterministic ? 9 : 8);
 }
 
 int pimd_energy_forces(pimd_ctx* c, const double* x_dev, double* e_dev, double* f_dev, double* virial_dev)

@@ -79,6 +79,7 @@ struct DescParams {
     Real rc, pi_over_rc, eta_R;
     Real r_mu[NR];
     Real eta_A[4];
+    Real eta_R_l2, eta_A_l2[4];   // widths times log2(e) (FP32 exponentials use exp2)
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

@@ -23,8 +23,21 @@ static void set_smem(K kernel, size_t bytes, size_t& done)
     }
 }
 
-__device__ __forceinline__ float f_exp(float v) { return expf(v); }
-__device__ __forceinline__ double f_exp(double v) { return exp(v); }
+// Gaussian factor exp(-eta x2). FAST (BF16 network path, whose tolerance is
+// 1e-2): exp2(-(eta log2 e) x2) on the special-function unit; otherwise the
+// accurate expf / exp.
+template <bool FAST>
+__device__ __forceinline__ float gauss(float eta, float eta_l2, float x2)
+{
+    if (FAST) return exp2f(-eta_l2 * x2);
+    return expf(-eta * x2);
+}
+template <bool FAST>
+__device__ __forceinline__ double gauss(double eta, double eta_l2, double x2)
+{
+    (void)eta_l2;
+    return exp(-eta * x2);
+}
 __device__ __forceinline__ float f_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double f_sqrt(double v) { return sqrt(v); }
 
@@ -158,10 +171,33 @@ struct PairWalk {
     }
 };
 
-// one warp step of the band schedule: this lane's cell
+// this lane's cell of the band schedule; cells c = band * n + j advance by 32
+// per warp step (n >= 33 here, so j wraps at most once per step)
 struct BandCell {
     int j, dlo, len, band;
     bool act;
+    __device__ __forceinline__ void start(int lane, int n, int D, int R, int NB)
+    {
+        band = 0;
+        j = lane;
+        set(D, R, NB);
+    }
+    __device__ __forceinline__ void next(int n, int D, int R, int NB)
+    {
+        j += 32;
+        if (j >= n) {
+            j -= n;
+            ++band;
+        }
+        set(D, R, NB);
+    }
+    __device__ __forceinline__ void set(int D, int R, int NB)
+    {
+        act = band < NB;
+        dlo = 1 + band * R;
+        len = act ? min(D - dlo + 1, R) : 0;
+        if (!act) j = 0;
+    }
 };
 
 __device__ __forceinline__ void band_geometry(int n, int rmax, int& D, int& NB, int& R, int& ncell)
@@ -172,35 +208,79 @@ __device__ __forceinline__ void band_geometry(int n, int rmax, int& D, int& NB, 
     ncell = NB * n;
 }
 
-__device__ __forceinline__ BandCell band_cell(int c, int n, int D, int R, int ncell)
+// forward contribution of pair (j, k): ga[q*4+e] += (1 + lambda c)^zeta B_e,
+// q = zeta_index * 2 + lambda_index. FP64: 32 scalar FMAs. FP32: packed
+// FP32x2 over lambda = (+1, -1): g2[z*4+e] = (ga[(2z)*4+e], ga[(2z+1)*4+e]).
+template <typename Real> struct FwdAcc;
+template <> struct FwdAcc<double> {
+    double g[NA];
+};
+template <> struct FwdAcc<float> {
+    float2 g[16];
+};
+
+__device__ __forceinline__ void acc_zero(FwdAcc<double>& a)
 {
-    BandCell b;
-    b.act = c < ncell;
-    b.band = b.act ? c / n : -1;
-    b.j = b.act ? c - b.band * n : 0;
-    b.dlo = 1 + b.band * R;
-    b.len = b.act ? min(D - b.dlo + 1, R) : 0;
-    return b;
+#pragma unroll
+    for (int c = 0; c < NA; ++c) a.g[c] = 0.0;
+}
+__device__ __forceinline__ void acc_zero(FwdAcc<float>& a)
+{
+#pragma unroll
+    for (int c = 0; c < 16; ++c) a.g[c] = make_float2(0.0f, 0.0f);
+}
+__device__ __forceinline__ void acc_out(const FwdAcc<double>& a, double (&ga)[NA])
+{
+#pragma unroll
+    for (int c = 0; c < NA; ++c) ga[c] = a.g[c];
+}
+__device__ __forceinline__ void acc_out(const FwdAcc<float>& a, float (&ga)[NA])
+{
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ga[(2 * z) * 4 + e] = a.g[z * 4 + e].x;
+            ga[(2 * z + 1) * 4 + e] = a.g[z * 4 + e].y;
+        }
 }
 
-// forward contribution of pair (j, k): ga[q*4+e] += (1 + lambda c)^zeta B_e
-template <typename Real, typename V4>
-__device__ __forceinline__ void fwd_pair(const V4& uj, const V4& aj, const V4& uk, const V4& ak, Real (&ga)[NA])
+__device__ __forceinline__ void fwd_pair(const Dbl4& uj, const Dbl4& aj, const Dbl4& uk, const Dbl4& ak,
+                                         FwdAcc<double>& acc)
 {
-    const Real c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-    const Real Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
-    const Real xp = Real(1) + c, xm = Real(1) - c;
-    const Real xp2 = xp * xp, xm2 = xm * xm;
-    const Real xp4 = xp2 * xp2, xm4 = xm2 * xm2;
-    const Real Pq[8] = {xp, xm, xp2, xm2, xp4, xm4, xp4 * xp4, xm4 * xm4};
+    const double c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+    const double Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
+    const double xp = 1.0 + c, xm = 1.0 - c;
+    const double xp2 = xp * xp, xm2 = xm * xm;
+    const double xp4 = xp2 * xp2, xm4 = xm2 * xm2;
+    const double Pq[8] = {xp, xm, xp2, xm2, xp4, xm4, xp4 * xp4, xm4 * xm4};
 #pragma unroll
     for (int q = 0; q < 8; ++q)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) ga[q * 4 + e] += Pq[q] * Bv[e];
+        for (int e = 0; e < 4; ++e) acc.g[q * 4 + e] += Pq[q] * Bv[e];
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(256) desc_fwd_kernel(
+__device__ __forceinline__ void fwd_pair(const float4& uj, const float4& aj, const float4& uk, const float4& ak,
+                                         FwdAcc<float>& acc)
+{
+    const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
+    const float Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
+    // X_n = ((1 + c)^n, (1 - c)^n)
+    const float2 X1 = __ffma2_rn(make_float2(c, c), make_float2(1.0f, -1.0f), make_float2(1.0f, 1.0f));
+    const float2 X2 = __fmul2_rn(X1, X1);
+    const float2 X4 = __fmul2_rn(X2, X2);
+    const float2 X8 = __fmul2_rn(X4, X4);
+    const float2 Xz[4] = {X1, X2, X4, X8};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float2 Bb = make_float2(Bv[e], Bv[e]);
+#pragma unroll
+        for (int z = 0; z < 4; ++z) acc.g[z * 4 + e] = __ffma2_rn(Xz[z], Bb, acc.g[z * 4 + e]);
+    }
+}
+
+template <typename Real, bool FAST>
+__global__ void __launch_bounds__(256, 4) desc_fwd_kernel(
     const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<Real> dp, Sched sc, Real* __restrict__ G)
@@ -234,42 +314,47 @@ __global__ void __launch_bounds__(256) desc_fwd_kernel(
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
             const Real t = r - dp.r_mu[c];
-            gr[c] += f_exp(-dp.eta_R * t * t) * fc;
+            gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
         }
         U[s] = make4<V4, Real>(dx * ir, dy * ir, dz * ir, r);
-        A[s] = make4<V4, Real>(f_exp(-dp.eta_A[0] * r2) * fc, f_exp(-dp.eta_A[1] * r2) * fc,
-                               f_exp(-dp.eta_A[2] * r2) * fc, f_exp(-dp.eta_A[3] * r2) * fc);
+        A[s] = make4<V4, Real>(gauss<FAST>(dp.eta_A[0], dp.eta_A_l2[0], r2) * fc,
+                               gauss<FAST>(dp.eta_A[1], dp.eta_A_l2[1], r2) * fc,
+                               gauss<FAST>(dp.eta_A[2], dp.eta_A_l2[2], r2) * fc,
+                               gauss<FAST>(dp.eta_A[3], dp.eta_A_l2[3], r2) * fc);
     }
     const Real Gr = transpose_reduce32(gr, lane);
     __syncwarp();
 
-    Real ga[NA];
-#pragma unroll
-    for (int c = 0; c < NA; ++c) ga[c] = Real(0);
+    FwdAcc<Real> acc;
+    acc_zero(acc);
     if (n >= sc.band_min) {
         int D, NB, R, ncell;
         band_geometry(n, sc.rmax, D, NB, R, ncell);
-        for (int c0 = 0; c0 < ncell; c0 += 32) {
-            const BandCell cl = band_cell(c0 + (int)lane, n, D, R, ncell);
+        BandCell cl;
+        cl.start((int)lane, n, D, R, NB);
+        for (int c0 = 0; c0 < ncell; c0 += 32, cl.next(n, D, R, NB)) {
             const V4 uj = U[cl.j], aj = A[cl.j];
+#pragma unroll 2
             for (int r = 0; r < cl.len; ++r) {
                 int k = cl.j + cl.dlo + r;
                 k = k >= n ? k - n : k;
-                fwd_pair(uj, aj, U[k], A[k], ga);
+                fwd_pair(uj, aj, U[k], A[k], acc);
             }
         }
         if ((n & 1) == 0) {
             const int h = n >> 1;
-            for (int j = (int)lane; j < h; j += 32) fwd_pair(U[j], A[j], U[j + h], A[j + h], ga);
+            for (int j = (int)lane; j < h; j += 32) fwd_pair(U[j], A[j], U[j + h], A[j + h], acc);
         }
     } else {
         PairWalk w;
         w.init(n, (int)lane);
         for (; w.valid(); w.advance(32)) {
             const int k = w.k();
-            fwd_pair(U[w.j], A[w.j], U[k], A[k], ga);
+            fwd_pair(U[w.j], A[w.j], U[k], A[k], acc);
         }
     }
+    Real ga[NA];
+    acc_out(acc, ga);
     Real Ga = transpose_reduce32(ga, lane);
     // 2^(1 - zeta) for zeta = 1, 2, 4, 8 (channel zeta index = lane / 8)
     const int zi = (int)lane >> 3;
@@ -288,22 +373,30 @@ static int desc_warps(int maxnb)
     return w;
 }
 
+template <bool FAST>
+static void run_desc_f32(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    const int w = desc_warps<float>(d.maxnb);
+    const size_t sm = (size_t)w * 2 * d.maxnb * sizeof(float4);
+    { static size_t done = 0; set_smem(desc_fwd_kernel<float, FAST>, sm, done); }
+    desc_fwd_kernel<float, FAST><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+        *(const DescParams<float>*)dpv, d.sched, (float*)d.G);
+}
+
 void launch_descriptors(const Dev& d, const void* dpv, cudaStream_t st)
 {
     if (d.precision == 0) {
         const int w = desc_warps<double>(d.maxnb);
         const size_t sm = (size_t)w * 2 * d.maxnb * sizeof(Dbl4);
-        { static size_t done = 0; set_smem(desc_fwd_kernel<double>, sm, done); }
-        desc_fwd_kernel<double><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+        { static size_t done = 0; set_smem(desc_fwd_kernel<double, false>, sm, done); }
+        desc_fwd_kernel<double, false><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
             (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
             *(const DescParams<double>*)dpv, d.sched, (double*)d.G);
+    } else if (d.precision == 2) {
+        run_desc_f32<true>(d, dpv, st);
     } else {
-        const int w = desc_warps<float>(d.maxnb);
-        const size_t sm = (size_t)w * 2 * d.maxnb * sizeof(float4);
-        { static size_t done = 0; set_smem(desc_fwd_kernel<float>, sm, done); }
-        desc_fwd_kernel<float><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
-            (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-            *(const DescParams<float>*)dpv, d.sched, (float*)d.G);
+        run_desc_f32<false>(d, dpv, st);
     }
 }
 
@@ -334,37 +427,108 @@ __device__ __forceinline__ void atomic_add_vec(Dbl4* f, double ax, double ay, do
     atomicAdd(&f->z, az);
 }
 
-// adjoint contribution of pair (j, k): jd / kd += (dE/dA(.)[4], w[3], s)
-template <typename Real, typename V4>
-__device__ __forceinline__ void adj_pair(const Real (&gp)[NA], const V4& uj, const V4& aj, const V4& uk,
-                                         const V4& ak, Real (&jd)[8], Real (&kd)[8])
+// adjoint contribution of pair (j, k): jd / kd += (dE/dA(.)[4], w[3], s).
+// Coefficients g'_nu = 2^(1-zeta) g_(32+nu); FP32 packs them over lambda:
+// g2[z*4+e] = (g'_((2z)*4+e), g'_((2z+1)*4+e)).
+template <typename Real> struct AdjCoef;
+template <> struct AdjCoef<double> {
+    double g[NA];
+};
+template <> struct AdjCoef<float> {
+    float2 g[16];
+};
+
+__device__ __forceinline__ double zeta_scale(int zi) { return zi == 0 ? 1.0 : zi == 1 ? 0.5 : zi == 2 ? 0.125 : 0.0078125; }
+
+__device__ __forceinline__ void coef_load(AdjCoef<double>& a, const double* gs)
 {
-    const Real c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-    const Real Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
-    const Real xp = Real(1) + c, xm = Real(1) - c;
-    const Real xp2 = xp * xp, xm2 = xm * xm;
-    const Real xp3 = xp2 * xp, xm3 = xm2 * xm;
-    const Real xp4 = xp2 * xp2, xm4 = xm2 * xm2;
-    const Real xp7 = xp4 * xp3, xm7 = xm4 * xm3;
-    const Real Pq[8] = {xp, xm, xp2, xm2, xp4, xm4, xp4 * xp4, xm4 * xm4};
-    Real H[8];
+#pragma unroll
+    for (int nu = 0; nu < NA; ++nu) a.g[nu] = gs[NR + nu] * zeta_scale(nu >> 3);
+}
+__device__ __forceinline__ void coef_load(AdjCoef<float>& a, const float* gs)
+{
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float sc = (float)zeta_scale(z);
+            a.g[z * 4 + e] = make_float2(gs[NR + (2 * z) * 4 + e] * sc, gs[NR + (2 * z + 1) * 4 + e] * sc);
+        }
+}
+
+__device__ __forceinline__ void adj_pair(const AdjCoef<double>& cf, const Dbl4& uj, const Dbl4& aj, const Dbl4& uk,
+                                         const Dbl4& ak, double (&jd)[8], double (&kd)[8])
+{
+    const double c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+    const double Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
+    const double xp = 1.0 + c, xm = 1.0 - c;
+    const double xp2 = xp * xp, xm2 = xm * xm;
+    const double xp3 = xp2 * xp, xm3 = xm2 * xm;
+    const double xp4 = xp2 * xp2, xm4 = xm2 * xm2;
+    const double xp7 = xp4 * xp3, xm7 = xm4 * xm3;
+    const double Pq[8] = {xp, xm, xp2, xm2, xp4, xm4, xp4 * xp4, xm4 * xm4};
+    double H[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        H[q] = gp[q * 4] * Bv[0];
+        H[q] = cf.g[q * 4] * Bv[0];
 #pragma unroll
-        for (int e = 1; e < 4; ++e) H[q] += gp[q * 4 + e] * Bv[e];
+        for (int e = 1; e < 4; ++e) H[q] += cf.g[q * 4 + e] * Bv[e];
     }
     // dE/dc = sum_q zeta lambda (1 + lambda c)^(zeta - 1) H_q
-    Real dEdc = H[0] - H[1];
-    dEdc += Real(2) * (xp * H[2] - xm * H[3]);
-    dEdc += Real(4) * (xp3 * H[4] - xm3 * H[5]);
-    dEdc += Real(8) * (xp7 * H[6] - xm7 * H[7]);
-    Real K[4];
+    double dEdc = H[0] - H[1];
+    dEdc += 2.0 * (xp * H[2] - xm * H[3]);
+    dEdc += 4.0 * (xp3 * H[4] - xm3 * H[5]);
+    dEdc += 8.0 * (xp7 * H[6] - xm7 * H[7]);
+    double K[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        K[e] = gp[e] * Pq[0];
+        K[e] = cf.g[e] * Pq[0];
 #pragma unroll
-        for (int q = 1; q < 8; ++q) K[e] += gp[q * 4 + e] * Pq[q];
+        for (int q = 1; q < 8; ++q) K[e] += cf.g[q * 4 + e] * Pq[q];
+    }
+    jd[0] += K[0] * ak.x; jd[1] += K[1] * ak.y; jd[2] += K[2] * ak.z; jd[3] += K[3] * ak.w;
+    kd[0] += K[0] * aj.x; kd[1] += K[1] * aj.y; kd[2] += K[2] * aj.z; kd[3] += K[3] * aj.w;
+    jd[4] += dEdc * uk.x; jd[5] += dEdc * uk.y; jd[6] += dEdc * uk.z; jd[7] += dEdc * c;
+    kd[4] += dEdc * uj.x; kd[5] += dEdc * uj.y; kd[6] += dEdc * uj.z; kd[7] += dEdc * c;
+}
+
+__device__ __forceinline__ void adj_pair(const AdjCoef<float>& cf, const float4& uj, const float4& aj,
+                                         const float4& uk, const float4& ak, float (&jd)[8], float (&kd)[8])
+{
+    const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
+    const float Bv[4] = {aj.x * ak.x, aj.y * ak.y, aj.z * ak.z, aj.w * ak.w};
+    // X_n = ((1 + c)^n, (1 - c)^n)
+    const float2 X1 = __ffma2_rn(make_float2(c, c), make_float2(1.0f, -1.0f), make_float2(1.0f, 1.0f));
+    const float2 X2 = __fmul2_rn(X1, X1);
+    const float2 X3 = __fmul2_rn(X2, X1);
+    const float2 X4 = __fmul2_rn(X2, X2);
+    const float2 X7 = __fmul2_rn(X4, X3);
+    const float2 X8 = __fmul2_rn(X4, X4);
+    // H_z = (sum_e g'_(z,+,e) B_e, sum_e g'_(z,-,e) B_e)
+    float2 Bb[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Bb[e] = make_float2(Bv[e], Bv[e]);
+    float2 H[4];
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+        H[z] = __fmul2_rn(cf.g[z * 4], Bb[0]);
+#pragma unroll
+        for (int e = 1; e < 4; ++e) H[z] = __ffma2_rn(cf.g[z * 4 + e], Bb[e], H[z]);
+    }
+    // dE/dc = sum_z zeta (xp^(zeta-1) H_(z,+) - xm^(zeta-1) H_(z,-))
+    float2 T = __ffma2_rn(__fmul2_rn(X1, make_float2(2.0f, 2.0f)), H[1], H[0]);
+    T = __ffma2_rn(__fmul2_rn(X3, make_float2(4.0f, 4.0f)), H[2], T);
+    T = __ffma2_rn(__fmul2_rn(X7, make_float2(8.0f, 8.0f)), H[3], T);
+    const float dEdc = T.x - T.y;
+    // K_e = sum_z (g'_(z,+,e) xp^zeta + g'_(z,-,e) xm^zeta)
+    float K[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float2 k2 = __fmul2_rn(cf.g[e], X1);
+        k2 = __ffma2_rn(cf.g[4 + e], X2, k2);
+        k2 = __ffma2_rn(cf.g[8 + e], X4, k2);
+        k2 = __ffma2_rn(cf.g[12 + e], X8, k2);
+        K[e] = k2.x + k2.y;
     }
     jd[0] += K[0] * ak.x; jd[1] += K[1] * ak.y; jd[2] += K[2] * ak.z; jd[3] += K[3] * ak.w;
     kd[0] += K[0] * aj.x; kd[1] += K[1] * aj.y; kd[2] += K[2] * aj.z; kd[3] += K[3] * aj.w;
@@ -383,12 +547,12 @@ __device__ __forceinline__ void acc_rmw(V4* ACC0, V4* ACC1, int s, const Real (&
     ACC1[s] = b;
 }
 
-template <typename Real>
+template <typename Real, bool FAST>
 __global__ void __launch_bounds__(256) desc_adj_kernel(
     const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<Real> dp, Sched sc, const Real* __restrict__ dEdG, Vec4<Real>* __restrict__ f,
-    double* __restrict__ Wv)
+    Real* __restrict__ wbuf, int det, Vec4<Real>* __restrict__ vbuf)
 {
     using V4 = Vec4<Real>;
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -430,13 +594,13 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
             const Real t = r - dp.r_mu[c];
-            const Real e = f_exp(-dp.eta_R * t * t);
+            const Real e = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t);
             dEdr += gs[c] * e * (Real(-2) * dp.eta_R * t * fc + dfc);
         }
         Real a[4], da[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const Real ex = f_exp(-dp.eta_A[e] * r2);
+            const Real ex = gauss<FAST>(dp.eta_A[e], dp.eta_A_l2[e], r2);
             a[e] = ex * fc;
             da[e] = ex * (Real(-2) * dp.eta_A[e] * r * fc + dfc);
         }
@@ -450,18 +614,14 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
     __syncwarp();
 
     // angular coefficients g'_nu = 2^(1-zeta) g_(32+nu)
-    Real gp[NA];
-#pragma unroll
-    for (int nu = 0; nu < NA; ++nu) {
-        const int zi = nu >> 3;
-        const Real sc = (zi == 0) ? Real(1) : (zi == 1) ? Real(0.5) : (zi == 2) ? Real(0.125) : Real(0.0078125);
-        gp[nu] = gs[NR + nu] * sc;
-    }
+    AdjCoef<Real> gp;
+    coef_load(gp, gs);
     if (n >= sc.band_min) {
         int D, NB, R, ncell;
         band_geometry(n, sc.rmax, D, NB, R, ncell);
-        for (int c0 = 0; c0 < ncell; c0 += 32) {
-            const BandCell cl = band_cell(c0 + (int)lane, n, D, R, ncell);
+        BandCell cl;
+        cl.start((int)lane, n, D, R, NB);
+        for (int c0 = 0; c0 < ncell; c0 += 32, cl.next(n, D, R, NB)) {
             const int band_up = __shfl_down_sync(0xffffffffu, cl.band, 1);
             const int band_dn = __shfl_up_sync(0xffffffffu, cl.band, 1);
             const bool recv = cl.act && lane < 31 && band_up == cl.band;   // carry arrives from lane + 1
@@ -473,6 +633,7 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
             Real jd[8], kd[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) jd[q] = kd[q] = Real(0);
+#pragma unroll 2
             for (int r = 0; r < nst; ++r) {
                 const bool valid = r < cl.len;
                 if (valid) {
@@ -534,6 +695,21 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
                 __syncwarp();
             }
         }
+    } else if (det) {
+        // ordered pairs, j-side sums only: every unordered pair is evaluated
+        // twice, and each lane owns its j's accumulators (fixed order)
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int j = j0 + (int)lane;
+            if (j < n) {
+                const V4 uj = U[j], aj = A[j];
+                Real jd[8], kd[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) jd[q] = kd[q] = Real(0);
+                for (int k = 0; k < n; ++k)
+                    if (k != j) adj_pair(gp, uj, aj, U[k], A[k], jd, kd);
+                acc_rmw(ACC0, ACC1, j, jd);
+            }
+        }
     } else {
         PairWalk w;
         w.init(n, (int)lane);
@@ -569,7 +745,10 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
         const Real ir = Real(1) / u.w;
         const Real v[3] = {dEdr * u.x + (a1.x - a1.w * u.x) * ir, dEdr * u.y + (a1.y - a1.w * u.y) * ir,
                            dEdr * u.z + (a1.z - a1.w * u.z) * ir};
-        atomic_add_vec(&f[sy.ba0 + j], -v[0], -v[1], -v[2]);
+        if (det)
+            vbuf[(size_t)b * maxnb + s] = make4<V4, Real>(v[0], v[1], v[2], Real(0));
+        else
+            atomic_add_vec(&f[sy.ba0 + j], -v[0], -v[1], -v[2]);
         const Real d3[3] = {u.x * u.w, u.y * u.w, u.z * u.w};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -583,11 +762,72 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
 #pragma unroll
     for (int q = 0; q < 9; ++q) wl[q] = warp_sum(wl[q]);
     if (lane == 0) {
-        atomic_add_vec(&f[b], fi[0], fi[1], fi[2]);
-        const int s = ba_sys[b];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) atomicAdd(&Wv[(size_t)s * 9 + q], (double)wl[q]);
+        if (det)
+            f[b] = make4<V4, Real>(fi[0], fi[1], fi[2], Real(0));   // gathered later
+        else
+            atomic_add_vec(&f[b], fi[0], fi[1], fi[2]);
     }
+    if (lane < 9) {
+        Real mine = wl[0];
+#pragma unroll
+        for (int q = 1; q < 9; ++q)
+            if ((int)lane == q) mine = wl[q];
+        wbuf[(size_t)b * 9 + lane] = mine;   // per bead-atom virial, reduced per bead in FP64
+    }
+}
+
+// Deterministic force gather: F_b = (sum of b's own pair vectors) - sum over
+// neighbours j of the pair vector j stored for b (b's slot in j's sorted
+// list, found by bisection). Fixed order, no atomics. Warp per bead-atom.
+template <typename Real>
+__global__ void __launch_bounds__(256) force_gather_kernel(const int* __restrict__ ba_sys,
+                                                           const BeadSys* __restrict__ bsys,
+                                                           const int* __restrict__ nbr, const int* __restrict__ nnb,
+                                                           int maxnb, int B, const Vec4<Real>* __restrict__ vbuf,
+                                                           Vec4<Real>* __restrict__ f)
+{
+    using V4 = Vec4<Real>;
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = lane_id();
+    if (b >= B) return;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const int il = b - sy.ba0;
+    const int n = min(nnb[b], maxnb);
+    Real acc[3] = {Real(0), Real(0), Real(0)};
+    for (int s = (int)lane; s < n; s += 32) {
+        const int jg = sy.ba0 + nbr[(size_t)b * maxnb + s];
+        const int* L = nbr + (size_t)jg * maxnb;
+        int lo = 0, hi = min(nnb[jg], maxnb);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (L[mid] < il) lo = mid + 1;
+            else hi = mid;
+        }
+        const V4 v = vbuf[(size_t)jg * maxnb + lo];
+        acc[0] += v.x;
+        acc[1] += v.y;
+        acc[2] += v.z;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[a] = warp_sum(acc[a]);
+    if (lane == 0) {
+        V4 v = f[b];
+        v.x -= acc[0];
+        v.y -= acc[1];
+        v.z -= acc[2];
+        f[b] = v;
+    }
+}
+
+void launch_force_gather(const Dev& d, cudaStream_t st)
+{
+    const int blocks = (int)(((size_t)d.B * 32 + 255) / 256);
+    if (d.precision == 0)
+        force_gather_kernel<double><<<blocks, 256, 0, st>>>(d.ba_sys, d.bsys, d.nbr, d.nnb, d.maxnb, d.B,
+                                                            (const Dbl4*)d.vbuf, (Dbl4*)d.f);
+    else
+        force_gather_kernel<float><<<blocks, 256, 0, st>>>(d.ba_sys, d.bsys, d.nbr, d.nnb, d.maxnb, d.B,
+                                                           (const float4*)d.vbuf, (float4*)d.f);
 }
 
 template <typename Real>
@@ -605,22 +845,32 @@ static int adj_warps(int maxnb)
     return w;
 }
 
+template <bool FAST>
+static void run_adj_f32(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    const int w = adj_warps<float>(d.maxnb);
+    const size_t sm = (size_t)w * adj_smem_per_warp<float>(d.maxnb);
+    { static size_t done = 0; set_smem(desc_adj_kernel<float, FAST>, sm, done); }
+    desc_adj_kernel<float, FAST><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+        *(const DescParams<float>*)dpv, d.sched, (const float*)d.dEdG, (float4*)d.f, (float*)d.wbuf,
+        d.deterministic, (float4*)d.vbuf);
+}
+
 void launch_adjoint(const Dev& d, const void* dpv, cudaStream_t st)
 {
     if (d.precision == 0) {
         const int w = adj_warps<double>(d.maxnb);
         const size_t sm = (size_t)w * adj_smem_per_warp<double>(d.maxnb);
-        { static size_t done = 0; set_smem(desc_adj_kernel<double>, sm, done); }
-        desc_adj_kernel<double><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
+        { static size_t done = 0; set_smem(desc_adj_kernel<double, false>, sm, done); }
+        desc_adj_kernel<double, false><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
             (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-            *(const DescParams<double>*)dpv, d.sched, (const double*)d.dEdG, (Dbl4*)d.f, d.W);
+            *(const DescParams<double>*)dpv, d.sched, (const double*)d.dEdG, (Dbl4*)d.f, (double*)d.wbuf,
+            d.deterministic, (Dbl4*)d.vbuf);
+    } else if (d.precision == 2) {
+        run_adj_f32<true>(d, dpv, st);
     } else {
-        const int w = adj_warps<float>(d.maxnb);
-        const size_t sm = (size_t)w * adj_smem_per_warp<float>(d.maxnb);
-        { static size_t done = 0; set_smem(desc_adj_kernel<float>, sm, done); }
-        desc_adj_kernel<float><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
-            (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-            *(const DescParams<float>*)dpv, d.sched, (const float*)d.dEdG, (float4*)d.f, d.W);
+        run_adj_f32<false>(d, dpv, st);
     }
 }
 
@@ -843,26 +1093,46 @@ void launch_network_fp(const Dev& d, cudaStream_t st)
 // per bead).
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void energy_reduce_kernel(const Real* __restrict__ Eatom, const BeadSys* __restrict__ bsys, int S,
-                                     double* __restrict__ V)
+__global__ void __launch_bounds__(256) energy_reduce_kernel(const Real* __restrict__ Eatom,
+                                                            const Real* __restrict__ wbuf,
+                                                            const BeadSys* __restrict__ bsys, int S,
+                                                            double* __restrict__ V, double* __restrict__ Wv)
 {
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned lane = lane_id();
-    if (s >= S) return;
+    // one block per bead; FP64 sums over its atoms in a fixed order
+    __shared__ double red[10][8];
+    const int s = blockIdx.x;
     const BeadSys sy = bsys[s];
-    double acc = 0.0;
-    for (int i = (int)lane; i < sy.N; i += 32) acc += (double)Eatom[sy.ba0 + i];
-    acc = warp_sum(acc);
-    if (lane == 0) V[s] = acc;
+    double acc[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+    for (int i = threadIdx.x; i < sy.N; i += blockDim.x) {
+        acc[0] += (double)Eatom[sy.ba0 + i];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[1 + q] += (double)wbuf[(size_t)(sy.ba0 + i) * 9 + q];
+    }
+    const int wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        const double v = warp_sum(acc[q]);
+        if ((threadIdx.x & 31) == 0) red[q][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+        if (threadIdx.x == 0) V[s] = t;
+        else Wv[(size_t)s * 9 + threadIdx.x - 1] = t;
+    }
 }
 
 void launch_energy_reduce(const Dev& d, cudaStream_t st)
 {
-    const int blocks = (d.S * 32 + 255) / 256;
     if (d.precision == 0)
-        energy_reduce_kernel<double><<<blocks, 256, 0, st>>>((const double*)d.Eatom, d.bsys, d.S, d.V);
+        energy_reduce_kernel<double><<<d.S, 256, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
+                                                          d.V, d.W);
     else
-        energy_reduce_kernel<float><<<blocks, 256, 0, st>>>((const float*)d.Eatom, d.bsys, d.S, d.V);
+        energy_reduce_kernel<float><<<d.S, 256, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
+                                                         d.V, d.W);
 }
 
 // ---------------------------------------------------------------------------
@@ -872,7 +1142,7 @@ template <typename Real>
 __global__ void harmonic_kernel(const Vec4<Real>* __restrict__ x, const int* __restrict__ ba_sys,
                                 const BeadSys* __restrict__ bsys, const Rep* __restrict__ reps,
                                 const double* __restrict__ mass, int B, double omega, Real* __restrict__ Eatom,
-                                Vec4<Real>* __restrict__ f, double* __restrict__ Wv)
+                                Vec4<Real>* __restrict__ f, Real* __restrict__ wbuf)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
@@ -890,7 +1160,7 @@ __global__ void harmonic_kernel(const Vec4<Real>* __restrict__ x, const int* __r
     fv.w = Real(0);
     f[b] = fv;
     for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) atomicAdd(&Wv[(size_t)s * 9 + 3 * a + c], -k * p[a] * p[c]);
+        for (int c = 0; c < 3; ++c) wbuf[(size_t)b * 9 + 3 * a + c] = (Real)(-k * p[a] * p[c]);
 }
 
 void launch_harmonic(const Dev& d, cudaStream_t st)
@@ -898,10 +1168,10 @@ void launch_harmonic(const Dev& d, cudaStream_t st)
     const int blocks = (d.B + 255) / 256;
     if (d.precision == 0)
         harmonic_kernel<double><<<blocks, 256, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.mass, d.B,
-                                                        d.omega_harm, (double*)d.Eatom, (Dbl4*)d.f, d.W);
+                                                        d.omega_harm, (double*)d.Eatom, (Dbl4*)d.f, (double*)d.wbuf);
     else
         harmonic_kernel<float><<<blocks, 256, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.mass, d.B,
-                                                       d.omega_harm, (float*)d.Eatom, (float4*)d.f, d.W);
+                                                       d.omega_harm, (float*)d.Eatom, (float4*)d.f, (float*)d.wbuf);
 }
 
 // ---------------------------------------------------------------------------

@@ -48,6 +48,11 @@ struct Dev {
     double* p = nullptr;               // [3B] normal-mode momenta
     double* fnm = nullptr;             // [3B] normal-mode forces
     double* Q = nullptr;               // [R] thermostat heat
+    double* qpart = nullptr;           // [2][n_rp_blocks] thermostat heat per block and half step
+    int* rep_blk0 = nullptr;           // [R + 1] first ring-polymer block of each replica
+    void* wbuf = nullptr;              // Real[B][9] per bead-atom virial
+    void* vbuf = nullptr;              // Vec4<Real>[B][maxnb] pair vectors (deterministic mode)
+    int deterministic = 0;
     unsigned long long* step = nullptr;
     DevErr* err = nullptr;
     double* est = nullptr;             // [R][EST_STRIDE]
@@ -64,7 +69,7 @@ struct Dev {
     float* wtc_vec = nullptr;          // FP32 vectors for the tensor-core epilogues
     size_t wtc_vec_per_type = 0;
 
-    Sched sched = {8, 48};             // pair schedule
+    Sched sched = {8, 40};             // pair schedule (band length 8, bands for n >= 40)
 
     // integrator
     double dt = 0.5, gamma0 = 0.0, lambda = 1.0;
@@ -85,6 +90,7 @@ void launch_network_fp(const Dev& d, cudaStream_t st);
 void launch_network_tc(const Dev& d, cudaStream_t st);
 void launch_adjoint(const Dev& d, const void* dp, cudaStream_t st);
 void launch_energy_reduce(const Dev& d, cudaStream_t st);
+void launch_force_gather(const Dev& d, cudaStream_t st);
 void launch_harmonic(const Dev& d, cudaStream_t st);
 void launch_pack_positions(const Dev& d, const double* x3, cudaStream_t st);
 void launch_unpack(const Dev& d, double* f3, double* e, double* vir, double* x3, cudaStream_t st);

@@ -387,6 +387,298 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// Wide network (hidden width 256): weights stream through shared memory in
+// K-chunks of 64 (double-buffered bulk copies; a tcgen05.commit per chunk
+// releases its buffer), one activation buffer serves as the next layer's A
+// operand, and hidden activations needed again by the backward pass
+// (h_1 .. h_{L-2}) are parked in tensor memory as packed BF16 next to the
+// 256-column accumulator (512 TMEM columns).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int WW = 256;          // hidden width of the wide kernel
+constexpr int KCH = 64;          // K elements per weight chunk
+
+__host__ __device__ __forceinline__ int wide_phase_layer(int L, int p) { return p < L ? p + 1 : 2 * L - p; }
+__host__ __device__ __forceinline__ int wide_phase_K(int L, int p)
+{
+    return (p < L && wide_phase_layer(L, p) == 1) ? ND : WW;
+}
+__host__ __device__ __forceinline__ int wide_phase_N(int L, int p)
+{
+    return (p >= L && wide_phase_layer(L, p) == 1) ? ND : WW;
+}
+// chunks of all phases, in issue order
+__host__ __device__ __forceinline__ int wide_nchunks(int L)
+{
+    int g = 0;
+    for (int p = 0; p < 2 * L; ++p) g += wide_phase_K(L, p) / KCH;
+    return g;
+}
+// byte offset of chunk g in one type's image, and its phase's N
+__host__ __device__ __forceinline__ size_t wide_chunk_offset(int L, int g, int* Nout)
+{
+    size_t o = 0;
+    int gg = 0;
+    for (int p = 0; p < 2 * L; ++p) {
+        const int nch = wide_phase_K(L, p) / KCH, N = wide_phase_N(L, p);
+        for (int c = 0; c < nch; ++c, ++gg) {
+            if (gg == g) {
+                if (Nout) *Nout = N;
+                return o;
+            }
+            o += (size_t)N * KCH * 2;
+        }
+    }
+    if (Nout) *Nout = 0;
+    return o;
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+}  // namespace
+
+template <int L>
+__global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
+    const float* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
+    const unsigned char* __restrict__ wimg, size_t img_per_type, const float* __restrict__ wvec,
+    size_t vec_per_type, float* __restrict__ Eatom, float* __restrict__ dEdG, DevErr* __restrict__ err)
+{
+    constexpr int M = 128;
+    constexpr int A0_B = M * ND * 2;          // 16 KB
+    constexpr int ACT_B = M * WW * 2;         // 64 KB
+    constexpr int WB_B = WW * KCH * 2;        // 32 KB per chunk buffer
+    constexpr int NCH = (L == 1 ? 1 : 1 + 4 * (L - 1)) + 4 * L;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A0 = sm;
+    unsigned char* ACT = A0 + A0_B;
+    unsigned char* GA = ACT + ACT_B;
+    unsigned char* WB[2] = {GA + ACT_B, GA + ACT_B + WB_B};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(GA + ACT_B + 2 * WB_B);   // mma, wload[2], wfree[2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 6);
+    float* ysum = reinterpret_cast<float*>(tslot + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hsel = warp >> 2;
+    const int row = 32 * q + lane;
+    const int row0 = blockIdx.x * M;
+    const int type = tile_type[row0 / TILE_ROWS];
+    const unsigned char* img = wimg + (size_t)type * img_per_type;
+    const float* vec = wvec + (size_t)type * vec_per_type;
+    const float* b_l = vec;
+    const float* w_out = vec + L * WW;
+    const float* mu = w_out + WW;
+    const float* sigma = mu + ND;
+    const float b_out = sigma[ND], s_E = sigma[ND + 1], e_Z = sigma[ND + 2];
+
+    const uint32_t bar_mma = smem_u32(&bars[0]);
+    const uint32_t bar_ld[2] = {smem_u32(&bars[1]), smem_u32(&bars[2])};
+    const uint32_t bar_free[2] = {smem_u32(&bars[3]), smem_u32(&bars[4])};
+    if (tid == 0) {
+        mbar_init(bar_mma, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar_ld[i], 1);
+            mbar_init(bar_free[i], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+
+    int issued = 0;   // chunks whose bulk copy thread 0 has started
+    auto load_chunk = [&](int g) {
+        int N = 0;
+        const size_t off = wide_chunk_offset(L, g, &N);
+        bulk_load(smem_u32(WB[g & 1]), img + off, (uint32_t)(N * KCH * 2), bar_ld[g & 1]);
+    };
+    if (tid == 0) {
+        load_chunk(0);
+        issued = 1;
+        if (NCH > 1) {
+            load_chunk(1);
+            issued = 2;
+        }
+    }
+
+    // h_0 = (G - mu) / sigma in BF16
+    {
+        const int r = tid & (M - 1), c0 = (tid >> 7) * 32;
+        const int ba = perm[row0 + r];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + 8 * g + j;
+                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : 0.0f;
+            }
+            uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                  pack_bf16(v[6], v[7]));
+            *reinterpret_cast<uint4*>(A0 + 2 * cm_index(r, c0 + 8 * g, ND)) = pk;
+        }
+    }
+    fence_proxy();
+    __syncthreads();
+
+    bool ok = true;
+    float y_part = 0.0f;
+    int g0 = 0;   // first chunk of the current phase
+    for (int p = 0; p < 2 * L && ok; ++p) {
+        const bool fwd = p < L;
+        const int l = wide_phase_layer(L, p);
+        const int K = wide_phase_K(L, p), N = wide_phase_N(L, p);
+        const int nch = K / KCH;
+        const unsigned char* Aop = fwd ? (l == 1 ? A0 : ACT) : GA;
+        bool good = true;
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(Aop);
+            const uint32_t sbo_a = (uint32_t)(K / 8) * 128u;
+            const uint32_t idesc = make_idesc(M, N);
+            for (int c = 0; c < nch && good; ++c) {
+                const int g = g0 + c;
+                good = mbar_wait(bar_ld[g & 1], (uint32_t)((g >> 1) & 1));
+                if (!good) break;
+                fence_after();
+                const uint32_t b0 = smem_u32(WB[g & 1]);
+                for (int ks = 0; ks < KCH / 16; ++ks) {
+                    const uint64_t ad = make_desc(a0 + (uint32_t)c * 1024u + ks * 256u, 128u, sbo_a);
+                    const uint64_t bd = make_desc(b0 + ks * 256u, 128u, 1024u);
+                    mma_bf16(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                }
+                mma_commit(bar_free[g & 1]);
+                // buffer of chunk g-1 is reused for chunk g+1 once chunk g-1's MMAs are done
+                if (g >= 1 && g + 1 < NCH && issued == g + 1) {
+                    good = mbar_wait(bar_free[(g + 1) & 1], (uint32_t)(((g - 1) >> 1) & 1));
+                    if (good) {
+                        load_chunk(g + 1);
+                        issued = g + 2;
+                    }
+                }
+            }
+            if (good) mma_commit(bar_mma);
+        }
+        good = mbar_wait(bar_mma, (uint32_t)(p & 1)) && good;
+        ok = __syncthreads_and(good ? 1 : 0) != 0;
+        if (!ok) break;
+        fence_after();
+        g0 += nch;
+        const int cbeg = hsel * (N / 2), cend = cbeg + N / 2;
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)c0, v);
+            if (fwd) {
+                float h[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) h[j] = tanh_f(v[j] + b_l[(l - 1) * WW + c0 + j]);
+                if (l < L) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) pk[t] = pack_bf16(h[2 * t], h[2 * t + 1]);
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+                        *reinterpret_cast<uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, WW)) =
+                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                    if (l <= L - 2) tmem_st8(lane_base + 256u + 128u * (uint32_t)(l - 1) + (uint32_t)(c0 >> 1), pk);
+                } else {
+                    float ga[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float wo = w_out[c0 + j];
+                        y_part += wo * h[j];
+                        ga[j] = s_E * wo * (1.0f - h[j] * h[j]);
+                    }
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+                        *reinterpret_cast<uint4*>(GA + 2 * cm_index(row, c0 + 8 * g, WW)) =
+                            make_uint4(pack_bf16(ga[8 * g], ga[8 * g + 1]), pack_bf16(ga[8 * g + 2], ga[8 * g + 3]),
+                                       pack_bf16(ga[8 * g + 4], ga[8 * g + 5]), pack_bf16(ga[8 * g + 6], ga[8 * g + 7]));
+                }
+            } else if (l > 1) {
+                // h_{l-1}: h_{L-1} is still in ACT; earlier ones were parked in TMEM
+                uint32_t hw[8];
+                if (l - 1 == L - 1) {
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        const uint4 u = *reinterpret_cast<const uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, WW));
+                        hw[4 * g] = u.x; hw[4 * g + 1] = u.y; hw[4 * g + 2] = u.z; hw[4 * g + 3] = u.w;
+                    }
+                } else {
+                    tmem_ld8(lane_base + 256u + 128u * (uint32_t)(l - 2) + (uint32_t)(c0 >> 1), hw);
+                }
+                uint32_t pk[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float2 hh = unpack_bf16(hw[t]);
+                    pk[t] = pack_bf16(v[2 * t] * (1.0f - hh.x * hh.x), v[2 * t + 1] * (1.0f - hh.y * hh.y));
+                }
+#pragma unroll
+                for (int g = 0; g < 2; ++g)
+                    *reinterpret_cast<uint4*>(GA + 2 * cm_index(row, c0 + 8 * g, WW)) =
+                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+            } else {
+                const int ba = perm[row0 + row];
+                if (ba >= 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4) {
+                        float4 o = make_float4(v[j] / sigma[c0 + j], v[j + 1] / sigma[c0 + j + 1],
+                                               v[j + 2] / sigma[c0 + j + 2], v[j + 3] / sigma[c0 + j + 3]);
+                        *reinterpret_cast<float4*>(dEdG + (size_t)ba * ND + c0 + j) = o;
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        if (fwd && l == L) ysum[hsel * M + row] = y_part;
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (fwd && l == L && hsel == 0) {
+            const int ba = perm[row0 + row];
+            if (ba >= 0) Eatom[ba] = s_E * (ysum[row] + ysum[M + row] + b_out) + e_Z;
+        }
+    }
+    if (!ok) {
+        // a wait gave up: report, let started copies land, then release TMEM
+        if (tid == 0) {
+            atomicOr(&err->flags, ERR_TIMEOUT);
+            for (int g = (issued > 2 ? issued - 2 : 0); g < issued; ++g)
+                mbar_wait(bar_ld[g & 1], (uint32_t)((g >> 1) & 1));
+        }
+        __syncthreads();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static size_t tc_smem(int W, int L, bool db)
@@ -396,14 +688,24 @@ static size_t tc_smem(int W, int L, bool db)
     return A0_B + (L > 1 ? (L - 1) : 1) * H_B + H_B + (db ? 2 : 1) * WB_B + 64 + 2 * 128 * 4 + 1024;
 }
 
+static size_t tc_wide_smem()
+{
+    return (size_t)128 * ND * 2 + 2 * (size_t)128 * WW * 2 + 2 * (size_t)WW * KCH * 2 + 64 + 2 * 128 * 4 + 1024;
+}
+
 bool network_tc_supported(int width, int n_hidden)
 {
-    if (width != 64 && width != 128) return false;
     if (n_hidden < 1 || n_hidden > MAX_LAYERS) return false;
+    if (width == WW) return tc_wide_smem() <= 227 * 1024;
+    if (width != 64 && width != 128) return false;
     return tc_smem(width, n_hidden, false) <= 227 * 1024;
 }
 
-size_t tc_weight_bytes(int width, int n_hidden) { return img_offset(width, n_hidden, 2 * n_hidden); }
+size_t tc_weight_bytes(int width, int n_hidden)
+{
+    if (width == WW) return wide_chunk_offset(n_hidden, wide_nchunks(n_hidden), nullptr);
+    return img_offset(width, n_hidden, 2 * n_hidden);
+}
 
 // weight images (BF16, core-matrix layout) and FP32 epilogue vectors of one type
 void prepare_tc_weights(const Dev& d, int /*type*/, const double* blob, void* host_img, float* host_vec)
@@ -425,7 +727,26 @@ void prepare_tc_weights(const Dev& d, int /*type*/, const double* blob, void* ho
     const double* mu = blob + off; off += ND;
     const double* sigma = blob + off; off += ND;
     const double s_E = blob[off], e_Z = blob[off + 1];
-    for (int p = 0; p < 2 * L; ++p) {
+    if (W == WW) {
+        // chunked images: per phase, K-chunks of 64, each [N][64] core-matrix layout
+        int g = 0;
+        for (int p = 0; p < 2 * L; ++p) {
+            const int l = wide_phase_layer(L, p), K = wide_phase_K(L, p), N = wide_phase_N(L, p);
+            const int in = l == 1 ? ND : W;
+            const double* Wm = Wl[l - 1];   // [W][in]
+            for (int c = 0; c < K / KCH; ++c, ++g) {
+                int Nc = 0;
+                __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(img + wide_chunk_offset(L, g, &Nc));
+                for (int n = 0; n < N; ++n)
+                    for (int kk = 0; kk < KCH; ++kk) {
+                        const int k = c * KCH + kk;
+                        const double v = p < L ? Wm[(size_t)n * in + k] : Wm[(size_t)k * in + n];
+                        dst[cm_index(n, kk, KCH)] = __float2bfloat16_rn((float)v);
+                    }
+            }
+        }
+    }
+    for (int p = 0; p < 2 * L && W != WW; ++p) {
         const int l = p < L ? p + 1 : 2 * L - p;
         const int in = l == 1 ? ND : W;
         __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(img + img_offset(W, L, p));
@@ -475,9 +796,32 @@ static void run_tc(const Dev& d, cudaStream_t st)
     }
 }
 
+template <int L>
+static void run_tc_wide(const Dev& d, cudaStream_t st)
+{
+    const size_t sm = tc_wide_smem();
+    static size_t done = 0;
+    if (sm > done) {
+        cudaFuncSetAttribute(mlp_tc_wide_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        done = sm;
+    }
+    mlp_tc_wide_kernel<L><<<d.rows_pad / 128, TC_THREADS, sm, st>>>(
+        (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
+        d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err);
+}
+
 void launch_network_tc(const Dev& d, cudaStream_t st)
 {
     if (d.rows_pad == 0) return;
+    if (d.width == WW) {
+        switch (d.n_hidden) {
+            case 1: run_tc_wide<1>(d, st); break;
+            case 2: run_tc_wide<2>(d, st); break;
+            case 3: run_tc_wide<3>(d, st); break;
+            default: run_tc_wide<4>(d, st); break;
+        }
+        return;
+    }
     if (d.width == 64) {
         switch (d.n_hidden) {
             case 1: run_tc<64, 1>(d, st); break;

@@ -123,26 +123,47 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
         int* L = lst[wib];
         const int3 ci = cell_of(rp, xi);
         const int cbase = rp.cell0 + sy.bead * rp.ncells;
-        for (int s = 0; s < 27; ++s) {
-            int cx = ci.x + s / 9 - 1, cy = ci.y + (s / 3) % 3 - 1, cz = ci.z + s % 3 - 1;
+        // lane s < 27 holds stencil cell s; an inclusive scan of the counts
+        // flattens the 27 cells into one candidate list
+        int st = 0, ct = 0;
+        if (lane < 27) {
+            int cx = ci.x + (int)lane / 9 - 1, cy = ci.y + ((int)lane / 3) % 3 - 1, cz = ci.z + (int)lane % 3 - 1;
             cx += cx < 0 ? rp.nc[0] : (cx >= rp.nc[0] ? -rp.nc[0] : 0);
             cy += cy < 0 ? rp.nc[1] : (cy >= rp.nc[1] ? -rp.nc[1] : 0);
             cz += cz < 0 ? rp.nc[2] : (cz >= rp.nc[2] ? -rp.nc[2] : 0);
             const int cell = cbase + (cx * rp.nc[1] + cy) * rp.nc[2] + cz;
-            const int st = cell_start[cell], ct = cell_cnt[cell];
-            for (int t0 = 0; t0 < ct; t0 += 32) {
-                const int t = t0 + (int)lane;
-                int j = -1;
-                bool in = false;
-                if (t < ct) {
-                    j = cell_atoms[st + t];
-                    in = j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                if (in && pos < maxnb) L[pos] = j;
-                cnt += __popc(m);
+            st = cell_start[cell];
+            ct = cell_cnt[cell];
+        }
+        int incl = ct;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + (int)lane;
+            // stencil cell of candidate t: first s with incl[s] > t
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                if (v <= t) lo += step;
             }
+            const int sc = lo > 26 ? 26 : lo;
+            const int base = __shfl_sync(0xffffffffu, st, sc);
+            const int before = __shfl_sync(0xffffffffu, incl - ct, sc);
+            bool in = false;
+            int j = -1;
+            if (t < total) {
+                j = cell_atoms[base + (t - before)];
+                in = j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (in && pos < maxnb) L[pos] = j;
+            cnt += __popc(m);
         }
         __syncwarp();
         // ascending order: bitonic sort over the next power of two, padded

@@ -114,6 +114,8 @@ extern "C" int pimd_descriptors_noalloc(const double* x_dev, int n_atoms, const 
     dp.eta_R = (float)eta_R;
     for (int q = 0; q < NR; ++q) dp.r_mu[q] = (float)r_mu[q];
     for (int q = 0; q < 4; ++q) dp.eta_A[q] = (float)eta_A[q];
+    dp.eta_R_l2 = (float)(eta_R * M_LOG2E);
+    for (int q = 0; q < 4; ++q) dp.eta_A_l2[q] = (float)(eta_A[q] * M_LOG2E);
 
     Dev d;
     d.R = 1; d.S = 1; d.B = n_atoms; d.NA = n_atoms;

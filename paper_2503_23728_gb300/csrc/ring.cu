@@ -125,7 +125,8 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
                                 const double* __restrict__ cmat, const Mode* __restrict__ modes,
                                 const double* __restrict__ mass, const unsigned long long* __restrict__ stepp,
                                 double dt, int thermostat, double* __restrict__ q, double* __restrict__ p,
-                                const double* __restrict__ fnm, Vec4<Real>* __restrict__ x, double* __restrict__ Q)
+                                const double* __restrict__ fnm, Vec4<Real>* __restrict__ x,
+                                double* __restrict__ qpart)
 {
     extern __shared__ double sq[];
     __shared__ double red[32];
@@ -158,14 +159,14 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
         q[g] = qv;
         sq[le * t.P + k] = qv;
     }
-    // thermostat heat: block reduction, one atomic per block
+    // thermostat heat: block partial, summed per replica in block order later
     dK = warp_sum(dK);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dK;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        if (thermostat) atomicAdd(&Q[t.r], s * MVV2E);
+        qpart[blockIdx.x] = thermostat ? s * MVV2E : 0.0;
     }
     if (!t.active) return;
     const int j = t.kk;
@@ -181,7 +182,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
                                  const double* __restrict__ cmat, const Mode* __restrict__ modes,
                                  const double* __restrict__ mass, const unsigned long long* __restrict__ stepp,
                                  double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
-                                 double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ Q,
+                                 double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ qpart,
                                  DevErr* __restrict__ err)
 {
     extern __shared__ double sf[];
@@ -219,14 +220,32 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
     dK = warp_sum(dK);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dK;
     __syncthreads();
-    if (threadIdx.x == 0 && do_step && thermostat) {
+    if (threadIdx.x == 0 && do_step) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        atomicAdd(&Q[t.r], s * MVV2E);
+        qpart[gridDim.x + blockIdx.x] = thermostat ? s * MVV2E : 0.0;
     }
 }
 
-__global__ void bump_step_kernel(unsigned long long* step) { *step += 1ull; }
+// end of a step: thermostat heat of both O halves added per replica (one
+// block per replica, fixed-order reduction), then the step counter
+__global__ void bump_step_kernel(unsigned long long* step, double* __restrict__ Q, const double* __restrict__ qpart,
+                                 const int* __restrict__ rep_blk0, int nblk)
+{
+    __shared__ double red[8];
+    const int r = blockIdx.x;
+    double s = 0.0;
+    for (int b = rep_blk0[r] + threadIdx.x; b < rep_blk0[r + 1]; b += blockDim.x) s += qpart[b] + qpart[nblk + b];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        Q[r] += t;
+        if (r == 0) *step += 1ull;
+    }
+}
 
 static size_t rp_smem(const Dev& d) { return (size_t)d.rp_threads * sizeof(double); }
 
@@ -245,11 +264,11 @@ void launch_rp_start(const Dev& d, cudaStream_t st)
     if (d.precision == 0)
         rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.q, d.p, d.fnm, (Dbl4*)d.x,
-            d.Q);
+            d.qpart);
     else
         rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.q, d.p, d.fnm, (float4*)d.x,
-            d.Q);
+            d.qpart);
 }
 
 void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
@@ -257,14 +276,17 @@ void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
     if (d.precision == 0)
         rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, do_step ? 1 : 0,
-            (const Dbl4*)d.f, d.p, d.fnm, d.Q, d.err);
+            (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err);
     else
         rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, do_step ? 1 : 0,
-            (const float4*)d.f, d.p, d.fnm, d.Q, d.err);
+            (const float4*)d.f, d.p, d.fnm, d.qpart, d.err);
 }
 
-void launch_bump_step(const Dev& d, cudaStream_t st) { bump_step_kernel<<<1, 1, 0, st>>>(d.step); }
+void launch_bump_step(const Dev& d, cudaStream_t st)
+{
+    bump_step_kernel<<<d.R, 256, 0, st>>>(d.step, d.Q, d.qpart, d.rep_blk0, d.n_rp_blocks);
+}
 
 // ---------------------------------------------------------------------------
 // a8: estimators in normal-mode space, one block per replica (FP64).

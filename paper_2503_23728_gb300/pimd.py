@@ -23,7 +23,7 @@ POT_MODEL, POT_HARMONIC = 0, 1
 EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_weights", "pimd_step",
            "pimd_energy_forces", "pimd_descriptors", "pimd_estimators", "pimd_get_state", "pimd_set_state",
            "pimd_get_forces", "pimd_get_neighbours", "pimd_sync", "pimd_sizes", "pimd_destroy", "pimd_last_error",
-           "pimd_stage_times", "pimd_kernels_per_step"]
+           "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule"]
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
 
@@ -38,7 +38,7 @@ class pimd_config(ct.Structure):
                 ("cutoff_A", ct.c_double), ("precision", ct.c_int), ("thermostat", ct.c_int),
                 ("potential", ct.c_int), ("max_neighbours", ct.c_int), ("omega_harm", ct.c_double),
                 ("n_hidden", ct.c_int), ("widths", ct.c_int * 4), ("stream", ct.c_void_p), ("timing", ct.c_int),
-                ("nbr_algo", ct.c_int)]
+                ("nbr_algo", ct.c_int), ("deterministic", ct.c_int)]
 
 
 class pimd_replica_desc(ct.Structure):
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.pimd_stage_times.argtypes = [vp, ct.POINTER(ct.c_float)]
     L.pimd_kernels_per_step.argtypes = [vp]
     L.pimd_kernels_per_step.restype = ct.c_int
+    L.pimd_tune.argtypes = [vp, ct.c_int, dp]
+    L.pimd_set_schedule.argtypes = [vp, ct.c_int]
     L.pimd_descriptors_noalloc.argtypes = [vp, ct.c_int, dp, ct.c_double, ct.c_double, dp, dp, vp, vp]
     _lib = L
     return L
@@ -196,6 +198,16 @@ def pimd_stage_times(ctx) -> dict:
     return {k: float(v) for k, v in zip(STAGES, ms)}
 
 
+def pimd_tune(ctx, reps: int = 3) -> dict:
+    out = np.zeros(3)
+    _check(load().pimd_tune(ctx, int(reps), _dp(out)), ctx)
+    return {"best_ms": float(out[0]), "band_length": int(out[1]), "default_ms": float(out[2])}
+
+
+def pimd_set_schedule(ctx, band_length: int):
+    _check(load().pimd_set_schedule(ctx, int(band_length)), ctx)
+
+
 def pimd_kernels_per_step(ctx) -> int:
     return int(load().pimd_kernels_per_step(ctx))
 
@@ -234,7 +246,7 @@ def pimd_last_error(ctx=None) -> str:
 # ---------------------------------------------------------------- helpers
 def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128, 128, 128), pile_lambda=1.0,
                 thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128, stream=None,
-                timing=False, nbr_algo=0) -> pimd_config:
+                timing=False, nbr_algo=0, deterministic=False) -> pimd_config:
     c = pimd_config()
     c.dt_fs = dt_fs
     c.gamma0_per_fs = gamma0_per_fs
@@ -251,6 +263,7 @@ def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128,
     c.stream = stream
     c.timing = 1 if timing else 0
     c.nbr_algo = int(nbr_algo)
+    c.deterministic = 1 if deterministic else 0
     return c
 
 
@@ -314,7 +327,7 @@ class Context:
 
     def __init__(self, replicas, dt_fs, gamma0_per_fs, precision="fp32", widths=(128, 128, 128), cutoff=6.0,
                  pile_lambda=1.0, thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128,
-                 masses=None, stream=None, timing=False, nbr_algo=0):
+                 masses=None, stream=None, timing=False, nbr_algo=0, deterministic=False):
         import torch
         self.torch = torch
         self.keep = _Keep()
@@ -323,7 +336,8 @@ class Context:
             stream = torch.cuda.current_stream()
         self.stream = stream
         self.cfg = make_config(dt_fs, gamma0_per_fs, precision, cutoff, widths, pile_lambda, thermostat, potential,
-                               omega, max_neighbours, ct.c_void_p(stream.cuda_stream), timing, nbr_algo)
+                               omega, max_neighbours, ct.c_void_p(stream.cuda_stream), timing, nbr_algo,
+                               deterministic)
         self.reps = make_replicas(self.replicas, self.keep, masses)
         self.ws_bytes = pimd_workspace_size(self.cfg, self.reps)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -397,6 +411,12 @@ class Context:
 
     def kernels_per_step(self) -> int:
         return pimd_kernels_per_step(self.h)
+
+    def tune(self, reps: int = 3) -> dict:
+        return pimd_tune(self.h, reps)
+
+    def set_schedule(self, band_length: int):
+        pimd_set_schedule(self.h, band_length)
 
 
 def _autograd_function():

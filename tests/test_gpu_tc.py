@@ -80,7 +80,8 @@ def test_bf16_small_network_and_ragged_tiles():
         s0 += r.n_beads
 
 
-@pytest.mark.parametrize("widths", [(128,), (128, 128), (64, 64, 64, 64)])
+@pytest.mark.parametrize("widths", [(128,), (128, 128), (64, 64, 64, 64), (256,), (256, 256, 256),
+                                    (256, 256, 256, 256)])
 def test_bf16_network_depths(widths):
     P = _P()
     w = s.workload("water64")
