@@ -240,16 +240,16 @@ int pimd_stage_times(pimd_ctx* ctx, float* ms);
 
 /* Autotuner. Times the descriptor + adjoint kernels on the context's current
  * configuration for each candidate pair schedule (band length 4..16 with the
- * shuffle-carry schedule, or the flat pair walk) and keeps the fastest; the
+ * shuffle-carry schedule, or ordered pairs) and keeps the fastest; the
  * per-step graphs are re-recorded at the next pimd_step. reps: timed
  * repetitions per candidate (>= 1). out_ms: host [3] or NULL -> best time
- * (ms, descriptors + adjoint), chosen band length (0 = flat walk), time of
- * the default schedule. Synchronises. Errors: STATE before weights are set. */
+ * (ms, descriptors + adjoint), chosen band length (0 = ordered pairs), time
+ * of the default schedule. Synchronises. Errors: STATE before weights set.  */
 int pimd_tune(pimd_ctx* ctx, int reps, double* out_ms);
 
-/* Set the pair schedule directly: band_length 4..16 (shuffle-carry bands for
- * atoms with >= band_length + 32 neighbours, flat walk below), or 0 for the
- * flat walk everywhere. Errors: INVALID_ARG for other lengths.              */
+/* Set the pair schedule directly: band_length 1..16 (shuffle-carry bands for
+ * atoms with >= band_length + 32 neighbours, ordered pairs below), or 0 for
+ * ordered pairs everywhere. Errors: INVALID_ARG for other lengths.          */
 int pimd_set_schedule(pimd_ctx* ctx, int band_length);
 
 /* Number of kernels one step launches (memset nodes not counted).          */

@@ -518,6 +518,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     Dev& d = c->d;
     unsigned char* w = c->ws;
     d.R = b.R; d.S = b.S; d.B = b.B; d.NA = b.NA;
+    for (const Rep& rp : b.reps) d.max_N = std::max(d.max_N, rp.N);
     d.maxnb = cfg->max_neighbours == 0 ? 128 : cfg->max_neighbours;
     d.precision = cfg->precision;
     d.periodic_any = b.periodic_any;
@@ -772,12 +773,12 @@ int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
         if (e0) cudaEventDestroy(e0);
         return cuda_check(c, cudaErrorUnknown, "cudaEventCreate");
     }
-    const Sched defaults = {8, 40};
+    const Sched defaults = {8, 40, 0};
     Sched cands[8];
     int nc = 0;
     const int rl[6] = {4, 6, 8, 10, 12, 16};
-    for (int q = 0; q < 6; ++q) cands[nc++] = Sched{rl[q], rl[q] + 32};
-    cands[nc++] = Sched{8, 1 << 30};   // flat pair walk for every atom
+    for (int q = 0; q < 6; ++q) cands[nc++] = Sched{rl[q], rl[q] + 32, 0};
+    cands[nc++] = Sched{8, 1 << 30, 0};   // ordered pairs for every atom
     double best = 1e30, t_default = 0.0;
     Sched pick = defaults;
     for (int q = 0; q < nc && !rc; ++q) {
@@ -821,7 +822,7 @@ int pimd_set_schedule(pimd_ctx* c, int band_length)
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
     if (band_length != 0 && (band_length < 1 || band_length > 16))
         return fail(c, PIMD_ERR_INVALID_ARG, "band_length must be 0 or 1..16");
-    c->d.sched = band_length == 0 ? Sched{8, 1 << 30} : Sched{band_length, band_length + 32};
+    c->d.sched = band_length == 0 ? Sched{8, 1 << 30, 0} : Sched{band_length, band_length + 32, 0};
     if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
     if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
     c->forces_valid = false;

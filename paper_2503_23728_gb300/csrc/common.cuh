@@ -69,8 +69,10 @@ struct Mode {
 
 // pair schedule of the descriptor / adjoint kernels (chosen by the tuner)
 struct Sched {
-    int rmax;       // band length cap (<= 16)
-    int band_min;   // neighbours needed for the band schedule (>= rmax + 32)
+    int rmax;            // band length cap (<= 16)
+    int band_min;        // neighbours needed for the band schedule (>= rmax + 32)
+    int small_atomics;   // below band_min: 1 = flat walk with shared atomics,
+                         // 0 = ordered pairs (each pair twice, no atomics)
 };
 
 // symmetry-function parameters in the working precision

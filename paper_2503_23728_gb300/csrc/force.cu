@@ -504,24 +504,14 @@ __device__ __forceinline__ void adj_pair(const AdjCoef<float>& cf, const float4&
     const float2 X4 = __fmul2_rn(X2, X2);
     const float2 X7 = __fmul2_rn(X4, X3);
     const float2 X8 = __fmul2_rn(X4, X4);
-    // H_z = (sum_e g'_(z,+,e) B_e, sum_e g'_(z,-,e) B_e)
-    float2 Bb[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) Bb[e] = make_float2(Bv[e], Bv[e]);
-    float2 H[4];
-#pragma unroll
-    for (int z = 0; z < 4; ++z) {
-        H[z] = __fmul2_rn(cf.g[z * 4], Bb[0]);
-#pragma unroll
-        for (int e = 1; e < 4; ++e) H[z] = __ffma2_rn(cf.g[z * 4 + e], Bb[e], H[z]);
-    }
-    // dE/dc = sum_z zeta (xp^(zeta-1) H_(z,+) - xm^(zeta-1) H_(z,-))
-    float2 T = __ffma2_rn(__fmul2_rn(X1, make_float2(2.0f, 2.0f)), H[1], H[0]);
-    T = __ffma2_rn(__fmul2_rn(X3, make_float2(4.0f, 4.0f)), H[2], T);
-    T = __ffma2_rn(__fmul2_rn(X7, make_float2(8.0f, 8.0f)), H[3], T);
-    const float dEdc = T.x - T.y;
-    // K_e = sum_z (g'_(z,+,e) xp^zeta + g'_(z,-,e) xm^zeta)
+    // per eta channel e, with D_zeta = zeta X_(zeta-1) (the c-derivative of X_zeta):
+    //   K_e = sum_z (g'_(z,+,e) xp^zeta + g'_(z,-,e) xm^zeta)
+    //   M_e = sum_z zeta (g'_(z,+,e) xp^(zeta-1) - g'_(z,-,e) xm^(zeta-1)),  dE/dc = sum_e B_e M_e
+    const float2 D2 = __fmul2_rn(X1, make_float2(2.0f, 2.0f));
+    const float2 D4 = __fmul2_rn(X3, make_float2(4.0f, 4.0f));
+    const float2 D8 = __fmul2_rn(X7, make_float2(8.0f, 8.0f));
     float K[4];
+    float dEdc = 0.0f;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         float2 k2 = __fmul2_rn(cf.g[e], X1);
@@ -529,6 +519,10 @@ __device__ __forceinline__ void adj_pair(const AdjCoef<float>& cf, const float4&
         k2 = __ffma2_rn(cf.g[8 + e], X4, k2);
         k2 = __ffma2_rn(cf.g[12 + e], X8, k2);
         K[e] = k2.x + k2.y;
+        float2 m2 = __ffma2_rn(cf.g[4 + e], D2, cf.g[e]);
+        m2 = __ffma2_rn(cf.g[8 + e], D4, m2);
+        m2 = __ffma2_rn(cf.g[12 + e], D8, m2);
+        dEdc = fmaf(Bv[e], m2.x - m2.y, dEdc);
     }
     jd[0] += K[0] * ak.x; jd[1] += K[1] * ak.y; jd[2] += K[2] * ak.z; jd[3] += K[3] * ak.w;
     kd[0] += K[0] * aj.x; kd[1] += K[1] * aj.y; kd[2] += K[2] * aj.z; kd[3] += K[3] * aj.w;
@@ -695,9 +689,10 @@ __global__ void __launch_bounds__(256) desc_adj_kernel(
                 __syncwarp();
             }
         }
-    } else if (det) {
+    } else if (det || !sc.small_atomics) {
         // ordered pairs, j-side sums only: every unordered pair is evaluated
-        // twice, and each lane owns its j's accumulators (fixed order)
+        // twice, and each lane owns its j's accumulators (fixed order, no
+        // atomics; shared-memory float atomics cost ~4x more per pair)
         for (int j0 = 0; j0 < n; j0 += 32) {
             const int j = j0 + (int)lane;
             if (j < n) {
@@ -1127,12 +1122,15 @@ __global__ void __launch_bounds__(256) energy_reduce_kernel(const Real* __restri
 
 void launch_energy_reduce(const Dev& d, cudaStream_t st)
 {
+    // block size sized to the largest bead (small systems: one warp per bead)
+    int t = 32;
+    while (t < 256 && t < d.max_N) t <<= 1;
     if (d.precision == 0)
-        energy_reduce_kernel<double><<<d.S, 256, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
-                                                          d.V, d.W);
+        energy_reduce_kernel<double><<<d.S, t, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
+                                                        d.V, d.W);
     else
-        energy_reduce_kernel<float><<<d.S, 256, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
-                                                         d.V, d.W);
+        energy_reduce_kernel<float><<<d.S, t, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
+                                                       d.V, d.W);
 }
 
 // ---------------------------------------------------------------------------

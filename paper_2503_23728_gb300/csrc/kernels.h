@@ -14,6 +14,7 @@ namespace pimd {
 // Device pointers and sizes of one context (all inside the caller's workspace).
 struct Dev {
     int R = 0, S = 0, B = 0, NA = 0;   // replicas, bead-systems, bead-atoms, atoms
+    int max_N = 0;                     // largest replica
     int maxnb = 128;
     int precision = 1;                 // 0 FP64, 1 FP32, 2 BF16 tensor cores
     bool periodic_any = false;
@@ -69,7 +70,7 @@ struct Dev {
     float* wtc_vec = nullptr;          // FP32 vectors for the tensor-core epilogues
     size_t wtc_vec_per_type = 0;
 
-    Sched sched = {8, 40};             // pair schedule (band length 8, bands for n >= 40)
+    Sched sched = {8, 40, 0};          // pair schedule (band length 8, bands for n >= 40)
 
     // integrator
     double dt = 0.5, gamma0 = 0.0, lambda = 1.0;

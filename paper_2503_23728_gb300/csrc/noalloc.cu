@@ -119,6 +119,7 @@ extern "C" int pimd_descriptors_noalloc(const double* x_dev, int n_atoms, const 
 
     Dev d;
     d.R = 1; d.S = 1; d.B = n_atoms; d.NA = n_atoms;
+    d.max_N = n_atoms;
     d.maxnb = MAXNB;
     d.precision = PIMD_FP32;
     d.rc = cutoff_A;
