@@ -31,9 +31,17 @@ if ROOT not in sys.path:
 METRIC = "bead-atom force evals/sec & ns/day, ice P=32: BF16-TC fused vs plain FP32 GPU"
 UNIT = "bead-atom force evals/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12    # SMs x FP32 lanes x 2 flop x max SM clock
-# algorithmic FP32 flops of the adjoint (forces + virial) per unit
+# algorithmic FP32 flops of the adjoint (forces + virial) per unit.
+# Pair sums: per unordered neighbour pair, plus per neighbour (radial terms,
+# weights, chain rule, scatter).
 ADJ_FLOP_PER_PAIR = 205
 ADJ_FLOP_PER_NBR = 380
+# Moment tensors: per neighbour the nested Horner evaluation of the 4 degree-8
+# polynomials and their gradient (1340 FMA: 480 + 336 in x, 400 in y, 124 in
+# z) on top of the per-neighbour work above; per bead-atom Q = dE/dM (165
+# monomials x (16 FMA + 4 mul)).
+MOM_ADJ_FLOP_PER_NBR = 380 + 2 * 1340
+MOM_ADJ_FLOP_PER_ATOM = 165 * 36
 
 
 def args():
@@ -173,6 +181,8 @@ def timed_steps(a, ctx, stream, flush, barrier):
 def adjoint_flops(ctx) -> float:
     nnb, _ = ctx.neighbours()
     n = nnb.astype(np.float64)
+    if ctx.angular == "moments":
+        return float(np.sum(MOM_ADJ_FLOP_PER_NBR * n + MOM_ADJ_FLOP_PER_ATOM))
     return float(np.sum(ADJ_FLOP_PER_PAIR * n * (n - 1) / 2 + ADJ_FLOP_PER_NBR * n))
 
 
@@ -347,7 +357,9 @@ def main():
         "stages_ms": st_mean,
         "fp32_plain": fp32,
         "speedup_vs_fp32_plain": (value / fp32["value"]) if fp32 else None,
-        "roofline": {"bound": "alu", "kernel": "desc_adj_kernel (angular+radial adjoint, forces, virial)",
+        "angular": ctx.angular,
+        "roofline": {"bound": "alu", "kernel": ("desc_mom_adj_kernel" if ctx.angular == "moments" else
+                                                "desc_adj_kernel") + " (angular+radial adjoint, forces, virial)",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "flops_per_launch": adj_flops,

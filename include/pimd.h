@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define PIMD_ABI_VERSION 1
+#define PIMD_ABI_VERSION 2
 #define PIMD_N_RADIAL 32
 #define PIMD_N_ANGULAR 32
 #define PIMD_N_DESC 64
@@ -71,6 +71,30 @@ typedef enum {
     PIMD_BF16_TC = 2   /* FP32 descriptors/adjoint, BF16 network on tcgen05 tensor
                           cores with FP32 accumulation in tensor memory            */
 } pimd_precision;
+
+/* how the angular symmetry functions and their adjoint are evaluated */
+typedef enum {
+    PIMD_ANG_PAIRS = 0,   /* sums over the unordered neighbour pairs, O(n^2) per atom */
+    PIMD_ANG_MOMENTS = 1  /* moment tensors of degree <= 8, O(n) per atom (FP32 and
+                             BF16 precision; same values up to rounding)           */
+} pimd_angular;
+
+/* order of the sub-steps of one time step dt (O: PILE-L thermostat, B: force
+ * kick, A: free ring-polymer evolution, all in normal-mode space) */
+typedef enum {
+    PIMD_OBABO = 0,   /* O(dt/2) B(dt/2) A(dt) [forces] B(dt/2) O(dt/2); noise
+                         streams 2 and 3                                       */
+    PIMD_BAOAB = 1    /* B(dt/2) A(dt/2) O(dt) A(dt/2) [forces] B(dt/2); noise
+                         stream 2                                              */
+} pimd_splitting;
+
+/* free ring-polymer step of each internal mode k over a time h */
+typedef enum {
+    PIMD_FREE_RP_EXACT = 0,   /* exp(h L_k): rotation by omega_k h            */
+    PIMD_FREE_RP_CAYLEY = 1   /* Cayley transform (1 - h L_k/2)^-1 (1 + h L_k/2):
+                                 rotation by 2 atan(omega_k h / 2), stable for
+                                 any omega_k h                                 */
+} pimd_free_rp;
 
 typedef enum {
     PIMD_POT_MODEL = 0,     /* symmetry-function network (set by pimd_set_weights)  */
@@ -104,6 +128,8 @@ typedef struct {
                                 runs are bit-identical. Costs B*max_neighbours
                                 records of workspace and one more kernel.
                                 0: atomic force accumulation (faster).           */
+    int splitting;           /* pimd_splitting: order of the step's sub-steps    */
+    int free_rp;             /* pimd_free_rp: free ring-polymer propagator       */
 } pimd_config;
 
 /* stages of one step, in launch order (pimd_stage_times) */
@@ -239,18 +265,31 @@ int pimd_get_neighbours(pimd_ctx* ctx, int* nnb_host, int* nbr_host);
 int pimd_stage_times(pimd_ctx* ctx, float* ms);
 
 /* Autotuner. Times the descriptor + adjoint kernels on the context's current
- * configuration for each candidate pair schedule (band length 4..16 with the
- * shuffle-carry schedule, or ordered pairs) and keeps the fastest; the
- * per-step graphs are re-recorded at the next pimd_step. reps: timed
- * repetitions per candidate (>= 1). out_ms: host [3] or NULL -> best time
- * (ms, descriptors + adjoint), chosen band length (0 = ordered pairs), time
- * of the default schedule. Synchronises. Errors: STATE before weights set.  */
+ * configuration for each candidate (pair sums with band length 4..16 of the
+ * shuffle-carry schedule, ordered pairs, and -- in FP32 / BF16 precision --
+ * moment tensors) and keeps the fastest; the per-step graphs are re-recorded
+ * at the next pimd_step. reps: timed repetitions per candidate (>= 1).
+ * out_ms: host [3] or NULL -> best time (ms, descriptors + adjoint), the
+ * choice (band length, 0 = ordered pairs, -1 = moment tensors), time of the
+ * schedule in force before the call. Synchronises. Errors: STATE before
+ * weights set.                                                              */
 int pimd_tune(pimd_ctx* ctx, int reps, double* out_ms);
 
 /* Set the pair schedule directly: band_length 1..16 (shuffle-carry bands for
  * atoms with >= band_length + 32 neighbours, ordered pairs below), or 0 for
  * ordered pairs everywhere. Errors: INVALID_ARG for other lengths.          */
 int pimd_set_schedule(pimd_ctx* ctx, int band_length);
+
+/* Choose how the angular terms are evaluated (pimd_angular). The default is
+ * PIMD_ANG_MOMENTS in FP32 / BF16 precision when the mean neighbour count
+ * estimated from the replicas' densities is >= 24, else PIMD_ANG_PAIRS; the
+ * pair schedule of pimd_set_schedule applies to PIMD_ANG_PAIRS only.
+ * Errors: INVALID_ARG (unknown algo), UNSUPPORTED (moments in FP64 or
+ * without the model potential).                                             */
+int pimd_set_angular(pimd_ctx* ctx, int algo);
+
+/* The angular evaluation in force (pimd_angular), -1 for a NULL ctx.       */
+int pimd_get_angular(const pimd_ctx* ctx);
 
 /* Number of kernels one step launches (memset nodes not counted).          */
 int pimd_kernels_per_step(const pimd_ctx* ctx);

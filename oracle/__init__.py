@@ -58,6 +58,8 @@ class OrSys(ct.Structure):
         ("potential", ct.c_int),
         ("omega_harm", ct.c_double),
         ("maxnb", ct.c_int),
+        ("splitting", ct.c_int),
+        ("free_rp", ct.c_int),
     ]
 
 
@@ -98,6 +100,8 @@ def lib():
                               dp, dp, dp, dp, dp, dp]
         L.or_estimators.argtypes = [ct.POINTER(OrSys), dp, dp, dp, dp, dp, ct.c_double, ct.POINTER(OrEst)]
         L.or_set_threads.argtypes = [ct.c_int]
+        L.or_free_rp_step.argtypes = [ct.c_int, ct.c_double, ct.c_double, ct.c_double,
+                                      ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.or_get_threads.restype = ct.c_int
         _lib = L
     return _lib
@@ -232,6 +236,14 @@ def nm_freqs(P: int, omega_P: float) -> np.ndarray:
     return w
 
 
+def free_rp_step(free_rp: str, m: float, w: float, h: float, p: float, q: float) -> tuple:
+    """One free ring-polymer step of one mode: (p, q) after time h."""
+    pp, qq = ct.c_double(p), ct.c_double(q)
+    lib().or_free_rp_step({"exact": 0, "cayley": 1}[free_rp], float(m), float(w), float(h), ct.byref(pp),
+                          ct.byref(qq))
+    return pp.value, qq.value
+
+
 def philox(ctr, key) -> tuple:
     c = (ct.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
     k = (ct.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
@@ -252,7 +264,8 @@ class System:
 
     def __init__(self, replica, masses: dict, dt: float, gamma0: float, pile_lambda: float = 1.0,
                  model=None, thermostat: bool = True, potential: str = "model", omega: float = 0.0,
-                 replica_index: int = 0, maxnb: int = 256):
+                 replica_index: int = 0, maxnb: int = 256, splitting: str = "obabo",
+                 free_rp: str = "exact"):
         self.mh = None if model is None else (model if isinstance(model, ModelHandle) else ModelHandle(model))
         self.Z = np.ascontiguousarray(replica.Z, dtype=np.int32)
         self.mass = _f64([masses[int(z)] for z in replica.Z])
@@ -273,6 +286,8 @@ class System:
         s.potential = 1 if potential == "harmonic" else 0
         s.omega_harm = float(omega)
         s.maxnb = int(maxnb)
+        s.splitting = {"obabo": 0, "baoab": 1}[splitting]
+        s.free_rp = {"exact": 0, "cayley": 1}[free_rp]
         self.s = s
         self.N, self.P = N, P
         self.q = np.zeros((P, N, 3))

@@ -491,16 +491,16 @@ int or_forces(const or_sys* s, const or_model* m, const double* q_nm,
     return rc;
 }
 
-/* O: p <- c1 p + sqrt(m k_B T_P) c2 xi over time dt/2 (PILE-L friction
+/* O: p <- c1 p + sqrt(m k_B T_P) c2 xi over time h (PILE-L friction
  * gamma_0 on the centroid, 2 lambda omega_k on internal modes) */
-static void step_O(const or_sys* s, const double* wk, uint32_t step, uint32_t stream,
+static void step_O(const or_sys* s, const double* wk, double h, uint32_t step, uint32_t stream,
                    double* p_nm, double* Q)
 {
     int N = s->N, P = s->P;
     double kT = kT_P_md(s), dq = 0.0;
     for (int k = 0; k < P; ++k) {
         double gam = (k == 0) ? s->gamma0 : 2.0 * s->pile_lambda * wk[k];
-        double c1 = exp(-0.5 * s->dt * gam);
+        double c1 = exp(-h * gam);
         double c2 = sqrt(1.0 - c1 * c1);
         for (int i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
@@ -527,28 +527,47 @@ static void step_B(const or_sys* s, const double* C, const double* f, double* p_
             }
 }
 
-/* A: exact free ring-polymer evolution of each normal mode over dt */
-static void step_A(const or_sys* s, const double* wk, double* q_nm, double* p_nm)
+/* A: free ring-polymer evolution of each normal mode over time h. Mode k
+ * obeys d/dt (p, q) = L (p, q) with L = [[0, -m w_k^2], [1/m, 0]].
+ * exact:  (p, q) <- exp(h L) (p, q);
+ * Cayley: (p, q) <- (I - h L / 2)^-1 (I + h L / 2) (p, q), the Cayley
+ *         transform of h L (stable for any w_k h). The centroid (w_0 = 0)
+ *         drifts freely either way. */
+void or_free_rp_step(int free_rp, double m, double w, double h, double* p, double* q)
+{
+    double p0 = *p, q0 = *q;
+    if (w == 0.0) {
+        *q = q0 + p0 * h / m;
+    } else if (free_rp == 1) {
+        /* M+ = I + h L / 2, M- = I - h L / 2, inverse of M- by the 2x2 rule */
+        double ap[2][2] = {{1.0, -0.5 * h * m * w * w}, {0.5 * h / m, 1.0}};
+        double am[2][2] = {{1.0, 0.5 * h * m * w * w}, {-0.5 * h / m, 1.0}};
+        double det = am[0][0] * am[1][1] - am[0][1] * am[1][0];
+        double inv[2][2] = {{am[1][1] / det, -am[0][1] / det}, {-am[1][0] / det, am[0][0] / det}};
+        double u0 = ap[0][0] * p0 + ap[0][1] * q0, u1 = ap[1][0] * p0 + ap[1][1] * q0;
+        *p = inv[0][0] * u0 + inv[0][1] * u1;
+        *q = inv[1][0] * u0 + inv[1][1] * u1;
+    } else {
+        double cw = cos(w * h), sw = sin(w * h);
+        *p = cw * p0 - m * w * sw * q0;
+        *q = sw / (m * w) * p0 + cw * q0;
+    }
+}
+
+static void step_A(const or_sys* s, const double* wk, double h, double* q_nm, double* p_nm)
 {
     int N = s->N, P = s->P;
-    double dt = s->dt;
     for (int k = 0; k < P; ++k)
         for (int i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
                 size_t g = ((size_t)k * N + i) * 3 + d;
-                double m = s->mass[i], p = p_nm[g], q = q_nm[g];
-                if (k == 0) {
-                    q_nm[g] = q + p * dt / m;
-                } else {
-                    double w = wk[k], cw = cos(w * dt), sw = sin(w * dt);
-                    p_nm[g] = cw * p - m * w * sw * q;
-                    q_nm[g] = sw / (m * w) * p + cw * q;
-                }
+                or_free_rp_step(s->free_rp, s->mass[i], k == 0 ? 0.0 : wk[k], h, &p_nm[g], &q_nm[g]);
             }
 }
 
-/* one step = O(dt/2) B(dt/2) A(dt) [forces] B(dt/2) O(dt/2); the noise of
- * step n uses counter step n, streams 2 (first O) and 3 (second O) */
+/* one step, OBABO: O(dt/2) B(dt/2) A(dt) [forces] B(dt/2) O(dt/2), the noise
+ * of step n with counter step n, streams 2 (first O) and 3 (second O);
+ * BAOAB: B(dt/2) A(dt/2) O(dt) A(dt/2) [forces] B(dt/2), noise stream 2 */
 int or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
             double* q_nm, double* p_nm, double* f, double* V, double* W, double* Q_thermo)
 {
@@ -561,13 +580,20 @@ int or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
     int rc = 0;
     for (int n = 0; n < nsteps; ++n) {
         uint32_t st = (uint32_t)(*step);
-        if (s->thermostat) step_O(s, wk, st, 2u, p_nm, Q_thermo);
-        step_B(s, C, f, p_nm);
-        step_A(s, wk, q_nm, p_nm);
+        if (s->splitting == 1) {
+            step_B(s, C, f, p_nm);
+            step_A(s, wk, 0.5 * s->dt, q_nm, p_nm);
+            if (s->thermostat) step_O(s, wk, s->dt, st, 2u, p_nm, Q_thermo);
+            step_A(s, wk, 0.5 * s->dt, q_nm, p_nm);
+        } else {
+            if (s->thermostat) step_O(s, wk, 0.5 * s->dt, st, 2u, p_nm, Q_thermo);
+            step_B(s, C, f, p_nm);
+            step_A(s, wk, s->dt, q_nm, p_nm);
+        }
         rc = or_forces(s, m, q_nm, xb, f, V, W);
         if (rc < 0) break;
         step_B(s, C, f, p_nm);
-        if (s->thermostat) step_O(s, wk, st, 3u, p_nm, Q_thermo);
+        if (s->thermostat && s->splitting != 1) step_O(s, wk, 0.5 * s->dt, st, 3u, p_nm, Q_thermo);
         *step += 1;
     }
     free(C); free(wk); free(xb);

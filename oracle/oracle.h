@@ -59,6 +59,8 @@ typedef struct {
     int potential;           /* 0 = network, 1 = harmonic 0.5 m w^2 |x|^2    */
     double omega_harm;       /* 1/fs                                         */
     int maxnb;               /* neighbour slots per atom                     */
+    int splitting;           /* 0 = OBABO, 1 = BAOAB                         */
+    int free_rp;             /* free ring-polymer step: 0 = exact, 1 = Cayley */
 } or_sys;
 
 /* estimator record, all eV except T_kin (K) */
@@ -86,6 +88,9 @@ void or_nm_freqs(int P, double omega_P, double* wk);
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_normal(uint64_t seed, uint32_t index, uint32_t step, uint32_t replica, uint32_t stream);
 int  or_init(const or_sys* s, const double* x0, double* q_nm, double* p_nm);
+/* one free ring-polymer step of a single mode (w = 0: free drift) over time
+ * h; free_rp 0 = exact, 1 = Cayley; p in amu A/fs, q in A                  */
+void or_free_rp_step(int free_rp, double m, double w, double h, double* p, double* q);
 int  or_forces(const or_sys* s, const or_model* m, const double* q_nm,
                double* xb, double* f, double* V, double* W);
 int  or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,

@@ -57,6 +57,7 @@ struct Build {
     int R = 0, S = 0, B = 0, NA = 0, rows_pad = 0;
     size_t blob = 0, wtc_bytes = 0, wtc_vec = 0;
     bool periodic_any = false;
+    double nb_est = 0.0;   // mean neighbour count per bead-atom (estimate from density)
 };
 
 struct Carve {
@@ -73,7 +74,7 @@ struct Carve {
 struct Offsets {
     size_t reps, bsys, ba_sys, mass, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
-        fnm, Q, qpart, rep_blk0, wbuf, vbuf, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
+        fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
 };
 
 int check_config(const pimd_config* cfg, std::string& e)
@@ -83,6 +84,8 @@ int check_config(const pimd_config* cfg, std::string& e)
     if (cfg->precision < 0 || cfg->precision > 2) { e = "unknown precision"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat != 0 && cfg->thermostat != 1) { e = "thermostat must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->nbr_algo < 0 || cfg->nbr_algo > 2) { e = "nbr_algo must be 0, 1 or 2"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->splitting != PIMD_OBABO && cfg->splitting != PIMD_BAOAB) { e = "splitting must be PIMD_OBABO or PIMD_BAOAB"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->free_rp != PIMD_FREE_RP_EXACT && cfg->free_rp != PIMD_FREE_RP_CAYLEY) { e = "free_rp must be PIMD_FREE_RP_EXACT or PIMD_FREE_RP_CAYLEY"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->deterministic != 0 && cfg->deterministic != 1) { e = "deterministic must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->potential != PIMD_POT_MODEL && cfg->potential != PIMD_POT_HARMONIC) { e = "unknown potential"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat == 1 && !(cfg->gamma0_per_fs >= 0.0)) { e = "gamma0_per_fs must be >= 0"; return PIMD_ERR_INVALID_ARG; }
@@ -216,15 +219,34 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
             }
         }
         b.reps.push_back(rp);
+        {
+            double est = h.N - 1.0;
+            if (rp.periodic)
+                est = std::min(est, h.N / (h.box[0] * h.box[1] * h.box[2]) * 4.0 / 3.0 * M_PI * cfg->cutoff_A *
+                                        cfg->cutoff_A * cfg->cutoff_A);
+            b.nb_est += est * h.N * h.P;
+        }
         const double wP = h.P * KB * h.T / HBAR;
+        // durations of the A and O sub-steps: OBABO A(dt) O(dt/2), BAOAB A(dt/2) O(dt)
+        const double hA = cfg->splitting == PIMD_BAOAB ? 0.5 * cfg->dt_fs : cfg->dt_fs;
+        const double hO = cfg->splitting == PIMD_BAOAB ? cfg->dt_fs : 0.5 * cfg->dt_fs;
         for (int k = 0; k < h.P; ++k) {
             Mode md;
             std::memset(&md, 0, sizeof(md));
             md.w = 2.0 * wP * std::sin(k * M_PI / h.P);
-            md.cw = std::cos(md.w * cfg->dt_fs);
-            md.sw = std::sin(md.w * cfg->dt_fs);
+            if (cfg->free_rp == PIMD_FREE_RP_CAYLEY) {
+                // Cayley transform of hA L_k: a rotation of the scaled phase
+                // plane with cos = (1 - a) / (1 + a), sin = w hA / (1 + a),
+                // a = (w hA / 2)^2
+                const double a = 0.25 * md.w * md.w * hA * hA;
+                md.cw = (1.0 - a) / (1.0 + a);
+                md.sw = md.w * hA / (1.0 + a);
+            } else {
+                md.cw = std::cos(md.w * hA);
+                md.sw = std::sin(md.w * hA);
+            }
             const double gam = (k == 0) ? cfg->gamma0_per_fs : 2.0 * cfg->pile_lambda * md.w;
-            md.c1 = std::exp(-0.5 * cfg->dt_fs * gam);
+            md.c1 = std::exp(-hO * gam);
             md.c2 = std::sqrt(1.0 - md.c1 * md.c1);
             b.modes.push_back(md);
         }
@@ -245,6 +267,7 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         ba0 += h.N * h.P; bs0 += h.P; atom0 += h.N; mode0 += h.P;
     }
     b.rep_blk0.push_back((int)b.rp_blocks.size());
+    b.nb_est /= std::max(1, b.B);
     // network rows grouped by element type, each group padded to 128 rows
     if (cfg->potential == PIMD_POT_MODEL) {
         std::vector<std::vector<int>> rows(zs.size());
@@ -308,6 +331,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.rep_blk0 = c.take(sizeof(int) * b.rep_blk0.size());
     o.wbuf = c.take(rs * 9 * (size_t)b.B);
     o.vbuf = c.take(cfg->deterministic && model ? v4 * (size_t)b.B * mnb : 0);
+    o.mom = c.take(model && cfg->precision != PIMD_FP64 ? sizeof(float4) * moment_elems_per_atom() * (size_t)b.B : 0);
     o.step = c.take(sizeof(unsigned long long));
     o.err = c.take(sizeof(DevErr));
     o.est = c.take(sizeof(double) * EST_STRIDE * b.R);
@@ -556,6 +580,10 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.rep_blk0 = (int*)(w + o.rep_blk0);
     d.wbuf = w + o.wbuf;
     d.vbuf = w + o.vbuf;
+    d.mom = (cfg->potential == PIMD_POT_MODEL && cfg->precision != PIMD_FP64) ? (void*)(w + o.mom) : nullptr;
+    // angular terms through moment tensors when the mean neighbour count makes
+    // the O(n) moment path cheaper than the O(n^2) pair sums
+    d.sched.ang = (d.mom != nullptr && b.nb_est >= 24.0) ? 1 : 0;
     d.deterministic = cfg->deterministic ? 1 : 0;
     d.step = (unsigned long long*)(w + o.step);
     d.err = (DevErr*)(w + o.err);
@@ -576,6 +604,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.gamma0 = cfg->gamma0_per_fs;
     d.lambda = cfg->pile_lambda;
     d.thermostat = cfg->thermostat;
+    d.splitting = cfg->splitting;
     d.potential = cfg->potential;
     d.omega_harm = cfg->omega_harm;
     d.rc = cfg->cutoff_A;
@@ -773,14 +802,15 @@ int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
         if (e0) cudaEventDestroy(e0);
         return cuda_check(c, cudaErrorUnknown, "cudaEventCreate");
     }
-    const Sched defaults = {8, 40, 0};
+    const Sched before = c->d.sched;
     Sched cands[8];
     int nc = 0;
     const int rl[6] = {4, 6, 8, 10, 12, 16};
-    for (int q = 0; q < 6; ++q) cands[nc++] = Sched{rl[q], rl[q] + 32, 0};
-    cands[nc++] = Sched{8, 1 << 30, 0};   // ordered pairs for every atom
+    for (int q = 0; q < 6; ++q) cands[nc++] = Sched{rl[q], rl[q] + 32, 0, 0};
+    cands[nc++] = Sched{8, 1 << 30, 0, 0};                 // ordered pairs for every atom
+    if (c->d.mom) cands[nc++] = Sched{8, 40, 0, 1};       // moment tensors
     double best = 1e30, t_default = 0.0;
-    Sched pick = defaults;
+    Sched pick = before;
     for (int q = 0; q < nc && !rc; ++q) {
         c->d.sched = cands[q];
         launch_descriptors(c->d, dparams(c), c->st);   // warm the schedule
@@ -796,7 +826,10 @@ int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
             if (!rc) cudaEventElapsedTime(&ms, e0, e1);
             tmin = std::min(tmin, (double)ms);
         }
-        if (q == 2) t_default = tmin;   // band length 8 is the untuned default
+        const Sched& s = cands[q];
+        const bool same = s.ang == before.ang && (s.ang || (s.rmax == before.rmax && s.band_min == before.band_min &&
+                                                           s.small_atomics == before.small_atomics));
+        if (same) t_default = tmin;   // the schedule in force before tuning
         if (tmin < best) {
             best = tmin;
             pick = cands[q];
@@ -811,7 +844,7 @@ int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
     if (!rc) rc = device_errors(c);
     if (out_ms) {
         out_ms[0] = best;
-        out_ms[1] = pick.band_min >= (1 << 30) ? 0.0 : (double)pick.rmax;
+        out_ms[1] = pick.ang ? -1.0 : pick.band_min >= (1 << 30) ? 0.0 : (double)pick.rmax;
         out_ms[2] = t_default;
     }
     return rc;
@@ -822,11 +855,32 @@ int pimd_set_schedule(pimd_ctx* c, int band_length)
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
     if (band_length != 0 && (band_length < 1 || band_length > 16))
         return fail(c, PIMD_ERR_INVALID_ARG, "band_length must be 0 or 1..16");
-    c->d.sched = band_length == 0 ? Sched{8, 1 << 30, 0} : Sched{band_length, band_length + 32, 0};
+    const int ang = c->d.sched.ang;
+    c->d.sched = band_length == 0 ? Sched{8, 1 << 30, 0, ang} : Sched{band_length, band_length + 32, 0, ang};
     if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
     if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
     c->forces_valid = false;
     return PIMD_OK;
+}
+
+int pimd_set_angular(pimd_ctx* c, int algo)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (algo != PIMD_ANG_PAIRS && algo != PIMD_ANG_MOMENTS)
+        return fail(c, PIMD_ERR_INVALID_ARG, "algo must be PIMD_ANG_PAIRS or PIMD_ANG_MOMENTS");
+    if (algo == PIMD_ANG_MOMENTS && !c->d.mom)
+        return fail(c, PIMD_ERR_UNSUPPORTED, "moment tensors need the model potential in FP32 or BF16 precision");
+    c->d.sched.ang = algo == PIMD_ANG_MOMENTS ? 1 : 0;
+    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
+    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    c->forces_valid = false;
+    return PIMD_OK;
+}
+
+int pimd_get_angular(const pimd_ctx* c)
+{
+    if (!c) return -1;
+    return c->d.sched.ang ? PIMD_ANG_MOMENTS : PIMD_ANG_PAIRS;
 }
 
 int pimd_kernels_per_step(const pimd_ctx* c)

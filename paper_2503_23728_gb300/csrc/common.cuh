@@ -73,6 +73,7 @@ struct Sched {
     int band_min;        // neighbours needed for the band schedule (>= rmax + 32)
     int small_atomics;   // below band_min: 1 = flat walk with shared atomics,
                          // 0 = ordered pairs (each pair twice, no atomics)
+    int ang;             // angular terms: 0 = pair sums, 1 = moment tensors (FP32 only)
 };
 
 // symmetry-function parameters in the working precision

@@ -5,122 +5,10 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "geom.cuh"
 #include "kernels.h"
 
 namespace pimd {
-
-// ---------------------------------------------------------------------------
-// small helpers
-// ---------------------------------------------------------------------------
-// Raise a kernel's dynamic shared-memory limit once (before any graph capture
-// records the launch).
-template <typename K>
-static void set_smem(K kernel, size_t bytes, size_t& done)
-{
-    if (bytes > done) {
-        cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        done = bytes;
-    }
-}
-
-// Gaussian factor exp(-eta x2). FAST (BF16 network path, whose tolerance is
-// 1e-2): exp2(-(eta log2 e) x2) on the special-function unit; otherwise the
-// accurate expf / exp.
-template <bool FAST>
-__device__ __forceinline__ float gauss(float eta, float eta_l2, float x2)
-{
-    if (FAST) return exp2f(-eta_l2 * x2);
-    return expf(-eta * x2);
-}
-template <bool FAST>
-__device__ __forceinline__ double gauss(double eta, double eta_l2, double x2)
-{
-    (void)eta_l2;
-    return exp(-eta * x2);
-}
-__device__ __forceinline__ float f_sqrt(float v) { return sqrtf(v); }
-__device__ __forceinline__ double f_sqrt(double v) { return sqrt(v); }
-
-// Behler cosine cutoff fc(r) and its slope, from sincospi(r / rc)
-__device__ __forceinline__ void cutoff(float r, float rc, float pi_over_rc, float& fc, float& dfc)
-{
-    if (r < rc) {
-        float s, c;
-        sincospif(r / rc, &s, &c);
-        fc = 0.5f * (c + 1.0f);
-        dfc = -0.5f * pi_over_rc * s;
-    } else {
-        fc = 0.0f;
-        dfc = 0.0f;
-    }
-}
-__device__ __forceinline__ void cutoff(double r, double rc, double pi_over_rc, double& fc, double& dfc)
-{
-    if (r < rc) {
-        double s, c;
-        sincospi(r / rc, &s, &c);
-        fc = 0.5 * (c + 1.0);
-        dfc = -0.5 * pi_over_rc * s;
-    } else {
-        fc = 0.0;
-        dfc = 0.0;
-    }
-}
-
-// Minimum-image pair vector x_j - x_i in the working precision. FP32: the
-// difference is formed error-free (TwoSum: s + e = x_j - x_i exactly), shifted
-// by k = rint(s / L) boxes (s - k L_hi is exact for |k| <= 1 by Sterbenz) and
-// rounded once, so wrapped pairs are as accurate as unwrapped ones.
-__device__ __forceinline__ float pair_axis(float xi, float xj, float L, float invL, float Llo, bool per)
-{
-    const float a = xj, b = -xi;
-    const float s = __fadd_rn(a, b);
-    const float bp = __fsub_rn(s, a);
-    const float ap = __fsub_rn(s, bp);
-    float e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
-    float t = s;
-    if (per) {
-        const float k = rintf(__fmul_rn(s, invL));
-        t = __fmaf_rn(-k, L, s);
-        e = __fmaf_rn(-k, Llo, e);
-    }
-    return __fadd_rn(t, e);
-}
-template <typename V4>
-__device__ __forceinline__ void pair_vec(const Rep& rp, const V4& xi, const V4& xj, float& dx, float& dy, float& dz)
-{
-    const bool per = rp.periodic != 0;
-    dx = pair_axis(xi.x, xj.x, rp.Lf[0], rp.invLf[0], rp.Llo[0], per);
-    dy = pair_axis(xi.y, xj.y, rp.Lf[1], rp.invLf[1], rp.Llo[1], per);
-    dz = pair_axis(xi.z, xj.z, rp.Lf[2], rp.invLf[2], rp.Llo[2], per);
-}
-template <typename V4>
-__device__ __forceinline__ void pair_vec(const Rep& rp, const V4& xi, const V4& xj, double& dx, double& dy,
-                                         double& dz)
-{
-    dx = xj.x - xi.x;
-    dy = xj.y - xi.y;
-    dz = xj.z - xi.z;
-    if (rp.periodic) {
-        dx = __dsub_rn(dx, __dmul_rn(rp.L[0], rint(dx / rp.L[0])));
-        dy = __dsub_rn(dy, __dmul_rn(rp.L[1], rint(dy / rp.L[1])));
-        dz = __dsub_rn(dz, __dmul_rn(rp.L[2], rint(dz / rp.L[2])));
-    }
-}
-
-__device__ __forceinline__ float3 as_f32(const float4& v) { return make_float3(v.x, v.y, v.z); }
-__device__ __forceinline__ float3 as_f32(const Dbl4& v)
-{
-    return make_float3(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z));
-}
-
-template <typename V4, typename Real>
-__device__ __forceinline__ V4 make4(Real a, Real b, Real c, Real d)
-{
-    V4 v;
-    v.x = a; v.y = b; v.z = c; v.w = d;
-    return v;
-}
 
 // ---------------------------------------------------------------------------
 // a3: descriptors. Warp per bead-atom. Neighbour records (unit vector, r,
@@ -386,6 +274,10 @@ static void run_desc_f32(const Dev& d, const void* dpv, cudaStream_t st)
 
 void launch_descriptors(const Dev& d, const void* dpv, cudaStream_t st)
 {
+    if (d.precision != 0 && d.sched.ang && d.mom) {
+        launch_descriptors_moment(d, dpv, st);
+        return;
+    }
     if (d.precision == 0) {
         const int w = desc_warps<double>(d.maxnb);
         const size_t sm = (size_t)w * 2 * d.maxnb * sizeof(Dbl4);
@@ -854,6 +746,10 @@ static void run_adj_f32(const Dev& d, const void* dpv, cudaStream_t st)
 
 void launch_adjoint(const Dev& d, const void* dpv, cudaStream_t st)
 {
+    if (d.precision != 0 && d.sched.ang && d.mom) {
+        launch_adjoint_moment(d, dpv, st);
+        return;
+    }
     if (d.precision == 0) {
         const int w = adj_warps<double>(d.maxnb);
         const size_t sm = (size_t)w * adj_smem_per_warp<double>(d.maxnb);

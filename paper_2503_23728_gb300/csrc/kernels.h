@@ -53,6 +53,7 @@ struct Dev {
     int* rep_blk0 = nullptr;           // [R + 1] first ring-polymer block of each replica
     void* wbuf = nullptr;              // Real[B][9] per bead-atom virial
     void* vbuf = nullptr;              // Vec4<Real>[B][maxnb] pair vectors (deterministic mode)
+    void* mom = nullptr;               // float4[B][6][32] angular moments (moment path, FP32)
     int deterministic = 0;
     unsigned long long* step = nullptr;
     DevErr* err = nullptr;
@@ -75,6 +76,7 @@ struct Dev {
     // integrator
     double dt = 0.5, gamma0 = 0.0, lambda = 1.0;
     int thermostat = 1;
+    int splitting = 0;                 // 0 OBABO, 1 BAOAB
     int potential = 0;
     double omega_harm = 0.0;
     double rc = 6.0;
@@ -90,6 +92,9 @@ void launch_descriptors(const Dev& d, const void* dp, cudaStream_t st);
 void launch_network_fp(const Dev& d, cudaStream_t st);
 void launch_network_tc(const Dev& d, cudaStream_t st);
 void launch_adjoint(const Dev& d, const void* dp, cudaStream_t st);
+void launch_descriptors_moment(const Dev& d, const void* dp, cudaStream_t st);
+void launch_adjoint_moment(const Dev& d, const void* dp, cudaStream_t st);
+size_t moment_elems_per_atom();        // float4 moments per bead-atom
 void launch_energy_reduce(const Dev& d, cudaStream_t st);
 void launch_force_gather(const Dev& d, cudaStream_t st);
 void launch_harmonic(const Dev& d, cudaStream_t st);

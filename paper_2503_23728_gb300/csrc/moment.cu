@@ -1,0 +1,518 @@
+// moment.cu -- angular symmetry functions and their adjoint through moment
+// tensors, O(n) per atom in the neighbour count n (FP32 working precision).
+//
+// The G5 functions (Behler's angular functions without the r_jk term) have
+// an exponent that splits over the two neighbours, exp(-eta (r_ij^2 + r_ik^2))
+// fc(r_ij) fc(r_ik) = b_eta(j) b_eta(k) with b_eta(j) = exp(-eta r_ij^2)
+// fc(r_ij), and for integer zeta the angle term is a polynomial of the
+// cosine c_jk = u_j . u_k of the unit vectors. The multinomial theorem gives
+//   (1 + lambda u_j . u_k)^zeta = sum_{a+b+c <= zeta} w_zeta(a,b,c) lambda^(a+b+c) m_abc(u_j) m_abc(u_k),
+//   m_abc(u) = u_x^a u_y^b u_z^c,   w_zeta(a,b,c) = zeta! / ((zeta-a-b-c)! a! b! c!),
+// so with the moments M_eta,abc = sum_j b_eta(j) m_abc(u_j) over all
+// neighbours of the atom,
+//   sum_{j,k} (1 + lambda c_jk)^zeta b_eta(j) b_eta(k) = sum_abc w_zeta lambda^(a+b+c) M_eta,abc^2.
+// The sum over unordered pairs j < k is half of the sum over j != k, and the
+// j = k terms have c = 1, so
+//   G_(zeta,lambda,eta) = sum_abc 2^-zeta w_zeta(a,b,c) lambda^(a+b+c) M_eta,abc^2
+//                         - [lambda = +1] sum_j b_eta(j)^2,
+// the same value as the pair sum up to rounding. zeta <= 8 needs the 165
+// monomials of degree <= 8; per neighbour that is 165 x 4 multiply-adds
+// instead of ~n/2 pair evaluations.
+//
+// Adjoint: with D_nu = dE/dG_nu from the network,
+//   Q_eta,abc = dE/dM_eta,abc = 2 M_eta,abc sum_zeta 2^-zeta w_zeta (D_(zeta,+,eta) + (-1)^(a+b+c) D_(zeta,-,eta)),
+//   dE/db_eta(j) = sum_abc Q_eta,abc m_abc(u_j) - 2 b_eta(j) sum_zeta D_(zeta,+,eta),
+//   dE/du_j      = sum_eta b_eta(j) sum_abc Q_eta,abc grad m_abc(u_j),
+// and the chain rule through u = r / |r| and b_eta(r) gives dE_i/dr_ij.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "geom.cuh"
+#include "kernels.h"
+
+namespace pimd {
+
+constexpr int MDEG = 8;           // largest zeta
+constexpr int NMONO = 165;        // monomials u_x^a u_y^b u_z^c with a + b + c <= 8
+constexpr int MSLOT = 6;          // per lane: monomial m = lane + 32 * slot
+constexpr int MLAST = NMONO - 32 * (MSLOT - 1);   // lanes holding a monomial in the last slot
+
+// Monomial order ("chain order"): c outer, b middle, a inner. Per slot and
+// lane: cf[z] = 2^-zeta_z w_zeta_z(a,b,c) (0 where a+b+c > zeta_z or for the
+// padding beyond m = 164), sg = (-1)^(a+b+c).
+struct MonoTab {
+    float cf[MSLOT][4][32];
+    float sg[MSLOT][32];
+};
+
+constexpr double cfact(int n)
+{
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+constexpr MonoTab make_mono_tab()
+{
+    MonoTab t{};
+    const int zetas[4] = {1, 2, 4, 8};
+    int m = 0;
+    for (int c = 0; c <= MDEG; ++c)
+        for (int b = 0; b <= MDEG - c; ++b)
+            for (int a = 0; a <= MDEG - b - c; ++a, ++m) {
+                const int s = a + b + c;
+                for (int z = 0; z < 4; ++z) {
+                    const int ze = zetas[z];
+                    t.cf[m / 32][z][m % 32] =
+                        s > ze ? 0.0f
+                               : (float)(cfact(ze) / (cfact(ze - s) * cfact(a) * cfact(b) * cfact(c)) /
+                                         (double)(1 << ze));
+                }
+                t.sg[m / 32][m % 32] = (s & 1) ? -1.0f : 1.0f;
+            }
+    return t;
+}
+
+__device__ const MonoTab g_mono = make_mono_tab();
+
+// chain-order index of u_x^a u_y^b u_z^c
+__host__ __device__ constexpr int mono_index(int a, int b, int c)
+{
+    int m = 0;
+    for (int cc = 0; cc < c; ++cc) m += (MDEG - cc + 1) * (MDEG - cc + 2) / 2;
+    for (int bb = 0; bb < b; ++bb) m += MDEG - bb - c + 1;
+    return m + a;
+}
+static_assert(mono_index(0, 0, MDEG) == NMONO - 1, "monomial count");
+static_assert(mono_index(MDEG, 0, 0) == MDEG, "chain order");
+
+// shared memory of the forward kernel, per warp: monomials of 32 neighbours
+// (row stride 165 floats: odd, so the 32 rows written in one step hit distinct
+// banks) and their weights b_eta
+constexpr int FWD_WARP_FLOATS = 32 * NMONO + 32 * 4;
+constexpr int FWD_WARPS = 4;
+constexpr int MBLK = 4;   // neighbours per partial sum of the moments
+
+// s += v by Kahan's compensated summation on both halves; nc carries minus
+// the low-order part lost so far (the squared moments of the descriptors
+// would otherwise double the relative rounding error of a plain FP32 sum)
+__device__ __forceinline__ void kahan_add(float2& s, float2& nc, const float2 v)
+{
+    const float2 y = __fadd2_rn(v, nc);
+    const float2 t = __fadd2_rn(s, y);
+    nc = __fadd2_rn(__ffma2_rn(t, make_float2(-1.0f, -1.0f), s), y);
+    s = t;
+}
+
+// ---------------------------------------------------------------------------
+// forward: warp per bead-atom. Neighbours are taken 32 at a time: each lane
+// forms its neighbour's geometry, radial terms, weights b_eta and the 165
+// monomials (into shared memory); then each lane accumulates the moments of
+// its own monomials m = lane + 32 slot over the 32 neighbours (broadcast
+// weights, conflict-free monomial loads). Moments go to Mout for the adjoint.
+// ---------------------------------------------------------------------------
+template <bool FAST>
+__global__ void __launch_bounds__(32 * FWD_WARPS) desc_mom_fwd_kernel(
+    const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    float* MONO = reinterpret_cast<float*>(smem_raw) + (size_t)wib * FWD_WARP_FLOATS;
+    float4* BW = reinterpret_cast<float4*>(MONO + 32 * NMONO);
+    const int b = blockIdx.x * FWD_WARPS + wib;
+    if (b >= B) return;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const Rep& rp = reps[sy.rep];
+    const int n = min(nnb[b], maxnb);
+    const float4 xi = x[b];
+
+    float gr[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) gr[c] = 0.0f;
+    float dg[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // sum_j b_eta(j)^2 (this lane's neighbours)
+    float2 acc[MSLOT][2];                      // moments (eta 0,1) and (eta 2,3)
+    float2 cmp[MSLOT][2];                      // their compensation terms (FP32 path)
+#pragma unroll
+    for (int k = 0; k < MSLOT; ++k) acc[k][0] = acc[k][1] = cmp[k][0] = cmp[k][1] = make_float2(0.0f, 0.0f);
+
+    for (int s0 = 0; s0 < n; s0 += 32) {
+        const int s = s0 + (int)lane;
+        if (s < n) {
+            const int j = nbr[(size_t)b * maxnb + s];
+            const float4 xj = x[sy.ba0 + j];
+            float dx, dy, dz;
+            pair_vec(rp, xi, xj, dx, dy, dz);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float r = sqrtf(r2);
+            const float ir = 1.0f / r;
+            float fc, dfc;
+            cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const float t = r - dp.r_mu[c];
+                gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+            }
+            float bw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                bw[e] = gauss<FAST>(dp.eta_A[e], dp.eta_A_l2[e], r2) * fc;
+                dg[e] = fmaf(bw[e], bw[e], dg[e]);
+            }
+            BW[lane] = make_float4(bw[0], bw[1], bw[2], bw[3]);
+            float px[MDEG + 1], py[MDEG + 1], pz[MDEG + 1];
+            px[0] = py[0] = pz[0] = 1.0f;
+            px[1] = dx * ir;
+            py[1] = dy * ir;
+            pz[1] = dz * ir;
+#pragma unroll
+            for (int a = 2; a <= MDEG; ++a) {
+                px[a] = px[a - 1] * px[1];
+                py[a] = py[a - 1] * py[1];
+                pz[a] = pz[a - 1] * pz[1];
+            }
+            float* row = MONO + (size_t)lane * NMONO;
+            int m = 0;
+#pragma unroll
+            for (int c = 0; c <= MDEG; ++c)
+#pragma unroll
+                for (int bb = 0; bb <= MDEG - c; ++bb) {
+                    const float base = py[bb] * pz[c];
+#pragma unroll
+                    for (int a = 0; a <= MDEG - bb - c; ++a) row[m + a] = base * px[a];
+                    m += MDEG - bb - c + 1;
+                }
+        }
+        __syncwarp();
+        const int cnt = min(32, n - s0);
+        const float* col = MONO + lane;
+        // blocks of MBLK neighbours are summed into a small partial first,
+        // then added to the running moments (compensated on the FP32 path)
+        for (int j0 = 0; j0 < cnt; j0 += MBLK) {
+            float2 part[MSLOT][2];
+#pragma unroll
+            for (int k = 0; k < MSLOT; ++k) part[k][0] = part[k][1] = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int q = 0; q < MBLK; ++q) {
+                const int jj = j0 + q;
+                if (jj < cnt) {
+                    const float4 w4 = BW[jj];
+                    const float2 w01 = make_float2(w4.x, w4.y), w23 = make_float2(w4.z, w4.w);
+                    const float* rowj = col + (size_t)jj * NMONO;
+#pragma unroll
+                    for (int k = 0; k < MSLOT - 1; ++k) {
+                        const float mv = rowj[32 * k];
+                        const float2 m2 = make_float2(mv, mv);
+                        part[k][0] = __ffma2_rn(w01, m2, part[k][0]);
+                        part[k][1] = __ffma2_rn(w23, m2, part[k][1]);
+                    }
+                    if (lane < (unsigned)MLAST) {
+                        const float mv = rowj[32 * (MSLOT - 1)];
+                        const float2 m2 = make_float2(mv, mv);
+                        part[MSLOT - 1][0] = __ffma2_rn(w01, m2, part[MSLOT - 1][0]);
+                        part[MSLOT - 1][1] = __ffma2_rn(w23, m2, part[MSLOT - 1][1]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MSLOT; ++k)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (FAST)
+                        acc[k][h] = __fadd2_rn(acc[k][h], part[k][h]);
+                    else
+                        kahan_add(acc[k][h], cmp[k][h], part[k][h]);
+                }
+        }
+        __syncwarp();
+    }
+    if (!FAST) {
+#pragma unroll
+        for (int k = 0; k < MSLOT; ++k) {
+            acc[k][0] = __fadd2_rn(acc[k][0], cmp[k][0]);
+            acc[k][1] = __fadd2_rn(acc[k][1], cmp[k][1]);
+        }
+    }
+    const float Gr = transpose_reduce32(gr, lane);
+    float diag[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) diag[e] = warp_sum(dg[e]);
+
+    if (Mout != nullptr) {
+#pragma unroll
+        for (int k = 0; k < MSLOT; ++k)
+            Mout[((size_t)b * MSLOT + k) * 32 + lane] =
+                make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
+    }
+
+    // per lane: its monomials' share of sum_abc 2^-zeta w lambda^s M^2, packed
+    // over lambda = (+1, -1); then the 32-channel transposed reduction
+    float2 S[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) S[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < MSLOT; ++k) {
+        const float sg = g_mono.sg[k][lane];
+        const float mm[4] = {acc[k][0].x * acc[k][0].x, acc[k][0].y * acc[k][0].y, acc[k][1].x * acc[k][1].x,
+                             acc[k][1].y * acc[k][1].y};
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+            const float cz = g_mono.cf[k][z][lane];
+            const float2 c2 = make_float2(cz, cz * sg);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) S[z * 4 + e] = __ffma2_rn(c2, make_float2(mm[e], mm[e]), S[z * 4 + e]);
+        }
+    }
+    float ga[NA];
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ga[(2 * z) * 4 + e] = S[z * 4 + e].x;
+            ga[(2 * z + 1) * 4 + e] = S[z * 4 + e].y;
+        }
+    float Ga = transpose_reduce32(ga, lane);
+    // lane = channel nu = (zeta_index * 2 + lambda_index) * 4 + eta_index:
+    // remove the j = k terms, (1 + lambda)^zeta 2^-zeta sum_j b^2 = sum_j b^2 for lambda = +1
+    const int e = (int)lane & 3;
+    const float dge = e == 0 ? diag[0] : e == 1 ? diag[1] : e == 2 ? diag[2] : diag[3];
+    if ((lane & 4u) == 0) Ga -= dge;
+    G[(size_t)b * ND + lane] = Gr;
+    G[(size_t)b * ND + NR + lane] = Ga;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint: warp per bead-atom. The warp forms Q = dE/dM (lane-owned
+// monomials, into shared memory), then each lane takes one neighbour and
+// evaluates the polynomials sum_abc Q_eta,abc m_abc(u) and their gradient by
+// nested Horner recurrences (x innermost, then y, then z) with broadcast
+// loads of Q.
+// ---------------------------------------------------------------------------
+constexpr int ADJ_WARP_BYTES = NMONO * 16 + ND * 4;
+constexpr int ADJ_WARPS = 8;
+
+template <bool FAST>
+__global__ void __launch_bounds__(32 * ADJ_WARPS, 2) desc_mom_adj_kernel(
+    const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
+    float4* __restrict__ f, float* __restrict__ wbuf, int det, float4* __restrict__ vbuf)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    float4* Q = reinterpret_cast<float4*>(smem_raw + (size_t)wib * ADJ_WARP_BYTES);
+    float* gs = reinterpret_cast<float*>(Q + NMONO);
+    const int b = blockIdx.x * ADJ_WARPS + wib;
+    if (b >= B) return;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const Rep& rp = reps[sy.rep];
+    const int n = min(nnb[b], maxnb);
+    const float4 xi = x[b];
+    gs[lane] = dEdG[(size_t)b * ND + lane];
+    gs[NR + lane] = dEdG[(size_t)b * ND + NR + lane];
+    __syncwarp();
+
+    // D(zeta,+,eta) +- D(zeta,-,eta) and sum_zeta D(zeta,+,eta)
+    float Dp[16], Dm[16], dsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float dplus = gs[NR + (2 * z) * 4 + e], dminus = gs[NR + (2 * z + 1) * 4 + e];
+            Dp[z * 4 + e] = dplus + dminus;
+            Dm[z * 4 + e] = dplus - dminus;
+            dsum[e] += dplus;
+        }
+#pragma unroll
+    for (int k = 0; k < MSLOT; ++k) {
+        const int m = (int)lane + 32 * k;
+        if (k < MSLOT - 1 || lane < (unsigned)MLAST) {
+            const float4 M = Min[((size_t)b * MSLOT + k) * 32 + lane];
+            const bool odd = g_mono.sg[k][lane] < 0.0f;
+            float F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int z = 0; z < 4; ++z) {
+                const float cz = g_mono.cf[k][z][lane];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) F[e] = fmaf(cz, odd ? Dm[z * 4 + e] : Dp[z * 4 + e], F[e]);
+            }
+            Q[m] = make_float4(2.0f * M.x * F[0], 2.0f * M.y * F[1], 2.0f * M.z * F[2], 2.0f * M.w * F[3]);
+        }
+    }
+    __syncwarp();
+
+    float fi[3] = {0.0f, 0.0f, 0.0f};
+    float wl[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wl[q] = 0.0f;
+    for (int s = (int)lane; s < n; s += 32) {
+        const int j = nbr[(size_t)b * maxnb + s];
+        const float4 xj = x[sy.ba0 + j];
+        float dx, dy, dz;
+        pair_vec(rp, xi, xj, dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r = sqrtf(r2);
+        const float ir = 1.0f / r;
+        float fc, dfc;
+        cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+        float dEdr = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            const float t = r - dp.r_mu[c];
+            const float ex = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t);
+            dEdr += gs[c] * ex * (-2.0f * dp.eta_R * t * fc + dfc);
+        }
+        float bw[4], dbw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float ex = gauss<FAST>(dp.eta_A[e], dp.eta_A_l2[e], r2);
+            bw[e] = ex * fc;
+            dbw[e] = ex * (-2.0f * dp.eta_A[e] * r * fc + dfc);
+        }
+        const float ux = dx * ir, uy = dy * ir, uz = dz * ir;
+        const float2 X2 = make_float2(ux, ux), Y2 = make_float2(uy, uy), Z2 = make_float2(uz, uz);
+        // P_eta(u) = sum_abc Q_eta,abc u_x^a u_y^b u_z^c and its gradient by
+        // nested Horner recurrences (a, then b, then c, each descending);
+        // float2 pairs hold (eta 0, eta 1) and (eta 2, eta 3)
+        float2 V0, V1, VX0, VX1, VY0, VY1, VZ0, VZ1;
+#pragma unroll
+        for (int c = MDEG; c >= 0; --c) {
+            float2 S0, S1, SX0, SX1, SY0, SY1;
+#pragma unroll
+            for (int bb = MDEG - c; bb >= 0; --bb) {
+                const int A = MDEG - bb - c;
+                const int m0 = mono_index(0, bb, c);
+                float4 q = Q[m0 + A];
+                float2 R0 = make_float2(q.x, q.y), R1 = make_float2(q.z, q.w);
+                float2 RX0 = make_float2(0.0f, 0.0f), RX1 = RX0;
+#pragma unroll
+                for (int a = A - 1; a >= 0; --a) {
+                    q = Q[m0 + a];
+                    if (a == A - 1) {
+                        RX0 = R0;
+                        RX1 = R1;
+                    } else {
+                        RX0 = __ffma2_rn(RX0, X2, R0);
+                        RX1 = __ffma2_rn(RX1, X2, R1);
+                    }
+                    R0 = __ffma2_rn(R0, X2, make_float2(q.x, q.y));
+                    R1 = __ffma2_rn(R1, X2, make_float2(q.z, q.w));
+                }
+                if (bb == MDEG - c) {
+                    S0 = R0; S1 = R1; SX0 = RX0; SX1 = RX1;
+                    SY0 = SY1 = make_float2(0.0f, 0.0f);
+                } else {
+                    if (bb == MDEG - c - 1) {
+                        SY0 = S0;
+                        SY1 = S1;
+                    } else {
+                        SY0 = __ffma2_rn(SY0, Y2, S0);
+                        SY1 = __ffma2_rn(SY1, Y2, S1);
+                    }
+                    S0 = __ffma2_rn(S0, Y2, R0);
+                    S1 = __ffma2_rn(S1, Y2, R1);
+                    SX0 = __ffma2_rn(SX0, Y2, RX0);
+                    SX1 = __ffma2_rn(SX1, Y2, RX1);
+                }
+            }
+            if (c == MDEG) {
+                V0 = S0; V1 = S1; VX0 = SX0; VX1 = SX1; VY0 = SY0; VY1 = SY1;
+                VZ0 = VZ1 = make_float2(0.0f, 0.0f);
+            } else {
+                if (c == MDEG - 1) {
+                    VZ0 = V0;
+                    VZ1 = V1;
+                } else {
+                    VZ0 = __ffma2_rn(VZ0, Z2, V0);
+                    VZ1 = __ffma2_rn(VZ1, Z2, V1);
+                }
+                V0 = __ffma2_rn(V0, Z2, S0);
+                V1 = __ffma2_rn(V1, Z2, S1);
+                VX0 = __ffma2_rn(VX0, Z2, SX0);
+                VX1 = __ffma2_rn(VX1, Z2, SX1);
+                VY0 = __ffma2_rn(VY0, Z2, SY0);
+                VY1 = __ffma2_rn(VY1, Z2, SY1);
+            }
+        }
+        const float V[4] = {V0.x, V0.y, V1.x, V1.y};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dEdr = fmaf(V[e] - 2.0f * bw[e] * dsum[e], dbw[e], dEdr);
+        const float gx = bw[0] * VX0.x + bw[1] * VX0.y + bw[2] * VX1.x + bw[3] * VX1.y;
+        const float gy = bw[0] * VY0.x + bw[1] * VY0.y + bw[2] * VY1.x + bw[3] * VY1.y;
+        const float gz = bw[0] * VZ0.x + bw[1] * VZ0.y + bw[2] * VZ1.x + bw[3] * VZ1.y;
+        const float gu = gx * ux + gy * uy + gz * uz;
+        const float v[3] = {dEdr * ux + (gx - gu * ux) * ir, dEdr * uy + (gy - gu * uy) * ir,
+                            dEdr * uz + (gz - gu * uz) * ir};
+        if (det)
+            vbuf[(size_t)b * maxnb + s] = make_float4(v[0], v[1], v[2], 0.0f);
+        else
+            atomicAdd(&f[sy.ba0 + j], make_float4(-v[0], -v[1], -v[2], 0.0f));
+        const float d3[3] = {dx, dy, dz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            fi[a] += v[a];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) wl[3 * a + c] -= d3[a] * v[c];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fi[a] = warp_sum(fi[a]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wl[q] = warp_sum(wl[q]);
+    if (lane == 0) {
+        if (det)
+            f[b] = make_float4(fi[0], fi[1], fi[2], 0.0f);   // gathered later
+        else
+            atomicAdd(&f[b], make_float4(fi[0], fi[1], fi[2], 0.0f));
+    }
+    if (lane < 9) {
+        float mine = wl[0];
+#pragma unroll
+        for (int q = 1; q < 9; ++q)
+            if ((int)lane == q) mine = wl[q];
+        wbuf[(size_t)b * 9 + lane] = mine;
+    }
+}
+
+size_t moment_elems_per_atom() { return (size_t)MSLOT * 32; }   // float4 per bead-atom
+
+template <bool FAST>
+static void run_fwd(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    const size_t sm = (size_t)FWD_WARPS * FWD_WARP_FLOATS * sizeof(float);
+    { static size_t done = 0; set_smem(desc_mom_fwd_kernel<FAST>, sm, done); }
+    desc_mom_fwd_kernel<FAST><<<(d.B + FWD_WARPS - 1) / FWD_WARPS, 32 * FWD_WARPS, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+        *(const DescParams<float>*)dpv, (float*)d.G, (float4*)d.mom);
+}
+
+template <bool FAST>
+static void run_adj(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    const size_t sm = (size_t)ADJ_WARPS * ADJ_WARP_BYTES;
+    desc_mom_adj_kernel<FAST><<<(d.B + ADJ_WARPS - 1) / ADJ_WARPS, 32 * ADJ_WARPS, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+        *(const DescParams<float>*)dpv, (const float4*)d.mom, (const float*)d.dEdG, (float4*)d.f,
+        (float*)d.wbuf, d.deterministic, (float4*)d.vbuf);
+}
+
+void launch_descriptors_moment(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    if (d.precision == 2)
+        run_fwd<true>(d, dpv, st);
+    else
+        run_fwd<false>(d, dpv, st);
+}
+
+void launch_adjoint_moment(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    if (d.precision == 2)
+        run_adj<true>(d, dpv, st);
+    else
+        run_adj<false>(d, dpv, st);
+}
+
+}  // namespace pimd

@@ -119,12 +119,39 @@ __global__ void beads_kernel(const int2* __restrict__ blocks, const Rep* __restr
     comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
 }
 
-// O(dt/2) B(dt/2) A(dt) on each mode, then the new bead positions
+// free ring-polymer step of mode k over hA: centroid drift, or the rotation
+// (cw, sw) of the scaled phase plane that the host computed for the chosen
+// propagator (exact or Cayley)
+__device__ __forceinline__ void free_rp(int k, const Mode& md, double m, double hA, double& pv, double& qv)
+{
+    if (k == 0) {
+        qv += pv * hA / m;
+    } else {
+        const double pn = md.cw * pv - m * md.w * md.sw * qv;
+        qv = md.sw / (m * md.w) * pv + md.cw * qv;
+        pv = pn;
+    }
+}
+
+// PILE-L O sub-step with the host's (c1, c2) for its duration; returns the
+// kinetic-energy change
+__device__ __forceinline__ double pile_o(const Rep& rp, const Mode& md, double m, unsigned local, unsigned step,
+                                         unsigned rep, unsigned stream, double& pv)
+{
+    const double xi = normal_dev(rp.seed, local, step, rep, stream);
+    const double pn = md.c1 * pv + sqrt(m * rp.kT_md) * md.c2 * xi;
+    const double dK = (pn * pn - pv * pv) / (2.0 * m);
+    pv = pn;
+    return dK;
+}
+
+// OBABO: O(dt/2) B(dt/2) A(dt); BAOAB: B(dt/2) A(dt/2) O(dt) A(dt/2); on each
+// mode, then the new bead positions
 template <typename Real>
 __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
                                 const double* __restrict__ cmat, const Mode* __restrict__ modes,
                                 const double* __restrict__ mass, const unsigned long long* __restrict__ stepp,
-                                double dt, int thermostat, double* __restrict__ q, double* __restrict__ p,
+                                double dt, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
                                 const double* __restrict__ fnm, Vec4<Real>* __restrict__ x,
                                 double* __restrict__ qpart)
 {
@@ -140,20 +167,16 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
         const Mode md = modes[rp.mode0 + k];
         const double m = mass[rp.atom0 + t.i];
         double pv = p[g], qv = q[g];
-        if (thermostat) {
-            const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
-            const double xi = normal_dev(rp.seed, local, (unsigned)(*stepp), (unsigned)t.r, 2u);
-            const double pn = md.c1 * pv + sqrt(m * rp.kT_md) * md.c2 * xi;
-            dK = (pn * pn - pv * pv) / (2.0 * m);
-            pv = pn;
-        }
-        pv += 0.5 * dt * fnm[g] / MVV2E;
-        if (k == 0) {
-            qv += pv * dt / m;
+        const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
+        if (baoab) {
+            pv += 0.5 * dt * fnm[g] / MVV2E;
+            free_rp(k, md, m, 0.5 * dt, pv, qv);
+            if (thermostat) dK = pile_o(rp, md, m, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
+            free_rp(k, md, m, 0.5 * dt, pv, qv);
         } else {
-            const double pn = md.cw * pv - m * md.w * md.sw * qv;
-            qv = md.sw / (m * md.w) * pv + md.cw * qv;
-            pv = pn;
+            if (thermostat) dK = pile_o(rp, md, m, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
+            pv += 0.5 * dt * fnm[g] / MVV2E;
+            free_rp(k, md, m, dt, pv, qv);
         }
         p[g] = pv;
         q[g] = qv;
@@ -176,7 +199,7 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
     comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
 }
 
-// f_nm = C^T f; if do_step: B(dt/2) O(dt/2)
+// f_nm = C^T f; if do_step: B(dt/2), then O(dt/2) for OBABO
 template <typename Real>
 __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
                                  const double* __restrict__ cmat, const Mode* __restrict__ modes,
@@ -209,10 +232,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
             if (thermostat) {
                 const Mode md = modes[rp.mode0 + k];
                 const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
-                const double xi = normal_dev(rp.seed, local, (unsigned)(*stepp), (unsigned)t.r, 3u);
-                const double pn = md.c1 * pv + sqrt(m * rp.kT_md) * md.c2 * xi;
-                dK = (pn * pn - pv * pv) / (2.0 * m);
-                pv = pn;
+                dK = pile_o(rp, md, m, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
             }
             p[g] = pv;
         }
@@ -263,24 +283,24 @@ void launch_rp_start(const Dev& d, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.q, d.p, d.fnm, (Dbl4*)d.x,
-            d.qpart);
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            (Dbl4*)d.x, d.qpart);
     else
         rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.q, d.p, d.fnm, (float4*)d.x,
-            d.qpart);
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            (float4*)d.x, d.qpart);
 }
 
 void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, do_step ? 1 : 0,
-            (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err);
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat && !d.splitting,
+            do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err);
     else
         rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, do_step ? 1 : 0,
-            (const float4*)d.f, d.p, d.fnm, d.qpart, d.err);
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat && !d.splitting,
+            do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err);
 }
 
 void launch_bump_step(const Dev& d, cudaStream_t st)

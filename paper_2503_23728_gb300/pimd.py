@@ -23,7 +23,8 @@ POT_MODEL, POT_HARMONIC = 0, 1
 EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_weights", "pimd_step",
            "pimd_energy_forces", "pimd_descriptors", "pimd_estimators", "pimd_get_state", "pimd_set_state",
            "pimd_get_forces", "pimd_get_neighbours", "pimd_sync", "pimd_sizes", "pimd_destroy", "pimd_last_error",
-           "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule"]
+           "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule", "pimd_set_angular", "pimd_get_angular"]
+ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
 
@@ -38,7 +39,10 @@ class pimd_config(ct.Structure):
                 ("cutoff_A", ct.c_double), ("precision", ct.c_int), ("thermostat", ct.c_int),
                 ("potential", ct.c_int), ("max_neighbours", ct.c_int), ("omega_harm", ct.c_double),
                 ("n_hidden", ct.c_int), ("widths", ct.c_int * 4), ("stream", ct.c_void_p), ("timing", ct.c_int),
-                ("nbr_algo", ct.c_int), ("deterministic", ct.c_int)]
+                ("nbr_algo", ct.c_int), ("deterministic", ct.c_int), ("splitting", ct.c_int),
+                ("free_rp", ct.c_int)]
+SPLITTING = {"obabo": 0, "baoab": 1}
+FREE_RP = {"exact": 0, "cayley": 1}
 
 
 class pimd_replica_desc(ct.Structure):
@@ -103,6 +107,9 @@ def load(path: str = LIB_PATH):
     L.pimd_kernels_per_step.restype = ct.c_int
     L.pimd_tune.argtypes = [vp, ct.c_int, dp]
     L.pimd_set_schedule.argtypes = [vp, ct.c_int]
+    L.pimd_set_angular.argtypes = [vp, ct.c_int]
+    L.pimd_get_angular.argtypes = [vp]
+    L.pimd_get_angular.restype = ct.c_int
     L.pimd_descriptors_noalloc.argtypes = [vp, ct.c_int, dp, ct.c_double, ct.c_double, dp, dp, vp, vp]
     _lib = L
     return L
@@ -201,11 +208,22 @@ def pimd_stage_times(ctx) -> dict:
 def pimd_tune(ctx, reps: int = 3) -> dict:
     out = np.zeros(3)
     _check(load().pimd_tune(ctx, int(reps), _dp(out)), ctx)
-    return {"best_ms": float(out[0]), "band_length": int(out[1]), "default_ms": float(out[2])}
+    choice = int(out[1])
+    return {"best_ms": float(out[0]), "band_length": max(choice, 0),
+            "angular": "moments" if choice < 0 else "pairs", "default_ms": float(out[2])}
 
 
 def pimd_set_schedule(ctx, band_length: int):
     _check(load().pimd_set_schedule(ctx, int(band_length)), ctx)
+
+
+def pimd_set_angular(ctx, algo):
+    """algo: "pairs" | "moments" (or PIMD_ANG_* value)."""
+    _check(load().pimd_set_angular(ctx, ANGULAR.get(algo, algo) if isinstance(algo, str) else int(algo)), ctx)
+
+
+def pimd_get_angular(ctx) -> str:
+    return {0: "pairs", 1: "moments"}[int(load().pimd_get_angular(ctx))]
 
 
 def pimd_kernels_per_step(ctx) -> int:
@@ -246,7 +264,8 @@ def pimd_last_error(ctx=None) -> str:
 # ---------------------------------------------------------------- helpers
 def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128, 128, 128), pile_lambda=1.0,
                 thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128, stream=None,
-                timing=False, nbr_algo=0, deterministic=False) -> pimd_config:
+                timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
+                free_rp="exact") -> pimd_config:
     c = pimd_config()
     c.dt_fs = dt_fs
     c.gamma0_per_fs = gamma0_per_fs
@@ -264,6 +283,8 @@ def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128,
     c.timing = 1 if timing else 0
     c.nbr_algo = int(nbr_algo)
     c.deterministic = 1 if deterministic else 0
+    c.splitting = SPLITTING[splitting] if isinstance(splitting, str) else int(splitting)
+    c.free_rp = FREE_RP[free_rp] if isinstance(free_rp, str) else int(free_rp)
     return c
 
 
@@ -327,7 +348,8 @@ class Context:
 
     def __init__(self, replicas, dt_fs, gamma0_per_fs, precision="fp32", widths=(128, 128, 128), cutoff=6.0,
                  pile_lambda=1.0, thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128,
-                 masses=None, stream=None, timing=False, nbr_algo=0, deterministic=False):
+                 masses=None, stream=None, timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
+                 free_rp="exact"):
         import torch
         self.torch = torch
         self.keep = _Keep()
@@ -337,7 +359,7 @@ class Context:
         self.stream = stream
         self.cfg = make_config(dt_fs, gamma0_per_fs, precision, cutoff, widths, pile_lambda, thermostat, potential,
                                omega, max_neighbours, ct.c_void_p(stream.cuda_stream), timing, nbr_algo,
-                               deterministic)
+                               deterministic, splitting, free_rp)
         self.reps = make_replicas(self.replicas, self.keep, masses)
         self.ws_bytes = pimd_workspace_size(self.cfg, self.reps)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -417,6 +439,13 @@ class Context:
 
     def set_schedule(self, band_length: int):
         pimd_set_schedule(self.h, band_length)
+
+    def set_angular(self, algo: str):
+        pimd_set_angular(self.h, algo)
+
+    @property
+    def angular(self) -> str:
+        return pimd_get_angular(self.h)
 
 
 def _autograd_function():

@@ -42,3 +42,19 @@ def fad_model():
     _, F, _ = O.energy_forces(m, r.Z, r.x0, r.box)
     s.set_energy_scale(m, 1.0 / float(np.sqrt((F ** 2).mean())))
     return w, r, m
+
+
+@pytest.fixture(scope="session")
+def ice_model():
+    """Ice Ih, 432 molecules x 32 beads, 3x128 network calibrated like the
+    water-64 model."""
+    import oracle as O
+    from paper_2503_23728_gb300 import synth as s
+    w = s.workload("ice")
+    r = w.replicas[0]
+    m = s.xavier_model(s.elements_of(w.replicas), w.widths, seed=7)
+    G = O.descriptors(m, r.x0, r.box)
+    s.set_normalisation(m, G, r.Z)
+    _, F, _ = O.energy_forces(m, r.Z, r.x0, r.box)
+    s.set_energy_scale(m, 1.0 / float(np.sqrt((F ** 2).mean())))
+    return w, r, m

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert P.pimd_abi_version() == 1
+    assert P.pimd_abi_version() == 2
 
 
 def _cfg(**kw):
@@ -55,8 +55,12 @@ def test_workspace_size_scales_with_system(lib):
     big = P.make_replicas([s.water_box(5, seed=3)], keep)
     n2 = P.pimd_workspace_size(_cfg(), big)
     assert 0 < n1 < n2
-    # FP64 records are larger
-    assert P.pimd_workspace_size(_cfg(precision="fp64"), small) > n1
+    # FP32 / BF16 hold the angular moments (6 x 32 float4 per bead-atom); FP64
+    # records are larger than FP32 ones otherwise
+    B = sum(r.n_atoms * r.n_beads for r in w.replicas)
+    mom = 6 * 32 * 16 * B
+    assert n1 > mom
+    assert P.pimd_workspace_size(_cfg(precision="fp64"), small) > n1 - mom
 
 
 @pytest.mark.parametrize("bad", [

@@ -1,0 +1,185 @@
+"""GPU parity of the moment-tensor evaluation of the angular symmetry
+functions (O(n) per atom) against the FP64 oracle's pair sums and against the
+pair-sum kernels on the same inputs.
+
+Bars as for the FP32 path: descriptors within 1e-5 of each channel's scale,
+forces and virial within 1e-5 relative max-norm (FAD: 1e-4, its FP32 bar, see
+the deterministic-mode test)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_23728_gb300 import synth as s
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _P():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2503_23728_gb300 import pimd as P
+    return P
+
+
+def _relmax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _beads(rep, P, seed, sigma=0.08):
+    rng = np.random.default_rng(seed)
+    x = np.repeat(rep.x0[None], P, axis=0) + rng.normal(scale=sigma, size=(P, rep.n_atoms, 3))
+    return x.astype(np.float32).astype(np.float64)
+
+
+def _with_beads(rep, P):
+    return s.Replica(rep.Z, rep.x0, rep.box, P, rep.T, rep.seed, rep.name)
+
+
+def test_default_selection_and_errors(water64_model, fad_model):
+    P = _P()
+    w, r, m = water64_model
+    c = P.Context([_with_beads(r, 2)], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+    assert c.angular == "moments"          # ~90 neighbours per atom
+    wf, rf, mf = fad_model
+    c2 = P.Context([_with_beads(rf, 2)], wf.dt_fs, wf.gamma0_per_fs, precision="fp32", widths=wf.widths)
+    assert c2.angular == "pairs"           # 9 neighbours
+    c3 = P.Context([_with_beads(r, 2)], w.dt_fs, w.gamma0_per_fs, precision="fp64", widths=w.widths)
+    assert c3.angular == "pairs"
+    with pytest.raises(P.PimdError) as ei:
+        c3.set_angular("moments")
+    assert ei.value.code == -8
+    with pytest.raises(P.PimdError) as ei:
+        c.set_angular(5)
+    assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_tc"])
+def test_water_descriptors_forces_virial(water64_model, precision):
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 5)
+    xb = _beads(rep, 5, seed=23)
+    x = torch.tensor(xb.reshape(-1, 3), device="cuda")
+    out = {}
+    for algo in ("moments", "pairs"):
+        ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision=precision, widths=w.widths)
+        ctx.set_weights(m)
+        ctx.set_angular(algo)
+        G = ctx.descriptors(x).cpu().numpy()
+        e, f, v = ctx.energy_forces(x)
+        out[algo] = (G, e.cpu().numpy(), f.cpu().numpy().reshape(5, rep.n_atoms, 3), v.cpu().numpy())
+    G, e, f, v = out["moments"]
+    for k in range(5):
+        Go = O.descriptors(m, xb[k], rep.box)
+        Gg = G[k * rep.n_atoms:(k + 1) * rep.n_atoms]
+        scale = np.abs(Go).max(axis=0) + 1e-30
+        assert np.all(np.abs(Gg - Go) <= 1e-5 * scale), k
+    if precision == "fp32":
+        Eo, Fo, Wo = O.energy_forces_batch(m, rep.Z, xb, rep.box)
+        assert _relmax(f, Fo) < 1e-5
+        assert _relmax(v, Wo) < 1e-5
+        assert np.abs(e - Eo.sum(axis=1)).max() / rep.n_atoms < 1e-5
+    else:
+        # same BF16 network on both sides: the angular evaluation changes only
+        # FP32 rounding of the descriptors and of the adjoint
+        _, ep, fp, vp = out["pairs"]
+        assert np.sqrt(((f - fp) ** 2).mean() / (fp ** 2).mean()) < 1e-2
+        assert np.abs(e - ep).max() / rep.n_atoms < 1e-3
+    assert np.abs(f.sum(axis=1)).max() < 1e-4 * np.abs(f).max()
+
+
+def test_fad_forced_moments(fad_model):
+    """Small neighbour counts (9): the moment path is still exact."""
+    P = _P()
+    w, r, m = fad_model
+    rep = _with_beads(r, 6)
+    xb = _beads(rep, 6, seed=4, sigma=0.1)
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+    ctx.set_weights(m)
+    ctx.set_angular("moments")
+    e, f, v = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
+    Eo, Fo, Wo = O.energy_forces_batch(m, rep.Z, xb, None)
+    assert _relmax(f.cpu().numpy().reshape(Fo.shape), Fo) < 1e-4
+    assert _relmax(v.cpu().numpy(), Wo) < 1e-4
+
+
+def test_clusters_with_isolated_atom_and_empty_lists():
+    """Replicas of 1..24 atoms, one atom far from the others (no neighbours):
+    moment path forced, forces match the oracle, isolated atom gets zero."""
+    P = _P()
+    reps = s.batch(n_rep=5, seed=91, beads=(2, 3))
+    r0 = reps[0]
+    x0 = r0.x0.copy()
+    x0[0] += np.array([40.0, 0.0, 0.0])
+    reps[0] = s.Replica(r0.Z, x0, r0.box, r0.n_beads, r0.T, r0.seed)
+    lone = s.Replica(np.array([8], dtype=np.int32), np.zeros((1, 3)), (0.0, 0.0, 0.0), 2, 300.0, 5)
+    reps.append(lone)
+    m = s.xavier_model(s.elements_of(reps), (64, 64), seed=6)
+    G = np.concatenate([O.descriptors(m, r.x0, None) for r in reps])
+    Z = np.concatenate([r.Z for r in reps])
+    s.set_normalisation(m, G, Z)
+    ctx = P.Context(reps, 0.25, 0.01, precision="fp32", widths=(64, 64))
+    ctx.set_weights(m)
+    ctx.set_angular("moments")
+    xs = [_beads(r, r.n_beads, seed=50 + k, sigma=0.05) for k, r in enumerate(reps)]
+    e, f, _ = ctx.energy_forces(torch.tensor(np.concatenate([x.reshape(-1, 3) for x in xs]), device="cuda"))
+    e, f = e.cpu().numpy(), f.cpu().numpy()
+    b0 = s0 = 0
+    for r, x in zip(reps, xs):
+        Eo, Fo, _ = O.energy_forces_batch(m, r.Z, x, None)
+        n = r.n_atoms * r.n_beads
+        fg = f[b0:b0 + n].reshape(Fo.shape)
+        if np.abs(Fo).max() > 0:
+            assert _relmax(fg, Fo) < 1e-5
+        else:
+            assert np.abs(fg).max() == 0.0
+        assert np.abs(e[s0:s0 + r.n_beads] - Eo.sum(axis=1)).max() < 1e-5 * max(1, r.n_atoms)
+        b0 += n
+        s0 += r.n_beads
+    assert np.abs(f[:reps[0].n_atoms * reps[0].n_beads].reshape(reps[0].n_beads, -1, 3)[:, 0]).max() == 0.0
+
+
+def test_ice_full_size_moments_vs_pairs(ice_model):
+    """Ice Ih, 1296 atoms x 32 beads, moment path as launched by the bench:
+    forces of sampled beads against the oracle, and the whole batch against
+    the pair-sum kernels."""
+    P = _P()
+    w, r, m = ice_model
+    rep = r
+    xb = _beads(rep, rep.n_beads, seed=77, sigma=0.05)
+    x = torch.tensor(xb.reshape(-1, 3), device="cuda")
+    res = {}
+    for algo in ("moments", "pairs"):
+        ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+        ctx.set_weights(m)
+        ctx.set_angular(algo)
+        e, f, v = ctx.energy_forces(x)
+        res[algo] = (e.cpu().numpy(), f.cpu().numpy().reshape(rep.n_beads, rep.n_atoms, 3), v.cpu().numpy())
+        ctx.close()
+    e, f, v = res["moments"]
+    ep, fp, vp = res["pairs"]
+    for k in (0, 13, 31):
+        Eo, Fo, Wo = O.energy_forces_batch(m, rep.Z, xb[k:k + 1], rep.box)
+        assert _relmax(f[k:k + 1], Fo) < 1e-5, ("moments", k, _relmax(f[k:k + 1], Fo))
+        assert _relmax(fp[k:k + 1], Fo) < 1e-5, ("pairs", k, _relmax(fp[k:k + 1], Fo))
+        assert abs(e[k] - Eo.sum()) / rep.n_atoms < 1e-5
+    # two FP32 evaluations, each within 1e-5 of the oracle
+    assert _relmax(f, fp) < 2e-5
+    assert _relmax(v, vp) < 2e-5
+
+
+def test_deterministic_moments_bit_identical(water64_model):
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 3)
+    xb = _beads(rep, 3, seed=8)
+    x = torch.tensor(xb.reshape(-1, 3), device="cuda")
+    outs = []
+    for _ in range(2):
+        ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths, deterministic=True)
+        ctx.set_weights(m)
+        assert ctx.angular == "moments"
+        _, f, v = ctx.energy_forces(x)
+        outs.append((f.cpu().numpy(), v.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])

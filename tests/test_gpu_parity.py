@@ -278,6 +278,7 @@ def test_every_pair_schedule_matches_oracle(water_fp32, band):
     """The descriptor / adjoint pair schedules (flat walk, bands of 1..16
     with shuffle carries) all give the oracle's forces."""
     P, w, rep, m, ctx, xb = water_fp32
+    ctx.set_angular("pairs")
     ctx.set_schedule(band)
     try:
         e, f, _ = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
@@ -286,6 +287,7 @@ def test_every_pair_schedule_matches_oracle(water_fp32, band):
         assert np.abs(e.cpu().numpy() - Eo.sum(axis=1)).max() / rep.n_atoms < 1e-5
     finally:
         ctx.set_schedule(8)
+        ctx.set_angular("moments")
 
 
 def test_tuner_keeps_forces_correct(water64_model):
@@ -297,6 +299,7 @@ def test_tuner_keeps_forces_correct(water64_model):
     res = ctx.tune(reps=2)
     assert res["best_ms"] > 0 and res["best_ms"] <= res["default_ms"] + 1e-9
     assert res["band_length"] in (0, 4, 6, 8, 10, 12, 16)
+    assert res["angular"] in ("pairs", "moments") and ctx.angular == res["angular"]
     xb = _bead_positions(rep, 4, seed=31)
     _, f, _ = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
     _, Fo, _ = O.energy_forces_batch(m, rep.Z, xb, rep.box)
@@ -325,18 +328,20 @@ def test_nonfinite_forces_are_reported(water64_model):
     assert np.isfinite(ok.estimators()[0]["E_tot"])
 
 
-@pytest.mark.parametrize("which", ["water", "fad"])
+@pytest.mark.parametrize("which", ["water", "water-pairs", "fad"])
 def test_deterministic_mode_resume_is_bit_identical(water64_model, fad_model, which):
     """deterministic = 1: forces summed in a fixed order (pair vectors
     gathered per atom; ordered pairs for small neighbour counts), virial and
     thermostat heat reduced in fixed order, so a resumed run reproduces the
     uninterrupted one bit for bit, and matches the oracle."""
     P = _P()
-    w, r, m = water64_model if which == "water" else fad_model
+    w, r, m = fad_model if which == "fad" else water64_model
     rep = _with_beads(r, 4)
 
     def ctx():
         c = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths, deterministic=True)
+        if which == "water-pairs":
+            c.set_angular("pairs")
         c.set_weights(m)
         return c
 
@@ -357,6 +362,6 @@ def test_deterministic_mode_resume_is_bit_identical(water64_model, fad_model, wh
     # FAD's per-element normalisation rests on 2-4 atoms, so several sigma sit
     # at the 1e-2 floor and amplify FP32 descriptor round-off ~100x; its
     # specified precision is FP64 (1e-10 elsewhere). Water keeps the 1e-5 bar.
-    tol = 1e-5 if which == "water" else 1e-4
+    tol = 1e-4 if which == "fad" else 1e-5
     assert _relmax(f.cpu().numpy().reshape(Fo.shape), Fo) < tol
     assert b.kernels_per_step() == 9

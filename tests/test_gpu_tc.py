@@ -102,18 +102,6 @@ def test_bf16_network_depths(widths):
 
 
 # ---------------------------------------------------------------- ice, full size
-@pytest.fixture(scope="module")
-def ice_model():
-    w = s.workload("ice")
-    r = w.replicas[0]
-    m = s.xavier_model(s.elements_of(w.replicas), w.widths, seed=7)
-    G = O.descriptors(m, r.x0, r.box)
-    s.set_normalisation(m, G, r.Z)
-    _, F, _ = O.energy_forces(m, r.Z, r.x0, r.box)
-    s.set_energy_scale(m, 1.0 / float(np.sqrt((F ** 2).mean())))
-    return w, r, m
-
-
 @pytest.mark.parametrize("precision", ["bf16_tc", "fp32"])
 def test_ice_full_size_sampled_beads(ice_model, precision):
     """Ice Ih, 1296 atoms x 32 beads (41,472 bead-atoms) in the benchmark's
