@@ -38,10 +38,12 @@ def test_normal_modes_orthogonal_and_diagonalise_springs(P):
     np.testing.assert_allclose(C[:, 0], 1.0 / math.sqrt(P))
 
 
-def _harmonic_system(P, N=1, T=300.0, omega=0.0, dt=0.5, gamma0=0.01, thermostat=True, seed=5):
+def _harmonic_system(P, N=1, T=300.0, omega=0.0, dt=0.5, gamma0=0.01, thermostat=True, seed=5,
+                     splitting="obabo", free_rp="exact"):
     x0 = np.random.default_rng(seed).normal(size=(N, 3)) * 0.1
     rep = s.Replica(np.full(N, s.H, dtype=np.int32), x0, (0.0, 0.0, 0.0), P, T, seed)
-    return O.System(rep, s.MASS, dt, gamma0, thermostat=thermostat, potential="harmonic", omega=omega)
+    return O.System(rep, s.MASS, dt, gamma0, thermostat=thermostat, potential="harmonic", omega=omega,
+                    splitting=splitting, free_rp=free_rp)
 
 
 def test_free_ring_polymer_matches_ode_solver():
@@ -176,3 +178,77 @@ def test_nve_energy_conservation(fad_model):
         assert abs(slope * len(H)) < 3 * H.std() + 1e-12
     ratio = amp[0] / amp[1]
     assert 2.5 < ratio < 6.0, amp
+
+
+# ---------------------------------------------------------------- integrator variants
+@pytest.mark.parametrize("m,w,h", [(1.008, 0.3, 0.25), (15.999, 2.0, 0.5), (1.008, 400.0, 0.5)])
+def test_cayley_free_rp_step_is_a_rotation(m, w, h):
+    """The Cayley transform of h L (L = [[0, -m w^2], [1/m, 0]]) has the
+    eigenvalues (1 + i w h / 2) / (1 - i w h / 2) = exp(+-i theta) with
+    tan(theta / 2) = w h / 2: from (p, q) = (0, 1) one step gives
+    q = cos theta, p = -m w sin theta; the mode energy p^2/2m + m w^2 q^2/2 is
+    conserved for any w h, and a step of -h undoes a step of h."""
+    th = 2.0 * math.atan(0.5 * w * h)
+    p, q = O.free_rp_step("cayley", m, w, h, 0.0, 1.0)
+    assert abs(q - math.cos(th)) < 1e-13
+    assert abs(p + m * w * math.sin(th)) < 1e-13 * m * w
+    p0, q0 = 0.7, -0.3
+
+    def energy(p, q):
+        return p * p / (2 * m) + 0.5 * m * w * w * q * q
+
+    p1, q1 = O.free_rp_step("cayley", m, w, h, p0, q0)
+    assert abs(energy(p1, q1) - energy(p0, q0)) < 1e-13 * energy(p0, q0)
+    p2, q2 = O.free_rp_step("cayley", m, w, -h, p1, q1)
+    assert abs(p2 - p0) < 1e-12 * max(1.0, m * w) and abs(q2 - q0) < 1e-12
+
+
+def test_cayley_free_rp_step_is_second_order_accurate():
+    """Local error against the exact rotation is O(h^3): halving h divides it
+    by ~8 (theta - w h = -(w h)^3 / 12 + ...)."""
+    m, w = 1.008, 0.8
+    errs = []
+    for h in (0.2, 0.1, 0.05):
+        pe, qe = O.free_rp_step("exact", m, w, h, 0.4, 0.9)
+        pc, qc = O.free_rp_step("cayley", m, w, h, 0.4, 0.9)
+        errs.append(abs(qc - qe) + abs(pc - pe) / (m * w))
+    assert 7.5 < errs[0] / errs[1] < 8.5 and 7.5 < errs[1] / errs[2] < 8.5
+    # free drift of the centroid is the same for both
+    assert O.free_rp_step("cayley", m, 0.0, 0.3, 0.5, 1.0) == O.free_rp_step("exact", m, 0.0, 0.3, 0.5, 1.0)
+
+
+def test_baoab_without_thermostat_is_obabo(fad_model):
+    """With the thermostat off both splittings are velocity Verlet: B A(dt/2)
+    A(dt/2) B equals B A(dt) B because the exact free ring-polymer flow
+    composes."""
+    w, r, m = fad_model
+    rep = s.Replica(r.Z, r.x0, r.box, 4, r.T, r.seed, r.name)
+    a = O.System(rep, s.MASS, 0.25, 0.0, model=m, thermostat=False, splitting="obabo")
+    b = O.System(rep, s.MASS, 0.25, 0.0, model=m, thermostat=False, splitting="baoab")
+    a.step(20)
+    b.step(20)
+    assert np.abs(a.q - b.q).max() < 1e-10 * np.abs(a.q).max()
+    assert np.abs(a.p - b.p).max() < 1e-10 * np.abs(a.p).max()
+
+
+@pytest.mark.parametrize("splitting,free_rp", [("baoab", "exact"), ("obabo", "cayley"), ("baoab", "cayley")])
+def test_qho_averages_with_other_integrators(splitting, free_rp):
+    """The P = 4 oscillator averages of the closed form hold for BAOAB and
+    for the Cayley propagator too (within sampling error + O(dt^2))."""
+    P, T, w, N = 4, 300.0, 0.0786, 8
+    sysm = _harmonic_system(P, N, T=T, omega=w, dt=0.25, gamma0=0.08, splitting=splitting, free_rp=free_rp)
+    sysm.step(2000)
+    Ev, x2 = [], []
+    for _ in range(6000):
+        sysm.step(10)
+        Ev.append(sysm.estimators()["E_tot"] / N)
+        x2.append((sysm.beads() ** 2).sum(axis=2).mean())
+    exact = _qho_exact_EP(P, T, w)
+    mean, err = _block_mean(Ev)
+    assert abs(mean - exact) < 4 * err + 0.004 * exact, (mean, err, exact)
+    m = s.MASS[s.H]
+    wP = P * KB * T / HBAR
+    wk = 2 * wP * np.sin(np.arange(P) * np.pi / P)
+    x2_exact = 3 * (KB * T / MVV2E) / m * np.sum(1.0 / (w * w + wk ** 2))
+    mx, ex = _block_mean(x2)
+    assert abs(mx - x2_exact) < 4 * ex + 0.004 * x2_exact
