@@ -308,6 +308,38 @@ const char* pimd_last_error(const pimd_ctx* ctx);
 
 int pimd_abi_version(void);
 
+/* ---- structural analysis of the bead configurations (Sec. 3.2) ------------
+ * Both calls read the bead positions of the last force evaluation (after
+ * pimd_step, pimd_energy_forces or pimd_create) of one replica, run on the
+ * context stream and return without synchronising. Bins are decided in FP32
+ * by the neighbour-list rule: positions rounded to FP32, minimum image in
+ * FP32, r2 = (dx dx + dy dy) + dz dz without contraction; bin edges are
+ * formed in FP64 and rounded to FP32, so counts are reproducible exactly.  */
+
+/* Element numbers of the context's types in type order (ascending Z).
+ * Z: host [PIMD_MAX_ELEMENTS] or NULL. Returns the number of types.       */
+int pimd_element_types(const pimd_ctx* ctx, int* Z);
+
+/* Radial-distribution pair counts (Figs. 8, 9): for every bead of the
+ * replica and every pair i < j with r2 < ((n_bins) dr)^2, dr = r_max/n_bins,
+ * counts[p][k] += 1 where e_k <= r2 < e_(k+1), e_k = (float)((k dr)^2), and
+ * p = a (2T - a - 1) / 2 + b for the pair's types a <= b (T types).
+ * counts: device [T (T + 1) / 2][n_bins] uint64, added to (the caller zeroes
+ * it); g(r) follows by dividing by the ideal-gas pair count of each shell.
+ * Errors: INVALID_ARG (replica, n_bins outside 1..1024, r_max <= 0 or above
+ * half the smallest box edge, histogram larger than 200 KB).              */
+int pimd_rdf_counts(pimd_ctx* ctx, int replica, double r_max, int n_bins, unsigned long long* counts);
+
+/* Proton-transfer coordinate (Fig. 11): for every atom h with bond[h] >= 0
+ * (the replica-local index of its bonding atom), v = d(bond, h) - the
+ * smallest d(j, h) over the atoms j of element acceptor_Z other than the
+ * bonding atom, sqrtf of the rule's r2, difference in FP32. bond: device
+ * [N] int. v: device [P][N] float or NULL (NaN where undefined). hist:
+ * device [n_bins] uint64 or NULL, += 1 where e_k <= v < e_(k+1), e_k =
+ * (float)(v_min + k (v_max - v_min) / n_bins). Errors: INVALID_ARG.        */
+int pimd_pt_coordinate(pimd_ctx* ctx, int replica, const int* bond, int acceptor_Z, double v_min, double v_max,
+                       int n_bins, float* v, unsigned long long* hist);
+
 /* ---- descriptors without any device allocation ------------------------------
  * The paper has no counterpart to this call. It serves callers that cannot
  * allocate device memory at all -- a host engine that reserves the whole GPU

@@ -100,6 +100,10 @@ def lib():
                               dp, dp, dp, dp, dp, dp]
         L.or_estimators.argtypes = [ct.POINTER(OrSys), dp, dp, dp, dp, dp, ct.c_double, ct.POINTER(OrEst)]
         L.or_set_threads.argtypes = [ct.c_int]
+        u64p = ct.POINTER(ct.c_uint64)
+        L.or_rdf_counts.argtypes = [ct.c_int, dp, dp, ip, ct.c_int, ct.c_double, ct.c_int, u64p]
+        L.or_pt_coordinate.argtypes = [ct.c_int, dp, dp, ip, ip, ct.c_double, ct.c_double, ct.c_int,
+                                       ct.POINTER(ct.c_float), u64p]
         L.or_free_rp_step.argtypes = [ct.c_int, ct.c_double, ct.c_double, ct.c_double,
                                       ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.or_get_threads.restype = ct.c_int
@@ -234,6 +238,31 @@ def nm_freqs(P: int, omega_P: float) -> np.ndarray:
     w = np.zeros(P)
     lib().or_nm_freqs(P, omega_P, _dp(w))
     return w
+
+
+def rdf_counts(x, box, types, n_types: int, r_max: float, n_bins: int) -> np.ndarray:
+    """RDF pair counts [n_types (n_types + 1) / 2, n_bins] of one configuration
+    (FP32 distance rule; see or_rdf_counts)."""
+    x = _f64(x)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    out = np.zeros(n_types * (n_types + 1) // 2 * n_bins, dtype=np.uint64)
+    lib().or_rdf_counts(len(t), _dp(x), _dp(_box(box)), _ip(t), int(n_types), float(r_max), int(n_bins),
+                        out.ctypes.data_as(ct.POINTER(ct.c_uint64)))
+    return out.reshape(-1, n_bins)
+
+
+def pt_coordinate(x, box, bond, acceptor, v_min: float, v_max: float, n_bins: int):
+    """Proton-transfer coordinate per atom (NaN for non-protons) and its
+    histogram (see or_pt_coordinate)."""
+    x = _f64(x)
+    b = np.ascontiguousarray(bond, dtype=np.int32)
+    a = np.ascontiguousarray(acceptor, dtype=np.int32)
+    v = np.zeros(len(b), dtype=np.float32)
+    h = np.zeros(n_bins, dtype=np.uint64)
+    lib().or_pt_coordinate(len(b), _dp(x), _dp(_box(box)), _ip(b), _ip(a), float(v_min), float(v_max),
+                           int(n_bins), v.ctypes.data_as(ct.POINTER(ct.c_float)),
+                           h.ctypes.data_as(ct.POINTER(ct.c_uint64)))
+    return v, h
 
 
 def free_rp_step(free_rp: str, m: float, w: float, h: float, p: float, q: float) -> tuple:

@@ -43,38 +43,57 @@ int or_get_threads(void)
 /* ------------------------------------------------------------------------ */
 /* neighbour rule: FP32, no contraction, fixed operation order               */
 /* ------------------------------------------------------------------------ */
+typedef struct {
+    int periodic;
+    float L32[3], inv32[3];
+} box32;
+
+static box32 make_box32(const double* box)
+{
+    box32 b;
+    b.periodic = box != NULL && box[0] > 0.0;
+    for (int d = 0; d < 3; ++d) {
+        b.L32[d] = b.periodic ? (float)box[d] : 0.0f;
+        b.inv32[d] = b.periodic ? (float)(1.0 / box[d]) : 0.0f;
+    }
+    return b;
+}
+
+/* squared minimum-image distance of atoms i and j by the FP32 rule:
+ * x32 = (float)x, t = x32_j - x32_i, t -= L32 rint(t invL32), then
+ * r2 = (tx tx + ty ty) + tz tz, every operation rounded on its own */
+static float r2_f32(const double* x, int i, int j, const box32* b)
+{
+    float dd[3];
+    for (int d = 0; d < 3; ++d) {
+        float t = (float)x[3 * j + d] - (float)x[3 * i + d];
+        if (b->periodic) {
+            float k = rintf(t * b->inv32[d]);
+            float s = b->L32[d] * k;
+            t = t - s;
+        }
+        dd[d] = t;
+    }
+    float r2 = dd[0] * dd[0];
+    float yy = dd[1] * dd[1];
+    float zz = dd[2] * dd[2];
+    r2 = r2 + yy;
+    r2 = r2 + zz;
+    return r2;
+}
+
 int or_neighbours(int n, const double* x, const double* box, double rc, int maxnb,
                   int* nbr, int* nnb)
 {
-    int periodic = box != NULL && box[0] > 0.0;
-    float L32[3], inv32[3];
-    for (int d = 0; d < 3; ++d) {
-        L32[d] = periodic ? (float)box[d] : 0.0f;
-        inv32[d] = periodic ? (float)(1.0 / box[d]) : 0.0f;
-    }
+    box32 b = make_box32(box);
     float rc2 = (float)(rc * rc);
     int worst = 0;
 #pragma omp parallel for num_threads(or_get_threads()) reduction(max : worst) if (!omp_in_parallel())
     for (int i = 0; i < n; ++i) {
-        float xi[3] = {(float)x[3 * i], (float)x[3 * i + 1], (float)x[3 * i + 2]};
         int cnt = 0;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
-            float dd[3];
-            for (int d = 0; d < 3; ++d) {
-                float t = (float)x[3 * j + d] - xi[d];
-                if (periodic) {
-                    float k = rintf(t * inv32[d]);
-                    float s = L32[d] * k;
-                    t = t - s;
-                }
-                dd[d] = t;
-            }
-            float r2 = dd[0] * dd[0];
-            float yy = dd[1] * dd[1];
-            float zz = dd[2] * dd[2];
-            r2 = r2 + yy;
-            r2 = r2 + zz;
+            float r2 = r2_f32(x, i, j, &b);
             if (r2 < rc2) {
                 if (cnt < maxnb) nbr[(size_t)i * maxnb + cnt] = j;
                 ++cnt;
@@ -666,4 +685,70 @@ void or_estimators(const or_sys* s, const double* q_nm, const double* p_nm,
     out->Q_thermo = Q_thermo;
     out->T_kin = 2.0 * kin / (3.0 * N * P * KB);
     free(C); free(xb);
+}
+
+/* ------------------------------------------------------------------------ */
+/* structural analysis of bead configurations (Sec. 3.2, Figs. 8, 9, 11)     */
+/* ------------------------------------------------------------------------ */
+/* Pair counts of the radial distribution function. Element types a <= b
+ * index the pair p = a (2T - a - 1) / 2 + b. A pair i < j at squared FP32
+ * distance r2 (rule of r2_f32) lies in bin k when e_k <= r2 < e_(k+1), with
+ * edges e_k = (float)((k r_max / n_bins)^2) formed in FP64; pairs with r2 >=
+ * e_(n_bins) are not counted. counts[p][k] += the number of such pairs.     */
+void or_rdf_counts(int n, const double* x, const double* box, const int* type, int n_types,
+                   double r_max, int n_bins, unsigned long long* counts)
+{
+    box32 b = make_box32(box);
+    float* e = malloc(sizeof(float) * (n_bins + 1));
+    for (int k = 0; k <= n_bins; ++k) {
+        double rk = k * (r_max / n_bins);
+        e[k] = (float)(rk * rk);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            float r2 = r2_f32(x, i, j, &b);
+            if (!(r2 < e[n_bins])) continue;
+            int k = 0;
+            while (!(r2 < e[k + 1])) ++k;   /* plain scan of the edges */
+            int ta = type[i] < type[j] ? type[i] : type[j];
+            int tb = type[i] < type[j] ? type[j] : type[i];
+            int pidx = ta * (2 * n_types - ta - 1) / 2 + tb;
+            counts[(size_t)pidx * n_bins + k] += 1ull;
+        }
+    free(e);
+}
+
+/* Proton-transfer coordinate (Sec. 3.2, Fig. 11): for every proton h
+ * (bond[h] >= 0, the index of its bonding oxygen), v = d(O_bond, h) -
+ * min over the other acceptors O of d(O, h), acceptors being the atoms with
+ * acceptor[j] != 0. Distances sqrtf(r2_f32) and the difference in FP32
+ * (NaN for non-protons or without another acceptor). hist[k] += 1 when
+ * e_k <= v < e_(k+1), e_k = (float)(v_min + k (v_max - v_min) / n_bins)
+ * formed in FP64 (values outside [e_0, e_(n_bins)) are not counted).        */
+void or_pt_coordinate(int n, const double* x, const double* box, const int* bond, const int* acceptor,
+                      double v_min, double v_max, int n_bins, float* v, unsigned long long* hist)
+{
+    box32 b = make_box32(box);
+    float* e = malloc(sizeof(float) * (n_bins + 1));
+    for (int k = 0; k <= n_bins; ++k) e[k] = (float)(v_min + k * ((v_max - v_min) / n_bins));
+    for (int h = 0; h < n; ++h) {
+        v[h] = NAN;
+        if (bond[h] < 0) continue;
+        float db = sqrtf(r2_f32(x, h, bond[h], &b));
+        float dn = INFINITY;
+        for (int j = 0; j < n; ++j) {
+            if (j == bond[h] || j == h || !acceptor[j]) continue;
+            float d = sqrtf(r2_f32(x, h, j, &b));
+            if (d < dn) dn = d;
+        }
+        if (dn == INFINITY) continue;
+        float vv = db - dn;
+        v[h] = vv;
+        if (hist != NULL && vv >= e[0] && vv < e[n_bins]) {
+            int k = 0;
+            while (!(vv < e[k + 1])) ++k;
+            hist[k] += 1ull;
+        }
+    }
+    free(e);
 }

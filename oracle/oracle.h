@@ -98,6 +98,11 @@ int  or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
 void or_estimators(const or_sys* s, const double* q_nm, const double* p_nm,
                    const double* f, const double* V, const double* W, double Q_thermo,
                    or_est* out);
+/* --- structural analysis (RDF pair counts, proton-transfer coordinate) ---- */
+void or_rdf_counts(int n, const double* x, const double* box, const int* type, int n_types,
+                   double r_max, int n_bins, unsigned long long* counts);
+void or_pt_coordinate(int n, const double* x, const double* box, const int* bond, const int* acceptor,
+                      double v_min, double v_max, int n_bins, float* v, unsigned long long* hist);
 void or_set_threads(int n);
 int  or_get_threads(void);
 

@@ -1063,6 +1063,68 @@ int pimd_sizes(const pimd_ctx* c, int64_t* B, int64_t* S, int* R, int* maxnb)
     return PIMD_OK;
 }
 
+int pimd_element_types(const pimd_ctx* c, int* Z)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    const std::vector<int>& t = c->build.typeZ;
+    if (Z)
+        for (size_t k = 0; k < t.size(); ++k) Z[k] = t[k];
+    return (int)t.size();
+}
+
+namespace {
+int check_replica(pimd_ctx* c, int replica)
+{
+    if (replica < 0 || replica >= c->d.R) return fail(c, PIMD_ERR_INVALID_ARG, "replica out of range");
+    return PIMD_OK;
+}
+}  // namespace
+
+int pimd_rdf_counts(pimd_ctx* c, int replica, double r_max, int n_bins, unsigned long long* counts)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    if (!counts) return fail(c, PIMD_ERR_INVALID_ARG, "counts is NULL");
+    if (n_bins < 1 || n_bins > ANALYSIS_MAX_BINS) return fail(c, PIMD_ERR_INVALID_ARG, "n_bins must be 1..1024");
+    if (!(r_max > 0.0)) return fail(c, PIMD_ERR_INVALID_ARG, "r_max must be > 0");
+    const Rep& rp = c->build.reps[replica];
+    if (rp.periodic) {
+        const double half = 0.5 * std::min(std::min(rp.L[0], rp.L[1]), rp.L[2]);
+        if (r_max > half) return fail(c, PIMD_ERR_INVALID_ARG, "r_max exceeds half the smallest box edge");
+    }
+    if (rdf_smem_bytes(c->d.n_types, n_bins) > 200 * 1024)
+        return fail(c, PIMD_ERR_INVALID_ARG, "too many bins for the element pairs (shared-memory histogram)");
+    BinEdges e;
+    for (int k = 0; k <= n_bins; ++k) {
+        const double rk = k * (r_max / n_bins);
+        e.e[k] = (float)(rk * rk);
+    }
+    launch_rdf(c->d, replica, rp.P, rp.N, e, n_bins, (float)(n_bins / r_max), counts, c->st);
+    return cuda_check(c, cudaGetLastError(), "rdf kernel");
+}
+
+int pimd_pt_coordinate(pimd_ctx* c, int replica, const int* bond, int acceptor_Z, double v_min, double v_max,
+                       int n_bins, float* v, unsigned long long* hist)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    if (!bond) return fail(c, PIMD_ERR_INVALID_ARG, "bond is NULL");
+    if (!v && !hist) return fail(c, PIMD_ERR_INVALID_ARG, "v and hist are both NULL");
+    if (n_bins < 1 || n_bins > ANALYSIS_MAX_BINS) return fail(c, PIMD_ERR_INVALID_ARG, "n_bins must be 1..1024");
+    if (!(v_max > v_min)) return fail(c, PIMD_ERR_INVALID_ARG, "v_max must exceed v_min");
+    const std::vector<int>& tz = c->build.typeZ;
+    const auto it = std::find(tz.begin(), tz.end(), acceptor_Z);
+    if (it == tz.end()) return fail(c, PIMD_ERR_INVALID_ARG, "acceptor_Z is not an element of the context");
+    const Rep& rp = c->build.reps[replica];
+    BinEdges e;
+    for (int k = 0; k <= n_bins; ++k) e.e[k] = (float)(v_min + k * ((v_max - v_min) / n_bins));
+    launch_pt(c->d, replica, rp.P, rp.N, bond, (int)(it - tz.begin()), e, n_bins, (float)(n_bins / (v_max - v_min)),
+              v, hist, c->st);
+    return cuda_check(c, cudaGetLastError(), "proton-transfer kernel");
+}
+
 void pimd_destroy(pimd_ctx* c)
 {
     if (!c) return;

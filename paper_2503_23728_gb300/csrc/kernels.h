@@ -84,6 +84,12 @@ struct Dev {
 
 constexpr int EST_STRIDE = 24;
 
+// histogram bin edges passed by value to the analysis kernels
+constexpr int ANALYSIS_MAX_BINS = 1024;
+struct BinEdges {
+    float e[ANALYSIS_MAX_BINS + 1];
+};
+
 size_t blob_elems(int n_hidden, const int* widths);
 
 // force evaluation pieces
@@ -104,6 +110,13 @@ void launch_descriptors_out(const Dev& d, double* G, cudaStream_t st);
 bool network_tc_supported(int width, int n_hidden);
 size_t tc_weight_bytes(int width, int n_hidden);
 void prepare_tc_weights(const Dev& d, int type, const double* blob, void* host_img, float* host_vec);
+
+// structural analysis
+size_t rdf_smem_bytes(int n_types, int n_bins);
+void launch_rdf(const Dev& d, int rep, int P, int N, const BinEdges& edges, int n_bins, float inv_dr,
+                unsigned long long* counts, cudaStream_t st);
+void launch_pt(const Dev& d, int rep, int P, int N, const int* bond, int t_acc, const BinEdges& edges, int n_bins,
+               float inv_w, float* v_out, unsigned long long* hist, cudaStream_t st);
 
 // message returned by pimd_last_error(NULL) on this thread
 void set_thread_error(const std::string& msg);

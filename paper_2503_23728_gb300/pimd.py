@@ -23,7 +23,8 @@ POT_MODEL, POT_HARMONIC = 0, 1
 EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_weights", "pimd_step",
            "pimd_energy_forces", "pimd_descriptors", "pimd_estimators", "pimd_get_state", "pimd_set_state",
            "pimd_get_forces", "pimd_get_neighbours", "pimd_sync", "pimd_sizes", "pimd_destroy", "pimd_last_error",
-           "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule", "pimd_set_angular", "pimd_get_angular"]
+           "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule", "pimd_set_angular", "pimd_get_angular",
+           "pimd_element_types", "pimd_rdf_counts", "pimd_pt_coordinate"]
 ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
@@ -110,6 +111,10 @@ def load(path: str = LIB_PATH):
     L.pimd_set_angular.argtypes = [vp, ct.c_int]
     L.pimd_get_angular.argtypes = [vp]
     L.pimd_get_angular.restype = ct.c_int
+    L.pimd_element_types.argtypes = [vp, ct.POINTER(ct.c_int)]
+    L.pimd_element_types.restype = ct.c_int
+    L.pimd_rdf_counts.argtypes = [vp, ct.c_int, ct.c_double, ct.c_int, vp]
+    L.pimd_pt_coordinate.argtypes = [vp, ct.c_int, vp, ct.c_int, ct.c_double, ct.c_double, ct.c_int, vp, vp]
     L.pimd_descriptors_noalloc.argtypes = [vp, ct.c_int, dp, ct.c_double, ct.c_double, dp, dp, vp, vp]
     _lib = L
     return L
@@ -224,6 +229,45 @@ def pimd_set_angular(ctx, algo):
 
 def pimd_get_angular(ctx) -> str:
     return {0: "pairs", 1: "moments"}[int(load().pimd_get_angular(ctx))]
+
+
+def pimd_element_types(ctx) -> list:
+    z = (ct.c_int * 8)()
+    n = int(load().pimd_element_types(ctx, z))
+    if n < 0:
+        _check(n, ctx)
+    return [int(z[k]) for k in range(n)]
+
+
+def pimd_rdf_counts(ctx, replica: int, r_max: float, n_bins: int, counts_ptr):
+    _check(load().pimd_rdf_counts(ctx, int(replica), float(r_max), int(n_bins), ct.c_void_p(counts_ptr)), ctx)
+
+
+def pimd_pt_coordinate(ctx, replica: int, bond_ptr, acceptor_Z: int, v_min: float, v_max: float, n_bins: int,
+                       v_ptr, hist_ptr):
+    _check(load().pimd_pt_coordinate(ctx, int(replica), ct.c_void_p(bond_ptr), int(acceptor_Z), float(v_min),
+                                     float(v_max), int(n_bins), ct.c_void_p(v_ptr) if v_ptr else None,
+                                     ct.c_void_p(hist_ptr) if hist_ptr else None), ctx)
+
+
+def rdf_normalize(counts, n_per_type, volume: float, r_max: float, n_configs: int):
+    """g(r) per element pair from pair counts [T (T + 1) / 2, n_bins] summed
+    over n_configs configurations: counts / (ideal-gas pairs in the shell),
+    the ideal count being n_a n_b (a != b) or n_a (n_a - 1) / 2 (a = b) times
+    the shell volume over the box volume."""
+    counts = np.asarray(counts, dtype=np.float64)
+    T = len(n_per_type)
+    n_bins = counts.shape[1]
+    edges = np.arange(n_bins + 1) * (r_max / n_bins)
+    shell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    g = np.zeros_like(counts)
+    p = 0
+    for a in range(T):
+        for b in range(a, T):
+            pairs = n_per_type[a] * (n_per_type[a] - 1) / 2 if a == b else n_per_type[a] * n_per_type[b]
+            g[p] = counts[p] / (n_configs * pairs * shell / volume)
+            p += 1
+    return g
 
 
 def pimd_kernels_per_step(ctx) -> int:
@@ -442,6 +486,34 @@ class Context:
 
     def set_angular(self, algo: str):
         pimd_set_angular(self.h, algo)
+
+    def element_types(self) -> list:
+        return pimd_element_types(self.h)
+
+    def rdf_counts(self, r_max: float, n_bins: int, replica: int = 0, counts=None):
+        """Pair counts of every bead of one replica (device uint64 tensor
+        [T (T + 1) / 2, n_bins], accumulated into counts if given)."""
+        torch = self.torch
+        T = len(self.element_types())
+        if counts is None:
+            counts = torch.zeros((T * (T + 1) // 2, n_bins), dtype=torch.int64, device="cuda")
+        pimd_rdf_counts(self.h, replica, r_max, n_bins, counts.data_ptr())
+        return counts
+
+    def pt_coordinate(self, bond, acceptor_Z: int = 8, v_range=(-2.0, 1.0), n_bins: int = 60, replica: int = 0):
+        """Proton-transfer coordinate of every bead of one replica: (v [P, N]
+        float tensor, NaN for non-protons; histogram int64 tensor [n_bins]).
+        bond: per atom the replica-local index of its bonding atom, -1 for
+        atoms that are not protons."""
+        torch = self.torch
+        rep = self.replicas[replica]
+        b = torch.as_tensor(np.asarray(bond, dtype=np.int32), device="cuda")
+        v = torch.empty((rep.n_beads, rep.n_atoms), dtype=torch.float32, device="cuda")
+        h = torch.zeros(n_bins, dtype=torch.int64, device="cuda")
+        pimd_pt_coordinate(self.h, replica, b.data_ptr(), acceptor_Z, v_range[0], v_range[1], n_bins, v.data_ptr(),
+                           h.data_ptr())
+        self.torch.cuda.current_stream().synchronize() if self.stream is None else self.stream.synchronize()
+        return v, h
 
     @property
     def angular(self) -> str:
