@@ -42,6 +42,69 @@ class OrModel(ct.Structure):
     ]
 
 
+class OrMetad(ct.Structure):
+    _fields_ = [("cv", ct.c_int), ("n_terms", ct.c_int), ("ti", ct.c_int * 8), ("tj", ct.c_int * 8),
+                ("tc", ct.c_double * 8), ("Q", ct.c_double), ("f_atom", ct.POINTER(ct.c_double)),
+                ("h0", ct.c_double), ("sigma", ct.c_double), ("gamma", ct.c_double), ("stride", ct.c_int),
+                ("max_hills", ct.c_int), ("hill_s", ct.POINTER(ct.c_double)), ("hill_h", ct.POINTER(ct.c_double)),
+                ("n_hills", ct.c_int), ("cv_last", ct.POINTER(ct.c_double)), ("vb_last", ct.POINTER(ct.c_double))]
+
+
+class Metad:
+    """Well-tempered metadynamics state for one system (oracle side).
+    cv = ("distances", [(i, j, c), ...]) or ("xrd", Q, f_atom)."""
+
+    def __init__(self, cv, n_atoms: int, n_beads: int, h0: float, sigma: float, gamma: float, stride: int,
+                 max_hills: int = 4096):
+        m = OrMetad()
+        if cv[0] == "distances":
+            m.cv = 1
+            m.n_terms = len(cv[1])
+            for t, (i, j, c) in enumerate(cv[1]):
+                m.ti[t], m.tj[t], m.tc[t] = int(i), int(j), float(c)
+            self.f = None
+        else:
+            m.cv = 2
+            m.Q = float(cv[1])
+            self.f = _f64(cv[2])
+            m.f_atom = _dp(self.f)
+        m.h0, m.sigma, m.gamma, m.stride, m.max_hills = float(h0), float(sigma), float(gamma), int(stride), int(max_hills)
+        self.hs = np.zeros(max_hills)
+        self.hh = np.zeros(max_hills)
+        self.cv_last = np.zeros(n_beads)
+        self.vb_last = np.zeros(n_beads)
+        m.hill_s, m.hill_h = _dp(self.hs), _dp(self.hh)
+        m.cv_last, m.vb_last = _dp(self.cv_last), _dp(self.vb_last)
+        m.n_hills = 0
+        self.m = m
+        self.n_atoms = n_atoms
+
+    @property
+    def hills(self):
+        n = self.m.n_hills
+        return self.hs[:n].copy(), self.hh[:n].copy()
+
+    def cv(self, x, box, grad: bool = False):
+        """(s, ds/dx [n,3] or None, vir [3,3] or None) of one configuration"""
+        x = _f64(x)
+        g = np.zeros((self.n_atoms, 3)) if grad else None
+        v = np.zeros(9) if grad else None
+        s = lib().or_cv(ct.byref(self.m), self.n_atoms, _dp(x), _dp(_box(box)), _dp(g) if grad else None,
+                        _dp(v) if grad else None)
+        return s, g, (v.reshape(3, 3) if grad else None)
+
+    def deposit(self, cv_last, vb_last, T: float):
+        """one deposition from given per-bead CVs and biases"""
+        self.cv_last[:] = cv_last
+        self.vb_last[:] = vb_last
+        lib().or_metad_deposit(ct.byref(self.m), len(self.cv_last), float(T))
+
+    def bias(self, s: float):
+        dv = ct.c_double(0.0)
+        v = lib().or_metad_bias(ct.byref(self.m), float(s), ct.byref(dv))
+        return v, dv.value
+
+
 class OrSys(ct.Structure):
     _fields_ = [
         ("N", ct.c_int), ("P", ct.c_int),
@@ -60,6 +123,7 @@ class OrSys(ct.Structure):
         ("maxnb", ct.c_int),
         ("splitting", ct.c_int),
         ("free_rp", ct.c_int),
+        ("metad", ct.POINTER(OrMetad)),
     ]
 
 
@@ -104,6 +168,11 @@ def lib():
         L.or_rdf_counts.argtypes = [ct.c_int, dp, dp, ip, ct.c_int, ct.c_double, ct.c_int, u64p]
         L.or_pt_coordinate.argtypes = [ct.c_int, dp, dp, ip, ip, ct.c_double, ct.c_double, ct.c_int,
                                        ct.POINTER(ct.c_float), u64p]
+        L.or_cv.argtypes = [ct.POINTER(OrMetad), ct.c_int, dp, dp, dp, dp]
+        L.or_cv.restype = ct.c_double
+        L.or_metad_bias.argtypes = [ct.POINTER(OrMetad), ct.c_double, ct.POINTER(ct.c_double)]
+        L.or_metad_bias.restype = ct.c_double
+        L.or_metad_deposit.argtypes = [ct.POINTER(OrMetad), ct.c_int, ct.c_double]
         L.or_free_rp_step.argtypes = [ct.c_int, ct.c_double, ct.c_double, ct.c_double,
                                       ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.or_get_threads.restype = ct.c_int
@@ -294,7 +363,7 @@ class System:
     def __init__(self, replica, masses: dict, dt: float, gamma0: float, pile_lambda: float = 1.0,
                  model=None, thermostat: bool = True, potential: str = "model", omega: float = 0.0,
                  replica_index: int = 0, maxnb: int = 256, splitting: str = "obabo",
-                 free_rp: str = "exact"):
+                 free_rp: str = "exact", metad: "Metad" = None):
         self.mh = None if model is None else (model if isinstance(model, ModelHandle) else ModelHandle(model))
         self.Z = np.ascontiguousarray(replica.Z, dtype=np.int32)
         self.mass = _f64([masses[int(z)] for z in replica.Z])
@@ -317,6 +386,9 @@ class System:
         s.maxnb = int(maxnb)
         s.splitting = {"obabo": 0, "baoab": 1}[splitting]
         s.free_rp = {"exact": 0, "cayley": 1}[free_rp]
+        self.metad = metad
+        if metad is not None:
+            s.metad = ct.pointer(metad.m)
         self.s = s
         self.N, self.P = N, P
         self.q = np.zeros((P, N, 3))

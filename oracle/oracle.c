@@ -467,6 +467,108 @@ static void to_beads(const or_sys* s, const double* C, const double* q_nm, doubl
             }
 }
 
+/* ------------------------------------------------------------------------ */
+/* collective variables and well-tempered metadynamics (Sec. 2.5)            */
+/* ------------------------------------------------------------------------ */
+static double sinc(double y) { return sin(y) / y; }
+static double dsinc(double y) { return (y * cos(y) - sin(y)) / (y * y); }
+
+/* CV of one configuration. cv 1: s = sum_t c_t |r_(i_t j_t)|; cv 2 (XRD
+ * intensity, Sec. S3): s = (1/N) sum_i sum_j f_i f_j sin(Q R_ij) / (Q R_ij)
+ * with the i = j terms f_i^2. R_ij are minimum-image distances. grad
+ * [n][3] = ds/dx (may be NULL); vir [9] = sum over the pairs of r_ij (x)
+ * ds/dr_ij, r_ij = x_j - x_i (may be NULL). */
+double or_cv(const or_metad* md, int n, const double* x, const double* box, double* grad, double* vir)
+{
+    if (grad) memset(grad, 0, sizeof(double) * 3 * n);
+    if (vir) memset(vir, 0, sizeof(double) * 9);
+    double s = 0.0;
+    if (md->cv == 1) {
+        for (int t = 0; t < md->n_terms; ++t) {
+            int i = md->ti[t], j = md->tj[t];
+            double r[3];
+            min_image(x + 3 * i, x + 3 * j, box, r);
+            double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            s += md->tc[t] * d;
+            for (int a = 0; a < 3; ++a) {
+                double g = md->tc[t] * r[a] / d;   /* ds/dr_ij */
+                if (grad) {
+                    grad[3 * j + a] += g;
+                    grad[3 * i + a] -= g;
+                }
+                if (vir)
+                    for (int b = 0; b < 3; ++b) vir[3 * b + a] += r[b] * g;
+            }
+        }
+        return s;
+    }
+    for (int i = 0; i < n; ++i) s += md->f_atom[i] * md->f_atom[i];
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            double r[3];
+            min_image(x + 3 * i, x + 3 * j, box, r);
+            double R = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            double ff = md->f_atom[i] * md->f_atom[j];
+            s += 2.0 * ff * sinc(md->Q * R);
+            double c = 2.0 * ff * md->Q * dsinc(md->Q * R) / (n * R);   /* ds/dr_ij = c r_ij */
+            for (int a = 0; a < 3; ++a) {
+                if (grad) {
+                    grad[3 * j + a] += c * r[a];
+                    grad[3 * i + a] -= c * r[a];
+                }
+                if (vir)
+                    for (int b = 0; b < 3; ++b) vir[3 * b + a] += r[b] * c * r[a];
+            }
+        }
+    return s / n;
+}
+
+/* V(s) = sum_k h_k exp(-(s - s_k)^2 / (2 sigma^2)) and dV/ds */
+double or_metad_bias(const or_metad* md, double s, double* dVds)
+{
+    double v = 0.0, dv = 0.0;
+    for (int k = 0; k < md->n_hills; ++k) {
+        double u = s - md->hill_s[k];
+        double g = md->hill_h[k] * exp(-0.5 * u * u / (md->sigma * md->sigma));
+        v += g;
+        dv -= g * u / (md->sigma * md->sigma);
+    }
+    if (dVds) *dVds = dv;
+    return v;
+}
+
+/* one deposition: a hill at every bead's CV of the last evaluation, height
+ * (h0 / P) exp(-V(s_k) / (k_B T (gamma - 1))) with the bias before this
+ * deposition (the well-tempered rule of Sec. 2.5, shared over the P beads) */
+void or_metad_deposit(or_metad* md, int P, double T)
+{
+    if (md->n_hills + P > md->max_hills) return;
+    int base = md->n_hills;
+    for (int k = 0; k < P; ++k) {
+        md->hill_s[base + k] = md->cv_last[k];
+        md->hill_h[base + k] = md->h0 / P * exp(-md->vb_last[k] / (KB * T * (md->gamma - 1.0)));
+    }
+    md->n_hills += P;
+}
+
+/* bias of every bead: V_k += V(s_k), f_k -= dV/ds ds/dx, W_k -= dV/ds vir */
+static void add_bias(const or_sys* s, const double* xb, double* f, double* V, double* W)
+{
+    int N = s->N, P = s->P;
+    double* g = malloc(sizeof(double) * 3 * N);
+    for (int j = 0; j < P; ++j) {
+        double vir[9], dv;
+        double cv = or_cv(s->metad, N, xb + (size_t)j * N * 3, s->box, g, vir);
+        double vb = or_metad_bias(s->metad, cv, &dv);
+        s->metad->cv_last[j] = cv;
+        s->metad->vb_last[j] = vb;
+        V[j] += vb;
+        for (int q = 0; q < 3 * N; ++q) f[(size_t)j * N * 3 + q] -= dv * g[q];
+        for (int q = 0; q < 9; ++q) W[9 * j + q] -= dv * vir[q];
+    }
+    free(g);
+}
+
 int or_forces(const or_sys* s, const or_model* m, const double* q_nm,
               double* xb, double* f, double* V, double* W)
 {
@@ -494,6 +596,7 @@ int or_forces(const or_sys* s, const or_model* m, const double* q_nm,
                     W[9 * j + 3 * a + b2] = w;
                 }
         }
+        if (s->metad != NULL) add_bias(s, xb, f, V, W);
         return 0;
     }
     double* E = malloc(sizeof(double) * N);
@@ -507,6 +610,7 @@ int or_forces(const or_sys* s, const or_model* m, const double* q_nm,
         V[j] = v;
     }
     free(E);
+    if (rc >= 0 && s->metad != NULL) add_bias(s, xb, f, V, W);
     return rc;
 }
 
@@ -611,6 +715,10 @@ int or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
         }
         rc = or_forces(s, m, q_nm, xb, f, V, W);
         if (rc < 0) break;
+        /* hills go down after the force evaluation of step n when (n + 1) is a
+           multiple of the stride; they act from the next evaluation on */
+        if (s->metad != NULL && ((uint64_t)st + 1) % (uint64_t)s->metad->stride == 0)
+            or_metad_deposit(s->metad, P, s->T);
         step_B(s, C, f, p_nm);
         if (s->thermostat && s->splitting != 1) step_O(s, wk, 0.5 * s->dt, st, 3u, p_nm, Q_thermo);
         *step += 1;

@@ -43,6 +43,27 @@ typedef struct {
     double eta_A[4];
 } or_model;
 
+/* Well-tempered metadynamics on one collective variable of every bead
+ * (Sec. 2.5; CVs of Secs. S2-S3). State (hills) lives in the struct.      */
+typedef struct {
+    int cv;                  /* 1 = sum_t c_t d(i_t, j_t), 2 = XRD intensity  */
+    int n_terms;             /* cv 1: terms (<= 8)                           */
+    int ti[8], tj[8];
+    double tc[8];
+    double Q;                /* cv 2: scattering vector magnitude, 1/A       */
+    const double* f_atom;    /* cv 2: [N] atomic scattering factors           */
+    double h0;               /* initial Gaussian height, eV                  */
+    double sigma;            /* Gaussian width (standard deviation), CV units */
+    double gamma;            /* bias factor (> 1)                            */
+    int stride;              /* steps between depositions                    */
+    int max_hills;
+    double* hill_s;          /* [max_hills] centres                          */
+    double* hill_h;          /* [max_hills] heights, eV                      */
+    int n_hills;
+    double* cv_last;         /* [P] CV of each bead at the last evaluation   */
+    double* vb_last;         /* [P] bias of each bead at the last evaluation */
+} or_metad;
+
 /* One ring-polymer system and its integrator settings. */
 typedef struct {
     int N, P;
@@ -61,6 +82,7 @@ typedef struct {
     int maxnb;               /* neighbour slots per atom                     */
     int splitting;           /* 0 = OBABO, 1 = BAOAB                         */
     int free_rp;             /* free ring-polymer step: 0 = exact, 1 = Cayley */
+    or_metad* metad;         /* NULL = no bias                               */
 } or_sys;
 
 /* estimator record, all eV except T_kin (K) */
@@ -98,6 +120,11 @@ int  or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
 void or_estimators(const or_sys* s, const double* q_nm, const double* p_nm,
                    const double* f, const double* V, const double* W, double Q_thermo,
                    or_est* out);
+/* --- collective variables and the metadynamics bias ----------------------- */
+double or_cv(const or_metad* md, int n, const double* x, const double* box, double* grad, double* vir);
+double or_metad_bias(const or_metad* md, double s, double* dVds);
+void or_metad_deposit(or_metad* md, int P, double T);
+
 /* --- structural analysis (RDF pair counts, proton-transfer coordinate) ---- */
 void or_rdf_counts(int n, const double* x, const double* box, const int* type, int n_types,
                    double r_max, int n_bins, unsigned long long* counts);

@@ -122,6 +122,15 @@ def fad_template() -> tuple[np.ndarray, np.ndarray]:
     return Z, x
 
 
+def fad_dimer_cv_terms() -> list:
+    """Double-proton-transfer CV of the dimer (Sec. 3.1):
+    s = d(O1,H1) - d(O2,H1) + d(O4,H2) - d(O3,H2), each proton's bonding
+    oxygen with +1 and its hydrogen-bond acceptor with -1, as (i, j, c) over
+    the template's atom order (H1 = 3 bonded to O 1, accepted by O 7; H2 = 8
+    bonded to O 6, accepted by O 2)."""
+    return [(1, 3, 1.0), (7, 3, -1.0), (6, 8, 1.0), (2, 8, -1.0)]
+
+
 def fad(seed: int = 1001, n_beads: int = 16, T: float = 300.0, jitter: float = 0.05) -> Replica:
     rng = np.random.default_rng(seed)
     Z, x = fad_template()
