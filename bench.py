@@ -55,6 +55,7 @@ def args():
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default pair schedule")
+    ap.add_argument("--no-extras", action="store_true", help="skip the analysis / metadynamics timings")
     return ap.parse_args()
 
 
@@ -231,6 +232,93 @@ def e2e_host(a, ctx, stream, barrier):
     return ms, ctx.B * 3 * 8, ctx.B * 3 * 8 + ctx.S * 8
 
 
+# algorithmic FP32 operations per pair of the analysis kernels: the FP32
+# pair rule (3 differences, 3 x (scale, round, scale, subtract), 3 squares,
+# 2 adds) = 20, plus the bin choice (sqrt, scale) for the RDF
+RDF_FLOP_PER_PAIR = 22
+XRD_FLOP_PER_PAIR = 40   # pair vector 20, sqrt, sincos, sinc and sinc' 9, gradient 6, virial 9 (counted as 40)
+
+
+def time_call(fn, stream, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(reps):
+        fn()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def analysis_extras(ctx, w, stream):
+    """Timed once per run, outside the step: RDF pair counts and the
+    proton-transfer coordinate of every bead of the first replica, with
+    their pair throughput against the FP32 ALU peak."""
+    import torch
+    rep = w.replicas[0]
+    box = np.asarray(rep.box, dtype=float)
+    r_max = min(8.0, 0.5 * box.min()) if box[0] > 0 else 8.0
+    counts = torch.zeros((3, 400), dtype=torch.int64, device="cuda")
+    ms = time_call(lambda: ctx.rdf_counts(r_max, 400, counts=counts), stream)
+    pairs = rep.n_beads * rep.n_atoms * (rep.n_atoms - 1) / 2
+    out = {"rdf": {"ms": ms, "pairs": pairs, "pairs_per_s": pairs / (ms / 1e3),
+                   "achieved_tflops": RDF_FLOP_PER_PAIR * pairs / (ms / 1e3) / 1e12,
+                   "frac_fp32_peak": RDF_FLOP_PER_PAIR * pairs / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                   "config": {"r_max_A": r_max, "bins": 400, "beads": rep.n_beads, "atoms": rep.n_atoms}}}
+    if 1 in set(rep.Z.tolist()) and 8 in set(rep.Z.tolist()):
+        x, L = rep.x0, box
+        acc = np.where(rep.Z == 8)[0]
+        bond = np.full(rep.n_atoms, -1, dtype=np.int32)
+        for h in np.where(rep.Z == 1)[0]:
+            d = x[acc] - x[h]
+            d -= L * np.round(d / L)
+            bond[h] = acc[np.argmin((d ** 2).sum(axis=1))]
+        ms2 = time_call(lambda: ctx.pt_coordinate(bond, 8, (-2.5, 0.5), 60), stream)
+        n_pairs = rep.n_beads * int((rep.Z == 1).sum()) * rep.n_atoms
+        out["pt"] = {"ms": ms2, "pairs_scanned": n_pairs, "pairs_per_s": n_pairs / (ms2 / 1e3),
+                     "note": "includes the host-side bond upload and one stream synchronisation per call"}
+    return out
+
+
+def metad_extras(w, stream):
+    """WT-MetaD with the XRD CV (Sec. S3 settings: theta 11.95 deg, lambda
+    1.54 A, bias factor 60, f = Z) on the same system: the per-step cost of
+    the CV, bias and bias force, from the stage times of a biased and an
+    unbiased context (BF16 network)."""
+    import math
+    from paper_2503_23728_gb300 import pimd as P
+    Q = 4 * math.pi * math.sin(math.radians(11.95)) / 1.54
+    rep = w.replicas[0]
+    md = P.make_metad(("xrd", Q, {1: 1.0, 6: 6.0, 8: 8.0}), 0.0104, 0.5, 60.0, 100, 4096,
+                      elements=sorted(set(rep.Z.tolist())))
+    out = {}
+    for name, m in (("plain", None), ("xrd_metad", md)):
+        ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="bf16_tc", widths=w.widths, timing=True,
+                        metad=m)
+        model = s_model(w)
+        ctx.set_weights(model)
+        ctx.step(3)
+        acc = []
+        for _ in range(10):
+            ctx.step(1)
+            acc.append(ctx.stage_times())
+        out[name] = float(np.median([a["energy"] for a in acc]))
+        ctx.close()
+    pairs = rep.n_beads * rep.n_atoms * (rep.n_atoms - 1)
+    ms = out["xrd_metad"] - out["plain"]
+    return {"xrd_metad_ms_per_step": ms, "energy_stage_ms": out, "pairs_per_step": pairs,
+            "achieved_tflops": XRD_FLOP_PER_PAIR * pairs / max(ms, 1e-6) / 1e9,
+            "frac_fp32_peak": XRD_FLOP_PER_PAIR * pairs / max(ms, 1e-6) / 1e9 / FP32_PEAK_TFLOPS}
+
+
+def s_model(w):
+    from paper_2503_23728_gb300 import synth as s
+    return s.xavier_model(s.elements_of(w.replicas), w.widths, seed=7)
+
+
 def cpu_baseline(workload, model, budget_s=15.0):
     """FP64 oracle on the host cores: force evaluations of whole beads of the
     same workload until ~budget_s of CPU work."""
@@ -333,6 +421,10 @@ def main():
     except Exception:
         pass
     e2e_ms, h2d, d2h = e2e_host(a, ctx, stream, barrier)
+    extras = None
+    if not a.no_extras and world == 1:
+        extras = analysis_extras(ctx, w, stream)
+        extras["metad"] = metad_extras(w, stream)
     launches = ctx.kernels_per_step() * a.steps
     fp32 = None
     if not a.no_fp32 and a.precision != "fp32":
@@ -371,6 +463,7 @@ def main():
         "e2e": {"value": world * w.bead_atoms / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "what": "pimd_energy_forces with host positions in, forces out"},
         "gpu_launches": launches,
+        "next_rows": extras,
     }
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, model)

@@ -61,7 +61,8 @@ typedef enum {
     PIMD_ERR_NONFINITE = -5,
     PIMD_ERR_TIMEOUT = -6,
     PIMD_ERR_NBR_OVERFLOW = -7,
-    PIMD_ERR_UNSUPPORTED = -8
+    PIMD_ERR_UNSUPPORTED = -8,
+    PIMD_ERR_METAD_FULL = -9
 } pimd_status;
 
 /* arithmetic of the force evaluation */
@@ -101,6 +102,39 @@ typedef enum {
     PIMD_POT_HARMONIC = 1   /* V = sum_i 1/2 m_i omega^2 |x_i|^2 (Sec. S1 test case) */
 } pimd_potential;
 
+/* ---- well-tempered metadynamics (Sec. 2.5) --------------------------------
+ * A bias V(s) = sum_k h_k exp(-(s - s_k)^2 / (2 sigma^2)) on a collective
+ * variable s of every bead; each replica keeps its own hills. Hills go down
+ * after the force evaluation of step n when (n + 1) % stride == 0: one per
+ * bead at its CV, height (h0 / P) exp(-V(s_k) / (k_B T (gamma - 1))) with
+ * the bias before the deposition, T the replica's physical temperature.
+ * They act from the next force evaluation on. The bias enters each bead's
+ * potential, forces and virial (and so the estimators).                     */
+enum {
+    PIMD_CV_NONE = 0,
+    PIMD_CV_DISTANCES = 1,   /* s = sum_t c_t |x_(j_t) - x_(i_t)| (minimum image);
+                                e.g. the dimer's proton-transfer CV (Sec. 3.1)  */
+    PIMD_CV_XRD = 2          /* s = (1/N) sum_i sum_j f_i f_j sin(Q R_ij) / (Q R_ij),
+                                i = j terms f_i^2 (Sec. S3)                      */
+};
+
+typedef struct {
+    int cv;                  /* PIMD_CV_*                                       */
+    int n_terms;             /* DISTANCES: 1..8 terms                           */
+    int term_i[8], term_j[8];/* DISTANCES: replica-local atom indices           */
+    double term_c[8];        /* DISTANCES: coefficients                         */
+    double xrd_Q;            /* XRD: |Q| = 4 pi sin(theta) / lambda, 1/A        */
+    double xrd_f[PIMD_MAX_ELEMENTS]; /* XRD: scattering factor of each element
+                                in ascending-Z order (pimd_element_types)      */
+    double height_eV;        /* h0 > 0                                          */
+    double sigma;            /* Gaussian width > 0, CV units                    */
+    double bias_factor;      /* gamma > 1                                       */
+    int stride;              /* steps between depositions >= 1                  */
+    int max_hills;           /* hill capacity per replica (a deposition adds P);
+                                a deposition that does not fit sets
+                                PIMD_ERR_METAD_FULL at the next sync            */
+} pimd_metad_desc;
+
 typedef struct {
     double dt_fs;            /* time step                                          */
     double gamma0_per_fs;    /* PILE-L centroid friction 1/tau_0                   */
@@ -130,6 +164,8 @@ typedef struct {
                                 0: atomic force accumulation (faster).           */
     int splitting;           /* pimd_splitting: order of the step's sub-steps    */
     int free_rp;             /* pimd_free_rp: free ring-polymer propagator       */
+    const pimd_metad_desc* metad; /* NULL: no bias. Read during pimd_workspace_size
+                                and pimd_create only.                          */
 } pimd_config;
 
 /* stages of one step, in launch order (pimd_stage_times) */
@@ -307,6 +343,17 @@ void pimd_destroy(pimd_ctx* ctx);
 const char* pimd_last_error(const pimd_ctx* ctx);
 
 int pimd_abi_version(void);
+
+/* ---- metadynamics state (contexts created with cfg.metad) ---------------
+ * pimd_metad_hills: copies up to capacity hills of the replica (centres s,
+ * heights h, host arrays or NULL) and returns the number of hills (>= 0) or
+ * an error (< 0; STATE without a bias). pimd_metad_set_hills replaces them
+ * (checkpoint / resume; n <= max_hills). pimd_metad_cv: CV and bias of every
+ * bead-system at the last force evaluation, host [S] arrays or NULL.
+ * All three synchronise the context stream.                                */
+int pimd_metad_hills(pimd_ctx* ctx, int replica, double* s, double* h, int capacity);
+int pimd_metad_set_hills(pimd_ctx* ctx, int replica, const double* s, const double* h, int n);
+int pimd_metad_cv(pimd_ctx* ctx, double* cv, double* bias);
 
 /* ---- structural analysis of the bead configurations (Sec. 3.2) ------------
  * Both calls read the bead positions of the last force evaluation (after

@@ -74,7 +74,8 @@ struct Carve {
 struct Offsets {
     size_t reps, bsys, ba_sys, mass, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
-        fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
+        fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
+        md_virpart, md_grad, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
 };
 
 int check_config(const pimd_config* cfg, std::string& e)
@@ -170,6 +171,27 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
     if ((int)zs.size() > PIMD_MAX_ELEMENTS) { e = "more than 8 elements"; return PIMD_ERR_UNSUPPORTED; }
     b.typeZ = zs;
     b.R = n; b.S = (int)S; b.B = (int)B; b.NA = (int)NA;
+    if (cfg->metad && cfg->metad->cv != PIMD_CV_NONE) {
+        const pimd_metad_desc* m = cfg->metad;
+        int minN = 1 << 30, maxP = 1;
+        for (int r = 0; r < n; ++r) { minN = std::min(minN, hr[r].N); maxP = std::max(maxP, hr[r].P); }
+        if (m->cv != PIMD_CV_DISTANCES && m->cv != PIMD_CV_XRD) { e = "metad: unknown cv"; return PIMD_ERR_INVALID_ARG; }
+        if (m->cv == PIMD_CV_DISTANCES) {
+            if (m->n_terms < 1 || m->n_terms > 8) { e = "metad: n_terms must be 1..8"; return PIMD_ERR_INVALID_ARG; }
+            for (int t = 0; t < m->n_terms; ++t)
+                if (m->term_i[t] < 0 || m->term_j[t] < 0 || m->term_i[t] >= minN || m->term_j[t] >= minN ||
+                    m->term_i[t] == m->term_j[t] || !std::isfinite(m->term_c[t])) {
+                    e = "metad: term " + std::to_string(t) + " has bad atom indices or coefficient"; return PIMD_ERR_INVALID_ARG;
+                }
+        } else {
+            if (!(m->xrd_Q > 0.0) || !std::isfinite(m->xrd_Q)) { e = "metad: xrd_Q must be > 0"; return PIMD_ERR_INVALID_ARG; }
+            for (size_t t = 0; t < zs.size(); ++t)
+                if (!std::isfinite(m->xrd_f[t])) { e = "metad: xrd_f must be finite"; return PIMD_ERR_INVALID_ARG; }
+        }
+        if (!(m->height_eV > 0.0) || !(m->sigma > 0.0) || !(m->bias_factor > 1.0) || m->stride < 1)
+            { e = "metad: need height_eV > 0, sigma > 0, bias_factor > 1, stride >= 1"; return PIMD_ERR_INVALID_ARG; }
+        if (m->max_hills < maxP || m->max_hills > (1 << 24)) { e = "metad: max_hills must be in [max P, 2^24]"; return PIMD_ERR_INVALID_ARG; }
+    }
 
     // normal-mode matrices, one per distinct P
     std::map<int, int> cm_off;
@@ -332,6 +354,20 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.wbuf = c.take(rs * 9 * (size_t)b.B);
     o.vbuf = c.take(cfg->deterministic && model ? v4 * (size_t)b.B * mnb : 0);
     o.mom = c.take(model && cfg->precision != PIMD_FP64 ? sizeof(float4) * moment_elems_per_atom() * (size_t)b.B : 0);
+    {
+        const bool md = cfg->metad && cfg->metad->cv != PIMD_CV_NONE;
+        int maxN = 1;
+        for (const Rep& rp : b.reps) maxN = std::max(maxN, rp.N);
+        const size_t nt = md ? (size_t)metad_tiles(maxN) : 0;
+        o.md_hills = c.take(md ? sizeof(double2) * (size_t)b.R * cfg->metad->max_hills : 0);
+        o.md_nhill = c.take(md ? sizeof(int) * b.R : 0);
+        o.md_cv = c.take(md ? sizeof(double) * b.S : 0);
+        o.md_vb = c.take(md ? sizeof(double) * b.S : 0);
+        o.md_dvds = c.take(md ? sizeof(double) * b.S : 0);
+        o.md_cvpart = c.take(sizeof(double) * b.S * nt);
+        o.md_virpart = c.take(sizeof(double) * 9 * b.S * nt);
+        o.md_grad = c.take(md ? v4 * (size_t)b.B : 0);
+    }
     o.step = c.take(sizeof(unsigned long long));
     o.err = c.take(sizeof(DevErr));
     o.est = c.take(sizeof(double) * EST_STRIDE * b.R);
@@ -395,7 +431,7 @@ void mark(pimd_ctx* c, int i, cudaStream_t st, bool timed)
     if (timed && c->ev[i]) cudaEventRecordWithFlags(c->ev[i], st, cudaEventRecordExternal);
 }
 
-void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false)
+void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit = false)
 {
     Dev& d = c->d;
     const size_t v4 = d.precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
@@ -420,6 +456,7 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false)
     }
     mark(c, PIMD_STAGE_ENERGY, st, timed);
     launch_energy_reduce(d, st);
+    if (d.metad.cv) launch_metad(d, deposit, st);   // bias on every bead (and hills on deposition steps)
 }
 void eval_forces(pimd_ctx* c) { eval_forces(c, c->st); }
 
@@ -427,7 +464,7 @@ void one_step(pimd_ctx* c, cudaStream_t st, bool timed)
 {
     mark(c, PIMD_STAGE_RING_START, st, timed);
     launch_rp_start(c->d, st);
-    eval_forces(c, st, timed);
+    eval_forces(c, st, timed, true);
     mark(c, PIMD_STAGE_RING_FINISH, st, timed);
     launch_rp_finish(c->d, true, st);
     launch_bump_step(c->d, st);
@@ -479,6 +516,7 @@ int device_errors(pimd_ctx* c)
                                                       " neighbours, max_neighbours is " + std::to_string(c->d.maxnb));
         if (h.flags & ERR_NONFINITE) return fail(c, PIMD_ERR_NONFINITE, "non-finite forces");
         if (h.flags & ERR_TIMEOUT) return fail(c, PIMD_ERR_TIMEOUT, "device wait timed out");
+        if (h.flags & ERR_METAD_FULL) return fail(c, PIMD_ERR_METAD_FULL, "metadynamics hill capacity exhausted");
     }
     return PIMD_OK;
 }
@@ -581,6 +619,33 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.wbuf = w + o.wbuf;
     d.vbuf = w + o.vbuf;
     d.mom = (cfg->potential == PIMD_POT_MODEL && cfg->precision != PIMD_FP64) ? (void*)(w + o.mom) : nullptr;
+    for (const Rep& rp : b.reps) d.max_P = std::max(d.max_P, rp.P);
+    if (cfg->metad && cfg->metad->cv != PIMD_CV_NONE) {
+        const pimd_metad_desc* m = cfg->metad;
+        MetadParams& mp = d.metad;
+        mp.cv = m->cv;
+        mp.n_terms = m->cv == PIMD_CV_DISTANCES ? m->n_terms : 0;
+        for (int t = 0; t < mp.n_terms; ++t) {
+            mp.ti[t] = m->term_i[t];
+            mp.tj[t] = m->term_j[t];
+            mp.tc[t] = m->term_c[t];
+        }
+        mp.Q = m->xrd_Q;
+        for (int t = 0; t < 8; ++t) mp.f_type[t] = m->cv == PIMD_CV_XRD ? m->xrd_f[t] : 0.0;
+        mp.h0 = m->height_eV;
+        mp.sigma = m->sigma;
+        mp.gamma = m->bias_factor;
+        mp.stride = m->stride;
+        mp.max_hills = m->max_hills;
+        d.md_hills = (double2*)(w + o.md_hills);
+        d.md_nhill = (int*)(w + o.md_nhill);
+        d.md_cv = (double*)(w + o.md_cv);
+        d.md_vb = (double*)(w + o.md_vb);
+        d.md_dvds = (double*)(w + o.md_dvds);
+        d.md_cvpart = (double*)(w + o.md_cvpart);
+        d.md_virpart = (double*)(w + o.md_virpart);
+        d.md_grad = w + o.md_grad;
+    }
     // angular terms through moment tensors when the mean neighbour count makes
     // the O(n) moment path cheaper than the O(n^2) pair sums
     d.sched.ang = (d.mom != nullptr && b.nb_est >= 24.0) ? 1 : 0;
@@ -650,6 +715,11 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
         if (rc) { std::string m = c->err; delete c; return fail(nullptr, rc, m); }
     }
     cudaMemsetAsync(d.Q, 0, sizeof(double) * d.R, c->st);
+    if (d.metad.cv) {
+        cudaMemsetAsync(d.md_nhill, 0, sizeof(int) * d.R, c->st);
+        cudaMemsetAsync(d.md_cv, 0, sizeof(double) * d.S, c->st);
+        cudaMemsetAsync(d.md_vb, 0, sizeof(double) * d.S, c->st);
+    }
     cudaMemsetAsync(d.step, 0, sizeof(unsigned long long), c->st);
     cudaMemsetAsync(d.err, 0, sizeof(DevErr), c->st);
     cudaMemsetAsync(d.nnb, 0, sizeof(int) * d.B, c->st);
@@ -886,8 +956,10 @@ int pimd_get_angular(const pimd_ctx* c)
 int pimd_kernels_per_step(const pimd_ctx* c)
 {
     if (!c) return 0;
-    // ring start, neighbours, descriptors, network, adjoint, energy, ring finish, step counter
-    return c->d.potential == PIMD_POT_HARMONIC ? 5 : (c->d.deterministic ? 9 : 8);
+    // ring start, neighbours, descriptors, network, adjoint, energy, ring finish, step counter;
+    // metadynamics: CV, bias, bias force
+    const int md = c->d.metad.cv ? 3 : 0;
+    return (c->d.potential == PIMD_POT_HARMONIC ? 5 : (c->d.deterministic ? 9 : 8)) + md;
 }
 
 int pimd_energy_forces(pimd_ctx* c, const double* x_dev, double* e_dev, double* f_dev, double* virial_dev)
@@ -1063,6 +1135,72 @@ int pimd_sizes(const pimd_ctx* c, int64_t* B, int64_t* S, int* R, int* maxnb)
     return PIMD_OK;
 }
 
+namespace {
+int check_replica(pimd_ctx* c, int replica)
+{
+    if (replica < 0 || replica >= c->d.R) return fail(c, PIMD_ERR_INVALID_ARG, "replica out of range");
+    return PIMD_OK;
+}
+}  // namespace
+
+int pimd_metad_hills(pimd_ctx* c, int replica, double* s, double* h, int capacity)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d.metad.cv) return fail(c, PIMD_ERR_STATE, "no metadynamics bias configured");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    int n = 0;
+    rc = cuda_check(c, cudaMemcpyAsync(&n, c->d.md_nhill + replica, sizeof(int), cudaMemcpyDeviceToHost, c->st), "hills");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "hills");
+    if (rc) return rc;
+    const int m = std::min(n, std::max(capacity, 0));
+    if (m > 0 && (s || h)) {
+        std::vector<double2> buf(m);
+        rc = cuda_check(c, cudaMemcpyAsync(buf.data(), c->d.md_hills + (size_t)replica * c->d.metad.max_hills,
+                                           sizeof(double2) * m, cudaMemcpyDeviceToHost, c->st), "hills");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "hills");
+        if (rc) return rc;
+        for (int k = 0; k < m; ++k) {
+            if (s) s[k] = buf[k].x;
+            if (h) h[k] = buf[k].y;
+        }
+    }
+    return n;
+}
+
+int pimd_metad_set_hills(pimd_ctx* c, int replica, const double* s, const double* h, int n)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d.metad.cv) return fail(c, PIMD_ERR_STATE, "no metadynamics bias configured");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    if (n < 0 || n > c->d.metad.max_hills || (n > 0 && (!s || !h)))
+        return fail(c, PIMD_ERR_INVALID_ARG, "n must be 0..max_hills with s and h given");
+    std::vector<double2> buf(n);
+    for (int k = 0; k < n; ++k) buf[k] = make_double2(s[k], h[k]);
+    if (n > 0)
+        rc = cuda_check(c, cudaMemcpyAsync(c->d.md_hills + (size_t)replica * c->d.metad.max_hills, buf.data(),
+                                           sizeof(double2) * n, cudaMemcpyHostToDevice, c->st), "set hills");
+    if (!rc)
+        rc = cuda_check(c, cudaMemcpyAsync(c->d.md_nhill + replica, &n, sizeof(int), cudaMemcpyHostToDevice, c->st),
+                        "set hills");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "set hills");
+    c->forces_valid = false;
+    return rc;
+}
+
+int pimd_metad_cv(pimd_ctx* c, double* cv, double* bias)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d.metad.cv) return fail(c, PIMD_ERR_STATE, "no metadynamics bias configured");
+    int rc = PIMD_OK;
+    if (cv) rc = cuda_check(c, cudaMemcpyAsync(cv, c->d.md_cv, sizeof(double) * c->d.S, cudaMemcpyDeviceToHost, c->st), "cv");
+    if (!rc && bias)
+        rc = cuda_check(c, cudaMemcpyAsync(bias, c->d.md_vb, sizeof(double) * c->d.S, cudaMemcpyDeviceToHost, c->st), "cv");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "cv");
+    return rc;
+}
+
 int pimd_element_types(const pimd_ctx* c, int* Z)
 {
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
@@ -1071,14 +1209,6 @@ int pimd_element_types(const pimd_ctx* c, int* Z)
         for (size_t k = 0; k < t.size(); ++k) Z[k] = t[k];
     return (int)t.size();
 }
-
-namespace {
-int check_replica(pimd_ctx* c, int replica)
-{
-    if (replica < 0 || replica >= c->d.R) return fail(c, PIMD_ERR_INVALID_ARG, "replica out of range");
-    return PIMD_OK;
-}
-}  // namespace
 
 int pimd_rdf_counts(pimd_ctx* c, int replica, double r_max, int n_bins, unsigned long long* counts)
 {

@@ -19,7 +19,7 @@ constexpr int TILE_ROWS = 128;     // network rows per tensor-core tile; element
 #define PIMD_SORT_CAP 256          // neighbour-list sort buffer per warp (>= max_neighbours)
 
 // device error word
-enum : unsigned { ERR_NBR_OVERFLOW = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u };
+enum : unsigned { ERR_NBR_OVERFLOW = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u, ERR_METAD_FULL = 8u };
 struct DevErr {
     unsigned flags;
     int max_nbr;
@@ -74,6 +74,18 @@ struct Sched {
     int small_atomics;   // below band_min: 1 = flat walk with shared atomics,
                          // 0 = ordered pairs (each pair twice, no atomics)
     int ang;             // angular terms: 0 = pair sums, 1 = moment tensors (FP32 only)
+};
+
+// metadynamics: CV definition and bias parameters (by value to the kernels)
+struct MetadParams {
+    int cv;              // 0 none, 1 distance combination, 2 XRD intensity
+    int n_terms;
+    int ti[8], tj[8];
+    double tc[8];
+    double Q;            // XRD scattering vector magnitude, 1/A
+    double f_type[8];    // XRD scattering factor per element type
+    double h0, sigma, gamma;
+    int stride, max_hills;
 };
 
 // symmetry-function parameters in the working precision

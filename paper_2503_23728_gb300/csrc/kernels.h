@@ -54,6 +54,18 @@ struct Dev {
     void* wbuf = nullptr;              // Real[B][9] per bead-atom virial
     void* vbuf = nullptr;              // Vec4<Real>[B][maxnb] pair vectors (deterministic mode)
     void* mom = nullptr;               // float4[B][6][32] angular moments (moment path, FP32)
+    int max_P = 1;                     // largest bead count
+
+    // metadynamics (md_* in the workspace when metad.cv != 0)
+    MetadParams metad = {};
+    double2* md_hills = nullptr;       // [R][max_hills] (centre, height)
+    int* md_nhill = nullptr;           // [R]
+    double* md_cv = nullptr;           // [S] CV of each bead at the last evaluation
+    double* md_vb = nullptr;           // [S] bias
+    double* md_dvds = nullptr;         // [S] dV/ds
+    double* md_cvpart = nullptr;       // [S][tiles] CV partial sums
+    double* md_virpart = nullptr;      // [S][tiles][9] pair-virial partial sums
+    void* md_grad = nullptr;           // Vec4<Real>[B] ds/dx
     int deterministic = 0;
     unsigned long long* step = nullptr;
     DevErr* err = nullptr;
@@ -110,6 +122,10 @@ void launch_descriptors_out(const Dev& d, double* G, cudaStream_t st);
 bool network_tc_supported(int width, int n_hidden);
 size_t tc_weight_bytes(int width, int n_hidden);
 void prepare_tc_weights(const Dev& d, int type, const double* blob, void* host_img, float* host_vec);
+
+// metadynamics
+int metad_tiles(int max_N);
+void launch_metad(const Dev& d, bool deposit, cudaStream_t st);
 
 // structural analysis
 size_t rdf_smem_bytes(int n_types, int n_bins);

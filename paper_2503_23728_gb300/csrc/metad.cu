@@ -1,0 +1,239 @@
+// metad.cu -- well-tempered metadynamics on a collective variable of every
+// bead (Sec. 2.5): the CV and its gradient per bead, the Gaussian bias and
+// its force, and the deposition of hills.
+//
+// CVs (Secs. S2-S3):
+//   distances:  s = sum_t c_t |x_(j_t) - x_(i_t)|   (the dimer's proton-transfer CV)
+//   XRD:        s = (1/N) sum_i sum_j f_i f_j sin(Q R_ij) / (Q R_ij), i = j terms f_i^2
+// Bias: V(s) = sum_k h_k exp(-(s - s_k)^2 / (2 sigma^2)) on every bead; hills
+// go down after the force evaluation of step n when (n + 1) % stride == 0,
+// one per bead at its CV with height (h0 / P) exp(-V(s_k) / (k_B T (gamma-1))).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "geom.cuh"
+#include "kernels.h"
+#include "pimd.h"
+
+namespace pimd {
+
+// ---------------------------------------------------------------------------
+// distance-combination CV: one thread per bead-system
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void cv_dist_kernel(const Vec4<Real>* __restrict__ x, const BeadSys* __restrict__ bsys,
+                               const Rep* __restrict__ reps, int S, MetadParams mp, Vec4<Real>* __restrict__ grad,
+                               double* __restrict__ cvpart, double* __restrict__ virpart, int ntile)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    const BeadSys sy = bsys[k];
+    const Rep& rp = reps[sy.rep];
+    double s = 0.0, vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < mp.n_terms; ++t) {
+        const int i = mp.ti[t], j = mp.tj[t];
+        Real r[3];
+        pair_vec(rp, x[sy.ba0 + i], x[sy.ba0 + j], r[0], r[1], r[2]);
+        const double rx = (double)r[0], ry = (double)r[1], rz = (double)r[2];
+        const double d = sqrt(rx * rx + ry * ry + rz * rz);
+        s += mp.tc[t] * d;
+        const double g[3] = {mp.tc[t] * rx / d, mp.tc[t] * ry / d, mp.tc[t] * rz / d};
+        Vec4<Real>& gj = grad[sy.ba0 + j];
+        Vec4<Real>& gi = grad[sy.ba0 + i];
+        gj.x += (Real)g[0]; gj.y += (Real)g[1]; gj.z += (Real)g[2];
+        gi.x -= (Real)g[0]; gi.y -= (Real)g[1]; gi.z -= (Real)g[2];
+        const double rv[3] = {rx, ry, rz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) vir[3 * a + b] += rv[a] * g[b];
+    }
+    cvpart[(size_t)k * ntile] = s;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) virpart[((size_t)k * ntile) * 9 + q] = vir[q];
+}
+
+// ---------------------------------------------------------------------------
+// XRD CV: grid (atom tiles, bead-systems); thread per atom i sums its whole
+// row j != i (no atomics: every pair is seen from both ends), giving
+//   N s = sum_i [f_i^2 + sum_(j != i) f_i f_j sinc(Q R_ij)],
+//   ds/dx_i = (2/N) sum_(j != i) f_i f_j Q sinc'(Q R_ij) (x_i - x_j) / R_ij,
+// and the pair virial (halved, each pair twice). Block sums in FP64 go to
+// per-tile partials, added in fixed order by the bias kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sincos_r(float y, float& s, float& c) { sincosf(y, &s, &c); }
+__device__ __forceinline__ void sincos_r(double y, double& s, double& c) { sincos(y, &s, &c); }
+
+template <typename Real>
+__global__ void __launch_bounds__(128) cv_xrd_kernel(const Vec4<Real>* __restrict__ x,
+                                                     const BeadSys* __restrict__ bsys, const Rep* __restrict__ reps,
+                                                     const int* __restrict__ atype, MetadParams mp,
+                                                     Vec4<Real>* __restrict__ grad, double* __restrict__ cvpart,
+                                                     double* __restrict__ virpart, int ntile)
+{
+    __shared__ double red[10][4];
+    const int k = blockIdx.y;
+    const BeadSys sy = bsys[k];
+    const Rep& rp = reps[sy.rep];
+    const int N = sy.N;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Real Q = (Real)mp.Q;
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // N s share, then the 9 virial entries
+    if (i < N) {
+        const Vec4<Real> xi = x[sy.ba0 + i];
+        const Real fi = (Real)mp.f_type[atype[rp.atom0 + i]];
+        Real srow = Real(0), g[3] = {Real(0), Real(0), Real(0)}, vir[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vir[q] = Real(0);
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            Real r[3];
+            pair_vec(rp, xi, x[sy.ba0 + j], r[0], r[1], r[2]);
+            const Real R2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            const Real R = f_sqrt(R2);
+            const Real y = Q * R;
+            Real sn, cs;
+            sincos_r(y, sn, cs);
+            const Real ff = fi * (Real)mp.f_type[atype[rp.atom0 + j]];
+            srow += ff * sn / y;
+            // ds/dr_ij = c r_ij, c = 2 f_i f_j Q sinc'(QR) / (N R)
+            const Real c = Real(2) * ff * Q * (y * cs - sn) / (y * y * R * (Real)N);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                g[a] -= c * r[a];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) vir[3 * a + b] += r[a] * c * r[b];
+            }
+        }
+        grad[sy.ba0 + i] = make4<Vec4<Real>, Real>(g[0], g[1], g[2], Real(0));
+        acc[0] = (double)fi * (double)fi + (double)srow;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[1 + q] = 0.5 * (double)vir[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) acc[q] = warp_sum(acc[q]);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 10; ++q) red[q][w] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        const double v = red[threadIdx.x][0] + red[threadIdx.x][1] + red[threadIdx.x][2] + red[threadIdx.x][3];
+        if (threadIdx.x == 0)
+            cvpart[(size_t)k * ntile + blockIdx.x] = v;
+        else
+            virpart[((size_t)k * ntile + blockIdx.x) * 9 + threadIdx.x - 1] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bias: one block per replica, thread per bead. s from the tile partials
+// (fixed order), V(s) and dV/ds over the replica's hills, the bias energy
+// and virial into the bead's V and W, then (deposition steps only) one hill
+// per bead.
+// ---------------------------------------------------------------------------
+__global__ void bias_kernel(const Rep* __restrict__ reps, const BeadSys* __restrict__ bsys, MetadParams mp,
+                            const double* __restrict__ cvpart, const double* __restrict__ virpart, int ntile,
+                            double2* __restrict__ hills, int* __restrict__ nhill, double* __restrict__ cv,
+                            double* __restrict__ vb, double* __restrict__ dvds, double* __restrict__ V,
+                            double* __restrict__ W, const unsigned long long* __restrict__ stepp, int deposit,
+                            DevErr* __restrict__ err)
+{
+    const int r = blockIdx.x;
+    const Rep& rp = reps[r];
+    const int k = threadIdx.x;
+    const int n = nhill[r];
+    const double2* H = hills + (size_t)r * mp.max_hills;
+    double s = 0.0, v = 0.0;
+    if (k < rp.P) {
+        const int bs = rp.bs0 + k;
+        const int ntl = mp.cv == PIMD_CV_XRD ? ntile : 1;
+        for (int t = 0; t < ntl; ++t) s += cvpart[(size_t)bs * ntile + t];
+        if (mp.cv == PIMD_CV_XRD) s /= (double)bsys[bs].N;
+        double dv = 0.0;
+        const double is2 = 1.0 / (mp.sigma * mp.sigma);
+        for (int h = 0; h < n; ++h) {
+            const double u = s - H[h].x;
+            const double g = H[h].y * exp(-0.5 * u * u * is2);
+            v += g;
+            dv -= g * u * is2;
+        }
+        cv[bs] = s;
+        vb[bs] = v;
+        dvds[bs] = dv;
+        V[bs] += v;
+        for (int q = 0; q < 9; ++q) {
+            double w = 0.0;
+            for (int t = 0; t < ntl; ++t) w += virpart[((size_t)bs * ntile + t) * 9 + q];
+            W[(size_t)bs * 9 + q] -= dv * w;
+        }
+    }
+    if (!deposit || ((*stepp + 1ull) % (unsigned long long)mp.stride) != 0ull) return;
+    __syncthreads();   // every bead has read the hills before any is added
+    if (n + rp.P > mp.max_hills) {
+        if (k == 0) atomicOr(&err->flags, ERR_METAD_FULL);
+        return;
+    }
+    if (k < rp.P) {
+        const double kT = rp.kT_md * MVV2E / rp.P;   // k_B T of the physical temperature, eV
+        const double h = mp.h0 / rp.P * exp(-v / (kT * (mp.gamma - 1.0)));
+        hills[(size_t)r * mp.max_hills + n + k] = make_double2(s, h);
+    }
+    __syncthreads();
+    if (k == 0) nhill[r] = n + rp.P;
+}
+
+// f_b -= dV/ds ds/dx_b for every bead-atom
+template <typename Real>
+__global__ void bias_force_kernel(const int* __restrict__ ba_sys, const Vec4<Real>* __restrict__ grad,
+                                  const double* __restrict__ dvds, Vec4<Real>* __restrict__ f, int B)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const Real dv = (Real)dvds[ba_sys[b]];
+    const Vec4<Real> g = grad[b];
+    Vec4<Real> v = f[b];
+    v.x -= dv * g.x;
+    v.y -= dv * g.y;
+    v.z -= dv * g.z;
+    f[b] = v;
+}
+
+int metad_tiles(int max_N) { return (max_N + 127) / 128; }
+
+void launch_metad(const Dev& d, bool deposit, cudaStream_t st)
+{
+    const MetadParams& mp = d.metad;
+    const int ntile = metad_tiles(d.max_N);
+    const size_t v4 = d.precision == 0 ? sizeof(Dbl4) : sizeof(float4);
+    if (mp.cv == PIMD_CV_DISTANCES) {
+        cudaMemsetAsync(d.md_grad, 0, v4 * d.B, st);
+        if (d.precision == 0)
+            cv_dist_kernel<double><<<(d.S + 127) / 128, 128, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, d.S, mp,
+                                                                      (Dbl4*)d.md_grad, d.md_cvpart, d.md_virpart,
+                                                                      ntile);
+        else
+            cv_dist_kernel<float><<<(d.S + 127) / 128, 128, 0, st>>>((const float4*)d.x, d.bsys, d.reps, d.S, mp,
+                                                                     (float4*)d.md_grad, d.md_cvpart, d.md_virpart,
+                                                                     ntile);
+    } else {
+        const dim3 grid(ntile, d.S);
+        if (d.precision == 0)
+            cv_xrd_kernel<double><<<grid, 128, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, d.atype, mp,
+                                                        (Dbl4*)d.md_grad, d.md_cvpart, d.md_virpart, ntile);
+        else
+            cv_xrd_kernel<float><<<grid, 128, 0, st>>>((const float4*)d.x, d.bsys, d.reps, d.atype, mp,
+                                                       (float4*)d.md_grad, d.md_cvpart, d.md_virpart, ntile);
+    }
+    bias_kernel<<<d.R, d.max_P, 0, st>>>(d.reps, d.bsys, mp, d.md_cvpart, d.md_virpart, ntile, d.md_hills,
+                                         d.md_nhill, d.md_cv, d.md_vb, d.md_dvds, d.V, d.W, d.step,
+                                         deposit ? 1 : 0, d.err);
+    if (d.precision == 0)
+        bias_force_kernel<double><<<(d.B + 255) / 256, 256, 0, st>>>(d.ba_sys, (const Dbl4*)d.md_grad, d.md_dvds,
+                                                                     (Dbl4*)d.f, d.B);
+    else
+        bias_force_kernel<float><<<(d.B + 255) / 256, 256, 0, st>>>(d.ba_sys, (const float4*)d.md_grad, d.md_dvds,
+                                                                    (float4*)d.f, d.B);
+}
+
+}  // namespace pimd

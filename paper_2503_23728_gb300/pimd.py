@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpimd.so")
 
 PIMD_OK = 0
-STATUS = {0: "OK", -1: "INVALID_ARG", -2: "STATE", -3: "WORKSPACE_TOO_SMALL", -4: "CUDA", -5: "NONFINITE",
+STATUS = {-9: "METAD_FULL", 0: "OK", -1: "INVALID_ARG", -2: "STATE", -3: "WORKSPACE_TOO_SMALL", -4: "CUDA", -5: "NONFINITE",
           -6: "TIMEOUT", -7: "NBR_OVERFLOW", -8: "UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16_tc": 2}
 POT_MODEL, POT_HARMONIC = 0, 1
@@ -24,7 +24,8 @@ EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_w
            "pimd_energy_forces", "pimd_descriptors", "pimd_estimators", "pimd_get_state", "pimd_set_state",
            "pimd_get_forces", "pimd_get_neighbours", "pimd_sync", "pimd_sizes", "pimd_destroy", "pimd_last_error",
            "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule", "pimd_set_angular", "pimd_get_angular",
-           "pimd_element_types", "pimd_rdf_counts", "pimd_pt_coordinate"]
+           "pimd_element_types", "pimd_rdf_counts", "pimd_pt_coordinate",
+           "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv"]
 ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
@@ -35,13 +36,40 @@ class PimdError(RuntimeError):
         self.code = code
 
 
+class pimd_metad_desc(ct.Structure):
+    _fields_ = [("cv", ct.c_int), ("n_terms", ct.c_int), ("term_i", ct.c_int * 8), ("term_j", ct.c_int * 8),
+                ("term_c", ct.c_double * 8), ("xrd_Q", ct.c_double), ("xrd_f", ct.c_double * 8),
+                ("height_eV", ct.c_double), ("sigma", ct.c_double), ("bias_factor", ct.c_double),
+                ("stride", ct.c_int), ("max_hills", ct.c_int)]
+
+
+def make_metad(cv, height_eV: float, sigma: float, bias_factor: float, stride: int, max_hills: int,
+               elements=None) -> pimd_metad_desc:
+    """cv = ("distances", [(i, j, c), ...]) or ("xrd", Q, {Z: f}); for XRD the
+    factors are laid out in ascending-Z order of `elements`."""
+    m = pimd_metad_desc()
+    if cv[0] == "distances":
+        m.cv = 1
+        m.n_terms = len(cv[1])
+        for t, (i, j, c) in enumerate(cv[1]):
+            m.term_i[t], m.term_j[t], m.term_c[t] = int(i), int(j), float(c)
+    else:
+        m.cv = 2
+        m.xrd_Q = float(cv[1])
+        for t, z in enumerate(sorted(elements)):
+            m.xrd_f[t] = float(cv[2][int(z)])
+    m.height_eV, m.sigma, m.bias_factor = float(height_eV), float(sigma), float(bias_factor)
+    m.stride, m.max_hills = int(stride), int(max_hills)
+    return m
+
+
 class pimd_config(ct.Structure):
     _fields_ = [("dt_fs", ct.c_double), ("gamma0_per_fs", ct.c_double), ("pile_lambda", ct.c_double),
                 ("cutoff_A", ct.c_double), ("precision", ct.c_int), ("thermostat", ct.c_int),
                 ("potential", ct.c_int), ("max_neighbours", ct.c_int), ("omega_harm", ct.c_double),
                 ("n_hidden", ct.c_int), ("widths", ct.c_int * 4), ("stream", ct.c_void_p), ("timing", ct.c_int),
                 ("nbr_algo", ct.c_int), ("deterministic", ct.c_int), ("splitting", ct.c_int),
-                ("free_rp", ct.c_int)]
+                ("free_rp", ct.c_int), ("metad", ct.POINTER(pimd_metad_desc))]
 SPLITTING = {"obabo": 0, "baoab": 1}
 FREE_RP = {"exact": 0, "cayley": 1}
 
@@ -111,6 +139,10 @@ def load(path: str = LIB_PATH):
     L.pimd_set_angular.argtypes = [vp, ct.c_int]
     L.pimd_get_angular.argtypes = [vp]
     L.pimd_get_angular.restype = ct.c_int
+    L.pimd_metad_hills.argtypes = [vp, ct.c_int, dp, dp, ct.c_int]
+    L.pimd_metad_hills.restype = ct.c_int
+    L.pimd_metad_set_hills.argtypes = [vp, ct.c_int, dp, dp, ct.c_int]
+    L.pimd_metad_cv.argtypes = [vp, dp, dp]
     L.pimd_element_types.argtypes = [vp, ct.POINTER(ct.c_int)]
     L.pimd_element_types.restype = ct.c_int
     L.pimd_rdf_counts.argtypes = [vp, ct.c_int, ct.c_double, ct.c_int, vp]
@@ -231,6 +263,44 @@ def pimd_get_angular(ctx) -> str:
     return {0: "pairs", 1: "moments"}[int(load().pimd_get_angular(ctx))]
 
 
+def pimd_metad_hills(ctx, replica: int, capacity: int = 1 << 20):
+    n = int(load().pimd_metad_hills(ctx, int(replica), None, None, 0))
+    if n < 0:
+        _check(n, ctx)
+    s = np.zeros(n)
+    h = np.zeros(n)
+    if n:
+        n2 = int(load().pimd_metad_hills(ctx, int(replica), _dp(s), _dp(h), n))
+        if n2 < 0:
+            _check(n2, ctx)
+    return s, h
+
+
+def pimd_metad_set_hills(ctx, replica: int, s, h):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    _check(load().pimd_metad_set_hills(ctx, int(replica), _dp(s), _dp(h), len(s)), ctx)
+
+
+def pimd_metad_cv(ctx, S: int):
+    cv = np.zeros(S)
+    vb = np.zeros(S)
+    _check(load().pimd_metad_cv(ctx, _dp(cv), _dp(vb)), ctx)
+    return cv, vb
+
+
+def metad_fes(s_grid, hills_s, hills_h, sigma: float, bias_factor: float):
+    """Free-energy profile from a converged well-tempered bias (Sec. 2.5):
+    F(s) = -(gamma / (gamma - 1)) V(s), V the sum of the hills, shifted to a
+    zero minimum. With the bias on every bead's CV this is the bead-averaged
+    (path-integral) profile of Sec. 2.5."""
+    s_grid = np.asarray(s_grid, dtype=np.float64)
+    d = s_grid[:, None] - np.asarray(hills_s, dtype=np.float64)[None, :]
+    V = (np.asarray(hills_h, dtype=np.float64)[None, :] * np.exp(-0.5 * d * d / (sigma * sigma))).sum(axis=1)
+    F = -bias_factor / (bias_factor - 1.0) * V
+    return F - F.min()
+
+
 def pimd_element_types(ctx) -> list:
     z = (ct.c_int * 8)()
     n = int(load().pimd_element_types(ctx, z))
@@ -309,7 +379,7 @@ def pimd_last_error(ctx=None) -> str:
 def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128, 128, 128), pile_lambda=1.0,
                 thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128, stream=None,
                 timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
-                free_rp="exact") -> pimd_config:
+                free_rp="exact", metad=None) -> pimd_config:
     c = pimd_config()
     c.dt_fs = dt_fs
     c.gamma0_per_fs = gamma0_per_fs
@@ -329,6 +399,8 @@ def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128,
     c.deterministic = 1 if deterministic else 0
     c.splitting = SPLITTING[splitting] if isinstance(splitting, str) else int(splitting)
     c.free_rp = FREE_RP[free_rp] if isinstance(free_rp, str) else int(free_rp)
+    if metad is not None:
+        c.metad = ct.pointer(metad)
     return c
 
 
@@ -393,7 +465,7 @@ class Context:
     def __init__(self, replicas, dt_fs, gamma0_per_fs, precision="fp32", widths=(128, 128, 128), cutoff=6.0,
                  pile_lambda=1.0, thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128,
                  masses=None, stream=None, timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
-                 free_rp="exact"):
+                 free_rp="exact", metad=None):
         import torch
         self.torch = torch
         self.keep = _Keep()
@@ -403,7 +475,8 @@ class Context:
         self.stream = stream
         self.cfg = make_config(dt_fs, gamma0_per_fs, precision, cutoff, widths, pile_lambda, thermostat, potential,
                                omega, max_neighbours, ct.c_void_p(stream.cuda_stream), timing, nbr_algo,
-                               deterministic, splitting, free_rp)
+                               deterministic, splitting, free_rp, metad)
+        self.metad_desc = metad
         self.reps = make_replicas(self.replicas, self.keep, masses)
         self.ws_bytes = pimd_workspace_size(self.cfg, self.reps)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -486,6 +559,16 @@ class Context:
 
     def set_angular(self, algo: str):
         pimd_set_angular(self.h, algo)
+
+    def metad_hills(self, replica: int = 0):
+        return pimd_metad_hills(self.h, replica)
+
+    def metad_set_hills(self, s, h, replica: int = 0):
+        pimd_metad_set_hills(self.h, replica, s, h)
+
+    def metad_cv(self):
+        """(CV, bias) of every bead-system at the last force evaluation"""
+        return pimd_metad_cv(self.h, sum(r.n_beads for r in self.replicas))
 
     def element_types(self) -> list:
         return pimd_element_types(self.h)
