@@ -61,8 +61,38 @@ __global__ void cv_dist_kernel(const Vec4<Real>* __restrict__ x, const BeadSys* 
 // and the pair virial (halved, each pair twice). Block sums in FP64 go to
 // per-tile partials, added in fixed order by the bias kernel.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void sincos_r(float y, float& s, float& c) { sincosf(y, &s, &c); }
+// sin and cos of y >= 0. FP32: Cody-Waite reduction y - 2 pi k with 2 pi
+// split into a float head and the float of the remainder (k = rint(y / 2 pi)
+// stays small here: Q R < 100), then the special-function unit on
+// [-pi, pi] (absolute error ~5e-7, far inside the CV's use as a bias
+// coordinate). FP64: the accurate library routine.
+constexpr float TWO_PI_HI = 6.28318548202514648f;                    // float(2 pi)
+constexpr float TWO_PI_LO = (float)(6.283185307179586477 - 6.28318548202514648);
+__device__ __forceinline__ void sincos_r(float y, float& s, float& c)
+{
+    const float k = rintf(y * (1.0f / 6.283185307179586f));
+    float t = fmaf(-k, TWO_PI_HI, y);
+    t = fmaf(-k, TWO_PI_LO, t);
+    s = __sinf(t);
+    c = __cosf(t);
+}
 __device__ __forceinline__ void sincos_r(double y, double& s, double& c) { sincos(y, &s, &c); }
+
+// plain minimum-image difference (the CV needs no error-free pair vector)
+__device__ __forceinline__ void xrd_pair(const Rep& rp, const float4& a, const float4& b, float (&r)[3])
+{
+    r[0] = b.x - a.x; r[1] = b.y - a.y; r[2] = b.z - a.z;
+    if (rp.periodic) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) r[d] = fmaf(-rp.Lf[d], rintf(r[d] * rp.invLf[d]), r[d]);
+    }
+}
+__device__ __forceinline__ void xrd_pair(const Rep& rp, const Dbl4& a, const Dbl4& b, double (&r)[3])
+{
+    pair_vec(rp, a, b, r[0], r[1], r[2]);
+}
+__device__ __forceinline__ float xrd_rcp(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double xrd_rcp(double v) { return 1.0 / v; }
 
 template <typename Real>
 __global__ void __launch_bounds__(128) cv_xrd_kernel(const Vec4<Real>* __restrict__ x,
@@ -85,26 +115,32 @@ __global__ void __launch_bounds__(128) cv_xrd_kernel(const Vec4<Real>* __restric
         Real srow = Real(0), g[3] = {Real(0), Real(0), Real(0)}, vir[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir[q] = Real(0);
+        const Real c0 = Real(2) * Q * Q / (Real)N;   // c = c0 f_i f_j (y cos y - sin y) / y^3
         for (int j = 0; j < N; ++j) {
             if (j == i) continue;
             Real r[3];
-            pair_vec(rp, xi, x[sy.ba0 + j], r[0], r[1], r[2]);
+            xrd_pair(rp, xi, x[sy.ba0 + j], r);
             const Real R2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
             const Real R = f_sqrt(R2);
             const Real y = Q * R;
             Real sn, cs;
             sincos_r(y, sn, cs);
+            const Real iy = xrd_rcp(y);
             const Real ff = fi * (Real)mp.f_type[atype[rp.atom0 + j]];
-            srow += ff * sn / y;
-            // ds/dr_ij = c r_ij, c = 2 f_i f_j Q sinc'(QR) / (N R)
-            const Real c = Real(2) * ff * Q * (y * cs - sn) / (y * y * R * (Real)N);
+            const Real sc = sn * iy;                      // sinc(QR)
+            srow += ff * sc;
+            // ds/dr_ij = c r_ij, c = 2 f_i f_j Q sinc'(QR) / (N R) = c0 f_i f_j (cos y - sinc y) / y^2
+            const Real c = c0 * ff * (cs - sc) * iy * iy;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 g[a] -= c * r[a];
 #pragma unroll
-                for (int b = 0; b < 3; ++b) vir[3 * a + b] += r[a] * c * r[b];
+                for (int b = a; b < 3; ++b) vir[3 * a + b] += r[a] * c * r[b];
             }
         }
+        vir[3] = vir[1];
+        vir[6] = vir[2];
+        vir[7] = vir[5];
         grad[sy.ba0 + i] = make4<Vec4<Real>, Real>(g[0], g[1], g[2], Real(0));
         acc[0] = (double)fi * (double)fi + (double)srow;
 #pragma unroll

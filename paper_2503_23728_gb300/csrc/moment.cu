@@ -104,6 +104,58 @@ __device__ __forceinline__ void kahan_add(float2& s, float2& nc, const float2 v)
     s = t;
 }
 
+// Store the moments (lane slots) for the adjoint, and form G: per lane its
+// monomials' share of sum_abc 2^-zeta w lambda^s M^2, packed over lambda =
+// (+1, -1), then the 32-channel transposed reduction; the j = k terms
+// (1 + lambda)^zeta 2^-zeta sum_j b^2 = sum_j b^2 leave the lambda = +1
+// channels. Lane = channel nu = (zeta_index * 2 + lambda_index) * 4 + eta_index.
+__device__ __forceinline__ void finish_moments(const float2 (&acc)[MSLOT][2], const float (&diag)[4], float Gr,
+                                               unsigned lane, int b, float* __restrict__ G,
+                                               float4* __restrict__ Mout)
+{
+    if (Mout != nullptr) {
+#pragma unroll
+        for (int k = 0; k < MSLOT; ++k)
+            Mout[((size_t)b * MSLOT + k) * 32 + lane] =
+                make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
+    }
+
+    // per lane: its monomials' share of sum_abc 2^-zeta w lambda^s M^2, packed
+    // over lambda = (+1, -1); then the 32-channel transposed reduction
+    float2 S[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) S[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < MSLOT; ++k) {
+        const float sg = g_mono.sg[k][lane];
+        const float mm[4] = {acc[k][0].x * acc[k][0].x, acc[k][0].y * acc[k][0].y, acc[k][1].x * acc[k][1].x,
+                             acc[k][1].y * acc[k][1].y};
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+            const float cz = g_mono.cf[k][z][lane];
+            const float2 c2 = make_float2(cz, cz * sg);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) S[z * 4 + e] = __ffma2_rn(c2, make_float2(mm[e], mm[e]), S[z * 4 + e]);
+        }
+    }
+    float ga[NA];
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ga[(2 * z) * 4 + e] = S[z * 4 + e].x;
+            ga[(2 * z + 1) * 4 + e] = S[z * 4 + e].y;
+        }
+    float Ga = transpose_reduce32(ga, lane);
+    // lane = channel nu = (zeta_index * 2 + lambda_index) * 4 + eta_index:
+    // remove the j = k terms, (1 + lambda)^zeta 2^-zeta sum_j b^2 = sum_j b^2 for lambda = +1
+    const int e = (int)lane & 3;
+    const float dge = e == 0 ? diag[0] : e == 1 ? diag[1] : e == 2 ? diag[2] : diag[3];
+    if ((lane & 4u) == 0) Ga -= dge;
+    G[(size_t)b * ND + lane] = Gr;
+    G[(size_t)b * ND + NR + lane] = Ga;
+}
+
 // ---------------------------------------------------------------------------
 // forward: warp per bead-atom. Neighbours are taken 32 at a time: each lane
 // forms its neighbour's geometry, radial terms, weights b_eta and the 165
@@ -239,48 +291,217 @@ __global__ void __launch_bounds__(32 * FWD_WARPS) desc_mom_fwd_kernel(
     float diag[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) diag[e] = warp_sum(dg[e]);
+    finish_moments(acc, diag, Gr, lane, b, G, Mout);
+}
 
-    if (Mout != nullptr) {
-#pragma unroll
-        for (int k = 0; k < MSLOT; ++k)
-            Mout[((size_t)b * MSLOT + k) * 32 + lane] =
-                make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
+// ---------------------------------------------------------------------------
+// Reduced basis (BF16 network path). On the unit sphere x^2 = 1 - y^2 - z^2,
+// so m_abc = m_(a-2)bc - m_(a-2)(b+2)c - m_(a-2)b(c+2): every polynomial of
+// degree <= 8 in u equals one in the 81 monomials with a in {0, 1}, and
+// the moments of all 165 monomials follow from those 81 by that recurrence
+// (a = 2 .. 8 in turn). The adjoint needs only the tangential gradient of
+// sum Q m(u), which the restricted polynomial shares, so it folds Q onto the
+// 81 by the transposed recurrence. Differences cancel in the recurrence, so
+// the exact FP32 path keeps the 165-monomial form.
+// ---------------------------------------------------------------------------
+constexpr int NRED = 81;
+constexpr int RSLOT = 3;
+constexpr int RLAST = NRED - 32 * (RSLOT - 1);   // lanes holding a monomial in the last slot
+
+struct RedTab {
+    short red_full[RSLOT * 32];   // chain-order index of reduced monomial m' = lane + 32 slot, -1 beyond 81
+    short up[7][32][4];           // level a = 2..8: (m_abc, m_(a-2)bc, m_(a-2)(b+2)c, m_(a-2)b(c+2)), -1 idle
+    short down[7][2][32][4];      // level a = 8..2: target m_(a-2)BC and sources (a,B,C), (a,B-2,C), (a,B,C-2)
+};
+
+constexpr RedTab make_red_tab()
+{
+    RedTab t{};
+    for (int q = 0; q < RSLOT * 32; ++q) t.red_full[q] = -1;
+    int m = 0;
+    for (int c = 0; c <= MDEG; ++c)
+        for (int b = 0; b <= MDEG - c; ++b)
+            for (int a = 0; a <= 1 && a + b + c <= MDEG; ++a) t.red_full[m++] = (short)mono_index(a, b, c);
+    for (int L = 0; L < 7; ++L) {
+        const int a = L + 2;
+        int q = 0;
+        for (int i = 0; i < 32; ++i)
+            for (int k = 0; k < 4; ++k) t.up[L][i][k] = -1;
+        for (int c = 0; c <= MDEG - a; ++c)
+            for (int b = 0; b <= MDEG - a - c; ++b, ++q) {
+                t.up[L][q][0] = (short)mono_index(a, b, c);
+                t.up[L][q][1] = (short)mono_index(a - 2, b, c);
+                t.up[L][q][2] = (short)mono_index(a - 2, b + 2, c);
+                t.up[L][q][3] = (short)mono_index(a - 2, b, c + 2);
+            }
     }
+    for (int L = 0; L < 7; ++L) {
+        const int a = MDEG - L;   // 8 .. 2
+        for (int h = 0; h < 2; ++h)
+            for (int i = 0; i < 32; ++i)
+                for (int k = 0; k < 4; ++k) t.down[L][h][i][k] = -1;
+        int q = 0;
+        for (int C = 0; C <= MDEG - a + 2; ++C)
+            for (int B = 0; B <= MDEG - a + 2 - C; ++B, ++q) {
+                short* e = t.down[L][q / 32][q % 32];
+                e[0] = (short)mono_index(a - 2, B, C);
+                if (a + B + C <= MDEG) e[1] = (short)mono_index(a, B, C);
+                if (B >= 2) e[2] = (short)mono_index(a, B - 2, C);
+                if (C >= 2) e[3] = (short)mono_index(a, B, C - 2);
+            }
+    }
+    return t;
+}
 
-    // per lane: its monomials' share of sum_abc 2^-zeta w lambda^s M^2, packed
-    // over lambda = (+1, -1); then the 32-channel transposed reduction
-    float2 S[16];
+__device__ const RedTab g_red = make_red_tab();
+
+// reduced-basis forward (BF16 path): the 81 monomials per neighbour, 3 slots
+// per lane; the 165 moments are then rebuilt in shared memory by the
+// recurrence and finished as in the full forward
+constexpr int FWDR_WARP_FLOATS = 32 * NRED + 32 * 4;   // monomial rows (stride 81, odd) + weights
+constexpr int FWDR_WARPS = 8;
+static_assert(32 * NRED >= 4 * NMONO, "moment table reuses the monomial rows");
+
+template <bool FAST>
+__global__ void __launch_bounds__(32 * FWDR_WARPS, 2) desc_mom_fwd_red_kernel(
+    const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    float* MONO = reinterpret_cast<float*>(smem_raw) + (size_t)wib * FWDR_WARP_FLOATS;
+    float4* BW = reinterpret_cast<float4*>(MONO + 32 * NRED);
+    const int b = blockIdx.x * FWDR_WARPS + wib;
+    if (b >= B) return;
+    const BeadSys sy = bsys[ba_sys[b]];
+    const Rep& rp = reps[sy.rep];
+    const int n = min(nnb[b], maxnb);
+    const float4 xi = x[b];
+
+    float gr[NR];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) S[q] = make_float2(0.0f, 0.0f);
+    for (int c = 0; c < NR; ++c) gr[c] = 0.0f;
+    float dg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float2 acc[RSLOT][2];
+#pragma unroll
+    for (int k = 0; k < RSLOT; ++k) acc[k][0] = acc[k][1] = make_float2(0.0f, 0.0f);
+
+    for (int s0 = 0; s0 < n; s0 += 32) {
+        const int s = s0 + (int)lane;
+        if (s < n) {
+            const int j = nbr[(size_t)b * maxnb + s];
+            const float4 xj = x[sy.ba0 + j];
+            float dx, dy, dz;
+            pair_vec(rp, xi, xj, dx, dy, dz);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float r = sqrtf(r2);
+            const float ir = 1.0f / r;
+            float fc, dfc;
+            cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const float t = r - dp.r_mu[c];
+                gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+            }
+            float bw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                bw[e] = gauss<FAST>(dp.eta_A[e], dp.eta_A_l2[e], r2) * fc;
+                dg[e] = fmaf(bw[e], bw[e], dg[e]);
+            }
+            BW[lane] = make_float4(bw[0], bw[1], bw[2], bw[3]);
+            const float ux = dx * ir;
+            float py[MDEG + 1], pz[MDEG + 1];
+            py[0] = pz[0] = 1.0f;
+            py[1] = dy * ir;
+            pz[1] = dz * ir;
+#pragma unroll
+            for (int a = 2; a <= MDEG; ++a) {
+                py[a] = py[a - 1] * py[1];
+                pz[a] = pz[a - 1] * pz[1];
+            }
+            float* row = MONO + (size_t)lane * NRED;
+            int m = 0;
+#pragma unroll
+            for (int c = 0; c <= MDEG; ++c)
+#pragma unroll
+                for (int bb = 0; bb <= MDEG - c; ++bb) {
+                    const float base = py[bb] * pz[c];
+                    row[m++] = base;
+                    if (bb + c < MDEG) row[m++] = base * ux;
+                }
+        }
+        __syncwarp();
+        const int cnt = min(32, n - s0);
+        const float* col = MONO + lane;
+        int j0 = 0;
+        // blocks of four neighbours without bounds checks, then the rest
+        for (; j0 + 4 <= cnt; j0 += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 w4 = BW[j0 + q];
+                const float2 w01 = make_float2(w4.x, w4.y), w23 = make_float2(w4.z, w4.w);
+                const float* rowj = col + (size_t)(j0 + q) * NRED;
+#pragma unroll
+                for (int k = 0; k < RSLOT; ++k) {
+                    if (k < RSLOT - 1 || lane < (unsigned)RLAST) {
+                        const float mv = rowj[32 * k];
+                        const float2 m2 = make_float2(mv, mv);
+                        acc[k][0] = __ffma2_rn(w01, m2, acc[k][0]);
+                        acc[k][1] = __ffma2_rn(w23, m2, acc[k][1]);
+                    }
+                }
+            }
+        }
+        for (; j0 < cnt; ++j0) {
+            const float4 w4 = BW[j0];
+            const float2 w01 = make_float2(w4.x, w4.y), w23 = make_float2(w4.z, w4.w);
+            const float* rowj = col + (size_t)j0 * NRED;
+#pragma unroll
+            for (int k = 0; k < RSLOT; ++k) {
+                if (k < RSLOT - 1 || lane < (unsigned)RLAST) {
+                    const float mv = rowj[32 * k];
+                    const float2 m2 = make_float2(mv, mv);
+                    acc[k][0] = __ffma2_rn(w01, m2, acc[k][0]);
+                    acc[k][1] = __ffma2_rn(w23, m2, acc[k][1]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    const float Gr = transpose_reduce32(gr, lane);
+    float diag[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) diag[e] = warp_sum(dg[e]);
+
+    // the 165 moments from the 81 (rows of the last chunk are no longer needed)
+    float4* T = reinterpret_cast<float4*>(MONO);
+#pragma unroll
+    for (int k = 0; k < RSLOT; ++k) {
+        const int mf = g_red.red_full[k * 32 + lane];
+        if (mf >= 0) T[mf] = make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int L = 0; L < 7; ++L) {
+        const short* e = g_red.up[L][lane];
+        if (e[0] >= 0) {
+            const float4 a0 = T[e[1]], a1 = T[e[2]], a2 = T[e[3]];
+            T[e[0]] = make_float4(a0.x - a1.x - a2.x, a0.y - a1.y - a2.y, a0.z - a1.z - a2.z, a0.w - a1.w - a2.w);
+        }
+        __syncwarp();
+    }
+    float2 full[MSLOT][2];
 #pragma unroll
     for (int k = 0; k < MSLOT; ++k) {
-        const float sg = g_mono.sg[k][lane];
-        const float mm[4] = {acc[k][0].x * acc[k][0].x, acc[k][0].y * acc[k][0].y, acc[k][1].x * acc[k][1].x,
-                             acc[k][1].y * acc[k][1].y};
-#pragma unroll
-        for (int z = 0; z < 4; ++z) {
-            const float cz = g_mono.cf[k][z][lane];
-            const float2 c2 = make_float2(cz, cz * sg);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) S[z * 4 + e] = __ffma2_rn(c2, make_float2(mm[e], mm[e]), S[z * 4 + e]);
-        }
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (k < MSLOT - 1 || lane < (unsigned)MLAST) v = T[lane + 32 * k];
+        full[k][0] = make_float2(v.x, v.y);
+        full[k][1] = make_float2(v.z, v.w);
     }
-    float ga[NA];
-#pragma unroll
-    for (int z = 0; z < 4; ++z)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            ga[(2 * z) * 4 + e] = S[z * 4 + e].x;
-            ga[(2 * z + 1) * 4 + e] = S[z * 4 + e].y;
-        }
-    float Ga = transpose_reduce32(ga, lane);
-    // lane = channel nu = (zeta_index * 2 + lambda_index) * 4 + eta_index:
-    // remove the j = k terms, (1 + lambda)^zeta 2^-zeta sum_j b^2 = sum_j b^2 for lambda = +1
-    const int e = (int)lane & 3;
-    const float dge = e == 0 ? diag[0] : e == 1 ? diag[1] : e == 2 ? diag[2] : diag[3];
-    if ((lane & 4u) == 0) Ga -= dge;
-    G[(size_t)b * ND + lane] = Gr;
-    G[(size_t)b * ND + NR + lane] = Ga;
+    finish_moments(full, diag, Gr, lane, b, G, Mout);
 }
 
 // ---------------------------------------------------------------------------
@@ -343,6 +564,34 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS, 2) desc_mom_adj_kernel(
         }
     }
     __syncwarp();
+    if (FAST) {
+        // reduced basis: fold Q onto the monomials with a in {0, 1} by the
+        // transposed recurrence, a = 8 .. 2 (sources at level a, targets at a - 2)
+#pragma unroll 1
+        for (int L = 0; L < 7; ++L) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const short* e = g_red.down[L][h][lane];
+                if (e[0] >= 0) {
+                    float4 t = Q[e[0]];
+                    if (e[1] >= 0) {
+                        const float4 u = Q[e[1]];
+                        t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+                    }
+                    if (e[2] >= 0) {
+                        const float4 u = Q[e[2]];
+                        t.x -= u.x; t.y -= u.y; t.z -= u.z; t.w -= u.w;
+                    }
+                    if (e[3] >= 0) {
+                        const float4 u = Q[e[3]];
+                        t.x -= u.x; t.y -= u.y; t.z -= u.z; t.w -= u.w;
+                    }
+                    Q[e[0]] = t;
+                }
+            }
+            __syncwarp();
+        }
+    }
 
     float fi[3] = {0.0f, 0.0f, 0.0f};
     float wl[9];
@@ -383,7 +632,8 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS, 2) desc_mom_adj_kernel(
             float2 S0, S1, SX0, SX1, SY0, SY1;
 #pragma unroll
             for (int bb = MDEG - c; bb >= 0; --bb) {
-                const int A = MDEG - bb - c;
+                // x-degree of the chain: up to 8, or 1 in the reduced basis
+                const int A = (FAST && MDEG - bb - c > 1) ? 1 : MDEG - bb - c;
                 const int m0 = mono_index(0, bb, c);
                 float4 q = Q[m0 + A];
                 float2 R0 = make_float2(q.x, q.y), R1 = make_float2(q.z, q.w);
@@ -499,10 +749,19 @@ static void run_adj(const Dev& d, const void* dpv, cudaStream_t st)
         (float*)d.wbuf, d.deterministic, (float4*)d.vbuf);
 }
 
+static void run_fwd_red(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    const size_t sm = (size_t)FWDR_WARPS * FWDR_WARP_FLOATS * sizeof(float);
+    { static size_t done = 0; set_smem(desc_mom_fwd_red_kernel<true>, sm, done); }
+    desc_mom_fwd_red_kernel<true><<<(d.B + FWDR_WARPS - 1) / FWDR_WARPS, 32 * FWDR_WARPS, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+        *(const DescParams<float>*)dpv, (float*)d.G, (float4*)d.mom);
+}
+
 void launch_descriptors_moment(const Dev& d, const void* dpv, cudaStream_t st)
 {
     if (d.precision == 2)
-        run_fwd<true>(d, dpv, st);
+        run_fwd_red(d, dpv, st);
     else
         run_fwd<false>(d, dpv, st);
 }
