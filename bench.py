@@ -42,6 +42,11 @@ ADJ_FLOP_PER_NBR = 380
 # monomials x (16 FMA + 4 mul)).
 MOM_ADJ_FLOP_PER_NBR = 380 + 2 * 1340
 MOM_ADJ_FLOP_PER_ATOM = 165 * 36
+# BF16 network path, reduced basis (the 81 monomials with x-degree <= 1):
+# 668 FMA per neighbour (144 in x, 400 in y, 124 in z); per bead-atom also
+# the fold of dE/dM onto the 81 (161 targets x up to 3 adds x 4 widths)
+MOM_RED_ADJ_FLOP_PER_NBR = 380 + 2 * 668
+MOM_RED_ADJ_FLOP_PER_ATOM = 165 * 36 + 161 * 3 * 4
 
 
 def args():
@@ -182,6 +187,8 @@ def timed_steps(a, ctx, stream, flush, barrier):
 def adjoint_flops(ctx) -> float:
     nnb, _ = ctx.neighbours()
     n = nnb.astype(np.float64)
+    if ctx.angular == "moments" and ctx.precision == "bf16_tc":
+        return float(np.sum(MOM_RED_ADJ_FLOP_PER_NBR * n + MOM_RED_ADJ_FLOP_PER_ATOM))
     if ctx.angular == "moments":
         return float(np.sum(MOM_ADJ_FLOP_PER_NBR * n + MOM_ADJ_FLOP_PER_ATOM))
     return float(np.sum(ADJ_FLOP_PER_PAIR * n * (n - 1) / 2 + ADJ_FLOP_PER_NBR * n))

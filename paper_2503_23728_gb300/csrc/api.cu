@@ -366,7 +366,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
         o.md_dvds = c.take(md ? sizeof(double) * b.S : 0);
         o.md_cvpart = c.take(sizeof(double) * b.S * nt);
         o.md_virpart = c.take(sizeof(double) * 9 * b.S * nt);
-        o.md_grad = c.take(md ? v4 * (size_t)b.B : 0);
+        o.md_grad = c.take(md ? v4 * (size_t)b.B * (cfg->metad->cv == PIMD_CV_XRD ? MD_SLICES : 1) : 0);
     }
     o.step = c.take(sizeof(unsigned long long));
     o.err = c.take(sizeof(DevErr));

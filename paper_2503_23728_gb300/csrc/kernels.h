@@ -124,7 +124,8 @@ size_t tc_weight_bytes(int width, int n_hidden);
 void prepare_tc_weights(const Dev& d, int type, const double* blob, void* host_img, float* host_vec);
 
 // metadynamics
-int metad_tiles(int max_N);
+constexpr int MD_SLICES = 8;           // XRD CV: row slices per atom tile (gradient buffers)
+int metad_tiles(int max_N);            // partial sums per bead-system (tiles x slices)
 void launch_metad(const Dev& d, bool deposit, cudaStream_t st);
 
 // structural analysis

@@ -54,12 +54,14 @@ __global__ void cv_dist_kernel(const Vec4<Real>* __restrict__ x, const BeadSys* 
 }
 
 // ---------------------------------------------------------------------------
-// XRD CV: grid (atom tiles, bead-systems); thread per atom i sums its whole
-// row j != i (no atomics: every pair is seen from both ends), giving
+// XRD CV: grid (atom tiles x row slices, bead-systems); thread per atom i
+// sums its row j != i over one of MD_SLICES slices (no atomics: every pair is
+// seen from both ends), giving
 //   N s = sum_i [f_i^2 + sum_(j != i) f_i f_j sinc(Q R_ij)],
 //   ds/dx_i = (2/N) sum_(j != i) f_i f_j Q sinc'(Q R_ij) (x_i - x_j) / R_ij,
-// and the pair virial (halved, each pair twice). Block sums in FP64 go to
-// per-tile partials, added in fixed order by the bias kernel.
+// and the pair virial (halved, each pair twice). Gradients go to per-slice
+// buffers and block sums (FP64) to per-(tile, slice) partials; the bias
+// kernels add both in a fixed order.
 // ---------------------------------------------------------------------------
 // sin and cos of y >= 0. FP32: Cody-Waite reduction y - 2 pi k with 2 pi
 // split into a float head and the float of the remainder (k = rint(y / 2 pi)
@@ -99,14 +101,17 @@ __global__ void __launch_bounds__(128) cv_xrd_kernel(const Vec4<Real>* __restric
                                                      const BeadSys* __restrict__ bsys, const Rep* __restrict__ reps,
                                                      const int* __restrict__ atype, MetadParams mp,
                                                      Vec4<Real>* __restrict__ grad, double* __restrict__ cvpart,
-                                                     double* __restrict__ virpart, int ntile)
+                                                     double* __restrict__ virpart, int ntile, int B)
 {
     __shared__ double red[10][4];
     const int k = blockIdx.y;
     const BeadSys sy = bsys[k];
     const Rep& rp = reps[sy.rep];
     const int N = sy.N;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tile = blockIdx.x / MD_SLICES, slice = blockIdx.x - tile * MD_SLICES;
+    const int i = tile * blockDim.x + threadIdx.x;
+    const int jper = (N + MD_SLICES - 1) / MD_SLICES;
+    const int jlo = slice * jper, jhi = min(N, jlo + jper);
     const Real Q = (Real)mp.Q;
     double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // N s share, then the 9 virial entries
     if (i < N) {
@@ -116,7 +121,7 @@ __global__ void __launch_bounds__(128) cv_xrd_kernel(const Vec4<Real>* __restric
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir[q] = Real(0);
         const Real c0 = Real(2) * Q * Q / (Real)N;   // c = c0 f_i f_j (y cos y - sin y) / y^3
-        for (int j = 0; j < N; ++j) {
+        for (int j = jlo; j < jhi; ++j) {
             if (j == i) continue;
             Real r[3];
             xrd_pair(rp, xi, x[sy.ba0 + j], r);
@@ -141,8 +146,8 @@ __global__ void __launch_bounds__(128) cv_xrd_kernel(const Vec4<Real>* __restric
         vir[3] = vir[1];
         vir[6] = vir[2];
         vir[7] = vir[5];
-        grad[sy.ba0 + i] = make4<Vec4<Real>, Real>(g[0], g[1], g[2], Real(0));
-        acc[0] = (double)fi * (double)fi + (double)srow;
+        grad[(size_t)slice * B + sy.ba0 + i] = make4<Vec4<Real>, Real>(g[0], g[1], g[2], Real(0));
+        acc[0] = (slice == 0 ? (double)fi * (double)fi : 0.0) + (double)srow;
 #pragma unroll
         for (int q = 0; q < 9; ++q) acc[1 + q] = 0.5 * (double)vir[q];
     }
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(128) cv_xrd_kernel(const Vec4<Real>* __restric
         if (threadIdx.x == 0)
             cvpart[(size_t)k * ntile + blockIdx.x] = v;
         else
-            virpart[((size_t)k * ntile + blockIdx.x) * 9 + threadIdx.x - 1] = v;
+            virpart[((size_t)k * ntile + blockIdx.x) * 9 + threadIdx.x - 1] = v;   // ntile counts (tile, slice)
     }
 }
 
@@ -219,15 +224,19 @@ __global__ void bias_kernel(const Rep* __restrict__ reps, const BeadSys* __restr
     if (k == 0) nhill[r] = n + rp.P;
 }
 
-// f_b -= dV/ds ds/dx_b for every bead-atom
+// f_b -= dV/ds ds/dx_b for every bead-atom (gradient slices added in order)
 template <typename Real>
 __global__ void bias_force_kernel(const int* __restrict__ ba_sys, const Vec4<Real>* __restrict__ grad,
-                                  const double* __restrict__ dvds, Vec4<Real>* __restrict__ f, int B)
+                                  const double* __restrict__ dvds, Vec4<Real>* __restrict__ f, int B, int nslice)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const Real dv = (Real)dvds[ba_sys[b]];
-    const Vec4<Real> g = grad[b];
+    Vec4<Real> g = grad[b];
+    for (int q = 1; q < nslice; ++q) {
+        const Vec4<Real> h = grad[(size_t)q * B + b];
+        g.x += h.x; g.y += h.y; g.z += h.z;
+    }
     Vec4<Real> v = f[b];
     v.x -= dv * g.x;
     v.y -= dv * g.y;
@@ -235,13 +244,14 @@ __global__ void bias_force_kernel(const int* __restrict__ ba_sys, const Vec4<Rea
     f[b] = v;
 }
 
-int metad_tiles(int max_N) { return (max_N + 127) / 128; }
+int metad_tiles(int max_N) { return (max_N + 127) / 128 * MD_SLICES; }
 
 void launch_metad(const Dev& d, bool deposit, cudaStream_t st)
 {
     const MetadParams& mp = d.metad;
     const int ntile = metad_tiles(d.max_N);
     const size_t v4 = d.precision == 0 ? sizeof(Dbl4) : sizeof(float4);
+    const int nslice = mp.cv == PIMD_CV_XRD ? MD_SLICES : 1;
     if (mp.cv == PIMD_CV_DISTANCES) {
         cudaMemsetAsync(d.md_grad, 0, v4 * d.B, st);
         if (d.precision == 0)
@@ -256,20 +266,20 @@ void launch_metad(const Dev& d, bool deposit, cudaStream_t st)
         const dim3 grid(ntile, d.S);
         if (d.precision == 0)
             cv_xrd_kernel<double><<<grid, 128, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, d.atype, mp,
-                                                        (Dbl4*)d.md_grad, d.md_cvpart, d.md_virpart, ntile);
+                                                        (Dbl4*)d.md_grad, d.md_cvpart, d.md_virpart, ntile, d.B);
         else
             cv_xrd_kernel<float><<<grid, 128, 0, st>>>((const float4*)d.x, d.bsys, d.reps, d.atype, mp,
-                                                       (float4*)d.md_grad, d.md_cvpart, d.md_virpart, ntile);
+                                                       (float4*)d.md_grad, d.md_cvpart, d.md_virpart, ntile, d.B);
     }
     bias_kernel<<<d.R, d.max_P, 0, st>>>(d.reps, d.bsys, mp, d.md_cvpart, d.md_virpart, ntile, d.md_hills,
                                          d.md_nhill, d.md_cv, d.md_vb, d.md_dvds, d.V, d.W, d.step,
                                          deposit ? 1 : 0, d.err);
     if (d.precision == 0)
         bias_force_kernel<double><<<(d.B + 255) / 256, 256, 0, st>>>(d.ba_sys, (const Dbl4*)d.md_grad, d.md_dvds,
-                                                                     (Dbl4*)d.f, d.B);
+                                                                     (Dbl4*)d.f, d.B, nslice);
     else
         bias_force_kernel<float><<<(d.B + 255) / 256, 256, 0, st>>>(d.ba_sys, (const float4*)d.md_grad, d.md_dvds,
-                                                                    (float4*)d.f, d.B);
+                                                                    (float4*)d.f, d.B, nslice);
 }
 
 }  // namespace pimd

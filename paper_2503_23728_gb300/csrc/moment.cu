@@ -359,7 +359,7 @@ __device__ const RedTab g_red = make_red_tab();
 // per lane; the 165 moments are then rebuilt in shared memory by the
 // recurrence and finished as in the full forward
 constexpr int FWDR_WARP_FLOATS = 32 * NRED + 32 * 4;   // monomial rows (stride 81, odd) + weights
-constexpr int FWDR_WARPS = 8;
+constexpr int FWDR_WARPS = 4;
 static_assert(32 * NRED >= 4 * NMONO, "moment table reuses the monomial rows");
 
 template <bool FAST>
@@ -388,11 +388,13 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 2) desc_mom_fwd_red_kernel(
 #pragma unroll
     for (int k = 0; k < RSLOT; ++k) acc[k][0] = acc[k][1] = make_float2(0.0f, 0.0f);
 
+    // the next chunk's neighbour position is loaded while this chunk computes
+    float4 xnext = ((int)lane < n) ? x[sy.ba0 + nbr[(size_t)b * maxnb + lane]] : xi;
     for (int s0 = 0; s0 < n; s0 += 32) {
         const int s = s0 + (int)lane;
+        const float4 xj = xnext;
+        if (s + 32 < n) xnext = x[sy.ba0 + nbr[(size_t)b * maxnb + s + 32]];
         if (s < n) {
-            const int j = nbr[(size_t)b * maxnb + s];
-            const float4 xj = x[sy.ba0 + j];
             float dx, dy, dz;
             pair_vec(rp, xi, xj, dx, dy, dz);
             const float r2 = dx * dx + dy * dy + dz * dz;

@@ -470,6 +470,7 @@ class Context:
         self.torch = torch
         self.keep = _Keep()
         self.replicas = list(replicas)
+        self.precision = precision if isinstance(precision, str) else {v: k for k, v in PRECISION.items()}[precision]
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
