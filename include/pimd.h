@@ -166,6 +166,14 @@ typedef struct {
     int free_rp;             /* pimd_free_rp: free ring-polymer propagator       */
     const pimd_metad_desc* metad; /* NULL: no bias. Read during pimd_workspace_size
                                 and pimd_create only.                          */
+    double nbr_skin_A;       /* Verlet skin of the neighbour candidates: each
+                                bead keeps the atoms within r_c + skin, rebuilt
+                                when the two largest atom displacements since the
+                                last build add up to 0.98 skin; every step filters
+                                them with the exact rule, so the lists equal a
+                                full rebuild. < 0: 1 A (reduced to 0.9 of the room
+                                between r_c and half the box, off below 0.05 A);
+                                0: rebuild every step.                         */
 } pimd_config;
 
 /* stages of one step, in launch order (pimd_stage_times) */

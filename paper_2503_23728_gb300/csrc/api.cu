@@ -57,8 +57,14 @@ struct Build {
     int R = 0, S = 0, B = 0, NA = 0, rows_pad = 0;
     size_t blob = 0, wtc_bytes = 0, wtc_vec = 0;
     bool periodic_any = false;
+    bool any_skin = false;
     double nb_est = 0.0;   // mean neighbour count per bead-atom (estimate from density)
 };
+
+// candidate slots per atom for Verlet lists: 1.5 x the neighbour slots
+// (a skin of 0.5 A at r_c = 6 A holds 1.27 x the neighbours), multiple of 32,
+// at most the sort capacity
+int max_candidates(int maxnb) { return std::min(PIMD_SORT_CAP, (maxnb * 3 / 2 + 31) / 32 * 32); }
 
 struct Carve {
     size_t off = 0;
@@ -75,7 +81,7 @@ struct Offsets {
     size_t reps, bsys, ba_sys, mass, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
         fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
-        md_virpart, md_grad, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
+        md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
 };
 
 int check_config(const pimd_config* cfg, std::string& e)
@@ -85,6 +91,7 @@ int check_config(const pimd_config* cfg, std::string& e)
     if (cfg->precision < 0 || cfg->precision > 2) { e = "unknown precision"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat != 0 && cfg->thermostat != 1) { e = "thermostat must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->nbr_algo < 0 || cfg->nbr_algo > 2) { e = "nbr_algo must be 0, 1 or 2"; return PIMD_ERR_INVALID_ARG; }
+    if (!std::isfinite(cfg->nbr_skin_A)) { e = "nbr_skin_A must be finite"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->splitting != PIMD_OBABO && cfg->splitting != PIMD_BAOAB) { e = "splitting must be PIMD_OBABO or PIMD_BAOAB"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->free_rp != PIMD_FREE_RP_EXACT && cfg->free_rp != PIMD_FREE_RP_CAYLEY) { e = "free_rp must be PIMD_FREE_RP_EXACT or PIMD_FREE_RP_CAYLEY"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->deterministic != 0 && cfg->deterministic != 1) { e = "deterministic must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
@@ -221,11 +228,24 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         }
         rp.kT_md = h.P * KB * h.T / MVV2E;
         rp.seed = h.seed;
-        // cell lists: >= 3 cells per side with edge >= cutoff (1e-5 margin
-        // against rounding of the FP32 cell coordinate)
+        // Verlet skin of the candidate lists: at most 0.9 of the room between
+        // r_c and half the box (unique minimum images), off below 0.05 A
+        if (cfg->potential == PIMD_POT_MODEL) {
+            double sk = cfg->nbr_skin_A < 0.0 ? 1.0 : cfg->nbr_skin_A;
+            if (rp.periodic)
+                sk = std::min(sk, 0.9 * (0.5 * std::min(std::min(h.box[0], h.box[1]), h.box[2]) - cfg->cutoff_A));
+            if (sk < 0.05) sk = 0.0;
+            rp.skin = (float)sk;
+            const double rcs = cfg->cutoff_A + sk;
+            rp.rcs2 = (float)(rcs * rcs);
+            if (sk > 0.0) b.any_skin = true;
+        }
+        // cell lists: >= 3 cells per side with edge >= cutoff + skin (1e-5
+        // margin against rounding of the FP32 cell coordinate)
         if (rp.periodic && cfg->potential == PIMD_POT_MODEL && cfg->nbr_algo != 1) {
             int nc[3];
-            for (int a = 0; a < 3; ++a) nc[a] = (int)std::floor(h.box[a] / (cfg->cutoff_A * (1.0 + 1e-5)));
+            for (int a = 0; a < 3; ++a)
+                nc[a] = (int)std::floor(h.box[a] / ((cfg->cutoff_A + rp.skin) * (1.0 + 1e-5)));
             const long long ncell = (long long)nc[0] * nc[1] * nc[2];
             // auto: cells when the stencil scan (+ sort) beats scanning the bead
             const double warp_iter_cells = 27.0 * h.N / std::max(1ll, ncell) / 32.0 + 12.0;
@@ -354,6 +374,13 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.wbuf = c.take(rs * 9 * (size_t)b.B);
     o.vbuf = c.take(cfg->deterministic && model ? v4 * (size_t)b.B * mnb : 0);
     o.mom = c.take(model && cfg->precision != PIMD_FP64 ? sizeof(float4) * moment_elems_per_atom() * (size_t)b.B : 0);
+    {
+        const size_t mc = b.any_skin ? (size_t)max_candidates(mnb) : 0;
+        o.cand = c.take(sizeof(int) * (size_t)b.B * mc);
+        o.ncand = c.take(mc ? sizeof(int) * (size_t)b.B : 0);
+        o.xref = c.take(mc ? sizeof(float4) * (size_t)b.B : 0);
+        o.rebuild = c.take(mc ? sizeof(int) * (size_t)b.S : 0);
+    }
     {
         const bool md = cfg->metad && cfg->metad->cv != PIMD_CV_NONE;
         int maxN = 1;
@@ -619,6 +646,13 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.wbuf = w + o.wbuf;
     d.vbuf = w + o.vbuf;
     d.mom = (cfg->potential == PIMD_POT_MODEL && cfg->precision != PIMD_FP64) ? (void*)(w + o.mom) : nullptr;
+    if (b.any_skin) {
+        d.maxcand = max_candidates(d.maxnb);
+        d.cand = (int*)(w + o.cand);
+        d.ncand = (int*)(w + o.ncand);
+        d.xref = (float4*)(w + o.xref);
+        d.rebuild = (int*)(w + o.rebuild);
+    }
     for (const Rep& rp : b.reps) d.max_P = std::max(d.max_P, rp.P);
     if (cfg->metad && cfg->metad->cv != PIMD_CV_NONE) {
         const pimd_metad_desc* m = cfg->metad;
@@ -715,6 +749,11 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
         if (rc) { std::string m = c->err; delete c; return fail(nullptr, rc, m); }
     }
     cudaMemsetAsync(d.Q, 0, sizeof(double) * d.R, c->st);
+    if (d.maxcand) {
+        // reference positions far away: the first list build rebuilds every bead
+        cudaMemsetAsync(d.xref, 0x7f, sizeof(float4) * d.B, c->st);
+        cudaMemsetAsync(d.ncand, 0, sizeof(int) * d.B, c->st);
+    }
     if (d.metad.cv) {
         cudaMemsetAsync(d.md_nhill, 0, sizeof(int) * d.R, c->st);
         cudaMemsetAsync(d.md_cv, 0, sizeof(double) * d.S, c->st);

@@ -54,6 +54,8 @@ struct Rep {
     int nc[3];               // cells per side (cell lists), 0 = scan all atoms
     int ncells;              // nc[0] nc[1] nc[2], 0 without cells
     int cell0;               // first cell of bead 0; bead k owns cell0 + k ncells ..
+    float skin;              // Verlet skin of the candidate lists, A (0 = rebuild every step)
+    float rcs2;              // (float)((r_c + skin)^2), candidate radius squared
     int pad;
 };
 

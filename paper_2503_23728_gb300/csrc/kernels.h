@@ -39,6 +39,11 @@ struct Dev {
     int* cell_cnt = nullptr;           // per cell: atom count
     int* cell_atoms = nullptr;         // [B] atoms of each bead grouped by cell
     int* cell_bs = nullptr;            // beads that use cell lists
+    int* cand = nullptr;               // [B][maxcand] Verlet candidate lists (r < r_c + skin)
+    int* ncand = nullptr;              // [B]
+    float4* xref = nullptr;            // [B] FP32 positions at the last candidate build
+    int* rebuild = nullptr;            // [S] 1: rebuild this bead's candidates now
+    int maxcand = 0;                   // 0: no replica uses a skin
     int n_cell_bs = 0, max_cells = 0;
     void* G = nullptr;                 // Real[B][64]
     void* dEdG = nullptr;              // Real[B][64]

@@ -91,36 +91,27 @@ __global__ void cell_build_kernel(const V4* __restrict__ x, const BeadSys* __res
     }
 }
 
-// warp per bead-atom
+// Neighbours of bead-atom il (FP32 position xi) with rule radius r2cut, in
+// ascending order into out[0 .. cap); returns the count (may exceed cap).
+// Beads without cells scan all their atoms; beads with cells scan the 27
+// stencil cells and sort what passes (L: the warp's shared sort buffer).
 template <typename V4>
-__global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, const int* __restrict__ ba_sys,
-                                                  const BeadSys* __restrict__ bsys, const Rep* __restrict__ reps,
-                                                  const int* __restrict__ cell_start, const int* __restrict__ cell_cnt,
-                                                  const int* __restrict__ cell_atoms, float rc2, int maxnb, int B,
-                                                  int* __restrict__ nbr, int* __restrict__ nnb,
-                                                  DevErr* __restrict__ err)
+__device__ int scan_list(const V4* __restrict__ x, const BeadSys& sy, const Rep& rp, int il, const float3& xi,
+                         const int* __restrict__ cell_start, const int* __restrict__ cell_cnt,
+                         const int* __restrict__ cell_atoms, float r2cut, int* __restrict__ out, int cap, int* L,
+                         unsigned lane)
 {
-    __shared__ int lst[8][PIMD_SORT_CAP];
-    const int wib = threadIdx.x >> 5;
-    const int b = blockIdx.x * (blockDim.x >> 5) + wib;
-    const unsigned lane = lane_id();
-    if (b >= B) return;
-    const BeadSys sy = bsys[ba_sys[b]];
-    const Rep& rp = reps[sy.rep];
-    const int il = b - sy.ba0;
-    const float3 xi = pos_f32(x[b]);
     int cnt = 0;
     if (rp.ncells == 0) {
         for (int j0 = 0; j0 < sy.N; j0 += 32) {
             const int j = j0 + (int)lane;
-            const bool in = j < sy.N && j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
+            const bool in = j < sy.N && j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), r2cut);
             const unsigned m = __ballot_sync(0xffffffffu, in);
             const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-            if (in && pos < maxnb) nbr[(size_t)b * maxnb + pos] = j;
+            if (in && pos < cap) out[pos] = j;
             cnt += __popc(m);
         }
     } else {
-        int* L = lst[wib];
         const int3 ci = cell_of(rp, xi);
         const int cbase = rp.cell0 + sy.bead * rp.ncells;
         // lane s < 27 holds stencil cell s; an inclusive scan of the counts
@@ -158,16 +149,16 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
             int j = -1;
             if (t < total) {
                 j = cell_atoms[base + (t - before)];
-                in = j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
+                in = j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), r2cut);
             }
             const unsigned m = __ballot_sync(0xffffffffu, in);
             const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-            if (in && pos < maxnb) L[pos] = j;
+            if (in && pos < cap) L[pos] = j;
             cnt += __popc(m);
         }
         __syncwarp();
         // ascending order: bitonic sort over the next power of two, padded
-        const int m = cnt < maxnb ? cnt : maxnb;
+        const int m = cnt < cap ? cnt : cap;
         int n2 = 1;
         while (n2 < m) n2 <<= 1;
         for (int t = m + (int)lane; t < n2; t += 32) L[t] = 0x7fffffff;
@@ -188,7 +179,111 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
                 __syncwarp();
             }
         }
-        for (int t = (int)lane; t < m; t += 32) nbr[(size_t)b * maxnb + t] = L[t];
+        for (int t = (int)lane; t < m; t += 32) out[t] = L[t];
+    }
+    return cnt;
+}
+
+// Verlet candidates: a pair's distance changes by at most the sum of its two
+// atoms' displacements, so a bead's candidates stay complete while the two
+// largest displacements (FP32 positions, since the last build) sum to less
+// than 0.98 skin; block per bead, top-two reduction.
+__device__ __forceinline__ void top2_merge(float& a1, float& a2, float b1, float b2)
+{
+    // (a1 >= a2), (b1 >= b2) -> the two largest of the four
+    const float hi = fmaxf(a1, b1), lo = fminf(a1, b1);
+    a2 = fmaxf(lo, fmaxf(a2, b2));
+    a1 = hi;
+}
+
+template <typename V4>
+__global__ void skin_check_kernel(const V4* __restrict__ x, const BeadSys* __restrict__ bsys,
+                                  const Rep* __restrict__ reps, const float4* __restrict__ xref,
+                                  int* __restrict__ rebuild)
+{
+    __shared__ float red[2][32];
+    const BeadSys sy = bsys[blockIdx.x];
+    const Rep& rp = reps[sy.rep];
+    float m1 = 0.0f, m2 = 0.0f;
+    for (int i = threadIdx.x; i < sy.N; i += blockDim.x) {
+        const float3 p = pos_f32(x[sy.ba0 + i]);
+        const float4 r = xref[sy.ba0 + i];
+        const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
+        const float d = sqrtf(dx * dx + dy * dy + dz * dz);   // +inf after a reset of the references
+        top2_merge(m1, m2, d, 0.0f);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const float b1 = __shfl_xor_sync(0xffffffffu, m1, o), b2 = __shfl_xor_sync(0xffffffffu, m2, o);
+        top2_merge(m1, m2, b1, b2);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = m1;
+        red[1][threadIdx.x >> 5] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a1 = red[0][0], a2 = red[1][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) top2_merge(a1, a2, red[0][w], red[1][w]);
+        rebuild[blockIdx.x] = (rp.skin > 0.0f && !(a1 + a2 < 0.98f * rp.skin)) ? 1 : 0;
+    }
+}
+
+// warp per bead-atom. With a skin: rebuild the candidates (r < r_c + skin)
+// when the bead is flagged, then keep the candidates the exact rule accepts,
+// in their ascending order, so the list equals a full scan; without a skin,
+// or when the candidates overflowed their slots, scan directly.
+template <typename V4>
+__global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, const int* __restrict__ ba_sys,
+                                                  const BeadSys* __restrict__ bsys, const Rep* __restrict__ reps,
+                                                  const int* __restrict__ cell_start, const int* __restrict__ cell_cnt,
+                                                  const int* __restrict__ cell_atoms, float rc2, int maxnb, int B,
+                                                  int* __restrict__ nbr, int* __restrict__ nnb,
+                                                  DevErr* __restrict__ err, int* __restrict__ cand,
+                                                  int* __restrict__ ncand, float4* __restrict__ xref,
+                                                  const int* __restrict__ rebuild, int maxcand)
+{
+    __shared__ int lst[8][PIMD_SORT_CAP];
+    const int wib = threadIdx.x >> 5;
+    const int b = blockIdx.x * (blockDim.x >> 5) + wib;
+    const unsigned lane = lane_id();
+    if (b >= B) return;
+    const int bs = ba_sys[b];
+    const BeadSys sy = bsys[bs];
+    const Rep& rp = reps[sy.rep];
+    const int il = b - sy.ba0;
+    const float3 xi = pos_f32(x[b]);
+    int* out = nbr + (size_t)b * maxnb;
+    int cnt;
+    if (rp.skin > 0.0f && maxcand > 0) {
+        int* cl = cand + (size_t)b * maxcand;
+        int nc;
+        if (rebuild[bs]) {
+            nc = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rp.rcs2, cl, maxcand, lst[wib], lane);
+            if (lane == 0) {
+                ncand[b] = nc;
+                xref[b] = make_float4(xi.x, xi.y, xi.z, 0.0f);
+            }
+            __syncwarp();   // the candidates written by all lanes are read by all lanes below
+        } else {
+            nc = ncand[b];
+        }
+        if (nc <= maxcand) {
+            cnt = 0;
+            for (int t0 = 0; t0 < nc; t0 += 32) {
+                const int t = t0 + (int)lane;
+                const int j = t < nc ? cl[t] : -1;
+                const bool in = t < nc && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                if (in && pos < maxnb) out[pos] = j;
+                cnt += __popc(m);
+            }
+        } else {
+            cnt = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rc2, out, maxnb, lst[wib], lane);
+        }
+    } else {
+        cnt = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rc2, out, maxnb, lst[wib], lane);
     }
     if (lane == 0) {
         nnb[b] = cnt;
@@ -208,15 +303,20 @@ void launch_neighbours(const Dev& d, cudaStream_t st)
         if (d.n_cell_bs)
             cell_build_kernel<Dbl4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
                 (const Dbl4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
+        if (d.maxcand)
+            skin_check_kernel<Dbl4><<<d.S, 128, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
         nbr_kernel<Dbl4><<<blocks, threads, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
-                                                     d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb, d.err);
+                                                     d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb, d.err,
+                                                     d.cand, d.ncand, d.xref, d.rebuild, d.maxcand);
     } else {
         if (d.n_cell_bs)
             cell_build_kernel<float4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
                 (const float4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
+        if (d.maxcand)
+            skin_check_kernel<float4><<<d.S, 128, 0, st>>>((const float4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
         nbr_kernel<float4><<<blocks, threads, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
                                                        d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb,
-                                                       d.err);
+                                                       d.err, d.cand, d.ncand, d.xref, d.rebuild, d.maxcand);
     }
 }
 
