@@ -140,7 +140,15 @@ __device__ __forceinline__ float2 unpack_bf16(uint32_t u)
     return __bfloat1622float2(h);
 }
 
-__device__ __forceinline__ float tanh_f(float v) { return tanhf(v); }
+// tanh on the special-function unit (tanh.approx.f32, relative error ~2^-11):
+// the activations are rounded to BF16 (2^-9) right after, so the accurate
+// library tanh would not change the result beyond that rounding
+__device__ __forceinline__ float tanh_f(float v)
+{
+    float r;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 
 // byte sizes / offsets of the weight images of one element type:
 // forward images W_l [W][in_l], then backward images W_l^T [in_l][W]
