@@ -171,9 +171,10 @@ typedef struct {
                                 when the two largest atom displacements since the
                                 last build add up to 0.98 skin; every step filters
                                 them with the exact rule, so the lists equal a
-                                full rebuild. < 0: 1 A (reduced to 0.9 of the room
-                                between r_c and half the box, off below 0.05 A);
-                                0: rebuild every step.                         */
+                                full rebuild. < 0: 1 A for replicas of >= 256
+                                atoms (reduced to 0.9 of the room between r_c
+                                and half the box, off below 0.05 A), none for
+                                smaller ones; 0: rebuild every step.           */
 } pimd_config;
 
 /* stages of one step, in launch order (pimd_stage_times) */

@@ -231,7 +231,9 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         // Verlet skin of the candidate lists: at most 0.9 of the room between
         // r_c and half the box (unique minimum images), off below 0.05 A
         if (cfg->potential == PIMD_POT_MODEL) {
-            double sk = cfg->nbr_skin_A < 0.0 ? 1.0 : cfg->nbr_skin_A;
+            // auto: 1 A for replicas of >= 256 atoms (small ones scan all atoms
+            // faster than they would check and filter candidates)
+            double sk = cfg->nbr_skin_A < 0.0 ? (h.N >= 256 ? 1.0 : 0.0) : cfg->nbr_skin_A;
             if (rp.periodic)
                 sk = std::min(sk, 0.9 * (0.5 * std::min(std::min(h.box[0], h.box[1]), h.box[2]) - cfg->cutoff_A));
             if (sk < 0.05) sk = 0.0;
