@@ -124,6 +124,7 @@ class OrSys(ct.Structure):
         ("splitting", ct.c_int),
         ("free_rp", ct.c_int),
         ("metad", ct.POINTER(OrMetad)),
+        ("transform", ct.c_int),
     ]
 
 
@@ -173,6 +174,9 @@ def lib():
         L.or_metad_bias.argtypes = [ct.POINTER(OrMetad), ct.c_double, ct.POINTER(ct.c_double)]
         L.or_metad_bias.restype = ct.c_double
         L.or_metad_deposit.argtypes = [ct.POINTER(OrMetad), ct.c_int, ct.c_double]
+        L.or_staging_to_beads.argtypes = [ct.c_int, dp, dp]
+        L.or_beads_to_staging.argtypes = [ct.c_int, dp, dp]
+        L.or_staging_forces.argtypes = [ct.c_int, dp, dp]
         L.or_free_rp_step.argtypes = [ct.c_int, ct.c_double, ct.c_double, ct.c_double,
                                       ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.or_get_threads.restype = ct.c_int
@@ -334,6 +338,41 @@ def pt_coordinate(x, box, bond, acceptor, v_min: float, v_max: float, n_bins: in
     return v, h
 
 
+def staging_to_beads(u):
+    """bead positions [P, N, 3] from staging coordinates [P, N, 3]"""
+    u = _f64(u)
+    P = u.shape[0]
+    x = np.zeros_like(u)
+    a, b = np.zeros(P), np.zeros(P)
+    for i in range(u.shape[1]):
+        for d in range(3):
+            a[:] = u[:, i, d]
+            lib().or_staging_to_beads(P, _dp(a), _dp(b))
+            x[:, i, d] = b
+    return x
+
+
+def beads_to_staging(x):
+    x = _f64(x)
+    P = x.shape[0]
+    u = np.zeros_like(x)
+    a, b = np.zeros(P), np.zeros(P)
+    for i in range(x.shape[1]):
+        for d in range(3):
+            a[:] = x[:, i, d]
+            lib().or_beads_to_staging(P, _dp(a), _dp(b))
+            u[:, i, d] = b
+    return u
+
+
+def staging_forces(f):
+    f = _f64(f)
+    P = len(f)
+    out = np.zeros(P)
+    lib().or_staging_forces(P, _dp(f), _dp(out))
+    return out
+
+
 def free_rp_step(free_rp: str, m: float, w: float, h: float, p: float, q: float) -> tuple:
     """One free ring-polymer step of one mode: (p, q) after time h."""
     pp, qq = ct.c_double(p), ct.c_double(q)
@@ -363,7 +402,7 @@ class System:
     def __init__(self, replica, masses: dict, dt: float, gamma0: float, pile_lambda: float = 1.0,
                  model=None, thermostat: bool = True, potential: str = "model", omega: float = 0.0,
                  replica_index: int = 0, maxnb: int = 256, splitting: str = "obabo",
-                 free_rp: str = "exact", metad: "Metad" = None):
+                 free_rp: str = "exact", metad: "Metad" = None, transform: str = "normal_modes"):
         self.mh = None if model is None else (model if isinstance(model, ModelHandle) else ModelHandle(model))
         self.Z = np.ascontiguousarray(replica.Z, dtype=np.int32)
         self.mass = _f64([masses[int(z)] for z in replica.Z])
@@ -386,6 +425,7 @@ class System:
         s.maxnb = int(maxnb)
         s.splitting = {"obabo": 0, "baoab": 1}[splitting]
         s.free_rp = {"exact": 0, "cayley": 1}[free_rp]
+        s.transform = {"normal_modes": 0, "staging": 1}[transform]
         self.metad = metad
         if metad is not None:
             s.metad = ct.pointer(metad.m)
@@ -419,6 +459,8 @@ class System:
             raise ValueError("oracle step failed (%d)" % r)
 
     def beads(self) -> np.ndarray:
+        if self.s.transform == 1:
+            return staging_to_beads(self.q)
         C = nm_matrix(self.P)
         return np.einsum("jk,kia->jia", C, self.q)
 

@@ -440,6 +440,58 @@ double or_normal(uint64_t seed, uint32_t index, uint32_t step, uint32_t replica,
 static double omega_P_of(const or_sys* s) { return s->P * KB * s->T / HBAR; }
 static double kT_P_md(const or_sys* s) { return s->P * KB * s->T / MVV2E; }
 
+/* ---- staging coordinates (Tuckerman's staging transformation) ------------
+ * For one (atom, dimension), beads x_1 .. x_P (x_(P+1) = x_1, array index
+ * k - 1):
+ *   u_1 = x_1,  u_k = x_k - ((k - 1) x_(k+1) + x_1) / k   (k = 2 .. P)
+ * and back, from k = P down to 2: x_k = u_k + ((k - 1)/k) x_(k+1) + x_1 / k.
+ * The spring energy sum_k 1/2 m w_P^2 (x_k - x_(k+1))^2 becomes
+ * sum_(k>=2) 1/2 m_k' w_P^2 u_k^2 with m_k' = k / (k - 1) m, so with these
+ * masses every u_k (k >= 2) oscillates at w_P and u_1 moves freely.
+ * Forces: -dPhi/du_1 = sum_j f_j, -dPhi/du_2 = f_2,
+ * -dPhi/du_k = f_k + ((k - 2)/(k - 1)) (-dPhi/du_(k-1)) for k >= 3.        */
+void or_staging_to_beads(int P, const double* u, double* x)
+{
+    x[0] = u[0];
+    double next = x[0];   /* x_(k+1), starting with x_(P+1) = x_1 */
+    for (int k = P; k >= 2; --k) {
+        x[k - 1] = u[k - 1] + ((double)(k - 1) / k) * next + x[0] / k;
+        next = x[k - 1];
+    }
+}
+
+void or_beads_to_staging(int P, const double* x, double* u)
+{
+    u[0] = x[0];
+    for (int k = 2; k <= P; ++k) {
+        double xn = (k == P) ? x[0] : x[k];
+        u[k - 1] = x[k - 1] - ((k - 1) * xn + x[0]) / k;
+    }
+}
+
+void or_staging_forces(int P, const double* f, double* Fu)
+{
+    double s = 0.0;
+    for (int j = 0; j < P; ++j) s += f[j];
+    Fu[0] = s;
+    if (P >= 2) Fu[1] = f[1];
+    for (int k = 3; k <= P; ++k) Fu[k - 1] = f[k - 1] + ((double)(k - 2) / (k - 1)) * Fu[k - 2];
+}
+
+/* mass of ring coordinate k (0-based) of atom i, and its free frequency */
+static double mode_mass(const or_sys* s, int k, int i)
+{
+    return (s->transform == 1 && k >= 1) ? s->mass[i] * (k + 1.0) / k : s->mass[i];
+}
+static void mode_freqs(const or_sys* s, double* wk)
+{
+    if (s->transform == 1) {
+        for (int k = 0; k < s->P; ++k) wk[k] = k == 0 ? 0.0 : omega_P_of(s);
+    } else {
+        or_nm_freqs(s->P, omega_P_of(s), wk);
+    }
+}
+
 int or_init(const or_sys* s, const double* x0, double* q_nm, double* p_nm)
 {
     int N = s->N, P = s->P;
@@ -448,8 +500,11 @@ int or_init(const or_sys* s, const double* x0, double* q_nm, double* p_nm)
         for (int i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
                 size_t g = ((size_t)k * N + i) * 3 + d;
-                q_nm[g] = (k == 0) ? sqrt((double)P) * x0[3 * i + d] : 0.0;
-                p_nm[g] = sqrt(s->mass[i] * kT) *
+                if (s->transform == 1)
+                    q_nm[g] = (k == 0) ? x0[3 * i + d] : 0.0;   /* all beads at x0 */
+                else
+                    q_nm[g] = (k == 0) ? sqrt((double)P) * x0[3 * i + d] : 0.0;
+                p_nm[g] = sqrt(mode_mass(s, k, i) * kT) *
                           or_normal(s->seed, (uint32_t)g, 0u, (uint32_t)s->replica, 1u);
             }
     return 0;
@@ -458,6 +513,19 @@ int or_init(const or_sys* s, const double* x0, double* q_nm, double* p_nm)
 static void to_beads(const or_sys* s, const double* C, const double* q_nm, double* xb)
 {
     int N = s->N, P = s->P;
+    if (s->transform == 1) {
+        double* u = malloc(sizeof(double) * P);
+        double* x = malloc(sizeof(double) * P);
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                for (int k = 0; k < P; ++k) u[k] = q_nm[((size_t)k * N + i) * 3 + d];
+                or_staging_to_beads(P, u, x);
+                for (int j = 0; j < P; ++j) xb[((size_t)j * N + i) * 3 + d] = x[j];
+            }
+        free(u);
+        free(x);
+        return;
+    }
     for (int j = 0; j < P; ++j)
         for (int i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
@@ -629,8 +697,9 @@ static void step_O(const or_sys* s, const double* wk, double h, uint32_t step, u
             for (int d = 0; d < 3; ++d) {
                 size_t g = ((size_t)k * N + i) * 3 + d;
                 double xi = or_normal(s->seed, (uint32_t)g, step, (uint32_t)s->replica, stream);
-                double pn = c1 * p_nm[g] + sqrt(s->mass[i] * kT) * c2 * xi;
-                dq += (pn * pn - p_nm[g] * p_nm[g]) / (2.0 * s->mass[i]);
+                double mk = mode_mass(s, k, i);
+                double pn = c1 * p_nm[g] + sqrt(mk * kT) * c2 * xi;
+                dq += (pn * pn - p_nm[g] * p_nm[g]) / (2.0 * mk);
                 p_nm[g] = pn;
             }
     }
@@ -641,6 +710,19 @@ static void step_O(const or_sys* s, const double* wk, double h, uint32_t step, u
 static void step_B(const or_sys* s, const double* C, const double* f, double* p_nm)
 {
     int N = s->N, P = s->P;
+    if (s->transform == 1) {
+        double* fb = malloc(sizeof(double) * P);
+        double* Fu = malloc(sizeof(double) * P);
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) {
+                for (int j = 0; j < P; ++j) fb[j] = f[((size_t)j * N + i) * 3 + d];
+                or_staging_forces(P, fb, Fu);
+                for (int k = 0; k < P; ++k) p_nm[((size_t)k * N + i) * 3 + d] += 0.5 * s->dt * Fu[k] / MVV2E;
+            }
+        free(fb);
+        free(Fu);
+        return;
+    }
     for (int k = 0; k < P; ++k)
         for (int i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
@@ -684,7 +766,7 @@ static void step_A(const or_sys* s, const double* wk, double h, double* q_nm, do
         for (int i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
                 size_t g = ((size_t)k * N + i) * 3 + d;
-                or_free_rp_step(s->free_rp, s->mass[i], k == 0 ? 0.0 : wk[k], h, &p_nm[g], &q_nm[g]);
+                or_free_rp_step(s->free_rp, mode_mass(s, k, i), k == 0 ? 0.0 : wk[k], h, &p_nm[g], &q_nm[g]);
             }
 }
 
@@ -699,7 +781,7 @@ int or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
     double* wk = malloc(sizeof(double) * P);
     double* xb = malloc(sizeof(double) * (size_t)P * N * 3);
     or_nm_matrix(P, C);
-    or_nm_freqs(P, omega_P_of(s), wk);
+    mode_freqs(s, wk);
     int rc = 0;
     for (int n = 0; n < nsteps; ++n) {
         uint32_t st = (uint32_t)(*step);
@@ -770,12 +852,12 @@ void or_estimators(const or_sys* s, const double* q_nm, const double* p_nm,
         }
     double K_cv = 3.0 * N / (2.0 * beta) - cv / (2.0 * P);
 
-    double kin = 0.0; /* sum p^2 / 2m over all modes, eV */
+    double kin = 0.0; /* sum p^2 / 2m over all ring coordinates, eV */
     for (int k = 0; k < P; ++k)
         for (int i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) {
                 double p = p_nm[((size_t)k * N + i) * 3 + d];
-                kin += p * p / (2.0 * s->mass[i]) * MVV2E;
+                kin += p * p / (2.0 * mode_mass(s, k, i)) * MVV2E;
             }
     double H_P = kin + spring;
     for (int j = 0; j < P; ++j) H_P += V[j];

@@ -83,6 +83,7 @@ typedef struct {
     int splitting;           /* 0 = OBABO, 1 = BAOAB                         */
     int free_rp;             /* free ring-polymer step: 0 = exact, 1 = Cayley */
     or_metad* metad;         /* NULL = no bias                               */
+    int transform;           /* ring coordinates: 0 = normal modes, 1 = staging */
 } or_sys;
 
 /* estimator record, all eV except T_kin (K) */
@@ -113,6 +114,11 @@ int  or_init(const or_sys* s, const double* x0, double* q_nm, double* p_nm);
 /* one free ring-polymer step of a single mode (w = 0: free drift) over time
  * h; free_rp 0 = exact, 1 = Cayley; p in amu A/fs, q in A                  */
 void or_free_rp_step(int free_rp, double m, double w, double h, double* p, double* q);
+/* staging coordinates of one (atom, dimension): u <-> bead positions x [P] */
+void or_staging_to_beads(int P, const double* u, double* x);
+void or_beads_to_staging(int P, const double* x, double* u);
+/* -dPhi/du from bead forces f = -dPhi/dx [P] */
+void or_staging_forces(int P, const double* f, double* Fu);
 int  or_forces(const or_sys* s, const or_model* m, const double* q_nm,
                double* xb, double* f, double* V, double* W);
 int  or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,

@@ -252,3 +252,99 @@ def test_qho_averages_with_other_integrators(splitting, free_rp):
     x2_exact = 3 * (KB * T / MVV2E) / m * np.sum(1.0 / (w * w + wk ** 2))
     mx, ex = _block_mean(x2)
     assert abs(mx - x2_exact) < 4 * ex + 0.004 * x2_exact
+
+
+# ---------------------------------------------------------------- staging transform
+def test_staging_round_trip_and_spring_identity():
+    """u -> x -> u is the identity, and the ring's spring energy
+    sum_k (x_k - x_(k+1))^2 equals sum_(k>=2) k/(k-1) u_k^2 (the staging
+    masses m_k' = k/(k-1) m)."""
+    rng = np.random.default_rng(12)
+    for P in (1, 2, 5, 32):
+        x = rng.normal(size=(P, 3, 3))
+        u = O.beads_to_staging(x)
+        assert np.abs(O.staging_to_beads(u) - x).max() < 1e-13
+        spring = ((x - np.roll(x, -1, axis=0)) ** 2).sum()
+        k = np.arange(1, P + 1, dtype=float)
+        fac = np.where(k >= 2, k / np.maximum(k - 1, 1), 0.0)
+        assert abs(spring - (fac[:, None, None] * u ** 2).sum()) < 1e-12 * max(1.0, spring)
+        assert np.abs(u[0] - x[0]).max() == 0.0
+
+
+def test_staging_forces_are_minus_gradients():
+    """-dPhi/du from the force recursion equals a finite difference of
+    Phi(x(u)) for a random quadratic bead potential."""
+    rng = np.random.default_rng(3)
+    P = 7
+    A = rng.normal(size=(P, P))
+    A = A @ A.T
+    c = rng.normal(size=P)
+
+    def beads(u):
+        u3 = np.zeros((P, 1, 3))
+        u3[:, 0, 0] = u
+        return O.staging_to_beads(u3)[:, 0, 0]
+
+    def phi_of_u(u):
+        x = beads(u)
+        return 0.5 * x @ A @ x + c @ x
+
+    u = rng.normal(size=P)
+    x = beads(u)
+    f = -(A @ x + c)
+    Fu = O.staging_forces(f)
+    h = 1e-6
+    for k in range(P):
+        up, um = u.copy(), u.copy()
+        up[k] += h
+        um[k] -= h
+        fd = -(phi_of_u(up) - phi_of_u(um)) / (2 * h)
+        assert abs(fd - Fu[k]) < 1e-6 * max(1.0, abs(Fu).max()), k
+
+
+@pytest.mark.parametrize("P", [4, 16])
+def test_qho_averages_with_staging(P):
+    """Staging coordinates (masses k/(k-1) m, exact propagation at w_P)
+    sample the same P-bead oscillator: closed-form <E_P> and <|x|^2>."""
+    T, w, N = 300.0, 0.0786, 8
+    x0 = np.random.default_rng(5).normal(size=(N, 3)) * 0.1
+    rep = s.Replica(np.full(N, s.H, dtype=np.int32), x0, (0.0, 0.0, 0.0), P, T, 5)
+    sysm = O.System(rep, s.MASS, 0.25, 0.08, potential="harmonic", omega=w, transform="staging")
+    sysm.step(2000)
+    Ev, x2 = [], []
+    for _ in range(6000):
+        sysm.step(10)
+        Ev.append(sysm.estimators()["E_tot"] / N)
+        x2.append((sysm.beads() ** 2).sum(axis=2).mean())
+    exact = _qho_exact_EP(P, T, w)
+    mean, err = _block_mean(Ev)
+    assert abs(mean - exact) < 4 * err + 0.004 * exact, (mean, err, exact)
+    m = s.MASS[s.H]
+    wP = P * KB * T / HBAR
+    wk = 2 * wP * np.sin(np.arange(P) * np.pi / P)
+    x2_exact = 3 * (KB * T / MVV2E) / m * np.sum(1.0 / (w * w + wk ** 2))
+    mx, ex = _block_mean(x2)
+    assert abs(mx - x2_exact) < 4 * ex + 0.004 * x2_exact
+
+
+def test_staging_nve_energy_conservation():
+    """Staging NVE on oscillators (P = 4, 200 fs): no drift of H_P and
+    fluctuations that scale as dt^2. (In staging coordinates u_1 carries the
+    whole ring's force on one bead's mass, so its motion is sqrt(P) faster
+    than a bead's; the random-init network's steep regions make FAD runs a
+    poor conservation probe at these steps.)"""
+    amp = []
+    x0 = np.random.default_rng(5).normal(size=(3, 3)) * 0.1
+    for dt in (0.1, 0.05):
+        rep = s.Replica(np.full(3, s.H, dtype=np.int32), x0, (0.0, 0.0, 0.0), 4, 300.0, 5)
+        sysm = O.System(rep, s.MASS, dt, 0.0, potential="harmonic", omega=0.0786, thermostat=False,
+                        transform="staging")
+        H = []
+        for _ in range(int(round(200.0 / dt))):
+            sysm.step(1)
+            H.append(sysm.estimators()["H_cons"])
+        H = np.array(H)
+        slope = np.polyfit(np.arange(len(H)), H, 1)[0]
+        amp.append(H.std())
+        assert abs(slope * len(H)) < 3 * H.std() + 1e-12
+    assert 2.5 < amp[0] / amp[1] < 6.0, amp
