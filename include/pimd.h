@@ -89,6 +89,15 @@ typedef enum {
                          stream 2                                              */
 } pimd_splitting;
 
+/* coordinates of the ring-polymer state (pimd_get_state / pimd_set_state) */
+typedef enum {
+    PIMD_TRANSFORM_NORMAL_MODES = 0,  /* orthogonal normal modes, mass m, frequencies
+                                         omega_k = 2 omega_P sin(k pi / P)        */
+    PIMD_TRANSFORM_STAGING = 1        /* staging u_1 = x_1, u_k = x_k - ((k-1) x_(k+1)
+                                         + x_1) / k, masses k/(k-1) m (k >= 2), all
+                                         at omega_P; u_1 drifts freely           */
+} pimd_transform;
+
 /* free ring-polymer step of each internal mode k over a time h */
 typedef enum {
     PIMD_FREE_RP_EXACT = 0,   /* exp(h L_k): rotation by omega_k h            */
@@ -175,6 +184,7 @@ typedef struct {
                                 atoms (reduced to 0.9 of the room between r_c
                                 and half the box, off below 0.05 A), none for
                                 smaller ones; 0: rebuild every step.           */
+    int transform;           /* pimd_transform: ring-polymer coordinates       */
 } pimd_config;
 
 /* stages of one step, in launch order (pimd_stage_times) */

@@ -92,6 +92,8 @@ int check_config(const pimd_config* cfg, std::string& e)
     if (cfg->thermostat != 0 && cfg->thermostat != 1) { e = "thermostat must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->nbr_algo < 0 || cfg->nbr_algo > 2) { e = "nbr_algo must be 0, 1 or 2"; return PIMD_ERR_INVALID_ARG; }
     if (!std::isfinite(cfg->nbr_skin_A)) { e = "nbr_skin_A must be finite"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->transform != PIMD_TRANSFORM_NORMAL_MODES && cfg->transform != PIMD_TRANSFORM_STAGING)
+        { e = "transform must be PIMD_TRANSFORM_NORMAL_MODES or PIMD_TRANSFORM_STAGING"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->splitting != PIMD_OBABO && cfg->splitting != PIMD_BAOAB) { e = "splitting must be PIMD_OBABO or PIMD_BAOAB"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->free_rp != PIMD_FREE_RP_EXACT && cfg->free_rp != PIMD_FREE_RP_CAYLEY) { e = "free_rp must be PIMD_FREE_RP_EXACT or PIMD_FREE_RP_CAYLEY"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->deterministic != 0 && cfg->deterministic != 1) { e = "deterministic must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
@@ -127,6 +129,21 @@ void nm_matrix(int P, double* C)
             else if (2 * k == P) v = ((j & 1) ? -1.0 : 1.0) / std::sqrt((double)P);
             else v = std::sqrt(2.0 / P) * std::sin(2.0 * M_PI * j * k / P);
             C[(size_t)j * P + k] = v;
+        }
+}
+
+// staging transform as a matrix, x = S u: x_1 = u_1 and, for beads k >= 2,
+// x_k = u_1 + sum_(j=k..P) ((k-1)/(j-1)) u_j (1-based; from the recursion
+// x_k = u_k + ((k-1)/k) x_(k+1) + x_1/k with x_(P+1) = x_1). Staging forces
+// are S^T f, the same product as the normal-mode forces C^T f.
+void staging_matrix(int P, double* S)
+{
+    for (int j = 1; j <= P; ++j)
+        for (int k = 1; k <= P; ++k) {
+            double v = 0.0;
+            if (k == 1) v = 1.0;
+            else if (j >= 2 && j <= k) v = (double)(j - 1) / (k - 1);
+            S[(size_t)(j - 1) * P + (k - 1)] = v;
         }
 }
 
@@ -207,7 +224,10 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         if (!cm_off.count(P)) {
             cm_off[P] = (int)b.cmat.size();
             b.cmat.resize(b.cmat.size() + (size_t)P * P);
-            nm_matrix(P, b.cmat.data() + cm_off[P]);
+            if (cfg->transform == PIMD_TRANSFORM_STAGING)
+                staging_matrix(P, b.cmat.data() + cm_off[P]);
+            else
+                nm_matrix(P, b.cmat.data() + cm_off[P]);
         }
     }
     const int rp_threads = 256;
@@ -277,7 +297,12 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         for (int k = 0; k < h.P; ++k) {
             Mode md;
             std::memset(&md, 0, sizeof(md));
-            md.w = 2.0 * wP * std::sin(k * M_PI / h.P);
+            const bool stg = cfg->transform == PIMD_TRANSFORM_STAGING;
+            md.w = stg ? (k == 0 ? 0.0 : wP) : 2.0 * wP * std::sin(k * M_PI / h.P);
+            md.mfac = (stg && k >= 1) ? (k + 1.0) / k : 1.0;
+            // column sums of the transform (centroid) and the total-force factor
+            md.cs = stg ? (k == 0 ? (double)h.P : 0.5 * (k + 1)) : (k == 0 ? std::sqrt((double)h.P) : 0.0);
+            md.ft = stg ? 1.0 : std::sqrt((double)h.P);
             if (cfg->free_rp == PIMD_FREE_RP_CAYLEY) {
                 // Cayley transform of hA L_k: a rotation of the scaled phase
                 // plane with cos = (1 - a) / (1 + a), sin = w hA / (1 + a),

@@ -66,7 +66,10 @@ struct BeadSys {
 
 // per normal mode of a replica
 struct Mode {
-    double w, cw, sw, c1, c2, pad[3];
+    double w, cw, sw, c1, c2;
+    double mfac;   // mass of this ring coordinate / atom mass (normal modes 1; staging k/(k-1))
+    double cs;     // sum over beads of the transform column: centroid = sum_k cs_k q_k / P
+    double ft;     // total bead force = ft * (C^T f)_0 (normal modes sqrt(P), staging 1)
 };
 
 // pair schedule of the descriptor / adjoint kernels (chosen by the tuner)

@@ -52,7 +52,8 @@ __device__ __forceinline__ Real& comp(Vec4<Real>& v, int d)
 // with Philox stream 1, step 0. One thread per state entry.
 // ---------------------------------------------------------------------------
 __global__ void rp_init_kernel(const Rep* __restrict__ reps, const BeadSys* __restrict__ bsys,
-                               const int* __restrict__ ba_sys, const double* __restrict__ mass,
+                               const int* __restrict__ ba_sys, const Mode* __restrict__ modes,
+                               const double* __restrict__ mass,
                                const double* __restrict__ x0, int B, double* __restrict__ q, double* __restrict__ p)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,14 +64,17 @@ __global__ void rp_init_kernel(const Rep* __restrict__ reps, const BeadSys* __re
     const int i = b - sy.ba0;
     const int k = sy.bead;
     const unsigned local = (unsigned)((k * rp.N + i) * 3 + dd);
-    const double m = mass[rp.atom0 + i];
-    q[g] = (k == 0) ? sqrt((double)rp.P) * x0[3 * (size_t)(rp.atom0 + i) + dd] : 0.0;
+    const Mode md = modes[rp.mode0 + k];
+    const double m = mass[rp.atom0 + i] * md.mfac;
+    // all beads at x0: q_0 = P x0 / (column sum of mode 0), other modes 0
+    q[g] = (k == 0) ? (double)rp.P / md.cs * x0[3 * (size_t)(rp.atom0 + i) + dd] : 0.0;
     p[g] = sqrt(m * rp.kT_md) * normal_dev(rp.seed, local, 0u, (unsigned)sy.rep, 1u);
 }
 
 void launch_rp_init(const Dev& d, cudaStream_t st)
 {
-    rp_init_kernel<<<(3 * d.B + 255) / 256, 256, 0, st>>>(d.reps, d.bsys, d.ba_sys, d.mass, d.x0, d.B, d.q, d.p);
+    rp_init_kernel<<<(3 * d.B + 255) / 256, 256, 0, st>>>(d.reps, d.bsys, d.ba_sys, d.modes, d.mass, d.x0, d.B, d.q,
+                                                          d.p);
 }
 
 // ---------------------------------------------------------------------------
@@ -165,7 +169,7 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
         const int k = t.kk;
         const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
         const Mode md = modes[rp.mode0 + k];
-        const double m = mass[rp.atom0 + t.i];
+        const double m = mass[rp.atom0 + t.i] * md.mfac;
         double pv = p[g], qv = q[g];
         const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
         if (baoab) {
@@ -227,10 +231,10 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         fnm[g] = fn;
         if (!isfinite(fn)) atomicOr(&err->flags, ERR_NONFINITE);
         if (do_step) {
-            const double m = mass[rp.atom0 + t.i];
+            const Mode md = modes[rp.mode0 + k];
+            const double m = mass[rp.atom0 + t.i] * md.mfac;
             double pv = p[g] + 0.5 * dt * fn / MVV2E;
             if (thermostat) {
-                const Mode md = modes[rp.mode0 + k];
                 const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
                 dK = pile_o(rp, md, m, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
             }
@@ -329,16 +333,23 @@ __global__ void estimators_kernel(const Rep* __restrict__ reps, const Mode* __re
     const int N = rp.N, P = rp.P;
     double spring = 0.0, cv = 0.0, kin = 0.0, nsum = 0.0;
     int nmax = 0;
-    const int total = 3 * N * P;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int k = e / (3 * N);
-        const int i = (e - k * 3 * N) / 3;
-        const size_t g = 3 * (size_t)rp.ba0 + e;
-        const double m = mass[rp.atom0 + i];
-        const double w = modes[rp.mode0 + k].w;
-        spring += 0.5 * m * w * w * q[g] * q[g];
-        if (k > 0) cv += q[g] * fnm[g];
-        kin += p[g] * p[g] / (2.0 * m);
+    // per (atom, dimension): spring sum_k 1/2 m_k w_k^2 q_k^2, kinetic
+    // sum_k p_k^2 / 2 m_k, and sum_j (x_j - centroid) f_j = sum_k q_k fnm_k
+    // - centroid * total force (the transform is x = C q, fnm = C^T f)
+    for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
+        const int i = e / 3;
+        const double m0 = mass[rp.atom0 + i];
+        double qf = 0.0, xc = 0.0;
+        for (int k = 0; k < P; ++k) {
+            const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * N) + e;
+            const Mode& md = modes[rp.mode0 + k];
+            const double m = m0 * md.mfac;
+            spring += 0.5 * m * md.w * md.w * q[g] * q[g];
+            kin += p[g] * p[g] / (2.0 * m);
+            qf += q[g] * fnm[g];
+            xc += md.cs * q[g];
+        }
+        cv += qf - (xc / P) * modes[rp.mode0].ft * fnm[3 * (size_t)rp.ba0 + e];
     }
     for (int b = threadIdx.x; b < N * P; b += blockDim.x) {
         const int c = nnb[rp.ba0 + b];

@@ -69,7 +69,9 @@ class pimd_config(ct.Structure):
                 ("potential", ct.c_int), ("max_neighbours", ct.c_int), ("omega_harm", ct.c_double),
                 ("n_hidden", ct.c_int), ("widths", ct.c_int * 4), ("stream", ct.c_void_p), ("timing", ct.c_int),
                 ("nbr_algo", ct.c_int), ("deterministic", ct.c_int), ("splitting", ct.c_int),
-                ("free_rp", ct.c_int), ("metad", ct.POINTER(pimd_metad_desc)), ("nbr_skin_A", ct.c_double)]
+                ("free_rp", ct.c_int), ("metad", ct.POINTER(pimd_metad_desc)), ("nbr_skin_A", ct.c_double),
+                ("transform", ct.c_int)]
+TRANSFORM = {"normal_modes": 0, "staging": 1}
 SPLITTING = {"obabo": 0, "baoab": 1}
 FREE_RP = {"exact": 0, "cayley": 1}
 
@@ -379,7 +381,7 @@ def pimd_last_error(ctx=None) -> str:
 def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128, 128, 128), pile_lambda=1.0,
                 thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128, stream=None,
                 timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
-                free_rp="exact", metad=None, nbr_skin=-1.0) -> pimd_config:
+                free_rp="exact", metad=None, nbr_skin=-1.0, transform="normal_modes") -> pimd_config:
     c = pimd_config()
     c.dt_fs = dt_fs
     c.gamma0_per_fs = gamma0_per_fs
@@ -402,6 +404,7 @@ def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128,
     if metad is not None:
         c.metad = ct.pointer(metad)
     c.nbr_skin_A = float(nbr_skin)
+    c.transform = TRANSFORM[transform] if isinstance(transform, str) else int(transform)
     return c
 
 
@@ -466,7 +469,7 @@ class Context:
     def __init__(self, replicas, dt_fs, gamma0_per_fs, precision="fp32", widths=(128, 128, 128), cutoff=6.0,
                  pile_lambda=1.0, thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128,
                  masses=None, stream=None, timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
-                 free_rp="exact", metad=None, nbr_skin=-1.0):
+                 free_rp="exact", metad=None, nbr_skin=-1.0, transform="normal_modes"):
         import torch
         self.torch = torch
         self.keep = _Keep()
@@ -477,7 +480,7 @@ class Context:
         self.stream = stream
         self.cfg = make_config(dt_fs, gamma0_per_fs, precision, cutoff, widths, pile_lambda, thermostat, potential,
                                omega, max_neighbours, ct.c_void_p(stream.cuda_stream), timing, nbr_algo,
-                               deterministic, splitting, free_rp, metad, nbr_skin)
+                               deterministic, splitting, free_rp, metad, nbr_skin, transform)
         self.metad_desc = metad
         self.reps = make_replicas(self.replicas, self.keep, masses)
         self.ws_bytes = pimd_workspace_size(self.cfg, self.reps)

@@ -74,3 +74,43 @@ def test_large_omega_dt_cayley_stays_bounded():
     ctx.step(500)
     e = ctx.estimators()[0]
     assert all(np.isfinite(e[k]) for k in ("E_tot", "K_prim", "K_cv", "H_cons"))
+
+
+@pytest.mark.parametrize("splitting", ["obabo", "baoab"])
+def test_staging_fp64_trajectory_and_estimators_match_oracle(fad_model, splitting):
+    """Staging coordinates (masses k/(k-1) m, all at omega_P), FAD P = 16,
+    FP64: state after 10 steps and every estimator against the oracle."""
+    P = _P()
+    w, rep, m = fad_model
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp64", widths=w.widths, splitting=splitting,
+                    transform="staging")
+    ctx.set_weights(m)
+    so = O.System(rep, s.MASS, w.dt_fs, w.gamma0_per_fs, model=m, splitting=splitting, transform="staging")
+    q0, p0, _, _ = ctx.get_state()
+    np.testing.assert_allclose(q0.reshape(so.q.shape), so.q, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(p0.reshape(so.p.shape), so.p, rtol=1e-12, atol=1e-14)
+    ctx.step(10)
+    so.step(10)
+    q, p, st, _ = ctx.get_state()
+    np.testing.assert_allclose(q.reshape(so.q.shape), so.q, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(p.reshape(so.p.shape), so.p, rtol=0, atol=1e-9 * np.abs(so.p).max())
+    eg, eo = ctx.estimators()[0], so.estimators()
+    for k in ("V_mean", "K_prim", "K_cv", "E_tot", "H_cons", "Q_thermo", "T_kin"):
+        assert abs(eg[k] - eo[k]) <= 1e-8 * max(1.0, abs(eo[k])), k
+
+
+def test_staging_fp32_water_matches_oracle(water64_model):
+    P = _P()
+    w, r, m = water64_model
+    rep = s.Replica(r.Z, r.x0, r.box, 4, r.T, r.seed, r.name)
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths, transform="staging")
+    ctx.set_weights(m)
+    so = O.System(rep, s.MASS, w.dt_fs, w.gamma0_per_fs, model=m, transform="staging")
+    ctx.step(5)
+    so.step(5)
+    q, p, _, _ = ctx.get_state()
+    np.testing.assert_allclose(q.reshape(so.q.shape), so.q, rtol=0, atol=2e-5)
+    assert float(np.abs(p.reshape(so.p.shape) - so.p).max() / np.abs(so.p).max()) < 1e-4
+    eg, eo = ctx.estimators()[0], so.estimators()
+    for k in ("V_mean", "K_cv", "E_tot"):
+        assert abs(eg[k] - eo[k]) <= 1e-4 * max(1.0, abs(eo[k])), k
