@@ -374,6 +374,17 @@ int pimd_metad_hills(pimd_ctx* ctx, int replica, double* s, double* h, int capac
 int pimd_metad_set_hills(pimd_ctx* ctx, int replica, const double* s, const double* h, int n);
 int pimd_metad_cv(pimd_ctx* ctx, double* cv, double* bias);
 
+/* ---- self-test of the bounded waits -----------------------------------------
+ * The paper has no counterpart. Every spin wait in the library's kernels
+ * (tensor-core MMA and copy barriers) gives up after about a second of GPU
+ * clock, records PIMD_ERR_TIMEOUT and returns, so a stalled pipeline never
+ * hangs the GPU. This call runs one such wait on an mbarrier that nothing
+ * completes, bounded by `seconds` of SM clock (2 GHz nominal, 0 < seconds <=
+ * 10), on `stream` (NULL = default), and returns PIMD_ERR_TIMEOUT when the
+ * bound expired (the expected outcome) or PIMD_OK if the barrier completed.
+ * Synchronises the stream. No context is involved.                         */
+int pimd_selftest_bounded_wait(void* stream, double seconds);
+
 /* ---- structural analysis of the bead configurations (Sec. 3.2) ------------
  * Both calls read the bead positions of the last force evaluation (after
  * pimd_step, pimd_energy_forces or pimd_create) of one replica, run on the

@@ -846,6 +846,17 @@ int pimd_set_weights(pimd_ctx* c, const pimd_model_desc* m)
     for (int q = 0; q < 4; ++q) c->dpf.eta_A[q] = (float)c->dpd.eta_A[q];
     c->dpd.eta_R_l2 = c->dpd.eta_R * M_LOG2E;
     c->dpf.eta_R_l2 = (float)c->dpd.eta_R_l2;
+    {
+        const double dr = (m->r_mu[NR - 1] - m->r_mu[0]) / (NR - 1);
+        bool even = dr > 0.0;
+        for (int q = 0; q < NR && even; ++q)
+            even = std::fabs(m->r_mu[q] - (m->r_mu[0] + q * dr)) <= 1e-9 * std::max(1.0, std::fabs(m->r_mu[q]));
+        c->dpf.r_even = c->dpd.r_even = even ? 1 : 0;
+        c->dpd.r_delta = dr;
+        c->dpf.r_delta = (float)dr;
+        c->dpd.rec_k = std::exp2(-2.0 * c->dpd.eta_R_l2 * dr * dr);
+        c->dpf.rec_k = (float)c->dpd.rec_k;
+    }
     for (int q = 0; q < 4; ++q) {
         c->dpd.eta_A_l2[q] = c->dpd.eta_A[q] * M_LOG2E;
         c->dpf.eta_A_l2[q] = (float)c->dpd.eta_A_l2[q];
@@ -1265,6 +1276,17 @@ int pimd_metad_cv(pimd_ctx* c, double* cv, double* bias)
         rc = cuda_check(c, cudaMemcpyAsync(bias, c->d.md_vb, sizeof(double) * c->d.S, cudaMemcpyDeviceToHost, c->st), "cv");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "cv");
     return rc;
+}
+
+int pimd_selftest_bounded_wait(void* stream, double seconds)
+{
+    if (!(seconds > 0.0) || seconds > 10.0) return fail(nullptr, PIMD_ERR_INVALID_ARG, "seconds must be in (0, 10]");
+    int timed_out = 0;
+    if (run_wait_selftest((cudaStream_t)stream, (long long)(seconds * 2.0e9), &timed_out)) {
+        cudaGetLastError();
+        return fail(nullptr, PIMD_ERR_CUDA, "self-test launch failed");
+    }
+    return timed_out ? fail(nullptr, PIMD_ERR_TIMEOUT, "bounded wait expired (as designed)") : PIMD_OK;
 }
 
 int pimd_element_types(const pimd_ctx* c, int* Z)

@@ -100,6 +100,11 @@ struct DescParams {
     Real r_mu[NR];
     Real eta_A[4];
     Real eta_R_l2, eta_A_l2[4];   // widths times log2(e) (FP32 exponentials use exp2)
+    // evenly spaced radial centres (r_mu[c] = r_mu[0] + c r_delta): the BF16
+    // path forms the Gaussians of a group of 8 centres by a product recurrence
+    int r_even;
+    Real r_delta;
+    Real rec_k;    // 2^(-2 eta_R log2(e) r_delta^2), the ratio of successive ratios
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

@@ -989,30 +989,25 @@ __global__ void __launch_bounds__(256) energy_reduce_kernel(const Real* __restri
                                                             const BeadSys* __restrict__ bsys, int S,
                                                             double* __restrict__ V, double* __restrict__ Wv)
 {
-    // one block per bead; FP64 sums over its atoms in a fixed order
-    __shared__ double red[10][8];
-    const int s = blockIdx.x;
+    // block (bead, component): component 0 the energy, 1..9 the virial
+    // entries; FP64 sums over the bead's atoms in a fixed order
+    __shared__ double red[8];
+    const int s = blockIdx.x, q = blockIdx.y;
     const BeadSys sy = bsys[s];
-    double acc[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-    for (int i = threadIdx.x; i < sy.N; i += blockDim.x) {
-        acc[0] += (double)Eatom[sy.ba0 + i];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc[1 + q] += (double)wbuf[(size_t)(sy.ba0 + i) * 9 + q];
+    double acc = 0.0;
+    if (q == 0) {
+        for (int i = threadIdx.x; i < sy.N; i += blockDim.x) acc += (double)Eatom[sy.ba0 + i];
+    } else {
+        for (int i = threadIdx.x; i < sy.N; i += blockDim.x) acc += (double)wbuf[(size_t)(sy.ba0 + i) * 9 + q - 1];
     }
-    const int wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-        const double v = warp_sum(acc[q]);
-        if ((threadIdx.x & 31) == 0) red[q][wid] = v;
-    }
+    const double v = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x < 10) {
+    if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
-        if (threadIdx.x == 0) V[s] = t;
-        else Wv[(size_t)s * 9 + threadIdx.x - 1] = t;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        if (q == 0) V[s] = t;
+        else Wv[(size_t)s * 9 + q - 1] = t;
     }
 }
 
@@ -1021,12 +1016,13 @@ void launch_energy_reduce(const Dev& d, cudaStream_t st)
     // block size sized to the largest bead (small systems: one warp per bead)
     int t = 32;
     while (t < 256 && t < d.max_N) t <<= 1;
+    const dim3 grid(d.S, 10);
     if (d.precision == 0)
-        energy_reduce_kernel<double><<<d.S, t, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
-                                                        d.V, d.W);
+        energy_reduce_kernel<double><<<grid, t, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
+                                                         d.V, d.W);
     else
-        energy_reduce_kernel<float><<<d.S, t, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
-                                                       d.V, d.W);
+        energy_reduce_kernel<float><<<grid, t, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
+                                                        d.V, d.W);
 }
 
 // ---------------------------------------------------------------------------

@@ -32,6 +32,31 @@ __device__ __forceinline__ float gauss(float eta, float eta_l2, float x2)
     if (FAST) return exp2f(-eta_l2 * x2);
     return expf(-eta * x2);
 }
+// The 32 radial Gaussians exp2(-eta' (r - r_mu)^2) of evenly spaced centres,
+// in groups of 8: exact at the group's first centre, then g_(c+1) = g_c R_c
+// with R_c = 2^(eta' (2 t_c dr - dr^2)) and R_(c+1) = R_c 2^(-2 eta' dr^2)
+// (t_c = r - r_mu[c]; 2 exponentials and 14 products per group instead of 8
+// exponentials; ~8 roundings of relative error). A group whose first value
+// underflows (eta' t_0^2 > 149) leaves its members at 0 although the last
+// one is 2^(-eta' (t_0 - 7 dr)^2); for the 32 centres over 0.5 .. 5.5 A that
+// is below 2^-39 of the peak value 1.
+template <typename DP>
+__device__ __forceinline__ void radial_gauss32(const DP& dp, float r, float (&g)[32])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float t0 = r - dp.r_mu[8 * q];
+        float e = exp2f(-dp.eta_R_l2 * t0 * t0);
+        float R = exp2f(dp.eta_R_l2 * (2.0f * t0 * dp.r_delta - dp.r_delta * dp.r_delta));
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            g[8 * q + c] = e;
+            e *= R;
+            R *= dp.rec_k;
+        }
+    }
+}
+
 template <bool FAST>
 __device__ __forceinline__ double gauss(double eta, double eta_l2, double x2)
 {

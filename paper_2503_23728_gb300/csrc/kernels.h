@@ -140,6 +140,9 @@ void launch_rdf(const Dev& d, int rep, int P, int N, const BinEdges& edges, int 
 void launch_pt(const Dev& d, int rep, int P, int N, const int* bond, int t_acc, const BinEdges& edges, int n_bins,
                float inv_w, float* v_out, unsigned long long* hist, cudaStream_t st);
 
+// bounded-wait self-test (mlp_tc.cu): 0 on success, *timed_out = 1 when the bound expired
+int run_wait_selftest(cudaStream_t st, long long cycles, int* timed_out);
+
 // message returned by pimd_last_error(NULL) on this thread
 void set_thread_error(const std::string& msg);
 

@@ -847,4 +847,36 @@ void launch_network_tc(const Dev& d, cudaStream_t st)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Self-test of the bounded waits: one thread initialises an mbarrier that
+// nothing arrives on and waits on it with mbar_wait, exactly as the network
+// kernels wait on their MMA and copy barriers; the bound expires after
+// ~WAIT_CYCLES and the kernel records the timeout and returns.
+// ---------------------------------------------------------------------------
+__device__ int g_wait_selftest;
+
+__global__ void wait_selftest_kernel(long long cycles)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const long long t0 = clock64();
+    bool done = false;
+    while (!(done = mbar_try(b, 0u))) {
+        if (clock64() - t0 > cycles) break;
+    }
+    g_wait_selftest = done ? 0 : 1;
+}
+
+int run_wait_selftest(cudaStream_t st, long long cycles, int* timed_out)
+{
+    wait_selftest_kernel<<<1, 1, 0, st>>>(cycles);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(timed_out, g_wait_selftest, sizeof(int), 0,
+                                                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace pimd

@@ -402,10 +402,17 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 2) desc_mom_fwd_red_kernel(
             const float ir = 1.0f / r;
             float fc, dfc;
             cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+            if (FAST && dp.r_even) {
+                float g[NR];
+                radial_gauss32(dp, r, g);
 #pragma unroll
-            for (int c = 0; c < NR; ++c) {
-                const float t = r - dp.r_mu[c];
-                gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+                for (int c = 0; c < NR; ++c) gr[c] = fmaf(g[c], fc, gr[c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    const float t = r - dp.r_mu[c];
+                    gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+                }
             }
             float bw[4];
 #pragma unroll
@@ -514,10 +521,10 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 2) desc_mom_fwd_red_kernel(
 // loads of Q.
 // ---------------------------------------------------------------------------
 constexpr int ADJ_WARP_BYTES = NMONO * 16 + ND * 4;
-constexpr int ADJ_WARPS = 8;
+constexpr int ADJ_WARPS = 4;
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * ADJ_WARPS, 2) desc_mom_adj_kernel(
+__global__ void __launch_bounds__(32 * ADJ_WARPS, 4) desc_mom_adj_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
@@ -610,11 +617,21 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS, 2) desc_mom_adj_kernel(
         float fc, dfc;
         cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
         float dEdr = 0.0f;
+        if (FAST && dp.r_even) {
+            float g[NR];
+            radial_gauss32(dp, r, g);
 #pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            const float t = r - dp.r_mu[c];
-            const float ex = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t);
-            dEdr += gs[c] * ex * (-2.0f * dp.eta_R * t * fc + dfc);
+            for (int c = 0; c < NR; ++c) {
+                const float t = r - dp.r_mu[c];
+                dEdr += gs[c] * g[c] * (-2.0f * dp.eta_R * t * fc + dfc);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const float t = r - dp.r_mu[c];
+                const float ex = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t);
+                dEdr += gs[c] * ex * (-2.0f * dp.eta_R * t * fc + dfc);
+            }
         }
         float bw[4], dbw[4];
 #pragma unroll

@@ -25,7 +25,7 @@ EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_w
            "pimd_get_forces", "pimd_get_neighbours", "pimd_sync", "pimd_sizes", "pimd_destroy", "pimd_last_error",
            "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule", "pimd_set_angular", "pimd_get_angular",
            "pimd_element_types", "pimd_rdf_counts", "pimd_pt_coordinate",
-           "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv"]
+           "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv", "pimd_selftest_bounded_wait"]
 ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
@@ -141,6 +141,7 @@ def load(path: str = LIB_PATH):
     L.pimd_set_angular.argtypes = [vp, ct.c_int]
     L.pimd_get_angular.argtypes = [vp]
     L.pimd_get_angular.restype = ct.c_int
+    L.pimd_selftest_bounded_wait.argtypes = [vp, ct.c_double]
     L.pimd_metad_hills.argtypes = [vp, ct.c_int, dp, dp, ct.c_int]
     L.pimd_metad_hills.restype = ct.c_int
     L.pimd_metad_set_hills.argtypes = [vp, ct.c_int, dp, dp, ct.c_int]
@@ -263,6 +264,11 @@ def pimd_set_angular(ctx, algo):
 
 def pimd_get_angular(ctx) -> str:
     return {0: "pairs", 1: "moments"}[int(load().pimd_get_angular(ctx))]
+
+
+def pimd_selftest_bounded_wait(seconds: float = 0.2, stream=None) -> int:
+    """Status of one bounded wait that nothing completes (PIMD_ERR_TIMEOUT = -6 expected)."""
+    return int(load().pimd_selftest_bounded_wait(stream, float(seconds)))
 
 
 def pimd_metad_hills(ctx, replica: int, capacity: int = 1 << 20):

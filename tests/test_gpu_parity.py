@@ -412,3 +412,16 @@ def test_verlet_candidate_overflow_falls_back(ice_model):
         for i in range(rep.n_atoms):
             b = k * rep.n_atoms + i
             assert np.array_equal(nbr[b, :nnb[b]], want[i]), (k, i)
+
+
+def test_bounded_wait_times_out_and_gpu_stays_usable(water64_model):
+    """A spin wait on a barrier that nothing completes gives up at its bound
+    and reports TIMEOUT; the device keeps working afterwards."""
+    P = _P()
+    assert P.pimd_selftest_bounded_wait(0.2) == -6
+    assert "bounded wait expired" in P.pimd_last_error()
+    w, r, m = water64_model
+    ctx = P.Context([_with_beads(r, 2)], w.dt_fs, w.gamma0_per_fs, precision="bf16_tc", widths=w.widths)
+    ctx.set_weights(m)
+    ctx.step(2)
+    assert np.isfinite(ctx.estimators()[0]["E_tot"])
