@@ -78,7 +78,7 @@ struct Carve {
 };
 
 struct Offsets {
-    size_t reps, bsys, ba_sys, mass, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
+    size_t reps, bsys, ba_sys, mass, minv, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
         fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
         md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
@@ -317,6 +317,10 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
             const double gam = (k == 0) ? cfg->gamma0_per_fs : 2.0 * cfg->pile_lambda * md.w;
             md.c1 = std::exp(-hO * gam);
             md.c2 = std::sqrt(1.0 - md.c1 * md.c1);
+            md.sw_w = md.w > 0.0 ? md.sw / md.w : 0.0;
+            md.wsw = md.w * md.sw;
+            md.smf = std::sqrt(md.mfac);
+            md.imf = 1.0 / md.mfac;
             b.modes.push_back(md);
         }
         for (int k = 0; k < h.P; ++k) {
@@ -373,6 +377,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.bsys = c.take(sizeof(BeadSys) * b.S);
     o.ba_sys = c.take(sizeof(int) * b.B);
     o.mass = c.take(sizeof(double) * b.NA);
+    o.minv = c.take(sizeof(double2) * b.NA);
     o.atype = c.take(sizeof(int) * b.NA);
     o.x0 = c.take(sizeof(double) * 3 * (size_t)b.NA);
     o.cmat = c.take(sizeof(double) * b.cmat.size());
@@ -642,6 +647,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.bsys = (BeadSys*)(w + o.bsys);
     d.ba_sys = (int*)(w + o.ba_sys);
     d.mass = (double*)(w + o.mass);
+    d.minv = (double2*)(w + o.minv);
     d.atype = (int*)(w + o.atype);
     d.x0 = (double*)(w + o.x0);
     d.cmat = (double*)(w + o.cmat);
@@ -739,6 +745,15 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     if (!rc) rc = upload(c, d.bsys, b.bsys);
     if (!rc) rc = upload(c, d.ba_sys, b.ba_sys);
     if (!rc) rc = upload(c, d.mass, b.mass);
+    if (!rc) {
+        std::vector<double2> mi(b.NA);
+        for (const Rep& rp : b.reps)
+            for (int i = 0; i < rp.N; ++i) {
+                const double m = b.mass[rp.atom0 + i];
+                mi[rp.atom0 + i] = make_double2(1.0 / m, std::sqrt(m * rp.kT_md));
+            }
+        rc = upload(c, d.minv, mi);
+    }
     if (!rc) rc = upload(c, d.atype, b.atype);
     if (!rc) rc = upload(c, d.x0, b.x0);
     if (!rc) rc = upload(c, d.cmat, b.cmat);

@@ -70,7 +70,12 @@ struct Mode {
     double mfac;   // mass of this ring coordinate / atom mass (normal modes 1; staging k/(k-1))
     double cs;     // sum over beads of the transform column: centroid = sum_k cs_k q_k / P
     double ft;     // total bead force = ft * (C^T f)_0 (normal modes sqrt(P), staging 1)
+    // derived on the host so that the FP64 kernels divide and take roots
+    // only in the random deviates: sw / w, w sw, sqrt(mfac), 1 / mfac
+    double sw_w, wsw, smf, imf;
 };
+
+constexpr double INV_MVV2E = 1.0 / MVV2E;
 
 // pair schedule of the descriptor / adjoint kernels (chosen by the tuner)
 struct Sched {

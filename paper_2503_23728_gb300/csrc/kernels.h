@@ -23,6 +23,7 @@ struct Dev {
     BeadSys* bsys = nullptr;
     int* ba_sys = nullptr;             // [B] bead-system of each bead-atom
     double* mass = nullptr;            // [NA]
+    double2* minv = nullptr;           // [NA] (1 / m, sqrt(m k_B T_P) of the atom's replica)
     int* atype = nullptr;              // [NA] element type index
     double* x0 = nullptr;              // [NA][3]
     double* cmat = nullptr;            // normal-mode matrices

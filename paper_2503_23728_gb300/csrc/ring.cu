@@ -126,25 +126,27 @@ __global__ void beads_kernel(const int2* __restrict__ blocks, const Rep* __restr
 // free ring-polymer step of mode k over hA: centroid drift, or the rotation
 // (cw, sw) of the scaled phase plane that the host computed for the chosen
 // propagator (exact or Cayley)
-__device__ __forceinline__ void free_rp(int k, const Mode& md, double m, double hA, double& pv, double& qv)
+// (m: the coordinate's mass, im: its inverse)
+__device__ __forceinline__ void free_rp(int k, const Mode& md, double m, double im, double hA, double& pv,
+                                        double& qv)
 {
     if (k == 0) {
-        qv += pv * hA / m;
+        qv += pv * hA * im;
     } else {
-        const double pn = md.cw * pv - m * md.w * md.sw * qv;
-        qv = md.sw / (m * md.w) * pv + md.cw * qv;
+        const double pn = md.cw * pv - m * md.wsw * qv;
+        qv = md.sw_w * im * pv + md.cw * qv;
         pv = pn;
     }
 }
 
 // PILE-L O sub-step with the host's (c1, c2) for its duration; returns the
-// kinetic-energy change
-__device__ __forceinline__ double pile_o(const Rep& rp, const Mode& md, double m, unsigned local, unsigned step,
-                                         unsigned rep, unsigned stream, double& pv)
+// kinetic-energy change (smkT = sqrt(m k_B T_P) of the coordinate, im = 1/m)
+__device__ __forceinline__ double pile_o(const Rep& rp, const Mode& md, double smkT, double im, unsigned local,
+                                         unsigned step, unsigned rep, unsigned stream, double& pv)
 {
     const double xi = normal_dev(rp.seed, local, step, rep, stream);
-    const double pn = md.c1 * pv + sqrt(m * rp.kT_md) * md.c2 * xi;
-    const double dK = (pn * pn - pv * pv) / (2.0 * m);
+    const double pn = md.c1 * pv + smkT * md.c2 * xi;
+    const double dK = (pn * pn - pv * pv) * 0.5 * im;
     pv = pn;
     return dK;
 }
@@ -154,8 +156,8 @@ __device__ __forceinline__ double pile_o(const Rep& rp, const Mode& md, double m
 template <typename Real>
 __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
                                 const double* __restrict__ cmat, const Mode* __restrict__ modes,
-                                const double* __restrict__ mass, const unsigned long long* __restrict__ stepp,
-                                double dt, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
+                                const double* __restrict__ mass, const double2* __restrict__ minv,
+                                const unsigned long long* __restrict__ stepp, double dt, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
                                 const double* __restrict__ fnm, Vec4<Real>* __restrict__ x,
                                 double* __restrict__ qpart)
 {
@@ -169,18 +171,20 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
         const int k = t.kk;
         const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
         const Mode md = modes[rp.mode0 + k];
-        const double m = mass[rp.atom0 + t.i] * md.mfac;
+        const double2 mi = minv[rp.atom0 + t.i];
+        const double m = mass[rp.atom0 + t.i] * md.mfac, im = mi.x * md.imf, smkT = mi.y * md.smf;
+        const double kick = 0.5 * dt * INV_MVV2E;
         double pv = p[g], qv = q[g];
         const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
         if (baoab) {
-            pv += 0.5 * dt * fnm[g] / MVV2E;
-            free_rp(k, md, m, 0.5 * dt, pv, qv);
-            if (thermostat) dK = pile_o(rp, md, m, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
-            free_rp(k, md, m, 0.5 * dt, pv, qv);
+            pv += kick * fnm[g];
+            free_rp(k, md, m, im, 0.5 * dt, pv, qv);
+            if (thermostat) dK = pile_o(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
+            free_rp(k, md, m, im, 0.5 * dt, pv, qv);
         } else {
-            if (thermostat) dK = pile_o(rp, md, m, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
-            pv += 0.5 * dt * fnm[g] / MVV2E;
-            free_rp(k, md, m, dt, pv, qv);
+            if (thermostat) dK = pile_o(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
+            pv += kick * fnm[g];
+            free_rp(k, md, m, im, dt, pv, qv);
         }
         p[g] = pv;
         q[g] = qv;
@@ -207,8 +211,8 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
 template <typename Real>
 __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
                                  const double* __restrict__ cmat, const Mode* __restrict__ modes,
-                                 const double* __restrict__ mass, const unsigned long long* __restrict__ stepp,
-                                 double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
+                                 const double* __restrict__ mass, const double2* __restrict__ minv,
+                                 const unsigned long long* __restrict__ stepp, double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
                                  double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ qpart,
                                  DevErr* __restrict__ err)
 {
@@ -232,11 +236,11 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         if (!isfinite(fn)) atomicOr(&err->flags, ERR_NONFINITE);
         if (do_step) {
             const Mode md = modes[rp.mode0 + k];
-            const double m = mass[rp.atom0 + t.i] * md.mfac;
-            double pv = p[g] + 0.5 * dt * fn / MVV2E;
+            const double2 mi = minv[rp.atom0 + t.i];
+            double pv = p[g] + 0.5 * dt * INV_MVV2E * fn;
             if (thermostat) {
                 const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
-                dK = pile_o(rp, md, m, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
+                dK = pile_o(rp, md, mi.y * md.smf, mi.x * md.imf, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
             }
             p[g] = pv;
         }
@@ -287,11 +291,11 @@ void launch_rp_start(const Dev& d, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
             (Dbl4*)d.x, d.qpart);
     else
         rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
             (float4*)d.x, d.qpart);
 }
 
@@ -299,11 +303,11 @@ void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat && !d.splitting,
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err);
     else
         rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.step, d.dt, d.thermostat && !d.splitting,
+            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err);
 }
 
