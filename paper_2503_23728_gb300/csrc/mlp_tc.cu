@@ -121,6 +121,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -395,6 +411,223 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// Network for widths 64 / 128 with two tiles resident per SM: the hidden
+// activations h_1 .. h_(L-1) are parked in tensor memory (packed BF16 pairs
+// next to the accumulator) for the backward pass, so shared memory holds only
+// the descriptor tile, one activation / gradient tile and one weight buffer
+// (80 KB at width 128) and tensor memory 256 columns per CTA. While one CTA
+// waits on its MMA or its weight copy, the other runs its epilogue.
+// ---------------------------------------------------------------------------
+template <int W, int L>
+__host__ __device__ constexpr int park_cols() { return (W < 64 ? 64 : W) + (L - 1) * (W / 2); }
+
+template <int W, int L>
+__global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
+    const float* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
+    const unsigned char* __restrict__ wimg, size_t img_per_type, const float* __restrict__ wvec,
+    size_t vec_per_type, float* __restrict__ Eatom, float* __restrict__ dEdG, DevErr* __restrict__ err)
+{
+    constexpr int M = 128;
+    constexpr int A0_B = M * ND * 2;
+    constexpr int H_B = M * W * 2;
+    constexpr int WB_B = W * W * 2 > W * ND * 2 ? W * W * 2 : W * ND * 2;
+    constexpr int TACC = W < 64 ? 64 : W;       // accumulator columns
+    constexpr int TALLOC = 256;                  // per CTA: two CTAs share the SM's 512 columns
+    static_assert(park_cols<W, L>() <= TALLOC, "parked activations exceed tensor memory");
+    constexpr int NPH = 2 * L;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A0 = sm;
+    unsigned char* ACT = A0 + A0_B;              // h_(l-1) as the next A operand, later dE/da_l
+    unsigned char* WB = ACT + H_B;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(WB + WB_B);   // [0] mma, [1] weights
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+    float* ysum = reinterpret_cast<float*>(tslot + 4);          // [2][128]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hsel = warp >> 2;
+    const int row = 32 * q + lane;
+    const int row0 = blockIdx.x * M;
+    const int type = tile_type[row0 / TILE_ROWS];
+    const unsigned char* img = wimg + (size_t)type * img_per_type;
+    const float* vec = wvec + (size_t)type * vec_per_type;
+    const float* b_l = vec;
+    const float* w_out = vec + L * W;
+    const float* mu = w_out + W;
+    const float* sigma = mu + ND;
+    const float b_out = sigma[ND], s_E = sigma[ND + 1], e_Z = sigma[ND + 2];
+
+    const uint32_t bar_mma = smem_u32(&bars[0]);
+    const uint32_t bar_w = smem_u32(&bars[1]);
+    if (tid == 0) {
+        mbar_init(bar_mma, 1);
+        mbar_init(bar_w, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TALLOC)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+
+    int issued = 0;   // weight copies issued (phase p uses parity p & 1)
+    auto issue_w = [&](int p) {
+        const int l = p < L ? p + 1 : 2 * L - p;
+        const int in = l == 1 ? ND : W;
+        bulk_load(smem_u32(WB), img + img_offset(W, L, p), (uint32_t)img_bytes(W, in), bar_w);
+    };
+    if (tid == 0) {
+        issue_w(0);
+        issued = 1;
+    }
+
+    // h_0 = (G - mu) / sigma in BF16: thread -> (row tid % 128, 32 columns)
+    {
+        const int r = tid & (M - 1), c0 = (tid >> 7) * 32;
+        const int ba = perm[row0 + r];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + 8 * g + j;
+                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : 0.0f;
+            }
+            uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                  pack_bf16(v[6], v[7]));
+            *reinterpret_cast<uint4*>(A0 + 2 * cm_index(r, c0 + 8 * g, ND)) = pk;
+        }
+    }
+    fence_proxy();
+    __syncthreads();
+
+    bool ok = true;
+    float y_part = 0.0f;
+    int p_fail = -1;
+    for (int p = 0; p < NPH && ok; ++p) {
+        const bool fwd = p < L;
+        const int l = fwd ? p + 1 : 2 * L - p;
+        const int K = fwd ? (l == 1 ? ND : W) : W;
+        const int N = fwd ? W : (l == 1 ? ND : W);
+        const unsigned char* Aop = (fwd && l == 1) ? A0 : ACT;
+        p_fail = p;
+        bool good = true;
+        if (tid == 0) {
+            good = mbar_wait(bar_w, (uint32_t)(p & 1));
+            if (good) {
+                fence_after();
+                const uint32_t a0 = smem_u32(Aop), b0 = smem_u32(WB);
+                const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+                const uint32_t idesc = make_idesc(M, N);
+                for (int ks = 0; ks < K / 16; ++ks) {
+                    const uint64_t ad = make_desc(a0 + ks * 256u, 128u, sbo);
+                    const uint64_t bd = make_desc(b0 + ks * 256u, 128u, sbo);
+                    mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+                mma_commit(bar_mma);
+            }
+        }
+        good = mbar_wait(bar_mma, (uint32_t)(p & 1)) && good;
+        ok = __syncthreads_and(good ? 1 : 0) != 0;
+        if (!ok) break;
+        fence_after();
+        // the MMA has read the weights and the A tile: next weights, then the epilogue
+        if (tid == 0 && p + 1 < NPH) {
+            issue_w(p + 1);
+            issued = p + 2;
+        }
+        const int cbeg = hsel * (N / 2), cend = cbeg + N / 2;
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)c0, v);
+            if (fwd) {
+                float h[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) h[j] = tanh_f(v[j] + b_l[(l - 1) * W + c0 + j]);
+                if (l < L) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) pk[t] = pack_bf16(h[2 * t], h[2 * t + 1]);
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+                        *reinterpret_cast<uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, W)) =
+                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                    tmem_st8(lane_base + (uint32_t)(TACC + (l - 1) * (W / 2) + (c0 >> 1)), pk);
+                } else {
+                    float ga[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float wo = w_out[c0 + j];
+                        y_part += wo * h[j];
+                        ga[j] = s_E * wo * (1.0f - h[j] * h[j]);
+                    }
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+                        *reinterpret_cast<uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, W)) =
+                            make_uint4(pack_bf16(ga[8 * g], ga[8 * g + 1]), pack_bf16(ga[8 * g + 2], ga[8 * g + 3]),
+                                       pack_bf16(ga[8 * g + 4], ga[8 * g + 5]), pack_bf16(ga[8 * g + 6], ga[8 * g + 7]));
+                }
+            } else if (l > 1) {
+                // dE/da_(l-1) = (W_l^T dE/da_l) * (1 - h_(l-1)^2), h_(l-1) from its parking place
+                uint32_t hw[8];
+                tmem_ld8(lane_base + (uint32_t)(TACC + (l - 2) * (W / 2) + (c0 >> 1)), hw);
+                uint32_t pk[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float2 hh = unpack_bf16(hw[t]);
+                    pk[t] = pack_bf16(v[2 * t] * (1.0f - hh.x * hh.x), v[2 * t + 1] * (1.0f - hh.y * hh.y));
+                }
+#pragma unroll
+                for (int g = 0; g < 2; ++g)
+                    *reinterpret_cast<uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, W)) =
+                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+            } else {
+                const int ba = perm[row0 + row];
+                if (ba >= 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4) {
+                        float4 o = make_float4(v[j] / sigma[c0 + j], v[j + 1] / sigma[c0 + j + 1],
+                                               v[j + 2] / sigma[c0 + j + 2], v[j + 3] / sigma[c0 + j + 3]);
+                        *reinterpret_cast<float4*>(dEdG + (size_t)ba * ND + c0 + j) = o;
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        if (fwd && l == L) ysum[hsel * M + row] = y_part;
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (fwd && l == L && hsel == 0) {
+            const int ba = perm[row0 + row];
+            if (ba >= 0) Eatom[ba] = s_E * (ysum[row] + ysum[M + row] + b_out) + e_Z;
+        }
+    }
+    if (!ok) {
+        // a wait gave up: report, let the last issued copy and an MMA still in
+        // flight finish (bounded), then release TMEM
+        if (tid == 0) {
+            atomicOr(&err->flags, ERR_TIMEOUT);
+            if (issued > 0) mbar_wait(bar_w, (uint32_t)((issued - 1) & 1));
+            if (p_fail >= 0) mbar_wait(bar_mma, (uint32_t)(p_fail & 1));
+        }
+        __syncthreads();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TALLOC) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Wide network (hidden width 256): weights stream through shared memory in
 // K-chunks of 64 (double-buffered bulk copies; a tcgen05.commit per chunk
 // releases its buffer), one activation buffer serves as the next layer's A
@@ -442,21 +675,6 @@ __host__ __device__ __forceinline__ size_t wide_chunk_offset(int L, int g, int* 
     return o;
 }
 
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(r[0]),
-                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr)
-                 : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 }  // namespace
 
@@ -780,8 +998,27 @@ void prepare_tc_weights(const Dev& d, int /*type*/, const double* blob, void* ho
 }
 
 template <int W, int L>
+static size_t park_smem()
+{
+    const size_t WB_B = (size_t)W * (W > ND ? W : ND) * 2;
+    return (size_t)128 * ND * 2 + (size_t)128 * W * 2 + WB_B + 64 + 2 * 128 * 4 + 1024;
+}
+
+template <int W, int L>
 static void run_tc(const Dev& d, cudaStream_t st)
 {
+    if constexpr (park_cols<W, L>() <= 256) {
+        const size_t sm = park_smem<W, L>();
+        static size_t done = 0;
+        if (sm > done) {
+            cudaFuncSetAttribute(mlp_tc_park_kernel<W, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            done = sm;
+        }
+        mlp_tc_park_kernel<W, L><<<d.rows_pad / 128, TC_THREADS, sm, st>>>(
+            (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
+            d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err);
+        return;
+    }
     const bool db = tc_smem(W, L, true) <= 227 * 1024;
     const size_t sm = tc_smem(W, L, db);
     static size_t done[2] = {0, 0};
