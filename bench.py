@@ -47,6 +47,11 @@ MOM_ADJ_FLOP_PER_ATOM = 165 * 36
 # the fold of dE/dM onto the 81 (161 targets x up to 3 adds x 4 widths)
 MOM_RED_ADJ_FLOP_PER_NBR = 380 + 2 * 668
 MOM_RED_ADJ_FLOP_PER_ATOM = 165 * 36 + 161 * 3 * 4
+# DRAM bytes (read + write) of one adjoint launch from an ncu capture of the
+# same kernel on the same workload (ice Ih, P = 32, BF16 network, reduced
+# moment basis): 139.7 MB read (mostly the 3 KB of moments per bead-atom)
+# + 3.9 MB written. Reported only for that configuration.
+ADJ_TRAFFIC_NCU = {("ice", "bf16_tc", "moments"): 139.745e6 + 3.857e6}
 
 
 def args():
@@ -460,7 +465,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": ("desc_mom_adj_kernel" if ctx.angular == "moments" else
                                                 "desc_adj_kernel") + " (angular+radial adjoint, forces, virial)",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": ADJ_TRAFFIC_NCU.get((w.name, a.precision, ctx.angular)),
                      "flops_per_launch": adj_flops,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
         "network_tensor": {"flops_per_launch": net_flops, "ms": st_mean["network"],
@@ -468,7 +474,9 @@ def main():
                            "peak_bf16_tflops_measured": peaks.get("bf16_tflops")},
         "clocks": clocks,
         "e2e": {"value": world * w.bead_atoms / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "what": "pimd_energy_forces with host positions in, forces out"},
+                "d2h_bytes_per_step": d2h, "what": "one force evaluation per step through pimd_energy_forces: bead positions H2D from "
+                        "pinned memory, energies and forces D2H; no ring-polymer step and no L2 flush, "
+                        "so it can exceed the device-timed full-step value"},
         "gpu_launches": launches,
         "next_rows": extras,
     }
