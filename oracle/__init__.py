@@ -7,6 +7,9 @@ normal modes and estimators; descriptor-based energy model of Sec. 1 / ref.
 [17] with forces as the energy gradient, Sec. 2.2; PILE-L of Tables S2-S3) in
 C, loaded through ctypes. It shares no code with the CUDA library.
 
+The graph-field-network force head (Sec. 2.2, direct forces) is the numpy
+module ``oracle.gfn``.
+
 Parity pins live in tests/test_oracle_*.py. Parts without an independent pin:
 long-time trajectory physics of the random-init network (parity unpinned).
 """

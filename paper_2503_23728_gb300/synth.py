@@ -406,3 +406,87 @@ def elements_of(replicas) -> tuple:
     for r in replicas:
         s.update(int(z) for z in r.Z)
     return tuple(sorted(s))
+
+
+# --------------------------------------------------------------------------
+# graph field network (direct-force head, Sec. 2.2): parameter shapes and
+# random-init weights. Layout of the flat FP64 blob (row-major matrices,
+# y = W x + b):
+#   emb [n_el][F]; W_e [F][32], b_e [F];
+#   per iteration l = 0 .. L-1: W_m [F][F], b_m [F], W_v1 [F][2F], b_v1 [F],
+#       W_v2 [F][F], b_v2 [F], W_a1 [F][F], b_a1 [F], W_a2 [F][F], b_a2 [F];
+#   W_f1 [F][F], b_f1 [F], w_f2 [F], b_f2 [1], s_F [1].
+# --------------------------------------------------------------------------
+GFN_ITER_KEYS = (("W_m", "FF"), ("b_m", "F"), ("W_v1", "F2F"), ("b_v1", "F"), ("W_v2", "FF"), ("b_v2", "F"),
+                 ("W_a1", "FF"), ("b_a1", "F"), ("W_a2", "FF"), ("b_a2", "F"))
+
+
+def gfn_offsets(F: int, L: int, n_el: int) -> dict:
+    shapes = {"F": (F,), "FF": (F, F), "F2F": (F, 2 * F)}
+    off, o = {}, 0
+
+    def put(key, shape):
+        nonlocal o
+        off[key] = (o, shape)
+        o += int(np.prod(shape))
+
+    put("emb", (n_el, F))
+    put("W_e", (F, N_RADIAL))
+    put("b_e", (F,))
+    for l in range(L):
+        for k, s in GFN_ITER_KEYS:
+            put("%s%d" % (k, l), shapes[s])
+    put("W_f1", (F, F))
+    put("b_f1", (F,))
+    put("w_f2", (F,))
+    put("b_f2", (1,))
+    put("s_F", (1,))
+    off["_size"] = o
+    return off
+
+
+@dataclass
+class GfnModel:
+    """Graph-field-network force head: feature width F, L message-passing
+    iterations, one FP64 parameter blob (layout in gfn_offsets), the radial
+    basis of the descriptors (r_mu, eta_R, cutoff)."""
+    elements: tuple
+    F: int
+    L: int
+    blob: np.ndarray
+    desc: dict
+
+    def view(self, key: str) -> np.ndarray:
+        o, shape = gfn_offsets(self.F, self.L, len(self.elements))[key]
+        return self.blob[o:o + int(np.prod(shape))].reshape(shape)
+
+
+def gfn_model(elements, F: int = 128, L: int = 3, seed: int = 11, cutoff: float = 6.0) -> GfnModel:
+    """Xavier-uniform matrices, small uniform biases (so that every term of
+    the head is exercised), N(0, 1) embeddings, s_F = 1."""
+    rng = np.random.default_rng(seed)
+    els = tuple(sorted(int(z) for z in elements))
+    off = gfn_offsets(F, L, len(els))
+    blob = np.zeros(off["_size"])
+    for key, val in off.items():
+        if key == "_size":
+            continue
+        o, shape = val
+        n = int(np.prod(shape))
+        if key == "emb":
+            blob[o:o + n] = rng.normal(size=n)
+        elif len(shape) == 2:
+            a = math.sqrt(6.0 / (shape[0] + shape[1]))
+            blob[o:o + n] = rng.uniform(-a, a, size=n)
+        elif key == "w_f2":
+            a = math.sqrt(6.0 / (shape[0] + 1))
+            blob[o:o + n] = rng.uniform(-a, a, size=n)
+        elif key == "s_F":
+            blob[o] = 1.0
+        else:
+            blob[o:o + n] = rng.uniform(-0.1, 0.1, size=n)
+    return GfnModel(els, F, L, blob, descriptor_params(cutoff))
+
+
+def set_force_scale(model: GfnModel, s_F: float) -> None:
+    model.view("s_F")[:] = s_F
