@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define PIMD_ABI_VERSION 2
+#define PIMD_ABI_VERSION 3
 #define PIMD_N_RADIAL 32
 #define PIMD_N_ANGULAR 32
 #define PIMD_N_DESC 64
@@ -108,7 +108,12 @@ typedef enum {
 
 typedef enum {
     PIMD_POT_MODEL = 0,     /* symmetry-function network (set by pimd_set_weights)  */
-    PIMD_POT_HARMONIC = 1   /* V = sum_i 1/2 m_i omega^2 |x_i|^2 (Sec. S1 test case) */
+    PIMD_POT_HARMONIC = 1,  /* V = sum_i 1/2 m_i omega^2 |x_i|^2 (Sec. S1 test case) */
+    PIMD_POT_GFN = 2        /* graph-field-network force head (Sec. 2.2, set by
+                               pimd_set_gfn): forces read out directly from edge
+                               representations, no energy (per-bead V = 0, so
+                               the energy estimators carry only the ring-polymer
+                               terms); FP32 precision only                       */
 } pimd_potential;
 
 /* ---- well-tempered metadynamics (Sec. 2.5) --------------------------------
@@ -185,6 +190,9 @@ typedef struct {
                                 and half the box, off below 0.05 A), none for
                                 smaller ones; 0: rebuild every step.           */
     int transform;           /* pimd_transform: ring-polymer coordinates       */
+    int gfn_features;        /* PIMD_POT_GFN: feature width F of node and edge
+                                representations: 32, 64 or 128                */
+    int gfn_iterations;      /* PIMD_POT_GFN: message-passing iterations L, 0..8 */
 } pimd_config;
 
 /* stages of one step, in launch order (pimd_stage_times) */
@@ -275,6 +283,37 @@ int pimd_set_weights(pimd_ctx* ctx, const pimd_model_desc* model);
  * A and PILE-L O (Philox counter: index, step, replica, stream 2 / 3).
  * Asynchronous on the context stream. Errors: STATE if weights are missing. */
 int pimd_step(pimd_ctx* ctx, int n_steps);
+
+/* ---- graph-field-network force head (Sec. 2.2) ----------------------------
+ * With F features and L iterations (pimd_config.gfn_features / _iterations)
+ * and SiLU activations:
+ *   n_i^(0) = emb[Z_i],  e_ij^(0) = W_e rho(r_ij) + b_e,
+ *     rho_mu(r) = exp(-eta_R (r - r_mu)^2) fc(r), mu = 0..31, fc the cosine
+ *     cutoff at pimd_config.cutoff_A;
+ *   for l = 0 .. L-1:
+ *     m_i     = sum_{j in N(i)} SiLU(W_m e_ij + b_m)
+ *     n_i'    = n_i + W_v2 SiLU(W_v1 [n_i; m_i] + b_v1) + b_v2
+ *     e_ij'   = e_ij + W_a2 SiLU(W_a1 (n_i + n_j) + b_a1) + b_a2   (pre-update n)
+ *   F_i = sum_{j in N(i)} s_F fc(r_ij) (x_i - x_j) / r_ij (w_f2 . SiLU(W_f1 e_ij^(L) + b_f1) + b_f2),
+ *   virial W = 1/2 sum_i sum_j (x_i - x_j) (x) F_ij.
+ * params: FP64 host blob, row-major matrices (y = W x): emb [n_el][F];
+ * W_e [F][32], b_e [F]; per iteration W_m [F][F], b_m [F], W_v1 [F][2F],
+ * b_v1 [F], W_v2 [F][F], b_v2 [F], W_a1 [F][F], b_a1 [F], W_a2 [F][F],
+ * b_a2 [F]; then W_f1 [F][F], b_f1 [F], w_f2 [F], b_f2, s_F.                */
+typedef struct {
+    int n_elements;                  /* element types, 1..PIMD_MAX_ELEMENTS        */
+    int Z[PIMD_MAX_ELEMENTS];        /* their atomic numbers, ascending (rows of emb) */
+    const double* params;            /* host, copied during the call               */
+    size_t n_params;                 /* length of params (checked against F, L)    */
+    double r_mu[32];                 /* radial centres, A                          */
+    double eta_R;                    /* radial width, 1/A^2                        */
+} pimd_gfn_desc;
+
+/* Set the graph-field-network parameters (converted to FP32 on the device).
+ * Errors: STATE (potential is not PIMD_POT_GFN), INVALID_ARG (NULL arrays,
+ * wrong n_params, Z not ascending or missing an element of the replicas,
+ * non-finite parameters).                                                   */
+int pimd_set_gfn(pimd_ctx* ctx, const pimd_gfn_desc* g);
 
 /* Potential energy, forces and virial of arbitrary bead positions, without
  * touching the dynamical state. x_dev: device [B][3] FP64 positions in

@@ -56,6 +56,7 @@ struct Build {
     int total_cells = 0, max_cells = 0;
     int R = 0, S = 0, B = 0, NA = 0, rows_pad = 0;
     size_t blob = 0, wtc_bytes = 0, wtc_vec = 0;
+    size_t gfn_params = 0;   // FP32 parameters of the graph-field-network head
     bool periodic_any = false;
     bool any_skin = false;
     double nb_est = 0.0;   // mean neighbour count per bead-atom (estimate from density)
@@ -65,6 +66,17 @@ struct Build {
 // (a skin of 0.5 A at r_c = 6 A holds 1.27 x the neighbours), multiple of 32,
 // at most the sort capacity
 int max_candidates(int maxnb) { return std::min(PIMD_SORT_CAP, (maxnb * 3 / 2 + 31) / 32 * 32); }
+
+// potentials evaluated on neighbour graphs (the network and the GFN head)
+bool graph_pot(int pot) { return pot == PIMD_POT_MODEL || pot == PIMD_POT_GFN; }
+
+// length of the graph-field-network parameter blob (layout in pimd.h)
+size_t gfn_blob_len(int F, int L, int n_el)
+{
+    const size_t FF = (size_t)F * F;
+    return (size_t)n_el * F + (size_t)F * NR + F + (size_t)L * (FF + F + 2 * FF + F + FF + F + FF + F + FF + F) + FF +
+           F + F + 2;
+}
 
 struct Carve {
     size_t off = 0;
@@ -81,7 +93,8 @@ struct Offsets {
     size_t reps, bsys, ba_sys, mass, minv, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
         fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
-        md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, total;
+        md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, gfn_w,
+        gfn_n, gfn_m, gfn_e, total;
 };
 
 int check_config(const pimd_config* cfg, std::string& e)
@@ -97,7 +110,8 @@ int check_config(const pimd_config* cfg, std::string& e)
     if (cfg->splitting != PIMD_OBABO && cfg->splitting != PIMD_BAOAB) { e = "splitting must be PIMD_OBABO or PIMD_BAOAB"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->free_rp != PIMD_FREE_RP_EXACT && cfg->free_rp != PIMD_FREE_RP_CAYLEY) { e = "free_rp must be PIMD_FREE_RP_EXACT or PIMD_FREE_RP_CAYLEY"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->deterministic != 0 && cfg->deterministic != 1) { e = "deterministic must be 0 or 1"; return PIMD_ERR_INVALID_ARG; }
-    if (cfg->potential != PIMD_POT_MODEL && cfg->potential != PIMD_POT_HARMONIC) { e = "unknown potential"; return PIMD_ERR_INVALID_ARG; }
+    if (cfg->potential != PIMD_POT_MODEL && cfg->potential != PIMD_POT_HARMONIC && cfg->potential != PIMD_POT_GFN)
+        { e = "unknown potential"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat == 1 && !(cfg->gamma0_per_fs >= 0.0)) { e = "gamma0_per_fs must be >= 0"; return PIMD_ERR_INVALID_ARG; }
     if (cfg->thermostat == 1 && !(cfg->pile_lambda >= 0.0)) { e = "pile_lambda must be >= 0"; return PIMD_ERR_INVALID_ARG; }
     int mnb = cfg->max_neighbours == 0 ? 128 : cfg->max_neighbours;
@@ -113,6 +127,13 @@ int check_config(const pimd_config* cfg, std::string& e)
         if (cfg->precision == PIMD_BF16_TC && !network_tc_supported(w, cfg->n_hidden)) {
             e = "tensor-core network does not support this width"; return PIMD_ERR_UNSUPPORTED;
         }
+    } else if (cfg->potential == PIMD_POT_GFN) {
+        if (!(cfg->cutoff_A > 0.0)) { e = "cutoff_A must be > 0"; return PIMD_ERR_INVALID_ARG; }
+        if (cfg->precision != PIMD_FP32) { e = "the GFN head runs in FP32 precision only"; return PIMD_ERR_UNSUPPORTED; }
+        if (cfg->gfn_features != 32 && cfg->gfn_features != 64 && cfg->gfn_features != 128)
+            { e = "gfn_features must be 32, 64 or 128"; return PIMD_ERR_UNSUPPORTED; }
+        if (cfg->gfn_iterations < 0 || cfg->gfn_iterations > GFN_MAX_ITERS)
+            { e = "gfn_iterations must be 0..8"; return PIMD_ERR_INVALID_ARG; }
     } else if (!(cfg->omega_harm >= 0.0)) {
         e = "omega_harm must be >= 0"; return PIMD_ERR_INVALID_ARG;
     }
@@ -166,7 +187,7 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         if (per) {
             for (int a = 0; a < 3; ++a)
                 if (!(d.box[a] > 0.0)) { e = "replica " + std::to_string(r) + ": box lengths must all be > 0 or all 0"; return PIMD_ERR_INVALID_ARG; }
-            if (cfg->potential == PIMD_POT_MODEL && std::min(d.box[0], std::min(d.box[1], d.box[2])) < 2.0 * cfg->cutoff_A) {
+            if (graph_pot(cfg->potential) && std::min(d.box[0], std::min(d.box[1], d.box[2])) < 2.0 * cfg->cutoff_A) {
                 e = "replica " + std::to_string(r) + ": periodic box shorter than twice the cutoff"; return PIMD_ERR_INVALID_ARG;
             }
         }
@@ -250,7 +271,7 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         rp.seed = h.seed;
         // Verlet skin of the candidate lists: at most 0.9 of the room between
         // r_c and half the box (unique minimum images), off below 0.05 A
-        if (cfg->potential == PIMD_POT_MODEL) {
+        if (graph_pot(cfg->potential)) {
             // auto: 1 A for replicas of >= 256 atoms (small ones scan all atoms
             // faster than they would check and filter candidates)
             double sk = cfg->nbr_skin_A < 0.0 ? (h.N >= 256 ? 1.0 : 0.0) : cfg->nbr_skin_A;
@@ -264,7 +285,7 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         }
         // cell lists: >= 3 cells per side with edge >= cutoff + skin (1e-5
         // margin against rounding of the FP32 cell coordinate)
-        if (rp.periodic && cfg->potential == PIMD_POT_MODEL && cfg->nbr_algo != 1) {
+        if (rp.periodic && graph_pot(cfg->potential) && cfg->nbr_algo != 1) {
             int nc[3];
             for (int a = 0; a < 3; ++a)
                 nc[a] = (int)std::floor(h.box[a] / ((cfg->cutoff_A + rp.skin) * (1.0 + 1e-5)));
@@ -363,6 +384,8 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
             b.wtc_vec = (size_t)cfg->n_hidden * cfg->widths[0] + cfg->widths[0] + 2 * ND + 4;
         }
     }
+    if (cfg->potential == PIMD_POT_GFN)
+        b.gfn_params = gfn_blob_len(cfg->gfn_features, cfg->gfn_iterations, (int)zs.size());
     return PIMD_OK;
 }
 
@@ -386,7 +409,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.x = c.take(v4 * b.B);
     o.f = c.take(v4 * b.B);
     const bool model = cfg->potential == PIMD_POT_MODEL;
-    o.nbr = c.take(model ? sizeof(int) * (size_t)b.B * mnb : 0);
+    o.nbr = c.take(graph_pot(cfg->potential) ? sizeof(int) * (size_t)b.B * mnb : 0);
     o.nnb = c.take(sizeof(int) * b.B);
     o.cell_start = c.take(sizeof(int) * (size_t)b.total_cells);
     o.cell_cnt = c.take(sizeof(int) * (size_t)b.total_cells);
@@ -435,6 +458,14 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.wts = c.take(rs * b.blob * b.typeZ.size());
     o.wtc = c.take(b.wtc_bytes * b.typeZ.size());
     o.wtc_vec = c.take(sizeof(float) * b.wtc_vec * b.typeZ.size());
+    {
+        const bool gfn = cfg->potential == PIMD_POT_GFN;
+        const size_t F = gfn ? (size_t)cfg->gfn_features : 0;
+        o.gfn_w = c.take(sizeof(float) * b.gfn_params);
+        o.gfn_n = c.take(sizeof(float) * F * b.B);
+        o.gfn_m = c.take(sizeof(float) * F * b.B);
+        o.gfn_e = c.take(sizeof(float) * F * (size_t)b.B * mnb);
+    }
     o.total = c.take(0) + 256;
     return o;
 }
@@ -501,6 +532,13 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
         launch_harmonic(d, st);
         mark(c, PIMD_STAGE_DESCRIPTORS, st, timed);
         mark(c, PIMD_STAGE_NETWORK, st, timed);
+        mark(c, PIMD_STAGE_ADJOINT, st, timed);
+    } else if (d.potential == PIMD_POT_GFN) {
+        // direct forces: the whole head runs in the network stage
+        launch_neighbours(d, st);
+        mark(c, PIMD_STAGE_DESCRIPTORS, st, timed);
+        mark(c, PIMD_STAGE_NETWORK, st, timed);
+        launch_gfn(d, st);
         mark(c, PIMD_STAGE_ADJOINT, st, timed);
     } else {
         launch_neighbours(d, st);
@@ -679,6 +717,14 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.wbuf = w + o.wbuf;
     d.vbuf = w + o.vbuf;
     d.mom = (cfg->potential == PIMD_POT_MODEL && cfg->precision != PIMD_FP64) ? (void*)(w + o.mom) : nullptr;
+    if (cfg->potential == PIMD_POT_GFN) {
+        d.gfn_w = (float*)(w + o.gfn_w);
+        d.gfn_n = (float*)(w + o.gfn_n);
+        d.gfn_m = (float*)(w + o.gfn_m);
+        d.gfn_e = (float*)(w + o.gfn_e);
+        d.gfn.F = cfg->gfn_features;
+        d.gfn.L = cfg->gfn_iterations;
+    }
     if (b.any_skin) {
         d.maxcand = max_candidates(d.maxnb);
         d.cand = (int*)(w + o.cand);
@@ -901,11 +947,96 @@ int pimd_set_weights(pimd_ctx* c, const pimd_model_desc* m)
     return rc;
 }
 
+int pimd_set_gfn(pimd_ctx* c, const pimd_gfn_desc* g)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!g) return fail(c, PIMD_ERR_INVALID_ARG, "desc is NULL");
+    if (c->d.potential != PIMD_POT_GFN) return fail(c, PIMD_ERR_STATE, "context does not use the GFN head");
+    Dev& d = c->d;
+    const Build& b = c->build;
+    const int F = d.gfn.F, L = d.gfn.L, ne = g->n_elements;
+    if (!g->params) return fail(c, PIMD_ERR_INVALID_ARG, "params is NULL");
+    if (ne < 1 || ne > PIMD_MAX_ELEMENTS) return fail(c, PIMD_ERR_INVALID_ARG, "n_elements must be 1..8");
+    for (int q = 1; q < ne; ++q)
+        if (!(g->Z[q] > g->Z[q - 1])) return fail(c, PIMD_ERR_INVALID_ARG, "Z must be ascending");
+    if (g->n_params != gfn_blob_len(F, L, ne))
+        return fail(c, PIMD_ERR_INVALID_ARG, "n_params is " + std::to_string(g->n_params) + ", the layout needs " +
+                                                 std::to_string(gfn_blob_len(F, L, ne)));
+    for (size_t q = 0; q < g->n_params; ++q)
+        if (!std::isfinite(g->params[q])) return fail(c, PIMD_ERR_INVALID_ARG, "non-finite GFN parameter");
+    if (!(g->eta_R > 0.0) || !std::isfinite(g->eta_R)) return fail(c, PIMD_ERR_INVALID_ARG, "eta_R must be > 0");
+    for (int q = 0; q < NR; ++q)
+        if (!std::isfinite(g->r_mu[q])) return fail(c, PIMD_ERR_INVALID_ARG, "non-finite r_mu");
+    // FP32 device image: the context's element types in ascending Z, matrices transposed
+    std::vector<float> w(b.gfn_params, 0.0f);
+    GfnParams gp = d.gfn;
+    unsigned o = 0;
+    const double* q = g->params;
+    gp.o_emb = o;
+    for (size_t t = 0; t < b.typeZ.size(); ++t) {
+        int e = -1;
+        for (int k = 0; k < ne; ++k)
+            if (g->Z[k] == b.typeZ[t]) e = k;
+        if (e < 0) return fail(c, PIMD_ERR_INVALID_ARG, "no embedding for element " + std::to_string(b.typeZ[t]));
+        for (int k = 0; k < F; ++k) w[o + t * F + k] = (float)q[(size_t)e * F + k];
+    }
+    o += (unsigned)(b.typeZ.size() * F);
+    q += (size_t)ne * F;
+    auto put_t = [&](int out, int in) {   // host W [out][in] -> device W^T [in][out]
+        const unsigned off = o;
+        for (int i = 0; i < in; ++i)
+            for (int j = 0; j < out; ++j) w[o + (size_t)i * out + j] = (float)q[(size_t)j * in + i];
+        o += (unsigned)(in * out);
+        q += (size_t)in * out;
+        return off;
+    };
+    auto put_v = [&](int n) {
+        const unsigned off = o;
+        for (int i = 0; i < n; ++i) w[o + i] = (float)q[i];
+        o += (unsigned)n;
+        q += n;
+        return off;
+    };
+    gp.o_We = put_t(F, NR);
+    gp.o_be = put_v(F);
+    for (int l = 0; l < L; ++l) {
+        gp.o_it[l][0] = put_t(F, F);
+        gp.o_it[l][1] = put_v(F);
+        gp.o_it[l][2] = put_t(F, 2 * F);
+        gp.o_it[l][3] = put_v(F);
+        gp.o_it[l][4] = put_t(F, F);
+        gp.o_it[l][5] = put_v(F);
+        gp.o_it[l][6] = put_t(F, F);
+        gp.o_it[l][7] = put_v(F);
+        gp.o_it[l][8] = put_t(F, F);
+        gp.o_it[l][9] = put_v(F);
+    }
+    gp.o_Wf1 = put_t(F, F);
+    gp.o_bf1 = put_v(F);
+    gp.o_wf2 = put_v(F);
+    gp.b_f2 = (float)q[0];
+    gp.s_F = (float)q[1];
+    gp.rc = (float)c->cfg.cutoff_A;
+    gp.pi_over_rc = (float)(M_PI / c->cfg.cutoff_A);
+    gp.eta_R = (float)g->eta_R;
+    for (int k = 0; k < NR; ++k) gp.r_mu[k] = (float)g->r_mu[k];
+    int rc = upload(c, d.gfn_w, w);
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "GFN parameter upload");
+    if (rc) return rc;
+    d.gfn = gp;
+    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
+    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    c->weights_set = true;
+    rc = refresh_forces(c);
+    if (!rc) rc = device_errors(c);
+    return rc;
+}
+
 int pimd_step(pimd_ctx* c, int n_steps)
 {
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
     if (n_steps < 0) return fail(c, PIMD_ERR_INVALID_ARG, "n_steps < 0");
-    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    if (graph_pot(c->d.potential) && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
     if (n_steps == 0) return PIMD_OK;
     int rc = PIMD_OK;
     if (!c->forces_valid) {
@@ -1051,13 +1182,15 @@ int pimd_kernels_per_step(const pimd_ctx* c)
     // ring start, neighbours, descriptors, network, adjoint, energy, ring finish, step counter;
     // metadynamics: CV, bias, bias force
     const int md = c->d.metad.cv ? 3 : 0;
+    if (c->d.potential == PIMD_POT_GFN)   // ring start, neighbours, the head, energy, ring finish, counter
+        return 5 + 2 + gfn_kernels_per_eval(c->d.gfn.L) + md;
     return (c->d.potential == PIMD_POT_HARMONIC ? 5 : (c->d.deterministic ? 9 : 8)) + md;
 }
 
 int pimd_energy_forces(pimd_ctx* c, const double* x_dev, double* e_dev, double* f_dev, double* virial_dev)
 {
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
-    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    if (graph_pot(c->d.potential) && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
     if (x_dev) {
         launch_pack_positions(c->d, x_dev, c->st);
         c->beads_current = false;
@@ -1102,7 +1235,7 @@ int pimd_estimators(pimd_ctx* c, pimd_est* out, int n_reps)
 {
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
     if (!out || n_reps != c->d.R) return fail(c, PIMD_ERR_INVALID_ARG, "n_reps must equal the replica count");
-    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    if (graph_pot(c->d.potential) && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
     int rc = PIMD_OK;
     if (!c->forces_valid) {
         rc = refresh_forces(c);
@@ -1158,7 +1291,7 @@ int pimd_set_state(pimd_ctx* c, const double* q_nm, const double* p_nm, uint64_t
     c->step_host = step;
     c->beads_current = false;
     c->forces_valid = false;
-    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return PIMD_OK;
+    if (graph_pot(c->d.potential) && !c->weights_set) return PIMD_OK;
     rc = refresh_forces(c);
     if (!rc) rc = device_errors(c);
     return rc;
@@ -1167,7 +1300,7 @@ int pimd_set_state(pimd_ctx* c, const double* q_nm, const double* p_nm, uint64_t
 int pimd_get_forces(pimd_ctx* c, double* x_host, double* f_host, double* V_host)
 {
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
-    if (c->d.potential == PIMD_POT_MODEL && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
+    if (graph_pot(c->d.potential) && !c->weights_set) return fail(c, PIMD_ERR_STATE, "weights not set");
     int rc = PIMD_OK;
     if (!c->forces_valid) {
         rc = refresh_forces(c);
@@ -1201,7 +1334,7 @@ int pimd_get_forces(pimd_ctx* c, double* x_host, double* f_host, double* V_host)
 int pimd_get_neighbours(pimd_ctx* c, int* nnb_host, int* nbr_host)
 {
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
-    if (c->d.potential != PIMD_POT_MODEL) return fail(c, PIMD_ERR_STATE, "no neighbour lists for this potential");
+    if (!graph_pot(c->d.potential)) return fail(c, PIMD_ERR_STATE, "no neighbour lists for this potential");
     int rc = PIMD_OK;
     if (nnb_host) rc = cuda_check(c, cudaMemcpyAsync(nnb_host, c->d.nnb, sizeof(int) * c->d.B, cudaMemcpyDeviceToHost, c->st), "copy");
     if (!rc && nbr_host)

@@ -112,6 +112,18 @@ struct DescParams {
     Real rec_k;    // 2^(-2 eta_R log2(e) r_delta^2), the ratio of successive ratios
 };
 
+// graph-field-network head: sizes, radial basis, scalars and the offsets
+// (floats) of its FP32 parameters in the device weight buffer; matrices are
+// stored transposed ([in][out]) for the tile products
+constexpr int GFN_MAX_ITERS = 8;
+struct GfnParams {
+    int F, L;
+    float rc, pi_over_rc, eta_R, s_F, b_f2;
+    float r_mu[NR];
+    unsigned o_emb, o_We, o_be, o_Wf1, o_bf1, o_wf2;
+    unsigned o_it[GFN_MAX_ITERS][10];   // W_m^T, b_m, W_v1^T, b_v1, W_v2^T, b_v2, W_a1^T, b_a1, W_a2^T, b_a2
+};
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Reduce 32 per-lane values so that lane c ends with the sum over lanes of

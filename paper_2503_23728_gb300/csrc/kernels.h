@@ -77,6 +77,13 @@ struct Dev {
     DevErr* err = nullptr;
     double* est = nullptr;             // [R][EST_STRIDE]
 
+    // graph-field-network head (potential PIMD_POT_GFN)
+    GfnParams gfn = {};
+    float* gfn_w = nullptr;            // FP32 parameters (layout in GfnParams)
+    float* gfn_n = nullptr;            // [B][F] node representations
+    float* gfn_m = nullptr;            // [B][F] messages
+    float* gfn_e = nullptr;            // [B][maxnb][F] edge representations
+
     // network
     int n_types = 0, n_hidden = 0, width = 0;
     size_t blob = 0;                   // elements per type blob
@@ -116,6 +123,8 @@ void launch_descriptors(const Dev& d, const void* dp, cudaStream_t st);
 void launch_network_fp(const Dev& d, cudaStream_t st);
 void launch_network_tc(const Dev& d, cudaStream_t st);
 void launch_adjoint(const Dev& d, const void* dp, cudaStream_t st);
+void launch_gfn(const Dev& d, cudaStream_t st);
+int gfn_kernels_per_eval(int L);
 void launch_descriptors_moment(const Dev& d, const void* dp, cudaStream_t st);
 void launch_adjoint_moment(const Dev& d, const void* dp, cudaStream_t st);
 size_t moment_elems_per_atom();        // float4 moments per bead-atom

@@ -19,13 +19,14 @@ PIMD_OK = 0
 STATUS = {-9: "METAD_FULL", 0: "OK", -1: "INVALID_ARG", -2: "STATE", -3: "WORKSPACE_TOO_SMALL", -4: "CUDA", -5: "NONFINITE",
           -6: "TIMEOUT", -7: "NBR_OVERFLOW", -8: "UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16_tc": 2}
-POT_MODEL, POT_HARMONIC = 0, 1
+POT_MODEL, POT_HARMONIC, POT_GFN = 0, 1, 2
 EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_weights", "pimd_step",
            "pimd_energy_forces", "pimd_descriptors", "pimd_estimators", "pimd_get_state", "pimd_set_state",
            "pimd_get_forces", "pimd_get_neighbours", "pimd_sync", "pimd_sizes", "pimd_destroy", "pimd_last_error",
            "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule", "pimd_set_angular", "pimd_get_angular",
            "pimd_element_types", "pimd_rdf_counts", "pimd_pt_coordinate",
-           "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv", "pimd_selftest_bounded_wait"]
+           "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv", "pimd_selftest_bounded_wait",
+           "pimd_set_gfn"]
 ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
@@ -70,7 +71,7 @@ class pimd_config(ct.Structure):
                 ("n_hidden", ct.c_int), ("widths", ct.c_int * 4), ("stream", ct.c_void_p), ("timing", ct.c_int),
                 ("nbr_algo", ct.c_int), ("deterministic", ct.c_int), ("splitting", ct.c_int),
                 ("free_rp", ct.c_int), ("metad", ct.POINTER(pimd_metad_desc)), ("nbr_skin_A", ct.c_double),
-                ("transform", ct.c_int)]
+                ("transform", ct.c_int), ("gfn_features", ct.c_int), ("gfn_iterations", ct.c_int)]
 TRANSFORM = {"normal_modes": 0, "staging": 1}
 SPLITTING = {"obabo": 0, "baoab": 1}
 FREE_RP = {"exact": 0, "cayley": 1}
@@ -87,6 +88,11 @@ class pimd_model_desc(ct.Structure):
                 ("widths", ct.POINTER(ct.c_int)), ("params", ct.POINTER(ct.POINTER(ct.c_double))),
                 ("eta_R", ct.c_double), ("r_mu", ct.POINTER(ct.c_double)), ("zeta", ct.POINTER(ct.c_int)),
                 ("lam", ct.POINTER(ct.c_double)), ("eta_A", ct.POINTER(ct.c_double))]
+
+
+class pimd_gfn_desc(ct.Structure):
+    _fields_ = [("n_elements", ct.c_int), ("Z", ct.c_int * 8), ("params", ct.POINTER(ct.c_double)),
+                ("n_params", ct.c_size_t), ("r_mu", ct.c_double * 32), ("eta_R", ct.c_double)]
 
 
 class pimd_est(ct.Structure):
@@ -139,6 +145,7 @@ def load(path: str = LIB_PATH):
     L.pimd_tune.argtypes = [vp, ct.c_int, dp]
     L.pimd_set_schedule.argtypes = [vp, ct.c_int]
     L.pimd_set_angular.argtypes = [vp, ct.c_int]
+    L.pimd_set_gfn.argtypes = [vp, vp]
     L.pimd_get_angular.argtypes = [vp]
     L.pimd_get_angular.restype = ct.c_int
     L.pimd_selftest_bounded_wait.argtypes = [vp, ct.c_double]
@@ -387,7 +394,7 @@ def pimd_last_error(ctx=None) -> str:
 def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128, 128, 128), pile_lambda=1.0,
                 thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128, stream=None,
                 timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
-                free_rp="exact", metad=None, nbr_skin=-1.0, transform="normal_modes") -> pimd_config:
+                free_rp="exact", metad=None, nbr_skin=-1.0, transform="normal_modes", gfn=(128, 3)) -> pimd_config:
     c = pimd_config()
     c.dt_fs = dt_fs
     c.gamma0_per_fs = gamma0_per_fs
@@ -411,6 +418,7 @@ def make_config(dt_fs, gamma0_per_fs, precision="fp32", cutoff=6.0, widths=(128,
         c.metad = ct.pointer(metad)
     c.nbr_skin_A = float(nbr_skin)
     c.transform = TRANSFORM[transform] if isinstance(transform, str) else int(transform)
+    c.gfn_features, c.gfn_iterations = int(gfn[0]), int(gfn[1])
     return c
 
 
@@ -447,6 +455,25 @@ def make_replicas(replicas, keep: _Keep, masses=None):
     return arr
 
 
+def make_gfn(model, keep: _Keep) -> pimd_gfn_desc:
+    """pimd_gfn_desc of a synth.GfnModel (FP64 blob in the pimd.h layout)."""
+    g = pimd_gfn_desc()
+    g.n_elements = len(model.elements)
+    for e, z in enumerate(model.elements):
+        g.Z[e] = int(z)
+    blob = keep.add(np.ascontiguousarray(model.blob, dtype=np.float64))
+    g.params = _dp(blob)
+    g.n_params = blob.size
+    for k, r in enumerate(model.desc["r_mu"]):
+        g.r_mu[k] = float(r)
+    g.eta_R = float(model.desc["eta_R"])
+    return g
+
+
+def pimd_set_gfn(ctx, g: pimd_gfn_desc):
+    _check(load().pimd_set_gfn(ctx, ct.byref(g)), ctx)
+
+
 def make_model(model, keep: _Keep) -> pimd_model_desc:
     m = pimd_model_desc()
     els = list(model.elements)
@@ -475,7 +502,9 @@ class Context:
     def __init__(self, replicas, dt_fs, gamma0_per_fs, precision="fp32", widths=(128, 128, 128), cutoff=6.0,
                  pile_lambda=1.0, thermostat=True, potential=POT_MODEL, omega=0.0, max_neighbours=128,
                  masses=None, stream=None, timing=False, nbr_algo=0, deterministic=False, splitting="obabo",
-                 free_rp="exact", metad=None, nbr_skin=-1.0, transform="normal_modes"):
+                 free_rp="exact", metad=None, nbr_skin=-1.0, transform="normal_modes", gfn=(128, 3)):
+        """gfn: (features, iterations) of the graph-field-network head, used
+        with potential=POT_GFN (FP32 precision)."""
         import torch
         self.torch = torch
         self.keep = _Keep()
@@ -486,7 +515,7 @@ class Context:
         self.stream = stream
         self.cfg = make_config(dt_fs, gamma0_per_fs, precision, cutoff, widths, pile_lambda, thermostat, potential,
                                omega, max_neighbours, ct.c_void_p(stream.cuda_stream), timing, nbr_algo,
-                               deterministic, splitting, free_rp, metad, nbr_skin, transform)
+                               deterministic, splitting, free_rp, metad, nbr_skin, transform, gfn)
         self.metad_desc = metad
         self.reps = make_replicas(self.replicas, self.keep, masses)
         self.ws_bytes = pimd_workspace_size(self.cfg, self.reps)
@@ -509,6 +538,11 @@ class Context:
         keep = _Keep()
         desc = make_model(model, keep)
         pimd_set_weights(self.h, desc)
+
+    def set_gfn(self, model):
+        """Parameters of the graph-field-network head (synth.GfnModel)."""
+        keep = _Keep()
+        pimd_set_gfn(self.h, make_gfn(model, keep))
 
     def step(self, n: int = 1):
         pimd_step(self.h, n)

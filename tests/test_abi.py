@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert P.pimd_abi_version() == 2
+    assert P.pimd_abi_version() == 3
 
 
 def _cfg(**kw):
@@ -74,6 +74,33 @@ def test_config_errors(lib, bad):
         P.pimd_workspace_size(_cfg(**bad), reps)
     assert ei.value.code in (-1, -8)
     assert P.pimd_last_error()
+
+
+@pytest.mark.parametrize("bad, code", [
+    (dict(precision="bf16_tc"), -8), (dict(precision="fp64"), -8), (dict(gfn=(48, 3)), -8),
+    (dict(gfn=(64, 9)), -1), (dict(gfn=(64, -1)), -1), (dict(cutoff=0.0), -1),
+])
+def test_gfn_config_errors(lib, bad, code):
+    keep = P._Keep()
+    reps = P.make_replicas(s.workload("water64").replicas, keep)
+    kw = dict(potential=P.POT_GFN, gfn=(64, 3))
+    kw.update(bad)
+    with pytest.raises(P.PimdError) as ei:
+        P.pimd_workspace_size(_cfg(**kw), reps)
+    assert ei.value.code == code
+
+
+def test_gfn_workspace_holds_edge_states(lib):
+    """The head keeps e_ij (maxnb slots x F floats per bead-atom) between
+    iterations; no descriptors, network buffers or moments."""
+    keep = P._Keep()
+    w = s.workload("water64")
+    reps = P.make_replicas(w.replicas, keep)
+    B = sum(r.n_atoms * r.n_beads for r in w.replicas)
+    n64 = P.pimd_workspace_size(_cfg(potential=P.POT_GFN, gfn=(64, 3)), reps)
+    n128 = P.pimd_workspace_size(_cfg(potential=P.POT_GFN, gfn=(128, 3)), reps)
+    assert n128 - n64 >= 4 * 64 * B * 128
+    assert n64 > 4 * 64 * B * 128
 
 
 def test_replica_errors(lib):
