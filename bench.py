@@ -326,6 +326,43 @@ def metad_extras(w, stream):
             "frac_fp32_peak": XRD_FLOP_PER_PAIR * pairs / max(ms, 1e-6) / 1e9 / FP32_PEAK_TFLOPS}
 
 
+def gfn_mac(F, L, edges, nodes):
+    """Multiply-adds of one evaluation of the graph-field-network head: per
+    directed edge the input layer (32 x F), per iteration the message layer
+    (F x F) and the two node-to-edge layers (2 F x F), the readout (F x F);
+    per node and iteration the update (2F x F + F x F)."""
+    return edges * (32 * F + L * 3 * F * F + F * F) + nodes * L * 3 * F * F
+
+
+def gfn_extras(w, stream, steps=5):
+    """The graph-field-network force head (Sec. 2.2, Table S1 sizes: F = 128,
+    L = 3) driving the same ring polymers: step time and the head's
+    throughput, next to the energy model's step on the same workload."""
+    from paper_2503_23728_gb300 import pimd as P
+    from paper_2503_23728_gb300 import synth as s
+    F, L = 128, 3
+    m = s.gfn_model(s.elements_of(w.replicas), F, L, seed=7)
+    out = {"features": F, "iterations": L}
+    for prec in ("fp32",):
+        ctx = P.Context(w.replicas, w.dt_fs, w.gamma0_per_fs, precision=prec, potential=P.POT_GFN, gfn=(F, L),
+                        timing=True)
+        ctx.set_gfn(m)
+        ctx.step(2)
+        acc = []
+        for _ in range(steps):
+            ctx.step(1)
+            acc.append(ctx.stage_times())
+        st = {k: float(np.median([a[k] for a in acc])) for k in acc[0]}
+        nnb, _ = ctx.neighbours()
+        mac = gfn_mac(F, L, float(nnb.sum()), ctx.B)
+        out[prec] = {"ms_per_step": float(sum(st.values())), "head_ms": st["network"],
+                     "head_tflops": 2 * mac / (st["network"] / 1e3) / 1e12,
+                     "frac_fp32_peak": 2 * mac / (st["network"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                     "bead_atom_evals_per_s": ctx.B / (sum(st.values()) / 1e3)}
+        ctx.close()
+    return out
+
+
 def s_model(w):
     from paper_2503_23728_gb300 import synth as s
     return s.xavier_model(s.elements_of(w.replicas), w.widths, seed=7)
@@ -437,6 +474,7 @@ def main():
     if not a.no_extras and world == 1:
         extras = analysis_extras(ctx, w, stream)
         extras["metad"] = metad_extras(w, stream)
+        extras["gfn"] = gfn_extras(w, stream)
     launches = ctx.kernels_per_step() * a.steps
     fp32 = None
     if not a.no_fp32 and a.precision != "fp32":
