@@ -343,7 +343,7 @@ def gfn_extras(w, stream, steps=5):
     F, L = 128, 3
     m = s.gfn_model(s.elements_of(w.replicas), F, L, seed=7)
     out = {"features": F, "iterations": L}
-    for prec in ("fp32",):
+    for prec in ("fp32", "bf16_tc"):
         ctx = P.Context(w.replicas, w.dt_fs, w.gamma0_per_fs, precision=prec, potential=P.POT_GFN, gfn=(F, L),
                         timing=True)
         ctx.set_gfn(m)

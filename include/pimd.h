@@ -113,7 +113,8 @@ typedef enum {
                                pimd_set_gfn): forces read out directly from edge
                                representations, no energy (per-bead V = 0, so
                                the energy estimators carry only the ring-polymer
-                               terms); FP32 precision only                       */
+                               terms); FP32 (CUDA cores) or BF16 precision
+                               (tensor cores, F = 64 or 128)                     */
 } pimd_potential;
 
 /* ---- well-tempered metadynamics (Sec. 2.5) --------------------------------

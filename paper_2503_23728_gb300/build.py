@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpimd.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "force.cu", "nbr.cu", "ring.cu", "mlp_tc.cu", "noalloc.cu", "moment.cu", "analysis.cu", "metad.cu", "gfn.cu"]
+SOURCES = ["api.cu", "force.cu", "nbr.cu", "ring.cu", "mlp_tc.cu", "noalloc.cu", "moment.cu", "analysis.cu", "metad.cu", "gfn.cu", "gfn_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -67,6 +67,12 @@ struct Build {
 // at most the sort capacity
 int max_candidates(int maxnb) { return std::min(PIMD_SORT_CAP, (maxnb * 3 / 2 + 31) / 32 * 32); }
 
+// element (r, k) of an R x K operand in the tensor cores' K-major core-matrix layout
+size_t cm_index_host(int r, int k, int K)
+{
+    return ((size_t)(r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
 // potentials evaluated on neighbour graphs (the network and the GFN head)
 bool graph_pot(int pot) { return pot == PIMD_POT_MODEL || pot == PIMD_POT_GFN; }
 
@@ -94,7 +100,7 @@ struct Offsets {
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
         fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
         md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, gfn_w,
-        gfn_n, gfn_m, gfn_e, total;
+        gfn_n, gfn_m, gfn_e, gfn_wtc, total;
 };
 
 int check_config(const pimd_config* cfg, std::string& e)
@@ -129,9 +135,11 @@ int check_config(const pimd_config* cfg, std::string& e)
         }
     } else if (cfg->potential == PIMD_POT_GFN) {
         if (!(cfg->cutoff_A > 0.0)) { e = "cutoff_A must be > 0"; return PIMD_ERR_INVALID_ARG; }
-        if (cfg->precision != PIMD_FP32) { e = "the GFN head runs in FP32 precision only"; return PIMD_ERR_UNSUPPORTED; }
+        if (cfg->precision == PIMD_FP64) { e = "the GFN head runs in FP32 or BF16 precision"; return PIMD_ERR_UNSUPPORTED; }
         if (cfg->gfn_features != 32 && cfg->gfn_features != 64 && cfg->gfn_features != 128)
             { e = "gfn_features must be 32, 64 or 128"; return PIMD_ERR_UNSUPPORTED; }
+        if (cfg->precision == PIMD_BF16_TC && cfg->gfn_features == 32)
+            { e = "the tensor-core GFN head needs gfn_features 64 or 128"; return PIMD_ERR_UNSUPPORTED; }
         if (cfg->gfn_iterations < 0 || cfg->gfn_iterations > GFN_MAX_ITERS)
             { e = "gfn_iterations must be 0..8"; return PIMD_ERR_INVALID_ARG; }
     } else if (!(cfg->omega_harm >= 0.0)) {
@@ -465,6 +473,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
         o.gfn_n = c.take(sizeof(float) * F * b.B);
         o.gfn_m = c.take(sizeof(float) * F * b.B);
         o.gfn_e = c.take(sizeof(float) * F * (size_t)b.B * mnb);
+        o.gfn_wtc = c.take(gfn && cfg->precision == PIMD_BF16_TC ? gfn_tc_image_bytes(cfg->gfn_features, cfg->gfn_iterations) : 0);
     }
     o.total = c.take(0) + 256;
     return o;
@@ -538,7 +547,8 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
         launch_neighbours(d, st);
         mark(c, PIMD_STAGE_DESCRIPTORS, st, timed);
         mark(c, PIMD_STAGE_NETWORK, st, timed);
-        launch_gfn(d, st);
+        if (d.gfn_wtc) launch_gfn_tc(d, st);
+        else launch_gfn(d, st);
         mark(c, PIMD_STAGE_ADJOINT, st, timed);
     } else {
         launch_neighbours(d, st);
@@ -722,6 +732,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
         d.gfn_n = (float*)(w + o.gfn_n);
         d.gfn_m = (float*)(w + o.gfn_m);
         d.gfn_e = (float*)(w + o.gfn_e);
+        d.gfn_wtc = cfg->precision == PIMD_BF16_TC ? (unsigned char*)(w + o.gfn_wtc) : nullptr;
         d.gfn.F = cfg->gfn_features;
         d.gfn.L = cfg->gfn_iterations;
     }
@@ -1021,6 +1032,35 @@ int pimd_set_gfn(pimd_ctx* c, const pimd_gfn_desc* g)
     gp.eta_R = (float)g->eta_R;
     for (int k = 0; k < NR; ++k) gp.r_mu[k] = (float)g->r_mu[k];
     int rc = upload(c, d.gfn_w, w);
+    if (!rc && d.gfn_wtc) {
+        // BF16 images [out][in] in the K-major core-matrix layout, from the FP32
+        // transposed copies just built
+        std::vector<unsigned short> img(gfn_tc_image_bytes(F, L) / 2);
+        size_t ob = 0;
+        auto put_img = [&](unsigned src, int out, int in) {   // w[src] holds W^T [in][out]
+            const unsigned off = (unsigned)(ob * 2);
+            for (int n2 = 0; n2 < out; ++n2)
+                for (int k = 0; k < in; ++k) {
+                    const float v = w[src + (size_t)k * out + n2];
+                    unsigned u;
+                    std::memcpy(&u, &v, 4);
+                    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even (finite values)
+                    img[ob + cm_index_host(n2, k, in)] = (unsigned short)(u >> 16);
+                }
+            ob += (size_t)out * in;
+            return off;
+        };
+        gp.t_We = put_img(gp.o_We, F, NR);
+        for (int l = 0; l < L; ++l) {
+            gp.t_it[l][0] = put_img(gp.o_it[l][0], F, F);
+            gp.t_it[l][1] = put_img(gp.o_it[l][6], F, F);
+            gp.t_it[l][2] = put_img(gp.o_it[l][8], F, F);
+            gp.t_it[l][3] = put_img(gp.o_it[l][2], F, 2 * F);
+            gp.t_it[l][4] = put_img(gp.o_it[l][4], F, F);
+        }
+        gp.t_Wf1 = put_img(gp.o_Wf1, F, F);
+        rc = upload(c, d.gfn_wtc, img);
+    }
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "GFN parameter upload");
     if (rc) return rc;
     d.gfn = gp;

@@ -122,6 +122,10 @@ struct GfnParams {
     float r_mu[NR];
     unsigned o_emb, o_We, o_be, o_Wf1, o_bf1, o_wf2;
     unsigned o_it[GFN_MAX_ITERS][10];   // W_m^T, b_m, W_v1^T, b_v1, W_v2^T, b_v2, W_a1^T, b_a1, W_a2^T, b_a2
+    // tensor-core path: byte offsets of the BF16 weight images ([out][in],
+    // K-major core-matrix layout) in the image buffer
+    unsigned t_We, t_Wf1;
+    unsigned t_it[GFN_MAX_ITERS][5];    // W_m, W_a1, W_a2, W_v1, W_v2
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

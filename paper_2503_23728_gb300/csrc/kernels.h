@@ -83,6 +83,7 @@ struct Dev {
     float* gfn_n = nullptr;            // [B][F] node representations
     float* gfn_m = nullptr;            // [B][F] messages
     float* gfn_e = nullptr;            // [B][maxnb][F] edge representations
+    unsigned char* gfn_wtc = nullptr;  // BF16 weight images (tensor-core path)
 
     // network
     int n_types = 0, n_hidden = 0, width = 0;
@@ -124,6 +125,8 @@ void launch_network_fp(const Dev& d, cudaStream_t st);
 void launch_network_tc(const Dev& d, cudaStream_t st);
 void launch_adjoint(const Dev& d, const void* dp, cudaStream_t st);
 void launch_gfn(const Dev& d, cudaStream_t st);
+void launch_gfn_tc(const Dev& d, cudaStream_t st);
+size_t gfn_tc_image_bytes(int F, int L);
 int gfn_kernels_per_eval(int L);
 void launch_descriptors_moment(const Dev& d, const void* dp, cudaStream_t st);
 void launch_adjoint_moment(const Dev& d, const void* dp, cudaStream_t st);

@@ -77,7 +77,7 @@ def test_config_errors(lib, bad):
 
 
 @pytest.mark.parametrize("bad, code", [
-    (dict(precision="bf16_tc"), -8), (dict(precision="fp64"), -8), (dict(gfn=(48, 3)), -8),
+    (dict(precision="bf16_tc", gfn=(32, 3)), -8), (dict(precision="fp64"), -8), (dict(gfn=(48, 3)), -8),
     (dict(gfn=(64, 9)), -1), (dict(gfn=(64, -1)), -1), (dict(cutoff=0.0), -1),
 ])
 def test_gfn_config_errors(lib, bad, code):

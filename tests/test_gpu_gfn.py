@@ -4,7 +4,9 @@ inputs and neighbour rule: forces and pair-force virials element by element
 (bar 1e-4 relative max-norm, 1e-5 relative RMS: FP32 products over K <= 256
 terms through L iterations), several feature widths and iteration counts,
 isolated atoms and one-atom replicas, neighbour lists over two 128-slot
-ranges, and dynamics driven by the head."""
+ranges, and dynamics driven by the head. The tensor-core variant (BF16
+operands, FP32 accumulation, F = 64 / 128) is held to 3e-2 relative RMS
+against the oracle on the same cases."""
 import numpy as np
 import pytest
 
@@ -40,8 +42,8 @@ def _with_beads(rep, P):
     return s.Replica(rep.Z, rep.x0, rep.box, P, rep.T, rep.seed, rep.name)
 
 
-def _run(P, reps, model, xs, maxnb=128, dt=0.5):
-    ctx = P.Context(reps, dt, 0.001, precision="fp32", potential=P.POT_GFN, gfn=(model.F, model.L),
+def _run(P, reps, model, xs, maxnb=128, dt=0.5, precision="fp32"):
+    ctx = P.Context(reps, dt, 0.001, precision=precision, potential=P.POT_GFN, gfn=(model.F, model.L),
                     max_neighbours=maxnb)
     ctx.set_gfn(model)
     x = torch.tensor(np.concatenate([q.reshape(-1, 3) for q in xs]), device="cuda")
@@ -147,3 +149,55 @@ def test_dynamics_conserve_momentum_and_errors():
         c2.set_gfn(m)
     assert ei.value.code == -2
     c2.close()
+
+
+@pytest.mark.parametrize("wl, F, L", [("fad", 64, 2), ("water64", 128, 3)])
+def test_tensor_core_head(wl, F, L):
+    P = _P()
+    w = s.workload(wl)
+    rep = _with_beads(w.replicas[0], 3)
+    m = s.gfn_model(s.elements_of([rep]), F, L, seed=31)
+    xb = _beads(rep, 3, seed=12)
+    box = rep.box if rep.box[0] > 0 else None
+    e, f, v = _run(P, [rep], m, [xb], precision="bf16_tc")
+    e32, f32, v32 = _run(P, [rep], m, [xb], precision="fp32")
+    assert np.all(e == 0.0)
+    f = f.reshape(3, rep.n_atoms, 3)
+    f32 = f32.reshape(3, rep.n_atoms, 3)
+    for k in range(3):
+        Fo, Wo = OG.forces(m, rep.Z, xb[k], box)
+        assert _relrms(f[k], Fo) < 3e-2, (k, _relrms(f[k], Fo))
+        assert _relrms(f32[k], Fo) < 1e-5
+        assert _relmax(v[k], Wo) < 5e-2
+        # pair forces stay equal and opposite in BF16
+        assert np.abs(f[k].sum(axis=0)).max() < 1e-4 * np.abs(Fo).max() * rep.n_atoms
+
+
+def test_tensor_core_head_ragged_lists():
+    """BF16 head on lists longer than 128 slots (two tiles per atom), gas-phase
+    clusters with an isolated atom (no tile) and a one-atom replica."""
+    P = _P()
+    dense = s.water_box(5, spacing=2.5, seed=516, n_beads=2)
+    cl = s.batch(n_rep=3, seed=94, beads=(2, 3))
+    r0 = cl[0]
+    x0 = r0.x0.copy()
+    x0[0] += np.array([40.0, 0.0, 0.0])
+    cl[0] = s.Replica(r0.Z, x0, r0.box, r0.n_beads, r0.T, r0.seed)
+    reps = [dense] + cl + [s.Replica(np.array([8], dtype=np.int32), np.zeros((1, 3)), (0.0, 0.0, 0.0), 2, 300.0, 5)]
+    m = s.gfn_model(s.elements_of(reps), 64, 2, seed=18)
+    xs = [_beads(r, r.n_beads, seed=60 + k) for k, r in enumerate(reps)]
+    e, f, v = _run(P, reps, m, xs, maxnb=256, precision="bf16_tc")
+    b0 = 0
+    for k, (r, x) in enumerate(zip(reps, xs)):
+        n = r.n_atoms * r.n_beads
+        fg = f[b0:b0 + n].reshape(r.n_beads, r.n_atoms, 3)
+        for q in range(r.n_beads):
+            Fo, _ = OG.forces(m, r.Z, x[q], r.box if r.box[0] > 0 else None, maxnb=256)
+            if np.abs(Fo).max() > 0:
+                assert _relrms(fg[q], Fo) < 3e-2, (k, q, _relrms(fg[q], Fo))
+            else:
+                assert np.abs(fg[q]).max() == 0.0
+        b0 += n
+    n0 = dense.n_atoms * dense.n_beads
+    assert np.abs(f[n0:n0 + cl[0].n_atoms * cl[0].n_beads].reshape(cl[0].n_beads, -1, 3)[:, 0]).max() == 0.0
+    assert np.abs(f[-2:]).max() == 0.0
