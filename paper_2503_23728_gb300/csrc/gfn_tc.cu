@@ -227,20 +227,26 @@ __global__ void __launch_bounds__(TR, 2) gfn_tc_init_kernel(
 }
 
 // iteration l on the rows of one bead-atom: m_i = sum_rows SiLU(W_m e + b_m);
-// e += W_a2 SiLU(W_a1 (n_i + n_j) + b_a1) + b_a2
+// e += W_a2 SiLU(W_a1 (n_i + n_j) + b_a1) + b_a2. One A buffer (e, then
+// n_i + n_j, then the hidden layer), so three CTAs share an SM; rows are
+// staged and the residual is added by whole warps on contiguous rows.
 template <int F>
-__global__ void __launch_bounds__(TR, 2) gfn_tc_iter_kernel(
+__global__ void __launch_bounds__(TR, 3) gfn_tc_iter_kernel(
     const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys, const int* __restrict__ nbr,
     const int* __restrict__ nnb, int maxnb, GfnParams gp, int l, const float* __restrict__ W,
     const unsigned char* __restrict__ Wtc, const float* __restrict__ nf, float* __restrict__ mf,
     float* __restrict__ ef, DevErr* __restrict__ err)
 {
+    constexpr int CPR = F / 8;                   // 16-byte BF16 chunks per row
+    constexpr int HC = F / 4;                    // columns of the FP32 staging of D per pass
+    constexpr int HCS = HC + 4;                  // its row stride (floats): 16-byte stores conflict-free
+    static_assert(TR * HCS * 4 <= TR * F * 2, "the FP32 staging of D fits the A buffer");
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* A1 = sm;                      // [TR][F] BF16: e, later SiLU(W_a1 (n_i + n_j) + b_a1)
-    unsigned char* A2 = A1 + TR * F * 2;         // [TR][F] BF16: n_i + n_j
-    unsigned char* WB = A2 + TR * F * 2;         // [F][F] BF16
+    unsigned char* A = sm;                       // [TR][F] BF16; also [TR][HCS] FP32
+    unsigned char* WB = A + TR * F * 2;          // [F][F] BF16
     float* msum = reinterpret_cast<float*>(WB + F * F * 2);   // [4][F]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(msum + 4 * F);
+    int* jrow = reinterpret_cast<int*>(msum + 4 * F);          // [TR] neighbour of each row, -1 beyond the list
+    uint64_t* bars = reinterpret_cast<uint64_t*>(jrow + TR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
     Tc t;
     tc_begin(t, bars, tslot, tcols<F>());
@@ -251,48 +257,59 @@ __global__ void __launch_bounds__(TR, 2) gfn_tc_iter_kernel(
     const unsigned* o = gp.o_it[l];
     const uint32_t wbytes = (uint32_t)(F * F * 2);
     float* eb = ef + (size_t)b * maxnb * F;
+    const float* ni = nf + (size_t)b * F;
     for (int c = row; c < 4 * F; c += TR) msum[c] = 0.0f;
     for (int t0 = 0; t0 < n && t.ok; t0 += TR) {
         tc_load_w(t, WB, Wtc + gp.t_it[l][0], wbytes);
         const int s = t0 + row;
         const bool act = s < n;
-        const int j = act ? nbr[(size_t)b * maxnb + s] : 0;
-        const float* er = eb + (size_t)s * F;
-        const float* ni = nf + (size_t)b * F;
-        const float* nj = nf + (size_t)(sy.ba0 + j) * F;
-        for (int k0 = 0; k0 < F; k0 += 8) {
-            float v[8], u[8];
-            if (act) {
-                const float4 e0 = reinterpret_cast<const float4*>(er + k0)[0];
-                const float4 e1 = reinterpret_cast<const float4*>(er + k0)[1];
-                const float4 a0 = reinterpret_cast<const float4*>(ni + k0)[0];
-                const float4 a1 = reinterpret_cast<const float4*>(ni + k0)[1];
-                const float4 c0 = reinterpret_cast<const float4*>(nj + k0)[0];
-                const float4 c1 = reinterpret_cast<const float4*>(nj + k0)[1];
-                v[0] = e0.x; v[1] = e0.y; v[2] = e0.z; v[3] = e0.w; v[4] = e1.x; v[5] = e1.y; v[6] = e1.z; v[7] = e1.w;
-                u[0] = a0.x + c0.x; u[1] = a0.y + c0.y; u[2] = a0.z + c0.z; u[3] = a0.w + c0.w;
-                u[4] = a1.x + c1.x; u[5] = a1.y + c1.y; u[6] = a1.z + c1.z; u[7] = a1.w + c1.w;
+        jrow[row] = act ? nbr[(size_t)b * maxnb + s] : -1;
+        __syncthreads();
+        // A = e rows (a warp stages its 32 rows, consecutive lanes on consecutive chunks)
+        for (int q = (int)lane; q < 32 * CPR; q += 32) {
+            const int r = 32 * warp + q / CPR, k0 = 8 * (q % CPR);
+            float v[8];
+            if (jrow[r] >= 0) {
+                const float4* src = reinterpret_cast<const float4*>(eb + (size_t)(t0 + r) * F + k0);
+                const float4 p0 = src[0], p1 = src[1];
+                v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w; v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
             } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = u[q] = 0.0f;
+                for (int u = 0; u < 8; ++u) v[u] = 0.0f;
             }
-            put8(A1, row, k0, F, v);
-            put8(A2, row, k0, F, u);
+            put8(A, r, k0, F, v);
         }
         // messages
-        tc_gemm(t, A1, WB, F, F);
+        tc_gemm(t, A, WB, F, F);
         if (!t.ok) break;
         tc_load_w(t, WB, Wtc + gp.t_it[l][1], wbytes);
         for (int c0 = 0; c0 < F; c0 += 16) {
             float v[16];
             tmem_ld16(lane_base(t) + (uint32_t)c0, v);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = act ? silu_f(v[q] + W[o[1] + c0 + q]) : 0.0f;
+            for (int u = 0; u < 16; ++u) v[u] = act ? silu_f(v[u] + W[o[1] + c0 + u]) : 0.0f;
             const float tot = tr_reduce16(v, lane);
             if (lane < 16) msum[warp * F + c0 + lane] += tot;
         }
+        // A = n_i + n_j (the message MMA has read A)
+        for (int q = (int)lane; q < 32 * CPR; q += 32) {
+            const int r = 32 * warp + q / CPR, k0 = 8 * (q % CPR);
+            const int j = jrow[r];
+            float v[8];
+            if (j >= 0) {
+                const float4* a = reinterpret_cast<const float4*>(ni + k0);
+                const float4* c = reinterpret_cast<const float4*>(nf + (size_t)(sy.ba0 + j) * F + k0);
+                const float4 a0 = a[0], a1 = a[1], c0 = c[0], c1 = c[1];
+                v[0] = a0.x + c0.x; v[1] = a0.y + c0.y; v[2] = a0.z + c0.z; v[3] = a0.w + c0.w;
+                v[4] = a1.x + c1.x; v[5] = a1.y + c1.y; v[6] = a1.z + c1.z; v[7] = a1.w + c1.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = 0.0f;
+            }
+            put8(A, r, k0, F, v);
+        }
         // edge update, first layer
-        tc_gemm(t, A2, WB, F, F);
+        tc_gemm(t, A, WB, F, F);
         if (!t.ok) break;
         tc_load_w(t, WB, Wtc + gp.t_it[l][2], wbytes);
         for (int c0 = 0; c0 < F; c0 += 16) {
@@ -302,26 +319,35 @@ __global__ void __launch_bounds__(TR, 2) gfn_tc_iter_kernel(
             for (int h = 0; h < 2; ++h) {
                 float w8[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) w8[q] = silu_f(v[8 * h + q] + W[o[7] + c0 + 8 * h + q]);
-                put8(A1, row, c0 + 8 * h, F, w8);
+                for (int u = 0; u < 8; ++u) w8[u] = silu_f(v[8 * h + u] + W[o[7] + c0 + 8 * h + u]);
+                put8(A, row, c0 + 8 * h, F, w8);
             }
         }
-        // edge update, second layer: e += W_a2 h + b_a2
-        tc_gemm(t, A1, WB, F, F);
+        // edge update, second layer: e += W_a2 h + b_a2, through an FP32 staging
+        // of HC columns at a time so that whole warps update contiguous rows
+        tc_gemm(t, A, WB, F, F);
         if (!t.ok) break;
-        for (int c0 = 0; c0 < F; c0 += 16) {
-            float v[16];
-            tmem_ld16(lane_base(t) + (uint32_t)c0, v);
-            if (act) {
-                float4* dst = reinterpret_cast<float4*>(eb + (size_t)s * F + c0);
-                const float4* bb = reinterpret_cast<const float4*>(W + o[9] + c0);
+        float* D = reinterpret_cast<float*>(A);   // [TR][HCS], the hidden layer has been read
+        for (int h0 = 0; h0 < F; h0 += HC) {
+            for (int c0 = h0; c0 < h0 + HC; c0 += 16) {
+                float v[16];
+                tmem_ld16(lane_base(t) + (uint32_t)c0, v);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 cur = dst[q], bv = bb[q];
-                    dst[q] = make_float4(cur.x + v[4 * q] + bv.x, cur.y + v[4 * q + 1] + bv.y,
-                                         cur.z + v[4 * q + 2] + bv.z, cur.w + v[4 * q + 3] + bv.w);
+                for (int u = 0; u < 16; u += 4)
+                    *reinterpret_cast<float4*>(D + row * HCS + (c0 - h0) + u) =
+                        make_float4(v[u] + W[o[9] + c0 + u], v[u + 1] + W[o[9] + c0 + u + 1],
+                                    v[u + 2] + W[o[9] + c0 + u + 2], v[u + 3] + W[o[9] + c0 + u + 3]);
+            }
+            __syncthreads();
+            for (int q = (int)lane; q < 32 * HC / 4; q += 32) {
+                const int r = 32 * warp + q / (HC / 4), c4 = q % (HC / 4);
+                if (jrow[r] >= 0) {
+                    float4* dst = reinterpret_cast<float4*>(eb + (size_t)(t0 + r) * F + h0) + c4;
+                    const float4 cur = *dst, add = reinterpret_cast<const float4*>(D + r * HCS)[c4];
+                    *dst = make_float4(cur.x + add.x, cur.y + add.y, cur.z + add.z, cur.w + add.w);
                 }
             }
+            __syncthreads();
         }
     }
     __syncthreads();
@@ -425,17 +451,19 @@ __global__ void __launch_bounds__(TR, 2) gfn_tc_force_kernel(
         tc_load_w(t, WB, Wtc + gp.t_Wf1, (uint32_t)(F * F * 2));
         const int s = t0 + row;
         const bool act = s < n;
-        for (int k0 = 0; k0 < F; k0 += 8) {
+        // a warp stages its 32 rows, consecutive lanes on consecutive chunks
+        for (int q = (int)lane; q < 32 * (F / 8); q += 32) {
+            const int r = 32 * warp + q / (F / 8), k0 = 8 * (q % (F / 8));
             float v[8];
-            if (act) {
-                const float4 p0 = reinterpret_cast<const float4*>(eb + (size_t)s * F + k0)[0];
-                const float4 p1 = reinterpret_cast<const float4*>(eb + (size_t)s * F + k0)[1];
+            if (t0 + r < n) {
+                const float4 p0 = reinterpret_cast<const float4*>(eb + (size_t)(t0 + r) * F + k0)[0];
+                const float4 p1 = reinterpret_cast<const float4*>(eb + (size_t)(t0 + r) * F + k0)[1];
                 v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w; v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
             } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+                for (int u = 0; u < 8; ++u) v[u] = 0.0f;
             }
-            put8(A, row, k0, F, v);
+            put8(A, r, k0, F, v);
         }
         tc_gemm(t, A, WB, F, F);
         if (!t.ok) break;
@@ -483,7 +511,7 @@ namespace {
 template <int F>
 size_t init_smem() { return 48 * 1024; }
 template <int F>
-size_t iter_smem() { return (size_t)2 * TR * F * 2 + (size_t)F * F * 2 + 4 * F * 4 + 64; }
+size_t iter_smem() { return (size_t)TR * F * 2 + (size_t)F * F * 2 + 4 * F * 4 + TR * 4 + 64; }
 template <int F>
 size_t node_smem() { return (size_t)TR * 2 * F * 2 + (size_t)F * 2 * F * 2 + 64; }
 template <int F>
