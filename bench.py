@@ -429,7 +429,8 @@ def config_of(w, precision, world):
             "precision": {"network": {"bf16_tc": "bf16 tcgen05, fp32 accumulate", "fp32": "fp32",
                                       "fp64": "fp64"}[precision],
                           "descriptors_adjoint": "fp64" if precision == "fp64" else "fp32",
-                          "ring_polymer_estimators": "fp64"}}
+                          "ring_polymer_estimators": "fp64" if precision == "fp64" else
+                          "fp64 state and estimators; fp32 deviates and normal-mode sums of the fluctuation modes"}}
 
 
 def main():

@@ -96,7 +96,7 @@ struct Carve {
 };
 
 struct Offsets {
-    size_t reps, bsys, ba_sys, mass, minv, atype, x0, cmat, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
+    size_t reps, bsys, ba_sys, mass, minv, atype, x0, cmat, cmatf, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
         fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
         md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, gfn_w,
@@ -412,6 +412,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.atype = c.take(sizeof(int) * b.NA);
     o.x0 = c.take(sizeof(double) * 3 * (size_t)b.NA);
     o.cmat = c.take(sizeof(double) * b.cmat.size());
+    o.cmatf = c.take(sizeof(float) * b.cmat.size());
     o.modes = c.take(sizeof(Mode) * b.modes.size());
     o.rp_blocks = c.take(sizeof(int2) * b.rp_blocks.size());
     o.x = c.take(v4 * b.B);
@@ -699,6 +700,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.atype = (int*)(w + o.atype);
     d.x0 = (double*)(w + o.x0);
     d.cmat = (double*)(w + o.cmat);
+    d.cmatf = (float*)(w + o.cmatf);
     d.modes = (Mode*)(w + o.modes);
     d.rp_blocks = (int2*)(w + o.rp_blocks);
     d.n_rp_blocks = (int)b.rp_blocks.size();
@@ -814,6 +816,8 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     if (!rc) rc = upload(c, d.atype, b.atype);
     if (!rc) rc = upload(c, d.x0, b.x0);
     if (!rc) rc = upload(c, d.cmat, b.cmat);
+    const std::vector<float> cmatf(b.cmat.begin(), b.cmat.end());
+    if (!rc) rc = upload(c, d.cmatf, cmatf);
     if (!rc) rc = upload(c, d.modes, b.modes);
     if (!rc) rc = upload(c, d.rp_blocks, b.rp_blocks);
     if (!rc) rc = upload(c, d.rep_blk0, b.rep_blk0);

@@ -27,6 +27,7 @@ struct Dev {
     int* atype = nullptr;              // [NA] element type index
     double* x0 = nullptr;              // [NA][3]
     double* cmat = nullptr;            // normal-mode matrices
+    float* cmatf = nullptr;            // the same in FP32 (FP32 paths)
     Mode* modes = nullptr;             // [sum P]
     int2* rp_blocks = nullptr;         // (replica, first entry) per ring-polymer block
     int n_rp_blocks = 0;

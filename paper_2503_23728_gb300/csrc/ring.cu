@@ -7,6 +7,8 @@
 // is a shared-memory matrix-vector product spread over T * P threads.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -39,6 +41,49 @@ __device__ __forceinline__ double normal_dev(unsigned long long seed, unsigned i
     const double u1 = ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6) + 1.0) * (1.0 / 9007199254740992.0);
     const double u2 = ((double)(w.z >> 5) * 67108864.0 + (double)(w.w >> 6) + 1.0) * (1.0 / 9007199254740992.0);
     return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// FP32 paths: the same deviate from the same counter with FP32 arithmetic.
+// The first uniform is the 53-bit one rounded to FP32 (not truncated, so the
+// log keeps its relative accuracy down to u1 ~ 2^-29); log, cos and sqrt
+// in FP32 (deviates within ~1e-7 relative of the FP64 ones). FP64 runs at a
+// small fraction of the FP32 rate on this GPU, and the FP32 force path's own
+// rounding is larger than this.
+__device__ __forceinline__ float normal_dev_f(unsigned long long seed, unsigned idx, unsigned step, unsigned rep,
+                                              unsigned stream)
+{
+    const uint4 w = philox10(make_uint4(idx, step, rep, stream), make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+    const float u1 = fmaf(__uint2float_rn(w.x >> 5), 7.450580596923828125e-9f,              // 2^-27
+                          __uint2float_rn((w.y >> 6) + 1u) * 1.1102230246251565e-16f);   // 2^-53
+    const float u2 = fmaf(__uint2float_rn(w.z >> 5), 7.450580596923828125e-9f,
+                          __uint2float_rn((w.w >> 6) + 1u) * 1.1102230246251565e-16f);
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+template <typename Real>
+__device__ __forceinline__ double normal_of(unsigned long long seed, unsigned idx, unsigned step, unsigned rep,
+                                            unsigned stream)
+{
+    if constexpr (std::is_same<Real, float>::value) return (double)normal_dev_f(seed, idx, step, rep, stream);
+    return normal_dev(seed, idx, step, rep, stream);
+}
+
+// bead coordinate j from the ring-polymer coordinates of one (atom, dim):
+// FP64 paths sum all P terms in FP64; FP32 paths keep the mode-0 term (the
+// absolute position) in FP64 and sum the other modes, deviations of tenths of
+// an Angstrom, in FP32 (rounding far below one FP32 ulp of the position)
+template <typename Real>
+__device__ __forceinline__ double to_bead(const double* __restrict__ C, const float* __restrict__ Cf,
+                                          const double* sq, const float* sqf, int P)
+{
+    if constexpr (std::is_same<Real, float>::value) {
+        float a = 0.0f;
+        for (int k = 1; k < P; ++k) a = fmaf(Cf[k], sqf[k], a);
+        return fma(C[0], sq[0], (double)a);
+    }
+    double acc = 0.0;
+    for (int k = 0; k < P; ++k) acc += C[k] * sq[k];
+    return acc;
 }
 
 template <typename Real>
@@ -106,20 +151,24 @@ __device__ __forceinline__ RpThread rp_thread(const int2* __restrict__ blocks, c
 // normal-mode -> bead positions for all beads (no dynamics)
 template <typename Real>
 __global__ void beads_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
-                             const double* __restrict__ cmat, const double* __restrict__ q,
-                             Vec4<Real>* __restrict__ x)
+                             const double* __restrict__ cmat, const float* __restrict__ cmatf,
+                             const double* __restrict__ q, Vec4<Real>* __restrict__ x)
 {
     extern __shared__ double sq[];
+    float* sqf = reinterpret_cast<float*>(sq + blockDim.x);
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
     const int le = threadIdx.x / t.P;
-    if (t.active) sq[le * t.P + t.kk] = q[3 * ((size_t)rp.ba0 + (size_t)t.kk * t.N + t.i) + t.dd];
+    if (t.active) {
+        const double qv = q[3 * ((size_t)rp.ba0 + (size_t)t.kk * t.N + t.i) + t.dd];
+        sq[le * t.P + t.kk] = qv;
+        sqf[le * t.P + t.kk] = (float)qv;
+    }
     __syncthreads();
     if (!t.active) return;
     const int j = t.kk;
-    const double* C = cmat + rp.cmat + (size_t)j * t.P;
-    double acc = 0.0;
-    for (int k = 0; k < t.P; ++k) acc += C[k] * sq[le * t.P + k];
+    const double acc = to_bead<Real>(cmat + rp.cmat + (size_t)j * t.P, cmatf + rp.cmat + (size_t)j * t.P,
+                                     sq + le * t.P, sqf + le * t.P, t.P);
     comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
 }
 
@@ -141,10 +190,11 @@ __device__ __forceinline__ void free_rp(int k, const Mode& md, double m, double 
 
 // PILE-L O sub-step with the host's (c1, c2) for its duration; returns the
 // kinetic-energy change (smkT = sqrt(m k_B T_P) of the coordinate, im = 1/m)
+template <typename Real>
 __device__ __forceinline__ double pile_o(const Rep& rp, const Mode& md, double smkT, double im, unsigned local,
                                          unsigned step, unsigned rep, unsigned stream, double& pv)
 {
-    const double xi = normal_dev(rp.seed, local, step, rep, stream);
+    const double xi = normal_of<Real>(rp.seed, local, step, rep, stream);
     const double pn = md.c1 * pv + smkT * md.c2 * xi;
     const double dK = (pn * pn - pv * pv) * 0.5 * im;
     pv = pn;
@@ -155,13 +205,15 @@ __device__ __forceinline__ double pile_o(const Rep& rp, const Mode& md, double s
 // mode, then the new bead positions
 template <typename Real>
 __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
-                                const double* __restrict__ cmat, const Mode* __restrict__ modes,
+                                const double* __restrict__ cmat, const float* __restrict__ cmatf,
+                                const Mode* __restrict__ modes,
                                 const double* __restrict__ mass, const double2* __restrict__ minv,
                                 const unsigned long long* __restrict__ stepp, double dt, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
                                 const double* __restrict__ fnm, Vec4<Real>* __restrict__ x,
                                 double* __restrict__ qpart)
 {
     extern __shared__ double sq[];
+    float* sqf = reinterpret_cast<float*>(sq + blockDim.x);
     __shared__ double red[32];
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
@@ -179,16 +231,17 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
         if (baoab) {
             pv += kick * fnm[g];
             free_rp(k, md, m, im, 0.5 * dt, pv, qv);
-            if (thermostat) dK = pile_o(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
+            if (thermostat) dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
             free_rp(k, md, m, im, 0.5 * dt, pv, qv);
         } else {
-            if (thermostat) dK = pile_o(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
+            if (thermostat) dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
             pv += kick * fnm[g];
             free_rp(k, md, m, im, dt, pv, qv);
         }
         p[g] = pv;
         q[g] = qv;
         sq[le * t.P + k] = qv;
+        sqf[le * t.P + k] = (float)qv;
     }
     // thermostat heat: block partial, summed per replica in block order later
     dK = warp_sum(dK);
@@ -201,36 +254,47 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
     }
     if (!t.active) return;
     const int j = t.kk;
-    const double* C = cmat + rp.cmat + (size_t)j * t.P;
-    double acc = 0.0;
-    for (int k = 0; k < t.P; ++k) acc += C[k] * sq[le * t.P + k];
+    const double acc = to_bead<Real>(cmat + rp.cmat + (size_t)j * t.P, cmatf + rp.cmat + (size_t)j * t.P,
+                                     sq + le * t.P, sqf + le * t.P, t.P);
     comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
 }
 
 // f_nm = C^T f; if do_step: B(dt/2), then O(dt/2) for OBABO
 template <typename Real>
 __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
-                                 const double* __restrict__ cmat, const Mode* __restrict__ modes,
+                                 const double* __restrict__ cmat, const float* __restrict__ cmatf,
+                                 const Mode* __restrict__ modes,
                                  const double* __restrict__ mass, const double2* __restrict__ minv,
                                  const unsigned long long* __restrict__ stepp, double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
                                  double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ qpart,
                                  DevErr* __restrict__ err)
 {
     extern __shared__ double sf[];
+    float* sff = reinterpret_cast<float*>(sf + blockDim.x);
     __shared__ double red[32];
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
     const int le = threadIdx.x / t.P;
     if (t.active) {
         Vec4<Real> fv = f[rp.ba0 + (size_t)t.kk * t.N + t.i];
-        sf[le * t.P + t.kk] = (double)comp<Real>(fv, t.dd);
+        if constexpr (std::is_same<Real, float>::value)
+            sff[le * t.P + t.kk] = comp<Real>(fv, t.dd);
+        else
+            sf[le * t.P + t.kk] = (double)comp<Real>(fv, t.dd);
     }
     __syncthreads();
     double dK = 0.0;
     if (t.active) {
         const int k = t.kk;
         double fn = 0.0;
-        for (int j = 0; j < t.P; ++j) fn += cmat[rp.cmat + (size_t)j * t.P + k] * sf[le * t.P + j];
+        if constexpr (std::is_same<Real, float>::value) {
+            // FP32 forces: their normal-mode components summed in FP32
+            float a = 0.0f;
+            for (int j = 0; j < t.P; ++j) a = fmaf(cmatf[rp.cmat + (size_t)j * t.P + k], sff[le * t.P + j], a);
+            fn = (double)a;
+        } else {
+            for (int j = 0; j < t.P; ++j) fn += cmat[rp.cmat + (size_t)j * t.P + k] * sf[le * t.P + j];
+        }
         const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
         fnm[g] = fn;
         if (!isfinite(fn)) atomicOr(&err->flags, ERR_NONFINITE);
@@ -240,7 +304,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
             double pv = p[g] + 0.5 * dt * INV_MVV2E * fn;
             if (thermostat) {
                 const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
-                dK = pile_o(rp, md, mi.y * md.smf, mi.x * md.imf, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
+                dK = pile_o<Real>(rp, md, mi.y * md.smf, mi.x * md.imf, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
             }
             p[g] = pv;
         }
@@ -275,15 +339,15 @@ __global__ void bump_step_kernel(unsigned long long* step, double* __restrict__ 
     }
 }
 
-static size_t rp_smem(const Dev& d) { return (size_t)d.rp_threads * sizeof(double); }
+static size_t rp_smem(const Dev& d) { return (size_t)d.rp_threads * (sizeof(double) + sizeof(float)); }
 
 void launch_beads(const Dev& d, cudaStream_t st)
 {
     if (d.precision == 0)
-        beads_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(d.rp_blocks, d.reps, d.cmat, d.q,
+        beads_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(d.rp_blocks, d.reps, d.cmat, d.cmatf, d.q,
                                                                                 (Dbl4*)d.x);
     else
-        beads_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(d.rp_blocks, d.reps, d.cmat, d.q,
+        beads_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(d.rp_blocks, d.reps, d.cmat, d.cmatf, d.q,
                                                                                (float4*)d.x);
 }
 
@@ -291,11 +355,11 @@ void launch_rp_start(const Dev& d, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
             (Dbl4*)d.x, d.qpart);
     else
         rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
             (float4*)d.x, d.qpart);
 }
 
@@ -303,11 +367,11 @@ void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err);
     else
         rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err);
 }
 
