@@ -363,7 +363,7 @@ constexpr int FWDR_WARPS = 4;
 static_assert(32 * NRED >= 4 * NMONO, "moment table reuses the monomial rows");
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * FWDR_WARPS, 2) desc_mom_fwd_red_kernel(
+__global__ void __launch_bounds__(32 * FWDR_WARPS, 5) desc_mom_fwd_red_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout)
@@ -520,11 +520,11 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 2) desc_mom_fwd_red_kernel(
 // nested Horner recurrences (x innermost, then y, then z) with broadcast
 // loads of Q.
 // ---------------------------------------------------------------------------
-constexpr int ADJ_WARP_BYTES = NMONO * 16 + ND * 4;
+constexpr int ADJ_WARP_BYTES = NMONO * 16 + ND * 4 + NR * 4;   // Q, dE/dG, radial dE/dG x r_mu
 constexpr int ADJ_WARPS = 4;
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * ADJ_WARPS, 4) desc_mom_adj_kernel(
+__global__ void __launch_bounds__(32 * ADJ_WARPS, FAST ? 5 : 4) desc_mom_adj_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
@@ -543,6 +543,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS, 4) desc_mom_adj_kernel(
     const float4 xi = x[b];
     gs[lane] = dEdG[(size_t)b * ND + lane];
     gs[NR + lane] = dEdG[(size_t)b * ND + NR + lane];
+    gs[ND + lane] = gs[lane] * dp.r_mu[lane];
     __syncwarp();
 
     // D(zeta,+,eta) +- D(zeta,-,eta) and sum_zeta D(zeta,+,eta)
@@ -618,13 +619,17 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS, 4) desc_mom_adj_kernel(
         cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
         float dEdr = 0.0f;
         if (FAST && dp.r_even) {
+            // sum_c gs_c g_c (-2 eta_R (r - r_mu_c) fc + dfc)
+            //   = (-2 eta_R r fc + dfc) sum_c gs_c g_c + 2 eta_R fc sum_c gs_c r_mu_c g_c
             float g[NR];
             radial_gauss32(dp, r, g);
+            float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
-                const float t = r - dp.r_mu[c];
-                dEdr += gs[c] * g[c] * (-2.0f * dp.eta_R * t * fc + dfc);
+                s1 = fmaf(gs[c], g[c], s1);
+                s2 = fmaf(gs[ND + c], g[c], s2);
             }
+            dEdr = s1 * (-2.0f * dp.eta_R * r * fc + dfc) + 2.0f * dp.eta_R * fc * s2;
         } else {
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
