@@ -343,6 +343,10 @@ def gfn_extras(w, stream, steps=5):
     F, L = 128, 3
     m = s.gfn_model(s.elements_of(w.replicas), F, L, seed=7)
     out = {"features": F, "iterations": L}
+    try:
+        bf16_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops")
+    except Exception:
+        bf16_peak = None
     for prec in ("fp32", "bf16_tc"):
         ctx = P.Context(w.replicas, w.dt_fs, w.gamma0_per_fs, precision=prec, potential=P.POT_GFN, gfn=(F, L),
                         timing=True)
@@ -355,10 +359,13 @@ def gfn_extras(w, stream, steps=5):
         st = {k: float(np.median([a[k] for a in acc])) for k in acc[0]}
         nnb, _ = ctx.neighbours()
         mac = gfn_mac(F, L, float(nnb.sum()), ctx.B)
-        out[prec] = {"ms_per_step": float(sum(st.values())), "head_ms": st["network"],
-                     "head_tflops": 2 * mac / (st["network"] / 1e3) / 1e12,
-                     "frac_fp32_peak": 2 * mac / (st["network"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+        tf = 2 * mac / (st["network"] / 1e3) / 1e12
+        out[prec] = {"ms_per_step": float(sum(st.values())), "head_ms": st["network"], "head_tflops": tf,
                      "bead_atom_evals_per_s": ctx.B / (sum(st.values()) / 1e3)}
+        if prec == "fp32":
+            out[prec]["frac_fp32_peak"] = tf / FP32_PEAK_TFLOPS
+        else:
+            out[prec]["frac_bf16_peak_measured"] = tf / bf16_peak if bf16_peak else None
         ctx.close()
     return out
 
