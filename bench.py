@@ -43,15 +43,19 @@ ADJ_FLOP_PER_NBR = 380
 MOM_ADJ_FLOP_PER_NBR = 380 + 2 * 1340
 MOM_ADJ_FLOP_PER_ATOM = 165 * 36
 # BF16 network path, reduced basis (the 81 monomials with x-degree <= 1):
-# 668 FMA per neighbour (144 in x, 400 in y, 124 in z); per bead-atom also
-# the fold of dE/dM onto the 81 (161 targets x up to 3 adds x 4 widths)
-MOM_RED_ADJ_FLOP_PER_NBR = 380 + 2 * 668
-MOM_RED_ADJ_FLOP_PER_ATOM = 165 * 36 + 161 * 3 * 4
+# the 4 polynomials and their gradient by Horner in y within each z-level,
+# the x-degree-1 term folded in first, then Horner in z: 628 FMA per
+# neighbour (256 + 58 FP32x2 pairs; no multiply-add spent on a chain's zero
+# starting value); per bead-atom
+# Q = M Phi(s) 2 / (a! b! c!) (165 x 4 x 2 mul), Phi (36 x 4 FMA) and the
+# fold onto the 81 (483 terms x 4 widths FMA)
+MOM_RED_ADJ_FLOP_PER_NBR = 380 + 2 * 628
+MOM_RED_ADJ_FLOP_PER_ATOM = 165 * 4 * 2 + 36 * 4 * 2 + 483 * 4 * 2
 # DRAM bytes (read + write) of one adjoint launch from an ncu capture of the
 # same kernel on the same workload (ice Ih, P = 32, BF16 network, reduced
-# moment basis): 139.7 MB read (mostly the 3 KB of moments per bead-atom)
-# + 3.9 MB written. Reported only for that configuration.
-ADJ_TRAFFIC_NCU = {("ice", "bf16_tc", "moments"): 139.745e6 + 3.857e6}
+# moment basis). Reported only for that configuration; empty until the
+# current kernel has been captured.
+ADJ_TRAFFIC_NCU = {}
 
 
 def args():
@@ -187,6 +191,12 @@ def timed_steps(a, ctx, stream, flush, barrier):
     barrier()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     return ms, stages
+
+
+def adjoint_kernel_name(ctx) -> str:
+    if ctx.angular == "moments":
+        return "desc_mom_adj_fast_kernel" if ctx.precision == "bf16_tc" else "desc_mom_adj_kernel"
+    return "desc_adj_kernel"
 
 
 def adjoint_flops(ctx) -> float:
@@ -508,8 +518,7 @@ def main():
         "fp32_plain": fp32,
         "speedup_vs_fp32_plain": (value / fp32["value"]) if fp32 else None,
         "angular": ctx.angular,
-        "roofline": {"bound": "alu", "kernel": ("desc_mom_adj_kernel" if ctx.angular == "moments" else
-                                                "desc_adj_kernel") + " (angular+radial adjoint, forces, virial)",
+        "roofline": {"bound": "alu", "kernel": adjoint_kernel_name(ctx) + " (angular+radial adjoint, forces, virial)",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": ADJ_TRAFFIC_NCU.get((w.name, a.precision, ctx.angular)),

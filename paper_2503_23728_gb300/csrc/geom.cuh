@@ -133,6 +133,45 @@ __device__ __forceinline__ void pair_vec(const Rep& rp, const V4& xi, const V4& 
     }
 }
 
+// FP32 box of a replica in registers (invL = 0 for free clusters: no shift)
+struct Box {
+    float L[3], invL[3];
+};
+__device__ __forceinline__ Box box_of(const Rep& rp)
+{
+    Box b;
+    for (int a = 0; a < 3; ++a) {
+        b.L[a] = rp.Lf[a];
+        b.invL[a] = rp.periodic ? rp.invLf[a] : 0.0f;
+    }
+    return b;
+}
+
+// BF16-path geometry of one neighbour (the path's bar is 1e-2 on the forces):
+// minimum-image pair vector with one rounding per component, the distance
+// and its inverse from the reciprocal square root, and the cutoff and its
+// slope from the special-function sine and cosine of pi r / r_c (absolute
+// error ~1e-6). The exact FP32 path keeps the error-free forms above.
+__device__ __forceinline__ void geo_fast(const Box& bx, const float4& xi, const float4& xj, float rc,
+                                         float pi_over_rc, float& dx, float& dy, float& dz, float& r, float& ir,
+                                         float& fc, float& dfc)
+{
+    dx = xj.x - xi.x;
+    dy = xj.y - xi.y;
+    dz = xj.z - xi.z;
+    dx = fmaf(-rintf(dx * bx.invL[0]), bx.L[0], dx);
+    dy = fmaf(-rintf(dy * bx.invL[1]), bx.L[1], dy);
+    dz = fmaf(-rintf(dz * bx.invL[2]), bx.L[2], dz);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    ir = rsqrtf(r2);
+    r = r2 * ir;
+    float s, c;
+    __sincosf(r * pi_over_rc, &s, &c);
+    const bool in = r < rc;
+    fc = in ? fmaf(0.5f, c, 0.5f) : 0.0f;
+    dfc = in ? -0.5f * pi_over_rc * s : 0.0f;
+}
+
 __device__ __forceinline__ float3 as_f32(const float4& v) { return make_float3(v.x, v.y, v.z); }
 __device__ __forceinline__ float3 as_f32(const Dbl4& v)
 {

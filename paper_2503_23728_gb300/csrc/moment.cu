@@ -75,13 +75,13 @@ constexpr MonoTab make_mono_tab()
 
 __device__ const MonoTab g_mono = make_mono_tab();
 
-// chain-order index of u_x^a u_y^b u_z^c
+// chain-order index of u_x^a u_y^b u_z^c: the monomials with z-degree below c
+// (tetrahedral numbers), those with z-degree c and y-degree below b, then a.
+// Closed form, so that it folds to a constant in the unrolled loops.
+__host__ __device__ constexpr int tet(int n) { return n * (n + 1) * (n + 2) / 6; }
 __host__ __device__ constexpr int mono_index(int a, int b, int c)
 {
-    int m = 0;
-    for (int cc = 0; cc < c; ++cc) m += (MDEG - cc + 1) * (MDEG - cc + 2) / 2;
-    for (int bb = 0; bb < b; ++bb) m += MDEG - bb - c + 1;
-    return m + a;
+    return tet(MDEG + 1) - tet(MDEG + 1 - c) + b * (MDEG + 1 - c) - b * (b - 1) / 2 + a;
 }
 static_assert(mono_index(0, 0, MDEG) == NMONO - 1, "monomial count");
 static_assert(mono_index(MDEG, 0, 0) == MDEG, "chain order");
@@ -377,12 +377,16 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 5) desc_mom_fwd_red_kernel(
     if (b >= B) return;
     const BeadSys sy = bsys[ba_sys[b]];
     const Rep& rp = reps[sy.rep];
+    const Box bx = box_of(rp);
     const int n = min(nnb[b], maxnb);
     const float4 xi = x[b];
 
-    float gr[NR];
+    // radial sums; evenly spaced centres on the fast path keep channels c and
+    // c + 16 in one register pair (gr2[8 qp + k] = channels 8 qp + k, 8 qp + k + 16)
+    float2 gr2[NR / 2];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) gr[c] = 0.0f;
+    for (int c = 0; c < NR / 2; ++c) gr2[c] = make_float2(0.0f, 0.0f);
+    const bool packed = FAST && dp.r_even;
     float dg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     float2 acc[RSLOT][2];
 #pragma unroll
@@ -395,23 +399,44 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 5) desc_mom_fwd_red_kernel(
         const float4 xj = xnext;
         if (s + 32 < n) xnext = x[sy.ba0 + nbr[(size_t)b * maxnb + s + 32]];
         if (s < n) {
-            float dx, dy, dz;
-            pair_vec(rp, xi, xj, dx, dy, dz);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float r = sqrtf(r2);
-            const float ir = 1.0f / r;
-            float fc, dfc;
-            cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
-            if (FAST && dp.r_even) {
-                float g[NR];
-                radial_gauss32(dp, r, g);
+            float dx, dy, dz, r, r2, ir, fc, dfc;
+            if (FAST) {
+                geo_fast(bx, xi, xj, dp.rc, dp.pi_over_rc, dx, dy, dz, r, ir, fc, dfc);
+                r2 = r * r;
+            } else {
+                pair_vec(rp, xi, xj, dx, dy, dz);
+                r2 = dx * dx + dy * dy + dz * dz;
+                r = sqrtf(r2);
+                ir = 1.0f / r;
+                cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+            }
+            if (packed) {
+                // product recurrence of radial_gauss32 on two groups at once
+                const float2 rho = make_float2(dp.rec_k, dp.rec_k);
+                const float dd = dp.r_delta * dp.r_delta;
 #pragma unroll
-                for (int c = 0; c < NR; ++c) gr[c] = fmaf(g[c], fc, gr[c]);
+                for (int qp = 0; qp < 2; ++qp) {
+                    const float ta = r - dp.r_mu[8 * qp], tb = r - dp.r_mu[8 * qp + 16];
+                    float2 e2 = make_float2(exp2f(-dp.eta_R_l2 * ta * ta) * fc, exp2f(-dp.eta_R_l2 * tb * tb) * fc);
+                    float2 R2 = make_float2(exp2f(dp.eta_R_l2 * fmaf(2.0f * ta, dp.r_delta, -dd)),
+                                            exp2f(dp.eta_R_l2 * fmaf(2.0f * tb, dp.r_delta, -dd)));
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        gr2[8 * qp + k] = __fadd2_rn(gr2[8 * qp + k], e2);
+                        if (k < 7) {
+                            e2 = __fmul2_rn(e2, R2);
+                            R2 = __fmul2_rn(R2, rho);
+                        }
+                    }
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
                     const float t = r - dp.r_mu[c];
-                    gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+                    const float g = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+                    float2& slot = gr2[8 * ((c >> 3) & 1) + (c & 7)];
+                    if (c < 16) slot.x += g;
+                    else slot.y += g;
                 }
             }
             float bw[4];
@@ -480,6 +505,14 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 5) desc_mom_fwd_red_kernel(
         }
         __syncwarp();
     }
+    float gr[NR];
+#pragma unroll
+    for (int qp = 0; qp < 2; ++qp)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            gr[8 * qp + k] = gr2[8 * qp + k].x;
+            gr[8 * qp + k + 16] = gr2[8 * qp + k].y;
+        }
     const float Gr = transpose_reduce32(gr, lane);
     float diag[4];
 #pragma unroll
@@ -751,6 +784,471 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS, FAST ? 5 : 4) desc_mom_adj_ker
     }
 }
 
+// ---------------------------------------------------------------------------
+// BF16-path adjoint (reduced basis, evenly spaced radial centres). The same
+// sums as desc_mom_adj_kernel<true>, arranged for the GB300 pipes:
+//  * per-atom set-up in one level: with s = a + b + c the coefficient
+//    2^-zeta w_zeta(a,b,c) = [zeta! / (zeta - s)!] 2^-zeta / (a! b! c!), so
+//    Q_abc = M_abc Phi(s) 2 / (a! b! c!) with Phi_eta(s) = sum_zeta
+//    [zeta! / (zeta - s)!] 2^-zeta D^(+/-)_(zeta,eta) (9 values per eta); the
+//    fold onto the 81 monomials with a in {0, 1} (x^2 = 1 - y^2 - z^2 on
+//    the sphere) is the sparse matrix R^T, x^(2k) -> (1 - y^2 - z^2)^k
+//    expanded by the trinomial theorem (483 terms), applied in one pass from
+//    a table that spreads the terms evenly over the lanes (at most 16 each);
+//  * while more than 32 neighbours remain each lane evaluates two of them in
+//    lockstep, so that every shared-memory broadcast of a coefficient float4
+//    of the compact 81-entry table feeds the Horner steps of both; the next
+//    round's neighbour positions are loaded while the current round computes;
+//  * the monomial index functions are closed forms: left as loops, the
+//    compiler does not always fold them inside the unrolled Horner steps
+//    and computes them at run time (3x the instructions);
+//  * the radial sums sum_c gs_c g_c and sum_c gs_c r_mu_c g_c run the
+//    product recurrence of radial_gauss32 on two groups of 8 centres at
+//    once (packed FP32x2), with (gs, gs r_mu) of both groups in one float4;
+//  * geometry and cutoff from geo_fast; the 12 per-atom sums (force on the
+//    centre, virial) in one transposed warp reduction.
+// ---------------------------------------------------------------------------
+constexpr int ADJF_WARPS = 4;
+constexpr int ADJF_RG = 16;   // float4 per warp: (gs_a, gs_b, gs_a r_a, gs_b r_b) for centre pairs (c, c + 16)
+constexpr int FOLD_MAX = 16;  // fold terms per lane
+
+// compact index of the reduced monomial u_x^a u_y^b u_z^c (a <= 1), chain
+// order: z-level cc holds 2 (MDEG - cc) + 1 of them, so the levels below c hold
+// c (2 MDEG + 2 - c); within the level two per y-degree (closed form, folds to
+// a constant in the unrolled loops)
+__host__ __device__ constexpr int red_index(int a, int b, int c)
+{
+    return c * (2 * MDEG + 2 - c) + 2 * b + a;
+}
+static_assert(red_index(0, 0, MDEG) == NRED - 1, "reduced monomial count");
+
+struct FoldTab {
+    // per lane and term: bits 0-7 source monomial (chain order), 8-15 compact
+    // target, bit 16 last term of its target, bits 24-31 signed coefficient
+    unsigned ent[FOLD_MAX][32];
+    // per slot and lane: 2 / (a! b! c!) and the degree s of monomial lane + 32 slot
+    float w[MSLOT][32];
+    int deg[MSLOT][32];
+    // Phi coefficients [zeta! / (zeta - s)!] 2^-zeta (0 for s > zeta), [zeta index][s]
+    float cphi[4][MDEG + 1];
+};
+
+constexpr FoldTab make_fold_tab()
+{
+    FoldTab t{};
+    // terms of each target: full (a, b, c) -> (a % 2, b + 2i, c + 2j), k = a / 2,
+    // coefficient (-1)^(i+j) k! / (i! j! (k-i-j)!)
+    int tgt_cnt[NRED] = {};
+    int src[NRED][16] = {};
+    int cof[NRED][16] = {};
+    for (int c = 0; c <= MDEG; ++c)
+        for (int b = 0; b <= MDEG - c; ++b)
+            for (int a = 0; a <= MDEG - b - c; ++a) {
+                const int k = a / 2;
+                for (int i = 0; i <= k; ++i)
+                    for (int j = 0; j <= k - i; ++j) {
+                        const int tg = red_index(a % 2, b + 2 * i, c + 2 * j);
+                        const int co = (((i + j) & 1) ? -1 : 1) *
+                                       (int)(cfact(k) / (cfact(i) * cfact(j) * cfact(k - i - j)));
+                        src[tg][tgt_cnt[tg]] = mono_index(a, b, c);
+                        cof[tg][tgt_cnt[tg]] = co;
+                        ++tgt_cnt[tg];
+                    }
+            }
+    // longest-processing-time assignment of the targets to the lanes
+    int load[32] = {};
+    bool done[NRED] = {};
+    int lane_terms[32][FOLD_MAX][3] = {};   // (source, target, coefficient)
+    for (int q = 0; q < NRED; ++q) {
+        int best = -1;
+        for (int tg = 0; tg < NRED; ++tg)
+            if (!done[tg] && (best < 0 || tgt_cnt[tg] > tgt_cnt[best])) best = tg;
+        done[best] = true;
+        int ln = 0;
+        for (int l = 1; l < 32; ++l)
+            if (load[l] < load[ln]) ln = l;
+        for (int e = 0; e < tgt_cnt[best]; ++e) {
+            lane_terms[ln][load[ln] + e][0] = src[best][e];
+            lane_terms[ln][load[ln] + e][1] = best;
+            lane_terms[ln][load[ln] + e][2] = cof[best][e];
+        }
+        load[ln] += tgt_cnt[best];
+    }
+    for (int l = 0; l < 32; ++l)
+        for (int e = 0; e < FOLD_MAX; ++e) {
+            if (e < load[l]) {
+                const bool last = e + 1 == load[l] || lane_terms[l][e + 1][1] != lane_terms[l][e][1];
+                t.ent[e][l] = (unsigned)lane_terms[l][e][0] | ((unsigned)lane_terms[l][e][1] << 8) |
+                              (last ? 0x10000u : 0u) | ((unsigned)(lane_terms[l][e][2] & 0xff) << 24);
+            } else {
+                t.ent[e][l] = 0u;   // coefficient 0, no store
+            }
+        }
+    int m = 0;
+    for (int c = 0; c <= MDEG; ++c)
+        for (int b = 0; b <= MDEG - c; ++b)
+            for (int a = 0; a <= MDEG - b - c; ++a, ++m) {
+                t.w[m / 32][m % 32] = (float)(2.0 / (cfact(a) * cfact(b) * cfact(c)));
+                t.deg[m / 32][m % 32] = a + b + c;
+            }
+    const int zetas[4] = {1, 2, 4, 8};
+    for (int z = 0; z < 4; ++z)
+        for (int sd = 0; sd <= MDEG; ++sd)
+            t.cphi[z][sd] = sd > zetas[z] ? 0.0f
+                                          : (float)(cfact(zetas[z]) / cfact(zetas[z] - sd) / (double)(1 << zetas[z]));
+    return t;
+}
+
+__device__ const FoldTab g_fold = make_fold_tab();
+
+template <int NB>
+__device__ __forceinline__ void adj_fast_eval(const Box& bx, const DescParams<float>& dp, const float4& xi,
+                                              const float4 (&xj)[NB], const bool (&valid)[NB],
+                                              const float4* __restrict__ Q, const float4* __restrict__ RG,
+                                              const float (&dsum)[4], float (&v)[NB][3], float (&d)[NB][3])
+{
+    float r[NB], ir[NB], fc[NB], dfc[NB];
+    float2 X2[NB], Y2[NB], Z2[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        float dx, dy, dz;
+        geo_fast(bx, xi, xj[t], dp.rc, dp.pi_over_rc, dx, dy, dz, r[t], ir[t], fc[t], dfc[t]);
+        if (!valid[t]) {   // an idle slot: a unit vector with zero weights gives v = 0
+            dx = 1.0f;
+            dy = dz = 0.0f;
+            r[t] = ir[t] = 1.0f;
+            fc[t] = dfc[t] = 0.0f;
+        }
+        X2[t] = make_float2(dx * ir[t], dx * ir[t]);
+        Y2[t] = make_float2(dy * ir[t], dy * ir[t]);
+        Z2[t] = make_float2(dz * ir[t], dz * ir[t]);
+    }
+
+    // radial sums; centres c and c + 16 share a register pair
+    float2 a1[NB], a2[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) a1[t] = a2[t] = make_float2(0.0f, 0.0f);
+    const float2 rho = make_float2(dp.rec_k, dp.rec_k);
+    const float dd = dp.r_delta * dp.r_delta;
+#pragma unroll
+    for (int qp = 0; qp < 2; ++qp) {
+        float2 e2[NB], R2[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            const float ta = r[t] - dp.r_mu[8 * qp], tb = r[t] - dp.r_mu[8 * qp + 16];
+            e2[t] = make_float2(exp2f(-dp.eta_R_l2 * ta * ta), exp2f(-dp.eta_R_l2 * tb * tb));
+            R2[t] = make_float2(exp2f(dp.eta_R_l2 * fmaf(2.0f * ta, dp.r_delta, -dd)),
+                                exp2f(dp.eta_R_l2 * fmaf(2.0f * tb, dp.r_delta, -dd)));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 g = RG[qp * 8 + k];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                a1[t] = __ffma2_rn(e2[t], make_float2(g.x, g.y), a1[t]);
+                a2[t] = __ffma2_rn(e2[t], make_float2(g.z, g.w), a2[t]);
+                if (k < 7) {
+                    e2[t] = __fmul2_rn(e2[t], R2[t]);
+                    R2[t] = __fmul2_rn(R2[t], rho);
+                }
+            }
+        }
+    }
+    float dEdr[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+        dEdr[t] = (a1[t].x + a1[t].y) * fmaf(-2.0f * dp.eta_R * r[t], fc[t], dfc[t]) +
+                  2.0f * dp.eta_R * fc[t] * (a2[t].x + a2[t].y);
+
+    // P_eta(u) = sum Q_eta,abc u_x^a u_y^b u_z^c (a <= 1) and its gradient:
+    // Horner in y within each z-level (x-degree 1 folded in first), then in z
+    float2 V[NB][2], VX[NB][2], VY[NB][2], VZ[NB][2];
+#pragma unroll
+    for (int c = MDEG; c >= 0; --c) {
+        float2 S[NB][2], SX[NB][2], SY[NB][2];
+#pragma unroll
+        for (int bb = MDEG - c; bb >= 0; --bb) {
+            const int m0 = red_index(0, bb, c);
+            const float4 q0 = Q[m0];
+            const float2 p0 = make_float2(q0.x, q0.y), p1 = make_float2(q0.z, q0.w);
+            if (bb == MDEG - c) {   // degree 8: no x term
+#pragma unroll
+                for (int t = 0; t < NB; ++t) {
+                    S[t][0] = p0;
+                    S[t][1] = p1;
+                }
+            } else {
+                const float4 q1 = Q[m0 + 1];
+                const float2 w0 = make_float2(q1.x, q1.y), w1 = make_float2(q1.z, q1.w);
+#pragma unroll
+                for (int t = 0; t < NB; ++t) {
+                    const float2 R0 = __ffma2_rn(w0, X2[t], p0), R1 = __ffma2_rn(w1, X2[t], p1);
+                    if (bb == MDEG - c - 1) {
+                        SY[t][0] = S[t][0];
+                        SY[t][1] = S[t][1];
+                        SX[t][0] = w0;
+                        SX[t][1] = w1;
+                    } else {
+                        SY[t][0] = __ffma2_rn(SY[t][0], Y2[t], S[t][0]);
+                        SY[t][1] = __ffma2_rn(SY[t][1], Y2[t], S[t][1]);
+                        SX[t][0] = __ffma2_rn(SX[t][0], Y2[t], w0);
+                        SX[t][1] = __ffma2_rn(SX[t][1], Y2[t], w1);
+                    }
+                    S[t][0] = __ffma2_rn(S[t][0], Y2[t], R0);
+                    S[t][1] = __ffma2_rn(S[t][1], Y2[t], R1);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (c == MDEG) {
+                    V[t][h] = S[t][h];
+                } else if (c == MDEG - 1) {
+                    VZ[t][h] = V[t][h];
+                    V[t][h] = __ffma2_rn(V[t][h], Z2[t], S[t][h]);
+                    VX[t][h] = SX[t][h];
+                    VY[t][h] = SY[t][h];
+                } else {
+                    VZ[t][h] = __ffma2_rn(VZ[t][h], Z2[t], V[t][h]);
+                    V[t][h] = __ffma2_rn(V[t][h], Z2[t], S[t][h]);
+                    VX[t][h] = __ffma2_rn(VX[t][h], Z2[t], SX[t][h]);
+                    VY[t][h] = __ffma2_rn(VY[t][h], Z2[t], SY[t][h]);
+                }
+            }
+    }
+
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        float bw[4], dbw[4];
+        const float r2 = r[t] * r[t];
+        const float sl = fmaf(-2.0f * r[t], fc[t], 0.0f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float ex = exp2f(-dp.eta_A_l2[e] * r2);
+            bw[e] = ex * fc[t];
+            dbw[e] = ex * fmaf(dp.eta_A[e], sl, dfc[t]);
+        }
+        const float Vv[4] = {V[t][0].x, V[t][0].y, V[t][1].x, V[t][1].y};
+        float de = dEdr[t];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) de = fmaf(fmaf(-2.0f * bw[e], dsum[e], Vv[e]), dbw[e], de);
+        const float gx = bw[0] * VX[t][0].x + bw[1] * VX[t][0].y + bw[2] * VX[t][1].x + bw[3] * VX[t][1].y;
+        const float gy = bw[0] * VY[t][0].x + bw[1] * VY[t][0].y + bw[2] * VY[t][1].x + bw[3] * VY[t][1].y;
+        const float gz = bw[0] * VZ[t][0].x + bw[1] * VZ[t][0].y + bw[2] * VZ[t][1].x + bw[3] * VZ[t][1].y;
+        const float ux = X2[t].x, uy = Y2[t].x, uz = Z2[t].x;
+        const float gu = gx * ux + gy * uy + gz * uz;
+        v[t][0] = de * ux + (gx - gu * ux) * ir[t];
+        v[t][1] = de * uy + (gy - gu * uy) * ir[t];
+        v[t][2] = de * uz + (gz - gu * uz) * ir[t];
+        d[t][0] = ux * r[t];   // the pair vector, for the virial
+        d[t][1] = uy * r[t];
+        d[t][2] = uz * r[t];
+    }
+}
+
+// asynchronous 16-byte copy global -> shared (LDGSTS); completion by
+// cp_async_wait_all in the issuing thread, then __syncwarp for the warp
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int ADJF_WARP_BYTES = NMONO * 16 + NRED * 16 + (MDEG + 1) * 16 + ADJF_RG * 16 + NA * 4;
+
+__global__ void __launch_bounds__(32 * ADJF_WARPS, 3) desc_mom_adj_fast_kernel(
+    const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
+    float4* __restrict__ f, float* __restrict__ wbuf, int det, float4* __restrict__ vbuf)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    float4* Qf = reinterpret_cast<float4*>(smem_raw + (size_t)wib * ADJF_WARP_BYTES);   // chain order, 165
+    float4* Qr = Qf + NMONO;                                                             // compact, 81
+    float4* Phi = Qr + NRED;                                                             // [s], over eta
+    float4* RG = Phi + (MDEG + 1);
+    float* gA = reinterpret_cast<float*>(RG + ADJF_RG);
+    const int b = blockIdx.x * ADJF_WARPS + wib;
+    if (b >= B) return;
+
+    // loads that depend only on b first: moments (copied asynchronously into
+    // the full table, scaled in place below), dE/dG, position, count
+#pragma unroll
+    for (int k = 0; k < MSLOT; ++k)
+        if (k < MSLOT - 1 || lane < (unsigned)MLAST)
+            cp_async16(&Qf[lane + 32 * k], &Min[((size_t)b * MSLOT + k) * 32 + lane]);
+    cp_async_commit();
+    const float gR = dEdG[(size_t)b * ND + lane];
+    const float gAn = dEdG[(size_t)b * ND + NR + lane];
+    const int n = min(nnb[b], maxnb);
+    const float4 xi = x[b];
+    const int* __restrict__ nb = nbr + (size_t)b * maxnb;
+    const BeadSys sy = bsys[ba_sys[b]];
+    // the first round's neighbours
+    int ja = 0, jb = 0;
+    float4 xa = xi, xb = xi;
+    if ((int)lane < n) {
+        ja = nb[lane];
+        xa = x[sy.ba0 + ja];
+    }
+    if (n > 32 && 32 + (int)lane < n) {
+        jb = nb[32 + lane];
+        xb = x[sy.ba0 + jb];
+    }
+    const Box bx = box_of(reps[sy.rep]);
+
+    {
+        const int q = (int)lane >> 3, k = (int)lane & 7;
+        float* rg = reinterpret_cast<float*>(RG) + ((q & 1) * 8 + k) * 4 + (q >> 1);
+        rg[0] = gR;
+        rg[2] = gR * dp.r_mu[lane];
+        gA[lane] = gAn;
+    }
+    __syncwarp();
+    // Phi_eta(s): lane (s = lane / 4, eta = lane % 4) for s < 8, then s = 8
+    {
+        const int sd = (int)lane >> 2, e = (int)lane & 3;
+        const int li = sd & 1;   // D^+ = D(+) + D(-) for even s, D^- = D(+) - D(-) for odd s
+        float ph = 0.0f;
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+            const float dd = li ? gA[(2 * z) * 4 + e] - gA[(2 * z + 1) * 4 + e]
+                                : gA[(2 * z) * 4 + e] + gA[(2 * z + 1) * 4 + e];
+            ph = fmaf(g_fold.cphi[z][sd], dd, ph);
+        }
+        reinterpret_cast<float*>(Phi)[lane] = ph;
+        if (lane < 4)
+            reinterpret_cast<float*>(Phi)[32 + lane] = g_fold.cphi[3][MDEG] * (gA[6 * 4 + lane] + gA[7 * 4 + lane]);
+    }
+    float dsum[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dsum[e] = gA[e] + gA[8 + e] + gA[16 + e] + gA[24 + e];
+    cp_async_wait_all();
+    __syncwarp();
+    // Q_abc = M_abc Phi(s) 2 / (a! b! c!)
+#pragma unroll
+    for (int k = 0; k < MSLOT; ++k) {
+        if (k < MSLOT - 1 || lane < (unsigned)MLAST) {
+            const float4 ph = Phi[g_fold.deg[k][lane]];
+            const float w = g_fold.w[k][lane];
+            const float4 M = Qf[lane + 32 * k];
+            Qf[lane + 32 * k] = make_float4(M.x * ph.x * w, M.y * ph.y * w, M.z * ph.z * w, M.w * ph.w * w);
+        }
+    }
+    __syncwarp();
+    // fold onto the compact reduced table, one pass
+    {
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int e = 0; e < FOLD_MAX; ++e) {
+            const unsigned w = g_fold.ent[e][lane];
+            const float cf = (float)((int)w >> 24);
+            const float4 q = Qf[w & 0xffu];
+            acc.x = fmaf(cf, q.x, acc.x);
+            acc.y = fmaf(cf, q.y, acc.y);
+            acc.z = fmaf(cf, q.z, acc.z);
+            acc.w = fmaf(cf, q.w, acc.w);
+            if (w & 0x10000u) {
+                Qr[(w >> 8) & 0xffu] = acc;
+                acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        }
+    }
+    __syncwarp();
+
+    float red[16];   // force on the centre (3), virial (9), padding
+#pragma unroll
+    for (int q = 0; q < 16; ++q) red[q] = 0.0f;
+    int s0 = 0;
+    while (s0 < n) {
+        // keeps the coefficient loads inside the round: hoisted out of the
+        // loop they would hold the 81 float4 in registers
+        asm volatile("" ::: "memory");
+        const bool paired = n - s0 > 32;        // warp-uniform
+        const int s1 = s0 + (paired ? 64 : 32);
+        const int sA = s0 + (int)lane, sB = sA + 32;
+        const float4 ca = xa, cb = xb;
+        const int ka = ja, kb = jb;
+        // the next round's neighbours
+        if (s1 + (int)lane < n) {
+            ja = nb[s1 + lane];
+            xa = x[sy.ba0 + ja];
+        }
+        if (n - s1 > 32 && s1 + 32 + (int)lane < n) {
+            jb = nb[s1 + 32 + lane];
+            xb = x[sy.ba0 + jb];
+        }
+        float v[2][3], dv[2][3];
+        bool ok[2];
+        if (paired) {
+            const float4 xx[2] = {ca, cb};
+            const bool vv[2] = {sA < n, sB < n};
+            adj_fast_eval<2>(bx, dp, xi, xx, vv, Qr, RG, dsum, v, dv);
+            ok[0] = vv[0];
+            ok[1] = vv[1];
+        } else {
+            const float4 xx[1] = {ca};
+            const bool vv[1] = {sA < n};
+            float v1[1][3], d1[1][3];
+            adj_fast_eval<1>(bx, dp, xi, xx, vv, Qr, RG, dsum, v1, d1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                v[0][a] = v1[0][a];
+                dv[0][a] = d1[0][a];
+                v[1][a] = dv[1][a] = 0.0f;
+            }
+            ok[0] = vv[0];
+            ok[1] = false;
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (!ok[t]) continue;
+            const int sl = t == 0 ? sA : sB;
+            const int j = t == 0 ? ka : kb;
+            if (det)
+                vbuf[(size_t)b * maxnb + sl] = make_float4(v[t][0], v[t][1], v[t][2], 0.0f);
+            else
+                atomicAdd(&f[sy.ba0 + j], make_float4(-v[t][0], -v[t][1], -v[t][2], 0.0f));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                red[a] += v[t][a];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) red[3 + 3 * a + c] -= dv[t][a] * v[t][c];
+            }
+        }
+        s0 = s1;
+    }
+    // lanes 2q and 2q + 1 end with the sum of value q
+#pragma unroll
+    for (int o = 16, cnt = 16; o >= 2; o >>= 1, cnt >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < cnt / 2; ++q) {
+            const float send = upper ? red[q] : red[q + cnt / 2];
+            const float keep = upper ? red[q + cnt / 2] : red[q];
+            red[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    const float tot = red[0] + __shfl_xor_sync(0xffffffffu, red[0], 1);
+    const int vi = (int)(lane >> 1);
+    if ((lane & 1) == 0) {
+        if (vi < 3) {
+            if (det)
+                reinterpret_cast<float*>(&f[b])[vi] = tot;   // gathered later
+            else
+                atomicAdd(reinterpret_cast<float*>(&f[b]) + vi, tot);
+        } else if (vi < 12) {
+            wbuf[(size_t)b * 9 + (vi - 3)] = tot;
+        }
+    }
+}
+
 size_t moment_elems_per_atom() { return (size_t)MSLOT * 32; }   // float4 per bead-atom
 
 template <bool FAST>
@@ -790,12 +1288,25 @@ void launch_descriptors_moment(const Dev& d, const void* dpv, cudaStream_t st)
         run_fwd<false>(d, dpv, st);
 }
 
+static void run_adj_fast(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    const size_t sm = (size_t)ADJF_WARPS * ADJF_WARP_BYTES;
+    desc_mom_adj_fast_kernel<<<(d.B + ADJF_WARPS - 1) / ADJF_WARPS, 32 * ADJF_WARPS, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+        *(const DescParams<float>*)dpv, (const float4*)d.mom, (const float*)d.dEdG, (float4*)d.f,
+        (float*)d.wbuf, d.deterministic, (float4*)d.vbuf);
+}
+
 void launch_adjoint_moment(const Dev& d, const void* dpv, cudaStream_t st)
 {
-    if (d.precision == 2)
-        run_adj<true>(d, dpv, st);
-    else
+    if (d.precision == 2) {
+        if (((const DescParams<float>*)dpv)->r_even)
+            run_adj_fast(d, dpv, st);
+        else
+            run_adj<true>(d, dpv, st);
+    } else {
         run_adj<false>(d, dpv, st);
+    }
 }
 
 }  // namespace pimd
