@@ -535,8 +535,10 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
 {
     Dev& d = c->d;
     const size_t v4 = d.precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
+    const bool summed = d.potential == PIMD_POT_MODEL && adjoint_sums_energy(d, dparams(c));
     cudaMemsetAsync(d.f, 0, v4 * d.B, st);
     cudaMemsetAsync(d.W, 0, sizeof(double) * 9 * d.S, st);
+    if (summed) cudaMemsetAsync(d.V, 0, sizeof(double) * d.S, st);
     mark(c, PIMD_STAGE_NEIGHBOURS, st, timed);
     if (d.potential == PIMD_POT_HARMONIC) {
         launch_harmonic(d, st);
@@ -563,7 +565,7 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
         if (d.deterministic) launch_force_gather(d, st);
     }
     mark(c, PIMD_STAGE_ENERGY, st, timed);
-    launch_energy_reduce(d, st);
+    if (!summed) launch_energy_reduce(d, st);
     if (d.metad.cv) launch_metad(d, deposit, st);   // bias on every bead (and hills on deposition steps)
 }
 void eval_forces(pimd_ctx* c) { eval_forces(c, c->st); }
@@ -1223,12 +1225,17 @@ int pimd_get_angular(const pimd_ctx* c)
 int pimd_kernels_per_step(const pimd_ctx* c)
 {
     if (!c) return 0;
-    // ring start, neighbours, descriptors, network, adjoint, energy, ring finish, step counter;
-    // metadynamics: CV, bias, bias force
-    const int md = c->d.metad.cv ? 3 : 0;
-    if (c->d.potential == PIMD_POT_GFN)   // ring start, neighbours, the head, energy, ring finish, counter
-        return 5 + 2 + gfn_kernels_per_eval(c->d.gfn.L) + md;
-    return (c->d.potential == PIMD_POT_HARMONIC ? 5 : (c->d.deterministic ? 9 : 8)) + md;
+    // ring start, ring finish, step counter; metadynamics: CV, bias, bias force
+    const Dev& d = c->d;
+    const int ring = 3, md = d.metad.cv ? 3 : 0;
+    if (d.potential == PIMD_POT_HARMONIC) return ring + 2 + md;   // harmonic forces, energy
+    if (d.potential == PIMD_POT_GFN)   // neighbours, the head, energy
+        return ring + 2 + 2 + gfn_kernels_per_eval(d.gfn.L) + md;
+    // neighbours (cell binning, Verlet skin check, lists), descriptors,
+    // network, adjoint (+ force gather), energy unless the adjoint sums it
+    const int nbr = 1 + (d.n_cell_bs ? 1 : 0) + (d.maxcand ? 1 : 0);
+    const int energy = adjoint_sums_energy(d, dparams(c)) ? 0 : 1;
+    return ring + nbr + 3 + (d.deterministic ? 1 : 0) + energy + md;
 }
 
 int pimd_energy_forces(pimd_ctx* c, const double* x_dev, double* e_dev, double* f_dev, double* virial_dev)

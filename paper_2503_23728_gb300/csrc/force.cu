@@ -744,6 +744,11 @@ static void run_adj_f32(const Dev& d, const void* dpv, cudaStream_t st)
         d.deterministic, (float4*)d.vbuf);
 }
 
+bool adjoint_sums_energy(const Dev& d, const void* dpv)
+{
+    return d.precision != 0 && d.sched.ang && d.mom && moment_adjoint_sums_energy(d, dpv);
+}
+
 void launch_adjoint(const Dev& d, const void* dpv, cudaStream_t st)
 {
     if (d.precision != 0 && d.sched.ang && d.mom) {

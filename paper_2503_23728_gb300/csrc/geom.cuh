@@ -146,22 +146,28 @@ __device__ __forceinline__ Box box_of(const Rep& rp)
     }
     return b;
 }
+__device__ __forceinline__ float box_len(const Box& b, int a) { return b.L[a]; }
+__device__ __forceinline__ float box_inv(const Box& b, int a) { return b.invL[a]; }
+__device__ __forceinline__ float box_len(const Rep& r, int a) { return r.Lf[a]; }
+__device__ __forceinline__ float box_inv(const Rep& r, int a) { return r.periodic ? r.invLf[a] : 0.0f; }
 
 // BF16-path geometry of one neighbour (the path's bar is 1e-2 on the forces):
 // minimum-image pair vector with one rounding per component, the distance
 // and its inverse from the reciprocal square root, and the cutoff and its
 // slope from the special-function sine and cosine of pi r / r_c (absolute
 // error ~1e-6). The exact FP32 path keeps the error-free forms above.
-__device__ __forceinline__ void geo_fast(const Box& bx, const float4& xi, const float4& xj, float rc,
+// BX: Box (registers) or Rep (fields read where they are used)
+template <typename BX>
+__device__ __forceinline__ void geo_fast(const BX& bx, const float4& xi, const float4& xj, float rc,
                                          float pi_over_rc, float& dx, float& dy, float& dz, float& r, float& ir,
                                          float& fc, float& dfc)
 {
     dx = xj.x - xi.x;
     dy = xj.y - xi.y;
     dz = xj.z - xi.z;
-    dx = fmaf(-rintf(dx * bx.invL[0]), bx.L[0], dx);
-    dy = fmaf(-rintf(dy * bx.invL[1]), bx.L[1], dy);
-    dz = fmaf(-rintf(dz * bx.invL[2]), bx.L[2], dz);
+    dx = fmaf(-rintf(dx * box_inv(bx, 0)), box_len(bx, 0), dx);
+    dy = fmaf(-rintf(dy * box_inv(bx, 1)), box_len(bx, 1), dy);
+    dz = fmaf(-rintf(dz * box_inv(bx, 2)), box_len(bx, 2), dz);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     ir = rsqrtf(r2);
     r = r2 * ir;

@@ -125,6 +125,10 @@ void launch_descriptors(const Dev& d, const void* dp, cudaStream_t st);
 void launch_network_fp(const Dev& d, cudaStream_t st);
 void launch_network_tc(const Dev& d, cudaStream_t st);
 void launch_adjoint(const Dev& d, const void* dp, cudaStream_t st);
+// true when the adjoint kernel also sums the per-bead energies V and virials
+// W (FP64 atomics; V and W zeroed before): the energy reduction is skipped
+bool adjoint_sums_energy(const Dev& d, const void* dp);
+bool moment_adjoint_sums_energy(const Dev& d, const void* dp);
 void launch_gfn(const Dev& d, cudaStream_t st);
 void launch_gfn_tc(const Dev& d, cudaStream_t st);
 size_t gfn_tc_image_bytes(int F, int L);

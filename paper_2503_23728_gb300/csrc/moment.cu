@@ -359,11 +359,11 @@ __device__ const RedTab g_red = make_red_tab();
 // per lane; the 165 moments are then rebuilt in shared memory by the
 // recurrence and finished as in the full forward
 constexpr int FWDR_WARP_FLOATS = 32 * NRED + 32 * 4;   // monomial rows (stride 81, odd) + weights
-constexpr int FWDR_WARPS = 4;
+constexpr int FWDR_WARPS = 2;
 static_assert(32 * NRED >= 4 * NMONO, "moment table reuses the monomial rows");
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * FWDR_WARPS, 5) desc_mom_fwd_red_kernel(
+__global__ void __launch_bounds__(32 * FWDR_WARPS, 10) desc_mom_fwd_red_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout)
@@ -377,7 +377,6 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 5) desc_mom_fwd_red_kernel(
     if (b >= B) return;
     const BeadSys sy = bsys[ba_sys[b]];
     const Rep& rp = reps[sy.rep];
-    const Box bx = box_of(rp);
     const int n = min(nnb[b], maxnb);
     const float4 xi = x[b];
 
@@ -401,7 +400,7 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 5) desc_mom_fwd_red_kernel(
         if (s < n) {
             float dx, dy, dz, r, r2, ir, fc, dfc;
             if (FAST) {
-                geo_fast(bx, xi, xj, dp.rc, dp.pi_over_rc, dx, dy, dz, r, ir, fc, dfc);
+                geo_fast(rp, xi, xj, dp.rc, dp.pi_over_rc, dx, dy, dz, r, ir, fc, dfc);
                 r2 = r * r;
             } else {
                 pair_vec(rp, xi, xj, dx, dy, dz);
@@ -808,7 +807,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS, FAST ? 5 : 4) desc_mom_adj_ker
 //  * geometry and cutoff from geo_fast; the 12 per-atom sums (force on the
 //    centre, virial) in one transposed warp reduction.
 // ---------------------------------------------------------------------------
-constexpr int ADJF_WARPS = 4;
+constexpr int ADJF_WARPS = 1;   // one-warp CTAs: a finished warp frees its slot at once
 constexpr int ADJF_RG = 16;   // float4 per warp: (gs_a, gs_b, gs_a r_a, gs_b r_b) for centre pairs (c, c + 16)
 constexpr int FOLD_MAX = 16;  // fold terms per lane
 
@@ -1060,11 +1059,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int ADJF_WARP_BYTES = NMONO * 16 + NRED * 16 + (MDEG + 1) * 16 + ADJF_RG * 16 + NA * 4;
 
-__global__ void __launch_bounds__(32 * ADJF_WARPS, 3) desc_mom_adj_fast_kernel(
+__global__ void __launch_bounds__(32 * ADJF_WARPS, 12) desc_mom_adj_fast_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
-    float4* __restrict__ f, float* __restrict__ wbuf, int det, float4* __restrict__ vbuf)
+    float4* __restrict__ f, float* __restrict__ wbuf, int det, float4* __restrict__ vbuf,
+    const float* __restrict__ Eatom, double* __restrict__ V, double* __restrict__ Wv)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wib = threadIdx.x >> 5;
@@ -1089,7 +1089,8 @@ __global__ void __launch_bounds__(32 * ADJF_WARPS, 3) desc_mom_adj_fast_kernel(
     const int n = min(nnb[b], maxnb);
     const float4 xi = x[b];
     const int* __restrict__ nb = nbr + (size_t)b * maxnb;
-    const BeadSys sy = bsys[ba_sys[b]];
+    const int bs = ba_sys[b];
+    const BeadSys sy = bsys[bs];
     // the first round's neighbours
     int ja = 0, jb = 0;
     float4 xa = xi, xb = xi;
@@ -1244,7 +1245,14 @@ __global__ void __launch_bounds__(32 * ADJF_WARPS, 3) desc_mom_adj_fast_kernel(
             else
                 atomicAdd(reinterpret_cast<float*>(&f[b]) + vi, tot);
         } else if (vi < 12) {
-            wbuf[(size_t)b * 9 + (vi - 3)] = tot;
+            // deterministic mode: per-atom virials, summed in a fixed order
+            // later; otherwise straight into the bead's FP64 sums
+            if (det)
+                wbuf[(size_t)b * 9 + (vi - 3)] = tot;
+            else
+                atomicAdd(&Wv[(size_t)bs * 9 + (vi - 3)], (double)tot);
+        } else if (vi == 12 && !det) {
+            atomicAdd(&V[bs], (double)Eatom[b]);
         }
     }
 }
@@ -1294,7 +1302,12 @@ static void run_adj_fast(const Dev& d, const void* dpv, cudaStream_t st)
     desc_mom_adj_fast_kernel<<<(d.B + ADJF_WARPS - 1) / ADJF_WARPS, 32 * ADJF_WARPS, sm, st>>>(
         (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
         *(const DescParams<float>*)dpv, (const float4*)d.mom, (const float*)d.dEdG, (float4*)d.f,
-        (float*)d.wbuf, d.deterministic, (float4*)d.vbuf);
+        (float*)d.wbuf, d.deterministic, (float4*)d.vbuf, (const float*)d.Eatom, d.V, d.W);
+}
+
+bool moment_adjoint_sums_energy(const Dev& d, const void* dpv)
+{
+    return d.precision == 2 && !d.deterministic && ((const DescParams<float>*)dpv)->r_even;
 }
 
 void launch_adjoint_moment(const Dev& d, const void* dpv, cudaStream_t st)

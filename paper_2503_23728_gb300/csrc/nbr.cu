@@ -269,14 +269,26 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
             nc = ncand[b];
         }
         if (nc <= maxcand) {
+            // all candidate indices first, then all their positions: two
+            // rounds of independent loads instead of two dependent ones per 32
+            constexpr int KC = PIMD_SORT_CAP / 32;
+            int jv[KC];
+            float3 pv[KC];
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const int t = 32 * k + (int)lane;
+                jv[k] = t < nc ? cl[t] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < KC; ++k) pv[k] = jv[k] >= 0 ? pos_f32(x[sy.ba0 + jv[k]]) : xi;
             cnt = 0;
-            for (int t0 = 0; t0 < nc; t0 += 32) {
-                const int t = t0 + (int)lane;
-                const int j = t < nc ? cl[t] : -1;
-                const bool in = t < nc && within(rp, xi, pos_f32(x[sy.ba0 + j]), rc2);
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                if (32 * k >= nc) break;   // warp-uniform
+                const bool in = jv[k] >= 0 && within(rp, xi, pv[k], rc2);
                 const unsigned m = __ballot_sync(0xffffffffu, in);
                 const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                if (in && pos < maxnb) out[pos] = j;
+                if (in && pos < maxnb) out[pos] = jv[k];
                 cnt += __popc(m);
             }
         } else {
@@ -304,7 +316,7 @@ void launch_neighbours(const Dev& d, cudaStream_t st)
             cell_build_kernel<Dbl4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
                 (const Dbl4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
         if (d.maxcand)
-            skin_check_kernel<Dbl4><<<d.S, 128, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
+            skin_check_kernel<Dbl4><<<d.S, 1024, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
         nbr_kernel<Dbl4><<<blocks, threads, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
                                                      d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb, d.err,
                                                      d.cand, d.ncand, d.xref, d.rebuild, d.maxcand);
@@ -313,7 +325,7 @@ void launch_neighbours(const Dev& d, cudaStream_t st)
             cell_build_kernel<float4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
                 (const float4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
         if (d.maxcand)
-            skin_check_kernel<float4><<<d.S, 128, 0, st>>>((const float4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
+            skin_check_kernel<float4><<<d.S, 1024, 0, st>>>((const float4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
         nbr_kernel<float4><<<blocks, threads, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
                                                        d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb,
                                                        d.err, d.cand, d.ncand, d.xref, d.rebuild, d.maxcand);
