@@ -269,27 +269,29 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
             nc = ncand[b];
         }
         if (nc <= maxcand) {
-            // all candidate indices first, then all their positions: two
-            // rounds of independent loads instead of two dependent ones per 32
-            constexpr int KC = PIMD_SORT_CAP / 32;
-            int jv[KC];
-            float3 pv[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const int t = 32 * k + (int)lane;
-                jv[k] = t < nc ? cl[t] : -1;
-            }
-#pragma unroll
-            for (int k = 0; k < KC; ++k) pv[k] = jv[k] >= 0 ? pos_f32(x[sy.ba0 + jv[k]]) : xi;
+            // groups of four chunks of 32: the group's candidate indices
+            // first, then their positions (independent loads), then the rule
+            constexpr int KC = 4;
             cnt = 0;
+            for (int g0 = 0; g0 < nc; g0 += 32 * KC) {
+                int jv[KC];
+                float3 pv[KC];
 #pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                if (32 * k >= nc) break;   // warp-uniform
-                const bool in = jv[k] >= 0 && within(rp, xi, pv[k], rc2);
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                if (in && pos < maxnb) out[pos] = jv[k];
-                cnt += __popc(m);
+                for (int k = 0; k < KC; ++k) {
+                    const int t = g0 + 32 * k + (int)lane;
+                    jv[k] = t < nc ? cl[t] : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < KC; ++k) pv[k] = jv[k] >= 0 ? pos_f32(x[sy.ba0 + jv[k]]) : xi;
+#pragma unroll
+                for (int k = 0; k < KC; ++k) {
+                    if (g0 + 32 * k >= nc) break;   // warp-uniform
+                    const bool in = jv[k] >= 0 && within(rp, xi, pv[k], rc2);
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+                    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (in && pos < maxnb) out[pos] = jv[k];
+                    cnt += __popc(m);
+                }
             }
         } else {
             cnt = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rc2, out, maxnb, lst[wib], lane);
