@@ -74,15 +74,15 @@ __device__ __forceinline__ double normal_of(unsigned long long seed, unsigned id
 // an Angstrom, in FP32 (rounding far below one FP32 ulp of the position)
 template <typename Real>
 __device__ __forceinline__ double to_bead(const double* __restrict__ C, const float* __restrict__ Cf,
-                                          const double* sq, const float* sqf, int P)
+                                          const double* sq, const float* sqf, int P, int stride)
 {
     if constexpr (std::is_same<Real, float>::value) {
         float a = 0.0f;
-        for (int k = 1; k < P; ++k) a = fmaf(Cf[k], sqf[k], a);
+        for (int k = 1; k < P; ++k) a = fmaf(Cf[k], sqf[k * stride], a);
         return fma(C[0], sq[0], (double)a);
     }
     double acc = 0.0;
-    for (int k = 0; k < P; ++k) acc += C[k] * sq[k];
+    for (int k = 0; k < P; ++k) acc += C[k] * sq[k * stride];
     return acc;
 }
 
@@ -123,10 +123,14 @@ void launch_rp_init(const Dev& d, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
-// block geometry: block -> (replica, first entry); thread -> (entry, mode)
+// block geometry: block -> (replica, first of T entries); thread -> (mode kk,
+// entry le) with the entry fastest, so that a warp touches consecutive
+// entries of one mode: the state [mode][atom][dim] and the bead records are
+// read and written in contiguous runs. Per-entry vectors over the modes sit
+// in shared memory as [mode][entry] (index kk * T + le).
 // ---------------------------------------------------------------------------
 struct RpThread {
-    int r, e, kk, N, P, i, dd;
+    int r, e, kk, le, T, N, P, i, dd;
     bool active;
 };
 
@@ -138,11 +142,11 @@ __device__ __forceinline__ RpThread rp_thread(const int2* __restrict__ blocks, c
     const Rep& rp = reps[t.r];
     t.N = rp.N;
     t.P = rp.P;
-    const int T = blockDim.x / t.P;
-    const int le = threadIdx.x / t.P;
-    t.kk = threadIdx.x - le * t.P;
-    t.e = bl.y + le;
-    t.active = le < T && t.e < 3 * t.N;
+    t.T = blockDim.x / t.P;
+    t.kk = threadIdx.x / t.T;
+    t.le = threadIdx.x - t.kk * t.T;
+    t.e = bl.y + t.le;
+    t.active = t.kk < t.P && t.e < 3 * t.N;
     t.i = t.e / 3;
     t.dd = t.e - 3 * t.i;
     return t;
@@ -158,17 +162,16 @@ __global__ void beads_kernel(const int2* __restrict__ blocks, const Rep* __restr
     float* sqf = reinterpret_cast<float*>(sq + blockDim.x);
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
-    const int le = threadIdx.x / t.P;
     if (t.active) {
         const double qv = q[3 * ((size_t)rp.ba0 + (size_t)t.kk * t.N + t.i) + t.dd];
-        sq[le * t.P + t.kk] = qv;
-        sqf[le * t.P + t.kk] = (float)qv;
+        sq[t.kk * t.T + t.le] = qv;
+        sqf[t.kk * t.T + t.le] = (float)qv;
     }
     __syncthreads();
     if (!t.active) return;
     const int j = t.kk;
     const double acc = to_bead<Real>(cmat + rp.cmat + (size_t)j * t.P, cmatf + rp.cmat + (size_t)j * t.P,
-                                     sq + le * t.P, sqf + le * t.P, t.P);
+                                     sq + t.le, sqf + t.le, t.P, t.T);
     comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
 }
 
@@ -217,7 +220,6 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
     __shared__ double red[32];
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
-    const int le = threadIdx.x / t.P;
     double dK = 0.0;
     if (t.active) {
         const int k = t.kk;
@@ -240,8 +242,8 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
         }
         p[g] = pv;
         q[g] = qv;
-        sq[le * t.P + k] = qv;
-        sqf[le * t.P + k] = (float)qv;
+        sq[k * t.T + t.le] = qv;
+        sqf[k * t.T + t.le] = (float)qv;
     }
     // thermostat heat: block partial, summed per replica in block order later
     dK = warp_sum(dK);
@@ -255,7 +257,7 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
     if (!t.active) return;
     const int j = t.kk;
     const double acc = to_bead<Real>(cmat + rp.cmat + (size_t)j * t.P, cmatf + rp.cmat + (size_t)j * t.P,
-                                     sq + le * t.P, sqf + le * t.P, t.P);
+                                     sq + t.le, sqf + t.le, t.P, t.T);
     comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
 }
 
@@ -274,13 +276,12 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
     __shared__ double red[32];
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
-    const int le = threadIdx.x / t.P;
     if (t.active) {
         Vec4<Real> fv = f[rp.ba0 + (size_t)t.kk * t.N + t.i];
         if constexpr (std::is_same<Real, float>::value)
-            sff[le * t.P + t.kk] = comp<Real>(fv, t.dd);
+            sff[t.kk * t.T + t.le] = comp<Real>(fv, t.dd);
         else
-            sf[le * t.P + t.kk] = (double)comp<Real>(fv, t.dd);
+            sf[t.kk * t.T + t.le] = (double)comp<Real>(fv, t.dd);
     }
     __syncthreads();
     double dK = 0.0;
@@ -290,10 +291,10 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         if constexpr (std::is_same<Real, float>::value) {
             // FP32 forces: their normal-mode components summed in FP32
             float a = 0.0f;
-            for (int j = 0; j < t.P; ++j) a = fmaf(cmatf[rp.cmat + (size_t)j * t.P + k], sff[le * t.P + j], a);
+            for (int j = 0; j < t.P; ++j) a = fmaf(cmatf[rp.cmat + (size_t)j * t.P + k], sff[j * t.T + t.le], a);
             fn = (double)a;
         } else {
-            for (int j = 0; j < t.P; ++j) fn += cmat[rp.cmat + (size_t)j * t.P + k] * sf[le * t.P + j];
+            for (int j = 0; j < t.P; ++j) fn += cmat[rp.cmat + (size_t)j * t.P + k] * sf[j * t.T + t.le];
         }
         const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
         fnm[g] = fn;
