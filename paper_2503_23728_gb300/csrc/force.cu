@@ -4,6 +4,8 @@
 // parts; bead-atoms are batched over all beads of all replicas.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "geom.cuh"
 #include "kernels.h"
@@ -988,46 +990,90 @@ void launch_network_fp(const Dev& d, cudaStream_t st)
 // a6: per-bead energy V_k = sum_i E_i, FP64 sum in a fixed order (one warp
 // per bead).
 // ---------------------------------------------------------------------------
+// (hi, lo) += v with Knuth's TwoSum: hi + lo holds the running sum of FP32
+// terms to ~2^-48 relative, on the FP32 pipes (FP64 runs at 2 lanes per SM
+// per clock on this GPU, which made the FP64 butterflies of many small beads
+// the cost of the whole reduction)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v)
+{
+    const float s = __fadd_rn(hi, v);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(256) energy_reduce_kernel(const Real* __restrict__ Eatom,
                                                             const Real* __restrict__ wbuf,
                                                             const BeadSys* __restrict__ bsys, int S,
                                                             double* __restrict__ V, double* __restrict__ Wv)
 {
-    // block (bead, component): component 0 the energy, 1..9 the virial
-    // entries; FP64 sums over the bead's atoms in a fixed order
-    __shared__ double red[8];
-    const int s = blockIdx.x, q = blockIdx.y;
+    // warp per bead: the energy and the 9 virial entries, summed over the
+    // bead's atoms in a fixed order (lane-strided, then a fixed butterfly);
+    // FP64 terms in FP64, FP32 terms as double-float pairs rounded to FP64
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned lane = lane_id();
+    if (s >= S) return;
     const BeadSys sy = bsys[s];
-    double acc = 0.0;
-    if (q == 0) {
-        for (int i = threadIdx.x; i < sy.N; i += blockDim.x) acc += (double)Eatom[sy.ba0 + i];
+    double out[10];
+    if constexpr (std::is_same<Real, double>::value) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) out[q] = 0.0;
+        for (int i = (int)lane; i < sy.N; i += 32) {
+            const size_t b = (size_t)(sy.ba0 + i);
+            out[0] += Eatom[b];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) out[1 + q] += wbuf[b * 9 + q];
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) out[q] = warp_sum(out[q]);
     } else {
-        for (int i = threadIdx.x; i < sy.N; i += blockDim.x) acc += (double)wbuf[(size_t)(sy.ba0 + i) * 9 + q - 1];
+        float hi[10], lo[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) hi[q] = lo[q] = 0.0f;
+        for (int i = (int)lane; i < sy.N; i += 32) {
+            const size_t b = (size_t)(sy.ba0 + i);
+            df_add(hi[0], lo[0], (float)Eatom[b]);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) df_add(hi[1 + q], lo[1 + q], (float)wbuf[b * 9 + q]);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                const float oh = __shfl_xor_sync(0xffffffffu, hi[q], o);
+                const float ol = __shfl_xor_sync(0xffffffffu, lo[q], o);
+                // both partners add in the same order (lower lane's pair first)
+                const bool upper = (lane & o) != 0;
+                float h = upper ? oh : hi[q], l = upper ? ol : lo[q];
+                df_add(h, l, upper ? hi[q] : oh);
+                l = __fadd_rn(l, upper ? lo[q] : ol);
+                hi[q] = h;
+                lo[q] = l;
+            }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) out[q] = (double)hi[q] + (double)lo[q];
     }
-    const double v = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        if (q == 0) V[s] = t;
-        else Wv[(size_t)s * 9 + q - 1] = t;
+    if (lane == 0) V[s] = out[0];
+    if (lane >= 1 && lane < 10) {
+        double mine = out[1];
+#pragma unroll
+        for (int q = 2; q < 10; ++q)
+            if ((int)lane == q) mine = out[q];
+        Wv[(size_t)s * 9 + lane - 1] = mine;
     }
 }
 
 void launch_energy_reduce(const Dev& d, cudaStream_t st)
 {
-    // block size sized to the largest bead (small systems: one warp per bead)
-    int t = 32;
-    while (t < 256 && t < d.max_N) t <<= 1;
-    const dim3 grid(d.S, 10);
+    const int blocks = (d.S + 7) / 8;
     if (d.precision == 0)
-        energy_reduce_kernel<double><<<grid, t, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
-                                                         d.V, d.W);
+        energy_reduce_kernel<double><<<blocks, 256, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
+                                                             d.V, d.W);
     else
-        energy_reduce_kernel<float><<<grid, t, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
-                                                        d.V, d.W);
+        energy_reduce_kernel<float><<<blocks, 256, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
+                                                            d.V, d.W);
 }
 
 // ---------------------------------------------------------------------------
