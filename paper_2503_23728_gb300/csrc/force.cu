@@ -746,6 +746,137 @@ static void run_adj_f32(const Dev& d, const void* dpv, cudaStream_t st)
         d.deterministic, (float4*)d.vbuf);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint for small clusters: every replica has at most 33 atoms, so n <= 32
+// neighbours. Half a warp per bead-atom (two per warp), ordered pairs (each
+// lane owns neighbours j = l and l + 16 and sums over all k != j), the same
+// arithmetic as desc_adj_kernel's ordered-pair schedule. A whole warp per
+// atom would leave the lanes beyond n idle: these clusters have 5-23
+// neighbours.
+// ---------------------------------------------------------------------------
+constexpr int SMALL_SL = 32;   // neighbour slots per atom
+constexpr int SMALL_ATOMS = 16; // bead-atoms per 256-thread block
+
+template <bool FAST>
+__global__ void __launch_bounds__(256) desc_adj_small_kernel(
+    const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<float> dp, const float* __restrict__ dEdG, float4* __restrict__ f, float* __restrict__ wbuf,
+    int det, float4* __restrict__ vbuf)
+{
+    __shared__ float4 U[SMALL_ATOMS][SMALL_SL], A[SMALL_ATOMS][SMALL_SL], DA[SMALL_ATOMS][SMALL_SL];
+    __shared__ float RAD[SMALL_ATOMS][SMALL_SL];
+    __shared__ float gsh[SMALL_ATOMS][ND];
+    const int hw = threadIdx.x >> 4;
+    const int hl = threadIdx.x & 15;
+    const int b = blockIdx.x * SMALL_ATOMS + hw;
+    // no early return: the two halves of a warp meet in __syncwarp
+    const bool live = b < B;
+    int n = 0;
+    BeadSys sy{0, 0, 0, 0};
+    float4 xi = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (live) {
+        sy = bsys[ba_sys[b]];
+        n = min(nnb[b], min(maxnb, SMALL_SL));
+        xi = x[b];
+#pragma unroll
+        for (int q = 0; q < ND / 16; ++q) gsh[hw][hl + 16 * q] = dEdG[(size_t)b * ND + hl + 16 * q];
+    }
+    const Rep& rp = reps[sy.rep];
+    __syncwarp();
+
+    for (int sl = hl; sl < n; sl += 16) {
+        const int j = nbr[(size_t)b * maxnb + sl];
+        const float4 xj = x[sy.ba0 + j];
+        float dx, dy, dz;
+        pair_vec(rp, xi, xj, dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r = sqrtf(r2);
+        const float ir = 1.0f / r;
+        float fc, dfc;
+        cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+        float dEdr = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            const float t = r - dp.r_mu[c];
+            const float e = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t);
+            dEdr += gsh[hw][c] * e * (-2.0f * dp.eta_R * t * fc + dfc);
+        }
+        float a[4], da[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float ex = gauss<FAST>(dp.eta_A[e], dp.eta_A_l2[e], r2);
+            a[e] = ex * fc;
+            da[e] = ex * (-2.0f * dp.eta_A[e] * r * fc + dfc);
+        }
+        U[hw][sl] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        A[hw][sl] = make_float4(a[0], a[1], a[2], a[3]);
+        DA[hw][sl] = make_float4(da[0], da[1], da[2], da[3]);
+        RAD[hw][sl] = dEdr;
+    }
+    __syncwarp();
+
+    AdjCoef<float> gp;
+    coef_load(gp, gsh[hw]);
+    float red[12];   // force on the centre (3), virial (9)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) red[q] = 0.0f;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+        const int sj = hl + 16 * jj;
+        if (sj < n) {
+            const float4 uj = U[hw][sj], aj = A[hw][sj];
+            float jd[8], kd[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) jd[q] = kd[q] = 0.0f;
+            for (int k = 0; k < n; ++k)
+                if (k != sj) adj_pair(gp, uj, aj, U[hw][k], A[hw][k], jd, kd);
+            const float4 da = DA[hw][sj];
+            const float dEdr = RAD[hw][sj] + jd[0] * da.x + jd[1] * da.y + jd[2] * da.z + jd[3] * da.w;
+            const float ir = 1.0f / uj.w;
+            const float v[3] = {dEdr * uj.x + (jd[4] - jd[7] * uj.x) * ir, dEdr * uj.y + (jd[5] - jd[7] * uj.y) * ir,
+                                dEdr * uj.z + (jd[6] - jd[7] * uj.z) * ir};
+            if (det)
+                vbuf[(size_t)b * maxnb + sj] = make_float4(v[0], v[1], v[2], 0.0f);
+            else
+                atomic_add_vec(&f[sy.ba0 + nbr[(size_t)b * maxnb + sj]], -v[0], -v[1], -v[2]);
+            const float d3[3] = {uj.x * uj.w, uj.y * uj.w, uj.z * uj.w};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                red[a] += v[a];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) red[3 + 3 * a + c] -= d3[a] * v[c];
+            }
+        }
+    }
+    // sums over the 16 lanes of the half
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 12; ++q) red[q] += __shfl_xor_sync(0xffffffffu, red[q], o);
+    if (live && hl == 0) {
+        if (det)
+            f[b] = make_float4(red[0], red[1], red[2], 0.0f);   // gathered later
+        else
+            atomic_add_vec(&f[b], red[0], red[1], red[2]);
+    }
+    if (live && hl < 9) {
+        float mine = red[3];
+#pragma unroll
+        for (int q = 1; q < 9; ++q)
+            if (hl == q) mine = red[3 + q];
+        wbuf[(size_t)b * 9 + hl] = mine;
+    }
+}
+
+template <bool FAST>
+static void run_adj_small(const Dev& d, const void* dpv, cudaStream_t st)
+{
+    desc_adj_small_kernel<FAST><<<(d.B + SMALL_ATOMS - 1) / SMALL_ATOMS, 256, 0, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B, *(const DescParams<float>*)dpv,
+        (const float*)d.dEdG, (float4*)d.f, (float*)d.wbuf, d.deterministic, (float4*)d.vbuf);
+}
+
 bool adjoint_sums_energy(const Dev& d, const void* dpv)
 {
     return d.precision != 0 && d.sched.ang && d.mom && moment_adjoint_sums_energy(d, dpv);
@@ -765,6 +896,9 @@ void launch_adjoint(const Dev& d, const void* dpv, cudaStream_t st)
             (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
             *(const DescParams<double>*)dpv, d.sched, (const double*)d.dEdG, (Dbl4*)d.f, (double*)d.wbuf,
             d.deterministic, (Dbl4*)d.vbuf);
+    } else if (d.max_N <= SMALL_SL + 1) {
+        if (d.precision == 2) run_adj_small<true>(d, dpv, st);
+        else run_adj_small<false>(d, dpv, st);
     } else if (d.precision == 2) {
         run_adj_f32<true>(d, dpv, st);
     } else {
