@@ -1140,74 +1140,107 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v)
 template <typename Real>
 __global__ void __launch_bounds__(256) energy_reduce_kernel(const Real* __restrict__ Eatom,
                                                             const Real* __restrict__ wbuf,
-                                                            const BeadSys* __restrict__ bsys, int S,
+                                                            const BeadSys* __restrict__ bsys, int S, int wpb,
                                                             double* __restrict__ V, double* __restrict__ Wv)
 {
-    // warp per bead: the energy and the 9 virial entries, summed over the
-    // bead's atoms in a fixed order (lane-strided, then a fixed butterfly);
-    // FP64 terms in FP64, FP32 terms as double-float pairs rounded to FP64
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // wpb warps per bead (8 / wpb beads per 256-thread block): the energy and
+    // the 9 virial entries summed over the bead's atoms in a fixed order
+    // (atoms strided over the bead's lanes, a fixed butterfly per warp, the
+    // warps' partials in warp order). FP64 terms in FP64; FP32 terms as
+    // double-float pairs, rounded to FP64 at the end.
+    __shared__ double part[8][10][2];
+    const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    if (s >= S) return;
-    const BeadSys sy = bsys[s];
-    double out[10];
+    const int s = blockIdx.x * (8 / wpb) + w / wpb, sub = w % wpb;
+    const bool live = s < S;
+    const BeadSys sy = live ? bsys[s] : BeadSys{0, 0, 0, 0};
+    double hi[10], lo[10];
     if constexpr (std::is_same<Real, double>::value) {
 #pragma unroll
-        for (int q = 0; q < 10; ++q) out[q] = 0.0;
-        for (int i = (int)lane; i < sy.N; i += 32) {
+        for (int q = 0; q < 10; ++q) hi[q] = lo[q] = 0.0;
+        for (int i = sub * 32 + (int)lane; i < sy.N; i += 32 * wpb) {
             const size_t b = (size_t)(sy.ba0 + i);
-            out[0] += Eatom[b];
+            hi[0] += Eatom[b];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) out[1 + q] += wbuf[b * 9 + q];
+            for (int q = 0; q < 9; ++q) hi[1 + q] += wbuf[b * 9 + q];
         }
 #pragma unroll
-        for (int q = 0; q < 10; ++q) out[q] = warp_sum(out[q]);
+        for (int q = 0; q < 10; ++q) hi[q] = warp_sum(hi[q]);
     } else {
-        float hi[10], lo[10];
+        float fh[10], fl[10];
 #pragma unroll
-        for (int q = 0; q < 10; ++q) hi[q] = lo[q] = 0.0f;
-        for (int i = (int)lane; i < sy.N; i += 32) {
+        for (int q = 0; q < 10; ++q) fh[q] = fl[q] = 0.0f;
+        for (int i = sub * 32 + (int)lane; i < sy.N; i += 32 * wpb) {
             const size_t b = (size_t)(sy.ba0 + i);
-            df_add(hi[0], lo[0], (float)Eatom[b]);
+            df_add(fh[0], fl[0], (float)Eatom[b]);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) df_add(hi[1 + q], lo[1 + q], (float)wbuf[b * 9 + q]);
+            for (int q = 0; q < 9; ++q) df_add(fh[1 + q], fl[1 + q], (float)wbuf[b * 9 + q]);
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1)
 #pragma unroll
             for (int q = 0; q < 10; ++q) {
-                const float oh = __shfl_xor_sync(0xffffffffu, hi[q], o);
-                const float ol = __shfl_xor_sync(0xffffffffu, lo[q], o);
+                const float oh = __shfl_xor_sync(0xffffffffu, fh[q], o);
+                const float ol = __shfl_xor_sync(0xffffffffu, fl[q], o);
                 // both partners add in the same order (lower lane's pair first)
                 const bool upper = (lane & o) != 0;
-                float h = upper ? oh : hi[q], l = upper ? ol : lo[q];
-                df_add(h, l, upper ? hi[q] : oh);
-                l = __fadd_rn(l, upper ? lo[q] : ol);
-                hi[q] = h;
-                lo[q] = l;
+                float h = upper ? oh : fh[q], l = upper ? ol : fl[q];
+                df_add(h, l, upper ? fh[q] : oh);
+                l = __fadd_rn(l, upper ? fl[q] : ol);
+                fh[q] = h;
+                fl[q] = l;
             }
 #pragma unroll
-        for (int q = 0; q < 10; ++q) out[q] = (double)hi[q] + (double)lo[q];
+        for (int q = 0; q < 10; ++q) {
+            hi[q] = (double)fh[q];
+            lo[q] = (double)fl[q];
+        }
     }
-    if (lane == 0) V[s] = out[0];
-    if (lane >= 1 && lane < 10) {
-        double mine = out[1];
+    if (wpb > 1) {
+        if (lane == 0) {
 #pragma unroll
-        for (int q = 2; q < 10; ++q)
-            if ((int)lane == q) mine = out[q];
-        Wv[(size_t)s * 9 + lane - 1] = mine;
+            for (int q = 0; q < 10; ++q) {
+                part[w][q][0] = hi[q];
+                part[w][q][1] = lo[q];
+            }
+        }
+        __syncthreads();
+        if (sub != 0 || !live) return;
+        if (lane < 10) {
+            double h = 0.0, l = 0.0;
+            for (int t = 0; t < wpb; ++t) {
+                h += part[w + t][lane][0];
+                l += part[w + t][lane][1];
+            }
+            const double tot = h + l;
+            if (lane == 0) V[s] = tot;
+            else Wv[(size_t)s * 9 + lane - 1] = tot;
+        }
+        return;
+    }
+    if (!live) return;
+    if (lane < 10) {
+        double mine = hi[0] + lo[0];
+#pragma unroll
+        for (int q = 1; q < 10; ++q)
+            if ((int)lane == q) mine = hi[q] + lo[q];
+        if (lane == 0) V[s] = mine;
+        else Wv[(size_t)s * 9 + lane - 1] = mine;
     }
 }
 
 void launch_energy_reduce(const Dev& d, cudaStream_t st)
 {
-    const int blocks = (d.S + 7) / 8;
+    // warps per bead from the largest bead: one up to 64 atoms, up to 8
+    const int wpb = d.max_N <= 64 ? 1 : d.max_N <= 256 ? 2 : d.max_N <= 1024 ? 4 : 8;
+    const int bpb = 8 / wpb;
+    const int blocks = (d.S + bpb - 1) / bpb;
     if (d.precision == 0)
         energy_reduce_kernel<double><<<blocks, 256, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
-                                                             d.V, d.W);
+                                                             wpb, d.V, d.W);
     else
         energy_reduce_kernel<float><<<blocks, 256, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
-                                                            d.V, d.W);
+                                                            wpb, d.V, d.W);
 }
 
 // ---------------------------------------------------------------------------
