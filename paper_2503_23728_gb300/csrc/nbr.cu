@@ -94,12 +94,16 @@ __global__ void cell_build_kernel(const V4* __restrict__ x, const BeadSys* __res
 // Neighbours of bead-atom il (FP32 position xi) with rule radius r2cut, in
 // ascending order into out[0 .. cap); returns the count (may exceed cap).
 // Beads without cells scan all their atoms; beads with cells scan the 27
-// stencil cells and sort what passes (L: the warp's shared sort buffer).
+// stencil cells and order what passes: through a bitmap over the bead's atom
+// indices when the bead has at most 32 x NBR_BM_WORDS atoms (BM: the warp's
+// shared bitmap), else by a bitonic sort (L: the warp's shared sort buffer).
+constexpr int NBR_BM_WORDS = 512;   // bitmap words per warp: beads of up to 16,384 atoms
+
 template <typename V4>
 __device__ int scan_list(const V4* __restrict__ x, const BeadSys& sy, const Rep& rp, int il, const float3& xi,
                          const int* __restrict__ cell_start, const int* __restrict__ cell_cnt,
                          const int* __restrict__ cell_atoms, float r2cut, int* __restrict__ out, int cap, int* L,
-                         unsigned lane)
+                         unsigned* BM, unsigned lane)
 {
     int cnt = 0;
     if (rp.ncells == 0) {
@@ -133,6 +137,12 @@ __device__ int scan_list(const V4* __restrict__ x, const BeadSys& sy, const Rep&
             if ((int)lane >= o) incl += v;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int words = (sy.N + 31) >> 5;
+        const bool use_bm = words <= NBR_BM_WORDS;
+        if (use_bm) {
+            for (int w = (int)lane; w < words; w += 32) BM[w] = 0u;
+            __syncwarp();
+        }
         for (int t0 = 0; t0 < total; t0 += 32) {
             const int t = t0 + (int)lane;
             // stencil cell of candidate t: first s with incl[s] > t
@@ -152,11 +162,40 @@ __device__ int scan_list(const V4* __restrict__ x, const BeadSys& sy, const Rep&
                 in = j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), r2cut);
             }
             const unsigned m = __ballot_sync(0xffffffffu, in);
-            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-            if (in && pos < cap) L[pos] = j;
+            if (use_bm) {
+                if (in) atomicOr(&BM[j >> 5], 1u << (j & 31));
+            } else {
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                if (in && pos < cap) L[pos] = j;
+            }
             cnt += __popc(m);
         }
         __syncwarp();
+        if (use_bm) {
+            // ascending order: 32 bitmap words at a time, lane -> word, the
+            // words' set bits placed by a prefix sum of their counts
+            int base = 0;
+            for (int w0 = 0; w0 < words; w0 += 32) {
+                const int w = w0 + (int)lane;
+                unsigned wv = w < words ? BM[w] : 0u;
+                const int pc = __popc(wv);
+                int inc = pc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                    if ((int)lane >= o) inc += v;
+                }
+                int pos = base + inc - pc;
+                while (wv) {
+                    const int bit = __ffs(wv) - 1;
+                    if (pos < cap) out[pos] = (w << 5) + bit;
+                    ++pos;
+                    wv &= wv - 1u;
+                }
+                base += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            return cnt;
+        }
         // ascending order: bitonic sort over the next power of two, padded
         const int m = cnt < cap ? cnt : cap;
         int n2 = 1;
@@ -244,6 +283,7 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
                                                   const int* __restrict__ rebuild, int maxcand)
 {
     __shared__ int lst[8][PIMD_SORT_CAP];
+    __shared__ unsigned bmap[8][NBR_BM_WORDS];
     const int wib = threadIdx.x >> 5;
     const int b = blockIdx.x * (blockDim.x >> 5) + wib;
     const unsigned lane = lane_id();
@@ -259,7 +299,7 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
         int* cl = cand + (size_t)b * maxcand;
         int nc;
         if (rebuild[bs]) {
-            nc = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rp.rcs2, cl, maxcand, lst[wib], lane);
+            nc = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rp.rcs2, cl, maxcand, lst[wib], bmap[wib], lane);
             if (lane == 0) {
                 ncand[b] = nc;
                 xref[b] = make_float4(xi.x, xi.y, xi.z, 0.0f);
@@ -294,10 +334,10 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
                 }
             }
         } else {
-            cnt = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rc2, out, maxnb, lst[wib], lane);
+            cnt = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rc2, out, maxnb, lst[wib], bmap[wib], lane);
         }
     } else {
-        cnt = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rc2, out, maxnb, lst[wib], lane);
+        cnt = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rc2, out, maxnb, lst[wib], bmap[wib], lane);
     }
     if (lane == 0) {
         nnb[b] = cnt;
