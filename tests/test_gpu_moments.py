@@ -183,3 +183,44 @@ def test_deterministic_moments_bit_identical(water64_model):
         _, f, v = ctx.energy_forces(x)
         outs.append((f.cpu().numpy(), v.cpu().numpy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_bf16_adjoint_deterministic_mode_and_summed_virial(water64_model):
+    """BF16 moment adjoint (two neighbours per lane, one-level fold). In
+    deterministic mode (pair vectors gathered per atom, energies and virials
+    reduced in a fixed order) two runs are bit-identical. They agree with the
+    default mode, whose adjoint adds the per-bead energies and virials itself
+    (FP64 atomics) and scatters forces with FP32 atomics: only the summation
+    order differs. The virial equals the BF16 pair-sum path's (same network).
+    It is 3.7e-2 (relative RMS) from the FP64 oracle, the diagonal ~3.5 %
+    low, on both BF16 paths: they share only the BF16 network, and the FP32
+    path is within 1e-5. Forces keep the 1e-2 bar, but the virial diagonal
+    adds the network's errors up without cancellation."""
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 4)
+    xb = _beads(rep, 4, seed=31)
+    x = torch.tensor(xb.reshape(-1, 3), device="cuda")
+    runs = []
+    for det in (False, True, True):
+        c = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="bf16_tc", widths=w.widths, deterministic=det)
+        c.set_weights(m)
+        assert c.angular == "moments"
+        e, f, v = c.energy_forces(x)
+        runs.append((e.cpu().numpy(), f.cpu().numpy(), v.cpu().numpy()))
+        c.close()
+    (e0, f0, v0), (e1, f1, v1), (e2, f2, v2) = runs
+    assert np.array_equal(e1, e2) and np.array_equal(f1, f2) and np.array_equal(v1, v2)
+    assert _relmax(f0, f1) < 1e-5
+    assert np.abs(e0 - e1).max() < 1e-9 * max(1.0, float(np.abs(e1).max()))
+    assert _relmax(v0, v1) < 1e-6
+    c = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="bf16_tc", widths=w.widths)
+    c.set_weights(m)
+    c.set_angular("pairs")
+    _, _, vp = c.energy_forces(x)
+    vp = vp.cpu().numpy()
+    c.close()
+    assert np.sqrt(((v0 - vp) ** 2).mean() / (vp ** 2).mean()) < 2e-3
+    _, _, Wo = O.energy_forces_batch(m, rep.Z, xb, rep.box)
+    Wo = np.asarray(Wo).reshape(v0.shape)
+    assert np.sqrt(((v0 - Wo) ** 2).mean() / (Wo ** 2).mean()) < 5e-2
