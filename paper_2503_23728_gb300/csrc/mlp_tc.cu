@@ -446,7 +446,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
                     for (int g = 0; g < 2; ++g)
                         *reinterpret_cast<uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, W)) =
                             make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
-                    tmem_st8(lane_base + (uint32_t)(TACC + (l - 1) * (W / 2) + (c0 >> 1)), pk);
+                    // parked for the backward: tanh' = 1 - h^2 from the FP32 h,
+                    // rounded once (from a BF16 h it loses its digits where
+                    // the unit saturates)
+                    uint32_t dk[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        dk[t] = pack_bf16(1.0f - h[2 * t] * h[2 * t], 1.0f - h[2 * t + 1] * h[2 * t + 1]);
+                    tmem_st8(lane_base + (uint32_t)(TACC + (l - 1) * (W / 2) + (c0 >> 1)), dk);
                 } else {
                     float ga[16];
 #pragma unroll
@@ -462,14 +469,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
                                        pack_bf16(ga[8 * g + 4], ga[8 * g + 5]), pack_bf16(ga[8 * g + 6], ga[8 * g + 7]));
                 }
             } else if (l > 1) {
-                // dE/da_(l-1) = (W_l^T dE/da_l) * (1 - h_(l-1)^2), h_(l-1) from its parking place
+                // dE/da_(l-1) = (W_l^T dE/da_l) * (1 - h_(l-1)^2), the derivative from its parking place
                 uint32_t hw[8];
                 tmem_ld8(lane_base + (uint32_t)(TACC + (l - 2) * (W / 2) + (c0 >> 1)), hw);
                 uint32_t pk[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const float2 hh = unpack_bf16(hw[t]);
-                    pk[t] = pack_bf16(v[2 * t] * (1.0f - hh.x * hh.x), v[2 * t + 1] * (1.0f - hh.y * hh.y));
+                    const float2 dd = unpack_bf16(hw[t]);
+                    pk[t] = pack_bf16(v[2 * t] * dd.x, v[2 * t + 1] * dd.y);
                 }
 #pragma unroll
                 for (int g = 0; g < 2; ++g)
@@ -716,7 +723,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
                     for (int g = 0; g < 2; ++g)
                         *reinterpret_cast<uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, WW)) =
                             make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
-                    if (l <= L - 2) tmem_st8(lane_base + 256u + 128u * (uint32_t)(l - 1) + (uint32_t)(c0 >> 1), pk);
+                    if (l <= L - 2) {
+                        // parked for the backward: tanh' = 1 - h^2 from the FP32 h
+                        uint32_t dk[8];
+#pragma unroll
+                        for (int t = 0; t < 8; ++t)
+                            dk[t] = pack_bf16(1.0f - h[2 * t] * h[2 * t], 1.0f - h[2 * t + 1] * h[2 * t + 1]);
+                        tmem_st8(lane_base + 256u + 128u * (uint32_t)(l - 1) + (uint32_t)(c0 >> 1), dk);
+                    }
                 } else {
                     float ga[16];
 #pragma unroll
@@ -732,9 +746,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
                                        pack_bf16(ga[8 * g + 4], ga[8 * g + 5]), pack_bf16(ga[8 * g + 6], ga[8 * g + 7]));
                 }
             } else if (l > 1) {
-                // h_{l-1}: h_{L-1} is still in ACT; earlier ones were parked in TMEM
+                // tanh'(a_{l-1}): h_{L-1} is still in ACT (BF16 h); earlier
+                // layers parked 1 - h^2 in TMEM
                 uint32_t hw[8];
-                if (l - 1 == L - 1) {
+                const bool from_act = l - 1 == L - 1;
+                if (from_act) {
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {
                         const uint4 u = *reinterpret_cast<const uint4*>(ACT + 2 * cm_index(row, c0 + 8 * g, WW));
@@ -747,7 +763,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const float2 hh = unpack_bf16(hw[t]);
-                    pk[t] = pack_bf16(v[2 * t] * (1.0f - hh.x * hh.x), v[2 * t + 1] * (1.0f - hh.y * hh.y));
+                    const float2 dd = from_act ? make_float2(1.0f - hh.x * hh.x, 1.0f - hh.y * hh.y) : hh;
+                    pk[t] = pack_bf16(v[2 * t] * dd.x, v[2 * t + 1] * dd.y);
                 }
 #pragma unroll
                 for (int g = 0; g < 2; ++g)
