@@ -253,6 +253,106 @@ __global__ void __launch_bounds__(256, 4) desc_fwd_kernel(
     G[(size_t)b * ND + NR + lane] = Ga;
 }
 
+// ---------------------------------------------------------------------------
+// Descriptors for small clusters: every replica has at most 33 atoms, so n <= 32
+// neighbours. Half a warp per bead-atom (two per warp): lanes l and l + 16 of
+// the half take the neighbours' radial terms and weights, and the unordered
+// pairs are walked over the half's 16 lanes. The arithmetic is that of
+// desc_fwd_kernel. A whole warp per atom would leave the lanes beyond n idle
+// in the neighbour phase; these clusters have 5-23 neighbours.
+// ---------------------------------------------------------------------------
+constexpr int SMALL_SL = 32;    // neighbour slots per atom
+constexpr int SMALL_ATOMS = 16; // bead-atoms per 256-thread block
+
+// Sums over the 16 lanes of a half warp of 32 per-lane values: lane l of the
+// half ends with the totals of values 2l (v[0]) and 2l + 1 (v[1]).
+__device__ __forceinline__ void half_reduce32(float (&v)[32], int hl)
+{
+#pragma unroll
+    for (int o = 8, n = 32; o >= 1; o >>= 1, n >>= 1) {
+        const bool upper = (hl & o) != 0;
+#pragma unroll
+        for (int q = 0; q < n / 2; ++q) {
+            const float send = upper ? v[q] : v[q + n / 2];
+            const float keep = upper ? v[q + n / 2] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
+template <bool FAST>
+__global__ void __launch_bounds__(256) desc_fwd_small_kernel(
+    const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
+    const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
+    DescParams<float> dp, float* __restrict__ G)
+{
+    __shared__ float4 U[SMALL_ATOMS][SMALL_SL], A[SMALL_ATOMS][SMALL_SL];
+    const int hw = threadIdx.x >> 4;
+    const int hl = threadIdx.x & 15;
+    const int b = blockIdx.x * SMALL_ATOMS + hw;
+    // no early return: the two halves of a warp meet in the shuffles
+    const bool live = b < B;
+    int n = 0;
+    BeadSys sy{0, 0, 0, 0};
+    float4 xi = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (live) {
+        sy = bsys[ba_sys[b]];
+        n = min(nnb[b], min(maxnb, SMALL_SL));
+        xi = x[b];
+    }
+    const Rep& rp = reps[sy.rep];
+
+    float gr[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) gr[c] = 0.0f;
+    for (int sl = hl; sl < n; sl += 16) {
+        const int j = nbr[(size_t)b * maxnb + sl];
+        const float4 xj = x[sy.ba0 + j];
+        float dx, dy, dz;
+        pair_vec(rp, xi, xj, dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r = sqrtf(r2);
+        const float ir = 1.0f / r;
+        float fc, dfc;
+        cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            const float t = r - dp.r_mu[c];
+            gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+        }
+        U[hw][sl] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        A[hw][sl] = make_float4(gauss<FAST>(dp.eta_A[0], dp.eta_A_l2[0], r2) * fc,
+                                gauss<FAST>(dp.eta_A[1], dp.eta_A_l2[1], r2) * fc,
+                                gauss<FAST>(dp.eta_A[2], dp.eta_A_l2[2], r2) * fc,
+                                gauss<FAST>(dp.eta_A[3], dp.eta_A_l2[3], r2) * fc);
+    }
+    half_reduce32(gr, hl);
+    __syncwarp();
+
+    FwdAcc<float> acc;
+    acc_zero(acc);
+    PairWalk w;
+    w.init(n, hl);
+    for (; w.valid(); w.advance(16)) {
+        const int k = w.k();
+        fwd_pair(U[hw][w.j], A[hw][w.j], U[hw][k], A[hw][k], acc);
+    }
+    float ga[NA];
+    acc_out(acc, ga);
+    half_reduce32(ga, hl);
+    if (live) {
+        // channels 2 hl and 2 hl + 1; 2^(1 - zeta) for zeta = 1, 2, 4, 8 (zeta index = channel / 8)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int ch = 2 * hl + k;
+            const int zi = ch >> 3;
+            const float sc = zi == 0 ? 1.0f : zi == 1 ? 0.5f : zi == 2 ? 0.125f : 0.0078125f;
+            G[(size_t)b * ND + ch] = gr[k];
+            G[(size_t)b * ND + NR + ch] = ga[k] * sc;
+        }
+    }
+}
+
 template <typename Real>
 static int desc_warps(int maxnb)
 {
@@ -287,6 +387,15 @@ void launch_descriptors(const Dev& d, const void* dpv, cudaStream_t st)
         desc_fwd_kernel<double, false><<<(d.B + w - 1) / w, 32 * w, sm, st>>>(
             (const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
             *(const DescParams<double>*)dpv, d.sched, (double*)d.G);
+    } else if (d.max_N <= SMALL_SL + 1) {
+        if (d.precision == 2)
+            desc_fwd_small_kernel<true><<<(d.B + SMALL_ATOMS - 1) / SMALL_ATOMS, 256, 0, st>>>(
+                (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+                *(const DescParams<float>*)dpv, (float*)d.G);
+        else
+            desc_fwd_small_kernel<false><<<(d.B + SMALL_ATOMS - 1) / SMALL_ATOMS, 256, 0, st>>>(
+                (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+                *(const DescParams<float>*)dpv, (float*)d.G);
     } else if (d.precision == 2) {
         run_desc_f32<true>(d, dpv, st);
     } else {
@@ -754,8 +863,6 @@ static void run_adj_f32(const Dev& d, const void* dpv, cudaStream_t st)
 // atom would leave the lanes beyond n idle: these clusters have 5-23
 // neighbours.
 // ---------------------------------------------------------------------------
-constexpr int SMALL_SL = 32;   // neighbour slots per atom
-constexpr int SMALL_ATOMS = 16; // bead-atoms per 256-thread block
 
 template <bool FAST>
 __global__ void __launch_bounds__(256) desc_adj_small_kernel(
