@@ -857,26 +857,34 @@ static void run_adj_f32(const Dev& d, const void* dpv, cudaStream_t st)
 
 // ---------------------------------------------------------------------------
 // Adjoint for small clusters: every replica has at most 33 atoms, so n <= 32
-// neighbours. Half a warp per bead-atom (two per warp), ordered pairs (each
-// lane owns neighbours j = l and l + 16 and sums over all k != j), the same
-// arithmetic as desc_adj_kernel's ordered-pair schedule. A whole warp per
-// atom would leave the lanes beyond n idle: these clusters have 5-23
-// neighbours.
+// neighbours. Half a warp per bead-atom (two per warp); lane l of the half
+// owns neighbour slots l and l + 16. The unordered pairs are walked along
+// the diagonals (p, p + d mod n), d = 1 .. n/2 (for even n the last one only
+// from p < n/2): each slot adds its own side of the pair in registers and
+// hands the other side to slot p + d through shared memory, which every
+// slot receives from exactly one sender per diagonal (no atomics). The pair
+// arithmetic is that of desc_adj_kernel. A whole warp per atom would leave
+// the lanes beyond n idle; these clusters have 5-23 neighbours.
 // ---------------------------------------------------------------------------
 
+constexpr int SMALL_ADJ_ATOMS = 8;   // bead-atoms per 128-thread block (shared memory under 48 KB)
+
 template <bool FAST>
-__global__ void __launch_bounds__(256) desc_adj_small_kernel(
+__global__ void __launch_bounds__(32 * SMALL_ADJ_ATOMS / 2) desc_adj_small_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, const float* __restrict__ dEdG, float4* __restrict__ f, float* __restrict__ wbuf,
     int det, float4* __restrict__ vbuf)
 {
-    __shared__ float4 U[SMALL_ATOMS][SMALL_SL], A[SMALL_ATOMS][SMALL_SL], DA[SMALL_ATOMS][SMALL_SL];
-    __shared__ float RAD[SMALL_ATOMS][SMALL_SL];
-    __shared__ float gsh[SMALL_ATOMS][ND];
+    __shared__ float4 U[SMALL_ADJ_ATOMS][SMALL_SL], A[SMALL_ADJ_ATOMS][SMALL_SL], DA[SMALL_ADJ_ATOMS][SMALL_SL];
+    __shared__ float4 KD[SMALL_ADJ_ATOMS][SMALL_SL][2];   // the other side of a pair, per receiving slot
+    __shared__ float4 RGs[SMALL_ADJ_ATOMS][16];
+    __shared__ float RAD[SMALL_ADJ_ATOMS][SMALL_SL];
+    __shared__ float gsh[SMALL_ADJ_ATOMS][ND];
     const int hw = threadIdx.x >> 4;
     const int hl = threadIdx.x & 15;
-    const int b = blockIdx.x * SMALL_ATOMS + hw;
+    const unsigned hmask = 0xffffu << (16 * (hw & 1));
+    const int b = blockIdx.x * SMALL_ADJ_ATOMS + hw;
     // no early return: the two halves of a warp meet in __syncwarp
     const bool live = b < B;
     int n = 0;
@@ -890,6 +898,14 @@ __global__ void __launch_bounds__(256) desc_adj_small_kernel(
         for (int q = 0; q < ND / 16; ++q) gsh[hw][hl + 16 * q] = dEdG[(size_t)b * ND + hl + 16 * q];
     }
     const Rep& rp = reps[sy.rep];
+    // BF16 path, evenly spaced centres: (gs_c, gs_(c+16), gs_c r_c, gs_(c+16) r_(c+16))
+    // for the product recurrence of the radial sums
+    const bool packed = FAST && dp.r_even;
+    if (packed && live) {
+        const int c = (hl >> 3) * 8 + (hl & 7);   // 0..7, 8..15
+        const float ga = dEdG[(size_t)b * ND + c], gb = dEdG[(size_t)b * ND + c + 16];
+        RGs[hw][hl] = make_float4(ga, gb, ga * dp.r_mu[c], gb * dp.r_mu[c + 16]);
+    }
     __syncwarp();
 
     for (int sl = hl; sl < n; sl += 16) {
@@ -903,11 +919,38 @@ __global__ void __launch_bounds__(256) desc_adj_small_kernel(
         float fc, dfc;
         cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
         float dEdr = 0.0f;
+        if (packed) {
+            // sum_c gs_c g_c (-2 eta (r - r_c) fc + dfc) = (-2 eta r fc + dfc) s1 + 2 eta fc s2,
+            // s1 = sum gs_c g_c, s2 = sum gs_c r_c g_c; g_c by the recurrence of radial_gauss32
+            // on the centre pairs (c, c + 16)
+            float2 a1 = make_float2(0.0f, 0.0f), a2 = a1;
+            const float2 rho = make_float2(dp.rec_k, dp.rec_k);
+            const float dd = dp.r_delta * dp.r_delta;
 #pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            const float t = r - dp.r_mu[c];
-            const float e = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t);
-            dEdr += gsh[hw][c] * e * (-2.0f * dp.eta_R * t * fc + dfc);
+            for (int qp = 0; qp < 2; ++qp) {
+                const float ta = r - dp.r_mu[8 * qp], tb = r - dp.r_mu[8 * qp + 16];
+                float2 e2 = make_float2(exp2f(-dp.eta_R_l2 * ta * ta), exp2f(-dp.eta_R_l2 * tb * tb));
+                float2 R2 = make_float2(exp2f(dp.eta_R_l2 * fmaf(2.0f * ta, dp.r_delta, -dd)),
+                                        exp2f(dp.eta_R_l2 * fmaf(2.0f * tb, dp.r_delta, -dd)));
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float4 g = RGs[hw][qp * 8 + k];
+                    a1 = __ffma2_rn(e2, make_float2(g.x, g.y), a1);
+                    a2 = __ffma2_rn(e2, make_float2(g.z, g.w), a2);
+                    if (k < 7) {
+                        e2 = __fmul2_rn(e2, R2);
+                        R2 = __fmul2_rn(R2, rho);
+                    }
+                }
+            }
+            dEdr = (a1.x + a1.y) * fmaf(-2.0f * dp.eta_R * r, fc, dfc) + 2.0f * dp.eta_R * fc * (a2.x + a2.y);
+        } else {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const float t = r - dp.r_mu[c];
+                const float e = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t);
+                dEdr += gsh[hw][c] * e * (-2.0f * dp.eta_R * t * fc + dfc);
+            }
         }
         float a[4], da[4];
 #pragma unroll
@@ -925,6 +968,39 @@ __global__ void __launch_bounds__(256) desc_adj_small_kernel(
 
     AdjCoef<float> gp;
     coef_load(gp, gsh[hw]);
+    float jd[2][8];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) jd[rr][q] = 0.0f;
+    for (int d = 1; 2 * d <= n; ++d) {   // uniform within the half
+        const bool last = 2 * d == n;    // even n: pairs (p, p + n/2) from p < n/2 only
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int sp = hl + 16 * rr;
+            if (sp < n && (!last || sp < d)) {
+                int sq = sp + d;
+                sq = sq >= n ? sq - n : sq;
+                float kd[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) kd[q] = 0.0f;
+                adj_pair(gp, U[hw][sp], A[hw][sp], U[hw][sq], A[hw][sq], jd[rr], kd);
+                KD[hw][sq][0] = make_float4(kd[0], kd[1], kd[2], kd[3]);
+                KD[hw][sq][1] = make_float4(kd[4], kd[5], kd[6], kd[7]);
+            }
+        }
+        __syncwarp(hmask);
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int sp = hl + 16 * rr;
+            if (sp < n && (!last || sp >= d)) {
+                const float4 k0 = KD[hw][sp][0], k1 = KD[hw][sp][1];
+                jd[rr][0] += k0.x; jd[rr][1] += k0.y; jd[rr][2] += k0.z; jd[rr][3] += k0.w;
+                jd[rr][4] += k1.x; jd[rr][5] += k1.y; jd[rr][6] += k1.z; jd[rr][7] += k1.w;
+            }
+        }
+        __syncwarp(hmask);
+    }
     float red[12];   // force on the centre (3), virial (9)
 #pragma unroll
     for (int q = 0; q < 12; ++q) red[q] = 0.0f;
@@ -932,17 +1008,13 @@ __global__ void __launch_bounds__(256) desc_adj_small_kernel(
     for (int jj = 0; jj < 2; ++jj) {
         const int sj = hl + 16 * jj;
         if (sj < n) {
-            const float4 uj = U[hw][sj], aj = A[hw][sj];
-            float jd[8], kd[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) jd[q] = kd[q] = 0.0f;
-            for (int k = 0; k < n; ++k)
-                if (k != sj) adj_pair(gp, uj, aj, U[hw][k], A[hw][k], jd, kd);
+            const float4 uj = U[hw][sj];
             const float4 da = DA[hw][sj];
-            const float dEdr = RAD[hw][sj] + jd[0] * da.x + jd[1] * da.y + jd[2] * da.z + jd[3] * da.w;
+            const float dEdr = RAD[hw][sj] + jd[jj][0] * da.x + jd[jj][1] * da.y + jd[jj][2] * da.z + jd[jj][3] * da.w;
             const float ir = 1.0f / uj.w;
-            const float v[3] = {dEdr * uj.x + (jd[4] - jd[7] * uj.x) * ir, dEdr * uj.y + (jd[5] - jd[7] * uj.y) * ir,
-                                dEdr * uj.z + (jd[6] - jd[7] * uj.z) * ir};
+            const float v[3] = {dEdr * uj.x + (jd[jj][4] - jd[jj][7] * uj.x) * ir,
+                                dEdr * uj.y + (jd[jj][5] - jd[jj][7] * uj.y) * ir,
+                                dEdr * uj.z + (jd[jj][6] - jd[jj][7] * uj.z) * ir};
             if (det)
                 vbuf[(size_t)b * maxnb + sj] = make_float4(v[0], v[1], v[2], 0.0f);
             else
@@ -979,7 +1051,7 @@ __global__ void __launch_bounds__(256) desc_adj_small_kernel(
 template <bool FAST>
 static void run_adj_small(const Dev& d, const void* dpv, cudaStream_t st)
 {
-    desc_adj_small_kernel<FAST><<<(d.B + SMALL_ATOMS - 1) / SMALL_ATOMS, 256, 0, st>>>(
+    desc_adj_small_kernel<FAST><<<(d.B + SMALL_ADJ_ATOMS - 1) / SMALL_ADJ_ATOMS, 16 * SMALL_ADJ_ATOMS, 0, st>>>(
         (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B, *(const DescParams<float>*)dpv,
         (const float*)d.dEdG, (float4*)d.f, (float*)d.wbuf, d.deterministic, (float4*)d.vbuf);
 }
