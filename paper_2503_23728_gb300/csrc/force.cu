@@ -302,9 +302,12 @@ __global__ void __launch_bounds__(256) desc_fwd_small_kernel(
     }
     const Rep& rp = reps[sy.rep];
 
-    float gr[NR];
+    // radial sums; on the BF16 path with evenly spaced centres the product
+    // recurrence of radial_gauss32 runs on centre pairs (c, c + 16), packed
+    const bool packed = FAST && dp.r_even;
+    float2 gr2[NR / 2];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) gr[c] = 0.0f;
+    for (int c = 0; c < NR / 2; ++c) gr2[c] = make_float2(0.0f, 0.0f);
     for (int sl = hl; sl < n; sl += 16) {
         const int j = nbr[(size_t)b * maxnb + sl];
         const float4 xj = x[sy.ba0 + j];
@@ -315,10 +318,33 @@ __global__ void __launch_bounds__(256) desc_fwd_small_kernel(
         const float ir = 1.0f / r;
         float fc, dfc;
         cutoff(r, dp.rc, dp.pi_over_rc, fc, dfc);
+        if (packed) {
+            const float2 rho = make_float2(dp.rec_k, dp.rec_k);
+            const float dd = dp.r_delta * dp.r_delta;
 #pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            const float t = r - dp.r_mu[c];
-            gr[c] += gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+            for (int qp = 0; qp < 2; ++qp) {
+                const float ta = r - dp.r_mu[8 * qp], tb = r - dp.r_mu[8 * qp + 16];
+                float2 e2 = make_float2(exp2f(-dp.eta_R_l2 * ta * ta) * fc, exp2f(-dp.eta_R_l2 * tb * tb) * fc);
+                float2 R2 = make_float2(exp2f(dp.eta_R_l2 * fmaf(2.0f * ta, dp.r_delta, -dd)),
+                                        exp2f(dp.eta_R_l2 * fmaf(2.0f * tb, dp.r_delta, -dd)));
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    gr2[8 * qp + k] = __fadd2_rn(gr2[8 * qp + k], e2);
+                    if (k < 7) {
+                        e2 = __fmul2_rn(e2, R2);
+                        R2 = __fmul2_rn(R2, rho);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const float t = r - dp.r_mu[c];
+                const float g = gauss<FAST>(dp.eta_R, dp.eta_R_l2, t * t) * fc;
+                float2& slot = gr2[8 * ((c >> 3) & 1) + (c & 7)];
+                if (c < 16) slot.x += g;
+                else slot.y += g;
+            }
         }
         U[hw][sl] = make_float4(dx * ir, dy * ir, dz * ir, r);
         A[hw][sl] = make_float4(gauss<FAST>(dp.eta_A[0], dp.eta_A_l2[0], r2) * fc,
@@ -326,6 +352,14 @@ __global__ void __launch_bounds__(256) desc_fwd_small_kernel(
                                 gauss<FAST>(dp.eta_A[2], dp.eta_A_l2[2], r2) * fc,
                                 gauss<FAST>(dp.eta_A[3], dp.eta_A_l2[3], r2) * fc);
     }
+    float gr[NR];
+#pragma unroll
+    for (int qp = 0; qp < 2; ++qp)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            gr[8 * qp + k] = gr2[8 * qp + k].x;
+            gr[8 * qp + k + 16] = gr2[8 * qp + k].y;
+        }
     half_reduce32(gr, hl);
     __syncwarp();
 
