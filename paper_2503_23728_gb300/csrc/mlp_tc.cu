@@ -339,11 +339,18 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
     const int type = tile_type[row0 / TILE_ROWS];
     const unsigned char* img = wimg + (size_t)type * img_per_type;
     const float* vec = wvec + (size_t)type * vec_per_type;
-    const float* b_l = vec;
     const float* w_out = vec + L * W;
     const float* mu = w_out + W;
     const float* sigma = mu + ND;
     const float b_out = sigma[ND], s_E = sigma[ND + 1], e_Z = sigma[ND + 2];
+    // the element's vectors in shared memory: biases, output weights, mu and
+    // 1 / sigma (the epilogues read them in every 16-column chunk)
+    float* sb = ysum + 2 * M;   // [L][W]
+    float* swo = sb + L * W;
+    float* smu = swo + W;
+    float* sis = smu + ND;
+    for (int i = threadIdx.x; i < L * W + W + ND; i += blockDim.x) sb[i] = vec[i];
+    for (int i = threadIdx.x; i < ND; i += blockDim.x) sis[i] = 1.0f / sigma[i];
 
     const uint32_t bar_mma = smem_u32(&bars[0]);
     const uint32_t bar_w = smem_u32(&bars[1]);
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = c0 + 8 * g + j;
-                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : 0.0f;
+                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - smu[c]) * sis[c] : 0.0f;
             }
             uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
                                   pack_bf16(v[6], v[7]));
@@ -437,7 +444,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
             if (fwd) {
                 float h[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) h[j] = tanh_f(v[j] + b_l[(l - 1) * W + c0 + j]);
+                for (int j = 0; j < 16; ++j) h[j] = tanh_f(v[j] + sb[(l - 1) * W + c0 + j]);
                 if (l < L) {
                     uint32_t pk[8];
 #pragma unroll
@@ -458,7 +465,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
                     float ga[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float wo = w_out[c0 + j];
+                        const float wo = swo[c0 + j];
                         y_part += wo * h[j];
                         ga[j] = s_E * wo * (1.0f - h[j] * h[j]);
                     }
@@ -487,8 +494,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
                 if (ba >= 0) {
 #pragma unroll
                     for (int j = 0; j < 16; j += 4) {
-                        float4 o = make_float4(v[j] / sigma[c0 + j], v[j + 1] / sigma[c0 + j + 1],
-                                               v[j + 2] / sigma[c0 + j + 2], v[j + 3] / sigma[c0 + j + 3]);
+                        float4 o = make_float4(v[j] * sis[c0 + j], v[j + 1] * sis[c0 + j + 1],
+                                               v[j + 2] * sis[c0 + j + 2], v[j + 3] * sis[c0 + j + 3]);
                         *reinterpret_cast<float4*>(dEdG + (size_t)ba * ND + c0 + j) = o;
                     }
                 }
@@ -601,11 +608,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
     const int type = tile_type[row0 / TILE_ROWS];
     const unsigned char* img = wimg + (size_t)type * img_per_type;
     const float* vec = wvec + (size_t)type * vec_per_type;
-    const float* b_l = vec;
     const float* w_out = vec + L * WW;
     const float* mu = w_out + WW;
     const float* sigma = mu + ND;
     const float b_out = sigma[ND], s_E = sigma[ND + 1], e_Z = sigma[ND + 2];
+    // the element's vectors in shared memory: biases, output weights, mu and
+    // 1 / sigma (the epilogues read them in every 16-column chunk)
+    float* sb = ysum + 2 * M;   // [L][WW]
+    float* swo = sb + L * WW;
+    float* smu = swo + WW;
+    float* sis = smu + ND;
+    for (int i = threadIdx.x; i < L * WW + WW + ND; i += blockDim.x) sb[i] = vec[i];
+    for (int i = threadIdx.x; i < ND; i += blockDim.x) sis[i] = 1.0f / sigma[i];
 
     const uint32_t bar_mma = smem_u32(&bars[0]);
     const uint32_t bar_ld[2] = {smem_u32(&bars[1]), smem_u32(&bars[2])};
@@ -655,7 +669,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = c0 + 8 * g + j;
-                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : 0.0f;
+                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - smu[c]) * sis[c] : 0.0f;
             }
             uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
                                   pack_bf16(v[6], v[7]));
@@ -714,7 +728,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
             if (fwd) {
                 float h[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) h[j] = tanh_f(v[j] + b_l[(l - 1) * WW + c0 + j]);
+                for (int j = 0; j < 16; ++j) h[j] = tanh_f(v[j] + sb[(l - 1) * WW + c0 + j]);
                 if (l < L) {
                     uint32_t pk[8];
 #pragma unroll
@@ -735,7 +749,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
                     float ga[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float wo = w_out[c0 + j];
+                        const float wo = swo[c0 + j];
                         y_part += wo * h[j];
                         ga[j] = s_E * wo * (1.0f - h[j] * h[j]);
                     }
@@ -775,8 +789,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_wide_kernel(
                 if (ba >= 0) {
 #pragma unroll
                     for (int j = 0; j < 16; j += 4) {
-                        float4 o = make_float4(v[j] / sigma[c0 + j], v[j + 1] / sigma[c0 + j + 1],
-                                               v[j + 2] / sigma[c0 + j + 2], v[j + 3] / sigma[c0 + j + 3]);
+                        float4 o = make_float4(v[j] * sis[c0 + j], v[j + 1] * sis[c0 + j + 1],
+                                               v[j + 2] * sis[c0 + j + 2], v[j + 3] * sis[c0 + j + 3]);
                         *reinterpret_cast<float4*>(dEdG + (size_t)ba * ND + c0 + j) = o;
                     }
                 }
@@ -822,7 +836,8 @@ static size_t tc_smem(int W, int L, bool db)
 
 static size_t tc_wide_smem()
 {
-    return (size_t)128 * ND * 2 + 2 * (size_t)128 * WW * 2 + 2 * (size_t)WW * KCH * 2 + 64 + 2 * 128 * 4 + 1024;
+    return (size_t)128 * ND * 2 + 2 * (size_t)128 * WW * 2 + 2 * (size_t)WW * KCH * 2 + 64 + 2 * 128 * 4 +
+           (size_t)(MAX_LAYERS * WW + WW + 2 * ND) * 4 + 1024;
 }
 
 bool network_tc_supported(int width, int n_hidden)
@@ -907,7 +922,8 @@ template <int W, int L>
 static size_t park_smem()
 {
     const size_t WB_B = (size_t)W * (W > ND ? W : ND) * 2;
-    return (size_t)128 * ND * 2 + (size_t)128 * W * 2 + WB_B + 64 + 2 * 128 * 4 + 1024;
+    return (size_t)128 * ND * 2 + (size_t)128 * W * 2 + WB_B + 64 + 2 * 128 * 4 + (size_t)(L * W + W + 2 * ND) * 4 +
+           1024;
 }
 
 template <int W, int L>
