@@ -305,11 +305,8 @@ __global__ void __launch_bounds__(32 * FWD_WARPS) desc_mom_fwd_kernel(
 // the exact FP32 path keeps the 165-monomial form.
 // ---------------------------------------------------------------------------
 constexpr int NRED = 81;
-constexpr int RSLOT = 3;
-constexpr int RLAST = NRED - 32 * (RSLOT - 1);   // lanes holding a monomial in the last slot
 
 struct RedTab {
-    short red_full[RSLOT * 32];   // chain-order index of reduced monomial m' = lane + 32 slot, -1 beyond 81
     short up[7][32][4];           // level a = 2..8: (m_abc, m_(a-2)bc, m_(a-2)(b+2)c, m_(a-2)b(c+2)), -1 idle
     short down[7][2][32][4];      // level a = 8..2: target m_(a-2)BC and sources (a,B,C), (a,B-2,C), (a,B,C-2)
 };
@@ -317,11 +314,6 @@ struct RedTab {
 constexpr RedTab make_red_tab()
 {
     RedTab t{};
-    for (int q = 0; q < RSLOT * 32; ++q) t.red_full[q] = -1;
-    int m = 0;
-    for (int c = 0; c <= MDEG; ++c)
-        for (int b = 0; b <= MDEG - c; ++b)
-            for (int a = 0; a <= 1 && a + b + c <= MDEG; ++a) t.red_full[m++] = (short)mono_index(a, b, c);
     for (int L = 0; L < 7; ++L) {
         const int a = L + 2;
         int q = 0;
@@ -355,15 +347,47 @@ constexpr RedTab make_red_tab()
 
 __device__ const RedTab g_red = make_red_tab();
 
-// reduced-basis forward (BF16 path): the 81 monomials per neighbour, 3 slots
-// per lane; the 165 moments are then rebuilt in shared memory by the
-// recurrence and finished as in the full forward
-constexpr int FWDR_WARP_FLOATS = 32 * NRED + 32 * 4;   // monomial rows (stride 81, odd) + weights
+// reduced-basis forward (BF16 path). The x-degree rides on the weights:
+// M_eta,1bc = sum_j (b_eta(j) u_x,j) u_y,j^b u_z,j^c, so per neighbour the
+// warp stores the 45 products u_y^b u_z^c (b + c <= 8; row stride 45, odd,
+// so the 32 rows written in one step hit distinct banks) and the weights
+// b_eta and b_eta u_x. Each half-warp then owns the 45 products (3 slots of
+// 16 lanes) and half of the neighbours: half h reads row t + 16 h in step
+// t, and 16 x 45 = 16 (mod 32) puts the two halves' loads in complementary
+// banks, so each load and each weight broadcast serves two neighbours. The
+// halves are added at the end, and the 165 moments are rebuilt in shared
+// memory by the recurrence and finished as in the full forward.
+constexpr int NBASE = 45;                    // u_y^b u_z^c, b + c <= MDEG
+constexpr int BSLOT = 3;                     // base slots of 16 lanes per half-warp
+constexpr int BLAST = NBASE - 16 * (BSLOT - 1);   // half-warp lanes holding a base in the last slot
+constexpr int FWDR_WPAD = 34;                // weight float4 per warp and kind: neighbour j at j + 2 (j / 16)
+constexpr int FWDR_WARP_FLOATS = 32 * NBASE + 2 * 4 * FWDR_WPAD;
 constexpr int FWDR_WARPS = 2;
-static_assert(32 * NRED >= 4 * NMONO, "moment table reuses the monomial rows");
+static_assert(32 * NBASE >= 4 * NMONO, "moment table reuses the product rows");
+static_assert((16 * NBASE) % 32 == 16, "half-warps read complementary banks");
+static_assert((32 * NBASE) % 4 == 0, "weights 16-byte aligned");
+
+// chain-order index of u_x^a u_y^b u_z^c for base slot q (c outer, b inner,
+// the order of a row), a = 0, 1; -1 beyond the 45 or where a + b + c > MDEG
+struct BaseTab {
+    short full[2][16 * BSLOT];
+};
+constexpr BaseTab make_base_tab()
+{
+    BaseTab t{};
+    for (int q = 0; q < 16 * BSLOT; ++q) t.full[0][q] = t.full[1][q] = -1;
+    int q = 0;
+    for (int c = 0; c <= MDEG; ++c)
+        for (int b = 0; b <= MDEG - c; ++b, ++q) {
+            t.full[0][q] = (short)mono_index(0, b, c);
+            if (b + c < MDEG) t.full[1][q] = (short)mono_index(1, b, c);
+        }
+    return t;
+}
+__device__ const BaseTab g_base = make_base_tab();
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * FWDR_WARPS, 10) desc_mom_fwd_red_kernel(
+__global__ void __launch_bounds__(32 * FWDR_WARPS, 9) desc_mom_fwd_red_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout)
@@ -371,14 +395,17 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 10) desc_mom_fwd_red_kernel(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wib = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    float* MONO = reinterpret_cast<float*>(smem_raw) + (size_t)wib * FWDR_WARP_FLOATS;
-    float4* BW = reinterpret_cast<float4*>(MONO + 32 * NRED);
+    float* ROW = reinterpret_cast<float*>(smem_raw) + (size_t)wib * FWDR_WARP_FLOATS;
+    float4* W0 = reinterpret_cast<float4*>(ROW + 32 * NBASE);   // b_eta
+    float4* W1 = W0 + FWDR_WPAD;                                 // b_eta u_x
     const int b = blockIdx.x * FWDR_WARPS + wib;
     if (b >= B) return;
     const BeadSys sy = bsys[ba_sys[b]];
     const Rep& rp = reps[sy.rep];
     const int n = min(nnb[b], maxnb);
     const float4 xi = x[b];
+    const unsigned hl = lane & 15u;    // base lane within the half-warp
+    const int hh = (int)(lane >> 4);   // half-warp
 
     // radial sums; evenly spaced centres on the fast path keep channels c and
     // c + 16 in one register pair (gr2[8 qp + k] = channels 8 qp + k, 8 qp + k + 16)
@@ -387,9 +414,12 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 10) desc_mom_fwd_red_kernel(
     for (int c = 0; c < NR / 2; ++c) gr2[c] = make_float2(0.0f, 0.0f);
     const bool packed = FAST && dp.r_even;
     float dg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float2 acc[RSLOT][2];
+    // acc[k][0..1]: moments of (0, b, c), widths (0, 1) and (2, 3); acc[k][2..3]: (1, b, c)
+    float2 acc[BSLOT][4];
 #pragma unroll
-    for (int k = 0; k < RSLOT; ++k) acc[k][0] = acc[k][1] = make_float2(0.0f, 0.0f);
+    for (int k = 0; k < BSLOT; ++k)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[k][v] = make_float2(0.0f, 0.0f);
 
     // the next chunk's neighbour position is loaded while this chunk computes
     float4 xnext = ((int)lane < n) ? x[sy.ba0 + nbr[(size_t)b * maxnb + lane]] : xi;
@@ -397,6 +427,10 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 10) desc_mom_fwd_red_kernel(
         const int s = s0 + (int)lane;
         const float4 xj = xnext;
         if (s + 32 < n) xnext = x[sy.ba0 + nbr[(size_t)b * maxnb + s + 32]];
+        // lanes past the end store zero weights and finite products, so that
+        // every step of the read loop can take both halves' rows
+        float bw[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float ux = 0.0f, uy = 0.0f, uz = 0.0f;
         if (s < n) {
             float dx, dy, dz, r, r2, ir, fc, dfc;
             if (FAST) {
@@ -438,67 +472,76 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 10) desc_mom_fwd_red_kernel(
                     else slot.y += g;
                 }
             }
-            float bw[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 bw[e] = gauss<FAST>(dp.eta_A[e], dp.eta_A_l2[e], r2) * fc;
                 dg[e] = fmaf(bw[e], bw[e], dg[e]);
             }
-            BW[lane] = make_float4(bw[0], bw[1], bw[2], bw[3]);
-            const float ux = dx * ir;
+            ux = dx * ir;
+            uy = dy * ir;
+            uz = dz * ir;
+        }
+        const int pw = (int)lane + 2 * (int)(lane >> 4);
+        W0[pw] = make_float4(bw[0], bw[1], bw[2], bw[3]);
+        W1[pw] = make_float4(bw[0] * ux, bw[1] * ux, bw[2] * ux, bw[3] * ux);
+        {
             float py[MDEG + 1], pz[MDEG + 1];
             py[0] = pz[0] = 1.0f;
-            py[1] = dy * ir;
-            pz[1] = dz * ir;
+            py[1] = uy;
+            pz[1] = uz;
 #pragma unroll
             for (int a = 2; a <= MDEG; ++a) {
                 py[a] = py[a - 1] * py[1];
                 pz[a] = pz[a - 1] * pz[1];
             }
-            float* row = MONO + (size_t)lane * NRED;
-            int m = 0;
+            float* row = ROW + (size_t)lane * NBASE;
+            int q = 0;
 #pragma unroll
             for (int c = 0; c <= MDEG; ++c)
 #pragma unroll
-                for (int bb = 0; bb <= MDEG - c; ++bb) {
-                    const float base = py[bb] * pz[c];
-                    row[m++] = base;
-                    if (bb + c < MDEG) row[m++] = base * ux;
-                }
+                for (int bb = 0; bb <= MDEG - c; ++bb) row[q++] = py[bb] * pz[c];
         }
         __syncwarp();
-        const int cnt = min(32, n - s0);
-        const float* col = MONO + lane;
-        int j0 = 0;
-        // blocks of four neighbours without bounds checks, then the rest
-        for (; j0 + 4 <= cnt; j0 += 4) {
+        // step t: half hh takes row t + 16 hh (zero weights past the end)
+        const int steps = min(32, n - s0) > 16 ? 16 : n - s0;
+        const float* col = ROW + (size_t)(16 * hh) * NBASE + hl;
+        const float4* w0p = W0 + 18 * hh;
+        const float4* w1p = W1 + 18 * hh;
+        int t = 0;
+        for (; t + 4 <= steps; t += 4) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 w4 = BW[j0 + q];
-                const float2 w01 = make_float2(w4.x, w4.y), w23 = make_float2(w4.z, w4.w);
-                const float* rowj = col + (size_t)(j0 + q) * NRED;
+            for (int u = 0; u < 4; ++u) {
+                const float4 a4 = w0p[t + u], c4 = w1p[t + u];
+                const float2 w01 = make_float2(a4.x, a4.y), w23 = make_float2(a4.z, a4.w);
+                const float2 x01 = make_float2(c4.x, c4.y), x23 = make_float2(c4.z, c4.w);
+                const float* rowj = col + (size_t)(t + u) * NBASE;
 #pragma unroll
-                for (int k = 0; k < RSLOT; ++k) {
-                    if (k < RSLOT - 1 || lane < (unsigned)RLAST) {
-                        const float mv = rowj[32 * k];
+                for (int k = 0; k < BSLOT; ++k) {
+                    if (k < BSLOT - 1 || hl < (unsigned)BLAST) {
+                        const float mv = rowj[16 * k];
                         const float2 m2 = make_float2(mv, mv);
                         acc[k][0] = __ffma2_rn(w01, m2, acc[k][0]);
                         acc[k][1] = __ffma2_rn(w23, m2, acc[k][1]);
+                        acc[k][2] = __ffma2_rn(x01, m2, acc[k][2]);
+                        acc[k][3] = __ffma2_rn(x23, m2, acc[k][3]);
                     }
                 }
             }
         }
-        for (; j0 < cnt; ++j0) {
-            const float4 w4 = BW[j0];
-            const float2 w01 = make_float2(w4.x, w4.y), w23 = make_float2(w4.z, w4.w);
-            const float* rowj = col + (size_t)j0 * NRED;
+        for (; t < steps; ++t) {
+            const float4 a4 = w0p[t], c4 = w1p[t];
+            const float2 w01 = make_float2(a4.x, a4.y), w23 = make_float2(a4.z, a4.w);
+            const float2 x01 = make_float2(c4.x, c4.y), x23 = make_float2(c4.z, c4.w);
+            const float* rowj = col + (size_t)t * NBASE;
 #pragma unroll
-            for (int k = 0; k < RSLOT; ++k) {
-                if (k < RSLOT - 1 || lane < (unsigned)RLAST) {
-                    const float mv = rowj[32 * k];
+            for (int k = 0; k < BSLOT; ++k) {
+                if (k < BSLOT - 1 || hl < (unsigned)BLAST) {
+                    const float mv = rowj[16 * k];
                     const float2 m2 = make_float2(mv, mv);
                     acc[k][0] = __ffma2_rn(w01, m2, acc[k][0]);
                     acc[k][1] = __ffma2_rn(w23, m2, acc[k][1]);
+                    acc[k][2] = __ffma2_rn(x01, m2, acc[k][2]);
+                    acc[k][3] = __ffma2_rn(x23, m2, acc[k][3]);
                 }
             }
         }
@@ -517,12 +560,20 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 10) desc_mom_fwd_red_kernel(
 #pragma unroll
     for (int e = 0; e < 4; ++e) diag[e] = warp_sum(dg[e]);
 
-    // the 165 moments from the 81 (rows of the last chunk are no longer needed)
-    float4* T = reinterpret_cast<float4*>(MONO);
+    // the two halves' sums; then half 0 stores the moments of (0, b, c) and
+    // half 1 those of (1, b, c) (rows of the last chunk are no longer needed)
+    float4* T = reinterpret_cast<float4*>(ROW);
 #pragma unroll
-    for (int k = 0; k < RSLOT; ++k) {
-        const int mf = g_red.red_full[k * 32 + lane];
-        if (mf >= 0) T[mf] = make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
+    for (int k = 0; k < BSLOT; ++k) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            acc[k][v].x += __shfl_xor_sync(0xffffffffu, acc[k][v].x, 16);
+            acc[k][v].y += __shfl_xor_sync(0xffffffffu, acc[k][v].y, 16);
+        }
+        const int mf = g_base.full[hh][16 * k + hl];
+        const float2 lo = hh ? acc[k][2] : acc[k][0];
+        const float2 hi = hh ? acc[k][3] : acc[k][1];
+        if (mf >= 0) T[mf] = make_float4(lo.x, lo.y, hi.x, hi.y);
     }
     __syncwarp();
 #pragma unroll 1
