@@ -362,7 +362,7 @@ constexpr int BSLOT = 3;                     // base slots of 16 lanes per half-
 constexpr int BLAST = NBASE - 16 * (BSLOT - 1);   // half-warp lanes holding a base in the last slot
 constexpr int FWDR_WPAD = 34;                // weight float4 per warp and kind: neighbour j at j + 2 (j / 16)
 constexpr int FWDR_WARP_FLOATS = 32 * NBASE + 2 * 4 * FWDR_WPAD;
-constexpr int FWDR_WARPS = 2;
+constexpr int FWDR_WARPS = 1;   // one-warp CTAs: a finished warp frees its slot at once
 static_assert(32 * NBASE >= 4 * NMONO, "moment table reuses the product rows");
 static_assert((16 * NBASE) % 32 == 16, "half-warps read complementary banks");
 static_assert((32 * NBASE) % 4 == 0, "weights 16-byte aligned");
@@ -387,7 +387,7 @@ constexpr BaseTab make_base_tab()
 __device__ const BaseTab g_base = make_base_tab();
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * FWDR_WARPS, 9) desc_mom_fwd_red_kernel(
+__global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout)
