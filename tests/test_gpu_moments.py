@@ -224,3 +224,51 @@ def test_bf16_adjoint_deterministic_mode_and_summed_virial(water64_model):
     _, _, Wo = O.energy_forces_batch(m, rep.Z, xb, rep.box)
     Wo = np.asarray(Wo).reshape(v0.shape)
     assert np.sqrt(((v0 - Wo) ** 2).mean() / (Wo ** 2).mean()) < 5e-2
+
+
+def test_bf16_reduced_forward_ragged_counts_and_empty_lists():
+    """BF16 path, moment evaluation forced, on replicas of 1..24 atoms with an
+    isolated atom: neighbour counts from 0 to 23 cover an empty list, a chunk
+    of at most 16 neighbours (one half-warp's rows) and one of 17..31 (the
+    second half-warp's rows padded with zero weights). Descriptors match the
+    oracle within 1e-5 of each channel's scale (1e-30 absolute floor: far
+    radial centres of a tiny cluster underflow in FP32); forces and energies
+    match the pair-sum kernels with the same BF16 network; the isolated atom
+    and the one-atom replica get exactly zero force."""
+    P = _P()
+    reps = s.batch(n_rep=5, seed=91, beads=(2, 3))
+    r0 = reps[0]
+    x0 = r0.x0.copy()
+    x0[0] += np.array([40.0, 0.0, 0.0])
+    reps[0] = s.Replica(r0.Z, x0, r0.box, r0.n_beads, r0.T, r0.seed)
+    lone = s.Replica(np.array([8], dtype=np.int32), np.zeros((1, 3)), (0.0, 0.0, 0.0), 2, 300.0, 5)
+    reps.append(lone)
+    m = s.xavier_model(s.elements_of(reps), (64, 64), seed=6)
+    G0 = np.concatenate([O.descriptors(m, r.x0, None) for r in reps])
+    Z = np.concatenate([r.Z for r in reps])
+    s.set_normalisation(m, G0, Z)
+    xs = [_beads(r, r.n_beads, seed=50 + k, sigma=0.05) for k, r in enumerate(reps)]
+    x = torch.tensor(np.concatenate([xx.reshape(-1, 3) for xx in xs]), device="cuda")
+    out = {}
+    for algo in ("moments", "pairs"):
+        ctx = P.Context(reps, 0.25, 0.01, precision="bf16_tc", widths=(64, 64))
+        ctx.set_weights(m)
+        ctx.set_angular(algo)
+        G = ctx.descriptors(x).cpu().numpy()
+        e, f, _ = ctx.energy_forces(x)
+        out[algo] = (G, e.cpu().numpy(), f.cpu().numpy())
+    G, e, f = out["moments"]
+    _, ep, fp = out["pairs"]
+    b0 = 0
+    for r, xx in zip(reps, xs):
+        for k in range(r.n_beads):
+            Go = O.descriptors(m, xx[k], None)
+            Gg = G[b0:b0 + r.n_atoms]
+            scale = np.abs(Go).max(axis=0)
+            assert np.all(np.abs(Gg - Go) <= 1e-5 * scale + 1e-30), (r.n_atoms, k)
+            b0 += r.n_atoms
+    assert b0 == G.shape[0]
+    assert np.sqrt(((f - fp) ** 2).mean() / (fp ** 2).mean()) < 1e-2
+    assert np.abs(e - ep).max() < 1e-3 * max(r.n_atoms for r in reps)
+    assert np.abs(f[:reps[0].n_atoms * reps[0].n_beads].reshape(reps[0].n_beads, -1, 3)[:, 0]).max() == 0.0
+    assert np.abs(f[-lone.n_beads:]).max() == 0.0
