@@ -427,8 +427,13 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
         const int s = s0 + (int)lane;
         const float4 xj = xnext;
         if (s + 32 < n) xnext = x[sy.ba0 + nbr[(size_t)b * maxnb + s + 32]];
-        // lanes past the end store zero weights and finite products, so that
-        // every step of the read loop can take both halves' rows
+        // the chunk's cnt neighbours split between the halves: lane l < hc
+        // (hc = ceil(cnt / 2)) writes row l, lane l >= hc row 16 + l - hc; for
+        // odd cnt, lane cnt writes the zero-weight row that half 1 reads last
+        const int cnt = min(32, n - s0);
+        const int hc = (cnt + 1) >> 1;
+        const int rl = (int)lane < hc ? (int)lane : 16 + (int)lane - hc;
+        const bool wr = (int)lane <= cnt;
         float bw[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         float ux = 0.0f, uy = 0.0f, uz = 0.0f;
         if (s < n) {
@@ -481,10 +486,10 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
             uy = dy * ir;
             uz = dz * ir;
         }
-        const int pw = (int)lane + 2 * (int)(lane >> 4);
-        W0[pw] = make_float4(bw[0], bw[1], bw[2], bw[3]);
-        W1[pw] = make_float4(bw[0] * ux, bw[1] * ux, bw[2] * ux, bw[3] * ux);
-        {
+        if (wr) {
+            const int pw = rl + 2 * (rl >> 4);
+            W0[pw] = make_float4(bw[0], bw[1], bw[2], bw[3]);
+            W1[pw] = make_float4(bw[0] * ux, bw[1] * ux, bw[2] * ux, bw[3] * ux);
             float py[MDEG + 1], pz[MDEG + 1];
             py[0] = pz[0] = 1.0f;
             py[1] = uy;
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
                 py[a] = py[a - 1] * py[1];
                 pz[a] = pz[a - 1] * pz[1];
             }
-            float* row = ROW + (size_t)lane * NBASE;
+            float* row = ROW + (size_t)rl * NBASE;
             int q = 0;
 #pragma unroll
             for (int c = 0; c <= MDEG; ++c)
@@ -502,8 +507,8 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
                 for (int bb = 0; bb <= MDEG - c; ++bb) row[q++] = py[bb] * pz[c];
         }
         __syncwarp();
-        // step t: half hh takes row t + 16 hh (zero weights past the end)
-        const int steps = min(32, n - s0) > 16 ? 16 : n - s0;
+        // step t: half hh takes row t + 16 hh
+        const int steps = hc;
         const float* col = ROW + (size_t)(16 * hh) * NBASE + hl;
         const float4* w0p = W0 + 18 * hh;
         const float4* w1p = W1 + 18 * hh;
