@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(32 * FWD_WARPS) desc_mom_fwd_kernel(
 // ---------------------------------------------------------------------------
 constexpr int NRED = 81;
 
-struct RedTab {
+struct alignas(16) RedTab {
     short up[7][32][4];           // level a = 2..8: (m_abc, m_(a-2)bc, m_(a-2)(b+2)c, m_(a-2)b(c+2)), -1 idle
     short down[7][2][32][4];      // level a = 8..2: target m_(a-2)BC and sources (a,B,C), (a,B-2,C), (a,B,C-2)
 };
@@ -402,6 +402,7 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
     if (b >= B) return;
     const BeadSys sy = bsys[ba_sys[b]];
     const Rep& rp = reps[sy.rep];
+    const Box bx = box_of(rp);   // read once, not in every chunk
     const int n = min(nnb[b], maxnb);
     const float4 xi = x[b];
     const unsigned hl = lane & 15u;    // base lane within the half-warp
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
         if (s < n) {
             float dx, dy, dz, r, r2, ir, fc, dfc;
             if (FAST) {
-                geo_fast(rp, xi, xj, dp.rc, dp.pi_over_rc, dx, dy, dz, r, ir, fc, dfc);
+                geo_fast(bx, xi, xj, dp.rc, dp.pi_over_rc, dx, dy, dz, r, ir, fc, dfc);
                 r2 = r * r;
             } else {
                 pair_vec(rp, xi, xj, dx, dy, dz);
@@ -583,10 +584,10 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
     __syncwarp();
 #pragma unroll 1
     for (int L = 0; L < 7; ++L) {
-        const short* e = g_red.up[L][lane];
-        if (e[0] >= 0) {
-            const float4 a0 = T[e[1]], a1 = T[e[2]], a2 = T[e[3]];
-            T[e[0]] = make_float4(a0.x - a1.x - a2.x, a0.y - a1.y - a2.y, a0.z - a1.z - a2.z, a0.w - a1.w - a2.w);
+        const short4 e = *reinterpret_cast<const short4*>(g_red.up[L][lane]);   // one 8-byte load
+        if (e.x >= 0) {
+            const float4 a0 = T[e.y], a1 = T[e.z], a2 = T[e.w];
+            T[e.x] = make_float4(a0.x - a1.x - a2.x, a0.y - a1.y - a2.y, a0.z - a1.z - a2.z, a0.w - a1.w - a2.w);
         }
         __syncwarp();
     }
