@@ -558,7 +558,7 @@ def reference(a, rank, world):
     s.set_normalisation(m, G, rep.Z)
     rng = np.random.default_rng(3)
     steps = min(a.steps, 20)
-    warm = min(a.warmup, 2)
+    warm = min(a.warmup, 5)   # at most 5 untimed evaluations (~0.6 s each on 16 cores)
     for _ in range(warm):
         O.energy_forces(m, rep.Z, rep.x0 + rng.normal(scale=0.05, size=rep.x0.shape), rep.box)
     t0 = time.perf_counter()
