@@ -348,3 +348,84 @@ def test_staging_nve_energy_conservation():
         amp.append(H.std())
         assert abs(slope * len(H)) < 3 * H.std() + 1e-12
     assert 2.5 < amp[0] / amp[1] < 6.0, amp
+
+
+# ---------------------------------------------------------------- thermostat heat
+def _free_ring_energy(sysm, transform):
+    """H_P of a ring polymer with V = 0, from the state arrays alone: the
+    kinetic energy of every coordinate plus the spring energy. Normal modes:
+    masses m, spring sum_k m w_k^2 q_k^2 / 2 (w_k = 2 w_P sin(k pi / P));
+    staging: masses m'_1 = m, m'_k = k / (k - 1) m, spring
+    sum_(k>=2) m'_k w_P^2 u_k^2 / 2 (the spring identity pinned above)."""
+    P, N = sysm.P, sysm.N
+    m = sysm.mass[None, :, None]
+    wP = P * KB * sysm.s.T / HBAR
+    if transform == "staging":
+        k = np.arange(1, P + 1, dtype=float)
+        fac = np.where(k >= 2, k / np.maximum(k - 1, 1), 1.0)[:, None, None]
+        mk = fac * m
+        w2 = np.where(k >= 2, wP * wP, 0.0)[:, None, None]
+    else:
+        mk = np.broadcast_to(m, (P, N, 1))
+        w2 = (2 * wP * np.sin(np.arange(P) * np.pi / P))[:, None, None] ** 2
+    kin = (sysm.p ** 2 / (2 * mk)).sum()
+    spring = (0.5 * mk * w2 * sysm.q ** 2).sum()
+    return (kin + spring) * MVV2E
+
+
+@pytest.mark.parametrize("P,splitting,free_rp,transform", [
+    (1, "obabo", "exact", "normal_modes"), (8, "obabo", "exact", "normal_modes"),
+    (5, "baoab", "exact", "normal_modes"), (8, "obabo", "cayley", "normal_modes"),
+    (6, "obabo", "exact", "staging")])
+def test_thermostat_heat_is_the_kinetic_energy_change_of_the_O_steps(P, splitting, free_rp, transform):
+    """Sec. 2.1 (H_eff) with PILE-L on (Tables S2-S3): with V = 0 the B steps
+    do nothing and the free ring-polymer A step conserves each mode's energy
+    exactly (the exact rotation and the Cayley rotation alike), so the
+    ring-polymer energy H_P changes only in the O steps. The accumulated heat
+    Q_thermo must therefore equal H_P(now) - H_P(start), with H_P computed
+    here from q and p, and H_cons = H_P - Q_thermo must stay at its initial
+    value. A sign or factor error in the heat, a dropped O step or the wrong
+    mode mass each break it."""
+    N, T = 5, 300.0
+    x0 = np.random.default_rng(9).normal(size=(N, 3)) * 0.1
+    Z = np.array([s.H, s.O, s.C, s.H, s.O], dtype=np.int32)
+    rep = s.Replica(Z, x0, (0.0, 0.0, 0.0), P, T, 17)
+    sysm = O.System(rep, s.MASS, 0.5, 0.05, potential="harmonic", omega=0.0, splitting=splitting,
+                    free_rp=free_rp, transform=transform)
+    H0 = _free_ring_energy(sysm, transform)
+    Hc0 = sysm.estimators()["H_cons"]
+    assert abs(Hc0 - H0) < 1e-12 * max(1.0, abs(H0))
+    for _ in range(6):
+        sysm.step(7)
+        e = sysm.estimators()
+        dH = _free_ring_energy(sysm, transform) - H0
+        assert abs(e["Q_thermo"]) > 1e-3          # the thermostat did move energy
+        assert abs(e["Q_thermo"] - dH) < 1e-10 * max(1.0, abs(dH))
+        assert abs(e["H_cons"] - H0) < 1e-10 * max(1.0, abs(H0))
+
+
+def test_conserved_energy_with_pile_l_on(fad_model):
+    """FAD, P = 4, PILE-L on: H_P itself fluctuates with the heat the
+    thermostat exchanges, but H_cons = H_P - Q_thermo shows no drift and its
+    fluctuation is the integrator's O(dt^2) error (pooled over three noise
+    seeds, halving dt divides it by ~4). H_P + Q_thermo (a sign error in the
+    heat) fluctuates a thousand times more."""
+    w, r, m = fad_model
+    amp = {0.1: [], 0.05: []}
+    for seed in (1, 2, 3):
+        for dt in (0.1, 0.05):
+            rep = s.Replica(r.Z, r.x0, r.box, 4, 300.0, seed)
+            sysm = O.System(rep, s.MASS, dt, 0.01, model=m, thermostat=True)
+            H, Hw = [], []
+            for _ in range(int(round(10.0 / dt))):
+                sysm.step(1)
+                e = sysm.estimators()
+                H.append(e["H_cons"])
+                Hw.append(e["H_cons"] + 2.0 * e["Q_thermo"])
+            H, Hw = np.array(H), np.array(Hw)
+            slope = np.polyfit(np.arange(len(H)), H, 1)[0]
+            assert abs(slope * len(H)) < 4 * H.std() + 1e-12
+            assert H.std() < 0.01 * Hw.std()
+            amp[dt].append(H.std())
+    ratio = np.mean(amp[0.1]) / np.mean(amp[0.05])
+    assert 2.5 < ratio < 8.0, amp
