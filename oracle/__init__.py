@@ -107,6 +107,19 @@ class Metad:
         v = lib().or_metad_bias(ct.byref(self.m), float(s), ct.byref(dv))
         return v, dv.value
 
+    def set_hills(self, s, h):
+        s, h = _f64(s), _f64(h)
+        self.hs[:len(s)] = s
+        self.hh[:len(h)] = h
+        self.m.n_hills = len(s)
+
+    def fes(self, s):
+        """F(s) = -(gamma / (gamma - 1)) V(s) of the current hills"""
+        s = _f64(np.atleast_1d(s))
+        F = np.zeros(len(s))
+        lib().or_metad_fes(ct.byref(self.m), len(s), _dp(s), _dp(F))
+        return F
+
 
 class OrSys(ct.Structure):
     _fields_ = [
@@ -183,6 +196,11 @@ def lib():
         L.or_free_rp_step.argtypes = [ct.c_int, ct.c_double, ct.c_double, ct.c_double,
                                       ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         L.or_get_threads.restype = ct.c_int
+        L.or_rdf_gr.argtypes = [ct.c_int, ip, ct.c_double, ct.c_double, ct.c_int, ct.c_double, u64p, dp]
+        L.or_cv_histogram.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_double, ct.c_double, ct.c_int,
+                                      ct.c_double, dp, dp]
+        L.or_pi_fes.argtypes = [ct.c_int, ct.c_int, dp, ct.c_double, ct.c_double, ct.c_double, dp, dp]
+        L.or_metad_fes.argtypes = [ct.POINTER(OrMetad), ct.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -339,6 +357,44 @@ def pt_coordinate(x, box, bond, acceptor, v_min: float, v_max: float, n_bins: in
                            int(n_bins), v.ctypes.data_as(ct.POINTER(ct.c_float)),
                            h.ctypes.data_as(ct.POINTER(ct.c_uint64)))
     return v, h
+
+
+def rdf_gr(counts, n_per_type, volume: float, r_max: float, n_configs: float) -> np.ndarray:
+    """g(r) per element pair from pair counts [T (T + 1) / 2, n_bins] summed
+    over n_configs configurations (see or_rdf_gr)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    n = np.ascontiguousarray(n_per_type, dtype=np.int32)
+    g = np.zeros(c.shape, dtype=np.float64)
+    lib().or_rdf_gr(len(n), _ip(n), float(volume), float(r_max), int(c.shape[1]), float(n_configs),
+                    c.ctypes.data_as(ct.POINTER(ct.c_uint64)), _dp(g))
+    return g
+
+
+class CvHistogram:
+    """Bead-resolved CV histogram of the path-integral FES (Sec. 2.5):
+    add() takes the P beads' CVs and biases of one configuration."""
+
+    def __init__(self, P: int, s_min: float, s_max: float, n_bins: int, T: float, log_w_shift: float = 0.0):
+        self.P, self.n_bins, self.T = int(P), int(n_bins), float(T)
+        self.s_min, self.s_max = float(s_min), float(s_max)
+        self.inv_ds = n_bins / (s_max - s_min)
+        self.shift = float(log_w_shift)
+        self.hist = np.zeros((self.P, self.n_bins))
+        self.wsum = np.zeros(1)
+
+    def add(self, s, vb=None):
+        s = _f64(s)
+        vb = np.zeros(self.P) if vb is None else _f64(vb)
+        lib().or_cv_histogram(self.P, _dp(s), _dp(vb), self.T, self.s_min, self.inv_ds, self.n_bins, self.shift,
+                              _dp(self.hist), _dp(self.wsum))
+
+    def fes(self):
+        """(F [n_bins], F_k [P, n_bins]) in eV, +inf where a bin is empty"""
+        F = np.zeros(self.n_bins)
+        Fk = np.zeros((self.P, self.n_bins))
+        lib().or_pi_fes(self.P, self.n_bins, _dp(self.hist), float(self.wsum[0]),
+                        (self.s_max - self.s_min) / self.n_bins, self.T, _dp(F), _dp(Fk))
+        return F, Fk
 
 
 def staging_to_beads(u):

@@ -942,3 +942,75 @@ void or_pt_coordinate(int n, const double* x, const double* box, const int* bond
     }
     free(e);
 }
+
+/* g(r) per element pair (Figs. 8, 9): the pair counts of the shell
+ * [k dr, (k + 1) dr), dr = r_max / n_bins, summed over n_configs bead
+ * configurations, divided by the ideal-gas expectation
+ * n_configs n_pairs shell_k / volume, shell_k = 4/3 pi ((k+1)^3 - k^3) dr^3,
+ * n_pairs = n_a n_b (a != b) or n_a (n_a - 1) / 2 (a = b). Pair p of types
+ * a <= b is p = a (2T - a - 1) / 2 + b, as in or_rdf_counts.              */
+void or_rdf_gr(int n_types, const int* n_per_type, double volume, double r_max, int n_bins,
+               double n_configs, const unsigned long long* counts, double* g)
+{
+    double dr = r_max / n_bins;
+    int p = 0;
+    for (int a = 0; a < n_types; ++a)
+        for (int b = a; b < n_types; ++b, ++p) {
+            double na = n_per_type[a], nb = n_per_type[b];
+            double pairs = (a == b) ? na * (na - 1.0) / 2.0 : na * nb;
+            for (int k = 0; k < n_bins; ++k) {
+                double r0 = k * dr, r1 = (k + 1) * dr;
+                double shell = 4.0 / 3.0 * M_PI * (r1 * r1 * r1 - r0 * r0 * r0);
+                double ideal = n_configs * pairs * shell / volume;
+                g[(size_t)p * n_bins + k] = ideal > 0.0 ? (double)counts[(size_t)p * n_bins + k] / ideal : 0.0;
+            }
+        }
+}
+
+/* Path-integral reweighting of Sec. 2.5, one sample of the bead-resolved
+ * CV histogram. Under a bias V_b acting on every bead's CV the ring
+ * polymer's configurational weight carries exp(-beta_P sum_k V_b(s_k)),
+ * beta_P = 1 / (k_B T P) the ring polymer's inverse temperature; the sample
+ * enters with the inverse factor w = exp(beta_P sum_k V_b(s_k) - shift)
+ * (w = exp(-shift) without a bias). Bead k's CV falls in bin
+ * b = floor((s_k - s_min) inv_ds), inv_ds = n_bins / (s_max - s_min), and
+ * is counted when 0 <= b < n_bins: hist[k][b] += w. Every sample adds w to
+ * *wsum, binned or not (the normalisation of the probability density).    */
+void or_cv_histogram(int P, const double* s, const double* vb, double T, double s_min, double inv_ds,
+                     int n_bins, double log_w_shift, double* hist, double* wsum)
+{
+    double v = 0.0;
+    for (int k = 0; k < P; ++k) v += vb[k];
+    double w = exp(v / (KB * T * P) - log_w_shift);
+    for (int k = 0; k < P; ++k) {
+        double t = (s[k] - s_min) * inv_ds;
+        if (t >= 0.0 && t < (double)n_bins) hist[(size_t)k * n_bins + (int)floor(t)] += w;
+    }
+    *wsum += w;
+}
+
+/* Sec. 2.5: each bead's free energy F_k(s) = -k_B T ln p_k(s), p_k the
+ * probability density of bead k's CV (histogram / (wsum ds)), and the
+ * path-integral free energy F(s) = -k_B T ln[(1/P) sum_k p_k(s)], which is
+ * -k_B T ln[(1/P) sum_k exp(-F_k(s) / k_B T)]. T is the physical
+ * temperature; empty bins give +inf. Fk may be NULL.                       */
+void or_pi_fes(int P, int n_bins, const double* hist, double wsum, double ds, double T, double* F, double* Fk)
+{
+    double kT = KB * T;
+    for (int b = 0; b < n_bins; ++b) {
+        double tot = 0.0;
+        for (int k = 0; k < P; ++k) {
+            double h = hist[(size_t)k * n_bins + b];
+            tot += h;
+            if (Fk) Fk[(size_t)k * n_bins + b] = h > 0.0 ? -kT * log(h / (wsum * ds)) : INFINITY;
+        }
+        F[b] = tot > 0.0 ? -kT * log(tot / (P * wsum * ds)) : INFINITY;
+    }
+}
+
+/* Sec. 2.5: the converged well-tempered bias is V(s) = -(1 - 1/gamma) F(s)
+ * up to a constant, so F(s) = -(gamma / (gamma - 1)) V(s).                 */
+void or_metad_fes(const or_metad* md, int n, const double* s, double* F)
+{
+    for (int i = 0; i < n; ++i) F[i] = -(md->gamma / (md->gamma - 1.0)) * or_metad_bias(md, s[i], NULL);
+}

@@ -136,6 +136,20 @@ void or_rdf_counts(int n, const double* x, const double* box, const int* type, i
                    double r_max, int n_bins, unsigned long long* counts);
 void or_pt_coordinate(int n, const double* x, const double* box, const int* bond, const int* acceptor,
                       double v_min, double v_max, int n_bins, float* v, unsigned long long* hist);
+/* g(r) of each element pair from pair counts summed over n_configs bead
+ * configurations: counts[p][k] / (n_configs pairs_p shell_k / volume) */
+void or_rdf_gr(int n_types, const int* n_per_type, double volume, double r_max, int n_bins,
+               double n_configs, const unsigned long long* counts, double* g);
+
+/* --- free-energy surfaces (Sec. 2.5) --------------------------------------- */
+/* one sample of the bead-resolved CV histogram of the path-integral FES */
+void or_cv_histogram(int P, const double* s, const double* vb, double T, double s_min, double inv_ds,
+                     int n_bins, double log_w_shift, double* hist, double* wsum);
+/* F_k(s) and the path-integral F(s) from that histogram */
+void or_pi_fes(int P, int n_bins, const double* hist, double wsum, double ds, double T, double* F, double* Fk);
+/* F(s) = -(gamma / (gamma - 1)) V(s) of a converged well-tempered bias */
+void or_metad_fes(const or_metad* md, int n, const double* s, double* F);
+
 void or_set_threads(int n);
 int  or_get_threads(void);
 
