@@ -201,6 +201,10 @@ def lib():
                                       ct.c_double, dp, dp]
         L.or_pi_fes.argtypes = [ct.c_int, ct.c_int, dp, ct.c_double, ct.c_double, ct.c_double, dp, dp]
         L.or_metad_fes.argtypes = [ct.POINTER(OrMetad), ct.c_int, dp, dp]
+        L.or_ring_start.argtypes = [ct.POINTER(OrSys), ct.c_uint64, ct.c_int, ct.c_int, dp, dp, dp, dp,
+                                    ct.POINTER(ct.c_double)]
+        L.or_ring_finish.argtypes = [ct.POINTER(OrSys), ct.c_uint64, ct.c_int, ct.c_int, dp, dp,
+                                     ct.POINTER(ct.c_double)]
         _lib = L
     return _lib
 
@@ -516,6 +520,21 @@ class System:
                           _dp(self.p), _dp(self.f), _dp(self.V), _dp(self.W), ct.byref(self.Q))
         if r < 0:
             raise ValueError("oracle step failed (%d)" % r)
+
+    def ring_start(self, lo: int, hi: int, f=None):
+        """First half of a step for atoms lo .. hi-1 with the bead forces f
+        ([P, N, 3], default: the last evaluated ones); their new bead
+        positions land in self.xb. The step counter is the caller's."""
+        f = self.f if f is None else _f64(f)
+        lib().or_ring_start(ct.byref(self.s), self.step_count.value, int(lo), int(hi), _dp(self.q), _dp(self.p),
+                            _dp(f), _dp(self.xb), ct.byref(self.Q))
+
+    def ring_finish(self, lo: int, hi: int, f):
+        """Second half of the step for atoms lo .. hi-1 with the forces f
+        ([P, N, 3]) of the new positions."""
+        f = _f64(f)
+        lib().or_ring_finish(ct.byref(self.s), self.step_count.value, int(lo), int(hi), _dp(self.p), _dp(f),
+                             ct.byref(self.Q))
 
     def beads(self) -> np.ndarray:
         if self.s.transform == 1:

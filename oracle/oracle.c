@@ -809,6 +809,126 @@ int or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
     return rc;
 }
 
+/* The two halves of one step for the atoms lo .. hi-1 only, with the bead
+ * forces supplied by the caller: the same splitting as or_step (Sec. 2.1),
+ * cut at the force evaluation, so that atoms can be advanced in separate
+ * shards once every bead's forces are known. Every coordinate (mode, atom,
+ * dim) gets exactly the operations of or_step, in the same order, with the
+ * same noise counters (global indices). Arrays are the full [P][N][3].
+ *   start:  OBABO: O(dt/2, stream 2), B(dt/2) with f, A(dt);
+ *           BAOAB: B(dt/2) with f, A(dt/2), O(dt, stream 2), A(dt/2);
+ *           then the bead positions xb of the range.
+ *   finish: B(dt/2) with the new forces f, then O(dt/2, stream 3) (OBABO).
+ * The heat of the range's O steps is added to *Q.                           */
+static void range_O(const or_sys* s, const double* wk, double h, uint32_t step, uint32_t stream, int lo, int hi,
+                    double* p_nm, double* Q)
+{
+    int N = s->N, P = s->P;
+    double kT = kT_P_md(s), dq = 0.0;
+    for (int k = 0; k < P; ++k) {
+        double gam = (k == 0) ? s->gamma0 : 2.0 * s->pile_lambda * wk[k];
+        double c1 = exp(-h * gam);
+        double c2 = sqrt(1.0 - c1 * c1);
+        for (int i = lo; i < hi; ++i)
+            for (int d = 0; d < 3; ++d) {
+                size_t g = ((size_t)k * N + i) * 3 + d;
+                double xi = or_normal(s->seed, (uint32_t)g, step, (uint32_t)s->replica, stream);
+                double mk = mode_mass(s, k, i);
+                double pn = c1 * p_nm[g] + sqrt(mk * kT) * c2 * xi;
+                dq += (pn * pn - p_nm[g] * p_nm[g]) / (2.0 * mk);
+                p_nm[g] = pn;
+            }
+    }
+    *Q += dq * MVV2E;
+}
+
+static void range_B(const or_sys* s, const double* C, const double* f, int lo, int hi, double* p_nm)
+{
+    int N = s->N, P = s->P;
+    if (s->transform == 1) {
+        double* fb = malloc(sizeof(double) * P);
+        double* Fu = malloc(sizeof(double) * P);
+        for (int i = lo; i < hi; ++i)
+            for (int d = 0; d < 3; ++d) {
+                for (int j = 0; j < P; ++j) fb[j] = f[((size_t)j * N + i) * 3 + d];
+                or_staging_forces(P, fb, Fu);
+                for (int k = 0; k < P; ++k) p_nm[((size_t)k * N + i) * 3 + d] += 0.5 * s->dt * Fu[k] / MVV2E;
+            }
+        free(fb);
+        free(Fu);
+        return;
+    }
+    for (int k = 0; k < P; ++k)
+        for (int i = lo; i < hi; ++i)
+            for (int d = 0; d < 3; ++d) {
+                double fn = 0.0;
+                for (int j = 0; j < P; ++j) fn += C[j * P + k] * f[((size_t)j * N + i) * 3 + d];
+                p_nm[((size_t)k * N + i) * 3 + d] += 0.5 * s->dt * fn / MVV2E;
+            }
+}
+
+static void range_A(const or_sys* s, const double* wk, double h, int lo, int hi, double* q_nm, double* p_nm)
+{
+    int N = s->N, P = s->P;
+    for (int k = 0; k < P; ++k)
+        for (int i = lo; i < hi; ++i)
+            for (int d = 0; d < 3; ++d) {
+                size_t g = ((size_t)k * N + i) * 3 + d;
+                or_free_rp_step(s->free_rp, mode_mass(s, k, i), k == 0 ? 0.0 : wk[k], h, &p_nm[g], &q_nm[g]);
+            }
+}
+
+void or_ring_start(const or_sys* s, uint64_t step, int lo, int hi, double* q_nm, double* p_nm, const double* f,
+                   double* xb, double* Q)
+{
+    int N = s->N, P = s->P;
+    double* C = malloc(sizeof(double) * P * P);
+    double* wk = malloc(sizeof(double) * P);
+    or_nm_matrix(P, C);
+    mode_freqs(s, wk);
+    uint32_t st = (uint32_t)step;
+    if (s->splitting == 1) {
+        range_B(s, C, f, lo, hi, p_nm);
+        range_A(s, wk, 0.5 * s->dt, lo, hi, q_nm, p_nm);
+        if (s->thermostat) range_O(s, wk, s->dt, st, 2u, lo, hi, p_nm, Q);
+        range_A(s, wk, 0.5 * s->dt, lo, hi, q_nm, p_nm);
+    } else {
+        if (s->thermostat) range_O(s, wk, 0.5 * s->dt, st, 2u, lo, hi, p_nm, Q);
+        range_B(s, C, f, lo, hi, p_nm);
+        range_A(s, wk, s->dt, lo, hi, q_nm, p_nm);
+    }
+    /* bead positions of the range (the transform of to_beads, per atom) */
+    double* u = malloc(sizeof(double) * P);
+    double* x = malloc(sizeof(double) * P);
+    for (int i = lo; i < hi; ++i)
+        for (int d = 0; d < 3; ++d) {
+            for (int k = 0; k < P; ++k) u[k] = q_nm[((size_t)k * N + i) * 3 + d];
+            if (s->transform == 1) {
+                or_staging_to_beads(P, u, x);
+            } else {
+                for (int j = 0; j < P; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < P; ++k) acc += C[j * P + k] * u[k];
+                    x[j] = acc;
+                }
+            }
+            for (int j = 0; j < P; ++j) xb[((size_t)j * N + i) * 3 + d] = x[j];
+        }
+    free(u); free(x); free(C); free(wk);
+}
+
+void or_ring_finish(const or_sys* s, uint64_t step, int lo, int hi, double* p_nm, const double* f, double* Q)
+{
+    int P = s->P;
+    double* C = malloc(sizeof(double) * P * P);
+    double* wk = malloc(sizeof(double) * P);
+    or_nm_matrix(P, C);
+    mode_freqs(s, wk);
+    range_B(s, C, f, lo, hi, p_nm);
+    if (s->thermostat && s->splitting != 1) range_O(s, wk, 0.5 * s->dt, (uint32_t)step, 3u, lo, hi, p_nm, Q);
+    free(C); free(wk);
+}
+
 /* ------------------------------------------------------------------------ */
 /* estimators of the finite-P ensemble average                               */
 /* ------------------------------------------------------------------------ */

@@ -123,6 +123,11 @@ int  or_forces(const or_sys* s, const or_model* m, const double* q_nm,
                double* xb, double* f, double* V, double* W);
 int  or_step(const or_sys* s, const or_model* m, int nsteps, uint64_t* step,
              double* q_nm, double* p_nm, double* f, double* V, double* W, double* Q_thermo);
+/* the two halves of one step for atoms lo .. hi-1 with caller-supplied bead
+ * forces (the sharded form of or_step) */
+void or_ring_start(const or_sys* s, uint64_t step, int lo, int hi, double* q_nm, double* p_nm, const double* f,
+                   double* xb, double* Q);
+void or_ring_finish(const or_sys* s, uint64_t step, int lo, int hi, double* p_nm, const double* f, double* Q);
 void or_estimators(const or_sys* s, const double* q_nm, const double* p_nm,
                    const double* f, const double* V, const double* W, double Q_thermo,
                    or_est* out);
