@@ -141,7 +141,7 @@ typedef struct {
     double xrd_Q;            /* XRD: |Q| = 4 pi sin(theta) / lambda, 1/A        */
     double xrd_f[PIMD_MAX_ELEMENTS]; /* XRD: scattering factor of each element
                                 in ascending-Z order (pimd_element_types)      */
-    double height_eV;        /* h0 > 0                                          */
+    double height_eV;        /* h0 >= 0 (0: the CV of every bead, no bias)      */
     double sigma;            /* Gaussian width > 0, CV units                    */
     double bias_factor;      /* gamma > 1                                       */
     int stride;              /* steps between depositions >= 1                  */
@@ -353,11 +353,51 @@ int pimd_get_forces(pimd_ctx* ctx, double* x_host, double* f_host, double* V_hos
  * Synchronises.                                                             */
 int pimd_get_neighbours(pimd_ctx* ctx, int* nnb_host, int* nbr_host);
 
-/* Device time (ms) of each stage of the most recent step run by pimd_step,
- * measured with CUDA events on the context stream (requires cfg.timing).
- * ms: host [PIMD_N_STAGES]. Synchronises. Errors: STATE without timing or
- * before the first step.                                                    */
+/* Device time (ms) of each stage of the last step of the most recent
+ * pimd_step call that ran with stage timing on, measured with CUDA events
+ * recorded inside the step's graph on the context stream (requires
+ * cfg.timing). ms: host [PIMD_N_STAGES]. Synchronises. Errors: STATE without
+ * timing or before the first marked step.                                   */
 int pimd_stage_times(pimd_ctx* ctx, float* ms);
+
+/* ---- ring-polymer step with forces from elsewhere (bead-sharded runs) -----
+ * The OBABO step cut at its force evaluation (Sec. 2.1: the beads of a ring
+ * polymer interact only through the springs of the ring-polymer step, so
+ * the forces of different beads can be evaluated apart). A run whose beads
+ * are spread over several GPUs gives each GPU a context holding all beads of
+ * a slice of the atoms (typically PIMD_POT_HARMONIC with omega_harm = 0, so
+ * that it evaluates no forces of its own) and advances it with:
+ *   pimd_set_forces(ctx, f)    bead forces of the current positions, once
+ *                              before the first step (and after set_state);
+ *   pimd_ring_start(ctx, x)    first half: OBABO O(dt/2) B(dt/2) A(dt)
+ *                              (BAOAB: B A O A) with the current forces, then
+ *                              the new bead positions into x;
+ *   pimd_ring_finish(ctx, f)   second half: B(dt/2) with the forces f of
+ *                              those positions, then O(dt/2); the step ends.
+ * x, f: device FP64 [sum P][N][3] in the context's (replica, bead, atom)
+ * order; f is rounded to the working precision like the library's own
+ * forces. pimd_set_noise_index makes replica `replica` draw its thermostat
+ * noise as atoms atom_offset .. of a system of n_atoms_total atoms, so that
+ * slices of one system reproduce the whole system's trajectory, and resets
+ * the replica's initial state (all beads at x0, momenta drawn at the new
+ * indices, step 0, no heat): call it right after pimd_create. Energies are
+ * not part of external forces, so the estimators of such a context hold the
+ * ring-polymer terms only. Context stream, no synchronisation except in
+ * pimd_set_noise_index. Errors: INVALID_ARG, STATE (start without forces,
+ * finish without a start). The paper has no counterpart of the split; it is
+ * the decomposition of its Sec. 2.1 step.                                   */
+int pimd_set_noise_index(pimd_ctx* ctx, int replica, int atom_offset, int n_atoms_total);
+int pimd_set_forces(pimd_ctx* ctx, const double* f);
+int pimd_ring_start(pimd_ctx* ctx, double* x);
+int pimd_ring_finish(pimd_ctx* ctx, const double* f);
+
+/* Stage timing on (default for cfg.timing contexts) or off. The event
+ * records that time the stages are nodes of the step's graph and cost some
+ * microseconds each, so with timing on only the last step of each pimd_step
+ * call carries them, and with it off no step does (the step then runs as
+ * fast as without cfg.timing). Errors: STATE without cfg.timing. The paper
+ * has no counterpart (instrumentation).                                     */
+int pimd_set_stage_timing(pimd_ctx* ctx, int on);
 
 /* Autotuner. Times the descriptor + adjoint kernels on the context's current
  * configuration for each candidate (pair sums with band length 4..16 of the
@@ -456,6 +496,54 @@ int pimd_rdf_counts(pimd_ctx* ctx, int replica, double r_max, int n_bins, unsign
  * (float)(v_min + k (v_max - v_min) / n_bins). Errors: INVALID_ARG.        */
 int pimd_pt_coordinate(pimd_ctx* ctx, int replica, const int* bond, int acceptor_Z, double v_min, double v_max,
                        int n_bins, float* v, unsigned long long* hist);
+
+/* g(r) of every element pair of a periodic replica (Figs. 8, 9) from pair
+ * counts of pimd_rdf_counts summed over n_configs bead configurations (one
+ * pimd_rdf_counts call adds P of them): g[p][k] = counts[p][k] /
+ * (n_configs n_pairs_p shell_k / V), shell_k = 4/3 pi ((k+1)^3 - k^3) dr^3,
+ * dr = r_max / n_bins, V the box volume, n_pairs_p = n_a n_b for types a != b
+ * and n_a (n_a - 1) / 2 for a = b (the replica's atoms of each type).
+ * counts: device [T (T + 1) / 2][n_bins] uint64; g: device, same shape,
+ * FP64. Context stream, no synchronisation. Errors: INVALID_ARG (replica,
+ * NULL pointers, n_bins outside 1..1024, r_max or n_configs <= 0, a
+ * non-periodic replica).                                                    */
+int pimd_rdf_gr(pimd_ctx* ctx, int replica, double r_max, int n_bins, double n_configs,
+                const unsigned long long* counts, double* g);
+
+/* ---- free-energy surfaces (Sec. 2.5) ---------------------------------------
+ * Path-integral reweighting: the quantum free energy along the CV is
+ * F(s) = -k_B T ln[(1/P) sum_k <delta(S(r^(k)) - s)>], the bead-resolved CV
+ * distributions averaged over the beads. Contexts created with cfg.metad
+ * evaluate the CV of every bead in each force evaluation (a zero-height,
+ * never-depositing bias, h0 = 0, gives the CV without biasing).
+ *
+ * pimd_cv_histogram adds the replica's current configuration (the P CVs and
+ * biases of the last force evaluation) as one sample: weight w = exp(sum_k
+ * V_b(s_k) / (k_B T P) - log_w_shift), which removes the bias V_b from the
+ * ring polymer's configurational weight (w = exp(-log_w_shift) when no hill
+ * has been deposited); hist[k][b] += w for bead k's bin b = floor((s_k -
+ * s_min) n_bins / (s_max - s_min)), counted only for 0 <= b < n_bins, and
+ * *wsum += w for every sample. The beads are summed in order by one thread,
+ * so the result does not depend on the run. hist: device [P][n_bins] FP64,
+ * wsum: device [1] FP64, both accumulated (the caller zeroes them). A
+ * constant log_w_shift keeps w in range over long runs and cancels in F.
+ *
+ * pimd_pi_fes turns such a histogram into F_k(s_b) = -k_B T ln(hist[k][b] /
+ * (wsum ds)) for every bead and the path-integral F(s_b) = -k_B T ln((1/P)
+ * sum_k hist[k][b] / (wsum ds)) = -k_B T ln[(1/P) sum_k exp(-F_k(s_b)/k_B T)],
+ * ds = (s_max - s_min) / n_bins, T the replica's temperature, in eV; +inf in
+ * empty bins. F: device [n_bins]; Fk: device [P][n_bins] or NULL.
+ *
+ * pimd_metad_fes gives F(s) = -(gamma / (gamma - 1)) V(s) from the
+ * replica's hills (the converged well-tempered bias), s and F device [n].
+ *
+ * All three run on the context stream without synchronising. Errors: STATE
+ * (no CV / bias configured; histogram and metad FES), INVALID_ARG.         */
+int pimd_cv_histogram(pimd_ctx* ctx, int replica, double s_min, double s_max, int n_bins, double log_w_shift,
+                      double* hist, double* wsum);
+int pimd_pi_fes(pimd_ctx* ctx, int replica, const double* hist, const double* wsum, double s_min, double s_max,
+                int n_bins, double* F, double* Fk);
+int pimd_metad_fes(pimd_ctx* ctx, int replica, const double* s, int n, double* F);
 
 /* ---- descriptors without any device allocation ------------------------------
  * The paper has no counterpart to this call. It serves callers that cannot

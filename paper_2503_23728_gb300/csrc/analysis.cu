@@ -6,6 +6,7 @@
 // minimum image in FP32, r2 = (dx dx + dy dy) + dz dz without contraction)
 // and bin edges formed in FP64 and rounded to FP32.
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -172,6 +173,28 @@ void launch_pt(const Dev& d, int rep, int P, int N, const int* bond, int t_acc, 
         pt_kernel<float><<<grid, 256, sm, st>>>((const float4*)d.x, d.reps, d.atype, rep, bond, t_acc, edges, n_bins,
                                                 inv_w, v_out, hist);
     }
+}
+
+// g(r) per element pair from pair counts summed over n_configs bead
+// configurations: counts / (n_configs pairs_p shell_k / volume), shell_k =
+// 4/3 pi ((k+1)^3 - k^3) dr^3; thread per (pair, bin)
+__global__ void rdf_gr_kernel(const unsigned long long* __restrict__ counts, RdfNorm nm, int n_pairs, int n_bins,
+                              double* __restrict__ g)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_pairs * n_bins) return;
+    const int p = q / n_bins, k = q - p * n_bins;
+    const double r0 = k * nm.dr, r1 = (k + 1) * nm.dr;
+    const double shell = 4.0 / 3.0 * CUDART_PI * (r1 * r1 * r1 - r0 * r0 * r0);
+    const double ideal = nm.n_configs * nm.pairs[p] * shell / nm.volume;
+    g[q] = ideal > 0.0 ? (double)counts[q] / ideal : 0.0;
+}
+
+void launch_rdf_gr(const unsigned long long* counts, const RdfNorm& nm, int n_pairs, int n_bins, double* g,
+                   cudaStream_t st)
+{
+    const int n = n_pairs * n_bins;
+    rdf_gr_kernel<<<(n + 127) / 128, 128, 0, st>>>(counts, nm, n_pairs, n_bins, g);
 }
 
 }  // namespace pimd

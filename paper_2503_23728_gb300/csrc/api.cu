@@ -52,6 +52,7 @@ struct Build {
     std::vector<int2> rp_blocks;
     std::vector<int> rep_blk0;
     std::vector<int> typeZ;
+    std::vector<double> repT;   // physical temperature of each replica, K
     std::vector<int> cell_bs;
     int total_cells = 0, max_cells = 0;
     int R = 0, S = 0, B = 0, NA = 0, rows_pad = 0;
@@ -98,7 +99,7 @@ struct Carve {
 struct Offsets {
     size_t reps, bsys, ba_sys, mass, minv, atype, x0, cmat, cmatf, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
-        fnm, Q, qpart, rep_blk0, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
+        fnm, Q, qpart, rep_blk0, step_cur, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
         md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, gfn_w,
         gfn_n, gfn_m, gfn_e, gfn_wtc, total;
 };
@@ -241,8 +242,8 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
             for (size_t t = 0; t < zs.size(); ++t)
                 if (!std::isfinite(m->xrd_f[t])) { e = "metad: xrd_f must be finite"; return PIMD_ERR_INVALID_ARG; }
         }
-        if (!(m->height_eV > 0.0) || !(m->sigma > 0.0) || !(m->bias_factor > 1.0) || m->stride < 1)
-            { e = "metad: need height_eV > 0, sigma > 0, bias_factor > 1, stride >= 1"; return PIMD_ERR_INVALID_ARG; }
+        if (!(m->height_eV >= 0.0) || !(m->sigma > 0.0) || !(m->bias_factor > 1.0) || m->stride < 1)
+            { e = "metad: need height_eV >= 0, sigma > 0, bias_factor > 1, stride >= 1"; return PIMD_ERR_INVALID_ARG; }
         if (m->max_hills < maxP || m->max_hills > (1 << 24)) { e = "metad: max_hills must be in [max P, 2^24]"; return PIMD_ERR_INVALID_ARG; }
     }
 
@@ -277,6 +278,9 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         }
         rp.kT_md = h.P * KB * h.T / MVV2E;
         rp.seed = h.seed;
+        rp.noise_atom0 = 0;
+        rp.noise_N = h.N;
+        b.repT.push_back(h.T);
         // Verlet skin of the candidate lists: at most 0.9 of the room between
         // r_c and half the box (unique minimum images), off below 0.05 A
         if (graph_pot(cfg->potential)) {
@@ -435,6 +439,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.Q = c.take(sizeof(double) * b.R);
     o.qpart = c.take(sizeof(double) * 2 * b.rp_blocks.size());
     o.rep_blk0 = c.take(sizeof(int) * b.rep_blk0.size());
+    o.step_cur = c.take(sizeof(unsigned long long));
     o.wbuf = c.take(rs * 9 * (size_t)b.B);
     o.vbuf = c.take(cfg->deterministic && model ? v4 * (size_t)b.B * mnb : 0);
     o.mom = c.take(model && cfg->precision != PIMD_FP64 ? sizeof(float4) * moment_elems_per_atom() * (size_t)b.B : 0);
@@ -493,7 +498,9 @@ struct pimd_ctx {
     DescParams<double> dpd;
     bool weights_set = false, forces_valid = false, beads_current = true;
     unsigned long long step_host = 0;
-    cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+    cudaGraphExec_t g1 = nullptr, g8 = nullptr;   // 1 and 8 steps, no stage markers
+    cudaGraphExec_t g1t = nullptr;                 // 1 step with the stage markers (timing contexts)
+    bool stage_timing = true;                      // mark the last step of each pimd_step call
     cudaStream_t cap = nullptr;
     cudaEvent_t ev[PIMD_N_STAGES + 1] = {};
     bool stepped = false;
@@ -502,6 +509,13 @@ struct pimd_ctx {
 };
 
 namespace {
+
+void drop_graphs(pimd_ctx* c)
+{
+    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
+    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    if (c->g1t) { cudaGraphExecDestroy(c->g1t); c->g1t = nullptr; }
+}
 
 int fail(pimd_ctx* c, int code, const std::string& msg)
 {
@@ -531,14 +545,18 @@ void mark(pimd_ctx* c, int i, cudaStream_t st, bool timed)
     if (timed && c->ev[i]) cudaEventRecordWithFlags(c->ev[i], st, cudaEventRecordExternal);
 }
 
-void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit = false)
+// zeroed: the ring start of this step has already cleared the forces, the
+// per-bead virials and energies
+void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit = false, bool zeroed = false)
 {
     Dev& d = c->d;
     const size_t v4 = d.precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
     const bool summed = d.potential == PIMD_POT_MODEL && adjoint_sums_energy(d, dparams(c));
-    cudaMemsetAsync(d.f, 0, v4 * d.B, st);
-    cudaMemsetAsync(d.W, 0, sizeof(double) * 9 * d.S, st);
-    if (summed) cudaMemsetAsync(d.V, 0, sizeof(double) * d.S, st);
+    if (!zeroed) {
+        cudaMemsetAsync(d.f, 0, v4 * d.B, st);
+        cudaMemsetAsync(d.W, 0, sizeof(double) * 9 * d.S, st);
+        if (summed) cudaMemsetAsync(d.V, 0, sizeof(double) * d.S, st);
+    }
     mark(c, PIMD_STAGE_NEIGHBOURS, st, timed);
     if (d.potential == PIMD_POT_HARMONIC) {
         launch_harmonic(d, st);
@@ -573,11 +591,11 @@ void eval_forces(pimd_ctx* c) { eval_forces(c, c->st); }
 void one_step(pimd_ctx* c, cudaStream_t st, bool timed)
 {
     mark(c, PIMD_STAGE_RING_START, st, timed);
-    launch_rp_start(c->d, st);
-    eval_forces(c, st, timed, true);
+    launch_rp_start(c->d, st);   // also clears f, W and V for the force evaluation
+    eval_forces(c, st, timed, true, true);
     mark(c, PIMD_STAGE_RING_FINISH, st, timed);
-    launch_rp_finish(c->d, true, st);
-    launch_bump_step(c->d, st);
+    launch_rp_finish(c->d, true, st);   // also advances the step counter
+    if (c->d.deterministic) launch_heat_sum(c->d, st);
     mark(c, PIMD_N_STAGES, st, timed);
 }
 
@@ -596,7 +614,7 @@ int refresh_forces(pimd_ctx* c)
 // Graphs are recorded on a private stream (the caller's stream may be the
 // legacy default stream, which cannot be captured) and launched on the
 // context stream.
-int capture(pimd_ctx* c, int nsteps, cudaGraphExec_t* out)
+int capture(pimd_ctx* c, int nsteps, bool marked, cudaGraphExec_t* out)
 {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaSuccess;
@@ -604,7 +622,7 @@ int capture(pimd_ctx* c, int nsteps, cudaGraphExec_t* out)
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamCreateWithFlags");
     e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamBeginCapture");
-    for (int s = 0; s < nsteps; ++s) one_step(c, c->cap, c->cfg.timing != 0 && s == nsteps - 1);
+    for (int s = 0; s < nsteps; ++s) one_step(c, c->cap, marked && s == nsteps - 1);
     e = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(out, g, 0);
@@ -639,6 +657,14 @@ int upload(pimd_ctx* c, void* dst, const std::vector<T>& v)
                       "upload");
 }
 
+}  // namespace
+
+namespace {
+int check_replica(pimd_ctx* c, int replica)
+{
+    if (replica < 0 || replica >= c->d.R) return fail(c, PIMD_ERR_INVALID_ARG, "replica out of range");
+    return PIMD_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -728,6 +754,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.Q = (double*)(w + o.Q);
     d.qpart = (double*)(w + o.qpart);
     d.rep_blk0 = (int*)(w + o.rep_blk0);
+    d.step_cur = (unsigned long long*)(w + o.step_cur);
     d.wbuf = w + o.wbuf;
     d.vbuf = w + o.vbuf;
     d.mom = (cfg->potential == PIMD_POT_MODEL && cfg->precision != PIMD_FP64) ? (void*)(w + o.mom) : nullptr;
@@ -1070,8 +1097,7 @@ int pimd_set_gfn(pimd_ctx* c, const pimd_gfn_desc* g)
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "GFN parameter upload");
     if (rc) return rc;
     d.gfn = gp;
-    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
-    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    drop_graphs(c);
     c->weights_set = true;
     rc = refresh_forces(c);
     if (!rc) rc = device_errors(c);
@@ -1089,15 +1115,22 @@ int pimd_step(pimd_ctx* c, int n_steps)
         rc = refresh_forces(c);
         if (rc) return rc;
     }
-    if (!c->g1) {
-        rc = capture(c, 1, &c->g1);
+    // the stage markers (event records inside the graph) cost time of their
+    // own, so only the last step of a call carries them, and only when asked
+    const bool marked = c->cfg.timing != 0 && c->stage_timing;
+    int left = n_steps - (marked ? 1 : 0);
+    if (left > 0 && !c->g1) {
+        rc = capture(c, 1, false, &c->g1);
         if (rc) return rc;
     }
-    if (n_steps >= 8 && !c->g8) {
-        rc = capture(c, 8, &c->g8);
+    if (left >= 8 && !c->g8) {
+        rc = capture(c, 8, false, &c->g8);
         if (rc) return rc;
     }
-    int left = n_steps;
+    if (marked && !c->g1t) {
+        rc = capture(c, 1, true, &c->g1t);
+        if (rc) return rc;
+    }
     while (left >= 8) {
         rc = cuda_check(c, cudaGraphLaunch(c->g8, c->st), "cudaGraphLaunch");
         if (rc) return rc;
@@ -1107,8 +1140,87 @@ int pimd_step(pimd_ctx* c, int n_steps)
         rc = cuda_check(c, cudaGraphLaunch(c->g1, c->st), "cudaGraphLaunch");
         if (rc) return rc;
     }
+    if (marked) {
+        rc = cuda_check(c, cudaGraphLaunch(c->g1t, c->st), "cudaGraphLaunch");
+        if (rc) return rc;
+        c->stepped = true;
+    }
     c->step_host += (unsigned long long)n_steps;
-    c->stepped = true;
+    return PIMD_OK;
+}
+
+int pimd_set_noise_index(pimd_ctx* c, int replica, int atom_offset, int n_atoms_total)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    Rep& rp = c->build.reps[replica];
+    if (atom_offset < 0 || n_atoms_total < rp.N || atom_offset > n_atoms_total - rp.N)
+        return fail(c, PIMD_ERR_INVALID_ARG, "the replica's atoms must lie inside 0 .. n_atoms_total - 1");
+    if ((long long)n_atoms_total * rp.P * 3 > 0xffffffffLL)
+        return fail(c, PIMD_ERR_INVALID_ARG, "noise counter index exceeds 32 bits");
+    rp.noise_atom0 = atom_offset;
+    rp.noise_N = n_atoms_total;
+    Dev& d = c->d;
+    rc = cuda_check(c, cudaMemcpyAsync(d.reps + replica, &rp, sizeof(Rep), cudaMemcpyHostToDevice, c->st), "copy");
+    // the initial state again, with the momenta drawn at the new indices
+    const unsigned long long zero = 0;
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(d.step, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->st), "copy");
+    if (!rc) rc = cuda_check(c, cudaMemsetAsync(d.Q, 0, sizeof(double) * d.R, c->st), "memset");
+    if (rc) return rc;
+    launch_rp_init(d, c->st);
+    launch_beads(d, c->st);
+    c->beads_current = true;
+    c->step_host = 0;
+    c->forces_valid = false;
+    rc = cuda_check(c, cudaStreamSynchronize(c->st), "initial state");
+    if (!rc && !(graph_pot(d.potential) && !c->weights_set)) rc = refresh_forces(c);
+    return rc;
+}
+
+int pimd_set_forces(pimd_ctx* c, const double* f_dev)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!f_dev) return fail(c, PIMD_ERR_INVALID_ARG, "f is NULL");
+    if (!c->beads_current) {
+        launch_beads(c->d, c->st);
+        c->beads_current = true;
+    }
+    launch_pack_forces(c->d, f_dev, c->st);
+    launch_rp_finish(c->d, false, c->st);   // f_nm = C^T f, no dynamics
+    c->forces_valid = true;
+    return cuda_check(c, cudaGetLastError(), "set forces");
+}
+
+int pimd_ring_start(pimd_ctx* c, double* x_dev)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!x_dev) return fail(c, PIMD_ERR_INVALID_ARG, "x is NULL");
+    if (!c->forces_valid) return fail(c, PIMD_ERR_STATE, "no forces for the first half step (pimd_set_forces)");
+    launch_rp_start(c->d, c->st);
+    launch_unpack(c->d, nullptr, nullptr, nullptr, x_dev, c->st);
+    c->forces_valid = false;   // the next forces belong to the new positions
+    return cuda_check(c, cudaGetLastError(), "ring start");
+}
+
+int pimd_ring_finish(pimd_ctx* c, const double* f_dev)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!f_dev) return fail(c, PIMD_ERR_INVALID_ARG, "f is NULL");
+    if (c->forces_valid) return fail(c, PIMD_ERR_STATE, "pimd_ring_finish without a pimd_ring_start before it");
+    launch_pack_forces(c->d, f_dev, c->st);
+    launch_rp_finish(c->d, true, c->st);
+    if (c->d.deterministic) launch_heat_sum(c->d, c->st);
+    c->forces_valid = true;
+    c->step_host += 1;
+    return cuda_check(c, cudaGetLastError(), "ring finish");
+}
+
+int pimd_set_stage_timing(pimd_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->cfg.timing) return fail(c, PIMD_ERR_STATE, "context was created without timing");
+    c->stage_timing = on != 0;
     return PIMD_OK;
 }
 
@@ -1177,8 +1289,7 @@ int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->d.sched = pick;
-    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
-    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    drop_graphs(c);
     if (!rc) rc = refresh_forces(c);   // forces with the chosen schedule
     if (!rc) rc = device_errors(c);
     if (out_ms) {
@@ -1196,8 +1307,7 @@ int pimd_set_schedule(pimd_ctx* c, int band_length)
         return fail(c, PIMD_ERR_INVALID_ARG, "band_length must be 0 or 1..16");
     const int ang = c->d.sched.ang;
     c->d.sched = band_length == 0 ? Sched{8, 1 << 30, 0, ang} : Sched{band_length, band_length + 32, 0, ang};
-    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
-    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    drop_graphs(c);
     c->forces_valid = false;
     return PIMD_OK;
 }
@@ -1210,8 +1320,7 @@ int pimd_set_angular(pimd_ctx* c, int algo)
     if (algo == PIMD_ANG_MOMENTS && !c->d.mom)
         return fail(c, PIMD_ERR_UNSUPPORTED, "moment tensors need the model potential in FP32 or BF16 precision");
     c->d.sched.ang = algo == PIMD_ANG_MOMENTS ? 1 : 0;
-    if (c->g1) { cudaGraphExecDestroy(c->g1); c->g1 = nullptr; }
-    if (c->g8) { cudaGraphExecDestroy(c->g8); c->g8 = nullptr; }
+    drop_graphs(c);
     c->forces_valid = false;
     return PIMD_OK;
 }
@@ -1225,9 +1334,10 @@ int pimd_get_angular(const pimd_ctx* c)
 int pimd_kernels_per_step(const pimd_ctx* c)
 {
     if (!c) return 0;
-    // ring start, ring finish, step counter; metadynamics: CV, bias, bias force
+    // ring start, ring finish (which also ends the step; deterministic mode
+    // adds the ordered heat sum); metadynamics: CV, bias, bias force
     const Dev& d = c->d;
-    const int ring = 3, md = d.metad.cv ? 3 : 0;
+    const int ring = 2 + (d.deterministic ? 1 : 0), md = d.metad.cv ? 3 : 0;
     if (d.potential == PIMD_POT_HARMONIC) return ring + 2 + md;   // harmonic forces, energy
     if (d.potential == PIMD_POT_GFN)   // neighbours, the head, energy
         return ring + 2 + 2 + gfn_kernels_per_eval(d.gfn.L) + md;
@@ -1411,13 +1521,6 @@ int pimd_sizes(const pimd_ctx* c, int64_t* B, int64_t* S, int* R, int* maxnb)
     return PIMD_OK;
 }
 
-namespace {
-int check_replica(pimd_ctx* c, int replica)
-{
-    if (replica < 0 || replica >= c->d.R) return fail(c, PIMD_ERR_INVALID_ARG, "replica out of range");
-    return PIMD_OK;
-}
-}  // namespace
 
 int pimd_metad_hills(pimd_ctx* c, int replica, double* s, double* h, int capacity)
 {
@@ -1542,12 +1645,83 @@ int pimd_pt_coordinate(pimd_ctx* c, int replica, const int* bond, int acceptor_Z
     return cuda_check(c, cudaGetLastError(), "proton-transfer kernel");
 }
 
+int pimd_rdf_gr(pimd_ctx* c, int replica, double r_max, int n_bins, double n_configs,
+                const unsigned long long* counts, double* g)
+{
+    static_assert(RDF_MAX_PAIRS == PIMD_MAX_ELEMENTS * (PIMD_MAX_ELEMENTS + 1) / 2, "pair slots");
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    if (!counts || !g) return fail(c, PIMD_ERR_INVALID_ARG, "counts or g is NULL");
+    if (n_bins < 1 || n_bins > ANALYSIS_MAX_BINS) return fail(c, PIMD_ERR_INVALID_ARG, "n_bins must be 1..1024");
+    if (!(r_max > 0.0)) return fail(c, PIMD_ERR_INVALID_ARG, "r_max must be > 0");
+    if (!(n_configs > 0.0)) return fail(c, PIMD_ERR_INVALID_ARG, "n_configs must be > 0");
+    const Rep& rp = c->build.reps[replica];
+    if (!rp.periodic) return fail(c, PIMD_ERR_INVALID_ARG, "g(r) needs a periodic replica (a box volume)");
+    const int T = (int)c->build.typeZ.size();
+    std::vector<double> n_per(T, 0.0);
+    for (int i = 0; i < rp.N; ++i) n_per[c->build.atype[rp.atom0 + i]] += 1.0;
+    RdfNorm nm{};
+    int p = 0;
+    for (int a = 0; a < T; ++a)
+        for (int b = a; b < T; ++b, ++p) nm.pairs[p] = a == b ? n_per[a] * (n_per[a] - 1.0) / 2.0 : n_per[a] * n_per[b];
+    nm.volume = rp.L[0] * rp.L[1] * rp.L[2];
+    nm.dr = r_max / n_bins;
+    nm.n_configs = n_configs;
+    launch_rdf_gr(counts, nm, p, n_bins, g, c->st);
+    return cuda_check(c, cudaGetLastError(), "g(r) kernel");
+}
+
+int pimd_cv_histogram(pimd_ctx* c, int replica, double s_min, double s_max, int n_bins, double log_w_shift,
+                      double* hist, double* wsum)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d.metad.cv) return fail(c, PIMD_ERR_STATE, "no collective variable configured (cfg.metad)");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    if (!hist || !wsum) return fail(c, PIMD_ERR_INVALID_ARG, "hist or wsum is NULL");
+    if (n_bins < 1 || n_bins > (1 << 20)) return fail(c, PIMD_ERR_INVALID_ARG, "n_bins must be 1..2^20");
+    if (!(s_max > s_min)) return fail(c, PIMD_ERR_INVALID_ARG, "s_max must exceed s_min");
+    if (!std::isfinite(log_w_shift)) return fail(c, PIMD_ERR_INVALID_ARG, "log_w_shift is not finite");
+    const Rep& rp = c->build.reps[replica];
+    const double kTP = KB * c->build.repT[replica] * rp.P;
+    launch_cv_hist(c->d, replica, rp.bs0, rp.P, kTP, s_min, n_bins / (s_max - s_min), n_bins, log_w_shift, hist,
+                   wsum, c->st);
+    return cuda_check(c, cudaGetLastError(), "cv histogram kernel");
+}
+
+int pimd_pi_fes(pimd_ctx* c, int replica, const double* hist, const double* wsum, double s_min, double s_max,
+                int n_bins, double* F, double* Fk)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    if (!hist || !wsum || !F) return fail(c, PIMD_ERR_INVALID_ARG, "hist, wsum or F is NULL");
+    if (n_bins < 1 || n_bins > (1 << 20)) return fail(c, PIMD_ERR_INVALID_ARG, "n_bins must be 1..2^20");
+    if (!(s_max > s_min)) return fail(c, PIMD_ERR_INVALID_ARG, "s_max must exceed s_min");
+    const Rep& rp = c->build.reps[replica];
+    launch_pi_fes(hist, wsum, rp.P, n_bins, (s_max - s_min) / n_bins, KB * c->build.repT[replica], F, Fk, c->st);
+    return cuda_check(c, cudaGetLastError(), "path-integral FES kernel");
+}
+
+int pimd_metad_fes(pimd_ctx* c, int replica, const double* s, int n, double* F)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d.metad.cv) return fail(c, PIMD_ERR_STATE, "no metadynamics bias configured");
+    int rc = check_replica(c, replica);
+    if (rc) return rc;
+    if (n < 0) return fail(c, PIMD_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return PIMD_OK;
+    if (!s || !F) return fail(c, PIMD_ERR_INVALID_ARG, "s or F is NULL");
+    launch_metad_fes(c->d, replica, s, n, F, c->st);
+    return cuda_check(c, cudaGetLastError(), "metadynamics FES kernel");
+}
+
 void pimd_destroy(pimd_ctx* c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->st);
-    if (c->g1) cudaGraphExecDestroy(c->g1);
-    if (c->g8) cudaGraphExecDestroy(c->g8);
+    drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (int i = 0; i <= PIMD_N_STAGES; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);

@@ -56,7 +56,10 @@ struct Rep {
     int cell0;               // first cell of bead 0; bead k owns cell0 + k ncells ..
     float skin;              // Verlet skin of the candidate lists, A (0 = rebuild every step)
     float rcs2;              // (float)((r_c + skin)^2), candidate radius squared
-    int pad;
+    // noise counters index atoms as atom noise_atom0 + i of a system of
+    // noise_N atoms (a shard of a larger ring polymer draws that system's
+    // deviates); 0 and N for a whole system
+    int noise_atom0, noise_N;
 };
 
 // one bead of one replica: N atoms starting at bead-atom index ba0

@@ -1519,6 +1519,16 @@ void launch_pack_positions(const Dev& d, const double* x3, cudaStream_t st)
         pack_kernel<float><<<blocks, 256, 0, st>>>(x3, (float4*)d.x, d.B);
 }
 
+// external bead forces [B][3] FP64 into the force records
+void launch_pack_forces(const Dev& d, const double* f3, cudaStream_t st)
+{
+    const int blocks = (d.B + 255) / 256;
+    if (d.precision == 0)
+        pack_kernel<double><<<blocks, 256, 0, st>>>(f3, (Dbl4*)d.f, d.B);
+    else
+        pack_kernel<float><<<blocks, 256, 0, st>>>(f3, (float4*)d.f, d.B);
+}
+
 template <typename Real>
 __global__ void unpack_kernel(const Vec4<Real>* __restrict__ f, const Vec4<Real>* __restrict__ x,
                               const double* __restrict__ V, const double* __restrict__ Wv, int B, int S,

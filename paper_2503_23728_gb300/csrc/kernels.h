@@ -58,6 +58,7 @@ struct Dev {
     double* Q = nullptr;               // [R] thermostat heat
     double* qpart = nullptr;           // [2][n_rp_blocks] thermostat heat per block and half step
     int* rep_blk0 = nullptr;           // [R + 1] first ring-polymer block of each replica
+    unsigned long long* step_cur = nullptr;   // the step being taken (copied by the ring start for the ring finish)
     void* wbuf = nullptr;              // Real[B][9] per bead-atom virial
     void* vbuf = nullptr;              // Vec4<Real>[B][maxnb] pair vectors (deterministic mode)
     void* mom = nullptr;               // float4[B][6][32] angular moments (moment path, FP32)
@@ -140,6 +141,7 @@ void launch_energy_reduce(const Dev& d, cudaStream_t st);
 void launch_force_gather(const Dev& d, cudaStream_t st);
 void launch_harmonic(const Dev& d, cudaStream_t st);
 void launch_pack_positions(const Dev& d, const double* x3, cudaStream_t st);
+void launch_pack_forces(const Dev& d, const double* f3, cudaStream_t st);
 void launch_unpack(const Dev& d, double* f3, double* e, double* vir, double* x3, cudaStream_t st);
 void launch_descriptors_out(const Dev& d, double* G, cudaStream_t st);
 bool network_tc_supported(int width, int n_hidden);
@@ -155,6 +157,20 @@ void launch_metad(const Dev& d, bool deposit, cudaStream_t st);
 size_t rdf_smem_bytes(int n_types, int n_bins);
 void launch_rdf(const Dev& d, int rep, int P, int N, const BinEdges& edges, int n_bins, float inv_dr,
                 unsigned long long* counts, cudaStream_t st);
+// normalisation of RDF counts: ideal-gas pairs per element pair, box volume,
+// shell width, number of configurations summed
+constexpr int RDF_MAX_PAIRS = 36;   // element pairs of up to 8 types
+struct RdfNorm {
+    double pairs[RDF_MAX_PAIRS];
+    double volume, dr, n_configs;
+};
+void launch_rdf_gr(const unsigned long long* counts, const RdfNorm& nm, int n_pairs, int n_bins, double* g,
+                   cudaStream_t st);
+void launch_cv_hist(const Dev& d, int replica, int bs0, int P, double kTP, double s_min, double inv_ds, int n_bins,
+                    double shift, double* hist, double* wsum, cudaStream_t st);
+void launch_pi_fes(const double* hist, const double* wsum, int P, int n_bins, double ds, double kT, double* F,
+                   double* Fk, cudaStream_t st);
+void launch_metad_fes(const Dev& d, int replica, const double* s, int n, double* F, cudaStream_t st);
 void launch_pt(const Dev& d, int rep, int P, int N, const int* bond, int t_acc, const BinEdges& edges, int n_bins,
                float inv_w, float* v_out, unsigned long long* hist, cudaStream_t st);
 
@@ -169,7 +185,7 @@ void launch_rp_init(const Dev& d, cudaStream_t st);
 void launch_beads(const Dev& d, cudaStream_t st);
 void launch_rp_start(const Dev& d, cudaStream_t st);
 void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st);
-void launch_bump_step(const Dev& d, cudaStream_t st);
+void launch_heat_sum(const Dev& d, cudaStream_t st);
 void launch_estimators(const Dev& d, cudaStream_t st);
 
 }  // namespace pimd

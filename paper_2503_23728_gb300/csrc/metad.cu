@@ -9,6 +9,7 @@
 // go down after the force evaluation of step n when (n + 1) % stride == 0,
 // one per bead at its CV with height (h0 / P) exp(-V(s_k) / (k_B T (gamma-1))).
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include "common.cuh"
 #include "geom.cuh"
@@ -280,6 +281,80 @@ void launch_metad(const Dev& d, bool deposit, cudaStream_t st)
     else
         bias_force_kernel<float><<<(d.B + 255) / 256, 256, 0, st>>>(d.ba_sys, (const float4*)d.md_grad, d.md_dvds,
                                                                     (float4*)d.f, d.B, nslice);
+}
+
+// ---------------------------------------------------------------------------
+// free-energy surfaces (Sec. 2.5)
+// ---------------------------------------------------------------------------
+// One sample of the bead-resolved CV histogram of the path-integral FES: the
+// replica's P beads (CVs and biases of the last force evaluation) with the
+// weight w = exp(sum_k V_b(s_k) / (k_B T P) - shift) that undoes the bias on
+// the ring polymer's configurational weight. One thread, beads in order, so
+// every sum has a fixed order.
+__global__ void cv_hist_kernel(const double* __restrict__ cv, const double* __restrict__ vb, int bs0, int P,
+                               double kTP, double s_min, double inv_ds, int n_bins, double shift,
+                               double* __restrict__ hist, double* __restrict__ wsum)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double v = 0.0;
+    for (int k = 0; k < P; ++k) v += vb[bs0 + k];
+    const double w = exp(v / kTP - shift);
+    for (int k = 0; k < P; ++k) {
+        const double tb = (cv[bs0 + k] - s_min) * inv_ds;
+        if (tb >= 0.0 && tb < (double)n_bins) hist[(size_t)k * n_bins + (int)floor(tb)] += w;
+    }
+    *wsum += w;
+}
+
+// F_k(s_b) = -k_B T ln(hist[k][b] / (wsum ds)) and the path-integral
+// F(s_b) = -k_B T ln((1/P) sum_k hist[k][b] / (wsum ds)); thread per bin
+__global__ void pi_fes_kernel(const double* __restrict__ hist, const double* __restrict__ wsum, int P, int n_bins,
+                              double ds, double kT, double* __restrict__ F, double* __restrict__ Fk)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bins) return;
+    const double ws = *wsum;
+    double tot = 0.0;
+    for (int k = 0; k < P; ++k) {
+        const double h = hist[(size_t)k * n_bins + b];
+        tot += h;
+        if (Fk) Fk[(size_t)k * n_bins + b] = h > 0.0 ? -kT * log(h / (ws * ds)) : CUDART_INF;
+    }
+    F[b] = tot > 0.0 ? -kT * log(tot / (P * ws * ds)) : CUDART_INF;
+}
+
+// F(s) = -(gamma / (gamma - 1)) V(s) over the replica's hills; thread per s
+__global__ void metad_fes_kernel(const double2* __restrict__ hills, const int* __restrict__ nhill, double sigma,
+                                 double gamma, const double* __restrict__ s, int n, double* __restrict__ F)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nh = *nhill;
+    double v = 0.0;
+    for (int h = 0; h < nh; ++h) {
+        const double u = s[i] - hills[h].x;
+        v += hills[h].y * exp(-0.5 * u * u / (sigma * sigma));
+    }
+    F[i] = -(gamma / (gamma - 1.0)) * v;
+}
+
+void launch_cv_hist(const Dev& d, int replica, int bs0, int P, double kTP, double s_min, double inv_ds, int n_bins,
+                    double shift, double* hist, double* wsum, cudaStream_t st)
+{
+    (void)replica;
+    cv_hist_kernel<<<1, 32, 0, st>>>(d.md_cv, d.md_vb, bs0, P, kTP, s_min, inv_ds, n_bins, shift, hist, wsum);
+}
+
+void launch_pi_fes(const double* hist, const double* wsum, int P, int n_bins, double ds, double kT, double* F,
+                   double* Fk, cudaStream_t st)
+{
+    pi_fes_kernel<<<(n_bins + 127) / 128, 128, 0, st>>>(hist, wsum, P, n_bins, ds, kT, F, Fk);
+}
+
+void launch_metad_fes(const Dev& d, int replica, const double* s, int n, double* F, cudaStream_t st)
+{
+    metad_fes_kernel<<<(n + 127) / 128, 128, 0, st>>>(d.md_hills + (size_t)replica * d.metad.max_hills,
+                                                       d.md_nhill + replica, d.metad.sigma, d.metad.gamma, s, n, F);
 }
 
 }  // namespace pimd

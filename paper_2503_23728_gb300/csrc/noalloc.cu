@@ -108,7 +108,7 @@ extern "C" int pimd_descriptors_noalloc(const double* x_dev, int n_atoms, const 
         rp.Llo[a] = (float)(rp.L[a] - (double)rp.Lf[a]);
     }
     BeadSys bs = {0, n_atoms, 0, 0};
-    DescParams<float> dp;
+    DescParams<float> dp{};   // r_even = 0: the FP32 path's exact radial Gaussians
     dp.rc = (float)cutoff_A;
     dp.pi_over_rc = (float)(M_PI / cutoff_A);
     dp.eta_R = (float)eta_R;

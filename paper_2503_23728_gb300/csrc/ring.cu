@@ -108,7 +108,7 @@ __global__ void rp_init_kernel(const Rep* __restrict__ reps, const BeadSys* __re
     const Rep& rp = reps[sy.rep];
     const int i = b - sy.ba0;
     const int k = sy.bead;
-    const unsigned local = (unsigned)((k * rp.N + i) * 3 + dd);
+    const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + i) * 3 + dd);
     const Mode md = modes[rp.mode0 + k];
     const double m = mass[rp.atom0 + i] * md.mfac;
     // all beads at x0: q_0 = P x0 / (column sum of mode 0), other modes 0
@@ -213,7 +213,9 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
                                 const double* __restrict__ mass, const double2* __restrict__ minv,
                                 const unsigned long long* __restrict__ stepp, double dt, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
                                 const double* __restrict__ fnm, Vec4<Real>* __restrict__ x,
-                                double* __restrict__ qpart)
+                                double* __restrict__ qpart, Vec4<Real>* __restrict__ f, double* __restrict__ W,
+                                double* __restrict__ V, double* __restrict__ Q, int ordered_heat,
+                                unsigned long long* __restrict__ stepc)
 {
     extern __shared__ double sq[];
     float* sqf = reinterpret_cast<float*>(sq + blockDim.x);
@@ -229,7 +231,7 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
         const double m = mass[rp.atom0 + t.i] * md.mfac, im = mi.x * md.imf, smkT = mi.y * md.smf;
         const double kick = 0.5 * dt * INV_MVV2E;
         double pv = p[g], qv = q[g];
-        const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
+        const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + t.i) * 3 + t.dd);
         if (baoab) {
             pv += kick * fnm[g];
             free_rp(k, md, m, im, 0.5 * dt, pv, qv);
@@ -252,24 +254,45 @@ __global__ void rp_start_kernel(const int2* __restrict__ blocks, const Rep* __re
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        qpart[blockIdx.x] = thermostat ? s * MVV2E : 0.0;
+        s = thermostat ? s * MVV2E : 0.0;
+        qpart[blockIdx.x] = s;
+        if (!ordered_heat && thermostat) atomicAdd(&Q[t.r], s);
+        if (blockIdx.x == 0) *stepc = *stepp;   // the step the ring finish will read
     }
     if (!t.active) return;
     const int j = t.kk;
     const double acc = to_bead<Real>(cmat + rp.cmat + (size_t)j * t.P, cmatf + rp.cmat + (size_t)j * t.P,
                                      sq + t.le, sqf + t.le, t.P, t.T);
     comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
+    // clear the force record of this bead-atom and, once per bead, its virial
+    // and energy, for the force evaluation that follows
+    if (t.dd == 0) {
+        Vec4<Real> z;
+        z.x = z.y = z.z = z.w = (Real)0;
+        f[rp.ba0 + (size_t)j * t.N + t.i] = z;
+        if (t.i == 0) {
+            const int bs = rp.bs0 + j;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) W[(size_t)bs * 9 + a] = 0.0;
+            V[bs] = 0.0;
+        }
+    }
 }
 
-// f_nm = C^T f; if do_step: B(dt/2), then O(dt/2) for OBABO
+// f_nm = C^T f; if do_step: B(dt/2), then O(dt/2) for OBABO, and the step
+// ends here: block 0 advances the step counter that the next ring start
+// reads (this kernel reads the copy that the ring start made), and each
+// block adds its thermostat heat to Q (FP64 atomics) unless the heat is
+// summed in a fixed order afterwards (deterministic mode).
 template <typename Real>
 __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
                                  const double* __restrict__ cmat, const float* __restrict__ cmatf,
                                  const Mode* __restrict__ modes,
                                  const double* __restrict__ mass, const double2* __restrict__ minv,
-                                 const unsigned long long* __restrict__ stepp, double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
+                                 const unsigned long long* stepp, double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
                                  double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ qpart,
-                                 DevErr* __restrict__ err)
+                                 DevErr* __restrict__ err, double* __restrict__ Q, int ordered_heat,
+                                 unsigned long long* stepw)
 {
     extern __shared__ double sf[];
     float* sff = reinterpret_cast<float*>(sf + blockDim.x);
@@ -304,7 +327,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
             const double2 mi = minv[rp.atom0 + t.i];
             double pv = p[g] + 0.5 * dt * INV_MVV2E * fn;
             if (thermostat) {
-                const unsigned local = (unsigned)((k * t.N + t.i) * 3 + t.dd);
+                const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + t.i) * 3 + t.dd);
                 dK = pile_o<Real>(rp, md, mi.y * md.smf, mi.x * md.imf, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
             }
             p[g] = pv;
@@ -313,17 +336,21 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
     dK = warp_sum(dK);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dK;
     __syncthreads();
-    if (threadIdx.x == 0 && do_step) {
+    if (!do_step) return;   // block-uniform
+    if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        qpart[gridDim.x + blockIdx.x] = thermostat ? s * MVV2E : 0.0;
+        s = thermostat ? s * MVV2E : 0.0;
+        qpart[gridDim.x + blockIdx.x] = s;
+        if (!ordered_heat && thermostat) atomicAdd(&Q[t.r], s);
+        if (blockIdx.x == 0) *stepw = *stepp + 1ull;   // no block of this kernel reads stepw
     }
 }
 
-// end of a step: thermostat heat of both O halves added per replica (one
-// block per replica, fixed-order reduction), then the step counter
-__global__ void bump_step_kernel(unsigned long long* step, double* __restrict__ Q, const double* __restrict__ qpart,
-                                 const int* __restrict__ rep_blk0, int nblk)
+// deterministic mode: thermostat heat of both O halves added per replica in a
+// fixed order (one block per replica) after the ring finish
+__global__ void heat_sum_kernel(double* __restrict__ Q, const double* __restrict__ qpart,
+                                const int* __restrict__ rep_blk0, int nblk)
 {
     __shared__ double red[8];
     const int r = blockIdx.x;
@@ -336,8 +363,12 @@ __global__ void bump_step_kernel(unsigned long long* step, double* __restrict__ 
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         Q[r] += t;
-        if (r == 0) *step += 1ull;
     }
+}
+
+void launch_heat_sum(const Dev& d, cudaStream_t st)
+{
+    heat_sum_kernel<<<d.R, 256, 0, st>>>(d.Q, d.qpart, d.rep_blk0, d.n_rp_blocks);
 }
 
 static size_t rp_smem(const Dev& d) { return (size_t)d.rp_threads * (sizeof(double) + sizeof(float)); }
@@ -357,29 +388,25 @@ void launch_rp_start(const Dev& d, cudaStream_t st)
     if (d.precision == 0)
         rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
-            (Dbl4*)d.x, d.qpart);
+            (Dbl4*)d.x, d.qpart, (Dbl4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
     else
         rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
-            (float4*)d.x, d.qpart);
+            (float4*)d.x, d.qpart, (float4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
 }
 
 void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
-            do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err);
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, d.dt, d.thermostat && !d.splitting,
+            do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
     else
         rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat && !d.splitting,
-            do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err);
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, d.dt, d.thermostat && !d.splitting,
+            do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
 }
 
-void launch_bump_step(const Dev& d, cudaStream_t st)
-{
-    bump_step_kernel<<<d.R, 256, 0, st>>>(d.step, d.Q, d.qpart, d.rep_blk0, d.n_rp_blocks);
-}
 
 // ---------------------------------------------------------------------------
 // a8: estimators in normal-mode space, one block per replica (FP64).

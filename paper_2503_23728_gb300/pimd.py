@@ -26,7 +26,8 @@ EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_w
            "pimd_stage_times", "pimd_kernels_per_step", "pimd_tune", "pimd_set_schedule", "pimd_set_angular", "pimd_get_angular",
            "pimd_element_types", "pimd_rdf_counts", "pimd_pt_coordinate",
            "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv", "pimd_selftest_bounded_wait",
-           "pimd_set_gfn"]
+           "pimd_set_gfn", "pimd_set_stage_timing", "pimd_rdf_gr", "pimd_cv_histogram", "pimd_pi_fes",
+           "pimd_metad_fes", "pimd_set_noise_index", "pimd_set_forces", "pimd_ring_start", "pimd_ring_finish"]
 ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
@@ -158,6 +159,15 @@ def load(path: str = LIB_PATH):
     L.pimd_rdf_counts.argtypes = [vp, ct.c_int, ct.c_double, ct.c_int, vp]
     L.pimd_pt_coordinate.argtypes = [vp, ct.c_int, vp, ct.c_int, ct.c_double, ct.c_double, ct.c_int, vp, vp]
     L.pimd_descriptors_noalloc.argtypes = [vp, ct.c_int, dp, ct.c_double, ct.c_double, dp, dp, vp, vp]
+    L.pimd_set_stage_timing.argtypes = [vp, ct.c_int]
+    L.pimd_rdf_gr.argtypes = [vp, ct.c_int, ct.c_double, ct.c_int, ct.c_double, vp, vp]
+    L.pimd_cv_histogram.argtypes = [vp, ct.c_int, ct.c_double, ct.c_double, ct.c_int, ct.c_double, vp, vp]
+    L.pimd_pi_fes.argtypes = [vp, ct.c_int, vp, vp, ct.c_double, ct.c_double, ct.c_int, vp, vp]
+    L.pimd_metad_fes.argtypes = [vp, ct.c_int, vp, ct.c_int, vp]
+    L.pimd_set_noise_index.argtypes = [vp, ct.c_int, ct.c_int, ct.c_int]
+    L.pimd_set_forces.argtypes = [vp, vp]
+    L.pimd_ring_start.argtypes = [vp, vp]
+    L.pimd_ring_finish.argtypes = [vp, vp]
     _lib = L
     return L
 
@@ -304,18 +314,6 @@ def pimd_metad_cv(ctx, S: int):
     return cv, vb
 
 
-def metad_fes(s_grid, hills_s, hills_h, sigma: float, bias_factor: float):
-    """Free-energy profile from a converged well-tempered bias (Sec. 2.5):
-    F(s) = -(gamma / (gamma - 1)) V(s), V the sum of the hills, shifted to a
-    zero minimum. With the bias on every bead's CV this is the bead-averaged
-    (path-integral) profile of Sec. 2.5."""
-    s_grid = np.asarray(s_grid, dtype=np.float64)
-    d = s_grid[:, None] - np.asarray(hills_s, dtype=np.float64)[None, :]
-    V = (np.asarray(hills_h, dtype=np.float64)[None, :] * np.exp(-0.5 * d * d / (sigma * sigma))).sum(axis=1)
-    F = -bias_factor / (bias_factor - 1.0) * V
-    return F - F.min()
-
-
 def pimd_element_types(ctx) -> list:
     z = (ct.c_int * 8)()
     n = int(load().pimd_element_types(ctx, z))
@@ -335,26 +333,6 @@ def pimd_pt_coordinate(ctx, replica: int, bond_ptr, acceptor_Z: int, v_min: floa
                                      ct.c_void_p(hist_ptr) if hist_ptr else None), ctx)
 
 
-def rdf_normalize(counts, n_per_type, volume: float, r_max: float, n_configs: int):
-    """g(r) per element pair from pair counts [T (T + 1) / 2, n_bins] summed
-    over n_configs configurations: counts / (ideal-gas pairs in the shell),
-    the ideal count being n_a n_b (a != b) or n_a (n_a - 1) / 2 (a = b) times
-    the shell volume over the box volume."""
-    counts = np.asarray(counts, dtype=np.float64)
-    T = len(n_per_type)
-    n_bins = counts.shape[1]
-    edges = np.arange(n_bins + 1) * (r_max / n_bins)
-    shell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
-    g = np.zeros_like(counts)
-    p = 0
-    for a in range(T):
-        for b in range(a, T):
-            pairs = n_per_type[a] * (n_per_type[a] - 1) / 2 if a == b else n_per_type[a] * n_per_type[b]
-            g[p] = counts[p] / (n_configs * pairs * shell / volume)
-            p += 1
-    return g
-
-
 def pimd_kernels_per_step(ctx) -> int:
     return int(load().pimd_kernels_per_step(ctx))
 
@@ -366,6 +344,9 @@ def pimd_descriptors_noalloc(x_ptr, n_atoms: int, box, cutoff: float, eta_R: flo
     b = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
     rm = np.ascontiguousarray(r_mu, dtype=np.float64)
     ea = np.ascontiguousarray(eta_A, dtype=np.float64)
+    # the library reads exactly 32, 4 and 3 values from these host arrays
+    if rm.size != 32 or ea.size != 4 or (b is not None and b.size != 3):
+        raise ValueError("r_mu needs 32 values, eta_A 4 and box 3 (or None)")
     _check(load().pimd_descriptors_noalloc(x_ptr, int(n_atoms), _dp(b), float(cutoff), float(eta_R), _dp(rm),
                                            _dp(ea), G_ptr, stream))
 
@@ -593,6 +574,34 @@ class Context:
     def stage_times(self) -> dict:
         return pimd_stage_times(self.h)
 
+    def set_noise_index(self, atom_offset: int, n_atoms_total: int, replica: int = 0):
+        """Draw the replica's thermostat noise as atoms atom_offset .. of a
+        system of n_atoms_total atoms (a slice of a larger ring polymer);
+        resets the replica's initial state."""
+        _check(load().pimd_set_noise_index(self.h, int(replica), int(atom_offset), int(n_atoms_total)), self.h)
+
+    def set_forces(self, f):
+        """Bead forces (CUDA FP64 [B, 3]) of the current positions, before the
+        first ring_start."""
+        f = f.contiguous()
+        _check(load().pimd_set_forces(self.h, ct.c_void_p(f.data_ptr())), self.h)
+
+    def ring_start(self):
+        """First half of a step with the current forces; the new bead
+        positions as a CUDA FP64 [B, 3] tensor."""
+        x = self.torch.empty((self.B, 3), dtype=self.torch.float64, device="cuda")
+        _check(load().pimd_ring_start(self.h, ct.c_void_p(x.data_ptr())), self.h)
+        return x
+
+    def ring_finish(self, f):
+        """Second half of the step with the forces f (CUDA FP64 [B, 3]) of the
+        positions ring_start returned."""
+        f = f.contiguous()
+        _check(load().pimd_ring_finish(self.h, ct.c_void_p(f.data_ptr())), self.h)
+
+    def set_stage_timing(self, on: bool):
+        _check(load().pimd_set_stage_timing(self.h, 1 if on else 0), self.h)
+
     def kernels_per_step(self) -> int:
         return pimd_kernels_per_step(self.h)
 
@@ -627,6 +636,52 @@ class Context:
             counts = torch.zeros((T * (T + 1) // 2, n_bins), dtype=torch.int64, device="cuda")
         pimd_rdf_counts(self.h, replica, r_max, n_bins, counts.data_ptr())
         return counts
+
+    def rdf_gr(self, counts, r_max: float, n_configs: float, replica: int = 0):
+        """g(r) per element pair (device FP64 tensor, counts' shape) from the
+        pair counts of rdf_counts summed over n_configs bead configurations."""
+        torch = self.torch
+        g = torch.empty(counts.shape, dtype=torch.float64, device="cuda")
+        _check(load().pimd_rdf_gr(self.h, int(replica), float(r_max), int(counts.shape[1]), float(n_configs),
+                                  ct.c_void_p(counts.data_ptr()), ct.c_void_p(g.data_ptr())), self.h)
+        return g
+
+    def cv_histogram(self, s_range, n_bins: int, hist=None, wsum=None, log_w_shift: float = 0.0,
+                     replica: int = 0):
+        """Adds the current configuration to the bead-resolved CV histogram
+        (device FP64 [P, n_bins] and [1], created zeroed when None) with the
+        weight that removes the bias; returns (hist, wsum)."""
+        torch = self.torch
+        if hist is None:
+            hist = torch.zeros((self.replicas[replica].n_beads, n_bins), dtype=torch.float64, device="cuda")
+        if wsum is None:
+            wsum = torch.zeros(1, dtype=torch.float64, device="cuda")
+        _check(load().pimd_cv_histogram(self.h, int(replica), float(s_range[0]), float(s_range[1]), int(n_bins),
+                                        float(log_w_shift), ct.c_void_p(hist.data_ptr()),
+                                        ct.c_void_p(wsum.data_ptr())), self.h)
+        return hist, wsum
+
+    def pi_fes(self, hist, wsum, s_range, replica: int = 0):
+        """(F [n_bins], F_k [P, n_bins]) in eV on the device: the path-integral
+        free energy and each bead's, from a cv_histogram histogram."""
+        torch = self.torch
+        P, n_bins = hist.shape
+        F = torch.empty(n_bins, dtype=torch.float64, device="cuda")
+        Fk = torch.empty((P, n_bins), dtype=torch.float64, device="cuda")
+        _check(load().pimd_pi_fes(self.h, int(replica), ct.c_void_p(hist.data_ptr()), ct.c_void_p(wsum.data_ptr()),
+                                  float(s_range[0]), float(s_range[1]), int(n_bins), ct.c_void_p(F.data_ptr()),
+                                  ct.c_void_p(Fk.data_ptr())), self.h)
+        return F, Fk
+
+    def metad_fes(self, s, replica: int = 0):
+        """F(s) = -(gamma / (gamma - 1)) V(s) of the replica's hills at the
+        CV values s (device FP64 tensor), on the device."""
+        torch = self.torch
+        s = s.to(device="cuda", dtype=torch.float64).contiguous()
+        F = torch.empty_like(s)
+        _check(load().pimd_metad_fes(self.h, int(replica), ct.c_void_p(s.data_ptr()), int(s.numel()),
+                                     ct.c_void_p(F.data_ptr())), self.h)
+        return F
 
     def pt_coordinate(self, bond, acceptor_Z: int = 8, v_range=(-2.0, 1.0), n_bins: int = 60, replica: int = 0):
         """Proton-transfer coordinate of every bead of one replica: (v [P, N]

@@ -54,12 +54,14 @@ def test_rdf_counts_water_bit_exact(water64_model, precision):
     t = _types(rep.Z, ctx.element_types() and [1, 8])
     want = sum(O.rdf_counts(xb[k], rep.box, t, 2, 6.0, 120) for k in range(3))
     assert np.array_equal(c, want)
-    # accumulation into a caller's array and the normalisation helper
+    # accumulation into a caller's array
     c2 = ctx.rdf_counts(6.0, 120, counts=torch.tensor(c.astype(np.int64), device="cuda")).cpu().numpy()
     assert np.array_equal(c2, 2 * c.astype(np.int64))
+    # g(r) on the device from the oracle's counts against the oracle's g(r)
     n_per = [int((rep.Z == 1).sum()), int((rep.Z == 8).sum())]
-    g = P.rdf_normalize(c, n_per, float(np.prod(rep.box)), 6.0, 3)
-    assert g.shape == c.shape and np.isfinite(g).all()
+    g = ctx.rdf_gr(torch.tensor(want.astype(np.int64), device="cuda"), 6.0, 3).cpu().numpy()
+    go = O.rdf_gr(want, n_per, float(np.prod(rep.box)), 6.0, 3)
+    np.testing.assert_allclose(g, go, rtol=1e-13, atol=0)
     assert g[2, :15].max() == 0.0                         # no O-O pairs below 0.75 A
 
 

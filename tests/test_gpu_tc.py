@@ -131,6 +131,6 @@ def test_ice_full_size_sampled_beads(ice_model, precision):
     st = ctx.stage_times()
     assert all(v >= 0 for v in st.values()) and st["adjoint"] > 0
     # ring start, skin check, lists, descriptors, network, adjoint, ring
-    # finish, step counter; the FP32 path adds the energy reduction (the BF16
-    # adjoint sums the per-bead energies and virials itself)
-    assert ctx.kernels_per_step() == (8 if precision == "bf16_tc" else 9)
+    # finish (which ends the step); the FP32 path adds the energy reduction
+    # (the BF16 adjoint sums the per-bead energies and virials itself)
+    assert ctx.kernels_per_step() == (7 if precision == "bf16_tc" else 8)
