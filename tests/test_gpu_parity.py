@@ -206,16 +206,49 @@ def test_neighbour_overflow_is_reported(water64_model):
 
 
 def test_autograd_energy(water_fp32):
+    """The torch.autograd.Function's backward (the adjoint kernel) against the
+    oracle's analytic gradient: x.grad of sum_k c_k e_k equals -c_k F_k with
+    F the FP64 oracle's forces on the same FP32 bead positions (1e-5
+    relative max-norm), and the forward's energies equal the oracle's."""
     P, w, rep, m, ctx, xb = water_fp32
     x = torch.tensor(xb.reshape(-1, 3), device="cuda", requires_grad=True)
     e = P.pimd_energy(x, ctx)
     coef = torch.linspace(0.5, 1.5, e.shape[0], device="cuda", dtype=torch.float64)
     (e * coef).sum().backward()
-    _, f, _ = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
-    bead = torch.arange(rep.n_beads, device="cuda").repeat_interleave(rep.n_atoms)
-    want = -(coef[bead].unsqueeze(1) * f)
-    # two evaluations agree to FP32 round-off (atomic accumulation order)
-    assert float((x.grad - want).abs().max() / want.abs().max()) < 1e-5
+    Eo, Fo, _ = O.energy_forces_batch(m, rep.Z, xb, rep.box)
+    c = coef.cpu().numpy()
+    want = -(c[:, None, None] * Fo)
+    got = x.grad.cpu().numpy().reshape(want.shape)
+    assert _relmax(got, want) < 1e-5
+    assert np.abs(e.detach().cpu().numpy() - Eo.sum(axis=1)).max() / rep.n_atoms < 1e-5
+
+
+def test_energy_central_differences_fp32(water64_model):
+    """Config 2's finite-difference check on the GPU: central differences of
+    the FP32 path's energy (through pimd_energy) for 8 random atoms of
+    water-64 against the oracle's analytic forces. The step is the FP32
+    rounding of x +- h, h = 2e-3 A; the FP32 energy's rounding (~1e-6 eV)
+    over 2h bounds the error at ~1e-3 of the force scale."""
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 1)
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths)
+    ctx.set_weights(m)
+    x0 = _bead_positions(rep, 1, seed=29)[0]
+    _, Fo, _ = O.energy_forces(m, rep.Z, x0, rep.box)
+    atoms = np.random.default_rng(31).choice(rep.n_atoms, size=8, replace=False)
+    h = 2e-3
+    fd = np.zeros((8, 3))
+    for a, i in enumerate(atoms):
+        for d in range(3):
+            xp, xm = x0.copy(), x0.copy()
+            xp[i, d] = np.float32(x0[i, d] + h)
+            xm[i, d] = np.float32(x0[i, d] - h)
+            with torch.no_grad():
+                ep = P.pimd_energy(torch.tensor(xp, device="cuda"), ctx).item()
+                em = P.pimd_energy(torch.tensor(xm, device="cuda"), ctx).item()
+            fd[a, d] = -(ep - em) / (xp[i, d] - xm[i, d])
+    assert np.abs(fd - Fo[atoms]).max() < 3e-3 * np.abs(Fo).max()
 
 
 # ---------------------------------------------------------------- uneven replicas
