@@ -175,8 +175,14 @@ def run_gpu(a, workload, precision, model=None):
     return ctx, model, stream, flush
 
 
-def timed_steps(a, ctx, stream, flush, barrier):
+def timed_steps(a, ctx, stream, flush, barrier, marked=False):
+    """K steps, each one graph launch bracketed by CUDA events on the context
+    stream, with the L2 flushed before each. marked: the steps carry the
+    stage markers (event records inside the step's graph, which cost time of
+    their own) and their stage times are returned; otherwise the steps run
+    without markers, as a user's steps do."""
     import torch
+    ctx.set_stage_timing(marked)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     stages = []
@@ -187,7 +193,8 @@ def timed_steps(a, ctx, stream, flush, barrier):
         starts[k].record(stream)
         ctx.step(1)
         ends[k].record(stream)
-        stages.append(ctx.stage_times())
+        if marked:
+            stages.append(ctx.stage_times())
     torch.cuda.synchronize()
     barrier()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -208,6 +215,37 @@ def adjoint_flops(ctx) -> float:
     if ctx.angular == "moments":
         return float(np.sum(MOM_ADJ_FLOP_PER_NBR * n + MOM_ADJ_FLOP_PER_ATOM))
     return float(np.sum(ADJ_FLOP_PER_PAIR * n * (n - 1) / 2 + ADJ_FLOP_PER_NBR * n))
+
+
+def forward_kernel_name(ctx) -> str:
+    if ctx.angular == "moments":
+        return "desc_mom_fwd_red_kernel" if ctx.precision == "bf16_tc" else "desc_mom_fwd_kernel"
+    return "desc_fwd_kernel"
+
+
+def forward_flops(ctx) -> float:
+    """Algorithmic FP32 work of the descriptor forward. Moment path, reduced
+    basis: per neighbour the 81 monomials x 4 widths multiply-adds into the
+    moments plus geometry, the 32 radial Gaussians and the 4 angular weights
+    (~200 flop); per bead-atom the rebuild of the 84 other moments (4 widths,
+    2 flop each) and G from the squared moments (165 monomials x 4 widths x
+    (1 square + 4 zeta x 2 lambda multiply-adds)). Pair sums: 81 flop per
+    pair (see the design notes) plus the per-neighbour terms."""
+    nnb, _ = ctx.neighbours()
+    n = nnb.astype(np.float64)
+    if ctx.angular == "moments":
+        per_nbr = (81 if ctx.precision == "bf16_tc" else 165) * 4 * 2 + 200
+        per_atom = 84 * 4 * 2 + 165 * 4 * (1 + 8) * 2
+        return float(np.sum(per_nbr * n + per_atom))
+    return float(np.sum(81 * n * (n - 1) / 2 + 200 * n))
+
+
+def step_roofline_ms(fp32_flops: float, tc_flops: float, peaks: dict) -> float:
+    """Bound of one step: the slower of its FP32 work on the derived FP32 peak
+    and its tensor-core work on the measured BF16 peak (the HBM traffic of a
+    step, ~0.3 GB, is below both)."""
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    return max(fp32_flops / (FP32_PEAK_TFLOPS * 1e12), tc_flops / (bf16 * 1e12)) * 1e3
 
 
 def network_flops(ctx, widths) -> float:
@@ -386,15 +424,28 @@ def s_model(w):
     return s.xavier_model(s.elements_of(w.replicas), w.widths, seed=7)
 
 
-def cpu_baseline(workload, model, budget_s=15.0):
-    """FP64 oracle on the host cores: force evaluations of whole beads of the
-    same workload until ~budget_s of CPU work."""
-    import oracle as O
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_beads(O, workload, model, budget_s, seed):
     rep = workload.replicas[0]
-    rng = np.random.default_rng(5)
-    threads = O.threads()
-    done, t0 = 0, time.perf_counter()
-    beads = 0
+    rng = np.random.default_rng(seed)
+    done, beads, t0 = 0, 0, time.perf_counter()
     while beads < rep.n_beads:
         x = rep.x0 + rng.normal(scale=0.05, size=rep.x0.shape)
         O.energy_forces(model, rep.Z, x, rep.box)
@@ -402,11 +453,28 @@ def cpu_baseline(workload, model, budget_s=15.0):
         done += rep.n_atoms
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
+    return done, beads, time.perf_counter() - t0
+
+
+def cpu_baseline(workload, model, budget_s=15.0, single_budget_s=8.0):
+    """FP64 oracle on the host cores: force evaluations of whole beads of the
+    same workload until ~budget_s of CPU work with OpenMP over all cores,
+    then at least one bead on a single thread."""
+    import oracle as O
+    rep = workload.replicas[0]
+    threads = O.threads()
+    done, beads, dt = _oracle_beads(O, workload, model, budget_s, 5)
+    O.set_threads(1)
+    try:
+        done1, beads1, dt1 = _oracle_beads(O, workload, model, single_budget_s, 6)
+    finally:
+        O.set_threads(threads)
     return {"value": done / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d of %d beads of the %s workload (%d bead-atoms), full FP64 force evaluation, "
                       "OpenMP over atoms" % (beads, rep.n_beads, workload.name, done),
-            "seconds": dt}
+            "seconds": dt, "cpu_model": cpu_model(),
+            "single_thread": {"value": done1 / dt1, "unit": UNIT, "cores": 1, "seconds": dt1,
+                              "sample": "%d bead(s) (%d bead-atoms) on one thread" % (beads1, done1)}}
 
 
 def max_over_ranks(value: float, dist=None, device=None) -> float:
@@ -472,7 +540,8 @@ def main():
     w = workload_of(a.workload, rank)
     ctx, model, stream, flush = run_gpu(a, w, a.precision)
     clk = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
-    ms, stages = timed_steps(a, ctx, stream, flush, barrier)
+    ms, _ = timed_steps(a, ctx, stream, flush, barrier)                      # the headline: no markers
+    ms_marked, stages = timed_steps(a, ctx, stream, flush, barrier, True)    # stage and kernel times
     clocks = clk.stop()
     total_ms = max_over_ranks(float(np.sum(ms)), dist, "cuda")
     steps_per_s = a.steps / (total_ms / 1e3)
@@ -482,6 +551,7 @@ def main():
     adj_flops = adjoint_flops(ctx)
     adj_ms = st_mean["adjoint"]
     achieved = adj_flops / (adj_ms / 1e3) / 1e12
+    fwd_flops = forward_flops(ctx)
     net_flops = network_flops(ctx, w.widths)
     peaks = {}
     try:
@@ -498,10 +568,18 @@ def main():
     fp32 = None
     if not a.no_fp32 and a.precision != "fp32":
         ctx2, _, stream2, flush2 = run_gpu(a, w, "fp32", model)
-        ms2, stages2 = timed_steps(a, ctx2, stream2, flush2, barrier)
+        ms2, _ = timed_steps(a, ctx2, stream2, flush2, barrier)
+        _, stages2 = timed_steps(a, ctx2, stream2, flush2, barrier, True)
         t2 = float(np.sum(ms2))
+        st2 = {k: float(np.mean([s[k] for s in stages2])) for k in stages2[0]}
         fp32 = {"value": world * w.bead_atoms * a.steps / (t2 / 1e3), "ms_per_step": t2 / a.steps,
-                "stages_ms": {k: float(np.mean([s[k] for s in stages2])) for k in stages2[0]}}
+                "stages_ms": st2,
+                "network_fp32": {"flops_per_launch": net_flops, "ms": st2["network"],
+                                 "achieved_tflops": net_flops / (st2["network"] / 1e3) / 1e12,
+                                 "frac_fp32_peak": net_flops / (st2["network"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
+                "adjoint": {"kernel": adjoint_kernel_name(ctx2), "flops_per_launch": adjoint_flops(ctx2),
+                            "ms": st2["adjoint"],
+                            "frac_fp32_peak": adjoint_flops(ctx2) / (st2["adjoint"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS}}
         ctx2.close()
     if rank != 0:
         ctx.close()
@@ -524,7 +602,17 @@ def main():
                      "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": ADJ_TRAFFIC_NCU.get((w.name, a.precision, ctx.angular)),
                      "flops_per_launch": adj_flops,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     # the whole step against its own bound: FP32 work of the
+                     # descriptor forward and the adjoint on the FP32 pipes,
+                     # network work on the tensor cores (measured BF16 peak)
+                     "step_frac": step_roofline_ms(fwd_flops + adj_flops, net_flops, peaks) / (total_ms / a.steps),
+                     "step_bound_ms": step_roofline_ms(fwd_flops + adj_flops, net_flops, peaks)},
+        "descriptor_forward": {"kernel": forward_kernel_name(ctx), "flops_per_launch": fwd_flops,
+                               "ms": st_mean["descriptors"],
+                               "achieved_tflops": fwd_flops / (st_mean["descriptors"] / 1e3) / 1e12,
+                               "frac_fp32_peak": fwd_flops / (st_mean["descriptors"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
+        "ms_per_step_with_stage_markers": float(np.sum(ms_marked)) / a.steps,
         "network_tensor": {"flops_per_launch": net_flops, "ms": st_mean["network"],
                            "achieved_tflops": net_flops / (st_mean["network"] / 1e3) / 1e12,
                            "peak_bf16_tflops_measured": peaks.get("bf16_tflops")},
