@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -56,6 +57,7 @@ struct Build {
     std::vector<int> cell_bs;
     int total_cells = 0, max_cells = 0;
     int R = 0, S = 0, B = 0, NA = 0, rows_pad = 0;
+    int split_ba = 0, split_tile = 0;   // halves of the bead-atoms / network tiles (0: one branch)
     size_t blob = 0, wtc_bytes = 0, wtc_vec = 0;
     size_t gfn_params = 0;   // FP32 parameters of the graph-field-network head
     bool periodic_any = false;
@@ -374,20 +376,38 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
     }
     b.rep_blk0.push_back((int)b.rp_blocks.size());
     b.nb_est /= std::max(1, b.B);
-    // network rows grouped by element type, each group padded to 128 rows
+    // network rows grouped by element type, each group padded to 128 rows.
+    // Large BF16 workloads split their bead-atoms into two halves of whole
+    // bead-systems (the two branches of an overlapped step); each half has
+    // its own element groups and tiles.
     if (cfg->potential == PIMD_POT_MODEL) {
-        std::vector<std::vector<int>> rows(zs.size());
-        for (int r = 0; r < n; ++r) {
-            const Rep& rp = b.reps[r];
-            for (int k = 0; k < rp.P; ++k)
-                for (int i = 0; i < rp.N; ++i) rows[b.atype[rp.atom0 + i]].push_back(rp.ba0 + k * rp.N + i);
+        b.split_ba = 0;
+        if (cfg->precision == PIMD_BF16_TC && b.B >= 16384 && b.S >= 2) {
+            int best = 0;
+            for (const BeadSys& sy : b.bsys)
+                if (std::abs(2 * sy.ba0 - b.B) < std::abs(2 * best - b.B)) best = sy.ba0;
+            b.split_ba = best;
         }
-        for (size_t t = 0; t < zs.size(); ++t) {
-            std::vector<int> v = rows[t];
-            std::sort(v.begin(), v.end());
-            size_t padded = (v.size() + TILE_ROWS - 1) / TILE_ROWS * TILE_ROWS;
-            for (size_t q = 0; q < padded; ++q) b.perm.push_back(q < v.size() ? v[q] : -1);
-            for (size_t q = 0; q < padded / TILE_ROWS; ++q) b.tile_type.push_back((int)t);
+        const int halves = b.split_ba > 0 ? 2 : 1;
+        for (int hv = 0; hv < halves; ++hv) {
+            const int lo = hv == 0 ? 0 : b.split_ba, hi = (hv == 0 && halves == 2) ? b.split_ba : b.B;
+            if (hv == 1) b.split_tile = (int)b.tile_type.size();
+            std::vector<std::vector<int>> rows(zs.size());
+            for (int r = 0; r < n; ++r) {
+                const Rep& rp = b.reps[r];
+                for (int k = 0; k < rp.P; ++k)
+                    for (int i = 0; i < rp.N; ++i) {
+                        const int ba = rp.ba0 + k * rp.N + i;
+                        if (ba >= lo && ba < hi) rows[b.atype[rp.atom0 + i]].push_back(ba);
+                    }
+            }
+            for (size_t t = 0; t < zs.size(); ++t) {
+                std::vector<int> v = rows[t];
+                std::sort(v.begin(), v.end());
+                size_t padded = (v.size() + TILE_ROWS - 1) / TILE_ROWS * TILE_ROWS;
+                for (size_t q = 0; q < padded; ++q) b.perm.push_back(q < v.size() ? v[q] : -1);
+                for (size_t q = 0; q < padded / TILE_ROWS; ++q) b.tile_type.push_back((int)t);
+            }
         }
         b.rows_pad = (int)b.perm.size();
         b.blob = blob_elems(cfg->n_hidden, cfg->widths);
@@ -501,7 +521,10 @@ struct pimd_ctx {
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;   // 1 and 8 steps, no stage markers
     cudaGraphExec_t g1t = nullptr;                 // 1 step with the stage markers (timing contexts)
     bool stage_timing = true;                      // mark the last step of each pimd_step call
+    bool overlap = true;                           // overlapped halves in unmarked step graphs
     cudaStream_t cap = nullptr;
+    cudaStream_t cap2 = nullptr;                   // second branch of an overlapped step (capture only)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev[PIMD_N_STAGES + 1] = {};
     bool stepped = false;
     std::string err;
@@ -547,7 +570,10 @@ void mark(pimd_ctx* c, int i, cudaStream_t st, bool timed)
 
 // zeroed: the ring start of this step has already cleared the forces, the
 // per-bead virials and energies
-void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit = false, bool zeroed = false)
+// branch: the step may run the force evaluation as two overlapping branches
+// (captured graphs without stage markers)
+void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit = false, bool zeroed = false,
+                 bool branch = false)
 {
     Dev& d = c->d;
     const size_t v4 = d.precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
@@ -571,6 +597,27 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
         if (d.gfn_wtc) launch_gfn_tc(d, st);
         else launch_gfn(d, st);
         mark(c, PIMD_STAGE_ADJOINT, st, timed);
+    } else if (branch && d.split_ba > 0 && moment_fast_path(d, dparams(c)) && network_tiles_available(d) && c->cap2 &&
+               c->ev_fork) {
+        // two halves of the bead-atoms as overlapping branches: the second
+        // half's forward starts when the first half's ends, so the first
+        // half's network (latency-bound, short) and adjoint run beside the
+        // second half's forward and network, and every kernel's last wave is
+        // filled by the other branch
+        const void* dp = dparams(c);
+        const int nt = d.rows_pad / TILE_ROWS;
+        launch_neighbours(d, st);
+        launch_descriptors_range(d, dp, 0, d.split_ba, st);
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
+        launch_descriptors_range(d, dp, d.split_ba, d.B, c->cap2);
+        launch_network_tiles(d, 0, d.split_tile, st, true);
+        launch_adjoint_range(d, dp, 0, d.split_ba, st);
+        launch_network_tiles(d, d.split_tile, nt - d.split_tile, c->cap2, true);
+        launch_adjoint_range(d, dp, d.split_ba, d.B, c->cap2);
+        cudaEventRecord(c->ev_join, c->cap2);
+        cudaStreamWaitEvent(st, c->ev_join, 0);
+        if (d.deterministic) launch_force_gather(d, st);
     } else {
         launch_neighbours(d, st);
         mark(c, PIMD_STAGE_DESCRIPTORS, st, timed);
@@ -592,7 +639,7 @@ void one_step(pimd_ctx* c, cudaStream_t st, bool timed)
 {
     mark(c, PIMD_STAGE_RING_START, st, timed);
     launch_rp_start(c->d, st);   // also clears f, W and V for the force evaluation
-    eval_forces(c, st, timed, true, true);
+    eval_forces(c, st, timed, true, true, !timed && c->overlap);
     mark(c, PIMD_STAGE_RING_FINISH, st, timed);
     launch_rp_finish(c->d, true, st);   // also advances the step counter
     if (c->d.deterministic) launch_heat_sum(c->d, st);
@@ -620,6 +667,12 @@ int capture(pimd_ctx* c, int nsteps, bool marked, cudaGraphExec_t* out)
     cudaError_t e = cudaSuccess;
     if (!c->cap) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamCreateWithFlags");
+    if (c->d.split_ba > 0 && !c->cap2) {
+        e = cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_check(c, e, "branch stream");
+    }
     e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamBeginCapture");
     for (int s = 0; s < nsteps; ++s) one_step(c, c->cap, marked && s == nsteps - 1);
@@ -811,6 +864,8 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.perm = (int*)(w + o.perm);
     d.tile_type = (int*)(w + o.tile_type);
     d.rows_pad = b.rows_pad;
+    d.split_ba = b.split_ba;
+    d.split_tile = b.split_tile;
     d.n_types = (int)b.typeZ.size();
     d.n_hidden = cfg->n_hidden;
     d.width = cfg->widths[0];
@@ -1214,6 +1269,14 @@ int pimd_ring_finish(pimd_ctx* c, const double* f_dev)
     c->forces_valid = true;
     c->step_host += 1;
     return cuda_check(c, cudaGetLastError(), "ring finish");
+}
+
+int pimd_set_overlap(pimd_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->overlap != (on != 0)) drop_graphs(c);
+    c->overlap = on != 0;
+    return (c->d.split_ba > 0 && network_tiles_available(c->d)) ? 1 : 0;
 }
 
 int pimd_set_stage_timing(pimd_ctx* c, int on)
@@ -1723,6 +1786,9 @@ void pimd_destroy(pimd_ctx* c)
     cudaStreamSynchronize(c->st);
     drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (int i = 0; i <= PIMD_N_STAGES; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     delete c;

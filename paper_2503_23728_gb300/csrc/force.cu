@@ -1122,7 +1122,9 @@ void launch_adjoint(const Dev& d, const void* dpv, cudaStream_t st)
 // ---------------------------------------------------------------------------
 // a4 on CUDA cores: per-element network forward and input gradient for a
 // tile of TM rows of one element. Activations of every layer stay in shared
-// memory; weight chunks of 32 along K are staged through shared memory.
+// memory, k-major ([feature][row]), so that a thread's rows are contiguous;
+// weight chunks of 32 along K pass through two shared-memory buffers; each
+// thread holds an RT x CT block of the layer's output in registers.
 // ---------------------------------------------------------------------------
 size_t blob_elems(int n_hidden, const int* widths)
 {
@@ -1135,48 +1137,128 @@ size_t blob_elems(int n_hidden, const int* widths)
     return o + prev + 1 + 2 * ND + 2;
 }
 
-constexpr int KC = 32;   // K chunk staged per step
+constexpr int KC = 32;   // K chunk of the weights staged per step
+constexpr int APAD = 4;  // row padding of the k-major activation tiles (keeps 16-byte alignment)
 
-// out[TM][NOUT] = A[TM][K] * Bmat[K][NOUT]; Bmat(k, o) = W[o * ldw + k] when
-// transB (forward: W is [out][in]), else W[k * ldw + o] (backward).
-// 256 threads: row group tr = tid / 16 owns RT rows, column lane tc owns
-// columns tc + 16 m.
-template <typename Real, int RT, int CT, bool transB>
-__device__ __forceinline__ void tile_gemm(const Real* __restrict__ Asm, int lda, int K, const Real* __restrict__ W,
-                                          int ldw, int NOUT, Real* __restrict__ Bs, Real (&acc)[RT][CT])
+// N consecutive values at p (16-byte aligned when N * sizeof(Real) >= 16)
+template <typename Real, int N>
+__device__ __forceinline__ void ld_vec(const Real* __restrict__ p, Real (&v)[N])
 {
-    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
-    const int ldb = NOUT + 1;
+    if constexpr (sizeof(Real) == 4 && N % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 x = reinterpret_cast<const float4*>(p)[q];
+            v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+        }
+    } else if constexpr (N % 2 == 0) {
+        using V2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q) {
+            const V2 x = reinterpret_cast<const V2*>(p)[q];
+            v[2 * q] = x.x; v[2 * q + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) v[q] = p[q];
+    }
+}
+
+template <typename Real, int N>
+__device__ __forceinline__ void st_vec(Real* __restrict__ p, const Real (&v)[N])
+{
+    if constexpr (sizeof(Real) == 4 && N % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q)
+            reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) p[q] = v[q];
+    }
+}
+
+// Column m of thread tx in a tile product: groups of 4 consecutive columns,
+// the threads' groups side by side (16 threads x 4 columns = 64), so that a
+// 16-byte load by the 16 column threads reads 256 contiguous bytes.
+__device__ __forceinline__ int tile_col(int tx, int m) { return (m >> 2) * 64 + tx * 4 + (m & 3); }
+
+// Register-blocked tile product out[TM][NOUT] = A[TM][K] Bmat[K][NOUT] with
+// A stored k-major in shared memory (A(r, k) = At[k * lda + r]) and
+// Bmat(k, o) = W[o * ldw + k] when transB (forward: W is [out][in]), else
+// W[k * ldw + o] (backward). 256 threads as 16 row groups x 16 column
+// groups: thread (ty, tx) owns the contiguous rows ty RT .. and the columns
+// tile_col(tx, m), so per k it loads RT + CT values as 16-byte vectors and
+// issues RT x CT multiply-adds. The weights pass through two shared-memory buffers
+// of KC rows: while a chunk is multiplied, each thread holds its share of
+// the next chunk in registers and stores it into the other buffer after, so
+// the global loads overlap the arithmetic (one barrier per chunk).
+template <typename Real, int RT, int CT, bool transB>
+__device__ __forceinline__ void tile_gemm(const Real* __restrict__ At, int lda, int K, const Real* __restrict__ W,
+                                          int ldw, Real* __restrict__ Bs, Real (&acc)[RT][CT])
+{
+    constexpr int NOUT = 16 * CT;
+    constexpr int ldb = NOUT + APAD;
+    constexpr int PER = KC * NOUT / 256;   // chunk elements per thread
+    static_assert(PER * 256 == KC * NOUT, "chunk split over the threads");
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
 #pragma unroll
     for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int m = 0; m < CT; ++m) acc[i][m] = Real(0);
-    for (int k0 = 0; k0 < K; k0 += KC) {
-        __syncthreads();
-        if (transB) {
-            for (int e = tid; e < KC * NOUT; e += 256) {
+    Real pre[PER];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + 256 * q;
+            if (transB) {
                 const int o = e / KC, kk = e - o * KC;
-                Bs[kk * ldb + o] = W[(size_t)o * ldw + k0 + kk];
-            }
-        } else {
-            for (int e = tid; e < KC * NOUT; e += 256) {
+                pre[q] = W[(size_t)o * ldw + k0 + kk];
+            } else {
                 const int kk = e / NOUT, o = e - kk * NOUT;
-                Bs[kk * ldb + o] = W[(size_t)(k0 + kk) * ldw + o];
+                pre[q] = W[(size_t)(k0 + kk) * ldw + o];
             }
         }
-        __syncthreads();
+    };
+    auto stash = [&](Real* buf) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + 256 * q;
+            if (transB) {
+                const int o = e / KC, kk = e - o * KC;
+                buf[kk * ldb + o] = pre[q];
+            } else {
+                const int kk = e / NOUT, o = e - kk * NOUT;
+                buf[kk * ldb + o] = pre[q];
+            }
+        }
+    };
+    __syncthreads();   // earlier readers of the buffers and of At's producers are done
+    fetch(0);
+    stash(Bs);
+    __syncthreads();
+    int cur = 0;
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        const bool more = k0 + KC < K;
+        if (more) fetch(k0 + KC);
+        const Real* B0 = Bs + cur * KC * ldb;
 #pragma unroll 4
         for (int kk = 0; kk < KC; ++kk) {
-            Real a[RT], bb[CT];
+            Real a[RT], b[CT];
+            ld_vec<Real, RT>(At + (size_t)(k0 + kk) * lda + ty * RT, a);
 #pragma unroll
-            for (int i = 0; i < RT; ++i) a[i] = Asm[(tr * RT + i) * lda + k0 + kk];
+            for (int g = 0; g < CT / 4; ++g) {
+                Real b4[4];
+                ld_vec<Real, 4>(B0 + kk * ldb + g * 64 + tx * 4, b4);
 #pragma unroll
-            for (int m = 0; m < CT; ++m) bb[m] = Bs[kk * ldb + tc + 16 * m];
+                for (int j = 0; j < 4; ++j) b[4 * g + j] = b4[j];
+            }
 #pragma unroll
             for (int i = 0; i < RT; ++i)
 #pragma unroll
-                for (int m = 0; m < CT; ++m) acc[i][m] += a[i] * bb[m];
+                for (int m = 0; m < CT; ++m) acc[i][m] = fma(a[i], b[m], acc[i][m]);
         }
+        if (more) stash(Bs + (cur ^ 1) * KC * ldb);
+        __syncthreads();
+        cur ^= 1;
     }
 }
 
@@ -1190,12 +1272,14 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
 {
     constexpr int TM = RT * 16;
     constexpr int Wd = CT * 16;         // hidden width
+    constexpr int lda = TM + APAD;      // activations are k-major: [feature][row]
+    constexpr int BW = (Wd > ND ? Wd : ND) + APAD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* H0 = reinterpret_cast<Real*>(smem_raw);            // [TM][ND + 1]
-    Real* Hl = H0 + TM * (ND + 1);                          // [n_hidden][TM][Wd + 1]
-    Real* Bs = Hl + (size_t)n_hidden * TM * (Wd + 1);       // [KC][max(Wd, ND) + 1]
-    Real* yv = Bs + KC * (Wd + 1);                          // [TM]
-    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    Real* H0 = reinterpret_cast<Real*>(smem_raw);            // [ND][lda]
+    Real* Hl = H0 + ND * lda;                                 // [n_hidden][Wd][lda]
+    Real* Bs = Hl + (size_t)n_hidden * Wd * lda;              // [2][KC][BW]
+    Real* yv = Bs + 2 * KC * BW;                              // [TM]
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int row0 = blockIdx.x * TM;
     const int type = tile_type[row0 / TILE_ROWS];
     const Real* P = wts + (size_t)type * blob;
@@ -1215,33 +1299,34 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
     const Real* sigma = P + off; off += ND;
     const Real s_E = P[off], e_Z = P[off + 1];
 
-    // h_0 = (G - mu) / sigma
+    // h_0 = (G - mu) / sigma, stored k-major
     for (int e = tid; e < TM * ND; e += 256) {
         const int r = e / ND, c = e - r * ND;
         const int ba = perm[row0 + r];
-        H0[r * (ND + 1) + c] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : Real(0);
+        H0[c * lda + r] = ba >= 0 ? (G[(size_t)ba * ND + c] - mu[c]) / sigma[c] : Real(0);
     }
     // forward through the hidden layers
     for (int l = 0; l < n_hidden; ++l) {
-        const Real* Ain = (l == 0) ? H0 : Hl + (size_t)(l - 1) * TM * (Wd + 1);
-        const int lda = (l == 0) ? ND + 1 : Wd + 1;
+        const Real* Ain = (l == 0) ? H0 : Hl + (size_t)(l - 1) * Wd * lda;
         const int K = (l == 0) ? ND : Wd;
         Real acc[RT][CT];
-        tile_gemm<Real, RT, CT, true>(Ain, lda, K, Wl[l], K, Wd, Bs, acc);
-        Real* Hout = Hl + (size_t)l * TM * (Wd + 1);
+        tile_gemm<Real, RT, CT, true>(Ain, lda, K, Wl[l], K, Bs, acc);
+        Real* Hout = Hl + (size_t)l * Wd * lda;
 #pragma unroll
-        for (int i = 0; i < RT; ++i)
+        for (int m = 0; m < CT; ++m) {
+            const int o = tile_col(tx, m);
+            const Real bo = bl[l][o];
+            Real v[RT];
 #pragma unroll
-            for (int m = 0; m < CT; ++m) {
-                const int o = tc + 16 * m;
-                Hout[(tr * RT + i) * (Wd + 1) + o] = f_tanh(acc[i][m] + bl[l][o]);
-            }
+            for (int i = 0; i < RT; ++i) v[i] = f_tanh(acc[i][m] + bo);
+            st_vec<Real, RT>(Hout + (size_t)o * lda + ty * RT, v);
+        }
     }
     __syncthreads();
-    Real* HL = Hl + (size_t)(n_hidden - 1) * TM * (Wd + 1);
+    Real* HL = Hl + (size_t)(n_hidden - 1) * Wd * lda;
     if (tid < TM) {
         Real y = b_out;
-        for (int k = 0; k < Wd; ++k) y += w_out[k] * HL[tid * (Wd + 1) + k];
+        for (int k = 0; k < Wd; ++k) y += w_out[k] * HL[k * lda + tid];
         yv[tid] = y;
         const int ba = perm[row0 + tid];
         if (ba >= 0) Eatom[ba] = s_E * y + e_Z;
@@ -1249,51 +1334,60 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
     __syncthreads();
     // dE/da_L = s_E w_out (1 - h_L^2), written over h_L
     for (int e = tid; e < TM * Wd; e += 256) {
-        const int r = e / Wd, k = e - r * Wd;
-        const Real h = HL[r * (Wd + 1) + k];
-        HL[r * (Wd + 1) + k] = s_E * w_out[k] * (Real(1) - h * h);
+        const int k = e / TM, r = e - k * TM;
+        const Real h = HL[k * lda + r];
+        HL[k * lda + r] = s_E * w_out[k] * (Real(1) - h * h);
     }
-    // backward: dE/dh_{l-1} = W_l^T dE/da_l
+    // backward: dE/dh_{l-1} = W_l^T dE/da_l, times tanh' of layer l-1
     for (int l = n_hidden - 1; l >= 0; --l) {
-        const Real* Ga = Hl + (size_t)l * TM * (Wd + 1);
+        const Real* Ga = Hl + (size_t)l * Wd * lda;
         if (l > 0) {
             Real acc[RT][CT];
-            tile_gemm<Real, RT, CT, false>(Ga, Wd + 1, Wd, Wl[l], Wd, Wd, Bs, acc);
-            Real* Hp = Hl + (size_t)(l - 1) * TM * (Wd + 1);
+            tile_gemm<Real, RT, CT, false>(Ga, lda, Wd, Wl[l], Wd, Bs, acc);
+            Real* Hp = Hl + (size_t)(l - 1) * Wd * lda;
 #pragma unroll
-            for (int i = 0; i < RT; ++i)
+            for (int m = 0; m < CT; ++m) {
+                const int k = tile_col(tx, m);
+                Real h[RT];
+                ld_vec<Real, RT>(Hp + (size_t)k * lda + ty * RT, h);
 #pragma unroll
-                for (int m = 0; m < CT; ++m) {
-                    const int k = tc + 16 * m;
-                    const int r = tr * RT + i;
-                    const Real h = Hp[r * (Wd + 1) + k];
-                    Hp[r * (Wd + 1) + k] = acc[i][m] * (Real(1) - h * h);
-                }
+                for (int i = 0; i < RT; ++i) h[i] = acc[i][m] * (Real(1) - h[i] * h[i]);
+                st_vec<Real, RT>(Hp + (size_t)k * lda + ty * RT, h);
+            }
         } else {
-            Real acc[RT][ND / 16];
-            tile_gemm<Real, RT, ND / 16, false>(Ga, Wd + 1, Wd, Wl[0], ND, ND, Bs, acc);
+            constexpr int C0 = ND / 16;
+            Real acc[RT][C0];
+            tile_gemm<Real, RT, C0, false>(Ga, lda, Wd, Wl[0], ND, Bs, acc);
+            static_assert(C0 == 4, "one group of 4 descriptor columns per thread");
+            Real is[C0];
+#pragma unroll
+            for (int m = 0; m < C0; ++m) is[m] = Real(1) / sigma[tile_col(tx, m)];
 #pragma unroll
             for (int i = 0; i < RT; ++i) {
-                const int r = tr * RT + i;
-                const int ba = perm[row0 + r];
+                const int ba = perm[row0 + ty * RT + i];
                 if (ba < 0) continue;
+                Real v[C0];
 #pragma unroll
-                for (int m = 0; m < ND / 16; ++m) {
-                    const int c = tc + 16 * m;
-                    dEdG[(size_t)ba * ND + c] = acc[i][m] / sigma[c];
-                }
+                for (int m = 0; m < C0; ++m) v[m] = acc[i][m] * is[m];
+                st_vec<Real, C0>(dEdG + (size_t)ba * ND + tx * C0, v);
             }
         }
-        __syncthreads();
     }
+}
+
+template <typename Real, int RT, int CT>
+static size_t mlp_fp_smem(int n_hidden)
+{
+    constexpr int TM = RT * 16, Wd = CT * 16;
+    constexpr int lda = TM + APAD, BW = (Wd > ND ? Wd : ND) + APAD;
+    return sizeof(Real) * ((size_t)ND * lda + (size_t)n_hidden * Wd * lda + (size_t)2 * KC * BW + TM);
 }
 
 template <typename Real, int RT, int CT>
 static void run_mlp_fp(const Dev& d, cudaStream_t st)
 {
-    constexpr int TM = RT * 16, Wd = CT * 16;
-    const size_t sm = sizeof(Real) * ((size_t)TM * (ND + 1) + (size_t)d.n_hidden * TM * (Wd + 1) +
-                                      (size_t)KC * (Wd + 1) + TM);
+    constexpr int TM = RT * 16;
+    const size_t sm = mlp_fp_smem<Real, RT, CT>(d.n_hidden);
     static size_t done = 0;
     set_smem(mlp_fp_kernel<Real, RT, CT>, sm, done);
     mlp_fp_kernel<Real, RT, CT><<<d.rows_pad / TM, 256, sm, st>>>(
@@ -1304,13 +1398,10 @@ static void run_mlp_fp(const Dev& d, cudaStream_t st)
 template <typename Real, int CT>
 static void dispatch_rows(const Dev& d, cudaStream_t st)
 {
-    constexpr int Wd = CT * 16;
     // largest row tile whose activations fit in ~200 KB of shared memory
-    const size_t per_row = sizeof(Real) * ((ND + 1) + (size_t)d.n_hidden * (Wd + 1) + 1);
-    const size_t fixed = sizeof(Real) * (size_t)KC * (Wd + 1);
-    if (fixed + per_row * 64 <= 200 * 1024)
+    if (mlp_fp_smem<Real, 4, CT>(d.n_hidden) <= 200 * 1024)
         run_mlp_fp<Real, 4, CT>(d, st);
-    else if (fixed + per_row * 32 <= 200 * 1024)
+    else if (mlp_fp_smem<Real, 2, CT>(d.n_hidden) <= 200 * 1024)
         run_mlp_fp<Real, 2, CT>(d, st);
     else
         run_mlp_fp<Real, 1, CT>(d, st);

@@ -94,6 +94,10 @@ struct Dev {
     int* perm = nullptr;               // [rows_pad] bead-atom of each network row, -1 pad
     int* tile_type = nullptr;          // [rows_pad / 128]
     int rows_pad = 0;
+    // two halves of the bead-atoms (whole bead-systems) for overlapping
+    // branches of the step: bead-atoms [0, split_ba) and [split_ba, B), network
+    // tiles [0, split_tile) and [split_tile, rows_pad / 128); 0 = one branch
+    int split_ba = 0, split_tile = 0;
     void* wtc = nullptr;               // tensor-core weight images
     size_t wtc_bytes_per_type = 0;
     float* wtc_vec = nullptr;          // FP32 vectors for the tensor-core epilogues
@@ -125,6 +129,13 @@ void launch_neighbours(const Dev& d, cudaStream_t st);
 void launch_descriptors(const Dev& d, const void* dp, cudaStream_t st);
 void launch_network_fp(const Dev& d, cudaStream_t st);
 void launch_network_tc(const Dev& d, cudaStream_t st);
+// halves of a step's bead-atoms as overlapping branches (BF16 moment path)
+bool moment_fast_path(const Dev& d, const void* dp);
+void launch_descriptors_range(const Dev& d, const void* dp, int b0, int b1, cudaStream_t st);
+void launch_adjoint_range(const Dev& d, const void* dp, int b0, int b1, cudaStream_t st);
+// urgent: the network's blocks at the highest stream priority
+bool launch_network_tiles(const Dev& d, int t0, int nt, cudaStream_t st, bool urgent = false);
+bool network_tiles_available(const Dev& d);
 void launch_adjoint(const Dev& d, const void* dp, cudaStream_t st);
 // true when the adjoint kernel also sums the per-bead energies V and virials
 // W (FP64 atomics; V and W zeroed before): the energy reduction is skipped

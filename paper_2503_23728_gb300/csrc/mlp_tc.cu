@@ -314,7 +314,7 @@ template <int W, int L>
 __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
     const float* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
     const unsigned char* __restrict__ wimg, size_t img_per_type, const float* __restrict__ wvec,
-    size_t vec_per_type, float* __restrict__ Eatom, float* __restrict__ dEdG, DevErr* __restrict__ err)
+    size_t vec_per_type, float* __restrict__ Eatom, float* __restrict__ dEdG, DevErr* __restrict__ err, int tile0)
 {
     constexpr int M = 128;
     constexpr int A0_B = M * ND * 2;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hsel = warp >> 2;
     const int row = 32 * q + lane;
-    const int row0 = blockIdx.x * M;
+    const int row0 = (tile0 + blockIdx.x) * M;   // tiles tile0 .. of the launch
     const int type = tile_type[row0 / TILE_ROWS];
     const unsigned char* img = wimg + (size_t)type * img_per_type;
     const float* vec = wvec + (size_t)type * vec_per_type;
@@ -927,20 +927,49 @@ static size_t park_smem()
 }
 
 template <int W, int L>
-static void run_tc(const Dev& d, cudaStream_t st)
+static bool run_tc_park(const Dev& d, int t0, int nt, cudaStream_t st, bool urgent = false)
 {
     if constexpr (park_cols<W, L>() <= 256) {
+        if (nt <= 0) return true;
         const size_t sm = park_smem<W, L>();
         static size_t done = 0;
         if (sm > done) {
             cudaFuncSetAttribute(mlp_tc_park_kernel<W, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             done = sm;
         }
-        mlp_tc_park_kernel<W, L><<<d.rows_pad / 128, TC_THREADS, sm, st>>>(
+        if (urgent) {
+            // the highest stream priority of the device for this launch: its
+            // blocks are placed before those of concurrent kernels
+            int least = 0, greatest = 0;
+            cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributePriority;
+            at[0].val.priority = greatest;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(nt);
+            cfg.blockDim = dim3(TC_THREADS);
+            cfg.dynamicSmemBytes = sm;
+            cfg.stream = st;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, mlp_tc_park_kernel<W, L>, (const float*)d.G, (const int*)d.perm,
+                               (const int*)d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type,
+                               (const float*)d.wtc_vec, d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err,
+                               t0);
+            return true;
+        }
+        mlp_tc_park_kernel<W, L><<<nt, TC_THREADS, sm, st>>>(
             (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
-            d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err);
-        return;
+            d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err, t0);
+        return true;
     }
+    return false;
+}
+
+template <int W, int L>
+static void run_tc(const Dev& d, cudaStream_t st)
+{
+    if (run_tc_park<W, L>(d, 0, d.rows_pad / 128, st)) return;
     const bool db = tc_smem(W, L, true) <= 227 * 1024;
     const size_t sm = tc_smem(W, L, db);
     static size_t done[2] = {0, 0};
@@ -975,6 +1004,39 @@ static void run_tc_wide(const Dev& d, cudaStream_t st)
     mlp_tc_wide_kernel<L><<<d.rows_pad / 128, TC_THREADS, sm, st>>>(
         (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
         d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err);
+}
+
+// Whether launch_network_tiles can run this configuration's network (widths
+// 64 / 128 with the hidden activations parked in tensor memory).
+bool network_tiles_available(const Dev& d)
+{
+    if (d.precision != 2 || d.rows_pad == 0) return false;
+    if (d.width == 64) return 64 + (d.n_hidden - 1) * 32 <= 256;
+    if (d.width == 128) return 128 + (d.n_hidden - 1) * 64 <= 256;
+    return false;
+}
+
+// The tiles t0 .. t0+nt-1 only (widths 64 / 128 with parked activations);
+// false when the configuration uses another network kernel.
+bool launch_network_tiles(const Dev& d, int t0, int nt, cudaStream_t st, bool urgent)
+{
+    if (d.width == 64) {
+        switch (d.n_hidden) {
+            case 1: return run_tc_park<64, 1>(d, t0, nt, st, urgent);
+            case 2: return run_tc_park<64, 2>(d, t0, nt, st, urgent);
+            case 3: return run_tc_park<64, 3>(d, t0, nt, st, urgent);
+            default: return run_tc_park<64, 4>(d, t0, nt, st, urgent);
+        }
+    }
+    if (d.width == 128) {
+        switch (d.n_hidden) {
+            case 1: return run_tc_park<128, 1>(d, t0, nt, st, urgent);
+            case 2: return run_tc_park<128, 2>(d, t0, nt, st, urgent);
+            case 3: return run_tc_park<128, 3>(d, t0, nt, st, urgent);
+            default: return run_tc_park<128, 4>(d, t0, nt, st, urgent);
+        }
+    }
+    return false;
 }
 
 void launch_network_tc(const Dev& d, cudaStream_t st)

@@ -390,7 +390,7 @@ template <bool FAST>
 __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
-    DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout)
+    DescParams<float> dp, float* __restrict__ G, float4* __restrict__ Mout, int b0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wib = threadIdx.x >> 5;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
     float* ROW = reinterpret_cast<float*>(smem_raw) + (size_t)wib * FWDR_WARP_FLOATS;
     float4* W0 = reinterpret_cast<float4*>(ROW + 32 * NBASE);   // b_eta
     float4* W1 = W0 + FWDR_WPAD;                                 // b_eta u_x
-    const int b = blockIdx.x * FWDR_WARPS + wib;
+    const int b = b0 + blockIdx.x * FWDR_WARPS + wib;   // bead-atoms b0 .. B-1
     if (b >= B) return;
     const BeadSys sy = bsys[ba_sys[b]];
     const Rep& rp = reps[sy.rep];
@@ -1121,7 +1121,7 @@ __global__ void __launch_bounds__(32 * ADJF_WARPS, 12) desc_mom_adj_fast_kernel(
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
     float4* __restrict__ f, float* __restrict__ wbuf, int det, float4* __restrict__ vbuf,
-    const float* __restrict__ Eatom, double* __restrict__ V, double* __restrict__ Wv)
+    const float* __restrict__ Eatom, double* __restrict__ V, double* __restrict__ Wv, int b0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wib = threadIdx.x >> 5;
@@ -1131,7 +1131,7 @@ __global__ void __launch_bounds__(32 * ADJF_WARPS, 12) desc_mom_adj_fast_kernel(
     float4* Phi = Qr + NRED;                                                             // [s], over eta
     float4* RG = Phi + (MDEG + 1);
     float* gA = reinterpret_cast<float*>(RG + ADJF_RG);
-    const int b = blockIdx.x * ADJF_WARPS + wib;
+    const int b = b0 + blockIdx.x * ADJF_WARPS + wib;   // bead-atoms b0 .. B-1
     if (b >= B) return;
 
     // loads that depend only on b first: moments (copied asynchronously into
@@ -1336,30 +1336,48 @@ static void run_adj(const Dev& d, const void* dpv, cudaStream_t st)
         (float*)d.wbuf, d.deterministic, (float4*)d.vbuf);
 }
 
-static void run_fwd_red(const Dev& d, const void* dpv, cudaStream_t st)
+static void run_fwd_red(const Dev& d, const void* dpv, int b0, int b1, cudaStream_t st)
 {
+    if (b1 <= b0) return;
     const size_t sm = (size_t)FWDR_WARPS * FWDR_WARP_FLOATS * sizeof(float);
     { static size_t done = 0; set_smem(desc_mom_fwd_red_kernel<true>, sm, done); }
-    desc_mom_fwd_red_kernel<true><<<(d.B + FWDR_WARPS - 1) / FWDR_WARPS, 32 * FWDR_WARPS, sm, st>>>(
-        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
-        *(const DescParams<float>*)dpv, (float*)d.G, (float4*)d.mom);
+    desc_mom_fwd_red_kernel<true><<<(b1 - b0 + FWDR_WARPS - 1) / FWDR_WARPS, 32 * FWDR_WARPS, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, b1,
+        *(const DescParams<float>*)dpv, (float*)d.G, (float4*)d.mom, b0);
 }
 
 void launch_descriptors_moment(const Dev& d, const void* dpv, cudaStream_t st)
 {
     if (d.precision == 2)
-        run_fwd_red(d, dpv, st);
+        run_fwd_red(d, dpv, 0, d.B, st);
     else
         run_fwd<false>(d, dpv, st);
 }
 
-static void run_adj_fast(const Dev& d, const void* dpv, cudaStream_t st)
+static void run_adj_fast(const Dev& d, const void* dpv, int b0, int b1, cudaStream_t st)
 {
+    if (b1 <= b0) return;
     const size_t sm = (size_t)ADJF_WARPS * ADJF_WARP_BYTES;
-    desc_mom_adj_fast_kernel<<<(d.B + ADJF_WARPS - 1) / ADJF_WARPS, 32 * ADJF_WARPS, sm, st>>>(
-        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, d.B,
+    desc_mom_adj_fast_kernel<<<(b1 - b0 + ADJF_WARPS - 1) / ADJF_WARPS, 32 * ADJF_WARPS, sm, st>>>(
+        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, b1,
         *(const DescParams<float>*)dpv, (const float4*)d.mom, (const float*)d.dEdG, (float4*)d.f,
-        (float*)d.wbuf, d.deterministic, (float4*)d.vbuf, (const float*)d.Eatom, d.V, d.W);
+        (float*)d.wbuf, d.deterministic, (float4*)d.vbuf, (const float*)d.Eatom, d.V, d.W, b0);
+}
+
+// The BF16 moment path (reduced-basis forward, fast adjoint) on the bead-atoms
+// b0 .. b1-1 only: the two halves of a step's beads can then run as
+// overlapping branches of the step's graph.
+bool moment_fast_path(const Dev& d, const void* dpv)
+{
+    return d.precision == 2 && d.sched.ang && d.mom && ((const DescParams<float>*)dpv)->r_even;
+}
+void launch_descriptors_range(const Dev& d, const void* dpv, int b0, int b1, cudaStream_t st)
+{
+    run_fwd_red(d, dpv, b0, b1, st);
+}
+void launch_adjoint_range(const Dev& d, const void* dpv, int b0, int b1, cudaStream_t st)
+{
+    run_adj_fast(d, dpv, b0, b1, st);
 }
 
 bool moment_adjoint_sums_energy(const Dev& d, const void* dpv)
@@ -1371,7 +1389,7 @@ void launch_adjoint_moment(const Dev& d, const void* dpv, cudaStream_t st)
 {
     if (d.precision == 2) {
         if (((const DescParams<float>*)dpv)->r_even)
-            run_adj_fast(d, dpv, st);
+            run_adj_fast(d, dpv, 0, d.B, st);
         else
             run_adj<true>(d, dpv, st);
     } else {

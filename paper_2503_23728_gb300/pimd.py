@@ -27,7 +27,8 @@ EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_w
            "pimd_element_types", "pimd_rdf_counts", "pimd_pt_coordinate",
            "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv", "pimd_selftest_bounded_wait",
            "pimd_set_gfn", "pimd_set_stage_timing", "pimd_rdf_gr", "pimd_cv_histogram", "pimd_pi_fes",
-           "pimd_metad_fes", "pimd_set_noise_index", "pimd_set_forces", "pimd_ring_start", "pimd_ring_finish"]
+           "pimd_metad_fes", "pimd_set_noise_index", "pimd_set_forces", "pimd_ring_start", "pimd_ring_finish",
+           "pimd_set_overlap"]
 ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
@@ -165,6 +166,8 @@ def load(path: str = LIB_PATH):
     L.pimd_pi_fes.argtypes = [vp, ct.c_int, vp, vp, ct.c_double, ct.c_double, ct.c_int, vp, vp]
     L.pimd_metad_fes.argtypes = [vp, ct.c_int, vp, ct.c_int, vp]
     L.pimd_set_noise_index.argtypes = [vp, ct.c_int, ct.c_int, ct.c_int]
+    L.pimd_set_overlap.argtypes = [vp, ct.c_int]
+    L.pimd_set_overlap.restype = ct.c_int
     L.pimd_set_forces.argtypes = [vp, vp]
     L.pimd_ring_start.argtypes = [vp, vp]
     L.pimd_ring_finish.argtypes = [vp, vp]
@@ -490,6 +493,7 @@ class Context:
         self.torch = torch
         self.keep = _Keep()
         self.replicas = list(replicas)
+        self.widths = tuple(int(v) for v in widths)
         self.precision = precision if isinstance(precision, str) else {v: k for k, v in PRECISION.items()}[precision]
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -598,6 +602,14 @@ class Context:
         positions ring_start returned."""
         f = f.contiguous()
         _check(load().pimd_ring_finish(self.h, ct.c_void_p(f.data_ptr())), self.h)
+
+    def set_overlap(self, on: bool) -> bool:
+        """Overlapped halves of the bead-atoms in the step's graph; returns
+        whether this context has halves."""
+        rc = load().pimd_set_overlap(self.h, 1 if on else 0)
+        if rc < 0:
+            _check(rc, self.h)
+        return rc == 1
 
     def set_stage_timing(self, on: bool):
         _check(load().pimd_set_stage_timing(self.h, 1 if on else 0), self.h)
