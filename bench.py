@@ -164,7 +164,11 @@ def run_gpu(a, workload, precision, model=None):
     else:
         ctx.set_weights(model)
     if not a.no_tune:
-        ctx.tune_result = ctx.tune(reps=3)   # pair schedule, set-up only (not timed)
+        # angular method, pair schedule and overlapped halves, measured on
+        # this workload during set-up (not timed); no cache, so every run
+        # measures afresh
+        from paper_2503_23728_gb300 import tuner
+        ctx.tune_result = tuner.tune(ctx, cache=None)
     else:
         ctx.tune_result = None
     stream = torch.cuda.current_stream()
