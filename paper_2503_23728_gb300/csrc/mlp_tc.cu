@@ -382,17 +382,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
         issued = 1;
     }
 
-    // h_0 = (G - mu) / sigma in BF16: thread -> (row tid % 128, 32 columns)
+    // h_0 = (G - mu) / sigma in BF16: thread -> (row tid % 128, 32 columns),
+    // the row's 32 FP32 values as eight 16-byte loads
     {
         const int r = tid & (M - 1), c0 = (tid >> 7) * 32;
         const int ba = perm[row0 + r];
+        float4 gv[8];
+        const float4* grow = reinterpret_cast<const float4*>(G + (size_t)(ba >= 0 ? ba : 0) * ND + c0);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) gv[g] = ba >= 0 ? grow[g] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             float v[8];
+            const float gg[8] = {gv[2 * g].x, gv[2 * g].y, gv[2 * g].z, gv[2 * g].w,
+                                 gv[2 * g + 1].x, gv[2 * g + 1].y, gv[2 * g + 1].z, gv[2 * g + 1].w};
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = c0 + 8 * g + j;
-                v[j] = ba >= 0 ? (G[(size_t)ba * ND + c] - smu[c]) * sis[c] : 0.0f;
+            for (int jj = 0; jj < 8; ++jj) {
+                const int c = c0 + 8 * g + jj;
+                v[jj] = ba >= 0 ? (gg[jj] - smu[c]) * sis[c] : 0.0f;
             }
             uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
                                   pack_bf16(v[6], v[7]));
