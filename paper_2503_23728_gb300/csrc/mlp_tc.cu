@@ -310,8 +310,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(
 template <int W, int L>
 __host__ __device__ constexpr int park_cols() { return (W < 64 ? 64 : W) + (L - 1) * (W / 2); }
 
+// threads of the parked kernel: four warps per tensor-memory lane quadrant,
+// each taking a quarter of a phase's columns in the epilogues
+constexpr int PARK_THREADS = 512;
+constexpr int PARK_NH = PARK_THREADS / 128;   // column groups per row
+
 template <int W, int L>
-__global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
+__global__ void __launch_bounds__(PARK_THREADS, 2) mlp_tc_park_kernel(
     const float* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
     const unsigned char* __restrict__ wimg, size_t img_per_type, const float* __restrict__ wvec,
     size_t vec_per_type, float* __restrict__ Eatom, float* __restrict__ dEdG, DevErr* __restrict__ err, int tile0)
@@ -323,6 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
     constexpr int TACC = W < 64 ? 64 : W;       // accumulator columns
     constexpr int TALLOC = 256;                  // per CTA: two CTAs share the SM's 512 columns
     static_assert(park_cols<W, L>() <= TALLOC, "parked activations exceed tensor memory");
+    static_assert((W / PARK_NH) % 16 == 0 && (ND / PARK_NH) % 16 == 0, "column groups of whole 16-column chunks");
     constexpr int NPH = 2 * L;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* A0 = sm;
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
     unsigned char* WB = ACT + H_B;
     uint64_t* bars = reinterpret_cast<uint64_t*>(WB + WB_B);   // [0] mma, [1] weights
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
-    float* ysum = reinterpret_cast<float*>(tslot + 4);          // [2][128]
+    float* ysum = reinterpret_cast<float*>(tslot + 4);          // [PARK_NH][128]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hsel = warp >> 2;
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
     const float b_out = sigma[ND], s_E = sigma[ND + 1], e_Z = sigma[ND + 2];
     // the element's vectors in shared memory: biases, output weights, mu and
     // 1 / sigma (the epilogues read them in every 16-column chunk)
-    float* sb = ysum + 2 * M;   // [L][W]
+    float* sb = ysum + PARK_NH * M;   // [L][W]
     float* swo = sb + L * W;
     float* smu = swo + W;
     float* sis = smu + ND;
@@ -382,17 +388,18 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
         issued = 1;
     }
 
-    // h_0 = (G - mu) / sigma in BF16: thread -> (row tid % 128, 32 columns),
-    // the row's 32 FP32 values as eight 16-byte loads
+    // h_0 = (G - mu) / sigma in BF16: thread -> (row tid % 128, CPT columns),
+    // the row's FP32 values as 16-byte loads
     {
-        const int r = tid & (M - 1), c0 = (tid >> 7) * 32;
+        constexpr int CPT = ND / PARK_NH;
+        const int r = tid & (M - 1), c0 = (tid >> 7) * CPT;
         const int ba = perm[row0 + r];
-        float4 gv[8];
+        float4 gv[CPT / 4];
         const float4* grow = reinterpret_cast<const float4*>(G + (size_t)(ba >= 0 ? ba : 0) * ND + c0);
 #pragma unroll
-        for (int g = 0; g < 8; ++g) gv[g] = ba >= 0 ? grow[g] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int g = 0; g < CPT / 4; ++g) gv[g] = ba >= 0 ? grow[g] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 0; g < CPT / 8; ++g) {
             float v[8];
             const float gg[8] = {gv[2 * g].x, gv[2 * g].y, gv[2 * g].z, gv[2 * g].w,
                                  gv[2 * g + 1].x, gv[2 * g + 1].y, gv[2 * g + 1].z, gv[2 * g + 1].w};
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
             issue_w(p + 1);
             issued = p + 2;
         }
-        const int cbeg = hsel * (N / 2), cend = cbeg + N / 2;
+        const int cbeg = hsel * (N / PARK_NH), cend = cbeg + N / PARK_NH;
         for (int c0 = cbeg; c0 < cend; c0 += 16) {
             float v[16];
             tmem_ld16(lane_base + (uint32_t)c0, v);
@@ -516,7 +523,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mlp_tc_park_kernel(
         fence_after();
         if (fwd && l == L && hsel == 0) {
             const int ba = perm[row0 + row];
-            if (ba >= 0) Eatom[ba] = s_E * (ysum[row] + ysum[M + row] + b_out) + e_Z;
+            float ys = 0.0f;
+#pragma unroll
+            for (int h = 0; h < PARK_NH; ++h) ys += ysum[h * M + row];
+            if (ba >= 0) Eatom[ba] = s_E * (ys + b_out) + e_Z;
         }
     }
     if (!ok) {
@@ -929,8 +939,8 @@ template <int W, int L>
 static size_t park_smem()
 {
     const size_t WB_B = (size_t)W * (W > ND ? W : ND) * 2;
-    return (size_t)128 * ND * 2 + (size_t)128 * W * 2 + WB_B + 64 + 2 * 128 * 4 + (size_t)(L * W + W + 2 * ND) * 4 +
-           1024;
+    return (size_t)128 * ND * 2 + (size_t)128 * W * 2 + WB_B + 64 + (size_t)PARK_NH * 128 * 4 +
+           (size_t)(L * W + W + 2 * ND) * 4 + 1024;
 }
 
 template <int W, int L>
@@ -954,7 +964,7 @@ static bool run_tc_park(const Dev& d, int t0, int nt, cudaStream_t st, bool urge
             at[0].val.priority = greatest;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(nt);
-            cfg.blockDim = dim3(TC_THREADS);
+            cfg.blockDim = dim3(PARK_THREADS);
             cfg.dynamicSmemBytes = sm;
             cfg.stream = st;
             cfg.attrs = at;
@@ -965,7 +975,7 @@ static bool run_tc_park(const Dev& d, int t0, int nt, cudaStream_t st, bool urge
                                t0);
             return true;
         }
-        mlp_tc_park_kernel<W, L><<<nt, TC_THREADS, sm, st>>>(
+        mlp_tc_park_kernel<W, L><<<nt, PARK_THREADS, sm, st>>>(
             (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
             d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err, t0);
         return true;
