@@ -10,8 +10,11 @@ C, loaded through ctypes. It shares no code with the CUDA library.
 The graph-field-network force head (Sec. 2.2, direct forces) is the numpy
 module ``oracle.gfn``.
 
-Parity pins live in tests/test_oracle_*.py. Parts without an independent pin:
-long-time trajectory physics of the random-init network (parity unpinned).
+Parity pins live in tests/test_oracle_*.py (the step cut at its force
+evaluation, for bead-sharded runs: tests/test_shard.py, bit for bit against
+the whole step; the free-energy and g(r) routines of Sec. 2.5 and Figs. 8-9:
+tests/test_oracle_fes.py). Parts without an independent pin: long-time
+trajectory physics of the random-init network (parity unpinned).
 """
 from __future__ import annotations
 

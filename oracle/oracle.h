@@ -7,7 +7,9 @@
  * the CUDA path: it is a plain, slow restatement of the method's definitions
  * (paper Sec. 2.1 Eqs. for H_eff, H_p, U and the estimator; BPNN descriptors
  * of ref. [17] cited in Sec. 1; energy-derived forces of Sec. 2.2) written for
- * a reader to check against the paper by eye.
+ * a reader to check against the paper by eye. Also: the step cut at its
+ * force evaluation (bead-sharded runs), the path-integral free energy of
+ * Sec. 2.5 from bead-resolved CV histograms, and g(r) (Figs. 8, 9).
  *
  * Units: Angstrom, fs, amu, eV, K.
  */
