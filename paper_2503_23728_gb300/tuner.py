@@ -8,9 +8,11 @@ For a context it chooses, by timing them on the live workload:
   * whether the step runs the two halves of its bead-atoms as overlapping
     branches of its graph (`pimd_set_overlap`), from whole-step timings.
 The choices are stored in a JSON file under a key of the workload's shape:
-atoms and beads of every replica (sorted multiset), the mean neighbour count
-rounded to an integer, the network widths and the precision. A later context
-with the same key applies them without timing anything.
+atoms and beads of every replica (sorted multiset), the network widths and
+the precision; each entry also records the mean neighbour count it was
+measured at. A later context with the same key and a mean neighbour count
+within 15 % of an entry's (the count drifts as the beads spread from their
+initial positions) applies that entry without timing anything.
 
 The step timings advance the trajectory; the tuner puts the state back
 (q, p, step counter and thermostat heat) before it returns.
@@ -25,8 +27,15 @@ import numpy as np
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
 
 
-def workload_key(ctx) -> str:
+NB_TOL = 0.15
+
+
+def mean_neighbours(ctx) -> float:
     nnb, _ = ctx.neighbours()
+    return round(float(np.asarray(nnb).mean()), 2) if len(nnb) else 0.0
+
+
+def workload_key(ctx) -> str:
     shapes = sorted((int(r.n_atoms), int(r.n_beads)) for r in ctx.replicas)
     # run-length form of the sorted (N, P) multiset keeps batch keys short
     runs = []
@@ -37,7 +46,19 @@ def workload_key(ctx) -> str:
             runs.append([s, 1])
     shp = ",".join("%dx%dx%d" % (n, p, c) for (n, p), c in runs)
     widths = "-".join(str(int(w)) for w in ctx.widths)
-    return "%s|nb%d|w%s|%s" % (shp, int(round(float(nnb.mean()))), widths, ctx.precision)
+    return "%s|w%s|%s" % (shp, widths, ctx.precision)
+
+
+def _lookup(entries, nb: float):
+    """The cached entry measured at the mean neighbour count closest to nb,
+    if within NB_TOL of it."""
+    best = None
+    for e in entries if isinstance(entries, list) else []:
+        ref = float(e.get("mean_neighbours", -1.0))
+        if ref > 0 and abs(nb - ref) <= NB_TOL * ref:
+            if best is None or abs(nb - ref) < abs(nb - float(best["mean_neighbours"])):
+                best = e
+    return best
 
 
 def _load(path: str) -> dict:
@@ -82,16 +103,18 @@ def tune(ctx, cache: str | None = DEFAULT_CACHE, reps: int = 3, steps: int = 10,
     when the workload's key is there, else measured and added to the cache.
     cache=None measures without reading or writing a file."""
     key = workload_key(ctx)
+    nb = mean_neighbours(ctx)
     table = _load(cache) if cache else {}
-    if not retune and key in table:
-        choice = dict(table[key])
+    hit = None if retune else _lookup(table.get(key), nb)
+    if hit is not None:
+        choice = dict(hit)
         apply(ctx, choice)
         choice["source"] = "cache"
         choice["key"] = key
         return choice
     kern = ctx.tune(reps=reps)   # angular method and pair schedule, applied by the library
     choice = {"angular": kern["angular"], "band_length": int(kern["band_length"]),
-              "kernels_ms": float(kern["best_ms"])}
+              "kernels_ms": float(kern["best_ms"]), "mean_neighbours": nb}
     # overlapped halves, from whole-step timings (state restored afterwards)
     q, p, step, Q = ctx.get_state()
     has = ctx.set_overlap(True)
@@ -106,7 +129,10 @@ def tune(ctx, cache: str | None = DEFAULT_CACHE, reps: int = 3, steps: int = 10,
     ctx.set_state(q, p, step, Q)
     if cache:
         table = _load(cache)
-        table[key] = {k: v for k, v in choice.items() if k not in ("source", "key")}
+        entries = [e for e in table.get(key, []) if isinstance(e, dict)
+                   and abs(float(e.get("mean_neighbours", -1.0)) - nb) > NB_TOL * nb]
+        entries.append({k: v for k, v in choice.items() if k not in ("source", "key")})
+        table[key] = entries
         _store(cache, table)
     choice["source"] = "measured"
     choice["key"] = key

@@ -51,16 +51,17 @@ class _FakeCtx:
 
 def test_key_names_the_workload_shape():
     k1 = tuner.workload_key(_FakeCtx([_Rep(1296, 32)]))
-    assert k1 == "1296x32x1|nb86|w128-128-128|bf16_tc"
+    assert k1 == "1296x32x1|w128-128-128|bf16_tc"
     k2 = tuner.workload_key(_FakeCtx([_Rep(10, 8), _Rep(12, 16), _Rep(10, 8)], mean_nbrs=9.0))
-    assert k2 == "10x8x2,12x16x1|nb9|w128-128-128|bf16_tc"
+    assert k2 == "10x8x2,12x16x1|w128-128-128|bf16_tc"
 
 
 def test_cached_choice_is_applied_without_timing(tmp_path, monkeypatch):
     path = str(tmp_path / "cache.json")
     ctx = _FakeCtx([_Rep(1296, 32)])
     key = tuner.workload_key(ctx)
-    json.dump({key: {"angular": "pairs", "band_length": 10, "overlap": False}}, open(path, "w"))
+    json.dump({key: [{"angular": "pairs", "band_length": 10, "overlap": False, "mean_neighbours": 85.0}]},
+              open(path, "w"))
     monkeypatch.setattr(tuner, "_step_ms", lambda *a, **k: (_ for _ in ()).throw(AssertionError("timed")))
     got = tuner.tune(ctx, cache=path)
     assert got["source"] == "cache" and got["band_length"] == 10
@@ -78,7 +79,23 @@ def test_measured_choice_is_stored_and_state_restored(tmp_path, monkeypatch):
     assert ctx.calls.count("tune") == 1 and ("set_state", 7) in ctx.calls
     assert ctx.overlap is True
     table = json.load(open(path))
-    assert table[tuner.workload_key(ctx)]["overlap"] is True
-    # a second context of the same shape reads it back
-    ctx2 = _FakeCtx([_Rep(1296, 32)])
+    (entry,) = table[tuner.workload_key(ctx)]
+    assert entry["overlap"] is True and entry["mean_neighbours"] == 86.3
+    # a second context of the same shape, its neighbour count drifted by a
+    # fraction (beads spread from their initial positions), reads it back
+    ctx2 = _FakeCtx([_Rep(1296, 32)], mean_nbrs=85.4)
     assert tuner.tune(ctx2, cache=path)["source"] == "cache"
+
+
+def test_a_different_density_is_measured_and_stored_beside(tmp_path, monkeypatch):
+    path = str(tmp_path / "cache.json")
+    times = iter([0.42, 0.44, 0.50, 0.40])
+    monkeypatch.setattr(tuner, "_step_ms", lambda *a, **k: next(times))
+    assert tuner.tune(_FakeCtx([_Rep(1296, 32)], mean_nbrs=86.3), cache=path)["overlap"] is True
+    got = tuner.tune(_FakeCtx([_Rep(1296, 32)], mean_nbrs=60.0), cache=path)
+    assert got["source"] == "measured" and got["overlap"] is False
+    table = json.load(open(path))
+    assert sorted(e["mean_neighbours"] for e in table[got["key"]]) == [60.0, 86.3]
+    # each density finds its own entry
+    assert tuner.tune(_FakeCtx([_Rep(1296, 32)], mean_nbrs=61.0), cache=path)["overlap"] is False
+    assert tuner.tune(_FakeCtx([_Rep(1296, 32)], mean_nbrs=88.0), cache=path)["overlap"] is True
