@@ -186,7 +186,7 @@ typedef struct {
                                 when the two largest atom displacements since the
                                 last build add up to 0.98 skin; every step filters
                                 them with the exact rule, so the lists equal a
-                                full rebuild. < 0: 1 A for replicas of >= 256
+                                full rebuild. < 0: 1.5 A for replicas of >= 256
                                 atoms (reduced to 0.9 of the room between r_c
                                 and half the box, off below 0.05 A), none for
                                 smaller ones; 0: rebuild every step.           */

@@ -62,13 +62,22 @@ struct Build {
     size_t gfn_params = 0;   // FP32 parameters of the graph-field-network head
     bool periodic_any = false;
     bool any_skin = false;
+    double max_skin = 0.0;   // largest Verlet skin among the replicas, A
     double nb_est = 0.0;   // mean neighbour count per bead-atom (estimate from density)
 };
 
 // candidate slots per atom for Verlet lists: 1.5 x the neighbour slots
 // (a skin of 0.5 A at r_c = 6 A holds 1.27 x the neighbours), multiple of 32,
 // at most the sort capacity
-int max_candidates(int maxnb) { return std::min(PIMD_SORT_CAP, (maxnb * 3 / 2 + 31) / 32 * 32); }
+// candidate slots per bead-atom: the neighbour slots scaled by the volume of
+// the r_c + skin sphere over the r_c sphere, 10 % margin, multiple of 32, at
+// most the sort buffer (an atom with more candidates is scanned directly)
+int max_candidates(int maxnb, double rc, double skin)
+{
+    const double v = std::pow((rc + skin) / rc, 3.0) * 1.1 * maxnb;
+    const int slots = ((int)std::ceil(v) + 31) / 32 * 32;
+    return std::min(PIMD_SORT_CAP, std::max(32, slots));
+}
 
 // element (r, k) of an R x K operand in the tensor cores' K-major core-matrix layout
 size_t cm_index_host(int r, int k, int K)
@@ -285,18 +294,19 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
         b.repT.push_back(h.T);
         // Verlet skin of the candidate lists: at most 0.9 of the room between
         // r_c and half the box (unique minimum images), off below 0.05 A
-        if (graph_pot(cfg->potential)) {
-            // auto: 1 A for replicas of >= 256 atoms (small ones scan all atoms
-            // faster than they would check and filter candidates)
-            double sk = cfg->nbr_skin_A < 0.0 ? (h.N >= 256 ? 1.0 : 0.0) : cfg->nbr_skin_A;
+        const bool auto_skin = cfg->nbr_skin_A < 0.0;
+        auto set_skin = [&](double sk) {
             if (rp.periodic)
                 sk = std::min(sk, 0.9 * (0.5 * std::min(std::min(h.box[0], h.box[1]), h.box[2]) - cfg->cutoff_A));
             if (sk < 0.05) sk = 0.0;
             rp.skin = (float)sk;
             const double rcs = cfg->cutoff_A + sk;
             rp.rcs2 = (float)(rcs * rcs);
-            if (sk > 0.0) b.any_skin = true;
-        }
+        };
+        if (graph_pot(cfg->potential))
+            // auto: 1.5 A for replicas of >= 256 atoms (small ones scan all
+            // atoms faster than they would check and filter candidates)
+            set_skin(auto_skin ? (h.N >= 256 ? 1.5 : 0.0) : cfg->nbr_skin_A);
         // cell lists: >= 3 cells per side with edge >= cutoff + skin (1e-5
         // margin against rounding of the FP32 cell coordinate)
         if (rp.periodic && graph_pot(cfg->potential) && cfg->nbr_algo != 1) {
@@ -317,6 +327,8 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
                 for (int k = 0; k < h.P; ++k) b.cell_bs.push_back(bs0 + k);
             }
         }
+        if (rp.skin > 0.0f) b.any_skin = true;
+        b.max_skin = std::max(b.max_skin, (double)rp.skin);
         b.reps.push_back(rp);
         {
             double est = h.N - 1.0;
@@ -464,7 +476,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.vbuf = c.take(cfg->deterministic && model ? v4 * (size_t)b.B * mnb : 0);
     o.mom = c.take(model && cfg->precision != PIMD_FP64 ? sizeof(float4) * moment_elems_per_atom() * (size_t)b.B : 0);
     {
-        const size_t mc = b.any_skin ? (size_t)max_candidates(mnb) : 0;
+        const size_t mc = b.any_skin ? (size_t)max_candidates(mnb, cfg->cutoff_A, b.max_skin) : 0;
         o.cand = c.take(sizeof(int) * (size_t)b.B * mc);
         o.ncand = c.take(mc ? sizeof(int) * (size_t)b.B : 0);
         o.xref = c.take(mc ? sizeof(float4) * (size_t)b.B : 0);
@@ -568,6 +580,15 @@ void mark(pimd_ctx* c, int i, cudaStream_t st, bool timed)
     if (timed && c->ev[i]) cudaEventRecordWithFlags(c->ev[i], st, cudaEventRecordExternal);
 }
 
+// the model's force evaluation can run as two overlapping branches (halves of
+// the bead-atoms on the BF16 moment path with tensor-core network tiles)
+bool splits_forces(const pimd_ctx* c)
+{
+    const Dev& d = c->d;
+    return d.potential == PIMD_POT_MODEL && d.split_ba > 0 && moment_fast_path(d, dparams(c)) &&
+           network_tiles_available(d);
+}
+
 // zeroed: the ring start of this step has already cleared the forces, the
 // per-bead virials and energies
 // branch: the step may run the force evaluation as two overlapping branches
@@ -597,8 +618,7 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
         if (d.gfn_wtc) launch_gfn_tc(d, st);
         else launch_gfn(d, st);
         mark(c, PIMD_STAGE_ADJOINT, st, timed);
-    } else if (branch && d.split_ba > 0 && moment_fast_path(d, dparams(c)) && network_tiles_available(d) && c->cap2 &&
-               c->ev_fork) {
+    } else if (branch && splits_forces(c) && c->cap2 && c->ev_fork) {
         // two halves of the bead-atoms as overlapping branches: the second
         // half's forward starts when the first half's ends, so the first
         // half's network (latency-bound, short) and adjoint run beside the
@@ -785,6 +805,8 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.modes = (Mode*)(w + o.modes);
     d.rp_blocks = (int2*)(w + o.rp_blocks);
     d.n_rp_blocks = (int)b.rp_blocks.size();
+    for (const Rep& rp : b.reps)
+        if (rp.P <= 64) d.rp_stage_P = std::max(d.rp_stage_P, rp.P);
     d.rp_threads = 256;
     d.x = w + o.x;
     d.f = w + o.f;
@@ -821,7 +843,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
         d.gfn.L = cfg->gfn_iterations;
     }
     if (b.any_skin) {
-        d.maxcand = max_candidates(d.maxnb);
+        d.maxcand = max_candidates(d.maxnb, cfg->cutoff_A, b.max_skin);
         d.cand = (int*)(w + o.cand);
         d.ncand = (int*)(w + o.ncand);
         d.xref = (float4*)(w + o.xref);
@@ -1406,9 +1428,12 @@ int pimd_kernels_per_step(const pimd_ctx* c)
         return ring + 2 + 2 + gfn_kernels_per_eval(d.gfn.L) + md;
     // neighbours (cell binning, Verlet skin check, lists), descriptors,
     // network, adjoint (+ force gather), energy unless the adjoint sums it
+    // the overlapped halves launch the descriptors, network and adjoint once
+    // per half
+    const int halves = c->overlap && splits_forces(c) ? 2 : 1;
     const int nbr = 1 + (d.n_cell_bs ? 1 : 0) + (d.maxcand ? 1 : 0);
     const int energy = adjoint_sums_energy(d, dparams(c)) ? 0 : 1;
-    return ring + nbr + 3 + (d.deterministic ? 1 : 0) + energy + md;
+    return ring + nbr + 3 * halves + (d.deterministic ? 1 : 0) + energy + md;
 }
 
 int pimd_energy_forces(pimd_ctx* c, const double* x_dev, double* e_dev, double* f_dev, double* virial_dev)

@@ -1137,7 +1137,9 @@ size_t blob_elems(int n_hidden, const int* widths)
     return o + prev + 1 + 2 * ND + 2;
 }
 
-constexpr int KC = 32;   // K chunk of the weights staged per step
+constexpr int KC_WIDE = 32;   // K chunk of the weights staged per step (one CTA per SM)
+constexpr int KC_PAIR = 8;    // the same for two CTAs per SM (less shared memory)
+constexpr size_t PAIR_SMEM_MAX = 113 * 1024;   // two CTAs per SM: 228 KB less 1 KB reserved per CTA
 constexpr int APAD = 4;  // row padding of the k-major activation tiles (keeps 16-byte alignment)
 
 // N consecutive values at p (16-byte aligned when N * sizeof(Real) >= 16)
@@ -1191,7 +1193,7 @@ __device__ __forceinline__ int tile_col(int tx, int m) { return (m >> 2) * 64 + 
 // of KC rows: while a chunk is multiplied, each thread holds its share of
 // the next chunk in registers and stores it into the other buffer after, so
 // the global loads overlap the arithmetic (one barrier per chunk).
-template <typename Real, int RT, int CT, bool transB>
+template <typename Real, int RT, int CT, bool transB, int KC>
 __device__ __forceinline__ void tile_gemm(const Real* __restrict__ At, int lda, int K, const Real* __restrict__ W,
                                           int ldw, Real* __restrict__ Bs, Real (&acc)[RT][CT])
 {
@@ -1265,18 +1267,36 @@ __device__ __forceinline__ void tile_gemm(const Real* __restrict__ At, int lda, 
 __device__ __forceinline__ float f_tanh(float v) { return tanhf(v); }
 __device__ __forceinline__ double f_tanh(double v) { return tanh(v); }
 
-template <typename Real, int RT, int CT>
-__global__ void __launch_bounds__(256) mlp_fp_kernel(
+// PAIR: two CTAs per SM. The weights then pass in chunks of KC_PAIR rows and
+// the input tile h_0 shares the buffer of the last hidden layer (h_0 is read
+// only by layer 1, whose reads end at the product's last barrier, before any
+// layer writes its output), which brings a 64-row tile of width 128 to
+// 110 KB of shared memory.
+template <typename Real, int RT, int CT, bool PAIR>
+struct FpTile {
+    static constexpr int TM = RT * 16;
+    static constexpr int Wd = CT * 16;          // hidden width
+    static constexpr int lda = TM + APAD;       // activations are k-major: [feature][row]
+    static constexpr int BW = (Wd > ND ? Wd : ND) + APAD;
+    static constexpr int KC = PAIR ? KC_PAIR : KC_WIDE;
+    static size_t smem(int n_hidden)
+    {
+        const size_t h0 = PAIR ? 0 : (size_t)ND * lda;
+        return sizeof(Real) * (h0 + (size_t)n_hidden * Wd * lda + (size_t)2 * KC * BW + TM);
+    }
+};
+
+template <typename Real, int RT, int CT, bool PAIR>
+__global__ void __launch_bounds__(256, PAIR ? 2 : 1) mlp_fp_kernel(
     const Real* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
     const Real* __restrict__ wts, size_t blob, int n_hidden, Real* __restrict__ Eatom, Real* __restrict__ dEdG)
 {
-    constexpr int TM = RT * 16;
-    constexpr int Wd = CT * 16;         // hidden width
-    constexpr int lda = TM + APAD;      // activations are k-major: [feature][row]
-    constexpr int BW = (Wd > ND ? Wd : ND) + APAD;
+    using Tl = FpTile<Real, RT, CT, PAIR>;
+    constexpr int TM = Tl::TM, Wd = Tl::Wd, lda = Tl::lda, BW = Tl::BW, KC = Tl::KC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* H0 = reinterpret_cast<Real*>(smem_raw);            // [ND][lda]
-    Real* Hl = H0 + ND * lda;                                 // [n_hidden][Wd][lda]
+    Real* base = reinterpret_cast<Real*>(smem_raw);
+    Real* Hl = PAIR ? base : base + ND * lda;                 // [n_hidden][Wd][lda]
+    Real* H0 = PAIR ? Hl + (size_t)(n_hidden - 1) * Wd * lda : base;   // [ND][lda]
     Real* Bs = Hl + (size_t)n_hidden * Wd * lda;              // [2][KC][BW]
     Real* yv = Bs + 2 * KC * BW;                              // [TM]
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -1310,7 +1330,7 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
         const Real* Ain = (l == 0) ? H0 : Hl + (size_t)(l - 1) * Wd * lda;
         const int K = (l == 0) ? ND : Wd;
         Real acc[RT][CT];
-        tile_gemm<Real, RT, CT, true>(Ain, lda, K, Wl[l], K, Bs, acc);
+        tile_gemm<Real, RT, CT, true, KC>(Ain, lda, K, Wl[l], K, Bs, acc);
         Real* Hout = Hl + (size_t)l * Wd * lda;
 #pragma unroll
         for (int m = 0; m < CT; ++m) {
@@ -1324,12 +1344,20 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
     }
     __syncthreads();
     Real* HL = Hl + (size_t)(n_hidden - 1) * Wd * lda;
-    if (tid < TM) {
-        Real y = b_out;
-        for (int k = 0; k < Wd; ++k) y += w_out[k] * HL[k * lda + tid];
-        yv[tid] = y;
-        const int ba = perm[row0 + tid];
-        if (ba >= 0) Eatom[ba] = s_E * y + e_Z;
+    // output layer: y = w_out . h_L + b_out, 256 / TM threads per row
+    {
+        constexpr int TPR = 256 / TM;   // threads per row (a power of two)
+        const int r = tid / TPR, part = tid - r * TPR;
+        Real y = Real(0);
+        for (int k = part; k < Wd; k += TPR) y += w_out[k] * HL[k * lda + r];
+#pragma unroll
+        for (int o = TPR / 2; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+        if (part == 0) {
+            y += b_out;
+            yv[r] = y;
+            const int ba = perm[row0 + r];
+            if (ba >= 0) Eatom[ba] = s_E * y + e_Z;
+        }
     }
     __syncthreads();
     // dE/da_L = s_E w_out (1 - h_L^2), written over h_L
@@ -1343,7 +1371,7 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
         const Real* Ga = Hl + (size_t)l * Wd * lda;
         if (l > 0) {
             Real acc[RT][CT];
-            tile_gemm<Real, RT, CT, false>(Ga, lda, Wd, Wl[l], Wd, Bs, acc);
+            tile_gemm<Real, RT, CT, false, KC>(Ga, lda, Wd, Wl[l], Wd, Bs, acc);
             Real* Hp = Hl + (size_t)(l - 1) * Wd * lda;
 #pragma unroll
             for (int m = 0; m < CT; ++m) {
@@ -1357,7 +1385,7 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
         } else {
             constexpr int C0 = ND / 16;
             Real acc[RT][C0];
-            tile_gemm<Real, RT, C0, false>(Ga, lda, Wd, Wl[0], ND, Bs, acc);
+            tile_gemm<Real, RT, C0, false, KC>(Ga, lda, Wd, Wl[0], ND, Bs, acc);
             static_assert(C0 == 4, "one group of 4 descriptor columns per thread");
             Real is[C0];
 #pragma unroll
@@ -1375,22 +1403,14 @@ __global__ void __launch_bounds__(256) mlp_fp_kernel(
     }
 }
 
-template <typename Real, int RT, int CT>
-static size_t mlp_fp_smem(int n_hidden)
-{
-    constexpr int TM = RT * 16, Wd = CT * 16;
-    constexpr int lda = TM + APAD, BW = (Wd > ND ? Wd : ND) + APAD;
-    return sizeof(Real) * ((size_t)ND * lda + (size_t)n_hidden * Wd * lda + (size_t)2 * KC * BW + TM);
-}
-
-template <typename Real, int RT, int CT>
+template <typename Real, int RT, int CT, bool PAIR>
 static void run_mlp_fp(const Dev& d, cudaStream_t st)
 {
-    constexpr int TM = RT * 16;
-    const size_t sm = mlp_fp_smem<Real, RT, CT>(d.n_hidden);
+    using Tl = FpTile<Real, RT, CT, PAIR>;
+    const size_t sm = Tl::smem(d.n_hidden);
     static size_t done = 0;
-    set_smem(mlp_fp_kernel<Real, RT, CT>, sm, done);
-    mlp_fp_kernel<Real, RT, CT><<<d.rows_pad / TM, 256, sm, st>>>(
+    set_smem(mlp_fp_kernel<Real, RT, CT, PAIR>, sm, done);
+    mlp_fp_kernel<Real, RT, CT, PAIR><<<d.rows_pad / Tl::TM, 256, sm, st>>>(
         (const Real*)d.G, d.perm, d.tile_type, (const Real*)d.wts, d.blob, d.n_hidden, (Real*)d.Eatom,
         (Real*)d.dEdG);
 }
@@ -1398,13 +1418,16 @@ static void run_mlp_fp(const Dev& d, cudaStream_t st)
 template <typename Real, int CT>
 static void dispatch_rows(const Dev& d, cudaStream_t st)
 {
-    // largest row tile whose activations fit in ~200 KB of shared memory
-    if (mlp_fp_smem<Real, 4, CT>(d.n_hidden) <= 200 * 1024)
-        run_mlp_fp<Real, 4, CT>(d, st);
-    else if (mlp_fp_smem<Real, 2, CT>(d.n_hidden) <= 200 * 1024)
-        run_mlp_fp<Real, 2, CT>(d, st);
+    // 64-row tiles two per SM when they fit in half the shared memory (width
+    // 128 in FP32), else the largest row tile that fits in ~200 KB, one per SM
+    if (FpTile<Real, 4, CT, true>::smem(d.n_hidden) <= PAIR_SMEM_MAX)
+        run_mlp_fp<Real, 4, CT, true>(d, st);
+    else if (FpTile<Real, 4, CT, false>::smem(d.n_hidden) <= 200 * 1024)
+        run_mlp_fp<Real, 4, CT, false>(d, st);
+    else if (FpTile<Real, 2, CT, false>::smem(d.n_hidden) <= 200 * 1024)
+        run_mlp_fp<Real, 2, CT, false>(d, st);
     else
-        run_mlp_fp<Real, 1, CT>(d, st);
+        run_mlp_fp<Real, 1, CT, false>(d, st);
 }
 
 void launch_network_fp(const Dev& d, cudaStream_t st)

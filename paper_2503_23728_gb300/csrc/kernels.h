@@ -32,6 +32,7 @@ struct Dev {
     int2* rp_blocks = nullptr;         // (replica, first entry) per ring-polymer block
     int n_rp_blocks = 0;
     int rp_threads = 256;
+    int rp_stage_P = 0;                // largest P <= 64 among the replicas (transform rows staged per block)
 
     void* x = nullptr;                 // Vec4<Real>[B] positions (w = type)
     void* f = nullptr;                 // Vec4<Real>[B] forces
@@ -126,6 +127,8 @@ size_t blob_elems(int n_hidden, const int* widths);
 
 // force evaluation pieces
 void launch_neighbours(const Dev& d, cudaStream_t st);
+void launch_neighbour_prep(const Dev& d, cudaStream_t st);
+void launch_neighbour_lists(const Dev& d, int b0, int b1, cudaStream_t st);
 void launch_descriptors(const Dev& d, const void* dp, cudaStream_t st);
 void launch_network_fp(const Dev& d, cudaStream_t st);
 void launch_network_tc(const Dev& d, cudaStream_t st);

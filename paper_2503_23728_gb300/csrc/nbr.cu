@@ -107,13 +107,26 @@ __device__ int scan_list(const V4* __restrict__ x, const BeadSys& sy, const Rep&
 {
     int cnt = 0;
     if (rp.ncells == 0) {
-        for (int j0 = 0; j0 < sy.N; j0 += 32) {
-            const int j = j0 + (int)lane;
-            const bool in = j < sy.N && j != il && within(rp, xi, pos_f32(x[sy.ba0 + j]), r2cut);
-            const unsigned m = __ballot_sync(0xffffffffu, in);
-            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-            if (in && pos < cap) out[pos] = j;
-            cnt += __popc(m);
+        // four chunks of 32 atoms per round: their positions are loaded
+        // together, then tested and stored in ascending order
+        constexpr int KS = 4;
+        for (int j0 = 0; j0 < sy.N; j0 += 32 * KS) {
+            float3 pj[KS];
+#pragma unroll
+            for (int k = 0; k < KS; ++k) {
+                const int j = j0 + 32 * k + (int)lane;
+                pj[k] = j < sy.N ? pos_f32(x[sy.ba0 + j]) : xi;
+            }
+#pragma unroll
+            for (int k = 0; k < KS; ++k) {
+                if (j0 + 32 * k >= sy.N) break;   // warp-uniform
+                const int j = j0 + 32 * k + (int)lane;
+                const bool in = j < sy.N && j != il && within(rp, xi, pj[k], r2cut);
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                if (in && pos < cap) out[pos] = j;
+                cnt += __popc(m);
+            }
         }
     } else {
         const int3 ci = cell_of(rp, xi);
@@ -280,12 +293,12 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
                                                   int* __restrict__ nbr, int* __restrict__ nnb,
                                                   DevErr* __restrict__ err, int* __restrict__ cand,
                                                   int* __restrict__ ncand, float4* __restrict__ xref,
-                                                  const int* __restrict__ rebuild, int maxcand)
+                                                  const int* __restrict__ rebuild, int maxcand, int b0)
 {
     __shared__ int lst[8][PIMD_SORT_CAP];
     __shared__ unsigned bmap[8][NBR_BM_WORDS];
     const int wib = threadIdx.x >> 5;
-    const int b = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int b = b0 + blockIdx.x * (blockDim.x >> 5) + wib;   // bead-atoms b0 .. B-1
     const unsigned lane = lane_id();
     if (b >= B) return;
     const int bs = ba_sys[b];
@@ -348,30 +361,46 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
     }
 }
 
-void launch_neighbours(const Dev& d, cudaStream_t st)
+// cell lists and the Verlet check of every bead (before any list range)
+void launch_neighbour_prep(const Dev& d, cudaStream_t st)
 {
-    const int threads = 256;
-    const int blocks = (int)(((size_t)d.B * 32 + threads - 1) / threads);
-    const float rc2 = (float)(d.rc * d.rc);
     if (d.precision == 0) {
         if (d.n_cell_bs)
             cell_build_kernel<Dbl4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
                 (const Dbl4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
         if (d.maxcand)
             skin_check_kernel<Dbl4><<<d.S, 1024, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
-        nbr_kernel<Dbl4><<<blocks, threads, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
-                                                     d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb, d.err,
-                                                     d.cand, d.ncand, d.xref, d.rebuild, d.maxcand);
     } else {
         if (d.n_cell_bs)
             cell_build_kernel<float4><<<d.n_cell_bs, 256, 2 * d.max_cells * sizeof(int), st>>>(
                 (const float4*)d.x, d.bsys, d.reps, d.cell_bs, d.cell_start, d.cell_cnt, d.cell_atoms);
         if (d.maxcand)
             skin_check_kernel<float4><<<d.S, 1024, 0, st>>>((const float4*)d.x, d.bsys, d.reps, d.xref, d.rebuild);
-        nbr_kernel<float4><<<blocks, threads, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
-                                                       d.cell_cnt, d.cell_atoms, rc2, d.maxnb, d.B, d.nbr, d.nnb,
-                                                       d.err, d.cand, d.ncand, d.xref, d.rebuild, d.maxcand);
     }
+}
+
+// the lists of bead-atoms b0 .. b1-1 (after launch_neighbour_prep); ranges
+// made of whole beads may run concurrently
+void launch_neighbour_lists(const Dev& d, int b0, int b1, cudaStream_t st)
+{
+    if (b1 <= b0) return;
+    const int threads = 256;
+    const int blocks = (int)(((size_t)(b1 - b0) * 32 + threads - 1) / threads);
+    const float rc2 = (float)(d.rc * d.rc);
+    if (d.precision == 0)
+        nbr_kernel<Dbl4><<<blocks, threads, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
+                                                     d.cell_cnt, d.cell_atoms, rc2, d.maxnb, b1, d.nbr, d.nnb, d.err,
+                                                     d.cand, d.ncand, d.xref, d.rebuild, d.maxcand, b0);
+    else
+        nbr_kernel<float4><<<blocks, threads, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
+                                                       d.cell_cnt, d.cell_atoms, rc2, d.maxnb, b1, d.nbr, d.nnb,
+                                                       d.err, d.cand, d.ncand, d.xref, d.rebuild, d.maxcand, b0);
+}
+
+void launch_neighbours(const Dev& d, cudaStream_t st)
+{
+    launch_neighbour_prep(d, st);
+    launch_neighbour_lists(d, 0, d.B, st);
 }
 
 }  // namespace pimd

@@ -73,7 +73,7 @@ __device__ __forceinline__ double normal_of(unsigned long long seed, unsigned id
 // absolute position) in FP64 and sum the other modes, deviations of tenths of
 // an Angstrom, in FP32 (rounding far below one FP32 ulp of the position)
 template <typename Real>
-__device__ __forceinline__ double to_bead(const double* __restrict__ C, const float* __restrict__ Cf,
+__device__ __forceinline__ double to_bead(const double* __restrict__ C, const float* Cf,
                                           const double* sq, const float* sqf, int P, int stride)
 {
     if constexpr (std::is_same<Real, float>::value) {
@@ -84,6 +84,28 @@ __device__ __forceinline__ double to_bead(const double* __restrict__ C, const fl
     double acc = 0.0;
     for (int k = 0; k < P; ++k) acc += C[k] * sq[k * stride];
     return acc;
+}
+
+// FP32 transform staged per block in shared memory ([P][P + 1], the padding
+// keeps the rows a warp touches in distinct banks) when P is at most
+// RP_STAGE_P; larger P read the global copy. Returns the rows to use. The
+// ring finish stages it (a thread reads a column); the ring start reads its
+// row from global memory (one row per thread, cached), which measured faster
+// than staging there.
+constexpr int RP_STAGE_P = 64;
+
+__device__ __forceinline__ const float* stage_cmatf(const float* __restrict__ cmatf, int P, float* buf, int& ld)
+{
+    if (P > RP_STAGE_P) {
+        ld = P;
+        return cmatf;
+    }
+    ld = P + 1;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        const int j = e / P;
+        buf[j * (P + 1) + (e - j * P)] = cmatf[e];
+    }
+    return buf;   // visible after the caller's next __syncthreads
 }
 
 template <typename Real>
@@ -299,12 +321,16 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
     __shared__ double red[32];
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
+    int ldc = t.P;
+    const float* Cfs = cmatf + rp.cmat;
+    if constexpr (std::is_same<Real, float>::value) Cfs = stage_cmatf(Cfs, t.P, sff + blockDim.x, ldc);
     if (t.active) {
-        Vec4<Real> fv = f[rp.ba0 + (size_t)t.kk * t.N + t.i];
+        const Vec4<Real> fv = f[rp.ba0 + (size_t)t.kk * t.N + t.i];
+        const Real fc = t.dd == 0 ? fv.x : (t.dd == 1 ? fv.y : fv.z);   // selects, no local array
         if constexpr (std::is_same<Real, float>::value)
-            sff[t.kk * t.T + t.le] = comp<Real>(fv, t.dd);
+            sff[t.kk * t.T + t.le] = fc;
         else
-            sf[t.kk * t.T + t.le] = (double)comp<Real>(fv, t.dd);
+            sf[t.kk * t.T + t.le] = (double)fc;
     }
     __syncthreads();
     double dK = 0.0;
@@ -314,7 +340,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         if constexpr (std::is_same<Real, float>::value) {
             // FP32 forces: their normal-mode components summed in FP32
             float a = 0.0f;
-            for (int j = 0; j < t.P; ++j) a = fmaf(cmatf[rp.cmat + (size_t)j * t.P + k], sff[j * t.T + t.le], a);
+            for (int j = 0; j < t.P; ++j) a = fmaf(Cfs[j * ldc + k], sff[j * t.T + t.le], a);
             fn = (double)a;
         } else {
             for (int j = 0; j < t.P; ++j) fn += cmat[rp.cmat + (size_t)j * t.P + k] * sf[j * t.T + t.le];
@@ -373,6 +399,14 @@ void launch_heat_sum(const Dev& d, cudaStream_t st)
 
 static size_t rp_smem(const Dev& d) { return (size_t)d.rp_threads * (sizeof(double) + sizeof(float)); }
 
+// ring finish: the per-entry vectors plus, on the FP32 paths, the staged
+// transform of the largest P <= RP_STAGE_P among the replicas
+static size_t rp_step_smem(const Dev& d)
+{
+    const size_t stage = d.precision == 0 ? 0 : (size_t)d.rp_stage_P * (d.rp_stage_P + 1) * sizeof(float);
+    return rp_smem(d) + stage;
+}
+
 void launch_beads(const Dev& d, cudaStream_t st)
 {
     if (d.precision == 0)
@@ -398,11 +432,11 @@ void launch_rp_start(const Dev& d, cudaStream_t st)
 void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
 {
     if (d.precision == 0)
-        rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
+        rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, d.dt, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
     else
-        rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
+        rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, d.dt, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
 }

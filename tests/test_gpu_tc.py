@@ -132,5 +132,12 @@ def test_ice_full_size_sampled_beads(ice_model, precision):
     assert all(v >= 0 for v in st.values()) and st["adjoint"] > 0
     # ring start, skin check, lists, descriptors, network, adjoint, ring
     # finish (which ends the step); the FP32 path adds the energy reduction
-    # (the BF16 adjoint sums the per-bead energies and virials itself)
-    assert ctx.kernels_per_step() == (7 if precision == "bf16_tc" else 8)
+    # (the BF16 adjoint sums the per-bead energies and virials itself). The
+    # BF16 step runs the descriptors, network and adjoint once per half of
+    # the bead-atoms (overlapped halves, on by default here).
+    if precision == "bf16_tc":
+        assert ctx.kernels_per_step() == 10
+        ctx.set_overlap(False)
+        assert ctx.kernels_per_step() == 7
+    else:
+        assert ctx.kernels_per_step() == 8
