@@ -416,7 +416,8 @@ int pimd_set_stage_timing(pimd_ctx* ctx, int on);
 /* Autotuner. Times the descriptor + adjoint kernels on the context's current
  * configuration for each candidate (pair sums with band length 4..16 of the
  * shuffle-carry schedule, ordered pairs, and -- in FP32 / BF16 precision --
- * moment tensors) and keeps the fastest; the per-step graphs are re-recorded
+ * moment tensors, in BF16 with the adjoint at 12 and at 16 warps per SM)
+ * and keeps the fastest; the per-step graphs are re-recorded
  * at the next pimd_step. reps: timed repetitions per candidate (>= 1).
  * out_ms: host [3] or NULL -> best time (ms, descriptors + adjoint), the
  * choice (band length, 0 = ordered pairs, -1 = moment tensors), time of the
@@ -439,6 +440,17 @@ int pimd_set_angular(pimd_ctx* ctx, int algo);
 
 /* The angular evaluation in force (pimd_angular), -1 for a NULL ctx.       */
 int pimd_get_angular(const pimd_ctx* ctx);
+
+/* Residency of the BF16 moment-tensor adjoint (the force kernel of the
+ * BF16_TC path with moment tensors; no counterpart in the paper, a launch
+ * configuration): 12 warps per SM (166 registers per thread) or 16 (a
+ * 128-register build). Same arithmetic per bead-atom either way; which is
+ * faster depends on the workload, so pimd_tune times both. The per-step
+ * graphs are re-recorded at the next pimd_step. Errors: INVALID_ARG
+ * (warps_per_sm not 12 or 16). pimd_get_adjoint_warps: the setting in force
+ * (12 or 16), -1 for a NULL ctx.                                            */
+int pimd_set_adjoint_warps(pimd_ctx* ctx, int warps_per_sm);
+int pimd_get_adjoint_warps(const pimd_ctx* ctx);
 
 /* Number of kernels one step launches (memset nodes not counted).          */
 int pimd_kernels_per_step(const pimd_ctx* ctx);

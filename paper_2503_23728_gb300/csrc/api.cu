@@ -1339,12 +1339,16 @@ int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
         return cuda_check(c, cudaErrorUnknown, "cudaEventCreate");
     }
     const Sched before = c->d.sched;
-    Sched cands[8];
+    Sched cands[10];
     int nc = 0;
     const int rl[6] = {4, 6, 8, 10, 12, 16};
     for (int q = 0; q < 6; ++q) cands[nc++] = Sched{rl[q], rl[q] + 32, 0, 0};
     cands[nc++] = Sched{8, 1 << 30, 0, 0};                 // ordered pairs for every atom
-    if (c->d.mom) cands[nc++] = Sched{8, 40, 0, 1};       // moment tensors
+    if (c->d.mom) {
+        cands[nc++] = Sched{8, 40, 0, 1, 0};                 // moment tensors
+        // the BF16 moment adjoint at 16 warps per SM (128 registers)
+        if (c->d.precision == PIMD_BF16_TC) cands[nc++] = Sched{8, 40, 0, 1, 1};
+    }
     double best = 1e30, t_default = 0.0;
     Sched pick = before;
     for (int q = 0; q < nc && !rc; ++q) {
@@ -1363,7 +1367,8 @@ int pimd_tune(pimd_ctx* c, int reps, double* out_ms)
             tmin = std::min(tmin, (double)ms);
         }
         const Sched& s = cands[q];
-        const bool same = s.ang == before.ang && (s.ang || (s.rmax == before.rmax && s.band_min == before.band_min &&
+        const bool same = s.ang == before.ang && (s.ang ? s.adj_wide == before.adj_wide
+                                                        : (s.rmax == before.rmax && s.band_min == before.band_min &&
                                                            s.small_atomics == before.small_atomics));
         if (same) t_default = tmin;   // the schedule in force before tuning
         if (tmin < best) {
@@ -1390,8 +1395,8 @@ int pimd_set_schedule(pimd_ctx* c, int band_length)
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
     if (band_length != 0 && (band_length < 1 || band_length > 16))
         return fail(c, PIMD_ERR_INVALID_ARG, "band_length must be 0 or 1..16");
-    const int ang = c->d.sched.ang;
-    c->d.sched = band_length == 0 ? Sched{8, 1 << 30, 0, ang} : Sched{band_length, band_length + 32, 0, ang};
+    const int ang = c->d.sched.ang, wide = c->d.sched.adj_wide;
+    c->d.sched = band_length == 0 ? Sched{8, 1 << 30, 0, ang, wide} : Sched{band_length, band_length + 32, 0, ang, wide};
     drop_graphs(c);
     c->forces_valid = false;
     return PIMD_OK;
@@ -1414,6 +1419,23 @@ int pimd_get_angular(const pimd_ctx* c)
 {
     if (!c) return -1;
     return c->d.sched.ang ? PIMD_ANG_MOMENTS : PIMD_ANG_PAIRS;
+}
+
+int pimd_set_adjoint_warps(pimd_ctx* c, int warps_per_sm)
+{
+    if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
+    if (warps_per_sm != 12 && warps_per_sm != 16)
+        return fail(c, PIMD_ERR_INVALID_ARG, "warps_per_sm must be 12 or 16");
+    c->d.sched.adj_wide = warps_per_sm == 16 ? 1 : 0;
+    drop_graphs(c);
+    c->forces_valid = false;
+    return PIMD_OK;
+}
+
+int pimd_get_adjoint_warps(const pimd_ctx* c)
+{
+    if (!c) return -1;
+    return c->d.sched.adj_wide ? 16 : 12;
 }
 
 int pimd_kernels_per_step(const pimd_ctx* c)

@@ -87,6 +87,8 @@ struct Sched {
     int small_atomics;   // below band_min: 1 = flat walk with shared atomics,
                          // 0 = ordered pairs (each pair twice, no atomics)
     int ang;             // angular terms: 0 = pair sums, 1 = moment tensors (FP32 only)
+    int adj_wide;        // BF16 moment adjoint: 0 = 12 warps per SM (166 registers),
+                         // 1 = 16 warps per SM (128 registers)
 };
 
 // metadynamics: CV definition and bias parameters (by value to the kernels)

@@ -1116,7 +1116,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int ADJF_WARP_BYTES = NMONO * 16 + NRED * 16 + (MDEG + 1) * 16 + ADJF_RG * 16 + NA * 4;
 
-__global__ void __launch_bounds__(32 * ADJF_WARPS, 12) desc_mom_adj_fast_kernel(
+// MINB: resident warps per SM that the register budget must allow (12: 166
+// registers; 14 gives a 128-register build, which the hardware then runs at
+// 16 warps per SM); which one is faster depends on the workload (tuned).
+template <int MINB>
+__global__ void __launch_bounds__(32 * ADJF_WARPS, MINB) desc_mom_adj_fast_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
@@ -1358,10 +1362,17 @@ static void run_adj_fast(const Dev& d, const void* dpv, int b0, int b1, cudaStre
 {
     if (b1 <= b0) return;
     const size_t sm = (size_t)ADJF_WARPS * ADJF_WARP_BYTES;
-    desc_mom_adj_fast_kernel<<<(b1 - b0 + ADJF_WARPS - 1) / ADJF_WARPS, 32 * ADJF_WARPS, sm, st>>>(
-        (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, b1,
-        *(const DescParams<float>*)dpv, (const float4*)d.mom, (const float*)d.dEdG, (float4*)d.f,
-        (float*)d.wbuf, d.deterministic, (float4*)d.vbuf, (const float*)d.Eatom, d.V, d.W, b0);
+    const int grid = (b1 - b0 + ADJF_WARPS - 1) / ADJF_WARPS;
+    if (d.sched.adj_wide)
+        desc_mom_adj_fast_kernel<14><<<grid, 32 * ADJF_WARPS, sm, st>>>(
+            (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, b1,
+            *(const DescParams<float>*)dpv, (const float4*)d.mom, (const float*)d.dEdG, (float4*)d.f,
+            (float*)d.wbuf, d.deterministic, (float4*)d.vbuf, (const float*)d.Eatom, d.V, d.W, b0);
+    else
+        desc_mom_adj_fast_kernel<12><<<grid, 32 * ADJF_WARPS, sm, st>>>(
+            (const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.nbr, d.nnb, d.maxnb, b1,
+            *(const DescParams<float>*)dpv, (const float4*)d.mom, (const float*)d.dEdG, (float4*)d.f,
+            (float*)d.wbuf, d.deterministic, (float4*)d.vbuf, (const float*)d.Eatom, d.V, d.W, b0);
 }
 
 // The BF16 moment path (reduced-basis forward, fast adjoint) on the bead-atoms

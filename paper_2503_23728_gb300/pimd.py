@@ -28,7 +28,7 @@ EXPORTS = ["pimd_abi_version", "pimd_workspace_size", "pimd_create", "pimd_set_w
            "pimd_metad_hills", "pimd_metad_set_hills", "pimd_metad_cv", "pimd_selftest_bounded_wait",
            "pimd_set_gfn", "pimd_set_stage_timing", "pimd_rdf_gr", "pimd_cv_histogram", "pimd_pi_fes",
            "pimd_metad_fes", "pimd_set_noise_index", "pimd_set_forces", "pimd_ring_start", "pimd_ring_finish",
-           "pimd_set_overlap"]
+           "pimd_set_overlap", "pimd_set_adjoint_warps", "pimd_get_adjoint_warps"]
 ANGULAR = {"pairs": 0, "moments": 1}
 STAGES = ["ring_start", "neighbours", "descriptors", "network", "adjoint", "energy", "ring_finish"]
 
@@ -150,6 +150,9 @@ def load(path: str = LIB_PATH):
     L.pimd_set_gfn.argtypes = [vp, vp]
     L.pimd_get_angular.argtypes = [vp]
     L.pimd_get_angular.restype = ct.c_int
+    L.pimd_set_adjoint_warps.argtypes = [vp, ct.c_int]
+    L.pimd_get_adjoint_warps.argtypes = [vp]
+    L.pimd_get_adjoint_warps.restype = ct.c_int
     L.pimd_selftest_bounded_wait.argtypes = [vp, ct.c_double]
     L.pimd_metad_hills.argtypes = [vp, ct.c_int, dp, dp, ct.c_int]
     L.pimd_metad_hills.restype = ct.c_int
@@ -270,7 +273,8 @@ def pimd_tune(ctx, reps: int = 3) -> dict:
     _check(load().pimd_tune(ctx, int(reps), _dp(out)), ctx)
     choice = int(out[1])
     return {"best_ms": float(out[0]), "band_length": max(choice, 0),
-            "angular": "moments" if choice < 0 else "pairs", "default_ms": float(out[2])}
+            "angular": "moments" if choice < 0 else "pairs", "default_ms": float(out[2]),
+            "adjoint_warps": int(load().pimd_get_adjoint_warps(ctx))}
 
 
 def pimd_set_schedule(ctx, band_length: int):
@@ -625,6 +629,14 @@ class Context:
 
     def set_angular(self, algo: str):
         pimd_set_angular(self.h, algo)
+
+    def set_adjoint_warps(self, warps_per_sm: int):
+        """Residency of the BF16 moment-tensor adjoint: 12 or 16 warps per SM."""
+        _check(load().pimd_set_adjoint_warps(self.h, int(warps_per_sm)), self.h)
+
+    @property
+    def adjoint_warps(self) -> int:
+        return int(load().pimd_get_adjoint_warps(self.h))
 
     def metad_hills(self, replica: int = 0):
         return pimd_metad_hills(self.h, replica)

@@ -1,10 +1,11 @@
 """Autotuner with a persistent cache of its choices.
 
 For a context it chooses, by timing them on the live workload:
-  * how the angular terms are evaluated (moment tensors or pair sums) and,
-    for pair sums, the band length of the pair schedule (`pimd_tune`, which
-    times the descriptor forward and the adjoint of every candidate with
-    CUDA events);
+  * how the angular terms are evaluated (moment tensors or pair sums), for
+    pair sums the band length of the pair schedule, and for the BF16
+    moment-tensor adjoint its residency, 12 or 16 warps per SM (`pimd_tune`,
+    which times the descriptor forward and the adjoint of every candidate
+    with CUDA events);
   * whether the step runs the two halves of its bead-atoms as overlapping
     branches of its graph (`pimd_set_overlap`), from whole-step timings.
 The choices are stored in a JSON file under a key of the workload's shape:
@@ -95,6 +96,7 @@ def apply(ctx, choice: dict) -> None:
     ctx.set_angular(choice["angular"])
     if choice["angular"] == "pairs":
         ctx.set_schedule(int(choice["band_length"]))
+    ctx.set_adjoint_warps(int(choice.get("adjoint_warps", 12)))
     ctx.set_overlap(bool(choice.get("overlap", True)))
 
 
@@ -114,6 +116,7 @@ def tune(ctx, cache: str | None = DEFAULT_CACHE, reps: int = 3, steps: int = 10,
         return choice
     kern = ctx.tune(reps=reps)   # angular method and pair schedule, applied by the library
     choice = {"angular": kern["angular"], "band_length": int(kern["band_length"]),
+              "adjoint_warps": int(kern.get("adjoint_warps", 12)),
               "kernels_ms": float(kern["best_ms"]), "mean_neighbours": nb}
     # overlapped halves, from whole-step timings (state restored afterwards)
     q, p, step, Q = ctx.get_state()

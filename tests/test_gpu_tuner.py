@@ -37,3 +37,27 @@ def test_tuner_measures_applies_and_caches(ice_model, tmp_path):
     again = tuner.tune(ctx2, cache=cache)
     assert again["source"] == "cache" and again["angular"] == got["angular"]
     assert again["overlap"] == got["overlap"]
+
+
+def test_adjoint_residency_changes_no_force(water64_model):
+    """The BF16 moment adjoint at 12 and at 16 warps per SM: the same
+    arithmetic per bead-atom, so deterministic-mode forces, energies and
+    virials are bit-identical; other values are refused."""
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2503_23728_gb300 import pimd as P
+    w, r, m = water64_model
+    ctx = P.Context(w.replicas, w.dt_fs, w.gamma0_per_fs, precision="bf16_tc", widths=w.widths,
+                    deterministic=True)
+    ctx.set_weights(m)
+    ctx.set_angular("moments")
+    assert ctx.adjoint_warps == 12
+    e12, f12, v12 = (t.cpu().numpy() for t in ctx.energy_forces())
+    ctx.set_adjoint_warps(16)
+    assert ctx.adjoint_warps == 16
+    e16, f16, v16 = (t.cpu().numpy() for t in ctx.energy_forces())
+    assert np.array_equal(f12, f16) and np.array_equal(e12, e16) and np.array_equal(v12, v16)
+    ctx.step(2)   # the step graph runs with the wide adjoint
+    with pytest.raises(P.PimdError):
+        ctx.set_adjoint_warps(14)
+    ctx.close()

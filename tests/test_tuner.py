@@ -29,13 +29,16 @@ class _FakeCtx:
 
     def tune(self, reps=3):
         self.calls.append("tune")
-        return {"angular": "moments", "band_length": 0, "best_ms": 0.3, "default_ms": 0.3}
+        return {"angular": "moments", "band_length": 0, "best_ms": 0.3, "default_ms": 0.3, "adjoint_warps": 16}
 
     def set_angular(self, a):
         self.calls.append(("angular", a))
 
     def set_schedule(self, b):
         self.calls.append(("schedule", b))
+
+    def set_adjoint_warps(self, n):
+        self.calls.append(("adjoint_warps", n))
 
     def set_overlap(self, on):
         self.calls.append(("overlap", on))
@@ -60,13 +63,14 @@ def test_cached_choice_is_applied_without_timing(tmp_path, monkeypatch):
     path = str(tmp_path / "cache.json")
     ctx = _FakeCtx([_Rep(1296, 32)])
     key = tuner.workload_key(ctx)
-    json.dump({key: [{"angular": "pairs", "band_length": 10, "overlap": False, "mean_neighbours": 85.0}]},
-              open(path, "w"))
+    json.dump({key: [{"angular": "pairs", "band_length": 10, "overlap": False, "mean_neighbours": 85.0,
+                      "adjoint_warps": 16}]}, open(path, "w"))
     monkeypatch.setattr(tuner, "_step_ms", lambda *a, **k: (_ for _ in ()).throw(AssertionError("timed")))
     got = tuner.tune(ctx, cache=path)
     assert got["source"] == "cache" and got["band_length"] == 10
     assert "tune" not in ctx.calls
     assert ("angular", "pairs") in ctx.calls and ("schedule", 10) in ctx.calls and ("overlap", False) in ctx.calls
+    assert ("adjoint_warps", 16) in ctx.calls
 
 
 def test_measured_choice_is_stored_and_state_restored(tmp_path, monkeypatch):
@@ -80,7 +84,7 @@ def test_measured_choice_is_stored_and_state_restored(tmp_path, monkeypatch):
     assert ctx.overlap is True
     table = json.load(open(path))
     (entry,) = table[tuner.workload_key(ctx)]
-    assert entry["overlap"] is True and entry["mean_neighbours"] == 86.3
+    assert entry["overlap"] is True and entry["mean_neighbours"] == 86.3 and entry["adjoint_warps"] == 16
     # a second context of the same shape, its neighbour count drifted by a
     # fraction (beads spread from their initial positions), reads it back
     ctx2 = _FakeCtx([_Rep(1296, 32)], mean_nbrs=85.4)
