@@ -1468,43 +1468,51 @@ template <typename Real>
 __global__ void __launch_bounds__(256) energy_reduce_kernel(const Real* __restrict__ Eatom,
                                                             const Real* __restrict__ wbuf,
                                                             const BeadSys* __restrict__ bsys, int S, int wpb,
-                                                            double* __restrict__ V, double* __restrict__ Wv)
+                                                            int lpb, double* __restrict__ V,
+                                                            double* __restrict__ Wv)
 {
-    // wpb warps per bead (8 / wpb beads per 256-thread block): the energy and
-    // the 9 virial entries summed over the bead's atoms in a fixed order
-    // (atoms strided over the bead's lanes, a fixed butterfly per warp, the
-    // warps' partials in warp order). FP64 terms in FP64; FP32 terms as
-    // double-float pairs, rounded to FP64 at the end.
+    // The energy and the 9 virial entries of a bead summed over its atoms in
+    // a fixed order: atoms strided over the bead's lanes, a fixed butterfly
+    // within the bead's lanes, the warps' partials in warp order. Large
+    // beads take wpb warps (8 / wpb beads per 256-thread block); small ones
+    // share a warp, lpb lanes each (a power of two <= 32; lpb = 32 when
+    // wpb > 1). FP64 terms in FP64; FP32 terms as double-float pairs,
+    // rounded to FP64 at the end.
     __shared__ double part[8][10][2];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    const int s = blockIdx.x * (8 / wpb) + w / wpb, sub = w % wpb;
+    const int gl = (int)lane & (lpb - 1);
+    const int s = (blockIdx.x * (8 / wpb) + w / wpb) * (32 / lpb) + (int)lane / lpb, sub = w % wpb;
     const bool live = s < S;
     const BeadSys sy = live ? bsys[s] : BeadSys{0, 0, 0, 0};
     double hi[10], lo[10];
     if constexpr (std::is_same<Real, double>::value) {
 #pragma unroll
         for (int q = 0; q < 10; ++q) hi[q] = lo[q] = 0.0;
-        for (int i = sub * 32 + (int)lane; i < sy.N; i += 32 * wpb) {
+        for (int i = sub * lpb + gl; i < sy.N; i += lpb * wpb) {
             const size_t b = (size_t)(sy.ba0 + i);
             hi[0] += Eatom[b];
 #pragma unroll
             for (int q = 0; q < 9; ++q) hi[1 + q] += wbuf[b * 9 + q];
         }
+        for (int o = lpb >> 1; o >= 1; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < 10; ++q) hi[q] = warp_sum(hi[q]);
+            for (int q = 0; q < 10; ++q) {
+                // both partners add in the same order (lower lane's value first)
+                const double oh = __shfl_xor_sync(0xffffffffu, hi[q], o);
+                hi[q] = ((int)lane & o) ? oh + hi[q] : hi[q] + oh;
+            }
     } else {
         float fh[10], fl[10];
 #pragma unroll
         for (int q = 0; q < 10; ++q) fh[q] = fl[q] = 0.0f;
-        for (int i = sub * 32 + (int)lane; i < sy.N; i += 32 * wpb) {
+        for (int i = sub * lpb + gl; i < sy.N; i += lpb * wpb) {
             const size_t b = (size_t)(sy.ba0 + i);
             df_add(fh[0], fl[0], (float)Eatom[b]);
 #pragma unroll
             for (int q = 0; q < 9; ++q) df_add(fh[1 + q], fl[1 + q], (float)wbuf[b * 9 + q]);
         }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1)
+        for (int o = lpb >> 1; o >= 1; o >>= 1)
 #pragma unroll
             for (int q = 0; q < 10; ++q) {
                 const float oh = __shfl_xor_sync(0xffffffffu, fh[q], o);
@@ -1545,29 +1553,28 @@ __global__ void __launch_bounds__(256) energy_reduce_kernel(const Real* __restri
         }
         return;
     }
-    if (!live) return;
-    if (lane < 10) {
-        double mine = hi[0] + lo[0];
+    if (!live || gl != 0) return;
+    V[s] = hi[0] + lo[0];
 #pragma unroll
-        for (int q = 1; q < 10; ++q)
-            if ((int)lane == q) mine = hi[q] + lo[q];
-        if (lane == 0) V[s] = mine;
-        else Wv[(size_t)s * 9 + lane - 1] = mine;
-    }
+    for (int q = 1; q < 10; ++q) Wv[(size_t)s * 9 + q - 1] = hi[q] + lo[q];
 }
 
 void launch_energy_reduce(const Dev& d, cudaStream_t st)
 {
-    // warps per bead from the largest bead: one up to 64 atoms, up to 8
+    // warps per bead from the largest bead: one up to 64 atoms, up to 8;
+    // beads of at most 64 atoms share a warp, about 4 atoms per lane
     const int wpb = d.max_N <= 64 ? 1 : d.max_N <= 256 ? 2 : d.max_N <= 1024 ? 4 : 8;
-    const int bpb = 8 / wpb;
+    int lpb = 32;
+    if (wpb == 1)
+        while (lpb > 4 && 4 * (lpb / 2) >= d.max_N) lpb >>= 1;
+    const int bpb = 8 / wpb * (32 / lpb);
     const int blocks = (d.S + bpb - 1) / bpb;
     if (d.precision == 0)
         energy_reduce_kernel<double><<<blocks, 256, 0, st>>>((const double*)d.Eatom, (const double*)d.wbuf, d.bsys, d.S,
-                                                             wpb, d.V, d.W);
+                                                             wpb, lpb, d.V, d.W);
     else
         energy_reduce_kernel<float><<<blocks, 256, 0, st>>>((const float*)d.Eatom, (const float*)d.wbuf, d.bsys, d.S,
-                                                            wpb, d.V, d.W);
+                                                            wpb, lpb, d.V, d.W);
 }
 
 // ---------------------------------------------------------------------------
