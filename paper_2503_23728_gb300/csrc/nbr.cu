@@ -361,6 +361,43 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
     }
 }
 
+// Every bead of at most 32 atoms, no cells and no candidates: one warp per
+// bead, lane = atom i; the bead's positions are shuffled to all lanes and
+// each lane tests j = 0 .. N-1 in order with the same rule, so the lists are
+// the full scan's (ascending, j = i skipped).
+template <typename V4>
+__global__ void __launch_bounds__(256) nbr_small_kernel(const V4* __restrict__ x, const BeadSys* __restrict__ bsys,
+                                                        const Rep* __restrict__ reps, float rc2, int maxnb, int S,
+                                                        int* __restrict__ nbr, int* __restrict__ nnb,
+                                                        DevErr* __restrict__ err)
+{
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= S) return;   // warp-uniform
+    const unsigned lane = lane_id();
+    const BeadSys sy = bsys[s];
+    const Rep& rp = reps[sy.rep];
+    const int n = sy.N;   // <= 32
+    const bool me = (int)lane < n;
+    const float3 xi = me ? pos_f32(x[sy.ba0 + lane]) : make_float3(0.0f, 0.0f, 0.0f);
+    int* out = nbr + (size_t)(sy.ba0 + (me ? (int)lane : 0)) * maxnb;
+    int cnt = 0;
+    for (int j = 0; j < n; ++j) {
+        const float3 xj = make_float3(__shfl_sync(0xffffffffu, xi.x, j), __shfl_sync(0xffffffffu, xi.y, j),
+                                      __shfl_sync(0xffffffffu, xi.z, j));
+        if (me && j != (int)lane && within(rp, xi, xj, rc2)) {
+            if (cnt < maxnb) out[cnt] = j;
+            ++cnt;
+        }
+    }
+    if (me) {
+        nnb[sy.ba0 + lane] = cnt;
+        if (cnt > maxnb) {
+            atomicOr(&err->flags, ERR_NBR_OVERFLOW);
+            atomicMax(&err->max_nbr, cnt);
+        }
+    }
+}
+
 // cell lists and the Verlet check of every bead (before any list range)
 void launch_neighbour_prep(const Dev& d, cudaStream_t st)
 {
@@ -399,6 +436,18 @@ void launch_neighbour_lists(const Dev& d, int b0, int b1, cudaStream_t st)
 
 void launch_neighbours(const Dev& d, cudaStream_t st)
 {
+    if (d.max_N <= 32 && d.n_cell_bs == 0 && d.maxcand == 0) {
+        // only small beads: a warp per bead instead of a warp per bead-atom
+        const float rc2 = (float)(d.rc * d.rc);
+        const int blocks = (d.S + 7) / 8;
+        if (d.precision == 0)
+            nbr_small_kernel<Dbl4><<<blocks, 256, 0, st>>>((const Dbl4*)d.x, d.bsys, d.reps, rc2, d.maxnb, d.S,
+                                                           d.nbr, d.nnb, d.err);
+        else
+            nbr_small_kernel<float4><<<blocks, 256, 0, st>>>((const float4*)d.x, d.bsys, d.reps, rc2, d.maxnb, d.S,
+                                                             d.nbr, d.nnb, d.err);
+        return;
+    }
     launch_neighbour_prep(d, st);
     launch_neighbour_lists(d, 0, d.B, st);
 }

@@ -458,3 +458,33 @@ def test_bounded_wait_times_out_and_gpu_stays_usable(water64_model):
     ctx.set_weights(m)
     ctx.step(2)
     assert np.isfinite(ctx.estimators()[0]["E_tot"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16_tc"])
+def test_small_bead_neighbours_bit_exact(fad_model, precision):
+    """Contexts whose beads all have at most 32 atoms (no cells, no Verlet
+    candidates) build their lists with one warp per bead: the lists equal
+    the oracle's exact FP32 rule for a gas-phase replica (FAD, 10 atoms) and
+    a periodic one (24 atoms in a 12.5 A box, minimum images)."""
+    P = _P()
+    w, r, m = fad_model
+    gas = _with_beads(r, 3)
+    rng = np.random.default_rng(5)
+    grid = np.stack(np.meshgrid(np.arange(3), np.arange(2), np.arange(4), indexing="ij"), -1).reshape(-1, 3)
+    box = np.array([12.5, 12.5, 12.5])
+    x0 = (grid * np.array([4.1, 6.2, 3.1]) + rng.normal(scale=0.3, size=grid.shape)) % box
+    Z = np.resize(r.Z, len(x0)).astype(np.int32)
+    per = s.Replica(Z, x0, box, 2, r.T, 9, "periodic24")
+    ctx = P.Context([gas, per], w.dt_fs, w.gamma0_per_fs, precision=precision, widths=w.widths)
+    ctx.set_weights(m)
+    xs = [_bead_positions(gas, 3, seed=1, sigma=0.3), _bead_positions(per, 2, seed=2, sigma=0.3)]
+    ctx.energy_forces(torch.tensor(np.concatenate([x.reshape(-1, 3) for x in xs]), device="cuda"))
+    nnb, nbr = ctx.neighbours()
+    b = 0
+    for rep, xb in zip((gas, per), xs):
+        for k in range(rep.n_beads):
+            want, _, _ = O.neighbours(xb[k], rep.box, 6.0)
+            for i in range(rep.n_atoms):
+                assert np.array_equal(nbr[b, :nnb[b]], want[i]), (rep.name, k, i)
+                b += 1
+    ctx.close()
