@@ -520,7 +520,7 @@ def config_of(w, precision, world):
                                       "fp64": "fp64"}[precision],
                           "descriptors_adjoint": "fp64" if precision == "fp64" else "fp32",
                           "ring_polymer_estimators": "fp64" if precision == "fp64" else
-                          "fp64 state and estimators; fp32 deviates and normal-mode sums of the fluctuation modes"}}
+                          "fp64 state and estimators; fp32 deviates, heat increments and normal-mode sums of the fluctuation modes"}}
 
 
 def main():

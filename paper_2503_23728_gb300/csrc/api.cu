@@ -364,6 +364,8 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
             const double gam = (k == 0) ? cfg->gamma0_per_fs : 2.0 * cfg->pile_lambda * md.w;
             md.c1 = std::exp(-hO * gam);
             md.c2 = std::sqrt(1.0 - md.c1 * md.c1);
+            md.c1m1 = (float)std::expm1(-hO * gam);
+            md.c1p1 = (float)(md.c1 + 1.0);
             md.sw_w = md.w > 0.0 ? md.sw / md.w : 0.0;
             md.wsw = md.w * md.sw;
             md.smf = std::sqrt(md.mfac);

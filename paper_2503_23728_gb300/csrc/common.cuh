@@ -76,6 +76,8 @@ struct Mode {
     // derived on the host so that the FP64 kernels divide and take roots
     // only in the random deviates: sw / w, w sw, sqrt(mfac), 1 / mfac
     double sw_w, wsw, smf, imf;
+    // c1 - 1 and c1 + 1 in FP32 (from FP64), for the FP32 paths' heat terms
+    float c1m1, c1p1;
 };
 
 constexpr double INV_MVV2E = 1.0 / MVV2E;

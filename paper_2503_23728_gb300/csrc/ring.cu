@@ -61,14 +61,6 @@ __device__ __forceinline__ float normal_dev_f(unsigned long long seed, unsigned 
     return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
-template <typename Real>
-__device__ __forceinline__ double normal_of(unsigned long long seed, unsigned idx, unsigned step, unsigned rep,
-                                            unsigned stream)
-{
-    if constexpr (std::is_same<Real, float>::value) return (double)normal_dev_f(seed, idx, step, rep, stream);
-    return normal_dev(seed, idx, step, rep, stream);
-}
-
 // bead coordinate j from the ring-polymer coordinates of one (atom, dim):
 // FP64 paths sum all P terms in FP64; FP32 paths keep the mode-0 term (the
 // absolute position) in FP64 and sum the other modes, deviations of tenths of
@@ -229,16 +221,33 @@ __device__ __forceinline__ void free_rp(int k, const Mode& md, double m, double 
 }
 
 // PILE-L O sub-step with the host's (c1, c2) for its duration; returns the
-// kinetic-energy change (smkT = sqrt(m k_B T_P) of the coordinate, im = 1/m)
+// kinetic-energy change (smkT = sqrt(m k_B T_P) of the coordinate, im = 1/m).
+// The momentum update is FP64 on every path. The FP32 paths form the heat
+// increment and its block sums in FP32 (this GPU runs FP64 at 2 lanes per SM
+// per clock): with a = sigma xi the noise kick, pn - pv = (c1 - 1) pv + a and
+// pn + pv = (c1 + 1) pv + a, each term of which is FP32-accurate.
 template <typename Real>
-__device__ __forceinline__ double pile_o(const Rep& rp, const Mode& md, double smkT, double im, unsigned local,
-                                         unsigned step, unsigned rep, unsigned stream, double& pv)
+using HeatT = typename std::conditional<std::is_same<Real, float>::value, float, double>::type;
+
+template <typename Real>
+__device__ __forceinline__ HeatT<Real> pile_o(const Rep& rp, const Mode& md, double smkT, double im, unsigned local,
+                                              unsigned step, unsigned rep, unsigned stream, double& pv)
 {
-    const double xi = normal_of<Real>(rp.seed, local, step, rep, stream);
-    const double pn = md.c1 * pv + smkT * md.c2 * xi;
-    const double dK = (pn * pn - pv * pv) * 0.5 * im;
-    pv = pn;
-    return dK;
+    if constexpr (std::is_same<Real, float>::value) {
+        const float xi = normal_dev_f(rp.seed, local, step, rep, stream);
+        const double sig = smkT * md.c2;
+        const double pn = md.c1 * pv + sig * (double)xi;
+        const float pvf = (float)pv, a = (float)sig * xi;
+        const float dK = 0.5f * (float)im * (fmaf(md.c1m1, pvf, a) * fmaf(md.c1p1, pvf, a));
+        pv = pn;
+        return dK;
+    } else {
+        const double xi = normal_dev(rp.seed, local, step, rep, stream);
+        const double pn = md.c1 * pv + smkT * md.c2 * xi;
+        const double dK = (pn * pn - pv * pv) * 0.5 * im;
+        pv = pn;
+        return dK;
+    }
 }
 
 // OBABO: O(dt/2) B(dt/2) A(dt); BAOAB: B(dt/2) A(dt/2) O(dt) A(dt/2); on each
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
     __shared__ double red[32];
     const RpThread t = rp_thread(blocks, reps);
     const Rep& rp = reps[t.r];
-    double dK = 0.0;
+    HeatT<Real> dK = 0;
     if (t.active) {
         const int k = t.kk;
         const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
     }
     // thermostat heat: block partial, summed per replica in block order later
     dK = warp_sum(dK);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dK;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)dK;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -348,7 +357,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
             sf[t.kk * t.T + t.le] = (double)fc;
     }
     __syncthreads();
-    double dK = 0.0;
+    HeatT<Real> dK = 0;
     if (t.active) {
         const int k = t.kk;
         double fn = 0.0;
@@ -375,7 +384,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         }
     }
     dK = warp_sum(dK);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dK;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)dK;
     __syncthreads();
     if (!do_step) return;   // block-uniform
     if (threadIdx.x == 0) {

@@ -58,7 +58,9 @@ def test_two_slices_reproduce_the_single_context(water64_model):
         assert np.array_equal(qs.reshape(rep.n_beads, hi - lo, 3), q[:, lo:hi, :])
         assert np.array_equal(ps.reshape(rep.n_beads, hi - lo, 3), p[:, lo:hi, :])
         Qs += float(Qk[0])
-    assert abs(Qs - float(Q[0])) <= 1e-9 * max(1.0, abs(float(Q[0])))
+    # the FP32 path forms heat increments and their block sums in FP32, and
+    # the slices group coordinates into blocks differently from the whole
+    assert abs(Qs - float(Q[0])) <= 1e-5 * max(1.0, abs(float(Q[0])))
     # and the whole trajectory against the FP64 oracle (FP32 path bar)
     so = O.System(rep, s.MASS, w.dt_fs, w.gamma0_per_fs, model=m)
     so.step(n)
