@@ -809,6 +809,9 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.n_rp_blocks = (int)b.rp_blocks.size();
     for (const Rep& rp : b.reps)
         if (rp.P <= 64) d.rp_stage_P = std::max(d.rp_stage_P, rp.P);
+    d.unit_mfac = 1;
+    for (const Mode& md : b.modes)
+        if (md.mfac != 1.0 || md.imf != 1.0 || md.smf != 1.0) d.unit_mfac = 0;
     d.rp_threads = 256;
     d.x = w + o.x;
     d.f = w + o.f;

@@ -33,6 +33,7 @@ struct Dev {
     int n_rp_blocks = 0;
     int rp_threads = 256;
     int rp_stage_P = 0;                // largest P <= 64 among the replicas (transform rows staged per block)
+    int unit_mfac = 0;                 // every ring coordinate has the atom's mass (normal modes): skip the factors
 
     void* x = nullptr;                 // Vec4<Real>[B] positions (w = type)
     void* f = nullptr;                 // Vec4<Real>[B] forces

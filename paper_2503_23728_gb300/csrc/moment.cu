@@ -114,10 +114,13 @@ __device__ __forceinline__ void finish_moments(const float2 (&acc)[MSLOT][2], co
                                                float4* __restrict__ Mout)
 {
     if (Mout != nullptr) {
+        // the last slot's lanes past the 165th monomial hold nothing (the
+        // adjoints read only the 165)
 #pragma unroll
         for (int k = 0; k < MSLOT; ++k)
-            Mout[((size_t)b * MSLOT + k) * 32 + lane] =
-                make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
+            if (k < MSLOT - 1 || lane < (unsigned)MLAST)
+                Mout[((size_t)b * MSLOT + k) * 32 + lane] =
+                    make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
     }
 
     // per lane: its monomials' share of sum_abc 2^-zeta w lambda^s M^2, packed
@@ -582,7 +585,7 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
         if (mf >= 0) T[mf] = make_float4(lo.x, lo.y, hi.x, hi.y);
     }
     __syncwarp();
-#pragma unroll 1
+#pragma unroll
     for (int L = 0; L < 7; ++L) {
         const short4 e = *reinterpret_cast<const short4*>(g_red.up[L][lane]);   // one 8-byte load
         if (e.x >= 0) {

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
                                 const double* __restrict__ cmat, const float* __restrict__ cmatf,
                                 const Mode* __restrict__ modes,
                                 const double* __restrict__ mass, const double2* __restrict__ minv,
-                                const unsigned long long* __restrict__ stepp, double dt, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
+                                const unsigned long long* __restrict__ stepp, double hdt, double kick, int unit_mfac, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
                                 const double* __restrict__ fnm, Vec4<Real>* __restrict__ x,
                                 double* __restrict__ qpart, Vec4<Real>* __restrict__ f, double* __restrict__ W,
                                 double* __restrict__ V, double* __restrict__ Q, int ordered_heat,
@@ -274,19 +274,21 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
         const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
         const Mode md = modes[rp.mode0 + k];
         const double2 mi = minv[rp.atom0 + t.i];
-        const double m = mass[rp.atom0 + t.i] * md.mfac, im = mi.x * md.imf, smkT = mi.y * md.smf;
-        const double kick = 0.5 * dt * INV_MVV2E;
+        // mass factors of the ring coordinate (all 1 for normal modes)
+        const double ma = mass[rp.atom0 + t.i];
+        const double m = unit_mfac ? ma : ma * md.mfac, im = unit_mfac ? mi.x : mi.x * md.imf,
+                     smkT = unit_mfac ? mi.y : mi.y * md.smf;
         double pv = p[g], qv = q[g];
         const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + t.i) * 3 + t.dd);
         if (baoab) {
             pv += kick * fnm[g];
-            free_rp(k, md, m, im, 0.5 * dt, pv, qv);
+            free_rp(k, md, m, im, hdt, pv, qv);
             if (thermostat) dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
-            free_rp(k, md, m, im, 0.5 * dt, pv, qv);
+            free_rp(k, md, m, im, hdt, pv, qv);
         } else {
             if (thermostat) dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
             pv += kick * fnm[g];
-            free_rp(k, md, m, im, dt, pv, qv);
+            free_rp(k, md, m, im, 2.0 * hdt, pv, qv);
         }
         p[g] = pv;
         q[g] = qv;
@@ -335,7 +337,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
                                  const double* __restrict__ cmat, const float* __restrict__ cmatf,
                                  const Mode* __restrict__ modes,
                                  const double* __restrict__ mass, const double2* __restrict__ minv,
-                                 const unsigned long long* stepp, double dt, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
+                                 const unsigned long long* stepp, double kick, int unit_mfac, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
                                  double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ qpart,
                                  DevErr* __restrict__ err, double* __restrict__ Q, int ordered_heat,
                                  unsigned long long* stepw)
@@ -375,10 +377,11 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         if (do_step) {
             const Mode md = modes[rp.mode0 + k];
             const double2 mi = minv[rp.atom0 + t.i];
-            double pv = p[g] + 0.5 * dt * INV_MVV2E * fn;
+            double pv = p[g] + kick * fn;
             if (thermostat) {
                 const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + t.i) * 3 + t.dd);
-                dK = pile_o<Real>(rp, md, mi.y * md.smf, mi.x * md.imf, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
+                const double smkT = unit_mfac ? mi.y : mi.y * md.smf, im = unit_mfac ? mi.x : mi.x * md.imf;
+                dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
             }
             p[g] = pv;
         }
@@ -445,11 +448,11 @@ void launch_rp_start(const Dev& d, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, 0.5 * d.dt, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat, d.splitting, d.q, d.p, d.fnm,
             (Dbl4*)d.x, d.qpart, (Dbl4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
     else
         rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, d.dt, d.thermostat, d.splitting, d.q, d.p, d.fnm,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, 0.5 * d.dt, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat, d.splitting, d.q, d.p, d.fnm,
             (float4*)d.x, d.qpart, (float4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
 }
 
@@ -457,11 +460,11 @@ void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
 {
     if (d.precision == 0)
         rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, d.dt, d.thermostat && !d.splitting,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
     else
         rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, d.dt, d.thermostat && !d.splitting,
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat && !d.splitting,
             do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
 }
 
