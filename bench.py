@@ -53,10 +53,10 @@ MOM_RED_ADJ_FLOP_PER_NBR = 380 + 2 * 628
 MOM_RED_ADJ_FLOP_PER_ATOM = 165 * 4 * 2 + 36 * 4 * 2 + 483 * 4 * 2
 # DRAM bytes (read + write) of one adjoint launch from an ncu capture of the
 # same kernel on the same workload (ice Ih, P = 32, BF16 network, reduced
-# moment basis, desc_mom_adj_fast_kernel): 139.9 MB read (mostly the 3 KB of
-# moments per bead-atom written by the forward) + 3.8 MB written. Reported
-# only for that configuration.
-ADJ_TRAFFIC_NCU = {("ice", "bf16_tc", "moments"): 139.90656e6 + 3.798016e6}
+# moment basis, desc_mom_adj_fast_kernel<12>): 139.9 MB read (mostly the
+# 2.6 KB of moments per bead-atom written by the forward) + 3.4 MB written.
+# Reported only for that configuration.
+ADJ_TRAFFIC_NCU = {("ice", "bf16_tc", "moments"): 139.896832e6 + 3.420928e6}
 
 
 def args():
