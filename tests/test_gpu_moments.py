@@ -3,8 +3,7 @@ functions (O(n) per atom) against the FP64 oracle's pair sums and against the
 pair-sum kernels on the same inputs.
 
 Bars as for the FP32 path: descriptors within 1e-5 of each channel's scale,
-forces and virial within 1e-5 relative max-norm (FAD: 1e-4, its FP32 bar, see
-the deterministic-mode test)."""
+forces and virial within 1e-5 relative max-norm."""
 import numpy as np
 import pytest
 
@@ -100,8 +99,8 @@ def test_fad_forced_moments(fad_model):
     ctx.set_angular("moments")
     e, f, v = ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
     Eo, Fo, Wo = O.energy_forces_batch(m, rep.Z, xb, None)
-    assert _relmax(f.cpu().numpy().reshape(Fo.shape), Fo) < 1e-4
-    assert _relmax(v.cpu().numpy(), Wo) < 1e-4
+    assert _relmax(f.cpu().numpy().reshape(Fo.shape), Fo) < 1e-5
+    assert _relmax(v.cpu().numpy(), Wo) < 1e-5
 
 
 def test_clusters_with_isolated_atom_and_empty_lists():

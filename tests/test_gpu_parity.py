@@ -392,11 +392,7 @@ def test_deterministic_mode_resume_is_bit_identical(water64_model, fad_model, wh
     xb = _bead_positions(rep, 4, seed=5)
     _, f, _ = b.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
     _, Fo, _ = O.energy_forces_batch(m, rep.Z, xb, rep.box)
-    # FAD's per-element normalisation rests on 2-4 atoms, so several sigma sit
-    # at the 1e-2 floor and amplify FP32 descriptor round-off ~100x; its
-    # specified precision is FP64 (1e-10 elsewhere). Water keeps the 1e-5 bar.
-    tol = 1e-4 if which == "fad" else 1e-5
-    assert _relmax(f.cpu().numpy().reshape(Fo.shape), Fo) < tol
+    assert _relmax(f.cpu().numpy().reshape(Fo.shape), Fo) < 1e-5
     assert b.kernels_per_step() == 9
 
 
