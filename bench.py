@@ -62,8 +62,8 @@ ADJ_TRAFFIC_NCU = {("ice", "bf16_tc", "moments"): 139.896832e6 + 3.420928e6}
 def args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16_tc", choices=["bf16_tc", "fp32", "fp64"])
     ap.add_argument("--workload", default="ice", choices=["ice", "water64", "fad", "batch", "water4096"])
@@ -649,10 +649,13 @@ def reference(a, rank, world):
     G = O.descriptors(m, rep.x0, rep.box)
     s.set_normalisation(m, G, rep.Z)
     rng = np.random.default_rng(3)
-    steps = min(a.steps, 20)
-    warm = min(a.warmup, 5)   # at most 5 untimed evaluations (~0.6 s each on 16 cores)
+    warm = max(1, min(a.warmup, 5))   # at most 5 untimed evaluations (~0.6 s each on 16 cores)
+    tw = time.perf_counter()
     for _ in range(warm):
         O.energy_forces(m, rep.Z, rep.x0 + rng.normal(scale=0.05, size=rep.x0.shape), rep.box)
+    per = (time.perf_counter() - tw) / warm
+    # exactly the requested steps while they fit in ~4 minutes, else as many as fit
+    steps = a.steps if a.steps * per <= 240.0 else max(1, int(240.0 / per))
     t0 = time.perf_counter()
     for _ in range(steps):
         O.energy_forces(m, rep.Z, rep.x0 + rng.normal(scale=0.05, size=rep.x0.shape), rep.box)
