@@ -310,13 +310,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(
 template <int W, int L>
 __host__ __device__ constexpr int park_cols() { return (W < 64 ? 64 : W) + (L - 1) * (W / 2); }
 
-// threads of the parked kernel: four warps per tensor-memory lane quadrant,
-// each taking a quarter of a phase's columns in the epilogues
-constexpr int PARK_THREADS = 512;
-constexpr int PARK_NH = PARK_THREADS / 128;   // column groups per row
+// threads of the parked kernel: NT / 128 warps per tensor-memory lane
+// quadrant, each taking that share of a phase's columns in the epilogues.
+// 512 threads and 256 tensor-memory columns per tile, two tiles per SM; a
+// narrow network whose parked columns fit in 128 runs 256 threads and 128
+// columns per tile, four tiles per SM.
+template <int W, int L>
+__host__ __device__ constexpr int park_threads() { return (W == 64 && park_cols<W, L>() <= 128) ? 256 : 512; }
 
 template <int W, int L>
-__global__ void __launch_bounds__(PARK_THREADS, 2) mlp_tc_park_kernel(
+__global__ void __launch_bounds__(park_threads<W, L>(), park_threads<W, L>() == 512 ? 2 : 4) mlp_tc_park_kernel(
     const float* __restrict__ G, const int* __restrict__ perm, const int* __restrict__ tile_type,
     const unsigned char* __restrict__ wimg, size_t img_per_type, const float* __restrict__ wvec,
     size_t vec_per_type, float* __restrict__ Eatom, float* __restrict__ dEdG, DevErr* __restrict__ err, int tile0)
@@ -325,8 +328,10 @@ __global__ void __launch_bounds__(PARK_THREADS, 2) mlp_tc_park_kernel(
     constexpr int A0_B = M * ND * 2;
     constexpr int H_B = M * W * 2;
     constexpr int WB_B = W * W * 2 > W * ND * 2 ? W * W * 2 : W * ND * 2;
+    constexpr int PARK_THREADS = park_threads<W, L>();
+    constexpr int PARK_NH = PARK_THREADS / 128;   // column groups per row
     constexpr int TACC = W < 64 ? 64 : W;       // accumulator columns
-    constexpr int TALLOC = 256;                  // per CTA: two CTAs share the SM's 512 columns
+    constexpr int TALLOC = PARK_THREADS == 512 ? 256 : 128;   // per CTA: the SM's 512 columns over 2 or 4 CTAs
     static_assert(park_cols<W, L>() <= TALLOC, "parked activations exceed tensor memory");
     static_assert((W / PARK_NH) % 16 == 0 && (ND / PARK_NH) % 16 == 0, "column groups of whole 16-column chunks");
     constexpr int NPH = 2 * L;
@@ -939,7 +944,7 @@ template <int W, int L>
 static size_t park_smem()
 {
     const size_t WB_B = (size_t)W * (W > ND ? W : ND) * 2;
-    return (size_t)128 * ND * 2 + (size_t)128 * W * 2 + WB_B + 64 + (size_t)PARK_NH * 128 * 4 +
+    return (size_t)128 * ND * 2 + (size_t)128 * W * 2 + WB_B + 64 + (size_t)(park_threads<W, L>() / 128) * 128 * 4 +
            (size_t)(L * W + W + 2 * ND) * 4 + 1024;
 }
 
@@ -964,7 +969,7 @@ static bool run_tc_park(const Dev& d, int t0, int nt, cudaStream_t st, bool urge
             at[0].val.priority = greatest;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(nt);
-            cfg.blockDim = dim3(PARK_THREADS);
+            cfg.blockDim = dim3(park_threads<W, L>());
             cfg.dynamicSmemBytes = sm;
             cfg.stream = st;
             cfg.attrs = at;
@@ -975,7 +980,7 @@ static bool run_tc_park(const Dev& d, int t0, int nt, cudaStream_t st, bool urge
                                t0);
             return true;
         }
-        mlp_tc_park_kernel<W, L><<<nt, PARK_THREADS, sm, st>>>(
+        mlp_tc_park_kernel<W, L><<<nt, park_threads<W, L>(), sm, st>>>(
             (const float*)d.G, d.perm, d.tile_type, (const unsigned char*)d.wtc, d.wtc_bytes_per_type, d.wtc_vec,
             d.wtc_vec_per_type, (float*)d.Eatom, (float*)d.dEdG, d.err, t0);
         return true;
