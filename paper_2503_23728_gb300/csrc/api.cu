@@ -111,7 +111,7 @@ struct Offsets {
     size_t reps, bsys, ba_sys, mass, minv, atype, x0, cmat, cmatf, modes, rp_blocks, x, f, nbr, nnb, cell_start, cell_cnt,
         cell_atoms, cell_bs, G, dEdG, Eatom, V, W, q, p,
         fnm, Q, qpart, rep_blk0, step_cur, wbuf, vbuf, mom, md_hills, md_nhill, md_cv, md_vb, md_dvds, md_cvpart,
-        md_virpart, md_grad, cand, ncand, xref, rebuild, step, err, est, perm, tile_type, wts, wtc, wtc_vec, gfn_w,
+        md_virpart, md_grad, cand, ncand, xref, rebuild, ba_info, step, err, est, perm, tile_type, wts, wtc, wtc_vec, gfn_w,
         gfn_n, gfn_m, gfn_e, gfn_wtc, total;
 };
 
@@ -445,6 +445,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.reps = c.take(sizeof(Rep) * b.R);
     o.bsys = c.take(sizeof(BeadSys) * b.S);
     o.ba_sys = c.take(sizeof(int) * b.B);
+    o.ba_info = c.take(sizeof(int4) * b.B);
     o.mass = c.take(sizeof(double) * b.NA);
     o.minv = c.take(sizeof(double2) * b.NA);
     o.atype = c.take(sizeof(int) * b.NA);
@@ -798,6 +799,7 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.reps = (Rep*)(w + o.reps);
     d.bsys = (BeadSys*)(w + o.bsys);
     d.ba_sys = (int*)(w + o.ba_sys);
+    d.ba_info = (int4*)(w + o.ba_info);
     d.mass = (double*)(w + o.mass);
     d.minv = (double2*)(w + o.minv);
     d.atype = (int*)(w + o.atype);
@@ -914,6 +916,14 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     rc = upload(c, d.reps, b.reps);
     if (!rc) rc = upload(c, d.bsys, b.bsys);
     if (!rc) rc = upload(c, d.ba_sys, b.ba_sys);
+    if (!rc) {
+        std::vector<int4> bi(b.B);
+        for (int i = 0; i < b.B; ++i) {
+            const BeadSys& sy = b.bsys[b.ba_sys[i]];
+            bi[i] = make_int4(b.ba_sys[i], sy.ba0, sy.N, sy.rep);
+        }
+        rc = upload(c, d.ba_info, bi);
+    }
     if (!rc) rc = upload(c, d.mass, b.mass);
     if (!rc) {
         std::vector<double2> mi(b.NA);

@@ -22,6 +22,7 @@ struct Dev {
     Rep* reps = nullptr;
     BeadSys* bsys = nullptr;
     int* ba_sys = nullptr;             // [B] bead-system of each bead-atom
+    int4* ba_info = nullptr;           // [B] (bead-system, its first bead-atom, its atoms, replica)
     double* mass = nullptr;            // [NA]
     double2* minv = nullptr;           // [NA] (1 / m, sqrt(m k_B T_P) of the atom's replica)
     int* atype = nullptr;              // [NA] element type index

@@ -293,7 +293,8 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
                                                   int* __restrict__ nbr, int* __restrict__ nnb,
                                                   DevErr* __restrict__ err, int* __restrict__ cand,
                                                   int* __restrict__ ncand, float4* __restrict__ xref,
-                                                  const int* __restrict__ rebuild, int maxcand, int b0)
+                                                  const int* __restrict__ rebuild, int maxcand, int b0,
+                                                  const int4* __restrict__ ba_info)
 {
     __shared__ int lst[8][PIMD_SORT_CAP];
     __shared__ unsigned bmap[8][NBR_BM_WORDS];
@@ -301,16 +302,33 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
     const int b = b0 + blockIdx.x * (blockDim.x >> 5) + wib;   // bead-atoms b0 .. B-1
     const unsigned lane = lane_id();
     if (b >= B) return;
-    const int bs = ba_sys[b];
-    const BeadSys sy = bsys[bs];
+    // the bead-atom's record in one load (bead-system, first bead-atom,
+    // atoms, replica) and its candidate count alongside, so that the
+    // replica record and the rebuild flag form the second round of loads
+    int bs;
+    BeadSys sy;
+    int nc0 = 0;
+    if (ba_info) {
+        const int4 bi = ba_info[b];
+        if (maxcand > 0) nc0 = ncand[b];
+        bs = bi.x;
+        sy.ba0 = bi.y;
+        sy.N = bi.z;
+        sy.rep = bi.w;
+    } else {
+        bs = ba_sys[b];
+        sy = bsys[bs];
+        if (maxcand > 0) nc0 = ncand[b];
+    }
     const Rep& rp = reps[sy.rep];
+    if (ba_info) sy.bead = bs - rp.bs0;
     const int il = b - sy.ba0;
     const float3 xi = pos_f32(x[b]);
     int* out = nbr + (size_t)b * maxnb;
     int cnt;
     if (rp.skin > 0.0f && maxcand > 0) {
         int* cl = cand + (size_t)b * maxcand;
-        int nc;
+        int nc = nc0;
         if (rebuild[bs]) {
             nc = scan_list(x, sy, rp, il, xi, cell_start, cell_cnt, cell_atoms, rp.rcs2, cl, maxcand, lst[wib], bmap[wib], lane);
             if (lane == 0) {
@@ -318,8 +336,6 @@ __global__ void __launch_bounds__(256) nbr_kernel(const V4* __restrict__ x, cons
                 xref[b] = make_float4(xi.x, xi.y, xi.z, 0.0f);
             }
             __syncwarp();   // the candidates written by all lanes are read by all lanes below
-        } else {
-            nc = ncand[b];
         }
         if (nc <= maxcand) {
             // groups of four chunks of 32: the group's candidate indices
@@ -427,11 +443,11 @@ void launch_neighbour_lists(const Dev& d, int b0, int b1, cudaStream_t st)
     if (d.precision == 0)
         nbr_kernel<Dbl4><<<blocks, threads, 0, st>>>((const Dbl4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
                                                      d.cell_cnt, d.cell_atoms, rc2, d.maxnb, b1, d.nbr, d.nnb, d.err,
-                                                     d.cand, d.ncand, d.xref, d.rebuild, d.maxcand, b0);
+                                                     d.cand, d.ncand, d.xref, d.rebuild, d.maxcand, b0, d.ba_info);
     else
         nbr_kernel<float4><<<blocks, threads, 0, st>>>((const float4*)d.x, d.ba_sys, d.bsys, d.reps, d.cell_start,
                                                        d.cell_cnt, d.cell_atoms, rc2, d.maxnb, b1, d.nbr, d.nnb,
-                                                       d.err, d.cand, d.ncand, d.xref, d.rebuild, d.maxcand, b0);
+                                                       d.err, d.cand, d.ncand, d.xref, d.rebuild, d.maxcand, b0, d.ba_info);
 }
 
 void launch_neighbours(const Dev& d, cudaStream_t st)
