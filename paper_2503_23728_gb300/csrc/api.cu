@@ -472,7 +472,7 @@ Offsets layout(const pimd_config* cfg, const Build& b)
     o.p = c.take(sizeof(double) * 3 * (size_t)b.B);
     o.fnm = c.take(sizeof(double) * 3 * (size_t)b.B);
     o.Q = c.take(sizeof(double) * b.R);
-    o.qpart = c.take(sizeof(double) * 2 * b.rp_blocks.size());
+    o.qpart = c.take(sizeof(double) * 3 * b.rp_blocks.size());
     o.rep_blk0 = c.take(sizeof(int) * b.rep_blk0.size());
     o.step_cur = c.take(sizeof(unsigned long long));
     o.wbuf = c.take(rs * 9 * (size_t)b.B);
@@ -597,7 +597,7 @@ bool splits_forces(const pimd_ctx* c)
 // branch: the step may run the force evaluation as two overlapping branches
 // (captured graphs without stage markers)
 void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit = false, bool zeroed = false,
-                 bool branch = false)
+                 bool branch = false, int step_offset = 0)
 {
     Dev& d = c->d;
     const size_t v4 = d.precision == PIMD_FP64 ? sizeof(Dbl4) : sizeof(float4);
@@ -654,7 +654,7 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
     }
     mark(c, PIMD_STAGE_ENERGY, st, timed);
     if (!summed) launch_energy_reduce(d, st);
-    if (d.metad.cv) launch_metad(d, deposit, st);   // bias on every bead (and hills on deposition steps)
+    if (d.metad.cv) launch_metad(d, deposit, st, step_offset);   // bias on every bead (and hills on deposition steps)
 }
 void eval_forces(pimd_ctx* c) { eval_forces(c, c->st); }
 
@@ -665,8 +665,26 @@ void one_step(pimd_ctx* c, cudaStream_t st, bool timed)
     eval_forces(c, st, timed, true, true, !timed && c->overlap);
     mark(c, PIMD_STAGE_RING_FINISH, st, timed);
     launch_rp_finish(c->d, true, st);   // also advances the step counter
-    if (c->d.deterministic) launch_heat_sum(c->d, st);
+    if (c->d.deterministic) launch_heat_sum(c->d, 0, st);
     mark(c, PIMD_N_STAGES, st, timed);
+}
+
+// n >= 2 steps in one launch: one ring start, then per step the force
+// evaluation and, between steps, the fused ring finish + next ring start;
+// the last step ends with a plain ring finish, so the state at the end of
+// the launch is the state after a ring finish, as with single steps
+void fused_steps(pimd_ctx* c, cudaStream_t st, int n)
+{
+    Dev& d = c->d;
+    launch_rp_start(d, st, 0);
+    for (int j = 0; j < n; ++j) {
+        eval_forces(c, st, false, true, true, c->overlap, j);
+        if (j + 1 < n)
+            launch_rp_finish_start(d, j, (j + 1) & 1, st);
+        else
+            launch_rp_finish(d, true, st, j);
+        if (d.deterministic) launch_heat_sum(d, j & 1, st);
+    }
 }
 
 int refresh_forces(pimd_ctx* c)
@@ -698,7 +716,10 @@ int capture(pimd_ctx* c, int nsteps, bool marked, cudaGraphExec_t* out)
     }
     e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamBeginCapture");
-    for (int s = 0; s < nsteps; ++s) one_step(c, c->cap, marked && s == nsteps - 1);
+    if (nsteps >= 2 && !marked)
+        fused_steps(c, c->cap, nsteps);
+    else
+        for (int s = 0; s < nsteps; ++s) one_step(c, c->cap, marked && s == nsteps - 1);
     e = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(out, g, 0);
@@ -1302,7 +1323,7 @@ int pimd_ring_finish(pimd_ctx* c, const double* f_dev)
     if (c->forces_valid) return fail(c, PIMD_ERR_STATE, "pimd_ring_finish without a pimd_ring_start before it");
     launch_pack_forces(c->d, f_dev, c->st);
     launch_rp_finish(c->d, true, c->st);
-    if (c->d.deterministic) launch_heat_sum(c->d, c->st);
+    if (c->d.deterministic) launch_heat_sum(c->d, 0, c->st);
     c->forces_valid = true;
     c->step_host += 1;
     return cuda_check(c, cudaGetLastError(), "ring finish");

@@ -59,7 +59,7 @@ struct Dev {
     double* p = nullptr;               // [3B] normal-mode momenta
     double* fnm = nullptr;             // [3B] normal-mode forces
     double* Q = nullptr;               // [R] thermostat heat
-    double* qpart = nullptr;           // [2][n_rp_blocks] thermostat heat per block and half step
+    double* qpart = nullptr;           // [3][n_rp_blocks] thermostat heat per block: start half (two buffers), finish half
     int* rep_blk0 = nullptr;           // [R + 1] first ring-polymer block of each replica
     unsigned long long* step_cur = nullptr;   // the step being taken (copied by the ring start for the ring finish)
     void* wbuf = nullptr;              // Real[B][9] per bead-atom virial
@@ -167,7 +167,7 @@ void prepare_tc_weights(const Dev& d, int type, const double* blob, void* host_i
 // metadynamics
 constexpr int MD_SLICES = 8;           // XRD CV: row slices per atom tile (gradient buffers)
 int metad_tiles(int max_N);            // partial sums per bead-system (tiles x slices)
-void launch_metad(const Dev& d, bool deposit, cudaStream_t st);
+void launch_metad(const Dev& d, bool deposit, cudaStream_t st, int step_offset = 0);
 
 // structural analysis
 size_t rdf_smem_bytes(int n_types, int n_bins);
@@ -199,9 +199,12 @@ void set_thread_error(const std::string& msg);
 // ring polymer
 void launch_rp_init(const Dev& d, cudaStream_t st);
 void launch_beads(const Dev& d, cudaStream_t st);
-void launch_rp_start(const Dev& d, cudaStream_t st);
-void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st);
-void launch_heat_sum(const Dev& d, cudaStream_t st);
+// lo: which of the two start-half heat buffers (0 / 1) a ring start writes and
+// an ordered heat sum reads; offset: steps since the call's first ring start
+void launch_rp_start(const Dev& d, cudaStream_t st, int lo = 0);
+void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st, int offset = 0);
+void launch_rp_finish_start(const Dev& d, int offset, int lo, cudaStream_t st);
+void launch_heat_sum(const Dev& d, int lo, cudaStream_t st);
 void launch_estimators(const Dev& d, cudaStream_t st);
 
 }  // namespace pimd

@@ -178,9 +178,11 @@ __global__ void bias_kernel(const Rep* __restrict__ reps, const BeadSys* __restr
                             const double* __restrict__ cvpart, const double* __restrict__ virpart, int ntile,
                             double2* __restrict__ hills, int* __restrict__ nhill, double* __restrict__ cv,
                             double* __restrict__ vb, double* __restrict__ dvds, double* __restrict__ V,
-                            double* __restrict__ W, const unsigned long long* __restrict__ stepp, int deposit,
-                            DevErr* __restrict__ err)
+                            double* __restrict__ W, const unsigned long long* __restrict__ stepp, int offset,
+                            int deposit, DevErr* __restrict__ err)
 {
+    // stepp: the step counter copy made by the ring start of the current
+    // launch; offset: the steps of a multi-step launch since that start
     const int r = blockIdx.x;
     const Rep& rp = reps[r];
     const int k = threadIdx.x;
@@ -210,7 +212,7 @@ __global__ void bias_kernel(const Rep* __restrict__ reps, const BeadSys* __restr
             W[(size_t)bs * 9 + q] -= dv * w;
         }
     }
-    if (!deposit || ((*stepp + 1ull) % (unsigned long long)mp.stride) != 0ull) return;
+    if (!deposit || ((*stepp + (unsigned long long)offset + 1ull) % (unsigned long long)mp.stride) != 0ull) return;
     __syncthreads();   // every bead has read the hills before any is added
     if (n + rp.P > mp.max_hills) {
         if (k == 0) atomicOr(&err->flags, ERR_METAD_FULL);
@@ -247,7 +249,7 @@ __global__ void bias_force_kernel(const int* __restrict__ ba_sys, const Vec4<Rea
 
 int metad_tiles(int max_N) { return (max_N + 127) / 128 * MD_SLICES; }
 
-void launch_metad(const Dev& d, bool deposit, cudaStream_t st)
+void launch_metad(const Dev& d, bool deposit, cudaStream_t st, int step_offset)
 {
     const MetadParams& mp = d.metad;
     const int ntile = metad_tiles(d.max_N);
@@ -273,8 +275,8 @@ void launch_metad(const Dev& d, bool deposit, cudaStream_t st)
                                                        (float4*)d.md_grad, d.md_cvpart, d.md_virpart, ntile, d.B);
     }
     bias_kernel<<<d.R, d.max_P, 0, st>>>(d.reps, d.bsys, mp, d.md_cvpart, d.md_virpart, ntile, d.md_hills,
-                                         d.md_nhill, d.md_cv, d.md_vb, d.md_dvds, d.V, d.W, d.step,
-                                         deposit ? 1 : 0, d.err);
+                                         d.md_nhill, d.md_cv, d.md_vb, d.md_dvds, d.V, d.W, d.step_cur,
+                                         step_offset, deposit ? 1 : 0, d.err);
     if (d.precision == 0)
         bias_force_kernel<double><<<(d.B + 255) / 256, 256, 0, st>>>(d.ba_sys, (const Dbl4*)d.md_grad, d.md_dvds,
                                                                      (Dbl4*)d.f, d.B, nslice);

@@ -89,7 +89,7 @@ __device__ __forceinline__ double to_bead(const double* __restrict__ C, const fl
         return fma(C[0], sq[0], (double)a);
     }
     double acc = 0.0;
-    for (int k = 0; k < P; ++k) acc += C[k] * sq[k * stride];
+    for (int k = 0; k < P; ++k) acc = fma(C[k], sq[k * stride], acc);
     return acc;
 }
 
@@ -211,11 +211,13 @@ __global__ void beads_kernel(const int2* __restrict__ blocks, const Rep* __restr
 __device__ __forceinline__ void free_rp(int k, const Mode& md, double m, double im, double hA, double& pv,
                                         double& qv)
 {
+    // explicit roundings, so that every kernel that takes this step (ring
+    // start, fused ring finish + start) produces the same bits
     if (k == 0) {
-        qv += pv * hA * im;
+        qv = fma(__dmul_rn(pv, hA), im, qv);
     } else {
-        const double pn = md.cw * pv - m * md.wsw * qv;
-        qv = md.sw_w * im * pv + md.cw * qv;
+        const double pn = fma(md.cw, pv, -__dmul_rn(__dmul_rn(m, md.wsw), qv));
+        qv = fma(__dmul_rn(md.sw_w, im), pv, __dmul_rn(md.cw, qv));
         pv = pn;
     }
 }
@@ -235,16 +237,16 @@ __device__ __forceinline__ HeatT<Real> pile_o(const Rep& rp, const Mode& md, dou
 {
     if constexpr (std::is_same<Real, float>::value) {
         const float xi = normal_dev_f(rp.seed, local, step, rep, stream);
-        const double sig = smkT * md.c2;
-        const double pn = md.c1 * pv + sig * (double)xi;
+        const double sig = __dmul_rn(smkT, md.c2);
+        const double pn = fma(md.c1, pv, __dmul_rn(sig, (double)xi));
         const float pvf = (float)pv, a = (float)sig * xi;
         const float dK = 0.5f * (float)im * (fmaf(md.c1m1, pvf, a) * fmaf(md.c1p1, pvf, a));
         pv = pn;
         return dK;
     } else {
         const double xi = normal_dev(rp.seed, local, step, rep, stream);
-        const double pn = md.c1 * pv + smkT * md.c2 * xi;
-        const double dK = (pn * pn - pv * pv) * 0.5 * im;
+        const double pn = fma(md.c1, pv, __dmul_rn(__dmul_rn(smkT, md.c2), xi));
+        const double dK = __dmul_rn(__dmul_rn(fma(pn, pn, -__dmul_rn(pv, pv)), 0.5), im);
         pv = pn;
         return dK;
     }
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
                                 const double* __restrict__ mass, const double2* __restrict__ minv,
                                 const unsigned long long* __restrict__ stepp, double hdt, double kick, int unit_mfac, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
                                 const double* __restrict__ fnm, Vec4<Real>* __restrict__ x,
-                                double* __restrict__ qpart, Vec4<Real>* __restrict__ f, double* __restrict__ W,
+                                double* __restrict__ qlo, Vec4<Real>* __restrict__ f, double* __restrict__ W,
                                 double* __restrict__ V, double* __restrict__ Q, int ordered_heat,
                                 unsigned long long* __restrict__ stepc)
 {
@@ -281,13 +283,13 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
         double pv = p[g], qv = q[g];
         const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + t.i) * 3 + t.dd);
         if (baoab) {
-            pv += kick * fnm[g];
+            pv = fma(kick, fnm[g], pv);   // B: one rounding, as in the fused boundary kernel
             free_rp(k, md, m, im, hdt, pv, qv);
             if (thermostat) dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
             free_rp(k, md, m, im, hdt, pv, qv);
         } else {
             if (thermostat) dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 2u, pv);
-            pv += kick * fnm[g];
+            pv = fma(kick, fnm[g], pv);   // B: one rounding, as in the fused boundary kernel
             free_rp(k, md, m, im, 2.0 * hdt, pv, qv);
         }
         p[g] = pv;
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         s = thermostat ? s * MVV2E : 0.0;
-        qpart[blockIdx.x] = s;
+        qlo[blockIdx.x] = s;
         if (!ordered_heat && thermostat) atomicAdd(&Q[t.r], s);
         if (blockIdx.x == 0) *stepc = *stepp;   // the step the ring finish will read
     }
@@ -329,16 +331,17 @@ __global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 5 : 4)
 
 // f_nm = C^T f; if do_step: B(dt/2), then O(dt/2) for OBABO, and the step
 // ends here: block 0 advances the step counter that the next ring start
-// reads (this kernel reads the copy that the ring start made), and each
-// block adds its thermostat heat to Q (FP64 atomics) unless the heat is
-// summed in a fixed order afterwards (deterministic mode).
+// reads (this kernel reads the copy that the ring start made, plus offset:
+// the steps of a multi-step launch since that ring start), and each block
+// adds its thermostat heat to Q (FP64 atomics) unless the heat is summed in
+// a fixed order afterwards (deterministic mode).
 template <typename Real>
 __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __restrict__ reps,
                                  const double* __restrict__ cmat, const float* __restrict__ cmatf,
                                  const Mode* __restrict__ modes,
                                  const double* __restrict__ mass, const double2* __restrict__ minv,
-                                 const unsigned long long* stepp, double kick, int unit_mfac, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
-                                 double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ qpart,
+                                 const unsigned long long* stepp, int offset, double kick, int unit_mfac, int thermostat, int do_step, const Vec4<Real>* __restrict__ f,
+                                 double* __restrict__ p, double* __restrict__ fnm, double* __restrict__ qhi,
                                  DevErr* __restrict__ err, double* __restrict__ Q, int ordered_heat,
                                  unsigned long long* stepw)
 {
@@ -369,7 +372,7 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
             for (int j = 0; j < t.P; ++j) a = fmaf(Cfs[j * ldc + k], sff[j * t.T + t.le], a);
             fn = (double)a;
         } else {
-            for (int j = 0; j < t.P; ++j) fn += cmat[rp.cmat + (size_t)j * t.P + k] * sf[j * t.T + t.le];
+            for (int j = 0; j < t.P; ++j) fn = fma(cmat[rp.cmat + (size_t)j * t.P + k], sf[j * t.T + t.le], fn);
         }
         const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
         fnm[g] = fn;
@@ -377,11 +380,12 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         if (do_step) {
             const Mode md = modes[rp.mode0 + k];
             const double2 mi = minv[rp.atom0 + t.i];
-            double pv = p[g] + kick * fn;
+            double pv = fma(kick, fn, p[g]);
             if (thermostat) {
                 const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + t.i) * 3 + t.dd);
                 const double smkT = unit_mfac ? mi.y : mi.y * md.smf, im = unit_mfac ? mi.x : mi.x * md.imf;
-                dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp), (unsigned)t.r, 3u, pv);
+                dK = pile_o<Real>(rp, md, smkT, im, local, (unsigned)(*stepp + (unsigned long long)offset), (unsigned)t.r,
+                                  3u, pv);
             }
             p[g] = pv;
         }
@@ -394,21 +398,21 @@ __global__ void rp_finish_kernel(const int2* __restrict__ blocks, const Rep* __r
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         s = thermostat ? s * MVV2E : 0.0;
-        qpart[gridDim.x + blockIdx.x] = s;
+        qhi[blockIdx.x] = s;
         if (!ordered_heat && thermostat) atomicAdd(&Q[t.r], s);
-        if (blockIdx.x == 0) *stepw = *stepp + 1ull;   // no block of this kernel reads stepw
+        if (blockIdx.x == 0) *stepw = *stepp + (unsigned long long)offset + 1ull;   // no block of this kernel reads stepw
     }
 }
 
 // deterministic mode: thermostat heat of both O halves added per replica in a
 // fixed order (one block per replica) after the ring finish
-__global__ void heat_sum_kernel(double* __restrict__ Q, const double* __restrict__ qpart,
-                                const int* __restrict__ rep_blk0, int nblk)
+__global__ void heat_sum_kernel(double* __restrict__ Q, const double* __restrict__ qlo,
+                                const double* __restrict__ qhi, const int* __restrict__ rep_blk0)
 {
     __shared__ double red[8];
     const int r = blockIdx.x;
     double s = 0.0;
-    for (int b = rep_blk0[r] + threadIdx.x; b < rep_blk0[r + 1]; b += blockDim.x) s += qpart[b] + qpart[nblk + b];
+    for (int b = rep_blk0[r] + threadIdx.x; b < rep_blk0[r + 1]; b += blockDim.x) s += qlo[b] + qhi[b];
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -419,9 +423,139 @@ __global__ void heat_sum_kernel(double* __restrict__ Q, const double* __restrict
     }
 }
 
-void launch_heat_sum(const Dev& d, cudaStream_t st)
+// Inside a multi-step launch, the ring finish of step j and the ring start
+// of step j + 1 (nothing runs between them) as one kernel: every coordinate
+// does the finish's f_nm = C^T f, B(dt/2) and (OBABO) O(dt/2), then the
+// start's O / B / A in the same registers, with the same operations in the
+// same order as the two kernels, so the state is bit-identical. Noise
+// counters: the call's first ring start copied the step counter to stepc;
+// this boundary ends step stepc + offset. The heat of the finish half goes
+// to qhi, that of the start half to qlo (the other lo half than the one the
+// step being finished used, for the ordered sums).
+template <typename Real>
+__global__ void __launch_bounds__(256, 4) rp_finish_start_kernel(
+    const int2* __restrict__ blocks, const Rep* __restrict__ reps, const double* __restrict__ cmat,
+    const float* __restrict__ cmatf, const Mode* __restrict__ modes, const double* __restrict__ mass,
+    const double2* __restrict__ minv, const unsigned long long* __restrict__ stepc, int offset, double hdt,
+    double kick, int unit_mfac, int thermostat, int baoab, double* __restrict__ q, double* __restrict__ p,
+    double* __restrict__ fnm, Vec4<Real>* __restrict__ x, Vec4<Real>* __restrict__ f, double* __restrict__ W,
+    double* __restrict__ V, double* __restrict__ qhi, double* __restrict__ qlo, DevErr* __restrict__ err,
+    double* __restrict__ Q, int ordered_heat)
 {
-    heat_sum_kernel<<<d.R, 256, 0, st>>>(d.Q, d.qpart, d.rep_blk0, d.n_rp_blocks);
+    extern __shared__ double sbuf[];   // forces, then positions: [T P] doubles, [T P] floats, staged C
+    double* sv = sbuf;
+    float* svf = reinterpret_cast<float*>(sbuf + blockDim.x);
+    __shared__ double red[2][32];
+    const RpThread t = rp_thread(blocks, reps);
+    const Rep& rp = reps[t.r];
+    int ldc = t.P;
+    const float* Cfs = cmatf + rp.cmat;
+    if constexpr (std::is_same<Real, float>::value) Cfs = stage_cmatf(Cfs, t.P, svf + blockDim.x, ldc);
+    if (t.active) {
+        const Vec4<Real> fv = f[rp.ba0 + (size_t)t.kk * t.N + t.i];
+        const Real fc = t.dd == 0 ? fv.x : (t.dd == 1 ? fv.y : fv.z);
+        if constexpr (std::is_same<Real, float>::value)
+            svf[t.kk * t.T + t.le] = fc;
+        else
+            sv[t.kk * t.T + t.le] = (double)fc;
+    }
+    __syncthreads();
+    HeatT<Real> dK1 = 0, dK2 = 0;
+    double qv = 0.0;
+    const unsigned long long s0 = *stepc + (unsigned long long)offset;
+    if (t.active) {
+        const int k = t.kk;
+        double fn = 0.0;
+        if constexpr (std::is_same<Real, float>::value) {
+            float a = 0.0f;
+            for (int j = 0; j < t.P; ++j) a = fmaf(Cfs[j * ldc + k], svf[j * t.T + t.le], a);
+            fn = (double)a;
+        } else {
+            for (int j = 0; j < t.P; ++j) fn = fma(cmat[rp.cmat + (size_t)j * t.P + k], sv[j * t.T + t.le], fn);
+        }
+        const size_t g = 3 * ((size_t)rp.ba0 + (size_t)k * t.N + t.i) + t.dd;
+        fnm[g] = fn;
+        if (!isfinite(fn)) atomicOr(&err->flags, ERR_NONFINITE);
+        const Mode md = modes[rp.mode0 + k];
+        const double2 mi = minv[rp.atom0 + t.i];
+        const double ma = mass[rp.atom0 + t.i];
+        const double m = unit_mfac ? ma : ma * md.mfac, im = unit_mfac ? mi.x : mi.x * md.imf,
+                     smkT = unit_mfac ? mi.y : mi.y * md.smf;
+        const unsigned local = (unsigned)((k * rp.noise_N + rp.noise_atom0 + t.i) * 3 + t.dd);
+        // the finish of step s0: B(dt/2), then O(dt/2) for OBABO
+        double pv = fma(kick, fn, p[g]);
+        if (thermostat && !baoab) dK1 = pile_o<Real>(rp, md, smkT, im, local, (unsigned)s0, (unsigned)t.r, 3u, pv);
+        // the start of step s0 + 1
+        qv = q[g];
+        const unsigned s1 = (unsigned)(s0 + 1ull);
+        if (baoab) {
+            pv = fma(kick, fn, pv);
+            free_rp(k, md, m, im, hdt, pv, qv);
+            if (thermostat) dK2 = pile_o<Real>(rp, md, smkT, im, local, s1, (unsigned)t.r, 2u, pv);
+            free_rp(k, md, m, im, hdt, pv, qv);
+        } else {
+            if (thermostat) dK2 = pile_o<Real>(rp, md, smkT, im, local, s1, (unsigned)t.r, 2u, pv);
+            pv = fma(kick, fn, pv);
+            free_rp(k, md, m, im, 2.0 * hdt, pv, qv);
+        }
+        p[g] = pv;
+        q[g] = qv;
+    }
+    dK1 = warp_sum(dK1);
+    dK2 = warp_sum(dK2);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = (double)dK1;
+        red[1][threadIdx.x >> 5] = (double)dK2;
+    }
+    __syncthreads();   // the forces in shared memory are read; the positions may overwrite them
+    if (t.active) {
+        sv[t.kk * t.T + t.le] = qv;
+        svf[t.kk * t.T + t.le] = (float)qv;
+    }
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        a = (thermostat && !baoab) ? a * MVV2E : 0.0;
+        b = thermostat ? b * MVV2E : 0.0;
+        qhi[blockIdx.x] = a;
+        qlo[blockIdx.x] = b;
+        if (!ordered_heat && thermostat) {
+            if (!baoab) atomicAdd(&Q[t.r], a);
+            atomicAdd(&Q[t.r], b);
+        }
+    }
+    __syncthreads();
+    if (!t.active) return;
+    const int j = t.kk;
+    const double acc = to_bead<Real>(cmat + rp.cmat + (size_t)j * t.P, cmatf + rp.cmat + (size_t)j * t.P,
+                                     sv + t.le, svf + t.le, t.P, t.T);
+    comp<Real>(x[rp.ba0 + (size_t)j * t.N + t.i], t.dd) = (Real)acc;
+    if (t.dd == 0) {
+        Vec4<Real> z;
+        z.x = z.y = z.z = z.w = (Real)0;
+        f[rp.ba0 + (size_t)j * t.N + t.i] = z;
+        if (t.i == 0) {
+            const int bs = rp.bs0 + j;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) W[(size_t)bs * 9 + a] = 0.0;
+            V[bs] = 0.0;
+        }
+    }
+}
+
+// heat partials: [lo 0][hi][lo 1], each n_rp_blocks. A ring start writes a
+// lo half (the start of step j of a multi-step launch writes lo (j & 1)), the
+// ring finish the hi half; the ordered sum after a finish adds the lo half of
+// the same step.
+static double* heat_lo(const Dev& d, int lo) { return d.qpart + (size_t)(lo ? 2 : 0) * d.n_rp_blocks; }
+static double* heat_hi(const Dev& d) { return d.qpart + (size_t)d.n_rp_blocks; }
+
+void launch_heat_sum(const Dev& d, int lo, cudaStream_t st)
+{
+    heat_sum_kernel<<<d.R, 256, 0, st>>>(d.Q, heat_lo(d, lo), heat_hi(d), d.rep_blk0);
 }
 
 static size_t rp_smem(const Dev& d) { return (size_t)d.rp_threads * (sizeof(double) + sizeof(float)); }
@@ -444,28 +578,42 @@ void launch_beads(const Dev& d, cudaStream_t st)
                                                                                (float4*)d.x);
 }
 
-void launch_rp_start(const Dev& d, cudaStream_t st)
+void launch_rp_start(const Dev& d, cudaStream_t st, int lo)
 {
     if (d.precision == 0)
         rp_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, 0.5 * d.dt, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat, d.splitting, d.q, d.p, d.fnm,
-            (Dbl4*)d.x, d.qpart, (Dbl4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
+            (Dbl4*)d.x, heat_lo(d, lo), (Dbl4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
     else
         rp_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_smem(d), st>>>(
             d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step, 0.5 * d.dt, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat, d.splitting, d.q, d.p, d.fnm,
-            (float4*)d.x, d.qpart, (float4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
+            (float4*)d.x, heat_lo(d, lo), (float4*)d.f, d.W, d.V, d.Q, d.deterministic, d.step_cur);
 }
 
-void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st)
+void launch_rp_finish(const Dev& d, bool do_step, cudaStream_t st, int offset)
 {
     if (d.precision == 0)
         rp_finish_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat && !d.splitting,
-            do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, offset, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat && !d.splitting,
+            do_step ? 1 : 0, (const Dbl4*)d.f, d.p, d.fnm, heat_hi(d), d.err, d.Q, d.deterministic, d.step);
     else
         rp_finish_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
-            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat && !d.splitting,
-            do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, d.qpart, d.err, d.Q, d.deterministic, d.step);
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, offset, 0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat && !d.splitting,
+            do_step ? 1 : 0, (const float4*)d.f, d.p, d.fnm, heat_hi(d), d.err, d.Q, d.deterministic, d.step);
+}
+
+void launch_rp_finish_start(const Dev& d, int offset, int lo, cudaStream_t st)
+{
+    if (d.precision == 0)
+        rp_finish_start_kernel<double><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, offset, 0.5 * d.dt,
+            0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat, d.splitting, d.q, d.p, d.fnm, (Dbl4*)d.x, (Dbl4*)d.f,
+            d.W, d.V, heat_hi(d), heat_lo(d, lo), d.err, d.Q, d.deterministic);
+    else
+        rp_finish_start_kernel<float><<<d.n_rp_blocks, d.rp_threads, rp_step_smem(d), st>>>(
+            d.rp_blocks, d.reps, d.cmat, d.cmatf, d.modes, d.mass, d.minv, d.step_cur, offset, 0.5 * d.dt,
+            0.5 * d.dt * INV_MVV2E, d.unit_mfac, d.thermostat, d.splitting, d.q, d.p, d.fnm, (float4*)d.x,
+            (float4*)d.f, d.W, d.V, heat_hi(d), heat_lo(d, lo), d.err, d.Q, d.deterministic);
 }
 
 

@@ -484,3 +484,38 @@ def test_small_bead_neighbours_bit_exact(fad_model, precision):
                 assert np.array_equal(nbr[b, :nnb[b]], want[i]), (rep.name, k, i)
                 b += 1
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,splitting", [("fp32", "obabo"), ("fp32", "baoab"), ("fp64", "obabo"),
+                                                 ("bf16_tc", "obabo")])
+def test_multistep_launch_fuses_ring_kernels_bit_identically(water64_model, precision, splitting):
+    """pimd_step(8) runs one graph whose inner step boundaries fuse the ring
+    finish with the next ring start; eight pimd_step(1) calls run the two
+    kernels separately. Deterministic mode: positions, momenta, step counter
+    and thermostat heat are bit-identical."""
+    P = _P()
+    w, r, m = water64_model
+    rep = _with_beads(r, 4)
+
+    def ctx():
+        c = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision=precision, widths=w.widths, deterministic=True,
+                      splitting=splitting)
+        c.set_weights(m)
+        return c
+
+    a, b = ctx(), ctx()
+    a.step(8)
+    for _ in range(8):
+        b.step(1)
+    qa, pa, sa, Qa = a.get_state()
+    qb, pb, sb, Qb = b.get_state()
+    assert sa == sb == 8
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb) and np.array_equal(Qa, Qb)
+    # and both continue identically (the fused graph leaves the state of a ring finish)
+    a.step(1)
+    b.step(1)
+    qa, pa, _, _ = a.get_state()
+    qb, pb, _, _ = b.get_state()
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
+    a.close()
+    b.close()
