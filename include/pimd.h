@@ -282,6 +282,9 @@ int pimd_set_weights(pimd_ctx* ctx, const pimd_model_desc* model);
 /* Advance all replicas by n_steps of OBABO in normal-mode space:
  * O(dt/2) B(dt/2) A(dt) [forces] B(dt/2) O(dt/2) with exact free-ring-polymer
  * A and PILE-L O (Philox counter: index, step, replica, stream 2 / 3).
+ * Runs of 8 steps are one graph launch whose inner step boundaries fuse the
+ * ring finish with the next ring start (the same bits as separate kernels);
+ * the state after the call is the state after the last step's ring finish.
  * Asynchronous on the context stream. Errors: STATE if weights are missing. */
 int pimd_step(pimd_ctx* ctx, int n_steps);
 
@@ -452,7 +455,9 @@ int pimd_get_angular(const pimd_ctx* ctx);
 int pimd_set_adjoint_warps(pimd_ctx* ctx, int warps_per_sm);
 int pimd_get_adjoint_warps(const pimd_ctx* ctx);
 
-/* Number of kernels one step launches (memset nodes not counted).          */
+/* Number of kernels one single-step launch runs (memset nodes not counted).
+ * Inside multi-step launches the ring finish of a step and the ring start of
+ * the next are one kernel, one fewer per inner step boundary.               */
 int pimd_kernels_per_step(const pimd_ctx* ctx);
 
 /* Block until all queued work is done; report device-side errors.          */
