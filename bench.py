@@ -263,6 +263,25 @@ def network_flops(ctx, widths) -> float:
     return 2.0 * macs * ctx.B
 
 
+def multistep_ms(ctx, stream, launches: int = 10) -> float:
+    """Mean step time of 8-step launches (one graph each, whose inner step
+    boundaries fuse the ring finish with the next ring start), back to back
+    without L2 flushes: the regime of a long production run. Reported beside
+    the headline, which times single flushed steps."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    ctx.set_stage_timing(False)   # a marked last step would split the graph
+    ctx.step(8)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(launches):
+        ctx.step(8)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (8 * launches)
+
+
 def e2e_host(a, ctx, stream, barrier):
     """Force evaluation through the C ABI with host buffers: H2D of the bead
     positions from pinned memory, pimd_energy_forces, D2H of forces and
@@ -563,6 +582,8 @@ def main():
     except Exception:
         pass
     e2e_ms, h2d, d2h = e2e_host(a, ctx, stream, barrier)
+    multi = {"ms_per_step": multistep_ms(ctx, stream), "launch": "8-step graphs, 10 back to back",
+             "l2": "not flushed between steps"}
     extras = None
     if not a.no_extras and world == 1:
         extras = analysis_extras(ctx, w, stream)
@@ -617,6 +638,7 @@ def main():
                                "achieved_tflops": fwd_flops / (st_mean["descriptors"] / 1e3) / 1e12,
                                "frac_fp32_peak": fwd_flops / (st_mean["descriptors"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
         "ms_per_step_with_stage_markers": float(np.sum(ms_marked)) / a.steps,
+        "multistep": multi,
         "network_tensor": {"flops_per_launch": net_flops, "ms": st_mean["network"],
                            "achieved_tflops": net_flops / (st_mean["network"] / 1e3) / 1e12,
                            "peak_bf16_tflops_measured": peaks.get("bf16_tflops")},
