@@ -43,6 +43,9 @@ double default_mass(int z)
     }
 }
 
+// overlapping parts of a large BF16 step's force evaluation
+constexpr int OVERLAP_PARTS = 2;
+
 // Everything the host computes before touching the device.
 struct Build {
     std::vector<Rep> reps;
@@ -57,7 +60,7 @@ struct Build {
     std::vector<int> cell_bs;
     int total_cells = 0, max_cells = 0;
     int R = 0, S = 0, B = 0, NA = 0, rows_pad = 0;
-    int split_ba = 0, split_tile = 0;   // halves of the bead-atoms / network tiles (0: one branch)
+    std::vector<int> part_ba, part_tile;   // parts of the bead-atoms / network tiles (boundaries; one part: none)
     size_t blob = 0, wtc_bytes = 0, wtc_vec = 0;
     size_t gfn_params = 0;   // FP32 parameters of the graph-field-network head
     bool periodic_any = false;
@@ -395,17 +398,22 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
     // bead-systems (the two branches of an overlapped step); each half has
     // its own element groups and tiles.
     if (cfg->potential == PIMD_POT_MODEL) {
-        b.split_ba = 0;
-        if (cfg->precision == PIMD_BF16_TC && b.B >= 16384 && b.S >= 2) {
-            int best = 0;
-            for (const BeadSys& sy : b.bsys)
-                if (std::abs(2 * sy.ba0 - b.B) < std::abs(2 * best - b.B)) best = sy.ba0;
-            b.split_ba = best;
+        // parts: whole bead-systems, boundaries nearest to k B / K
+        std::vector<int> cut = {0};
+        if (cfg->precision == PIMD_BF16_TC && b.B >= 16384 && b.S >= OVERLAP_PARTS) {
+            for (int k = 1; k < OVERLAP_PARTS; ++k) {
+                const long long want = (long long)k * b.B / OVERLAP_PARTS;
+                int best = 0;
+                for (const BeadSys& sy : b.bsys)
+                    if (std::llabs(sy.ba0 - want) < std::llabs(best - want)) best = sy.ba0;
+                if (best > cut.back()) cut.push_back(best);
+            }
         }
-        const int halves = b.split_ba > 0 ? 2 : 1;
-        for (int hv = 0; hv < halves; ++hv) {
-            const int lo = hv == 0 ? 0 : b.split_ba, hi = (hv == 0 && halves == 2) ? b.split_ba : b.B;
-            if (hv == 1) b.split_tile = (int)b.tile_type.size();
+        cut.push_back(b.B);
+        const int parts = (int)cut.size() - 1;
+        for (int pt = 0; pt < parts; ++pt) {
+            const int lo = cut[pt], hi = cut[pt + 1];
+            if (parts > 1) b.part_tile.push_back((int)b.tile_type.size());
             std::vector<std::vector<int>> rows(zs.size());
             for (int r = 0; r < n; ++r) {
                 const Rep& rp = b.reps[r];
@@ -422,6 +430,10 @@ int make_build(const pimd_config* cfg, const pimd_replica_desc* reps, int n, Bui
                 for (size_t q = 0; q < padded; ++q) b.perm.push_back(q < v.size() ? v[q] : -1);
                 for (size_t q = 0; q < padded / TILE_ROWS; ++q) b.tile_type.push_back((int)t);
             }
+        }
+        if (parts > 1) {
+            b.part_ba = cut;
+            b.part_tile.push_back((int)b.tile_type.size());
         }
         b.rows_pad = (int)b.perm.size();
         b.blob = blob_elems(cfg->n_hidden, cfg->widths);
@@ -538,8 +550,9 @@ struct pimd_ctx {
     bool stage_timing = true;                      // mark the last step of each pimd_step call
     bool overlap = true;                           // overlapped halves in unmarked step graphs
     cudaStream_t cap = nullptr;
-    cudaStream_t cap2 = nullptr;                   // second branch of an overlapped step (capture only)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t capx[MAX_PARTS] = {};             // branches 1.. of an overlapped step (capture only)
+    cudaEvent_t ev_fwd[MAX_PARTS] = {}, ev_end[MAX_PARTS] = {};
+    bool branches_ready = false;
     cudaEvent_t ev[PIMD_N_STAGES + 1] = {};
     bool stepped = false;
     std::string err;
@@ -588,7 +601,7 @@ void mark(pimd_ctx* c, int i, cudaStream_t st, bool timed)
 bool splits_forces(const pimd_ctx* c)
 {
     const Dev& d = c->d;
-    return d.potential == PIMD_POT_MODEL && d.split_ba > 0 && moment_fast_path(d, dparams(c)) &&
+    return d.potential == PIMD_POT_MODEL && d.n_parts > 1 && moment_fast_path(d, dparams(c)) &&
            network_tiles_available(d);
 }
 
@@ -621,25 +634,26 @@ void eval_forces(pimd_ctx* c, cudaStream_t st, bool timed = false, bool deposit 
         if (d.gfn_wtc) launch_gfn_tc(d, st);
         else launch_gfn(d, st);
         mark(c, PIMD_STAGE_ADJOINT, st, timed);
-    } else if (branch && splits_forces(c) && c->cap2 && c->ev_fork) {
-        // two halves of the bead-atoms as overlapping branches: the second
-        // half's forward starts when the first half's ends, so the first
-        // half's network (latency-bound, short) and adjoint run beside the
-        // second half's forward and network, and every kernel's last wave is
-        // filled by the other branch
+    } else if (branch && splits_forces(c) && c->branches_ready) {
+        // the parts as overlapping branches: part k's forward starts when
+        // part k-1's forward ends, and each part's network (latency-bound,
+        // short) and adjoint follow its forward on its own branch, beside the
+        // next parts' forwards; every kernel's last wave is filled by another
+        // branch
         const void* dp = dparams(c);
-        const int nt = d.rows_pad / TILE_ROWS;
         launch_neighbours(d, st);
-        launch_descriptors_range(d, dp, 0, d.split_ba, st);
-        cudaEventRecord(c->ev_fork, st);
-        cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
-        launch_descriptors_range(d, dp, d.split_ba, d.B, c->cap2);
-        launch_network_tiles(d, 0, d.split_tile, st, true);
-        launch_adjoint_range(d, dp, 0, d.split_ba, st);
-        launch_network_tiles(d, d.split_tile, nt - d.split_tile, c->cap2, true);
-        launch_adjoint_range(d, dp, d.split_ba, d.B, c->cap2);
-        cudaEventRecord(c->ev_join, c->cap2);
-        cudaStreamWaitEvent(st, c->ev_join, 0);
+        for (int k = 0; k < d.n_parts; ++k) {
+            cudaStream_t sk = k == 0 ? st : c->capx[k];
+            if (k > 0) cudaStreamWaitEvent(sk, c->ev_fwd[k - 1], 0);
+            launch_descriptors_range(d, dp, d.part_ba[k], d.part_ba[k + 1], sk);
+            if (k + 1 < d.n_parts) cudaEventRecord(c->ev_fwd[k], sk);
+            launch_network_tiles(d, d.part_tile[k], d.part_tile[k + 1] - d.part_tile[k], sk, true);
+            launch_adjoint_range(d, dp, d.part_ba[k], d.part_ba[k + 1], sk);
+        }
+        for (int k = 1; k < d.n_parts; ++k) {
+            cudaEventRecord(c->ev_end[k], c->capx[k]);
+            cudaStreamWaitEvent(st, c->ev_end[k], 0);
+        }
         if (d.deterministic) launch_force_gather(d, st);
     } else {
         launch_neighbours(d, st);
@@ -708,11 +722,14 @@ int capture(pimd_ctx* c, int nsteps, bool marked, cudaGraphExec_t* out)
     cudaError_t e = cudaSuccess;
     if (!c->cap) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamCreateWithFlags");
-    if (c->d.split_ba > 0 && !c->cap2) {
-        e = cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_check(c, e, "branch stream");
+    if (c->d.n_parts > 1 && !c->branches_ready) {
+        for (int k = 0; k < c->d.n_parts && e == cudaSuccess; ++k) {
+            if (k > 0) e = cudaStreamCreateWithFlags(&c->capx[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fwd[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_end[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_check(c, e, "branch streams");
+        c->branches_ready = true;
     }
     e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaStreamBeginCapture");
@@ -914,8 +931,11 @@ int pimd_create(const pimd_config* cfg, const pimd_replica_desc* reps, int n_rep
     d.perm = (int*)(w + o.perm);
     d.tile_type = (int*)(w + o.tile_type);
     d.rows_pad = b.rows_pad;
-    d.split_ba = b.split_ba;
-    d.split_tile = b.split_tile;
+    d.n_parts = b.part_ba.empty() ? 1 : (int)b.part_ba.size() - 1;
+    for (size_t k = 0; k < b.part_ba.size(); ++k) {
+        d.part_ba[k] = b.part_ba[k];
+        d.part_tile[k] = b.part_tile[k];
+    }
     d.n_types = (int)b.typeZ.size();
     d.n_hidden = cfg->n_hidden;
     d.width = cfg->widths[0];
@@ -1334,7 +1354,7 @@ int pimd_set_overlap(pimd_ctx* c, int on)
     if (!c) return fail(nullptr, PIMD_ERR_INVALID_ARG, "ctx is NULL");
     if (c->overlap != (on != 0)) drop_graphs(c);
     c->overlap = on != 0;
-    return (c->d.split_ba > 0 && network_tiles_available(c->d)) ? 1 : 0;
+    return (c->d.n_parts > 1 && network_tiles_available(c->d)) ? 1 : 0;
 }
 
 int pimd_set_stage_timing(pimd_ctx* c, int on)
@@ -1488,7 +1508,7 @@ int pimd_kernels_per_step(const pimd_ctx* c)
     // network, adjoint (+ force gather), energy unless the adjoint sums it
     // the overlapped halves launch the descriptors, network and adjoint once
     // per half
-    const int halves = c->overlap && splits_forces(c) ? 2 : 1;
+    const int halves = c->overlap && splits_forces(c) ? c->d.n_parts : 1;
     const int nbr = 1 + (d.n_cell_bs ? 1 : 0) + (d.maxcand ? 1 : 0);
     const int energy = adjoint_sums_energy(d, dparams(c)) ? 0 : 1;
     return ring + nbr + 3 * halves + (d.deterministic ? 1 : 0) + energy + md;
@@ -1869,9 +1889,11 @@ void pimd_destroy(pimd_ctx* c)
     cudaStreamSynchronize(c->st);
     drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
-    if (c->cap2) cudaStreamDestroy(c->cap2);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int k = 0; k < MAX_PARTS; ++k) {
+        if (c->capx[k]) cudaStreamDestroy(c->capx[k]);
+        if (c->ev_fwd[k]) cudaEventDestroy(c->ev_fwd[k]);
+        if (c->ev_end[k]) cudaEventDestroy(c->ev_end[k]);
+    }
     for (int i = 0; i <= PIMD_N_STAGES; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     delete c;

@@ -12,6 +12,8 @@
 namespace pimd {
 
 // Device pointers and sizes of one context (all inside the caller's workspace).
+constexpr int MAX_PARTS = 4;   // overlapping parts of a step's force evaluation
+
 struct Dev {
     int R = 0, S = 0, B = 0, NA = 0;   // replicas, bead-systems, bead-atoms, atoms
     int max_N = 0;                     // largest replica
@@ -98,9 +100,12 @@ struct Dev {
     int* tile_type = nullptr;          // [rows_pad / 128]
     int rows_pad = 0;
     // two halves of the bead-atoms (whole bead-systems) for overlapping
-    // branches of the step: bead-atoms [0, split_ba) and [split_ba, B), network
-    // tiles [0, split_tile) and [split_tile, rows_pad / 128); 0 = one branch
-    int split_ba = 0, split_tile = 0;
+    // parts of the step's force evaluation run as overlapping graph branches:
+    // part k owns bead-atoms [part_ba[k], part_ba[k + 1]) and network tiles
+    // [part_tile[k], part_tile[k + 1]); n_parts = 1: one branch
+    int n_parts = 1;
+    int part_ba[MAX_PARTS + 1] = {};
+    int part_tile[MAX_PARTS + 1] = {};
     void* wtc = nullptr;               // tensor-core weight images
     size_t wtc_bytes_per_type = 0;
     float* wtc_vec = nullptr;          // FP32 vectors for the tensor-core epilogues
