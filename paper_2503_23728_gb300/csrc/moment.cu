@@ -90,7 +90,7 @@ static_assert(mono_index(MDEG, 0, 0) == MDEG, "chain order");
 // (row stride 165 floats: odd, so the 32 rows written in one step hit distinct
 // banks) and their weights b_eta
 constexpr int FWD_WARP_FLOATS = 32 * NMONO + 32 * 4;
-constexpr int FWD_WARPS = 4;
+constexpr int FWD_WARPS = 1;
 constexpr int MBLK = 4;   // neighbours per partial sum of the moments
 
 // s += v by Kahan's compensated summation on both halves; nc carries minus
@@ -613,10 +613,10 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
 // loads of Q.
 // ---------------------------------------------------------------------------
 constexpr int ADJ_WARP_BYTES = NMONO * 16 + ND * 4 + NR * 4;   // Q, dE/dG, radial dE/dG x r_mu
-constexpr int ADJ_WARPS = 4;
+constexpr int ADJ_WARPS = 1;
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * ADJ_WARPS, FAST ? 5 : 4) desc_mom_adj_kernel(
+__global__ void __launch_bounds__(32 * ADJ_WARPS, FAST ? 20 : 12) desc_mom_adj_kernel(
     const float4* __restrict__ x, const int* __restrict__ ba_sys, const BeadSys* __restrict__ bsys,
     const Rep* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ nnb, int maxnb, int B,
     DescParams<float> dp, const float4* __restrict__ Min, const float* __restrict__ dEdG,
