@@ -397,18 +397,20 @@ def test_deterministic_mode_resume_is_bit_identical(water64_model, fad_model, wh
 
 
 # ---------------------------------------------------------------- Verlet candidates
-@pytest.mark.parametrize("which,skin", [("ice", 0.5), ("ice", 0.08), ("water", -1.0)])
-def test_verlet_candidates_give_the_same_lists_and_trajectory(water64_model, ice_model, which, skin):
+@pytest.mark.parametrize("which,skin,precision", [("ice", 0.5, "fp32"), ("ice", 0.08, "fp32"), ("water", -1.0, "fp32"),
+                                                  ("ice", 1.5, "bf16_tc"), ("water", -1.0, "bf16_tc")])
+def test_verlet_candidates_give_the_same_lists_and_trajectory(water64_model, ice_model, which, skin, precision):
     """Neighbour lists filtered from Verlet candidates (rebuilt when an atom
     has moved by half the skin) equal a full rebuild every step: deterministic
     trajectories with and without the skin are bit-identical, and the lists
-    match the oracle's at the end."""
+    match the oracle's at the end. On the BF16 moment path the descriptor
+    forward filters the candidates itself."""
     P = _P()
     w, r, m = ice_model if which == "ice" else water64_model
     rep = _with_beads(r, 4)
     out = []
     for sk in (skin, 0.0):
-        ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths, deterministic=True,
+        ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision=precision, widths=w.widths, deterministic=True,
                         nbr_skin=sk)
         ctx.set_weights(m)
         ctx.step(40)
@@ -423,15 +425,17 @@ def test_verlet_candidates_give_the_same_lists_and_trajectory(water64_model, ice
         assert np.array_equal(out[0][3][b, :n], out[1][3][b, :n])
 
 
-def test_verlet_candidate_overflow_falls_back(ice_model):
+@pytest.mark.parametrize("precision", ["fp32", "bf16_tc"])
+def test_verlet_candidate_overflow_falls_back(ice_model, precision):
     """Candidate slots too few for r_c + skin (ice, 96 neighbour slots, 144
     candidate slots, skin 1.2 A: ~149 candidates): the affected atoms scan
-    directly, lists still exact."""
+    directly, lists still exact (on the BF16 moment path the forward filters
+    the candidates of the other atoms)."""
     P = _P()
     w, r, m = ice_model
     rep = _with_beads(r, 2)
     xb = _bead_positions(rep, 2, seed=41)
-    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision="fp32", widths=w.widths, max_neighbours=96,
+    ctx = P.Context([rep], w.dt_fs, w.gamma0_per_fs, precision=precision, widths=w.widths, max_neighbours=96,
                     nbr_skin=1.2)
     ctx.set_weights(m)
     ctx.energy_forces(torch.tensor(xb.reshape(-1, 3), device="cuda"))
