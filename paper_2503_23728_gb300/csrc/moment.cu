@@ -311,6 +311,10 @@ constexpr int NRED = 81;
 
 struct alignas(16) RedTab {
     short up[7][32][4];           // level a = 2..8: (m_abc, m_(a-2)bc, m_(a-2)(b+2)c, m_(a-2)b(c+2)), -1 idle
+    // the same entries in 5 slots per lane over 4 rounds: levels a and a + 1
+    // both read level a - 2 and a - 1 only, so they share a round (slots
+    // 0-1: a = 2, 3; slot 2: a = 4, 5; slot 3: a = 6, 7; slot 4: a = 8)
+    short upr[5][32][4];
     short down[7][2][32][4];      // level a = 8..2: target m_(a-2)BC and sources (a,B,C), (a,B-2,C), (a,B,C-2)
 };
 
@@ -329,6 +333,22 @@ constexpr RedTab make_red_tab()
                 t.up[L][q][2] = (short)mono_index(a - 2, b + 2, c);
                 t.up[L][q][3] = (short)mono_index(a - 2, b, c + 2);
             }
+    }
+    {
+        int q[4] = {0, 0, 0, 0};   // entries placed per round
+        const int first_slot[4] = {0, 2, 3, 4};
+        for (int sl = 0; sl < 5; ++sl)
+            for (int i = 0; i < 32; ++i)
+                for (int k = 0; k < 4; ++k) t.upr[sl][i][k] = -1;
+        for (int L = 0; L < 7; ++L) {
+            const int rd = L / 2;
+            for (int i = 0; i < 32; ++i) {
+                if (t.up[L][i][0] < 0) continue;
+                const int pos = q[rd]++;
+                const int sl = first_slot[rd] + pos / 32;
+                for (int k = 0; k < 4; ++k) t.upr[sl][pos % 32][k] = t.up[L][i][k];
+            }
+        }
     }
     for (int L = 0; L < 7; ++L) {
         const int a = MDEG - L;   // 8 .. 2
@@ -569,6 +589,10 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
 #pragma unroll
     for (int e = 0; e < 4; ++e) diag[e] = warp_sum(dg[e]);
 
+    // the recurrence's table entries, loaded before the sums they wait for
+    short4 ue[5];
+#pragma unroll
+    for (int sl = 0; sl < 5; ++sl) ue[sl] = *reinterpret_cast<const short4*>(g_red.upr[sl][lane]);
     // the two halves' sums; then half 0 stores the moments of (0, b, c) and
     // half 1 those of (1, b, c) (rows of the last chunk are no longer needed)
     float4* T = reinterpret_cast<float4*>(ROW);
@@ -586,13 +610,13 @@ __global__ void __launch_bounds__(32 * FWDR_WARPS, 20) desc_mom_fwd_red_kernel(
     }
     __syncwarp();
 #pragma unroll
-    for (int L = 0; L < 7; ++L) {
-        const short4 e = *reinterpret_cast<const short4*>(g_red.up[L][lane]);   // one 8-byte load
+    for (int sl = 0; sl < 5; ++sl) {
+        const short4 e = ue[sl];
         if (e.x >= 0) {
             const float4 a0 = T[e.y], a1 = T[e.z], a2 = T[e.w];
             T[e.x] = make_float4(a0.x - a1.x - a2.x, a0.y - a1.y - a2.y, a0.z - a1.z - a2.z, a0.w - a1.w - a2.w);
         }
-        __syncwarp();
+        if (sl != 0) __syncwarp();   // slots 0 and 1 form one round
     }
     float2 full[MSLOT][2];
 #pragma unroll
