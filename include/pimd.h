@@ -394,18 +394,18 @@ int pimd_set_forces(pimd_ctx* ctx, const double* f);
 int pimd_ring_start(pimd_ctx* ctx, double* x);
 int pimd_ring_finish(pimd_ctx* ctx, const double* f);
 
-/* Overlapped halves (default on). Contexts of at least 16,384 bead-atoms on
+/* Overlapped parts (default on). Contexts of at least 16,384 bead-atoms on
  * the BF16 path with networks of width 64 or 128 (whose hidden activations
- * fit in tensor memory) split their bead-atoms into two halves of whole
- * beads; a
- * step then runs the first half's network and adjoint beside the second
- * half's descriptors and network (two branches of the step's graph), so the
- * network's short latency-bound launches and the last waves of every kernel
- * are filled with the other half's work. Results are the same either way
- * (every bead-atom's arithmetic is unchanged). Steps that carry the stage
- * markers always run the halves one after the other. Returns 1 when the
- * context has halves, 0 when it runs one branch anyway, < 0 on error. The
- * paper has no counterpart (a scheduling choice).                          */
+ * fit in tensor memory) split their bead-atoms into two parts of whole
+ * beads, the first with about 3/8 of the bead-atoms; a step then runs the
+ * first part's network and adjoint beside the second part's descriptors and
+ * network (two branches of the step's graph), so the network's short
+ * latency-bound launches and the last waves of every kernel are filled with
+ * the other part's work. Results are the same either way (every
+ * bead-atom's arithmetic is unchanged). Steps that carry the stage markers
+ * always run the parts one after the other. Returns 1 when the context has
+ * parts, 0 when it runs one branch anyway, < 0 on error. The paper has no
+ * counterpart (a scheduling choice).                                       */
 int pimd_set_overlap(pimd_ctx* ctx, int on);
 
 /* Stage timing on (default for cfg.timing contexts) or off. The event
