@@ -164,7 +164,7 @@ def run_gpu(a, workload, precision, model=None):
     else:
         ctx.set_weights(model)
     if not a.no_tune:
-        # angular method, pair schedule and overlapped halves, measured on
+        # angular method, pair schedule and overlapped parts, measured on
         # this workload during set-up (not timed); no cache, so every run
         # measures afresh
         from paper_2503_23728_gb300 import tuner

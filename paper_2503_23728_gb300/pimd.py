@@ -608,8 +608,8 @@ class Context:
         _check(load().pimd_ring_finish(self.h, ct.c_void_p(f.data_ptr())), self.h)
 
     def set_overlap(self, on: bool) -> bool:
-        """Overlapped halves of the bead-atoms in the step's graph; returns
-        whether this context has halves."""
+        """Overlapped parts of the bead-atoms in the step's graph; returns
+        whether this context has parts."""
         rc = load().pimd_set_overlap(self.h, 1 if on else 0)
         if rc < 0:
             _check(rc, self.h)

@@ -6,7 +6,7 @@ For a context it chooses, by timing them on the live workload:
     moment-tensor adjoint its residency, 12 or 16 warps per SM (`pimd_tune`,
     which times the descriptor forward and the adjoint of every candidate
     with CUDA events);
-  * whether the step runs the two halves of its bead-atoms as overlapping
+  * whether the step runs the two parts of its bead-atoms as overlapping
     branches of its graph (`pimd_set_overlap`), from whole-step timings.
 The choices are stored in a JSON file under a key of the workload's shape:
 atoms and beads of every replica (sorted multiset), the network widths and
@@ -118,7 +118,7 @@ def tune(ctx, cache: str | None = DEFAULT_CACHE, reps: int = 3, steps: int = 10,
     choice = {"angular": kern["angular"], "band_length": int(kern["band_length"]),
               "adjoint_warps": int(kern.get("adjoint_warps", 12)),
               "kernels_ms": float(kern["best_ms"]), "mean_neighbours": nb}
-    # overlapped halves, from whole-step timings (state restored afterwards)
+    # overlapped parts, from whole-step timings (state restored afterwards)
     q, p, step, Q = ctx.get_state()
     has = ctx.set_overlap(True)
     choice["overlap"] = has
