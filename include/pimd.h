@@ -594,12 +594,11 @@ int pimd_metad_fes(pimd_ctx* ctx, int replica, const double* s, int n, double* F
  * PIMD_NOALLOC_MAX_ATOMS and neighbours per atom to PIMD_NOALLOC_MAX_NEIGHBOURS;
  * larger inputs fail with INVALID_ARG, overfull neighbour lists with
  * NBR_OVERFLOW. No cudaMalloc, cudaFree or allocating library routine runs.
- * Each call looks up the array's address on the current device
- * (cudaGetSymbolAddress) and blocks: it synchronises `stream` to read the
- * neighbour-overflow flag, so it cannot be captured into a CUDA graph. All
- * calls share the one array, so calls that overlap on the GPU (other
- * threads, other streams) race with each other; serialise them. Error text:
- * pimd_last_error(NULL).                                                    */
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture. All calls share the one array, so calls that
+ * overlap on the GPU (other threads, other streams) race with each other;
+ * serialise them. Error text: pimd_last_error(NULL).                        */
 #define PIMD_NOALLOC_MAX_ATOMS 4096
 #define PIMD_NOALLOC_MAX_NEIGHBOURS 128
 int pimd_descriptors_noalloc(const double* x_dev, int n_atoms, const double* box, double cutoff_A,

@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "../../include/pimd.h"
@@ -38,6 +39,9 @@ constexpr size_t SCRATCH_BYTES = OFF_ERR + al(sizeof(DevErr));
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
+std::mutex g_mu;
+void* g_addr[256] = {};   // device address of g_noalloc_scratch, per device ordinal
+
 // message for pimd_last_error(NULL)
 int fail(int code, const std::string& m)
 {
@@ -47,16 +51,26 @@ int fail(int code, const std::string& m)
 
 int scratch_address(void** out)
 {
-    // host code only holds a stand-in for the symbol: ask the runtime for its
-    // address on the current device, on every call (no cache that a device
-    // reset or a reload of the module would leave stale)
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(PIMD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return fail(PIMD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     }
-    *out = p;
+    if (dev < 0 || dev >= 256) return fail(PIMD_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        // host code only holds a stand-in for the symbol: ask the runtime for
+        // its address on the current device
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PIMD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        }
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
     return PIMD_OK;
 }
 
