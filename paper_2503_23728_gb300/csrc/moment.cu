@@ -115,12 +115,14 @@ __device__ __forceinline__ void finish_moments(const float2 (&acc)[MSLOT][2], co
 {
     if (Mout != nullptr) {
         // the last slot's lanes past the 165th monomial hold nothing (the
-        // adjoints read only the 165)
+        // adjoints read only the 165); streaming (evict-first) stores, so the
+        // moments do not push the lists and positions the adjoint reads out
+        // of L2
 #pragma unroll
         for (int k = 0; k < MSLOT; ++k)
             if (k < MSLOT - 1 || lane < (unsigned)MLAST)
-                Mout[((size_t)b * MSLOT + k) * 32 + lane] =
-                    make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y);
+                __stcs(&Mout[((size_t)b * MSLOT + k) * 32 + lane],
+                       make_float4(acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y));
     }
 
     // per lane: its monomials' share of sum_abc 2^-zeta w lambda^s M^2, packed
